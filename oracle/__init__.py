@@ -1,0 +1,381 @@
+"""FP64 CPU oracle (test infrastructure).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It wraps ``oracle.c`` (plain C, FP64,
+compiled by :func:`build`) and composes the shading networks from its
+convolution primitives.  Every function follows a passage of the paper
+(arXiv 2202.05628):
+
+* :func:`fk`, :func:`lbs` - skeleton S = {r, R, T} and linear blend skinning,
+  Sec. 3.1 "Rigging and Deformation", Eq. 4.
+* :func:`render`, :func:`pixels`, :func:`pixel_brute` - exact ray / warped-voxel
+  hits and front-to-back compositing into the feature map F and coarse opacity
+  map A, Sec. 3.1 "Dynamic Volume Rendering", Eq. 5-6 and the early-stop rule.
+* :func:`tile_pairs` - screen-tile coverage of the warped voxels (the per-frame
+  indexing step that replaces the paper's octree rebuild).
+* :func:`shade_tiny`, :func:`shade_unet` - the neural shading network,
+  Sec. 3.1 "Neural Shading" (single-branch "Light" form, Sec. 6 "Runtime
+  Analysis").
+* :func:`render_backward`, :func:`lbs_backward` - gradients of Eq. 5-6 and
+  Eq. 4 (the paper optimises the feature table end to end).
+
+Pins: each of these is checked in ``tests/test_oracle_pins.py`` against
+closed forms, brute force, invariants and library routines.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lib = None
+_lock = threading.Lock()
+
+TAU_DEFAULT = 1e-4
+
+
+def build(force: bool = False) -> str:
+    """Compile ``oracle.c`` into ``liboracle.so`` (gcc, FP64, OpenMP when available)."""
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    base = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _L():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            _lib = ctypes.CDLL(_LIB_PATH)
+            _lib.orc_render.restype = ctypes.c_int64
+            _lib.orc_tile_pairs.restype = ctypes.c_int64
+    return _lib
+
+
+def num_threads() -> int:
+    return int(_L().orc_num_threads())
+
+
+class _Scene(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("C", ctypes.c_int), ("h", ctypes.c_double),
+                ("origin", ctypes.c_double * 3), ("ijk", ctypes.c_void_p), ("A", ctypes.c_void_p),
+                ("feat", ctypes.c_void_p), ("sigma", ctypes.c_void_p)]
+
+
+class _Cam(ctypes.Structure):
+    _fields_ = [("W", ctypes.c_int), ("H", ctypes.c_int), ("fx", ctypes.c_double),
+                ("fy", ctypes.c_double), ("cx", ctypes.c_double), ("cy", ctypes.c_double),
+                ("w2c", ctypes.c_double * 12), ("near_", ctypes.c_double), ("far_", ctypes.c_double)]
+
+
+def _p(a: Optional[np.ndarray]):
+    return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+class _Bound:
+    """Keeps the numpy arrays alive while C holds pointers to them."""
+
+    def __init__(self, octree, A: np.ndarray, features=None, density=None):
+        self.ijk = np.ascontiguousarray(octree.ijk, dtype=np.uint16)
+        self.A = _f64(A)
+        self.feat = _f64(octree.features if features is None else features)
+        self.sigma = _f64(octree.density if density is None else density)
+        s = _Scene()
+        s.n = self.ijk.shape[0]
+        s.C = self.feat.shape[1]
+        s.h = float(octree.extent) / float(1 << octree.depth)
+        for a in range(3):
+            s.origin[a] = float(octree.origin[a])
+        s.ijk, s.A, s.feat, s.sigma = (self.ijk.ctypes.data, self.A.ctypes.data,
+                                       self.feat.ctypes.data, self.sigma.ctypes.data)
+        self.s = s
+
+
+def _cam(c) -> _Cam:
+    k = _Cam()
+    k.W, k.H = int(c.W), int(c.H)
+    k.fx, k.fy, k.cx, k.cy = float(c.fx), float(c.fy), float(c.cx), float(c.cy)
+    m = np.asarray(c.world_to_cam, np.float64).reshape(12)
+    for i in range(12):
+        k.w2c[i] = float(m[i])
+    k.near_, k.far_ = float(c.near), float(c.far)
+    return k
+
+
+# ---------------------------------------------------------------------------
+# Eq. 4: skeleton and LBS
+# ---------------------------------------------------------------------------
+
+def rodrigues(r) -> np.ndarray:
+    out = np.zeros(9)
+    _L().orc_rodrigues(_p(_f64(r)), _p(out))
+    return out.reshape(3, 3)
+
+
+def fk(skeleton, pose) -> np.ndarray:
+    """G_j = M^t_j (M^c_j)^-1 for every joint, [J,3,4] FP64."""
+    J = skeleton.J
+    G = np.zeros((J, 12))
+    parent = np.ascontiguousarray(skeleton.parent, dtype=np.int32)
+    rest, aa = _f64(skeleton.rest), _f64(pose.axis_angle)
+    R, T = _f64(pose.R), _f64(pose.T)
+    rc = _L().orc_fk(ctypes.c_int(J), _p(parent), _p(rest), _p(aa), _p(R), _p(T), _p(G))
+    if rc != 0:
+        raise ValueError(f"orc_fk failed ({rc}): parent[j] must be < j with a single root 0")
+    return G.reshape(J, 3, 4)
+
+
+def lbs(octree, G: np.ndarray, weights=None) -> Tuple[np.ndarray, np.ndarray]:
+    """A_i = sum_k w_ik G_{j_ik} ([N,3,4]) and det of its 3x3 block ([N])."""
+    n = octree.n
+    G = _f64(G).reshape(-1, 12)
+    jidx = np.ascontiguousarray(octree.joint_idx, dtype=np.uint8)
+    w = _f64(octree.weights if weights is None else weights)
+    A = np.zeros((n, 12))
+    det = np.zeros(n)
+    _L().orc_lbs(ctypes.c_int64(n), ctypes.c_int(G.shape[0]), _p(G), _p(jidx), _p(w), _p(A), _p(det))
+    return A.reshape(n, 3, 4), det
+
+
+def pose_transforms(scene, pose, weights=None):
+    G = fk(scene.skeleton, pose)
+    A, det = lbs(scene.octree, G, weights)
+    return G, A, det
+
+
+# ---------------------------------------------------------------------------
+# Eq. 5-6: rays, hits, compositing
+# ---------------------------------------------------------------------------
+
+def pixel_ray(cam, x: int, y: int) -> Tuple[np.ndarray, np.ndarray]:
+    o, d = np.zeros(3), np.zeros(3)
+    k = _cam(cam)
+    _L().orc_pixel_ray(ctypes.byref(k), ctypes.c_int(x), ctypes.c_int(y), _p(o), _p(d))
+    return o, d
+
+
+def render(octree, A: np.ndarray, cam, tau: float = TAU_DEFAULT, hits: bool = False,
+           features=None, density=None) -> dict:
+    """Feature map F [H,W,C], coarse opacity A [H,W], per-pixel hit counts and,
+    with ``hits=True``, the ordered per-pixel hit lists (CSR)."""
+    b = _Bound(octree, np.asarray(A).reshape(-1, 12), features, density)
+    k = _cam(cam)
+    H, W, C = cam.H, cam.W, b.feat.shape[1]
+    F = np.zeros((H, W, C))
+    Am = np.zeros((H, W))
+    nhit = np.zeros((H, W), np.int32)
+    nused = np.zeros((H, W), np.int32)
+    L = _L()
+    out = dict(F=F, A=Am, nhit=nhit, nused=nused)
+    if not hits:
+        r = L.orc_render(ctypes.byref(b.s), ctypes.byref(k), ctypes.c_double(tau), _p(F), _p(Am),
+                         _p(nhit), _p(nused), None, None, None, None, ctypes.c_int64(0))
+        if r < 0:
+            raise MemoryError("orc_render failed")
+        return out
+    cap = int(1.5 * 64 * H * W) + 1024
+    while True:
+        off = np.zeros(H * W + 1, np.int64)
+        hid = np.zeros(cap, np.int64)
+        t0 = np.zeros(cap)
+        t1 = np.zeros(cap)
+        r = L.orc_render(ctypes.byref(b.s), ctypes.byref(k), ctypes.c_double(tau), _p(F), _p(Am),
+                         _p(nhit), _p(nused), _p(off), _p(hid), _p(t0), _p(t1), ctypes.c_int64(cap))
+        if r >= 0:
+            break
+        if r < -(1 << 40):
+            raise MemoryError("orc_render failed")
+        cap = int(-r) + 16
+    out.update(hit_off=off, hit_id=hid[:r], hit_t0=t0[:r], hit_t1=t1[:r])
+    return out
+
+
+def pixels(octree, A: np.ndarray, cam, px: Sequence[int], py: Sequence[int],
+           tau: float = TAU_DEFAULT, features=None, density=None) -> dict:
+    """Sampled pixels, each by brute force over every voxel."""
+    b = _Bound(octree, np.asarray(A).reshape(-1, 12), features, density)
+    k = _cam(cam)
+    px = np.ascontiguousarray(px, np.int32)
+    py = np.ascontiguousarray(py, np.int32)
+    m = px.shape[0]
+    F = np.zeros((m, b.feat.shape[1]))
+    Am = np.zeros(m)
+    nh = np.zeros(m, np.int32)
+    _L().orc_pixels(ctypes.byref(b.s), ctypes.byref(k), ctypes.c_int64(m), _p(px), _p(py),
+                    ctypes.c_double(tau), _p(F), _p(Am), _p(nh))
+    return dict(F=F, A=Am, nhit=nh)
+
+
+def pixel_brute(octree, A: np.ndarray, cam, x: int, y: int, tau: float = TAU_DEFAULT,
+                features=None, density=None, cap: int = 4096) -> dict:
+    b = _Bound(octree, np.asarray(A).reshape(-1, 12), features, density)
+    k = _cam(cam)
+    F = np.zeros(b.feat.shape[1])
+    Am = np.zeros(1)
+    ids = np.zeros(cap, np.int64)
+    t0 = np.zeros(cap)
+    t1 = np.zeros(cap)
+    used = ctypes.c_int(0)
+    m = _L().orc_pixel_brute(ctypes.byref(b.s), ctypes.byref(k), ctypes.c_int(x), ctypes.c_int(y),
+                             ctypes.c_double(tau), _p(F), _p(Am), _p(ids), _p(t0), _p(t1),
+                             ctypes.c_int(cap), ctypes.byref(used))
+    m2 = min(m, cap)
+    return dict(F=F, A=float(Am[0]), ids=ids[:m2], t0=t0[:m2], t1=t1[:m2], nhit=m, nused=used.value)
+
+
+def tile_pairs(octree, A: np.ndarray, cam, ts: int = 16) -> Tuple[np.ndarray, np.ndarray]:
+    """(tile id, voxel id) pairs of the screen-tile coverage, voxel-major."""
+    b = _Bound(octree, np.asarray(A).reshape(-1, 12))
+    k = _cam(cam)
+    cap = 4 * octree.n + 1024
+    while True:
+        tile = np.zeros(cap, np.int32)
+        vid = np.zeros(cap, np.int64)
+        r = _L().orc_tile_pairs(ctypes.byref(b.s), ctypes.byref(k), ctypes.c_int(ts), _p(tile),
+                                _p(vid), ctypes.c_int64(cap))
+        if r >= 0:
+            return tile[:r], vid[:r]
+        if r < -(1 << 40):
+            raise MemoryError("orc_tile_pairs failed")
+        cap = int(-r) + 16
+
+
+def voxel_bounds(octree, A: np.ndarray, cam) -> np.ndarray:
+    """Per voxel: ok, umin, umax, vmin, vmax, dmin, dmax (FP64)."""
+    b = _Bound(octree, np.asarray(A).reshape(-1, 12))
+    out = np.zeros((octree.n, 7))
+    _L().orc_voxel_bounds(ctypes.byref(b.s), ctypes.byref(_cam(cam)), _p(out))
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Gradients (project addition, see module docstring)
+# ---------------------------------------------------------------------------
+
+def render_backward(octree, A: np.ndarray, cam, gF: np.ndarray, gA: np.ndarray,
+                    tau: float = TAU_DEFAULT, features=None, density=None):
+    """dL/df [N,C], dL/dsigma [N], dL/dAinv [N,3,4] for upstream gF, gA."""
+    b = _Bound(octree, np.asarray(A).reshape(-1, 12), features, density)
+    k = _cam(cam)
+    n, C = octree.n, b.feat.shape[1]
+    gfeat = np.zeros((n, C))
+    gsig = np.zeros(n)
+    gAi = np.zeros((n, 12))
+    rc = _L().orc_render_backward(ctypes.byref(b.s), ctypes.byref(k), ctypes.c_double(tau),
+                                  _p(_f64(gF)), _p(_f64(gA)), _p(gfeat), _p(gsig), _p(gAi))
+    if rc != 0:
+        raise MemoryError("orc_render_backward failed")
+    return gfeat, gsig, gAi.reshape(n, 3, 4)
+
+
+def lbs_backward(octree, G: np.ndarray, A: np.ndarray, gAinv: np.ndarray):
+    """dL/dA [N,3,4] and dL/dw [N,4] from dL/dAinv."""
+    n = octree.n
+    G = _f64(G).reshape(-1, 12)
+    jidx = np.ascontiguousarray(octree.joint_idx, dtype=np.uint8)
+    gA = np.zeros((n, 12))
+    gw = np.zeros((n, 4))
+    _L().orc_lbs_backward(ctypes.c_int64(n), ctypes.c_int(G.shape[0]), _p(G), _p(jidx),
+                          _p(_f64(A).reshape(-1, 12)), _p(_f64(gAinv).reshape(-1, 12)), _p(gA), _p(gw))
+    return gA.reshape(n, 3, 4), gw
+
+
+# ---------------------------------------------------------------------------
+# Neural shading (Sec. 3.1 "Neural Shading")
+# ---------------------------------------------------------------------------
+
+ACT_NONE, ACT_RELU, ACT_SIGMOID = 0, 1, 2
+
+
+def conv2d(x: np.ndarray, w: np.ndarray, b: Optional[np.ndarray], act: int) -> np.ndarray:
+    """x [H,W,Cin], w [Cout,k,k,Cin], zero 'same' padding."""
+    x = _f64(x)
+    w = _f64(w)
+    H, W, Cin = x.shape
+    Cout, k = w.shape[0], w.shape[1]
+    assert w.shape == (Cout, k, k, Cin)
+    out = np.zeros((H, W, Cout))
+    bb = None if b is None else _f64(b)
+    _L().orc_conv2d(ctypes.c_int(H), ctypes.c_int(W), ctypes.c_int(Cin), ctypes.c_int(Cout),
+                    ctypes.c_int(k), _p(x), _p(w), _p(bb), _p(out), ctypes.c_int(act))
+    return out
+
+
+def maxpool2(x: np.ndarray) -> np.ndarray:
+    x = _f64(x)
+    H, W, C = x.shape
+    out = np.zeros((H // 2, W // 2, C))
+    _L().orc_maxpool2(ctypes.c_int(H), ctypes.c_int(W), ctypes.c_int(C), _p(x), _p(out))
+    return out
+
+
+def upsample2(x: np.ndarray) -> np.ndarray:
+    x = _f64(x)
+    H, W, C = x.shape
+    out = np.zeros((2 * H, 2 * W, C))
+    _L().orc_upsample2(ctypes.c_int(H), ctypes.c_int(W), ctypes.c_int(C), _p(x), _p(out))
+    return out
+
+
+def shade_tiny(F: np.ndarray, layers) -> np.ndarray:
+    """conv3x3 + ReLU, conv3x3 + ReLU, conv3x3 + sigmoid -> RGBA [H,W,4]."""
+    (w0, b0), (w1, b1), (w2, b2) = layers
+    x = conv2d(F, w0, b0, ACT_RELU)
+    x = conv2d(x, w1, b1, ACT_RELU)
+    return conv2d(x, w2, b2, ACT_SIGMOID)
+
+
+def shade_unet(F: np.ndarray, layers) -> np.ndarray:
+    """4-level U-Net: per level two conv3x3 + ReLU; 2x2 max-pool down; nearest
+    x2 up, concatenation [upsampled, skip] on channels, two conv3x3 + ReLU;
+    1x1 head + sigmoid -> RGBA [H,W,4]."""
+    it = iter(layers)
+
+    def block(x):
+        w, b = next(it)
+        x = conv2d(x, w, b, ACT_RELU)
+        w, b = next(it)
+        return conv2d(x, w, b, ACT_RELU)
+
+    e0 = block(F)
+    e1 = block(maxpool2(e0))
+    e2 = block(maxpool2(e1))
+    e3 = block(maxpool2(e2))
+    d2 = block(np.concatenate([upsample2(e3), e2], axis=2))
+    d1 = block(np.concatenate([upsample2(d2), e1], axis=2))
+    d0 = block(np.concatenate([upsample2(d1), e0], axis=2))
+    w, b = next(it)
+    return conv2d(d0, w, b, ACT_SIGMOID)
+
+
+def shade(F: np.ndarray, layers) -> np.ndarray:
+    return shade_tiny(F, layers) if len(layers) == 3 else shade_unet(F, layers)
+
+
+def render_frame(scene, pose, cam, layers=None, tau: float = TAU_DEFAULT) -> dict:
+    """Whole path for one view: FK, LBS, F and A maps, RGBA."""
+    G, A, det = pose_transforms(scene, pose)
+    out = render(scene.octree, A, cam, tau)
+    out["G"], out["Ablend"], out["det"] = G, A, det
+    if layers is not None:
+        out["rgba"] = shade(out["F"], layers)
+    return out

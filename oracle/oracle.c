@@ -1,0 +1,794 @@
+/*
+ * FP64 CPU oracle for the ARTEMIS neural-animal rendering path
+ * (arXiv 2202.05628, Sec. 3.1).  TEST INFRASTRUCTURE ONLY: it is called by
+ * the tests, by __graft_entry__.smoke() and by the CPU-baseline leg of the
+ * benchmark, never by the product path.  It shares no code with the CUDA
+ * library.
+ *
+ * Plain, slow, direct evaluation of:
+ *   - forward kinematics of the skeleton S = {r, R, T}        (Sec. 3.1, Eq. 4)
+ *   - linear blend skinning A_i = sum_k w_ik M^t_j (M^c_j)^-1  (Eq. 4)
+ *   - pinhole rays through pixel centres                     (Sec. 3.1, "Dynamic Volume Rendering")
+ *   - exact ray / warped-voxel intersection, chord delta_i    (Eq. 6, "distance of the ray travelling through a voxel")
+ *   - front-to-back compositing F = sum_i T_i (1 - exp(-sigma_i delta_i)) f_i,
+ *     T_i = exp(-sum_{j<i} sigma_j delta_j), A = 1 - T_final,
+ *     early stop once T < tau                                  (Eq. 5, Eq. 6, early-stop paragraph)
+ *   - direct convolutions of the shading network              (Sec. 3.1, "Neural Shading")
+ *   - the analytic gradient of the composite with respect to features,
+ *     densities and the blended transforms, and of LBS with respect to the
+ *     skinning weights (project addition; the paper trains end to end).
+ *
+ * Readings where the paper is silent or garbled (listed in the design doc):
+ *   - T_i uses the exclusive sum j < i (Eq. 6 prints j <= i; with j < i the
+ *     accumulated alpha equals 1 - T_final, which is how the coarse opacity
+ *     map is defined).
+ *   - the warped voxel is the parallelepiped A_i * (canonical cube); the ray is
+ *     mapped into the canonical frame by A_i^-1 (not renormalised, so the ray
+ *     parameter t is preserved) and slab-tested against the cube.
+ *   - hits are ordered by (t0, t1, voxel id); the stop test follows each hit.
+ *   - a voxel whose blended linear part has det < 1e-3, or any of whose eight
+ *     warped corners has camera z <= 1e-6, is not rendered.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_DET_MIN 1e-3
+#define ORC_Z_MIN 1e-6
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------------ */
+/* Small matrix helpers (row-major 3x3 and 3x4).                              */
+/* ------------------------------------------------------------------------ */
+
+/* Rodrigues' formula R = I + sin(th) K + (1 - cos(th)) K^2, K = [axis]_x. */
+void orc_rodrigues(const double r[3], double R[9]) {
+  double th = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+  memset(R, 0, 9 * sizeof(double));
+  R[0] = R[4] = R[8] = 1.0;
+  if (th == 0.0) return;
+  double k[3] = {r[0] / th, r[1] / th, r[2] / th};
+  double K[9] = {0, -k[2], k[1], k[2], 0, -k[0], -k[1], k[0], 0};
+  double K2[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double s = 0;
+      for (int m = 0; m < 3; ++m) s += K[i * 3 + m] * K[m * 3 + j];
+      K2[i * 3 + j] = s;
+    }
+  double s = sin(th), c = 1.0 - cos(th);
+  for (int i = 0; i < 9; ++i) R[i] += s * K[i] + c * K2[i];
+}
+
+/* C = A * B for 3x4 affine matrices (implicit bottom row 0 0 0 1). */
+static void affine_mul(const double A[12], const double B[12], double C[12]) {
+  for (int i = 0; i < 3; ++i) {
+    for (int j = 0; j < 4; ++j) {
+      double s = (j == 3) ? A[i * 4 + 3] : 0.0;
+      for (int m = 0; m < 3; ++m) s += A[i * 4 + m] * B[m * 4 + j];
+      C[i * 4 + j] = s;
+    }
+  }
+}
+
+static double det3(const double* A, int ld) {
+  /* determinant of the 3x3 block of a matrix with leading dimension ld */
+  return A[0] * (A[ld + 1] * A[2 * ld + 2] - A[ld + 2] * A[2 * ld + 1]) -
+         A[1] * (A[ld] * A[2 * ld + 2] - A[ld + 2] * A[2 * ld]) +
+         A[2] * (A[ld] * A[2 * ld + 1] - A[ld + 1] * A[2 * ld]);
+}
+
+/* Inverse of a 3x4 affine matrix via the adjugate of its 3x3 block. */
+static int affine_inv(const double A[12], double Ai[12]) {
+  double d = det3(A, 4);
+  if (d == 0.0) return 0;
+  double a = A[0], b = A[1], c = A[2];
+  double e = A[4], f = A[5], g = A[6];
+  double h = A[8], i = A[9], k = A[10];
+  double inv[9] = {(f * k - g * i), -(b * k - c * i), (b * g - c * f),
+                   -(e * k - g * h), (a * k - c * h), -(a * g - c * e),
+                   (e * i - f * h), -(a * i - b * h), (a * f - b * e)};
+  for (int r = 0; r < 3; ++r) {
+    for (int s = 0; s < 3; ++s) Ai[r * 4 + s] = inv[r * 3 + s] / d;
+    Ai[r * 4 + 3] = -(Ai[r * 4 + 0] * A[3] + Ai[r * 4 + 1] * A[7] + Ai[r * 4 + 2] * A[11]);
+  }
+  return 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Forward kinematics and LBS (Eq. 4).                                        */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Skeleton S = {r, R, T}: joint j has local transform [Rod(r_j) | rest_j -
+ * rest_parent] (root: [Rod(r_0) | rest_0], premultiplied by the global
+ * [Rod(R) | T]).  M^t_j = M^t_parent * local_j; canonical M^c_j = [I | rest_j]
+ * (zero joint rotations).  Output G_j = M^t_j (M^c_j)^-1 as 3x4 row-major.
+ * Requires parent[j] < j.  Returns 0 on success, -1 on a bad parent array.
+ */
+int orc_fk(int J, const int32_t* parent, const double* rest, const double* axis_angle,
+           const double Rg[3], const double T[3], double* G) {
+  double* M = (double*)malloc(sizeof(double) * 12 * (size_t)J);
+  if (!M) return -2;
+  double glob[12], Rm[9];
+  orc_rodrigues(Rg, Rm);
+  for (int i = 0; i < 3; ++i) {
+    for (int j = 0; j < 3; ++j) glob[i * 4 + j] = Rm[i * 3 + j];
+    glob[i * 4 + 3] = T[i];
+  }
+  for (int j = 0; j < J; ++j) {
+    int p = parent[j];
+    if (p >= j || (p < 0 && p != -1) || (j > 0 && p < 0) || (j == 0 && p != -1)) {
+      free(M);
+      return -1;
+    }
+    double local[12];
+    orc_rodrigues(axis_angle + 3 * j, Rm);
+    for (int a = 0; a < 3; ++a) {
+      for (int b = 0; b < 3; ++b) local[a * 4 + b] = Rm[a * 3 + b];
+      local[a * 4 + 3] = rest[3 * j + a] - (p >= 0 ? rest[3 * p + a] : 0.0);
+    }
+    affine_mul(p >= 0 ? M + 12 * p : glob, local, M + 12 * j);
+    /* G_j = M^t_j [I | -rest_j] */
+    double Minv_c[12] = {1, 0, 0, -rest[3 * j], 0, 1, 0, -rest[3 * j + 1], 0, 0, 1, -rest[3 * j + 2]};
+    affine_mul(M + 12 * j, Minv_c, G + 12 * j);
+  }
+  free(M);
+  return 0;
+}
+
+/* A_i = sum_{k<4} w_ik G_{j_ik} (not re-orthonormalised); det of its 3x3 block. */
+void orc_lbs(int64_t n, int J, const double* G, const uint8_t* jidx, const double* w, double* A,
+             double* det) {
+  for (int64_t i = 0; i < n; ++i) {
+    double* a = A + 12 * i;
+    for (int m = 0; m < 12; ++m) a[m] = 0.0;
+    for (int k = 0; k < 4; ++k) {
+      int j = jidx[4 * i + k];
+      double wk = w[4 * i + k];
+      if (j >= J) j = J - 1; /* callers validate; keep the oracle memory-safe */
+      for (int m = 0; m < 12; ++m) a[m] += wk * G[12 * j + m];
+    }
+    if (det) det[i] = det3(a, 4);
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Camera rays and the ray / warped-voxel hit.                                */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  int W, H;
+  double fx, fy, cx, cy;
+  double w2c[12];
+  double near_, far_;
+} orc_cam;
+
+/* Ray through the centre of pixel (x, y): origin o = -R^T t (camera centre)
+ * and direction d = R^T dc / |R^T dc| with dc = ((x+1/2-cx)/fx, (y+1/2-cy)/fy, 1).
+ * d is normalised after the rotation so that it is a unit vector even when R
+ * is not exactly orthonormal (e.g. stored in FP32); t is then a distance. */
+static void cam_ray(const orc_cam* c, int x, int y, double o[3], double d[3]) {
+  double dc[3] = {((double)x + 0.5 - c->cx) / c->fx, ((double)y + 0.5 - c->cy) / c->fy, 1.0};
+  for (int a = 0; a < 3; ++a) {
+    d[a] = c->w2c[0 * 4 + a] * dc[0] + c->w2c[1 * 4 + a] * dc[1] + c->w2c[2 * 4 + a] * dc[2];
+    o[a] = -(c->w2c[0 * 4 + a] * c->w2c[3] + c->w2c[1 * 4 + a] * c->w2c[7] +
+             c->w2c[2 * 4 + a] * c->w2c[11]);
+  }
+  double nrm = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  for (int a = 0; a < 3; ++a) d[a] /= nrm;
+}
+
+void orc_pixel_ray(const orc_cam* c, int x, int y, double* o, double* d) { cam_ray(c, x, y, o, d); }
+
+/*
+ * Slab test of the ray (o, d) against the canonical cube [lo, lo + h]^3 after
+ * mapping the ray into the canonical frame with Ainv (world -> canonical).
+ * t is the world ray parameter (distance, since |d| = 1).  The interval is
+ * clipped to [near, far]; a hit needs t1 > t0.  On a hit, the entry/exit
+ * planes are returned as axis*2 + side (side 0 = lo, 1 = hi) or -1 for a
+ * near/far clip.
+ */
+static int hit_voxel(const double Ainv[12], const double lo[3], double h, const double o[3],
+                     const double d[3], double tnear, double tfar, double* t0, double* t1,
+                     int* p0, int* p1) {
+  double a0 = tnear, a1 = tfar;
+  int q0 = -1, q1 = -1;
+  for (int a = 0; a < 3; ++a) {
+    double oa = Ainv[a * 4 + 0] * o[0] + Ainv[a * 4 + 1] * o[1] + Ainv[a * 4 + 2] * o[2] + Ainv[a * 4 + 3];
+    double da = Ainv[a * 4 + 0] * d[0] + Ainv[a * 4 + 1] * d[1] + Ainv[a * 4 + 2] * d[2];
+    double pl = lo[a], ph = lo[a] + h;
+    if (da == 0.0) {
+      if (oa < pl || oa > ph) return 0;
+      continue;
+    }
+    double ta = (pl - oa) / da, tb = (ph - oa) / da;
+    int sa = 0, sb = 1;
+    if (ta > tb) {
+      double tt = ta; ta = tb; tb = tt;
+      sa = 1; sb = 0;
+    }
+    if (ta > a0) { a0 = ta; q0 = 2 * a + sa; }
+    if (tb < a1) { a1 = tb; q1 = 2 * a + sb; }
+  }
+  *t0 = a0;
+  *t1 = a1;
+  if (p0) *p0 = q0;
+  if (p1) *p1 = q1;
+  return a1 > a0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Scene bookkeeping: per-voxel canonical cube, inverse transform, bbox.      */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  int64_t n;
+  int C;
+  double h;
+  double origin[3];
+  const uint16_t* ijk;
+  const double* A;     /* [n][12] blended transforms */
+  const double* feat;  /* [n][C] */
+  const double* sigma; /* [n] */
+} orc_scene;
+
+typedef struct {
+  double Ainv[12];
+  double lo[3];
+  int ok;                 /* det >= DET_MIN and all corners in front */
+  double umin, umax, vmin, vmax;
+  double dmin, dmax;      /* distance bounds |c - o| -+ r */
+} vox_info;
+
+static void voxel_info(const orc_scene* s, const orc_cam* c, int64_t i, vox_info* v) {
+  const double* A = s->A + 12 * i;
+  for (int a = 0; a < 3; ++a) v->lo[a] = s->origin[a] + (double)s->ijk[3 * i + a] * s->h;
+  v->ok = det3(A, 4) >= ORC_DET_MIN && affine_inv(A, v->Ainv);
+  if (!v->ok) return;
+  double o[3];
+  for (int a = 0; a < 3; ++a)
+    o[a] = -(c->w2c[0 * 4 + a] * c->w2c[3] + c->w2c[1 * 4 + a] * c->w2c[7] + c->w2c[2 * 4 + a] * c->w2c[11]);
+  double cw[3], corners[8][3];
+  for (int a = 0; a < 3; ++a) {
+    double cc[3] = {v->lo[0] + 0.5 * s->h, v->lo[1] + 0.5 * s->h, v->lo[2] + 0.5 * s->h};
+    cw[a] = A[a * 4] * cc[0] + A[a * 4 + 1] * cc[1] + A[a * 4 + 2] * cc[2] + A[a * 4 + 3];
+  }
+  v->umin = v->vmin = INFINITY;
+  v->umax = v->vmax = -INFINITY;
+  double r = 0.0;
+  for (int q = 0; q < 8; ++q) {
+    double p[3] = {v->lo[0] + ((q & 1) ? s->h : 0.0), v->lo[1] + ((q & 2) ? s->h : 0.0),
+                   v->lo[2] + ((q & 4) ? s->h : 0.0)};
+    double dd = 0;
+    for (int a = 0; a < 3; ++a) {
+      corners[q][a] = A[a * 4] * p[0] + A[a * 4 + 1] * p[1] + A[a * 4 + 2] * p[2] + A[a * 4 + 3];
+      dd += (corners[q][a] - cw[a]) * (corners[q][a] - cw[a]);
+    }
+    if (sqrt(dd) > r) r = sqrt(dd);
+    double X = c->w2c[0] * corners[q][0] + c->w2c[1] * corners[q][1] + c->w2c[2] * corners[q][2] + c->w2c[3];
+    double Y = c->w2c[4] * corners[q][0] + c->w2c[5] * corners[q][1] + c->w2c[6] * corners[q][2] + c->w2c[7];
+    double Z = c->w2c[8] * corners[q][0] + c->w2c[9] * corners[q][1] + c->w2c[10] * corners[q][2] + c->w2c[11];
+    if (Z <= ORC_Z_MIN) {
+      v->ok = 0;
+      return;
+    }
+    double u = c->fx * X / Z + c->cx, vv = c->fy * Y / Z + c->cy;
+    if (u < v->umin) v->umin = u;
+    if (u > v->umax) v->umax = u;
+    if (vv < v->vmin) v->vmin = vv;
+    if (vv > v->vmax) v->vmax = vv;
+  }
+  double dc = sqrt((cw[0] - o[0]) * (cw[0] - o[0]) + (cw[1] - o[1]) * (cw[1] - o[1]) +
+                   (cw[2] - o[2]) * (cw[2] - o[2]));
+  v->dmin = dc - r;
+  v->dmax = dc + r;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Per-pixel hit lists and compositing (Eq. 5, Eq. 6).                       */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  double t0, t1;
+  int64_t id;
+  int p0, p1;
+} hit_t;
+
+static int hit_cmp(const void* a, const void* b) {
+  const hit_t* x = (const hit_t*)a;
+  const hit_t* y = (const hit_t*)b;
+  if (x->t0 != y->t0) return x->t0 < y->t0 ? -1 : 1;
+  if (x->t1 != y->t1) return x->t1 < y->t1 ? -1 : 1;
+  return (x->id > y->id) - (x->id < y->id);
+}
+
+/* Front-to-back compositing of an ordered hit list (Eq. 5, Eq. 6):
+ *   T_i = exp(-sum_{j<i} sigma_j delta_j),  F = sum_i T_i (1 - exp(-sigma_i delta_i)) f_i,
+ *   stop after the first hit at which exp(-sum_{j<=i} sigma_j delta_j) < tau,
+ *   A = 1 - exp(-sum over composited hits).
+ * Returns the number of composited hits. */
+static int composite(const orc_scene* s, const hit_t* hits, int m, double tau, double* F, double* Aout) {
+  for (int c = 0; c < s->C; ++c) F[c] = 0.0;
+  double optical = 0.0;
+  int used = 0;
+  for (int i = 0; i < m; ++i) {
+    double sig = s->sigma[hits[i].id];
+    double delta = hits[i].t1 - hits[i].t0;
+    double Ti = exp(-optical);
+    double alpha = 1.0 - exp(-sig * delta);
+    const double* f = s->feat + (size_t)hits[i].id * s->C;
+    for (int c = 0; c < s->C; ++c) F[c] += Ti * alpha * f[c];
+    optical += sig * delta;
+    used = i + 1;
+    if (exp(-optical) < tau) break;
+  }
+  *Aout = 1.0 - exp(-optical);
+  return used;
+}
+
+/* Candidate lists: voxel i is a candidate of every pixel whose centre lies in
+ * its projected-corner bounding box grown by one pixel (a superset of the
+ * pixels whose ray can hit it; the exact test decides). */
+typedef struct {
+  int64_t* off; /* [W*H + 1] */
+  int64_t* vid;
+} cand_t;
+
+static int build_candidates(const orc_scene* s, const orc_cam* c, const vox_info* info, cand_t* out) {
+  int64_t npx = (int64_t)c->W * c->H;
+  int64_t* cnt = (int64_t*)calloc((size_t)npx + 1, sizeof(int64_t));
+  if (!cnt) return -2;
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int64_t i = 0; i < s->n; ++i) {
+      const vox_info* v = info + i;
+      if (!v->ok) continue;
+      int x0 = (int)ceil(v->umin - 0.5) - 1, x1 = (int)floor(v->umax - 0.5) + 1;
+      int y0 = (int)ceil(v->vmin - 0.5) - 1, y1 = (int)floor(v->vmax - 0.5) + 1;
+      if (x0 < 0) x0 = 0;
+      if (y0 < 0) y0 = 0;
+      if (x1 > c->W - 1) x1 = c->W - 1;
+      if (y1 > c->H - 1) y1 = c->H - 1;
+      for (int y = y0; y <= y1; ++y)
+        for (int x = x0; x <= x1; ++x) {
+          int64_t p = (int64_t)y * c->W + x;
+          if (pass == 0)
+            cnt[p + 1]++;
+          else
+            out->vid[cnt[p]++] = i;
+        }
+    }
+    if (pass == 0) {
+      for (int64_t p = 0; p < npx; ++p) cnt[p + 1] += cnt[p];
+      out->off = (int64_t*)malloc(sizeof(int64_t) * ((size_t)npx + 1));
+      out->vid = (int64_t*)malloc(sizeof(int64_t) * ((size_t)cnt[npx] + 1));
+      if (!out->off || !out->vid) {
+        free(cnt);
+        return -2;
+      }
+      memcpy(out->off, cnt, sizeof(int64_t) * ((size_t)npx + 1));
+    }
+  }
+  free(cnt);
+  return 0;
+}
+
+static int pixel_hits(const orc_scene* s, const orc_cam* c, const vox_info* info, const int64_t* ids,
+                      int64_t nid, int x, int y, hit_t** buf, int* cap) {
+  double o[3], d[3];
+  cam_ray(c, x, y, o, d);
+  int m = 0;
+  for (int64_t k = 0; k < nid; ++k) {
+    int64_t i = ids ? ids[k] : k;
+    const vox_info* v = info + i;
+    if (!v->ok) continue;
+    double t0, t1;
+    int p0, p1;
+    if (hit_voxel(v->Ainv, v->lo, s->h, o, d, c->near_, c->far_, &t0, &t1, &p0, &p1)) {
+      if (m == *cap) {
+        *cap = *cap ? 2 * *cap : 64;
+        *buf = (hit_t*)realloc(*buf, sizeof(hit_t) * (size_t)*cap);
+      }
+      (*buf)[m].t0 = t0;
+      (*buf)[m].t1 = t1;
+      (*buf)[m].id = i;
+      (*buf)[m].p0 = p0;
+      (*buf)[m].p1 = p1;
+      ++m;
+    }
+  }
+  qsort(*buf, (size_t)m, sizeof(hit_t), hit_cmp);
+  return m;
+}
+
+static vox_info* all_info(const orc_scene* s, const orc_cam* c) {
+  vox_info* info = (vox_info*)malloc(sizeof(vox_info) * (size_t)(s->n > 0 ? s->n : 1));
+  if (!info) return NULL;
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < s->n; ++i) voxel_info(s, c, i, info + i);
+  return info;
+}
+
+/*
+ * Render feature map F [H][W][C] and coarse opacity A [H][W].
+ * Optional outputs (NULL to skip): nhit [H*W] total hits, nused [H*W]
+ * composited hits, and the ordered hit lists as CSR (hit_off [H*W+1],
+ * hit_id / hit_t0 / hit_t1 [hit_cap]).  Returns the total hit count, or
+ * -(needed) when hit_cap is too small, or < -2^40 on allocation failure.
+ */
+int64_t orc_render(const orc_scene* s, const orc_cam* c, double tau, double* F, double* Aout,
+                   int32_t* nhit, int32_t* nused, int64_t* hit_off, int64_t* hit_id, double* hit_t0,
+                   double* hit_t1, int64_t hit_cap) {
+  vox_info* info = all_info(s, c);
+  if (!info) return -((int64_t)1 << 41);
+  cand_t cand = {0, 0};
+  if (build_candidates(s, c, info, &cand) != 0) {
+    free(info);
+    return -((int64_t)1 << 41);
+  }
+  int64_t npx = (int64_t)c->W * c->H;
+  int32_t* cnt = (int32_t*)malloc(sizeof(int32_t) * (size_t)npx);
+  int64_t total = 0;
+#pragma omp parallel
+  {
+    hit_t* buf = NULL;
+    int cap = 0;
+#pragma omp for schedule(dynamic, 16) reduction(+ : total)
+    for (int64_t p = 0; p < npx; ++p) {
+      int x = (int)(p % c->W), y = (int)(p / c->W);
+      int m = pixel_hits(s, c, info, cand.vid + cand.off[p], cand.off[p + 1] - cand.off[p], x, y, &buf, &cap);
+      int used = composite(s, buf, m, tau, F + p * s->C, Aout + p);
+      if (nhit) nhit[p] = m;
+      if (nused) nused[p] = used;
+      cnt[p] = m;
+      total += m;
+    }
+    free(buf);
+  }
+  int64_t ret = total;
+  if (hit_off) {
+    if (total > hit_cap) {
+      ret = -total;
+    } else {
+      hit_off[0] = 0;
+      for (int64_t p = 0; p < npx; ++p) hit_off[p + 1] = hit_off[p] + cnt[p];
+#pragma omp parallel
+      {
+        hit_t* buf = NULL;
+        int cap = 0;
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t p = 0; p < npx; ++p) {
+          int x = (int)(p % c->W), y = (int)(p / c->W);
+          int m = pixel_hits(s, c, info, cand.vid + cand.off[p], cand.off[p + 1] - cand.off[p], x, y, &buf, &cap);
+          for (int k = 0; k < m; ++k) {
+            hit_id[hit_off[p] + k] = buf[k].id;
+            hit_t0[hit_off[p] + k] = buf[k].t0;
+            hit_t1[hit_off[p] + k] = buf[k].t1;
+          }
+        }
+        free(buf);
+      }
+    }
+  }
+  free(cnt);
+  free(cand.off);
+  free(cand.vid);
+  free(info);
+  return ret;
+}
+
+/*
+ * One pixel, by brute force over every voxel (no candidate pre-selection).
+ * Writes F [C], A, and up to cap ordered hits.  Returns the number of hits.
+ */
+int orc_pixel_brute(const orc_scene* s, const orc_cam* c, int x, int y, double tau, double* F,
+                    double* Aout, int64_t* ids, double* t0, double* t1, int cap, int* used) {
+  vox_info* info = all_info(s, c);
+  if (!info) return -1;
+  hit_t* buf = NULL;
+  int bcap = 0;
+  int m = pixel_hits(s, c, info, NULL, s->n, x, y, &buf, &bcap);
+  int u = composite(s, buf, m, tau, F, Aout);
+  if (used) *used = u;
+  for (int k = 0; k < m && k < cap; ++k) {
+    ids[k] = buf[k].id;
+    t0[k] = buf[k].t0;
+    t1[k] = buf[k].t1;
+  }
+  free(buf);
+  free(info);
+  return m;
+}
+
+/*
+ * A list of pixels (px, py [np]) rendered one by one, each by brute force over
+ * all voxels.  Used to check sampled outputs of full-size frames.
+ */
+int orc_pixels(const orc_scene* s, const orc_cam* c, int64_t np, const int32_t* px, const int32_t* py,
+               double tau, double* F, double* Aout, int32_t* nhit) {
+  vox_info* info = all_info(s, c);
+  if (!info) return -1;
+#pragma omp parallel
+  {
+    hit_t* buf = NULL;
+    int bcap = 0;
+#pragma omp for schedule(dynamic, 1)
+    for (int64_t k = 0; k < np; ++k) {
+      int m = pixel_hits(s, c, info, NULL, s->n, px[k], py[k], &buf, &bcap);
+      composite(s, buf, m, tau, F + k * s->C, Aout + k);
+      if (nhit) nhit[k] = m;
+    }
+    free(buf);
+  }
+  free(info);
+  return 0;
+}
+
+/*
+ * Screen-tile coverage: voxel i covers tile (tx, ty) of size ts x ts when its
+ * projected-corner bounding box contains at least one pixel centre of the
+ * tile.  Voxels that are degenerate, cross the camera plane, or whose
+ * distance range [|c-o| - r, |c-o| + r] misses [near, far] cover nothing.
+ * Writes (tile id, voxel id) pairs in voxel order; returns the pair count or
+ * -(needed) when cap is too small.
+ */
+int64_t orc_tile_pairs(const orc_scene* s, const orc_cam* c, int ts, int32_t* tile, int64_t* vid, int64_t cap) {
+  vox_info* info = all_info(s, c);
+  if (!info) return -((int64_t)1 << 41);
+  int tw = (c->W + ts - 1) / ts;
+  int64_t m = 0;
+  for (int64_t i = 0; i < s->n; ++i) {
+    const vox_info* v = info + i;
+    if (!v->ok || v->dmin > c->far_ || v->dmax < c->near_) continue;
+    int x0 = (int)ceil(v->umin - 0.5), x1 = (int)floor(v->umax - 0.5);
+    int y0 = (int)ceil(v->vmin - 0.5), y1 = (int)floor(v->vmax - 0.5);
+    if (x0 < 0) x0 = 0;
+    if (y0 < 0) y0 = 0;
+    if (x1 > c->W - 1) x1 = c->W - 1;
+    if (y1 > c->H - 1) y1 = c->H - 1;
+    if (x0 > x1 || y0 > y1) continue;
+    for (int ty = y0 / ts; ty <= y1 / ts; ++ty)
+      for (int tx = x0 / ts; tx <= x1 / ts; ++tx) {
+        if (m < cap) {
+          tile[m] = ty * tw + tx;
+          vid[m] = i;
+        }
+        ++m;
+      }
+  }
+  free(info);
+  return m <= cap ? m : -m;
+}
+
+/* Per-voxel distance bounds and projected bounding boxes (for tests). */
+void orc_voxel_bounds(const orc_scene* s, const orc_cam* c, double* out /*[n][7]: ok,umin,umax,vmin,vmax,dmin,dmax*/) {
+  vox_info* info = all_info(s, c);
+  if (!info) return;
+  for (int64_t i = 0; i < s->n; ++i) {
+    out[7 * i + 0] = info[i].ok;
+    out[7 * i + 1] = info[i].umin;
+    out[7 * i + 2] = info[i].umax;
+    out[7 * i + 3] = info[i].vmin;
+    out[7 * i + 4] = info[i].vmax;
+    out[7 * i + 5] = info[i].dmin;
+    out[7 * i + 6] = info[i].dmax;
+  }
+  free(info);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Gradients of the composite (project addition; the paper optimises the    */
+/* FLUT end to end through Eq. 5-6).                                          */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * For loss L with dL/dF = gF [H][W][C] and dL/dA = gA [H][W], accumulate
+ * dL/df_i into gfeat [n][C], dL/dsigma_i into gsigma [n] and dL/dAinv_i into
+ * gAinv [n][12] (Ainv_i maps world -> canonical).  The hit set, the order
+ * and the stop index are held fixed.
+ *
+ * With w_i = T_i a_i, a_i = 1 - exp(-sigma_i delta_i), T_{i+1} = T_i (1-a_i):
+ *   dF/df_i      = w_i
+ *   dF/dsigma_i  = delta_i (T_{i+1} f_i - sum_{k>i} w_k f_k)
+ *   dA/dsigma_i  = delta_i T_final
+ *   d/ddelta_i   = the same with sigma_i in place of delta_i
+ *   dt/dAinv[a,:] = -[x_hit, 1] / d'_a for the active slab plane of axis a.
+ */
+int orc_render_backward(const orc_scene* s, const orc_cam* c, double tau, const double* gF, const double* gA,
+                        double* gfeat, double* gsigma, double* gAinv) {
+  vox_info* info = all_info(s, c);
+  if (!info) return -2;
+  cand_t cand = {0, 0};
+  if (build_candidates(s, c, info, &cand) != 0) {
+    free(info);
+    return -2;
+  }
+  int64_t npx = (int64_t)c->W * c->H;
+  int C = s->C;
+  /* serial over pixels: accumulation order is fixed and the oracle stays simple */
+  hit_t* buf = NULL;
+  int cap = 0;
+  double* suffix = (double*)malloc(sizeof(double) * (size_t)C);
+  double* Fp = (double*)malloc(sizeof(double) * (size_t)C);
+  for (int64_t p = 0; p < npx; ++p) {
+    int x = (int)(p % c->W), y = (int)(p / c->W);
+    int m = pixel_hits(s, c, info, cand.vid + cand.off[p], cand.off[p + 1] - cand.off[p], x, y, &buf, &cap);
+    if (m == 0) continue;
+    double Ap;
+    int used = composite(s, buf, m, tau, Fp, &Ap);
+    const double* g = gF + p * C;
+    double ga = gA[p];
+    double o[3], d[3];
+    cam_ray(c, x, y, o, d);
+    /* T_i before each hit, and T_final */
+    double* Tb = (double*)malloc(sizeof(double) * (size_t)(used + 1));
+    double optical = 0.0;
+    for (int i = 0; i < used; ++i) {
+      Tb[i] = exp(-optical);
+      optical += s->sigma[buf[i].id] * (buf[i].t1 - buf[i].t0);
+    }
+    Tb[used] = exp(-optical);
+    double Tfinal = Tb[used];
+    for (int cc = 0; cc < C; ++cc) suffix[cc] = 0.0;
+    for (int i = used - 1; i >= 0; --i) {
+      int64_t id = buf[i].id;
+      double sig = s->sigma[id];
+      double delta = buf[i].t1 - buf[i].t0;
+      double a = 1.0 - exp(-sig * delta);
+      double wgt = Tb[i] * a;
+      const double* f = s->feat + (size_t)id * C;
+      double fg = 0.0, sg = 0.0;
+      for (int cc = 0; cc < C; ++cc) {
+        gfeat[(size_t)id * C + cc] += wgt * g[cc];
+        fg += f[cc] * g[cc];
+        sg += suffix[cc] * g[cc];
+      }
+      double core = Tb[i + 1] * fg - sg + Tfinal * ga; /* d L / d(sigma*delta) */
+      gsigma[id] += delta * core;
+      double gdelta = sig * core;
+      /* delta = t1 - t0 */
+      const double* Ai = info[id].Ainv;
+      for (int side = 0; side < 2; ++side) {
+        int plane = side ? buf[i].p1 : buf[i].p0;
+        if (plane < 0) continue; /* near/far clip: no geometric dependence */
+        double t = side ? buf[i].t1 : buf[i].t0;
+        double sgn = side ? 1.0 : -1.0;
+        int ax = plane / 2;
+        double dp = Ai[ax * 4] * d[0] + Ai[ax * 4 + 1] * d[1] + Ai[ax * 4 + 2] * d[2];
+        double xh[3] = {o[0] + t * d[0], o[1] + t * d[1], o[2] + t * d[2]};
+        double gt = sgn * gdelta;
+        for (int k = 0; k < 3; ++k) gAinv[12 * id + ax * 4 + k] += gt * (-xh[k] / dp);
+        gAinv[12 * id + ax * 4 + 3] += gt * (-1.0 / dp);
+      }
+      for (int cc = 0; cc < C; ++cc) suffix[cc] += wgt * f[cc];
+    }
+    free(Tb);
+  }
+  free(suffix);
+  free(Fp);
+  free(buf);
+  free(cand.off);
+  free(cand.vid);
+  free(info);
+  return 0;
+}
+
+/*
+ * LBS backward: dL/dA_i from dL/dAinv_i (dN = -N dM N for N = M^-1, with M
+ * the 4x4 affine form of A_i), then dL/dw_ik = <dL/dA_i, G_{j_ik}>.
+ */
+void orc_lbs_backward(int64_t n, int J, const double* G, const uint8_t* jidx, const double* A,
+                      const double* gAinv, double* gA_out, double* gw) {
+  for (int64_t i = 0; i < n; ++i) {
+    double N[16] = {0}, M4[16] = {0}, GN[16] = {0}, GM[16];
+    for (int r = 0; r < 3; ++r)
+      for (int k = 0; k < 4; ++k) M4[r * 4 + k] = A[12 * i + r * 4 + k];
+    M4[15] = 1.0;
+    double Ai[12];
+    if (!affine_inv(A + 12 * i, Ai)) {
+      for (int k = 0; k < 4; ++k) gw[4 * i + k] = 0.0;
+      continue;
+    }
+    for (int r = 0; r < 3; ++r)
+      for (int k = 0; k < 4; ++k) {
+        N[r * 4 + k] = Ai[r * 4 + k];
+        GN[r * 4 + k] = gAinv[12 * i + r * 4 + k];
+      }
+    N[15] = 1.0;
+    /* GM = -N^T GN N^T */
+    double tmp[16];
+    for (int r = 0; r < 4; ++r)
+      for (int k = 0; k < 4; ++k) {
+        double acc = 0.0;
+        for (int m = 0; m < 4; ++m) acc += N[m * 4 + r] * GN[m * 4 + k];
+        tmp[r * 4 + k] = acc;
+      }
+    for (int r = 0; r < 4; ++r)
+      for (int k = 0; k < 4; ++k) {
+        double acc = 0.0;
+        for (int m = 0; m < 4; ++m) acc += tmp[r * 4 + m] * N[k * 4 + m];
+        GM[r * 4 + k] = -acc;
+      }
+    (void)M4;
+    for (int r = 0; r < 3; ++r)
+      for (int k = 0; k < 4; ++k)
+        if (gA_out) gA_out[12 * i + r * 4 + k] = GM[r * 4 + k];
+    for (int q = 0; q < 4; ++q) {
+      int j = jidx[4 * i + q];
+      if (j >= J) j = J - 1;
+      double acc = 0.0;
+      for (int r = 0; r < 3; ++r)
+        for (int k = 0; k < 4; ++k) acc += GM[r * 4 + k] * G[12 * j + r * 4 + k];
+      gw[4 * i + q] = acc;
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Shading network primitives (Sec. 3.1, "Neural Shading"), NHWC, FP64.      */
+/* ------------------------------------------------------------------------ */
+
+/* out[y][x][co] = act(b[co] + sum_{r,s,ci} w[co][r][s][ci] in[y+r-k/2][x+s-k/2][ci]),
+ * zero padding outside the image; act 0 = identity, 1 = ReLU, 2 = sigmoid. */
+void orc_conv2d(int H, int W, int Cin, int Cout, int k, const double* in, const double* w, const double* b,
+                double* out, int act) {
+  int pad = k / 2;
+#pragma omp parallel for schedule(static)
+  for (int y = 0; y < H; ++y) {
+    for (int x = 0; x < W; ++x) {
+      double* o = out + ((size_t)y * W + x) * Cout;
+      for (int co = 0; co < Cout; ++co) {
+        double acc = b ? b[co] : 0.0;
+        for (int r = 0; r < k; ++r) {
+          int yy = y + r - pad;
+          if (yy < 0 || yy >= H) continue;
+          for (int s2 = 0; s2 < k; ++s2) {
+            int xx = x + s2 - pad;
+            if (xx < 0 || xx >= W) continue;
+            const double* ip = in + ((size_t)yy * W + xx) * Cin;
+            const double* wp = w + (((size_t)co * k + r) * k + s2) * Cin;
+            for (int ci = 0; ci < Cin; ++ci) acc += wp[ci] * ip[ci];
+          }
+        }
+        if (act == 1) acc = acc > 0.0 ? acc : 0.0;
+        if (act == 2) acc = 1.0 / (1.0 + exp(-acc));
+        o[co] = acc;
+      }
+    }
+  }
+}
+
+/* 2x2 max pooling with stride 2 (H, W even). */
+void orc_maxpool2(int H, int W, int C, const double* in, double* out) {
+  for (int y = 0; y < H / 2; ++y)
+    for (int x = 0; x < W / 2; ++x)
+      for (int c = 0; c < C; ++c) {
+        double m = -INFINITY;
+        for (int dy = 0; dy < 2; ++dy)
+          for (int dx = 0; dx < 2; ++dx) {
+            double v = in[(((size_t)(2 * y + dy)) * W + (2 * x + dx)) * C + c];
+            if (v > m) m = v;
+          }
+        out[((size_t)y * (W / 2) + x) * C + c] = m;
+      }
+}
+
+/* Nearest-neighbour x2 upsampling: out[y][x] = in[y/2][x/2]. */
+void orc_upsample2(int H, int W, int C, const double* in, double* out) {
+  for (int y = 0; y < 2 * H; ++y)
+    for (int x = 0; x < 2 * W; ++x)
+      for (int c = 0; c < C; ++c)
+        out[((size_t)y * 2 * W + x) * C + c] = in[((size_t)(y / 2) * W + (x / 2)) * C + c];
+}

@@ -1,0 +1,627 @@
+"""Pins of the FP64 oracle to facts other than itself (CPU only).
+
+Each test fixes one function of ``oracle/`` against a closed form, brute
+force, an invariant of the method, or an independent library routine, chosen
+so that a plausible slip (a dropped term, a wrong sign or index, a transposed
+operand) fails at least one of them.  Paper: arXiv 2202.05628, Sec. 3.1.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import scenegen as sg
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------------------
+# helpers: hand-made scenes
+# ---------------------------------------------------------------------------
+
+def one_joint_skeleton(J=2):
+    parent = np.array([-1] + list(range(J - 1)), np.int32)
+    rest = np.zeros((J, 3), np.float32)
+    for j in range(1, J):
+        rest[j] = rest[j - 1] + np.array([0.1, 0.0, 0.0], np.float32)
+    return sg.Skeleton(parent, rest)
+
+
+def make_octree(ijk, depth=4, extent=1.0, origin=(-0.5, -0.5, -0.5), feats=None, dens=None,
+                jidx=None, w=None, C=3, seed=0):
+    ijk = np.asarray(ijk, np.uint16).reshape(-1, 3)
+    n = ijk.shape[0]
+    rng = np.random.default_rng(seed)
+    feats = rng.standard_normal((n, C)).astype(np.float32) if feats is None else np.asarray(feats, np.float32)
+    dens = np.full(n, 3.0, np.float32) if dens is None else np.asarray(dens, np.float32)
+    jidx = np.zeros((n, 4), np.uint8) if jidx is None else np.asarray(jidx, np.uint8)
+    if w is None:
+        w = np.zeros((n, 4), np.float32)
+        w[:, 0] = 1.0
+    return sg.Octree(depth, np.asarray(origin, np.float32), extent, ijk, jidx, np.asarray(w, np.float32),
+                     feats, dens, np.zeros(n, np.float32))
+
+
+def axis_camera(target, direction, dist=1.0, W=1, H=1, f=100.0, near=0.05, far=5.0):
+    """Camera whose pixel (0, 0) centre ray passes through ``target`` along
+    unit ``direction`` (the optical axis, since cx = cy = 0.5)."""
+    d = np.asarray(direction, np.float64)
+    d /= np.linalg.norm(d)
+    eye = np.asarray(target, np.float64) - dist * d
+    up = (0.0, 1.0, 0.0) if abs(d[1]) < 0.9 else (1.0, 0.0, 0.0)
+    M = sg.look_at(eye, target, up)
+    return sg.Camera(W=W, H=H, fx=f, fy=f, cx=0.5, cy=0.5, world_to_cam=M,
+                     near=near, far=far)
+
+
+def identity_A(n):
+    A = np.zeros((n, 3, 4))
+    A[:, 0, 0] = A[:, 1, 1] = A[:, 2, 2] = 1.0
+    return A
+
+
+def voxel_center(oc, i):
+    return oc.centers()[i]
+
+
+# ---------------------------------------------------------------------------
+# Eq. 4: forward kinematics and LBS
+# ---------------------------------------------------------------------------
+
+def test_rodrigues_matches_scipy():
+    Rot = pytest.importorskip("scipy.spatial.transform").Rotation
+    rng = np.random.default_rng(3)
+    for _ in range(50):
+        r = rng.standard_normal(3) * rng.uniform(0, 3)
+        np.testing.assert_allclose(oracle.rodrigues(r), Rot.from_rotvec(r).as_matrix(), atol=1e-13)
+    np.testing.assert_array_equal(oracle.rodrigues(np.zeros(3)), np.eye(3))
+
+
+def test_fk_rest_pose_is_identity():
+    sc = sg.preset("mini")
+    G = oracle.fk(sc.skeleton, sg.rest_pose())
+    for j in range(G.shape[0]):
+        np.testing.assert_allclose(G[j], np.hstack([np.eye(3), np.zeros((3, 1))]), atol=1e-15)
+
+
+def test_fk_two_joint_closed_form():
+    # root at origin, child at (0.1, 0, 0); rotate the root 90 deg about z:
+    # the child joint moves to (0, 0.1, 0) and a point on the child's bone
+    # (0.15, 0, 0) moves to (0, 0.15, 0).
+    sk = one_joint_skeleton(2)
+    aa = np.zeros((2, 3), np.float32)
+    aa[0] = [0, 0, math.pi / 2]
+    G = oracle.fk(sk, sg.Pose(aa, np.zeros(3, np.float32), np.zeros(3, np.float32)))
+    p = np.array([0.15, 0.0, 0.0, 1.0])
+    np.testing.assert_allclose(G[1] @ p, [0.0, 0.15, 0.0], atol=1e-7)
+    np.testing.assert_allclose(G[1] @ np.array([0.1, 0, 0, 1.0]), [0.0, 0.1, 0.0], atol=1e-7)
+    # a child rotation about z by -90 deg restores the orientation beyond the
+    # child joint, which itself sits at (0, 0.1, 0)
+    aa[1] = [0, 0, -math.pi / 2]
+    G = oracle.fk(sk, sg.Pose(aa, np.zeros(3, np.float32), np.zeros(3, np.float32)))
+    np.testing.assert_allclose(G[1] @ p, [0.05, 0.1, 0.0], atol=1e-7)
+
+
+def test_fk_preserves_bones_and_global_rigid():
+    sc = sg.preset("mini")
+    sk = sc.skeleton
+    pose = sg.random_pose(5)
+    G = oracle.fk(sk, pose)
+    rest = sk.rest.astype(np.float64)
+    posed = np.einsum("jab,jb->ja", G[:, :, :3], rest) + G[:, :, 3]
+    for j in range(1, sk.J):
+        p = sk.parent[j]
+        assert abs(np.linalg.norm(posed[j] - posed[p]) - np.linalg.norm(rest[j] - rest[p])) < 1e-6
+        Rj = G[j, :, :3]
+        np.testing.assert_allclose(Rj @ Rj.T, np.eye(3), atol=1e-6)
+        assert abs(np.linalg.det(Rj) - 1) < 1e-6
+    # global R, T compose on the left of every joint transform
+    Rg = np.array([0.3, -0.2, 0.5], np.float32)
+    Tg = np.array([0.1, 0.2, -0.3], np.float32)
+    G2 = oracle.fk(sk, sg.Pose(pose.axis_angle, Rg, Tg))
+    Rm = oracle.rodrigues(Rg)
+    for j in range(sk.J):
+        np.testing.assert_allclose(G2[j, :, :3], Rm @ G[j, :, :3], atol=1e-12)
+        np.testing.assert_allclose(G2[j, :, 3], Rm @ G[j, :, 3] + Tg, atol=1e-7)
+
+
+def test_fk_rejects_bad_parent():
+    sk = sg.Skeleton(np.array([-1, 2, 0], np.int32), np.zeros((3, 3), np.float32))
+    with pytest.raises(ValueError):
+        oracle.fk(sk, sg.rest_pose(3))
+
+
+def test_lbs_one_hot_and_linearity():
+    sc = sg.preset("mini")
+    oc = sc.octree
+    G = oracle.fk(sc.skeleton, sg.random_pose(2))
+    w1 = np.zeros_like(oc.weights)
+    w1[:, 0] = 1.0
+    A1, det = oracle.lbs(oc, G, w1)
+    np.testing.assert_allclose(A1, G[oc.joint_idx[:, 0]], atol=0)
+    np.testing.assert_allclose(det, 1.0, atol=1e-6)
+    # A is linear in the weights: A(a w + b w') = a A(w) + b A(w')
+    rng = np.random.default_rng(0)
+    wa = rng.uniform(0, 1, oc.weights.shape)
+    wb = rng.uniform(0, 1, oc.weights.shape)
+    Aa, _ = oracle.lbs(oc, G, wa)
+    Ab, _ = oracle.lbs(oc, G, wb)
+    Ac, _ = oracle.lbs(oc, G, 0.3 * wa + 0.7 * wb)
+    np.testing.assert_allclose(Ac, 0.3 * Aa + 0.7 * Ab, atol=1e-12)
+    # rest pose: every voxel keeps its canonical position
+    A0, det0 = oracle.lbs(oc, oracle.fk(sc.skeleton, sg.rest_pose()))
+    np.testing.assert_allclose(A0, identity_A(oc.n), atol=1e-7)
+
+
+# ---------------------------------------------------------------------------
+# rays
+# ---------------------------------------------------------------------------
+
+def test_pixel_ray_reprojects_to_pixel_centre():
+    sc = sg.preset("mini")
+    cam = sg.orbit_camera(sc.centroid, 40, 30, az_deg=37.0)
+    M = cam.world_to_cam.astype(np.float64)
+    for (x, y) in [(0, 0), (39, 29), (17, 11), (5, 28)]:
+        o, d = oracle.pixel_ray(cam, x, y)
+        assert abs(np.linalg.norm(d) - 1) < 1e-14
+        np.testing.assert_allclose(M[:, :3] @ o + M[:, 3], 0, atol=1e-6)
+        p = M[:, :3] @ (o + 1.7 * d) + M[:, 3]
+        np.testing.assert_allclose([cam.fx * p[0] / p[2] + cam.cx, cam.fy * p[1] / p[2] + cam.cy],
+                                   [x + 0.5, y + 0.5], atol=1e-5)
+
+
+# ---------------------------------------------------------------------------
+# Eq. 5-6: closed forms for one and two voxels
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("direction", [(0, 0, 1), (1, 0, 0), (0.3, -0.2, 1.0), (1.0, 0.9, -0.4), (-0.2, 1.0, 0.05)])
+def test_single_voxel_chord_through_centre(direction):
+    # A ray through the centre of an axis-aligned cube of side h travels
+    # h / max_a |d_a| inside it.
+    oc = make_octree([[7, 8, 9]], C=4)
+    c = voxel_center(oc, 0)
+    cam = axis_camera(c, direction)
+    d = np.asarray(direction, float) / np.linalg.norm(direction)
+    chord = oc.h / np.max(np.abs(d))
+    r = oracle.render(oc, identity_A(1), cam, hits=True)
+    sigma = float(oc.density[0])
+    a = 1 - math.exp(-sigma * chord)
+    np.testing.assert_allclose(r["F"][0, 0], a * oc.features[0].astype(float), rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(r["A"][0, 0], a, rtol=1e-12)
+    np.testing.assert_allclose(r["hit_t1"] - r["hit_t0"], [chord], rtol=1e-12)
+
+
+def test_single_warped_voxel_chord():
+    # A = blend of two rotations (not rigid).  In the canonical frame the
+    # direction is d' = A_lin^-1 d (unnormalised) and, through the centre, the
+    # ray is inside the cube for |t d'_a| <= h/2 on every axis: chord =
+    # h / max_a |d'_a|.
+    oc = make_octree([[3, 4, 5]], C=2)
+    R1 = oracle.rodrigues([0.0, 0.0, 0.6])
+    R2 = oracle.rodrigues([0.4, 0.1, 0.0])
+    L = 0.5 * (R1 + R2)
+    c = voxel_center(oc, 0)
+    t = np.array([0.05, -0.02, 0.03])
+    A = np.zeros((1, 3, 4))
+    A[0, :, :3] = L
+    A[0, :, 3] = t
+    cw = L @ c + t
+    for direction in [(0, 0, 1), (0.5, 0.2, -1.0), (1, 1, 1)]:
+        cam = axis_camera(cw, direction, dist=1.3)
+        d = np.asarray(direction, float) / np.linalg.norm(direction)
+        dl = np.linalg.solve(L, d)
+        chord = oc.h / np.max(np.abs(dl))
+        r = oracle.render(oc, A, cam, hits=True)
+        np.testing.assert_allclose(r["hit_t1"] - r["hit_t0"], [chord], rtol=1e-10)
+        np.testing.assert_allclose(r["hit_t0"] + r["hit_t1"], [2 * 1.3], rtol=1e-10)
+
+
+def test_two_stacked_voxels_closed_form():
+    # F = a1 f1 + (1 - a1) a2 f2, A = 1 - (1 - a1)(1 - a2) for two voxels
+    # stacked along the ray (exclusive transmittance, Eq. 6 read with j < i).
+    oc = make_octree([[5, 5, 5], [5, 5, 6]], dens=[7.0, 11.0], C=3)
+    c0, c1 = voxel_center(oc, 0), voxel_center(oc, 1)
+    cam = axis_camera(c0, (0, 0, 1))  # enters voxel 0 first
+    r = oracle.render(oc, identity_A(2), cam, hits=True)
+    a1 = 1 - math.exp(-7.0 * oc.h)
+    a2 = 1 - math.exp(-11.0 * oc.h)
+    f = oc.features.astype(float)
+    np.testing.assert_allclose(r["F"][0, 0], a1 * f[0] + (1 - a1) * a2 * f[1], rtol=1e-12)
+    np.testing.assert_allclose(r["A"][0, 0], 1 - (1 - a1) * (1 - a2), rtol=1e-12)
+    assert list(r["hit_id"]) == [0, 1]
+    # looking from the other side reverses the order
+    cam = axis_camera(c1, (0, 0, -1))
+    r = oracle.render(oc, identity_A(2), cam, hits=True)
+    np.testing.assert_allclose(r["F"][0, 0], a2 * f[1] + (1 - a2) * a1 * f[0], rtol=1e-12)
+    assert list(r["hit_id"]) == [1, 0]
+
+
+def test_near_far_clip():
+    oc = make_octree([[8, 8, 8]], C=1)
+    c = voxel_center(oc, 0)
+    # camera 1.0 from the centre; near plane cuts the voxel 0.3 h past its entry
+    near = 1.0 - 0.5 * oc.h + 0.3 * oc.h
+    cam = axis_camera(c, (0, 0, 1), dist=1.0, near=near)
+    r = oracle.render(oc, identity_A(1), cam, hits=True)
+    np.testing.assert_allclose(r["hit_t1"] - r["hit_t0"], [0.7 * oc.h], rtol=1e-9)
+    far = 1.0 - 0.5 * oc.h + 0.2 * oc.h
+    cam = axis_camera(c, (0, 0, 1), dist=1.0, near=0.1, far=far)
+    r = oracle.render(oc, identity_A(1), cam, hits=True)
+    np.testing.assert_allclose(r["hit_t1"] - r["hit_t0"], [0.2 * oc.h], rtol=1e-9)
+    cam = axis_camera(c, (0, 0, 1), dist=1.0, near=1.1)
+    assert oracle.render(oc, identity_A(1), cam)["nhit"][0, 0] == 0
+
+
+def test_golden_fixtures():
+    """Closed-form fixtures written by tests/golden/make_golden.py (exact
+    arithmetic in sympy, independent of the oracle)."""
+    with open(os.path.join(GOLDEN, "closed_forms.json")) as fh:
+        cases = json.load(fh)["cases"]
+    assert len(cases) >= 3
+    for case in cases:
+        oc = make_octree(case["ijk"], depth=case["depth"], feats=case["features"], dens=case["density"],
+                         C=len(case["features"][0]))
+        cam = axis_camera(np.asarray(case["target"]), case["direction"], dist=case["dist"])
+        r = oracle.render(oc, identity_A(oc.n), cam, tau=case["tau"], hits=True)
+        np.testing.assert_allclose(r["F"][0, 0], case["F"], rtol=1e-12, atol=1e-14)
+        np.testing.assert_allclose(r["A"][0, 0], case["A"], rtol=1e-12)
+        assert list(r["hit_id"]) == case["order"]
+        assert int(r["nused"][0, 0]) == case["used"]
+
+
+# ---------------------------------------------------------------------------
+# hit lists: brute force, invariants
+# ---------------------------------------------------------------------------
+
+def test_candidate_lists_equal_brute_force():
+    sc = sg.preset("mini")
+    oc = sc.octree
+    cam = sg.orbit_camera(sc.centroid, 64, 64, az_deg=30)
+    _, A, _ = oracle.pose_transforms(sc, sg.random_pose(11))
+    r = oracle.render(oc, A, cam, hits=True)
+    rng = np.random.default_rng(0)
+    ys, xs = np.nonzero(r["nhit"] >= 0)
+    pick = rng.choice(len(ys), 60, replace=False)
+    covered = np.argwhere(r["nhit"] > 0)
+    pick_c = covered[rng.choice(len(covered), min(60, len(covered)), replace=False)]
+    for y, x in list(zip(ys[pick], xs[pick])) + [tuple(p) for p in pick_c]:
+        b = oracle.pixel_brute(oc, A, cam, int(x), int(y))
+        p = y * cam.W + x
+        ids = r["hit_id"][r["hit_off"][p]:r["hit_off"][p + 1]]
+        np.testing.assert_array_equal(b["ids"], ids)
+        np.testing.assert_array_equal(b["F"], r["F"][y, x])
+
+
+def test_all_ones_features_give_accumulated_alpha():
+    # With f_i = 1, F = sum_i T_i a_i must equal A = 1 - T_final (exclusive T).
+    sc = sg.preset("tiny")
+    oc = sc.octree
+    cam = sg.orbit_camera(sc.centroid, 128, 128, az_deg=80)
+    _, A, _ = oracle.pose_transforms(sc, sg.random_pose(4))
+    ones = np.ones((oc.n, 1))
+    r = oracle.render(oc, A, cam, features=ones)
+    np.testing.assert_allclose(r["F"][..., 0], r["A"], atol=1e-13)
+    assert r["A"].min() >= 0 and r["A"].max() <= 1
+    assert (r["A"] > 0).sum() > 100
+
+
+def test_transmittance_monotone_and_early_stop():
+    sc = sg.preset("tiny")
+    oc = sc.octree
+    cam = sg.orbit_camera(sc.centroid, 128, 128)
+    _, A, _ = oracle.pose_transforms(sc, sg.random_pose(4))
+    dens = oc.density.astype(float) * 60.0  # opaque animal so that the stop fires
+    tau = 1e-4
+    r = oracle.render(oc, A, cam, tau=tau, hits=True, density=dens)
+    stopped = np.argwhere(r["nused"] < r["nhit"])
+    assert len(stopped) > 20
+    for y, x in stopped[:50]:
+        p = y * cam.W + x
+        s, e = r["hit_off"][p], r["hit_off"][p + 1]
+        ids = r["hit_id"][s:e]
+        delta = r["hit_t1"][s:e] - r["hit_t0"][s:e]
+        assert np.all(delta > 0)
+        T = np.exp(-np.cumsum(dens[ids] * delta))  # T after each hit: non-increasing
+        assert np.all(np.diff(T) <= 0)
+        u = r["nused"][y, x]
+        assert T[u - 1] < tau and (u == 1 or T[u - 2] >= tau)
+        np.testing.assert_allclose(r["A"][y, x], 1 - T[u - 1], rtol=1e-12)
+    # tau = 0 composites every hit
+    r0 = oracle.render(oc, A, cam, tau=0.0, density=dens)
+    assert np.array_equal(r0["nused"], r0["nhit"])
+
+
+def test_zero_density_voxels_invisible():
+    sc = sg.preset("tiny")
+    oc = sc.octree
+    cam = sg.orbit_camera(sc.centroid, 96, 96, az_deg=200)
+    _, A, _ = oracle.pose_transforms(sc, sg.random_pose(8))
+    rng = np.random.default_rng(1)
+    drop = rng.uniform(size=oc.n) < 0.4
+    dens = oc.density.astype(float).copy()
+    dens[drop] = 0.0
+    r1 = oracle.render(oc, A, cam, density=dens)
+    keep = np.nonzero(~drop)[0]
+    r2 = oracle.render(oc.subset(keep), A[keep], cam)
+    np.testing.assert_allclose(r1["F"], r2["F"], atol=1e-14)
+    np.testing.assert_allclose(r1["A"], r2["A"], atol=1e-14)
+
+
+def _cam64(cam, M=None):
+    """The same camera with an FP64 (exactly orthonormal up to rounding) matrix."""
+    if M is None:
+        M = sg.look_at(*_eye_target(cam))
+    return sg.Camera(cam.W, cam.H, cam.fx, cam.fy, cam.cx, cam.cy, M, cam.near, cam.far)
+
+
+def _eye_target(cam):
+    M = cam.world_to_cam.astype(np.float64)
+    eye = -M[:, :3].T @ M[:, 3]
+    return eye, eye + M[2, :3]
+
+
+def test_rigid_pose_equals_rigid_camera_motion():
+    sc = sg.preset("tiny")
+    oc = sc.octree
+    pose = sg.random_pose(9)
+    Rg = np.array([0.2, -0.4, 0.1], np.float32)
+    Tg = np.array([0.05, -0.03, 0.02], np.float32)
+    cam = _cam64(sg.orbit_camera(sc.centroid, 128, 128, az_deg=20))
+    w64 = oc.weights.astype(np.float64)
+    w64 /= w64.sum(1, keepdims=True)
+    G1 = oracle.fk(sc.skeleton, sg.Pose(pose.axis_angle, Rg, Tg))
+    A1, _ = oracle.lbs(oc, G1, w64)
+    r1 = oracle.render(oc, A1, cam)
+    # same animal without the global motion, camera moved by it:
+    # x_cam = R_c (Rg x + Tg) + t_c
+    Rm = oracle.rodrigues(Rg)
+    M = cam.world_to_cam
+    M2 = np.concatenate([M[:, :3] @ Rm, (M[:, :3] @ Tg.astype(np.float64) + M[:, 3])[:, None]], 1)
+    cam2 = _cam64(cam, M2)
+    G2 = oracle.fk(sc.skeleton, sg.Pose(pose.axis_angle, np.zeros(3, np.float32), np.zeros(3, np.float32)))
+    A2, _ = oracle.lbs(oc, G2, w64)
+    r2 = oracle.render(oc, A2, cam2)
+    assert (r1["A"] > 0).sum() > 100
+    np.testing.assert_allclose(r1["A"], r2["A"], atol=1e-9)
+    np.testing.assert_allclose(r1["F"], r2["F"], atol=1e-9)
+
+
+def test_one_hot_weights_equal_rigid_camera():
+    # All voxels bound to one joint: the warp is G_j, i.e. the canonical animal
+    # seen by the camera world_to_cam * G_j.
+    sc = sg.preset("tiny")
+    oc = sc.octree
+    w = np.zeros_like(oc.weights)
+    w[:, 0] = 1.0
+    jidx = np.full_like(oc.joint_idx, 5)
+    oc1 = sg.Octree(oc.depth, oc.origin, oc.extent, oc.ijk, jidx, w, oc.features, oc.density, oc.sdf)
+    sc1 = sg.Scene(oc1, sc.skeleton, sc.centroid, sc.scale, sc.bones, sc.capsules)
+    G, A, _ = oracle.pose_transforms(sc1, sg.random_pose(12))
+    cam = _cam64(sg.orbit_camera(sc.centroid, 128, 128, az_deg=-40))
+    r1 = oracle.render(oc1, A, cam)
+    M = cam.world_to_cam
+    Gj = G[5]
+    M2 = np.concatenate([M[:, :3] @ Gj[:, :3], (M[:, :3] @ Gj[:, 3] + M[:, 3])[:, None]], 1)
+    cam2 = sg.Camera(cam.W, cam.H, cam.fx, cam.fy, cam.cx, cam.cy, M2, cam.near, cam.far)
+    r2 = oracle.render(oc1, identity_A(oc.n), cam2)
+    assert (r1["A"] > 0).sum() > 50
+    np.testing.assert_allclose(r1["A"], r2["A"], atol=1e-10)
+    np.testing.assert_allclose(r1["F"], r2["F"], atol=1e-10)
+
+
+def test_voxel_order_invariance():
+    sc = sg.preset("mini")
+    oc = sc.octree
+    cam = sg.orbit_camera(sc.centroid, 64, 64, az_deg=120)
+    _, A, _ = oracle.pose_transforms(sc, sg.random_pose(3))
+    perm = np.random.default_rng(2).permutation(oc.n)
+    r1 = oracle.render(oc, A, cam)
+    r2 = oracle.render(oc.subset(perm), A[perm], cam)
+    np.testing.assert_allclose(r1["F"], r2["F"], atol=1e-12)
+    np.testing.assert_allclose(r1["A"], r2["A"], atol=1e-12)
+
+
+def test_degenerate_blend_dropped():
+    # Blending a joint with its 180-degree rotated copy gives det ~ 0.
+    oc = make_octree([[8, 8, 8]], C=1, jidx=[[0, 1, 0, 0]], w=[[0.5, 0.5, 0.0, 0.0]])
+    sk = one_joint_skeleton(2)
+    aa = np.zeros((2, 3), np.float32)
+    aa[1] = [0, math.pi, 0]
+    G = oracle.fk(sk, sg.Pose(aa, np.zeros(3, np.float32), np.zeros(3, np.float32)))
+    sc = sg.Scene(oc, sk, np.zeros(3), 1.0, None, [])
+    A, det = oracle.lbs(oc, G)
+    assert det[0] < 1e-3
+    cam = axis_camera(A[0][:, 3] + A[0][:, :3] @ voxel_center(oc, 0), (0, 0, 1))
+    assert oracle.render(oc, A, cam)["nhit"][0, 0] == 0
+    assert oracle.voxel_bounds(oc, A, cam)[0, 0] == 0
+
+
+# ---------------------------------------------------------------------------
+# screen-tile coverage
+# ---------------------------------------------------------------------------
+
+def test_tile_pairs_match_brute_force_bbox_and_cover_hits():
+    sc = sg.preset("mini")
+    oc = sc.octree
+    cam = sg.orbit_camera(sc.centroid, 80, 72, az_deg=60)
+    _, A, _ = oracle.pose_transforms(sc, sg.random_pose(6))
+    ts = 16
+    tiles, vids = oracle.tile_pairs(oc, A, cam, ts)
+    vb = oracle.voxel_bounds(oc, A, cam)
+    tw = (cam.W + ts - 1) // ts
+    px = np.arange(cam.W) + 0.5
+    py = np.arange(cam.H) + 0.5
+    want = set()
+    for i in range(oc.n):
+        ok, u0, u1, v0, v1, d0, d1 = vb[i]
+        if not ok or d0 > cam.far or d1 < cam.near:
+            continue
+        xs = np.nonzero((px >= u0) & (px <= u1))[0]
+        ys = np.nonzero((py >= v0) & (py <= v1))[0]
+        for ty in set(ys // ts):
+            for tx in set(xs // ts):
+                want.add((int(ty * tw + tx), i))
+    got = set(zip(tiles.tolist(), vids.tolist()))
+    assert got == want
+    r = oracle.render(oc, A, cam, hits=True)
+    for p in range(cam.W * cam.H):
+        y, x = divmod(p, cam.W)
+        t = (y // ts) * tw + x // ts
+        for i in r["hit_id"][r["hit_off"][p]:r["hit_off"][p + 1]]:
+            assert (t, int(i)) in got
+
+
+# ---------------------------------------------------------------------------
+# shading network primitives vs torch (FP64, CPU)
+# ---------------------------------------------------------------------------
+
+def test_conv_pool_upsample_match_torch():
+    torch = pytest.importorskip("torch")
+    import torch.nn.functional as Fn
+    rng = np.random.default_rng(0)
+    for (H, W, Cin, Cout, k) in [(9, 7, 5, 6, 3), (8, 12, 3, 4, 1), (1, 1, 2, 3, 3)]:
+        x = rng.standard_normal((H, W, Cin))
+        w = rng.standard_normal((Cout, k, k, Cin))
+        b = rng.standard_normal(Cout)
+        tx = torch.from_numpy(x).permute(2, 0, 1)[None]
+        tw = torch.from_numpy(w).permute(0, 3, 1, 2)
+        ref = Fn.conv2d(tx, tw, torch.from_numpy(b), padding=k // 2)[0].permute(1, 2, 0).numpy()
+        np.testing.assert_allclose(oracle.conv2d(x, w, b, oracle.ACT_NONE), ref, atol=1e-12)
+        np.testing.assert_allclose(oracle.conv2d(x, w, b, oracle.ACT_RELU), np.maximum(ref, 0), atol=1e-12)
+        np.testing.assert_allclose(oracle.conv2d(x, w, b, oracle.ACT_SIGMOID),
+                                   torch.sigmoid(torch.from_numpy(ref)).numpy(), atol=1e-12)
+    x = rng.standard_normal((6, 10, 3))
+    tx = torch.from_numpy(x).permute(2, 0, 1)[None]
+    np.testing.assert_array_equal(oracle.maxpool2(x), Fn.max_pool2d(tx, 2)[0].permute(1, 2, 0).numpy())
+    np.testing.assert_array_equal(oracle.upsample2(x),
+                                  Fn.interpolate(tx, scale_factor=2, mode="nearest")[0].permute(1, 2, 0).numpy())
+
+
+def test_unet_matches_torch_composition():
+    torch = pytest.importorskip("torch")
+    import torch.nn.functional as Fn
+    layers = sg.unet_weights(3, cin=5, ch=(4, 6, 8, 10))
+    x = np.random.default_rng(1).standard_normal((16, 24, 5))
+    got = oracle.shade_unet(x, layers)
+
+    def conv(t, wb, act):
+        w, b = wb
+        y = Fn.conv2d(t, torch.from_numpy(w.astype(np.float64)).permute(0, 3, 1, 2),
+                      torch.from_numpy(b.astype(np.float64)), padding=w.shape[1] // 2)
+        return torch.relu(y) if act == "relu" else torch.sigmoid(y)
+
+    t = torch.from_numpy(x).permute(2, 0, 1)[None]
+    L = list(layers)
+    e0 = conv(conv(t, L[0], "relu"), L[1], "relu")
+    e1 = conv(conv(Fn.max_pool2d(e0, 2), L[2], "relu"), L[3], "relu")
+    e2 = conv(conv(Fn.max_pool2d(e1, 2), L[4], "relu"), L[5], "relu")
+    e3 = conv(conv(Fn.max_pool2d(e2, 2), L[6], "relu"), L[7], "relu")
+    up = lambda z: Fn.interpolate(z, scale_factor=2, mode="nearest")
+    d2 = conv(conv(torch.cat([up(e3), e2], 1), L[8], "relu"), L[9], "relu")
+    d1 = conv(conv(torch.cat([up(d2), e1], 1), L[10], "relu"), L[11], "relu")
+    d0 = conv(conv(torch.cat([up(d1), e0], 1), L[12], "relu"), L[13], "relu")
+    ref = conv(d0, L[14], "sigmoid")[0].permute(1, 2, 0).numpy()
+    np.testing.assert_allclose(got, ref, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# gradients vs central finite differences
+# ---------------------------------------------------------------------------
+
+def _loss_setup(seed=0):
+    sc = sg.preset("mini")
+    oc = sc.octree
+    cam = sg.orbit_camera(sc.centroid, 48, 48, az_deg=70)
+    pose = sg.random_pose(seed + 21)
+    G, A, _ = oracle.pose_transforms(sc, pose)
+    rng = np.random.default_rng(seed)
+    tgtF = rng.standard_normal((cam.H, cam.W, oc.C)) * 0.1
+    tgtA = rng.uniform(0, 1, (cam.H, cam.W))
+    return sc, oc, cam, pose, G, A, tgtF, tgtA
+
+
+def _loss(oc, A, cam, tgtF, tgtA, features=None, density=None):
+    r = oracle.render(oc, A, cam, features=features, density=density)
+    return 0.5 * np.sum((r["F"] - tgtF) ** 2) + 0.5 * np.sum((r["A"] - tgtA) ** 2), r
+
+
+def test_backward_matches_finite_differences():
+    sc, oc, cam, pose, G, A, tgtF, tgtA = _loss_setup()
+    L0, r = _loss(oc, A, cam, tgtF, tgtA)
+    gF, gA = r["F"] - tgtF, r["A"] - tgtA
+    gfeat, gsig, gAinv = oracle.render_backward(oc, A, cam, gF, gA)
+    _, gw = oracle.lbs_backward(oc, G, A, gAinv)
+    hitv = np.nonzero(np.abs(gsig) > 0)[0]
+    assert len(hitv) > 50
+    rng = np.random.default_rng(5)
+    h = 1e-3
+    feats = oc.features.astype(np.float64)
+    dens = oc.density.astype(np.float64)
+    # features: F is linear in f, so the central difference is exact
+    for i in rng.choice(hitv, 20, replace=False):
+        c = int(rng.integers(oc.C))
+        fp, fm = feats.copy(), feats.copy()
+        fp[i, c] += h
+        fm[i, c] -= h
+        fd = (_loss(oc, A, cam, tgtF, tgtA, features=fp)[0] - _loss(oc, A, cam, tgtF, tgtA, features=fm)[0]) / (2 * h)
+        np.testing.assert_allclose(gfeat[i, c], fd, rtol=1e-6, atol=1e-10)
+    # densities
+    for i in rng.choice(hitv, 20, replace=False):
+        dp, dm = dens.copy(), dens.copy()
+        dp[i] += h
+        dm[i] -= h
+        fd = (_loss(oc, A, cam, tgtF, tgtA, density=dp)[0] - _loss(oc, A, cam, tgtF, tgtA, density=dm)[0]) / (2 * h)
+        np.testing.assert_allclose(gsig[i], fd, rtol=1e-5, atol=1e-9)
+    # skinning weights (geometry): skip samples whose hit set changes under +-h
+    checked = 0
+    w = oc.weights.astype(np.float64)
+    base_hits = oracle.render(oc, A, cam, hits=True)
+    for i in rng.choice(hitv, 60, replace=False):
+        k = int(rng.integers(4))
+        wp, wm = w.copy(), w.copy()
+        hw = 1e-5
+        wp[i, k] += hw
+        wm[i, k] -= hw
+        Ap, _ = oracle.lbs(oc, G, wp)
+        Am, _ = oracle.lbs(oc, G, wm)
+        rp = oracle.render(oc, Ap, cam, hits=True)
+        rm = oracle.render(oc, Am, cam, hits=True)
+        same = (np.array_equal(rp["hit_id"], base_hits["hit_id"]) and np.array_equal(rm["hit_id"], base_hits["hit_id"])
+                and np.array_equal(rp["hit_off"], base_hits["hit_off"]) and np.array_equal(rm["hit_off"], base_hits["hit_off"]))
+        if not same:
+            continue
+        Lp = 0.5 * np.sum((rp["F"] - tgtF) ** 2) + 0.5 * np.sum((rp["A"] - tgtA) ** 2)
+        Lm = 0.5 * np.sum((rm["F"] - tgtF) ** 2) + 0.5 * np.sum((rm["A"] - tgtA) ** 2)
+        fd = (Lp - Lm) / (2 * hw)
+        np.testing.assert_allclose(gw[i, k], fd, rtol=2e-4, atol=1e-7)
+        checked += 1
+    assert checked >= 20
+
+
+def test_lbs_backward_matrix_inverse_gradient():
+    # dL/dA from dL/dAinv against finite differences of the affine inverse.
+    rng = np.random.default_rng(0)
+    oc = make_octree([[1, 2, 3]], C=1, jidx=[[0, 1, 0, 0]], w=[[0.6, 0.4, 0.0, 0.0]])
+    G = np.stack([np.hstack([oracle.rodrigues(rng.standard_normal(3) * 0.5), rng.standard_normal((3, 1)) * 0.1])
+                  for _ in range(2)])
+    A, _ = oracle.lbs(oc, G)
+    gAinv = rng.standard_normal((1, 3, 4))
+
+    def inv_aff(M):
+        M4 = np.vstack([M, [0, 0, 0, 1]])
+        return np.linalg.inv(M4)[:3]
+
+    gA, gw = oracle.lbs_backward(oc, G, A, gAinv)
+    h = 1e-6
+    for r_ in range(3):
+        for c_ in range(4):
+            Ap, Am = A[0].copy(), A[0].copy()
+            Ap[r_, c_] += h
+            Am[r_, c_] -= h
+            fd = (np.sum(gAinv[0] * inv_aff(Ap)) - np.sum(gAinv[0] * inv_aff(Am))) / (2 * h)
+            np.testing.assert_allclose(gA[0, r_, c_], fd, rtol=1e-6, atol=1e-9)
+    np.testing.assert_allclose(gw[0, 0], np.sum(gA[0] * G[0]), rtol=1e-12)
+    np.testing.assert_allclose(gw[0, 1], np.sum(gA[0] * G[1]), rtol=1e-12)
