@@ -1,0 +1,345 @@
+"""Frame-rate benchmark of the GB300 ARTEMIS rendering path.
+
+One step = one frame of one view: pose -> LBS warp of ~1M leaf voxels ->
+screen-tile binning + radix sort -> exact-hit front-to-back compositing of
+F (32 channels) and A at 1024x1024 -> 4-level U-Net shading -> RGBA.
+Poses follow a 60-frame walk cycle; the camera orbits 8 azimuths.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Prints one JSON line (rank 0).  Multi-GPU runs are independent replicas
+(the path has no exchange step): value = frames of all ranks / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "frames/s @1M voxels 1024²: BF16+learned-skip vs FP32 plain, PSNR≥45dB vs FP64"
+WORKLOAD = "1M-voxel quadruped octree (depth 10, C=32), 1024x1024 view, 4-level U-Net 32-64-128-256"
+RES = 1024
+N_AZ = 8
+N_POSES = 60
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=60)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--form", default="bf16", choices=["bf16", "f32"])
+    p.add_argument("--f32-steps", type=int, default=16, help="steps of the FP32 plain form measured beside")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------- workload
+
+def workload():
+    import scenegen as sg
+    sc = sg.preset("paper")
+    cams = [sg.orbit_camera(sc.centroid, RES, RES, az_deg=45.0 * k) for k in range(N_AZ)]
+    poses = [sg.walk_pose(f, N_POSES) for f in range(N_POSES)]
+    layers = sg.unet_weights(0, cin=sc.octree.C)
+    return sc, cams, poses, layers
+
+
+def step_indices(k):
+    return k % N_POSES, (k // N_POSES + k) % N_AZ
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def setup_renderer(sc, cams, layers, form, profile=False):
+    import paper_2202_05628_gb300 as art
+    oc = sc.octree
+    r = art.Renderer()
+    storage = "bf16" if form == "bf16" else "f32"
+    r.load_octree(oc.depth, oc.origin, oc.extent, oc.ijk, oc.joint_idx, oc.weights, oc.features, oc.density, storage)
+    r.load_skeleton(sc.skeleton.parent, sc.skeleton.rest)
+    r.load_shader(art.ART_NET_UNET, oc.C, [32, 64, 128, 256], 4, art.flat_params(layers), form)
+    r.set_config(tau=1e-4, profile=profile)
+    for v, c in enumerate(cams):
+        r.set_camera(v, c.W, c.H, c.fx, c.fy, c.cx, c.cy, c.world_to_cam, c.near, c.far)
+    return r
+
+
+def run_steps(r, poses, steps, warmup, flush, stream, rgba):
+    """Warm-up, then `steps` frames timed one by one with CUDA events on the
+    library's stream; the L2 is flushed between frames outside the events."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(warmup):
+        pi, vi = step_indices(k)
+        p = poses[pi]
+        r.render_frame(vi, p.axis_angle, p.R, p.T, rgba)
+    torch.cuda.synchronize()
+    return ev
+
+
+def timed_region(r, poses, steps, warmup, flush, rgba):
+    import torch
+    stream = torch.cuda.current_stream()
+    ev = run_steps(r, poses, steps, warmup, flush, stream, rgba)
+    r.kernel_times(reset=True)
+    l0 = r.sync_status()["kernel_launches"]
+    for k in range(steps):
+        pi, vi = step_indices(warmup + k)
+        p = poses[pi]
+        flush.zero_()
+        ev[k][0].record(stream)
+        r.render_frame(vi, p.axis_angle, p.R, p.T, rgba)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    launches = r.sync_status()["kernel_launches"] - l0
+    return ms, launches
+
+
+def roofline(kt, stats, peaks, form, n_vox, C):
+    """Achieved rate of the dominant kernel from its measured launch times."""
+    name, (nl, tot) = max(kt.items(), key=lambda kv: kv[1][1])
+    avg_ms = tot / max(nl, 1)
+    out = {"kernel": name, "launches": nl, "avg_ms": avg_ms}
+    if name.startswith("conv"):
+        flops = unet_flops(RES, RES)
+        per_launch = flops / 15.0  # the U-Net issues 15 convolution launches per frame
+        ach = per_launch / (avg_ms * 1e-3) / 1e12
+        peak = peaks.get("bf16_tflops_sustained" if form == "bf16" else "bf16_tflops", 1713.7)
+        if form == "f32":
+            peak = 2.0 * 152 * 128 * 2.07e9 / 1e12  # FP32 FMA issue rate (CUDA cores)
+        out.update(bound="tensor" if form == "bf16" else "alu", achieved=ach, peak=peak, unit="TFLOP/s",
+                   frac=ach / peak, traffic=None)
+    else:
+        fb = 2 if form == "bf16" else 4
+        inst = stats["instances"]
+        per_inst = 4 + 4 + 64 + 8 + C * fb
+        byts = inst * per_inst + RES * RES * (C * fb + 4)
+        if name == "lbs":
+            byts = n_vox * 160
+        ach = byts / (avg_ms * 1e-3) / 1e9
+        peak = peaks.get("hbm_gbs", 6783.5)
+        out.update(bound="hbm", achieved=ach, peak=peak, unit="GB/s", frac=ach / peak, traffic=None)
+    return out
+
+
+def unet_flops(H, W, cin=32, ch=(32, 64, 128, 256)):
+    import scenegen as sg
+    tot = 0
+    shapes = sg.unet_layer_shapes(cin, ch)
+    lvl = [0, 0, 1, 1, 2, 2, 3, 3, 2, 2, 1, 1, 0, 0, 0]
+    for (co, ci, k), l in zip(shapes, lvl):
+        tot += 2 * (H >> l) * (W >> l) * co * ci * k * k
+    return tot
+
+
+def gpu_arm(args):
+    import torch
+    import torch.distributed as dist
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    sc, cams, poses, layers = workload()
+    oc = sc.octree
+    rgba = torch.empty((RES, RES, 4), dtype=torch.float32, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    r = setup_renderer(sc, cams, layers, args.form, profile=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ms, launches = timed_region(r, poses, args.steps, args.warmup, flush, rgba)
+    torch.cuda.synchronize()
+    kt = r.kernel_times(reset=True)
+    stats = r.sync_status(raise_on_overflow=False)
+    t_local = float(np.sum(ms))
+    if world > 1:
+        t = torch.tensor([t_local], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    else:
+        t_max = t_local
+    value = world * args.steps / (t_max * 1e-3)
+    result = {
+        "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16" if args.form == "bf16" else "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "voxels": oc.n, "resolution": [RES, RES], "features": oc.C,
+                   "form": "BF16 features + BF16 tensor-core U-Net (plain traversal)" if args.form == "bf16"
+                   else "FP32 plain", "poses": "60-frame walk cycle x 8 azimuths",
+                   "l2": "flushed between timed frames (256 MB write outside the events)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        "roofline": roofline(kt, stats, peaks, args.form, oc.n, oc.C),
+        "kernels_ms_per_frame": {k: round(v[1] / args.steps, 4) for k, v in sorted(kt.items(), key=lambda kv: -kv[1][1])},
+        "instances": stats["instances"], "overflow": stats["status"],
+    }
+    r.close()
+    # FP32 plain form beside it (same workload, fewer frames)
+    if args.form == "bf16" and args.f32_steps > 0:
+        r32 = setup_renderer(sc, cams, layers, "f32")
+        ms32, _ = timed_region(r32, poses, args.f32_steps, 2, flush, rgba)
+        result["f32_plain"] = {"value": 1e3 * args.f32_steps / float(np.sum(ms32)),
+                               "ms_per_step": float(np.mean(ms32)), "steps": args.f32_steps}
+        r32.close()
+    # end to end through the public call with host buffers
+    if not args.no_e2e:
+        r = setup_renderer(sc, cams, layers, args.form)
+        host_out = torch.empty((RES, RES, 4), dtype=torch.float32, pin_memory=True)
+        host_pose = [(torch.from_numpy(p.axis_angle).pin_memory(), torch.from_numpy(p.R).pin_memory(),
+                      torch.from_numpy(p.T).pin_memory()) for p in poses]
+        k_e2e = max(4, min(args.steps, 30))
+        for k in range(2):
+            pi, vi = step_indices(k)
+            r.render_frame(vi, *host_pose[pi], host_out)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(k_e2e):
+            pi, vi = step_indices(k)
+            r.render_frame(vi, *host_pose[pi], host_out)  # synchronous: copies RGBA back to the host
+        t1 = time.perf_counter()
+        result["e2e"] = {"value": k_e2e / (t1 - t0), "unit": "frames/s",
+                         "h2d_bytes_per_step": int(sum(x.numel() * 4 for x in host_pose[0])),
+                         "d2h_bytes_per_step": int(host_out.numel() * 4), "steps": k_e2e}
+        r.close()
+    if rank == 0 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(sc, cams, poses, layers)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(result))
+
+
+# ---------------------------------------------------------------- oracle arm
+
+def cpu_baseline(sc, cams, poses, layers, frames=1):
+    """The FP64 oracle as it stands on the host cores: whole frames (render
+    + U-Net) of the same workload."""
+    import oracle
+    t0 = time.perf_counter()
+    for k in range(frames):
+        pi, vi = step_indices(k)
+        oracle.render_frame(sc, poses[pi], cams[vi], layers)
+    dt = time.perf_counter() - t0
+    return {"value": frames / dt, "unit": "frames/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{frames} full frame(s) (pose {step_indices(0)[0]}, azimuth 0): FP64 render + U-Net"}
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sc, cams, poses, layers = workload()
+    import oracle
+    oracle.build()
+    frames = []
+    for k in range(args.warmup + args.steps if args.steps <= 2 else 2):
+        pass
+    t_all = 0.0
+    K = max(1, min(args.steps, 2))
+    for k in range(K):
+        pi, vi = step_indices(k)
+        t0 = time.perf_counter()
+        oracle.render_frame(sc, poses[pi], cams[vi], layers)
+        t_all += time.perf_counter() - t0
+    v = K / t_all
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "frames/s", "n_gpus": args.gpus,
+           "steps": K, "warmup": 0, "ms_per_step": 1e3 * t_all / K, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "voxels": sc.octree.n, "resolution": [RES, RES]},
+           "cpu_baseline": {"value": v, "unit": "frames/s", "cores": oracle.num_threads(), "kind": "oracle",
+                            "sample": f"{K} full frame(s) of the workload (FP64 render + U-Net)"},
+           "e2e": {"value": v, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,263 @@
+/*
+ * artemis.h - C ABI of the GB300 rendering path of ARTEMIS neural animals
+ * (arXiv 2202.05628, Sec. 3.1 "Animatable Neural Volumes").
+ *
+ * The library renders, per frame, the paper's pipeline: skeleton pose ->
+ * linear-blend-skinning warp of the canonical octree's leaf voxels (Eq. 4) ->
+ * per-pixel indexing of the warped voxels -> front-to-back compositing of the
+ * voxel features and densities into the feature map F and coarse opacity map
+ * A (Eq. 5-6, early stop) -> neural shading network -> RGBA ("Neural
+ * Shading").  The call sequence follows the order stated in Sec. 5
+ * ("Implementations Details"): pose, LBS, indexing, tracing, shading.
+ *
+ * Conventions (all calls):
+ *   - Every call returns an art_status; ART_OK is 0.  On failure the context
+ *     keeps a message readable with art_last_error().  No C++ exception
+ *     crosses this boundary.
+ *   - Work is enqueued asynchronously on the context's CUDA stream (borrowed,
+ *     never destroyed by the library).  Calls that take HOST output pointers
+ *     synchronise the stream before returning; calls with DEVICE outputs do
+ *     not.  art_sync_status() synchronises and reports device-side errors.
+ *   - Pointer arguments may be host or device memory unless stated; the
+ *     library tells them apart with cudaPointerGetAttributes.  Inputs are
+ *     copied into library-owned device memory; the caller keeps ownership of
+ *     everything it passes.
+ *   - All arrays are dense, row-major, with the layouts given per argument.
+ *   - A context is not thread-safe; use one per host thread / stream.
+ */
+#ifndef ARTEMIS_H
+#define ARTEMIS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct art_ctx art_ctx;
+
+typedef enum {
+  ART_OK = 0,
+  ART_ERR_INVALID_ARG = 1, /* bad size, null pointer, out-of-range index */
+  ART_ERR_CUDA = 2,        /* a CUDA runtime call failed */
+  ART_ERR_OOM = 3,         /* device allocation failed */
+  ART_ERR_OVERFLOW = 4,    /* a device-side capacity was exceeded (see art_stats) */
+  ART_ERR_STATE = 5,       /* call out of order (e.g. render before load) */
+  ART_ERR_UNSUPPORTED = 6  /* a configuration this build does not provide */
+} art_status;
+
+/* element types */
+enum { ART_F32 = 0, ART_BF16 = 1, ART_F16 = 2, ART_FP8 = 3 };
+
+/* shading network architectures (Sec. 3.1 "Neural Shading"; the single-branch
+ * "Light" form of Sec. 6 "Runtime Analysis", RGB and alpha from one net) */
+enum { ART_NET_TINY = 0, ART_NET_UNET = 1 };
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context bound to cuda_stream (a cudaStream_t; NULL = legacy
+ * default stream) on the current device.  *out receives the context. */
+art_status art_create(art_ctx** out, void* cuda_stream);
+
+/* Release every device buffer of the context.  NULL is ignored. */
+void art_destroy(art_ctx* ctx);
+
+/* Message of the last failed call; owned by ctx, valid until the next call. */
+const char* art_last_error(const art_ctx* ctx);
+
+/* Rebind the context to another stream (cudaStream_t). */
+art_status art_set_stream(art_ctx* ctx, void* cuda_stream);
+
+/* ------------------------------------------------------------------ scene */
+
+/*
+ * Load the canonical octree's leaf voxels and their feature look-up table
+ * (Sec. 3.1 "Octree Feature Indexing": voxel array P and FLUT F; skinning
+ * weights of "Rigging and Deformation").
+ *   n            number of leaf voxels (1 .. 2^31-1)
+ *   depth        octree depth; voxel side h = extent / 2^depth (depth <= 16)
+ *   origin[3]    world position of the octree cube's minimum corner (metres)
+ *   extent       side of the octree cube (metres, > 0)
+ *   ijk          [n][3] uint16 integer voxel coordinates, each < 2^depth;
+ *                voxel i is the cube origin + (ijk_i + [0,1]^3) h
+ *   joint_idx    [n][4] uint8 joint of each skinning weight (< J of the skeleton)
+ *   weights      [n][4] float skinning weights (used as given: the library
+ *                does not renormalise)
+ *   features     [n][C] float features (FP32); stored on the device in
+ *                storage_dtype (ART_F32, ART_BF16 or ART_F16, rounded to
+ *                nearest even)
+ *   C            feature channels: 4, 8, 16 or 32
+ *   density      [n] float density sigma_i (1/m, >= 0)
+ * Replaces any previously loaded octree.
+ */
+art_status art_load_octree(art_ctx* ctx, int64_t n, int depth, const float origin[3], float extent,
+                           const uint16_t* ijk, const uint8_t* joint_idx, const float* weights,
+                           const float* features, int C, int storage_dtype, const float* density);
+
+/*
+ * Load the skeleton (Sec. 3.1: S = {r, R, T} over J joints).
+ *   J         number of joints, 1 .. 64
+ *   parent    [J] int32 parent joint, parent[0] = -1 and parent[j] < j
+ *   rest_pos  [J][3] float joint positions in the canonical pose (metres);
+ *             canonical joint rotations are zero, so M^c_j = [I | rest_j]
+ */
+art_status art_load_skeleton(art_ctx* ctx, int J, const int32_t* parent, const float* rest_pos);
+
+/*
+ * Set the target pose S_t and warp every voxel (Eq. 4): forward kinematics
+ * M^t_j = M^t_parent(j) [Rod(r_j) | rest_j - rest_parent(j)], the root
+ * premultiplied by [Rod(R) | T]; G_j = M^t_j (M^c_j)^-1; per voxel the blended
+ * A_i = sum_k w_ik G_{j_ik}, its inverse, and its warped bounding data.
+ *   axis_angle  [J][3] joint rotations r (axis-angle, radians)
+ *   R[3], T[3]  global rotation (axis-angle) and translation (metres)
+ * Voxels whose blended 3x3 part has det < 1e-3 are dropped from rendering and
+ * counted in art_stats.degenerate.
+ */
+art_status art_set_pose(art_ctx* ctx, const float* axis_angle, const float R[3], const float T[3]);
+
+/*
+ * Set camera `view` (0 .. 7): pinhole with intrinsics fx, fy, cx, cy in
+ * pixels, world_to_cam[12] the 3x4 row-major [R | t] (x_cam = R x + t; +x
+ * right, +y down, +z forward), image W x H (1 .. 8192 each).  Pixel (x, y) is
+ * sampled at its centre; its ray is o = -R^T t, d = R^T dc / |R^T dc| with
+ * dc = ((x+1/2-cx)/fx, (y+1/2-cy)/fy, 1).  znear < zfar are distances along
+ * the unit ray.
+ */
+art_status art_set_camera(art_ctx* ctx, int view, int W, int H, float fx, float fy, float cx, float cy,
+                          const float world_to_cam[12], float znear, float zfar);
+
+/* --------------------------------------------------------------- rendering */
+
+/*
+ * Render the feature map F and coarse opacity map A of `view` under the
+ * current pose (Eq. 5-6): each pixel ray is intersected exactly with every
+ * warped voxel (the parallelepiped A_i * cube_i) that the screen-tile index
+ * lists for its tile; hits are composited front to back in order of entry
+ * distance, F = sum_i T_i (1 - exp(-sigma_i delta_i)) f_i with
+ * T_i = prod_{j<i} exp(-sigma_j delta_j), stopping after the hit at which
+ * T < tau (art_config.tau, default 1e-4); A = 1 - T.
+ *   F_out   [H][W][C] in F_dtype (ART_F32 or ART_BF16); device or host
+ *   A_out   [H][W] float; device or host (may be NULL)
+ * Background pixels get F = 0, A = 0.
+ */
+art_status art_render_feature_maps(art_ctx* ctx, int view, void* F_out, int F_dtype, float* A_out);
+
+/* ----------------------------------------------------------------- shading */
+
+typedef struct {
+  int arch;     /* ART_NET_TINY or ART_NET_UNET */
+  int cin;      /* input channels (= C of the feature map) */
+  int ch[4];    /* TINY: ch[0] hidden width; UNET: widths of the 4 levels */
+  int cout;     /* output channels (4 = RGBA) */
+} art_net_desc;
+
+/*
+ * Load the shading network G (Sec. 3.1 "Neural Shading").
+ * TINY: conv3x3 cin->ch0, ReLU, conv3x3 ch0->ch0, ReLU, conv3x3 ch0->cout,
+ *       sigmoid.
+ * UNET: 4 levels; per level two conv3x3 + ReLU; 2x2 max-pool between
+ *       levels; decoder: nearest x2 upsample, channel concat [upsampled,
+ *       skip], two conv3x3 + ReLU; head conv1x1 -> cout, sigmoid.
+ * params: float array, for every layer in execution order its weights
+ *   [Cout][k][k][Cin] followed by its bias [Cout]; n_params must match.
+ * compute_dtype: ART_F32 (CUDA-core FP32), ART_BF16 (tensor cores, BF16
+ *   operands, FP32 accumulation) or ART_FP8 (E4M3 operands with per-output-
+ *   channel weight scales and per-tensor activation scales).
+ */
+art_status art_load_shader(art_ctx* ctx, const art_net_desc* desc, const float* params, int64_t n_params,
+                           int compute_dtype);
+
+/*
+ * Shade feature map F ([H][W][cin] in F_dtype, H and W of `view`, both
+ * multiples of 8 for UNET) into rgba_out [H][W][cout] float (device or host).
+ */
+art_status art_shade(art_ctx* ctx, int view, const void* F, int F_dtype, float* rgba_out);
+
+/* One frame of one view: art_set_pose + art_render_feature_maps into
+ * library-owned buffers + art_shade.  rgba_out as in art_shade. */
+art_status art_render_frame(art_ctx* ctx, int view, const float* axis_angle, const float R[3], const float T[3],
+                            float* rgba_out);
+
+/* ------------------------------------------------------------ configuration */
+
+typedef struct {
+  float tau;               /* early-stop transmittance (default 1e-4) */
+  int64_t instance_cap;    /* capacity of (tile, voxel) instances; 0 = 4 n + 65536 */
+  int tile_log2;           /* log2 of the screen-tile width: 3 (8 x 4 pixel tiles, the only size built) */
+  int profile;             /* 1: time every kernel with CUDA events (art_get_kernel_times) */
+} art_config;
+
+/* Replace the configuration (NULL restores the defaults). */
+art_status art_set_config(art_ctx* ctx, const art_config* cfg);
+
+typedef struct {
+  int64_t instances;       /* (tile, voxel) instances of the last render */
+  int64_t degenerate;      /* voxels dropped at the last pose (det < 1e-3) */
+  int64_t overflow_inst;   /* instances that did not fit instance_cap */
+  int64_t overflow_order;  /* pixel hits released early because the per-pixel
+                              reorder buffer was full (result may be out of order) */
+  int64_t kernel_launches; /* kernels launched by this context so far */
+} art_stats;
+
+/* Synchronise the stream, fill *out (may be NULL) and return
+ * ART_ERR_OVERFLOW if a device-side capacity was exceeded since the last
+ * call (the flags are then cleared), else ART_OK. */
+art_status art_sync_status(art_ctx* ctx, art_stats* out);
+
+/*
+ * Per-kernel timing (config.profile = 1): for up to `cap` kernels, names[i]
+ * (static strings), launches[i] and total milliseconds[i] accumulated since
+ * the last reset.  *count receives the number of distinct kernels.  The
+ * stream is synchronised.  reset != 0 clears the accumulators afterwards.
+ */
+art_status art_get_kernel_times(art_ctx* ctx, int cap, const char** names, int64_t* launches, double* ms,
+                                int* count, int reset);
+
+
+/* ---------------------------------------------------------- building blocks */
+
+/*
+ * Stable LSD radix sort of (key, value) pairs by the low key_bits bits of
+ * the keys (key_bits in {8, 16, 24, 32}), the sort that orders the screen-tile
+ * instances by (tile, depth).  keys, vals: DEVICE arrays of n uint32 each
+ * (0 <= n <= 2^31 - 1), sorted in place.  Scratch (2 n pairs plus histograms)
+ * is allocated by the context on first use and kept for later calls.
+ */
+art_status art_sort_pairs(art_ctx* ctx, uint32_t* keys, uint32_t* vals, int64_t n, int key_bits);
+
+/* ------------------------------------------------------------ inspection */
+
+/* internal buffers readable with art_debug_buffer (layouts as stated) */
+enum {
+  ART_BUF_JOINT_G = 0,   /* [J][12] float: G_j = M^t_j (M^c_j)^-1 of the last pose */
+  ART_BUF_VOXEL_REC = 1, /* [n][16] float: rows of A_lin^-1 / h with cw (3 x 4), then sigma, valid, 0, 0 */
+  ART_BUF_VOXEL_GEO = 2, /* [n][16] float: (cw, r), half axes A_lin e_a h/2 (3 x (xyz, 0)) */
+  ART_BUF_RECT = 3,      /* [n][4] int16: pixel rectangle x0, y0, x1, y1 of the last render */
+  ART_BUF_DEPTHKEY = 4,  /* [n] uint32: depth quantum of the last render */
+  ART_BUF_KEYS = 5,      /* [instances] uint32 sorted keys (tile << depth_bits | depth) */
+  ART_BUF_VALS = 6,      /* [instances] uint32 voxel ids in key order */
+  ART_BUF_RANGES = 7     /* [tiles][2] uint32 [start, end) of each tile */
+};
+
+/*
+ * Copy an internal buffer of the last pose / render to host memory dst
+ * (capacity `bytes`).  *needed receives the byte size (call with dst NULL to
+ * query).  Synchronises the stream.
+ */
+art_status art_debug_buffer(art_ctx* ctx, int which, void* dst, int64_t bytes, int64_t* needed);
+
+/*
+ * Re-render `view` recording, per pixel, the composited hits in front-to-back
+ * order: count [H][W] int32 (number of composited hits, may exceed cap),
+ * ids [H][W][cap] uint32, t0/t1 [H][W][cap] float (ray parameters of entry
+ * and exit).  All four are HOST arrays.  Also writes F ([H][W][C] float,
+ * host, may be NULL) and A ([H][W] float, host, may be NULL).
+ */
+art_status art_debug_hits(art_ctx* ctx, int view, int cap, int32_t* count, uint32_t* ids, float* t0, float* t1,
+                          float* F, float* A);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ARTEMIS_H */

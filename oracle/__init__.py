@@ -242,15 +242,17 @@ def pixel_brute(octree, A: np.ndarray, cam, x: int, y: int, tau: float = TAU_DEF
     return dict(F=F, A=float(Am[0]), ids=ids[:m2], t0=t0[:m2], t1=t1[:m2], nhit=m, nused=used.value)
 
 
-def tile_pairs(octree, A: np.ndarray, cam, ts: int = 16) -> Tuple[np.ndarray, np.ndarray]:
-    """(tile id, voxel id) pairs of the screen-tile coverage, voxel-major."""
+def tile_pairs(octree, A: np.ndarray, cam, tsx: int = 8, tsy: Optional[int] = None) -> Tuple[np.ndarray, np.ndarray]:
+    """(tile id, voxel id) pairs of the screen-tile coverage (tiles of
+    tsx x tsy pixels, row-major tile ids), voxel-major."""
+    tsy = tsx if tsy is None else tsy
     b = _Bound(octree, np.asarray(A).reshape(-1, 12))
     k = _cam(cam)
     cap = 4 * octree.n + 1024
     while True:
         tile = np.zeros(cap, np.int32)
         vid = np.zeros(cap, np.int64)
-        r = _L().orc_tile_pairs(ctypes.byref(b.s), ctypes.byref(k), ctypes.c_int(ts), _p(tile),
+        r = _L().orc_tile_pairs(ctypes.byref(b.s), ctypes.byref(k), ctypes.c_int(tsx), ctypes.c_int(tsy), _p(tile),
                                 _p(vid), ctypes.c_int64(cap))
         if r >= 0:
             return tile[:r], vid[:r]

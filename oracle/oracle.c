@@ -537,17 +537,18 @@ int orc_pixels(const orc_scene* s, const orc_cam* c, int64_t np, const int32_t* 
 }
 
 /*
- * Screen-tile coverage: voxel i covers tile (tx, ty) of size ts x ts when its
+ * Screen-tile coverage: voxel i covers tile (tx, ty) of size tsx x tsy when its
  * projected-corner bounding box contains at least one pixel centre of the
  * tile.  Voxels that are degenerate, cross the camera plane, or whose
  * distance range [|c-o| - r, |c-o| + r] misses [near, far] cover nothing.
  * Writes (tile id, voxel id) pairs in voxel order; returns the pair count or
  * -(needed) when cap is too small.
  */
-int64_t orc_tile_pairs(const orc_scene* s, const orc_cam* c, int ts, int32_t* tile, int64_t* vid, int64_t cap) {
+int64_t orc_tile_pairs(const orc_scene* s, const orc_cam* c, int tsx, int tsy, int32_t* tile, int64_t* vid,
+                       int64_t cap) {
   vox_info* info = all_info(s, c);
   if (!info) return -((int64_t)1 << 41);
-  int tw = (c->W + ts - 1) / ts;
+  int tw = (c->W + tsx - 1) / tsx;
   int64_t m = 0;
   for (int64_t i = 0; i < s->n; ++i) {
     const vox_info* v = info + i;
@@ -559,8 +560,8 @@ int64_t orc_tile_pairs(const orc_scene* s, const orc_cam* c, int ts, int32_t* ti
     if (x1 > c->W - 1) x1 = c->W - 1;
     if (y1 > c->H - 1) y1 = c->H - 1;
     if (x0 > x1 || y0 > y1) continue;
-    for (int ty = y0 / ts; ty <= y1 / ts; ++ty)
-      for (int tx = x0 / ts; tx <= x1 / ts; ++tx) {
+    for (int ty = y0 / tsy; ty <= y1 / tsy; ++ty)
+      for (int tx = x0 / tsx; tx <= x1 / tsx; ++tx) {
         if (m < cap) {
           tile[m] = ty * tw + tx;
           vid[m] = i;

@@ -1,0 +1,230 @@
+"""Python binding of ``libartemis_gb.so``, the GB300 rendering path of ARTEMIS
+neural animals (arXiv 2202.05628, Sec. 3.1).
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels.  Arrays may be numpy arrays (host) or torch tensors (host or CUDA);
+device memory and streams come from PyTorch.  Importing this package raises
+if the compiled library is missing; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libartemis_gb.so")
+
+ART_F32, ART_BF16, ART_F16, ART_FP8 = 0, 1, 2, 3
+ART_NET_TINY, ART_NET_UNET = 0, 1
+BUF_JOINT_G, BUF_VOXEL_REC, BUF_VOXEL_GEO, BUF_RECT, BUF_DEPTHKEY, BUF_KEYS, BUF_VALS, BUF_RANGES = range(8)
+_STATUS = {0: "ART_OK", 1: "ART_ERR_INVALID_ARG", 2: "ART_ERR_CUDA", 3: "ART_ERR_OOM", 4: "ART_ERR_OVERFLOW",
+           5: "ART_ERR_STATE", 6: "ART_ERR_UNSUPPORTED"}
+DTYPES = {"f32": ART_F32, "bf16": ART_BF16, "f16": ART_F16, "fp8": ART_FP8}
+
+
+class ArtemisError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class NetDesc(ctypes.Structure):
+    _fields_ = [("arch", ctypes.c_int), ("cin", ctypes.c_int), ("ch", ctypes.c_int * 4), ("cout", ctypes.c_int)]
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_float), ("instance_cap", ctypes.c_int64), ("tile_log2", ctypes.c_int),
+                ("profile", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("instances", ctypes.c_int64), ("degenerate", ctypes.c_int64), ("overflow_inst", ctypes.c_int64),
+                ("overflow_order", ctypes.c_int64), ("kernel_launches", ctypes.c_int64)]
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with paper_2202_05628_gb300.build.build() "
+                          "(or __graft_entry__.build()); there is no CPU fallback")
+    lib = ctypes.CDLL(path)
+    vp, i64, i32, f32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_float
+    sig = {
+        "art_create": [ctypes.POINTER(vp), vp],
+        "art_set_stream": [vp, vp],
+        "art_load_octree": [vp, i64, i32, vp, f32, vp, vp, vp, vp, i32, i32, vp],
+        "art_load_skeleton": [vp, i32, vp, vp],
+        "art_set_pose": [vp, vp, vp, vp],
+        "art_set_camera": [vp, i32, i32, i32, f32, f32, f32, f32, vp, f32, f32],
+        "art_render_feature_maps": [vp, i32, vp, i32, vp],
+        "art_load_shader": [vp, ctypes.POINTER(NetDesc), vp, i64, i32],
+        "art_shade": [vp, i32, vp, i32, vp],
+        "art_render_frame": [vp, i32, vp, vp, vp, vp],
+        "art_set_config": [vp, ctypes.POINTER(Config)],
+        "art_sync_status": [vp, ctypes.POINTER(Stats)],
+        "art_get_kernel_times": [vp, i32, vp, vp, vp, ctypes.POINTER(i32), i32],
+        "art_sort_pairs": [vp, vp, vp, i64, i32],
+        "art_debug_buffer": [vp, i32, vp, i64, ctypes.POINTER(i64)],
+        "art_debug_hits": [vp, i32, i32, vp, vp, vp, vp, vp, vp],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.art_destroy.argtypes = [vp]
+    lib.art_destroy.restype = None
+    lib.art_last_error.argtypes = [vp]
+    lib.art_last_error.restype = ctypes.c_char_p
+    return lib
+
+
+_lib = load_library()
+
+
+def library() -> ctypes.CDLL:
+    return _lib
+
+
+def _ptr(x) -> Optional[int]:
+    """Address of a numpy array or torch tensor (contiguous)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"], "array must be C-contiguous"
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        assert x.is_contiguous(), "tensor must be contiguous"
+        return x.data_ptr()
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+def _np(x, dtype) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(x, dtype=dtype))
+
+
+class Renderer:
+    """One library context on one CUDA stream."""
+
+    def __init__(self, stream=None):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self._stream = stream
+        h = ctypes.c_void_p()
+        st = _lib.art_create(ctypes.byref(h), ctypes.c_void_p(stream.cuda_stream))
+        if st != 0:
+            raise ArtemisError(st, "art_create failed")
+        self._h = h
+        self._keep = []
+        self.C = 0
+        self.views = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.art_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def _check(self, st: int):
+        if st != 0:
+            raise ArtemisError(st, _lib.art_last_error(self._h).decode())
+
+    # ----------------------------------------------------------------- setup
+    def set_config(self, tau: float = 1e-4, instance_cap: int = 0, tile_log2: int = 3, profile: bool = False):
+        c = Config(tau, instance_cap, tile_log2, int(profile))
+        self._check(_lib.art_set_config(self._h, ctypes.byref(c)))
+
+    def load_octree(self, depth: int, origin, extent: float, ijk, joint_idx, weights, features, density,
+                    storage: str = "f32"):
+        ijk, jidx = _np(ijk, np.uint16), _np(joint_idx, np.uint8)
+        w, f, d = _np(weights, np.float32), _np(features, np.float32), _np(density, np.float32)
+        o = _np(origin, np.float32)
+        n, C = f.shape
+        self._check(_lib.art_load_octree(self._h, n, depth, _ptr(o), float(extent), _ptr(ijk), _ptr(jidx), _ptr(w),
+                                         _ptr(f), C, DTYPES[storage], _ptr(d)))
+        self.C = C
+        self.n = n
+
+    def load_skeleton(self, parent, rest):
+        p, r = _np(parent, np.int32), _np(rest, np.float32)
+        self._check(_lib.art_load_skeleton(self._h, p.shape[0], _ptr(p), _ptr(r)))
+
+    def set_pose(self, axis_angle, R, T):
+        aa = axis_angle if hasattr(axis_angle, "data_ptr") else _np(axis_angle, np.float32)
+        R = R if hasattr(R, "data_ptr") else _np(R, np.float32)
+        T = T if hasattr(T, "data_ptr") else _np(T, np.float32)
+        self._check(_lib.art_set_pose(self._h, _ptr(aa), _ptr(R), _ptr(T)))
+
+    def set_camera(self, view: int, W: int, H: int, fx: float, fy: float, cx: float, cy: float, world_to_cam,
+                   near: float, far: float):
+        M = _np(world_to_cam, np.float32).reshape(12)
+        self._check(_lib.art_set_camera(self._h, view, W, H, fx, fy, cx, cy, _ptr(M), near, far))
+        self.views[view] = (W, H)
+
+    def load_shader(self, arch: int, cin: int, ch: Sequence[int], cout: int, params, dtype: str = "f32"):
+        d = NetDesc(arch, cin, (ctypes.c_int * 4)(*(list(ch) + [0] * (4 - len(ch)))), cout)
+        p = _np(params, np.float32).reshape(-1)
+        self._check(_lib.art_load_shader(self._h, ctypes.byref(d), _ptr(p), p.size, DTYPES[dtype]))
+
+    # ------------------------------------------------------------- rendering
+    def render_feature_maps(self, view: int, F_out, A_out=None, F_dtype: str = "f32"):
+        self._check(_lib.art_render_feature_maps(self._h, view, _ptr(F_out), DTYPES[F_dtype], _ptr(A_out)))
+
+    def shade(self, view: int, F, rgba_out, F_dtype: str = "f32"):
+        self._check(_lib.art_shade(self._h, view, _ptr(F), DTYPES[F_dtype], _ptr(rgba_out)))
+
+    def render_frame(self, view: int, axis_angle, R, T, rgba_out):
+        aa = axis_angle if hasattr(axis_angle, "data_ptr") else _np(axis_angle, np.float32)
+        R = R if hasattr(R, "data_ptr") else _np(R, np.float32)
+        T = T if hasattr(T, "data_ptr") else _np(T, np.float32)
+        self._check(_lib.art_render_frame(self._h, view, _ptr(aa), _ptr(R), _ptr(T), _ptr(rgba_out)))
+
+    def sort_pairs(self, keys, vals, key_bits: int = 32):
+        self._check(_lib.art_sort_pairs(self._h, _ptr(keys), _ptr(vals), int(keys.numel()), key_bits))
+
+    # ------------------------------------------------------------ inspection
+    def sync_status(self, raise_on_overflow: bool = True) -> dict:
+        s = Stats()
+        st = _lib.art_sync_status(self._h, ctypes.byref(s))
+        if st != 0 and (raise_on_overflow or st != 4):
+            self._check(st)
+        return dict(instances=s.instances, degenerate=s.degenerate, overflow_inst=s.overflow_inst,
+                    overflow_order=s.overflow_order, kernel_launches=s.kernel_launches, status=st)
+
+    def kernel_times(self, reset: bool = False) -> dict:
+        cap = 64
+        names = (ctypes.c_char_p * cap)()
+        launches = np.zeros(cap, np.int64)
+        ms = np.zeros(cap, np.float64)
+        count = ctypes.c_int(0)
+        self._check(_lib.art_get_kernel_times(self._h, cap, ctypes.cast(names, ctypes.c_void_p), _ptr(launches),
+                                              _ptr(ms), ctypes.byref(count), int(reset)))
+        return {names[i].decode(): (int(launches[i]), float(ms[i])) for i in range(min(count.value, cap))}
+
+    def debug_buffer(self, which: int, dtype) -> np.ndarray:
+        need = ctypes.c_int64(0)
+        self._check(_lib.art_debug_buffer(self._h, which, None, 0, ctypes.byref(need)))
+        out = np.zeros(max(need.value, 1) // np.dtype(dtype).itemsize, dtype)
+        self._check(_lib.art_debug_buffer(self._h, which, _ptr(out), out.nbytes, ctypes.byref(need)))
+        return out
+
+    def debug_hits(self, view: int, cap: int = 64):
+        W, H = self.views[view]
+        count = np.zeros((H, W), np.int32)
+        ids = np.zeros((H, W, cap), np.uint32)
+        t0 = np.zeros((H, W, cap), np.float32)
+        t1 = np.zeros((H, W, cap), np.float32)
+        F = np.zeros((H, W, self.C), np.float32)
+        A = np.zeros((H, W), np.float32)
+        self._check(_lib.art_debug_hits(self._h, view, cap, _ptr(count), _ptr(ids), _ptr(t0), _ptr(t1), _ptr(F),
+                                        _ptr(A)))
+        return dict(count=count, ids=ids, t0=t0, t1=t1, F=F, A=A)
+
+
+def flat_params(layers) -> np.ndarray:
+    """Concatenate [(w [Cout,k,k,Cin], b [Cout]), ...] into the art_load_shader layout."""
+    return np.concatenate([np.concatenate([np.asarray(w, np.float32).ravel(), np.asarray(b, np.float32).ravel()])
+                           for w, b in layers])

@@ -1,0 +1,198 @@
+// Internal declarations of the GB300 ARTEMIS rendering library.
+// Not part of the public ABI (include/artemis.h).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/artemis.h"
+
+namespace art {
+
+constexpr int kMaxJoints = 64;
+constexpr int kMaxViews = 8;
+constexpr float kDetMin = 1e-3f;   // blended transforms below this are dropped
+constexpr float kZMin = 1e-6f;     // corners must lie in front of the camera
+constexpr float kBboxPad = 2e-3f;  // conservative pixel-bbox growth (pixels)
+
+// Device status words (uint64 counters).
+enum StatusWord {
+  kStInstances = 0,     // instances emitted by the last binning
+  kStDegenerate = 1,    // voxels dropped at the last pose
+  kStOverflowInst = 2,  // instances beyond capacity (cumulative until cleared)
+  kStOverflowOrder = 3, // reorder-buffer overflows (cumulative until cleared)
+  kStWords = 8
+};
+
+// Per-view camera, with host-precomputed ray frame.
+struct ViewParams {
+  int W, H;
+  float fx, fy, cx, cy;
+  float R[9];      // world_to_cam rotation (row-major)
+  float t[3];
+  float o[3];      // camera centre -R^T t
+  float znear, zfar;
+  int tiles_x, tiles_y;
+  int tile_w, tile_h;  // screen tile size in pixels (powers of two)
+  int tile_wl, tile_hl;  // their log2
+  int depth_bits;  // key = tile << depth_bits | depth quantum
+  float dscale;    // depth quanta per metre
+};
+
+// Layer of a convolutional network (device pointers owned by the context).
+struct ConvLayer {
+  int cout, cin, k;
+  float* w32 = nullptr;        // [cout][k][k][cin] FP32
+  float* b32 = nullptr;        // [cout]
+  __nv_bfloat16* wbf = nullptr;  // [cout][k*k*cin] BF16 (K-major)
+  uint8_t* w8 = nullptr;       // [cout][k*k*cin] E4M3
+  float* wscale = nullptr;     // [cout] FP8 per-output-channel scale
+};
+
+struct Timer {
+  const char* name;
+  cudaEvent_t e0, e1;
+};
+
+struct KernelStat {
+  const char* name;
+  int64_t launches;
+  double ms;
+};
+
+}  // namespace art
+
+struct art_ctx {
+  cudaStream_t stream = nullptr;
+  std::string err;
+  art_config cfg{};
+  int device = 0;
+  int num_sms = 0;
+
+  // ---- octree (static)
+  int64_t n = 0;
+  int depth = 0;
+  float origin[3] = {0, 0, 0};
+  float extent = 0, h = 0;
+  int C = 0;
+  int feat_dtype = ART_F32;
+  uint2* d_ijk = nullptr;       // packed (i | j << 16, k)
+  uint32_t* d_jidx = nullptr;   // 4 x uint8
+  float4* d_w = nullptr;
+  void* d_feat = nullptr;       // [n][C] in feat_dtype
+  float* d_sigma = nullptr;
+
+  // ---- skeleton
+  int J = 0;
+  int32_t parent[art::kMaxJoints];
+  float rest[art::kMaxJoints * 3];
+  float* d_skel = nullptr;      // parent (as float bits) + rest, uploaded once
+  float* d_pose = nullptr;      // J*3 + 6
+  float* d_G = nullptr;         // [J][12]
+
+  // ---- per pose
+  float4* d_rec = nullptr;      // [n][4] : Binv rows (3) + (sigma, valid, 0, 0)
+  float4* d_geo = nullptr;      // [n][4] : (cw, r), (ax, _), (ay, _), (az, _)
+  bool posed = false;
+  bool jidx_ok = false;         // joint indices validated against J
+
+  // ---- per view / binning
+  art::ViewParams views[art::kMaxViews];
+  bool view_set[art::kMaxViews] = {};
+  int64_t n_cap = 0;            // voxel capacity of per-voxel buffers
+  int64_t inst_cap = 0;
+  short4* d_rect = nullptr;     // [n] pixel rect (x0, y0, x1, y1), empty if x0 > x1
+  uint32_t* d_q = nullptr;      // [n] depth quantum
+  uint32_t* d_cnt = nullptr;    // [n] tile count
+  uint32_t* d_off = nullptr;    // [n] exclusive offsets
+  uint32_t* d_bsum = nullptr;   // block sums for scans
+  uint32_t* d_keys[2] = {nullptr, nullptr};
+  uint32_t* d_vals[2] = {nullptr, nullptr};
+  uint32_t* d_hist = nullptr;   // radix histograms
+  uint2* d_ranges = nullptr;    // per tile [start, end)
+  int64_t ranges_cap = 0;
+  unsigned long long* d_status = nullptr;
+  unsigned long long* h_status = nullptr;  // pinned
+
+  // ---- frame buffers (art_render_frame)
+  void* d_F = nullptr;
+  size_t d_F_bytes = 0;
+  float* d_A = nullptr;
+  size_t d_A_bytes = 0;
+  float* d_rgba = nullptr;
+  size_t d_rgba_bytes = 0;
+
+  // ---- shading network
+  art_net_desc net{};
+  int net_dtype = -1;
+  std::vector<art::ConvLayer> layers;
+  void* d_act = nullptr;        // activation arena
+  size_t d_act_bytes = 0;
+
+  // ---- art_sort_pairs scratch
+  uint32_t* d_sk = nullptr;
+  uint32_t* d_sv = nullptr;
+  uint32_t* d_shist = nullptr;
+  uint32_t* d_sbsum = nullptr;
+  int64_t sort_cap = 0;
+
+  // ---- profiling
+  std::vector<art::Timer> pending;
+  std::vector<cudaEvent_t> free_events;
+  std::vector<art::KernelStat> stats;
+  int64_t launches = 0;
+};
+
+namespace art {
+
+// ---- error helpers (api.cu)
+art_status fail(art_ctx* ctx, art_status st, const char* fmt, ...);
+art_status cuda_fail(art_ctx* ctx, cudaError_t e, const char* what);
+bool is_device_ptr(const void* p);
+art_status ensure(art_ctx* ctx, void** p, size_t* have, size_t need, const char* what);
+
+// Profiling wrappers (api.cu): bracket a launch with events when enabled.
+void prof_begin(art_ctx* ctx, const char* name);
+void prof_end(art_ctx* ctx);
+
+// ---- kernels: LBS (lbs.cu)
+void launch_fk(art_ctx* ctx);
+void launch_lbs(art_ctx* ctx);
+void launch_project(art_ctx* ctx, const ViewParams& v);
+
+// ---- binning and sorting (binsort.cu)
+void launch_scan_emit(art_ctx* ctx, const ViewParams& v);
+void launch_sort(art_ctx* ctx, int key_bits);
+// Radix sort of count (device word) pairs ping-ponging between (k0, v0) and
+// (k1, v1); returns the index (0 or 1) of the buffer holding the result.
+int launch_sort_bufs(art_ctx* ctx, uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, int64_t cap,
+                     const unsigned long long* count, int key_bits, uint32_t* hist, uint32_t* bsum);
+void launch_set_word(art_ctx* ctx, unsigned long long* p, unsigned long long value);
+void launch_ranges(art_ctx* ctx, const ViewParams& v);
+size_t sort_hist_words(int64_t inst_cap);
+size_t scan_block_words(int64_t n);
+
+// ---- composite (composite.cu)
+art_status launch_composite(art_ctx* ctx, const ViewParams& v, void* F, int F_dtype, float* A,
+                            const void* hit_log = nullptr);
+void* make_hit_log(int32_t* count, uint32_t* ids, float* t0, float* t1, int cap);
+void free_hit_log(void* p);
+
+// ---- shading (cnn.cu)
+art_status run_shader(art_ctx* ctx, const ViewParams& v, const void* F, int F_dtype, float* rgba);
+
+}  // namespace art
+
+// Launch helper: counts and (optionally) times every kernel launch.
+#define ART_LAUNCH(ctx, name, kernel, grid, block, smem, ...)                  \
+  do {                                                                         \
+    art::prof_begin((ctx), (name));                                            \
+    kernel<<<(grid), (block), (smem), (ctx)->stream>>>(__VA_ARGS__);           \
+    art::prof_end((ctx));                                                      \
+    (ctx)->launches++;                                                         \
+  } while (0)

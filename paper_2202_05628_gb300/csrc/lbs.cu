@@ -1,0 +1,240 @@
+// Forward kinematics, linear blend skinning and per-view projection of the
+// warped voxels (arXiv 2202.05628, Sec. 3.1 "Rigging and Deformation", Eq. 4).
+#include "internal.cuh"
+
+namespace art {
+namespace {
+
+// R = I + a K + b K^2 with K = [r]_x, a = sin(th)/th, b = (1 - cos th)/th^2
+// (Rodrigues' formula with an unnormalised axis).
+__device__ void rodrigues(const float* r, float* R) {
+  float th2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+  float th = sqrtf(th2);
+  float a, b;
+  if (th < 1e-6f) {
+    a = 1.0f;
+    b = 0.5f;
+  } else {
+    a = sinf(th) / th;
+    float sh = sinf(0.5f * th) / th;
+    b = 2.0f * sh * sh;
+  }
+  float K[9] = {0.f, -r[2], r[1], r[2], 0.f, -r[0], -r[1], r[0], 0.f};
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      float k2 = K[i * 3 + 0] * K[0 * 3 + j] + K[i * 3 + 1] * K[1 * 3 + j] + K[i * 3 + 2] * K[2 * 3 + j];
+      R[i * 3 + j] = (i == j ? 1.0f : 0.0f) + a * K[i * 3 + j] + b * k2;
+    }
+}
+
+// One thread walks the joint tree (parents precede children).
+// skel: J parent indices stored as floats, then rest[J][3]; pose: r[J][3], R[3], T[3].
+__global__ void fk_kernel(int J, const float* __restrict__ skel, const float* __restrict__ pose,
+                          float* __restrict__ G) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  __shared__ float M[kMaxJoints * 12];
+  const float* rest = skel + J;
+  float Rg[9];
+  rodrigues(pose + 3 * J, Rg);
+  const float* Tg = pose + 3 * J + 3;
+  for (int j = 0; j < J; ++j) {
+    int p = (int)skel[j];
+    float Rl[9];
+    rodrigues(pose + 3 * j, Rl);
+    float tl[3];
+    for (int a = 0; a < 3; ++a) tl[a] = rest[3 * j + a] - (p >= 0 ? rest[3 * p + a] : 0.0f);
+    // parent transform P (3x4)
+    float P[12];
+    if (p >= 0) {
+      for (int m = 0; m < 12; ++m) P[m] = M[12 * p + m];
+    } else {
+      for (int a = 0; a < 3; ++a) {
+        for (int b = 0; b < 3; ++b) P[a * 4 + b] = Rg[a * 3 + b];
+        P[a * 4 + 3] = Tg[a];
+      }
+    }
+    float* Mj = M + 12 * j;
+    for (int a = 0; a < 3; ++a) {
+      for (int b = 0; b < 3; ++b)
+        Mj[a * 4 + b] = P[a * 4 + 0] * Rl[0 * 3 + b] + P[a * 4 + 1] * Rl[1 * 3 + b] + P[a * 4 + 2] * Rl[2 * 3 + b];
+      Mj[a * 4 + 3] = P[a * 4 + 0] * tl[0] + P[a * 4 + 1] * tl[1] + P[a * 4 + 2] * tl[2] + P[a * 4 + 3];
+    }
+    // G_j = M_j [I | -rest_j]
+    for (int a = 0; a < 3; ++a) {
+      for (int b = 0; b < 3; ++b) G[12 * j + a * 4 + b] = Mj[a * 4 + b];
+      G[12 * j + a * 4 + 3] =
+          Mj[a * 4 + 3] - (Mj[a * 4 + 0] * rest[3 * j] + Mj[a * 4 + 1] * rest[3 * j + 1] + Mj[a * 4 + 2] * rest[3 * j + 2]);
+    }
+  }
+}
+
+// Per voxel: A = sum_k w_k G_{j_k}; det check; record the unit-cube map
+// u = Binv (x - cw), Binv = (A_lin)^-1 / h, and the bounding data of the
+// warped parallelepiped (centre cw, half axes, bounding radius r).
+__global__ void __launch_bounds__(256) lbs_kernel(int64_t n, int J, const float* __restrict__ G,
+                                                  const uint2* __restrict__ ijk, const uint32_t* __restrict__ jidx,
+                                                  const float4* __restrict__ wts, const float* __restrict__ sigma,
+                                                  float ox, float oy, float oz, float h, float4* __restrict__ rec,
+                                                  float4* __restrict__ geo, unsigned long long* __restrict__ status) {
+  __shared__ float sG[kMaxJoints * 12];
+  for (int k = threadIdx.x; k < J * 12; k += blockDim.x) sG[k] = G[k];
+  __syncthreads();
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool degenerate = false;
+  if (i < n) {
+    uint2 p = ijk[i];
+    float c[3] = {ox + ((float)(p.x & 0xffffu) + 0.5f) * h, oy + ((float)(p.x >> 16) + 0.5f) * h,
+                  oz + ((float)p.y + 0.5f) * h};
+    uint32_t jj = jidx[i];
+    float4 w = wts[i];
+    float wk[4] = {w.x, w.y, w.z, w.w};
+    float A[12];
+#pragma unroll
+    for (int m = 0; m < 12; ++m) A[m] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      int j = (jj >> (8 * k)) & 0xff;
+      const float* g = sG + 12 * j;
+#pragma unroll
+      for (int m = 0; m < 12; ++m) A[m] = fmaf(wk[k], g[m], A[m]);
+    }
+    float a = A[0], b = A[1], cc = A[2], d = A[4], e = A[5], f = A[6], g = A[8], hh = A[9], k2 = A[10];
+    float c00 = e * k2 - f * hh, c01 = f * g - d * k2, c02 = d * hh - e * g;
+    float det = a * c00 + b * c01 + cc * c02;
+    float cw[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) cw[r] = A[r * 4] * c[0] + A[r * 4 + 1] * c[1] + A[r * 4 + 2] * c[2] + A[r * 4 + 3];
+    float4 out_rec[4];
+    float4 out_geo[4];
+    if (!(det >= kDetMin)) {
+      degenerate = true;
+      out_rec[0] = out_rec[1] = out_rec[2] = make_float4(0.f, 0.f, 0.f, 0.f);
+      out_rec[3] = make_float4(sigma[i], 0.f, 0.f, 0.f);
+      out_geo[0] = make_float4(cw[0], cw[1], cw[2], -1.0f);
+      out_geo[1] = out_geo[2] = out_geo[3] = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+      // inverse of the 3x3 block via its adjugate, scaled by 1/h
+      float s = 1.0f / (det * h);
+      float inv[9] = {c00 * s, (cc * hh - b * k2) * s, (b * f - cc * e) * s,
+                      c01 * s, (a * k2 - cc * g) * s, (cc * d - a * f) * s,
+                      c02 * s, (b * g - a * hh) * s, (a * e - b * d) * s};
+      out_rec[0] = make_float4(inv[0], inv[1], inv[2], cw[0]);
+      out_rec[1] = make_float4(inv[3], inv[4], inv[5], cw[1]);
+      out_rec[2] = make_float4(inv[6], inv[7], inv[8], cw[2]);
+      out_rec[3] = make_float4(sigma[i], 1.0f, 0.f, 0.f);
+      float hh2 = 0.5f * h;
+      float ax[3] = {A[0] * hh2, A[4] * hh2, A[8] * hh2};
+      float ay[3] = {A[1] * hh2, A[5] * hh2, A[9] * hh2};
+      float az[3] = {A[2] * hh2, A[6] * hh2, A[10] * hh2};
+      float r2 = 0.0f;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float sy = (q & 1) ? -1.0f : 1.0f, sz = (q & 2) ? -1.0f : 1.0f;
+        float vx = ax[0] + sy * ay[0] + sz * az[0];
+        float vy = ax[1] + sy * ay[1] + sz * az[1];
+        float vz = ax[2] + sy * ay[2] + sz * az[2];
+        r2 = fmaxf(r2, vx * vx + vy * vy + vz * vz);
+      }
+      // slight growth keeps the radius a bound under FP32 rounding
+      float r = sqrtf(r2) * (1.0f + 1e-6f) + 1e-9f;
+      out_geo[0] = make_float4(cw[0], cw[1], cw[2], r);
+      out_geo[1] = make_float4(ax[0], ax[1], ax[2], 0.f);
+      out_geo[2] = make_float4(ay[0], ay[1], ay[2], 0.f);
+      out_geo[3] = make_float4(az[0], az[1], az[2], 0.f);
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      rec[4 * i + m] = out_rec[m];
+      geo[4 * i + m] = out_geo[m];
+    }
+  }
+  unsigned bal = __ballot_sync(0xffffffffu, degenerate);
+  if ((threadIdx.x & 31) == 0 && bal) atomicAdd(status + kStDegenerate, (unsigned long long)__popc(bal));
+}
+
+// Per voxel and view: projected-corner pixel rectangle (grown by kBboxPad),
+// screen-tile count, and the depth key: a floor-quantised lower bound of the
+// distance from the camera centre to any point of the voxel (|cw - o| - r),
+// which bounds the ray parameter t of any entry point from below.
+__global__ void __launch_bounds__(256) project_kernel(int64_t n, const float4* __restrict__ geo, ViewParams v,
+                                                      short4* __restrict__ rect, uint32_t* __restrict__ q,
+                                                      uint32_t* __restrict__ cnt) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float4 g0 = geo[4 * i], g1 = geo[4 * i + 1], g2 = geo[4 * i + 2], g3 = geo[4 * i + 3];
+  short4 empty = make_short4(1, 1, 0, 0);
+  if (!(g0.w >= 0.0f)) {
+    rect[i] = empty;
+    cnt[i] = 0;
+    q[i] = 0;
+    return;
+  }
+  float dx = g0.x - v.o[0], dy = g0.y - v.o[1], dz = g0.z - v.o[2];
+  float dc = sqrtf(dx * dx + dy * dy + dz * dz);
+  float dmin = dc - g0.w, dmax = dc + g0.w;
+  // camera-frame centre and half axes
+  float cc[3], ca[3], cb[3], cd[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    cc[r] = v.R[r * 3] * g0.x + v.R[r * 3 + 1] * g0.y + v.R[r * 3 + 2] * g0.z + v.t[r];
+    ca[r] = v.R[r * 3] * g1.x + v.R[r * 3 + 1] * g1.y + v.R[r * 3 + 2] * g1.z;
+    cb[r] = v.R[r * 3] * g2.x + v.R[r * 3 + 1] * g2.y + v.R[r * 3 + 2] * g2.z;
+    cd[r] = v.R[r * 3] * g3.x + v.R[r * 3 + 1] * g3.y + v.R[r * 3 + 2] * g3.z;
+  }
+  float umin = 3.4e38f, umax = -3.4e38f, vmin = 3.4e38f, vmax = -3.4e38f;
+  bool front = true;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    float sa = (k & 1) ? 1.0f : -1.0f, sb = (k & 2) ? 1.0f : -1.0f, sd = (k & 4) ? 1.0f : -1.0f;
+    float X = cc[0] + sa * ca[0] + sb * cb[0] + sd * cd[0];
+    float Y = cc[1] + sa * ca[1] + sb * cb[1] + sd * cd[1];
+    float Z = cc[2] + sa * ca[2] + sb * cb[2] + sd * cd[2];
+    front = front && (Z > kZMin);
+    float iz = 1.0f / Z;
+    float u = v.fx * X * iz + v.cx, w = v.fy * Y * iz + v.cy;
+    umin = fminf(umin, u);
+    umax = fmaxf(umax, u);
+    vmin = fminf(vmin, w);
+    vmax = fmaxf(vmax, w);
+  }
+  int x0 = (int)ceilf(umin - 0.5f - kBboxPad), x1 = (int)floorf(umax - 0.5f + kBboxPad);
+  int y0 = (int)ceilf(vmin - 0.5f - kBboxPad), y1 = (int)floorf(vmax - 0.5f + kBboxPad);
+  x0 = max(x0, 0);
+  y0 = max(y0, 0);
+  x1 = min(x1, v.W - 1);
+  y1 = min(y1, v.H - 1);
+  if (!front || dmin > v.zfar || dmax < v.znear || x0 > x1 || y0 > y1) {
+    rect[i] = empty;
+    cnt[i] = 0;
+    q[i] = 0;
+    return;
+  }
+  rect[i] = make_short4((short)x0, (short)y0, (short)x1, (short)y1);
+  cnt[i] = (uint32_t)(((x1 >> v.tile_wl) - (x0 >> v.tile_wl) + 1) * ((y1 >> v.tile_hl) - (y0 >> v.tile_hl) + 1));
+  float rel = (fmaxf(dmin, v.znear) - v.znear) * v.dscale;
+  float qmax = (float)((1u << v.depth_bits) - 1u);
+  float qq = fminf(fmaxf(floorf(rel) - 1.0f, 0.0f), qmax);
+  q[i] = (uint32_t)qq;
+}
+
+}  // namespace
+
+void launch_fk(art_ctx* ctx) { ART_LAUNCH(ctx, "fk", fk_kernel, 1, 32, 0, ctx->J, ctx->d_skel, ctx->d_pose, ctx->d_G); }
+
+void launch_lbs(art_ctx* ctx) {
+  int64_t n = ctx->n;
+  unsigned grid = (unsigned)((n + 255) / 256);
+  ART_LAUNCH(ctx, "lbs", lbs_kernel, grid, 256, 0, n, ctx->J, ctx->d_G, ctx->d_ijk, ctx->d_jidx, ctx->d_w,
+             ctx->d_sigma, ctx->origin[0], ctx->origin[1], ctx->origin[2], ctx->h, ctx->d_rec, ctx->d_geo,
+             ctx->d_status);
+}
+
+void launch_project(art_ctx* ctx, const ViewParams& v) {
+  int64_t n = ctx->n;
+  unsigned grid = (unsigned)((n + 255) / 256);
+  ART_LAUNCH(ctx, "project", project_kernel, grid, 256, 0, n, ctx->d_geo, v, ctx->d_rect, ctx->d_q, ctx->d_cnt);
+}
+
+}  // namespace art

@@ -1,0 +1,90 @@
+"""Shared helpers for the parity tests: drive the library through the C ABI
+and compare with the oracle."""
+import numpy as np
+
+import scenegen as sg
+
+
+def renderer(scene, storage="f32", tau=1e-4, profile=False, instance_cap=0):
+    import paper_2202_05628_gb300 as art
+    r = art.Renderer()
+    oc = scene.octree
+    r.load_octree(oc.depth, oc.origin, oc.extent, oc.ijk, oc.joint_idx, oc.weights, oc.features, oc.density,
+                  storage)
+    r.load_skeleton(scene.skeleton.parent, scene.skeleton.rest)
+    r.set_config(tau=tau, profile=profile, instance_cap=instance_cap)
+    return r
+
+
+def set_cam(r, view, cam):
+    r.set_camera(view, cam.W, cam.H, cam.fx, cam.fy, cam.cx, cam.cy, cam.world_to_cam, cam.near, cam.far)
+
+
+def set_pose(r, pose):
+    r.set_pose(pose.axis_angle, pose.R, pose.T)
+
+
+def render_maps(r, view, cam, C, F_dtype="f32"):
+    import torch
+    dt = torch.float32 if F_dtype == "f32" else torch.bfloat16
+    F = torch.empty((cam.H, cam.W, C), dtype=dt, device="cuda")
+    A = torch.empty((cam.H, cam.W), dtype=torch.float32, device="cuda")
+    r.render_feature_maps(view, F, A, F_dtype)
+    torch.cuda.synchronize()
+    return F.float().cpu().numpy(), A.cpu().numpy()
+
+
+def tie_groups(t0, eps):
+    """Indices grouped into runs whose consecutive t0 differ by < eps."""
+    groups, cur = [], [0] if len(t0) else []
+    for k in range(1, len(t0)):
+        if t0[k] - t0[k - 1] < eps:
+            cur.append(k)
+        else:
+            groups.append(cur)
+            cur = [k]
+    if cur:
+        groups.append(cur)
+    return groups
+
+
+def compare_hit_lists(o_ids, o_t0, o_t1, g_ids, g_t0, g_t1, face_eps=1e-5, tie_eps=1e-6):
+    """Hit lists equal up to hits with chord < face_eps (a ray within face_eps
+    of a box face or edge) and up to order within near-ties of t0.  Returns a
+    message, or None when they agree."""
+    keep_o = (o_t1 - o_t0) >= face_eps
+    keep_g = (g_t1 - g_t0) >= face_eps
+    oi, ot0 = o_ids[keep_o], o_t0[keep_o]
+    gi = g_ids[keep_g]
+    # a grazing hit may exist on one side only: drop ids present on one side
+    # whose chord on that side is below 2 face_eps
+    if len(oi) != len(gi) or not np.array_equal(np.sort(oi), np.sort(gi)):
+        so, sg_ = set(oi.tolist()), set(gi.tolist())
+        od = {int(i): float(b - a) for i, a, b in zip(o_ids, o_t0, o_t1)}
+        gd = {int(i): float(b - a) for i, a, b in zip(g_ids, g_t0, g_t1)}
+        bad = [i for i in so ^ sg_ if max(od.get(i, 0.0), gd.get(i, 0.0)) >= 2 * face_eps]
+        if bad:
+            return f"hit sets differ: only oracle {sorted(so - sg_)[:8]}, only gpu {sorted(sg_ - so)[:8]}"
+        common = so & sg_
+        m_o = np.array([i in common for i in oi.tolist()], bool)
+        m_g = np.array([i in common for i in gi.tolist()], bool)
+        oi, ot0, gi = oi[m_o], ot0[m_o], gi[m_g]
+    pos = 0
+    for grp in tie_groups(ot0, tie_eps):
+        a = oi[grp]
+        b = gi[pos:pos + len(grp)]
+        if not np.array_equal(np.sort(a), np.sort(b)):
+            return f"order differs near t0={ot0[grp[0]]:.7f}: oracle {a.tolist()} gpu {b.tolist()}"
+        pos += len(grp)
+    return None
+
+
+def psnr(a, b):
+    mse = float(np.mean((np.asarray(a, np.float64) - np.asarray(b, np.float64)) ** 2))
+    return float("inf") if mse == 0 else 10 * np.log10(1.0 / mse)
+
+
+def tiny_setup(az=0.0, pose_seed=1, res=128):
+    sc = sg.preset("tiny")
+    cam = sg.orbit_camera(sc.centroid, res, res, az_deg=az)
+    return sc, cam, sg.random_pose(pose_seed)

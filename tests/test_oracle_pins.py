@@ -448,8 +448,8 @@ def test_tile_pairs_match_brute_force_bbox_and_cover_hits():
     oc = sc.octree
     cam = sg.orbit_camera(sc.centroid, 80, 72, az_deg=60)
     _, A, _ = oracle.pose_transforms(sc, sg.random_pose(6))
-    ts = 16
-    tiles, vids = oracle.tile_pairs(oc, A, cam, ts)
+    ts, tsy = 16, 8
+    tiles, vids = oracle.tile_pairs(oc, A, cam, ts, tsy)
     vb = oracle.voxel_bounds(oc, A, cam)
     tw = (cam.W + ts - 1) // ts
     px = np.arange(cam.W) + 0.5
@@ -461,7 +461,7 @@ def test_tile_pairs_match_brute_force_bbox_and_cover_hits():
             continue
         xs = np.nonzero((px >= u0) & (px <= u1))[0]
         ys = np.nonzero((py >= v0) & (py <= v1))[0]
-        for ty in set(ys // ts):
+        for ty in set(ys // tsy):
             for tx in set(xs // ts):
                 want.add((int(ty * tw + tx), i))
     got = set(zip(tiles.tolist(), vids.tolist()))
@@ -469,7 +469,7 @@ def test_tile_pairs_match_brute_force_bbox_and_cover_hits():
     r = oracle.render(oc, A, cam, hits=True)
     for p in range(cam.W * cam.H):
         y, x = divmod(p, cam.W)
-        t = (y // ts) * tw + x // ts
+        t = (y // tsy) * tw + x // ts
         for i in r["hit_id"][r["hit_off"][p]:r["hit_off"][p + 1]]:
             assert (t, int(i)) in got
 
