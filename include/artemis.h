@@ -226,6 +226,34 @@ art_status art_get_kernel_times(art_ctx* ctx, int cap, const char** names, int64
  */
 art_status art_sort_pairs(art_ctx* ctx, uint32_t* keys, uint32_t* vals, int64_t n, int key_bits);
 
+/*
+ * The same stable radix sort as art_sort_pairs, for callers that must not
+ * allocate device memory while they run: a VR or game-engine frame loop that
+ * cannot afford the device-wide synchronisation and the unbounded latency a
+ * cudaMalloc/cudaFree may incur in the middle of a frame, and hosts whose
+ * device memory is owned by a pool allocator (PyTorch's caching allocator, an
+ * engine's arena) with a fixed budget.  It takes no context and allocates
+ * nothing: no cudaMalloc, cudaFree or allocating library routine.  (The
+ * paper has no counterpart; this is an interface choice of the library.)
+ *   keys, vals   DEVICE arrays of n uint32 each, sorted in place by the low
+ *                key_bits bits of the keys (key_bits in {8, 16, 24, 32})
+ *   n            0 .. ART_SORT_STATIC_MAX_PAIRS; larger n returns
+ *                ART_ERR_INVALID_ARG without launching anything
+ *   cuda_stream  cudaStream_t the work is enqueued on (asynchronous)
+ * Scratch: a fixed device array of about 8.6 MB inside the library (room for
+ * ART_SORT_STATIC_MAX_PAIRS pairs plus histograms), held by every GPU that
+ * loads the library until the process exits.  Every call rewrites the parts
+ * of it that it reads, so no state carries over between calls; but all calls
+ * share it, so calls that overlap on the GPU (other streams, other host
+ * threads) race: order them on one stream or with events.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Returns ART_ERR_CUDA if that lookup or a launch
+ * fails.
+ */
+#define ART_SORT_STATIC_MAX_PAIRS (1 << 20)
+art_status art_sort_pairs_static(uint32_t* keys, uint32_t* vals, int64_t n, int key_bits, void* cuda_stream);
+
 /* ------------------------------------------------------------ inspection */
 
 /* internal buffers readable with art_debug_buffer (layouts as stated) */

@@ -66,6 +66,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "art_sync_status": [vp, ctypes.POINTER(Stats)],
         "art_get_kernel_times": [vp, i32, vp, vp, vp, ctypes.POINTER(i32), i32],
         "art_sort_pairs": [vp, vp, vp, i64, i32],
+        "art_sort_pairs_static": [vp, vp, i64, i32, vp],
         "art_debug_buffer": [vp, i32, vp, i64, ctypes.POINTER(i64)],
         "art_debug_hits": [vp, i32, i32, vp, vp, vp, vp, vp, vp],
     }
@@ -222,6 +223,19 @@ class Renderer:
         self._check(_lib.art_debug_hits(self._h, view, cap, _ptr(count), _ptr(ids), _ptr(t0), _ptr(t1), _ptr(F),
                                         _ptr(A)))
         return dict(count=count, ids=ids, t0=t0, t1=t1, F=F, A=A)
+
+
+SORT_STATIC_MAX_PAIRS = 1 << 20
+
+
+def sort_pairs_static(keys, vals, key_bits: int = 32, stream=None) -> int:
+    """art_sort_pairs_static: the radix sort without any device allocation
+    (scratch in a fixed array inside the library; see include/artemis.h).
+    Returns the library status (0 = ART_OK)."""
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return int(_lib.art_sort_pairs_static(_ptr(keys), _ptr(vals), int(keys.numel()), key_bits,
+                                          ctypes.c_void_p(s.cuda_stream)))
 
 
 def flat_params(layers) -> np.ndarray:

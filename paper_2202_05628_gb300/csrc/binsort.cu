@@ -2,6 +2,8 @@
 // (tile, depth) keys.  This per-frame indexing step plays the role of the
 // paper's per-frame octree rebuild before the ray-voxel test (arXiv
 // 2202.05628, Sec. 3.1 "Dynamic Volume Rendering").
+#include <mutex>
+
 #include "internal.cuh"
 
 namespace art {
@@ -321,4 +323,100 @@ void launch_ranges(art_ctx* ctx, const ViewParams& v) {
              ctx->d_status + kStInstances, v.depth_bits, ctx->d_ranges);
 }
 
+// ------------------------------------------------ sort without allocation
+//
+// art_sort_pairs_static keeps all of its scratch in the fixed device array
+// below instead of memory it allocates: the ping-pong copy of the pairs, the
+// digit histograms, the scan block sums and the key count.  Every kernel of a
+// call rewrites the parts it reads, so nothing carries over from an earlier
+// call and nothing needs clearing.  Calls that overlap on the GPU share the
+// array and race.
+
+namespace {
+
+constexpr int64_t kStaticPairs = ART_SORT_STATIC_MAX_PAIRS;
+constexpr int64_t kStaticBlocks = (kStaticPairs + kSortBlock - 1) / kSortBlock;
+constexpr int64_t kStaticHist = kStaticBlocks * kRadix;
+constexpr int64_t kStaticBsum = (kStaticHist + kScanBlock - 1) / kScanBlock + 1;
+// byte offsets inside the array (each 256-byte aligned)
+constexpr size_t kOffKeys = 0;
+constexpr size_t kOffVals = kOffKeys + 4 * (size_t)kStaticPairs;
+constexpr size_t kOffHist = kOffVals + 4 * (size_t)kStaticPairs;
+constexpr size_t kOffBsum = kOffHist + 4 * (size_t)kStaticHist;
+constexpr size_t kOffCount = (kOffBsum + 4 * (size_t)kStaticBsum + 255) & ~(size_t)255;
+constexpr size_t kStaticBytes = kOffCount + 256;
+constexpr int kMaxDevices = 64;
+
+}  // namespace
+
+// Held by every GPU that loads the library, until the process exits.
+static __device__ __align__(256) unsigned char g_sort_scratch[kStaticBytes];
+
+namespace {
+
+std::mutex g_scratch_mu;
+void* g_scratch_addr[kMaxDevices] = {};
+
+// Device address of g_sort_scratch on the current device (looked up once per
+// device; in host code the symbol itself is only a host-side stand-in).
+cudaError_t static_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_sort_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_addr[dev] = p;
+  }
+  *out = g_scratch_addr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+
 }  // namespace art
+
+extern "C" art_status art_sort_pairs_static(uint32_t* keys, uint32_t* vals, int64_t n, int key_bits,
+                                            void* cuda_stream) {
+  using namespace art;
+  if (n < 0 || n > kStaticPairs) return ART_ERR_INVALID_ARG;
+  if (key_bits != 8 && key_bits != 16 && key_bits != 24 && key_bits != 32) return ART_ERR_INVALID_ARG;
+  if (n == 0) return ART_OK;
+  if (!keys || !vals) return ART_ERR_INVALID_ARG;
+  void* base = nullptr;
+  if (static_scratch(&base) != cudaSuccess) {
+    cudaGetLastError();
+    return ART_ERR_CUDA;
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  unsigned char* b = (unsigned char*)base;
+  uint32_t* sk = (uint32_t*)(b + kOffKeys);
+  uint32_t* sv = (uint32_t*)(b + kOffVals);
+  uint32_t* hist = (uint32_t*)(b + kOffHist);
+  uint32_t* bsum = (uint32_t*)(b + kOffBsum);
+  unsigned long long* count = (unsigned long long*)(b + kOffCount);
+  const int nb = (int)((n + kSortBlock - 1) / kSortBlock);
+  const int64_t hn = (int64_t)nb * kRadix;
+  const int hb = (int)((hn + kScanBlock - 1) / kScanBlock);
+  uint32_t* K[2] = {keys, sk};
+  uint32_t* V[2] = {vals, sv};
+  set_word_kernel<<<1, 1, 0, s>>>(count, (unsigned long long)n);
+  int src = 0;
+  for (int shift = 0; shift < key_bits; shift += kRadixBits) {
+    radix_hist_kernel<<<nb, kSortThreads, 0, s>>>(K[src], n, count, shift, nb, hist);
+    block_sum_kernel<<<hb, kScanThreads, 0, s>>>(hist, hn, nullptr, bsum);
+    scan_bsum_kernel<<<1, 1024, 0, s>>>(bsum, hb, nullptr);
+    scan_apply_kernel<<<hb, kScanThreads, 0, s>>>(hist, hist, hn, bsum);
+    radix_scatter_kernel<<<nb, kSortThreads, 0, s>>>(K[src], V[src], K[src ^ 1], V[src ^ 1], n, count, shift, nb,
+                                                     hist);
+    src ^= 1;
+  }
+  if (src == 1) {
+    cudaMemcpyAsync(keys, sk, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(vals, sv, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s);
+  }
+  return cudaGetLastError() == cudaSuccess ? ART_OK : ART_ERR_CUDA;
+}
