@@ -628,6 +628,13 @@ art_status art_sync_status(art_ctx* ctx, art_stats* out) {
     out->overflow_order = (int64_t)h[kStOverflowOrder];
     out->kernel_launches = ctx->launches;
   }
+  if (h[kStTcError]) {
+    art_status r = fail(ctx, ART_ERR_CUDA, "tensor-core convolution: %llu CTAs timed out waiting on their pipeline",
+                        h[kStTcError]);
+    cudaMemsetAsync(ctx->d_status + kStTcError, 0, sizeof(unsigned long long), ctx->stream);
+    cudaStreamSynchronize(ctx->stream);
+    return r;
+  }
   if (h[kStOverflowInst] || h[kStOverflowOrder]) {
     art_status r = fail(ctx, ART_ERR_OVERFLOW, "overflow: %llu instances beyond capacity %lld, %llu reorder-buffer releases",
                         h[kStOverflowInst], (long long)ctx->inst_cap, h[kStOverflowOrder]);

@@ -22,9 +22,6 @@ struct ConvArgs {
   int out_f32;     // output element type FP32 (else the activation type)
 };
 
-bool tc_conv_supported(const ConvArgs& a);
-void launch_tc_conv(art_ctx* ctx, const ConvArgs& a, const __nv_bfloat16* wbf);
-
 namespace {
 
 __device__ __forceinline__ float ld_act(const float* p) { return __ldg(p); }
@@ -135,12 +132,7 @@ __global__ void maxpool2_kernel(const T* __restrict__ in, T* __restrict__ out, i
 
 template <typename TI>
 void conv(art_ctx* ctx, const ConvArgs& a, const ConvLayer& L) {
-  if constexpr (sizeof(TI) == 2) {
-    if (L.wbf && tc_conv_supported(a)) {
-      launch_tc_conv(ctx, a, L.wbf);
-      return;
-    }
-  }
+  (void)L;
   int tpr = (a.W + 63) / 64;
   dim3 grid(tpr * a.H, (a.cout + 63) / 64);
   auto kfn = conv_simt_kernel<TI>;
@@ -234,6 +226,93 @@ art_status run_typed(art_ctx* ctx, const ViewParams& v, const void* F, float* rg
   return ART_OK;
 }
 
+// BF16 U-Net on the tensor cores.  Skip connections and upsampled decoder
+// inputs are written straight into per-level concatenation buffers
+// cat_l = [up(decoder below) | encoder skip] by the producing convolutions'
+// epilogues, so every decoder convolution reads one dense tensor; the last
+// convolution carries the 1x1 head + sigmoid in its epilogue.
+art_status run_unet_tc(art_ctx* ctx, const ViewParams& v, const __nv_bfloat16* F, float* rgba) {
+  const int H = v.H, W = v.W;
+  const art_net_desc& nd = ctx->net;
+  const int c0 = nd.ch[0], c1 = nd.ch[1], c2 = nd.ch[2], c3 = nd.ch[3];
+  struct Buf {
+    int h, w, c;
+    size_t off;
+  };
+  std::vector<Buf> bufs;
+  size_t total = 0;
+  auto add = [&](int h, int w, int c) {
+    bufs.push_back(Buf{h, w, c, total});
+    total += ((size_t)h * w * c * 2 + 255) & ~(size_t)255;
+    return (int)bufs.size() - 1;
+  };
+  const int e0a = add(H, W, c0), cat0 = add(H, W, c1 + c0), p0 = add(H / 2, W / 2, c0);
+  const int e1a = add(H / 2, W / 2, c1), cat1 = add(H / 2, W / 2, c2 + c1), p1 = add(H / 4, W / 4, c1);
+  const int e2a = add(H / 4, W / 4, c2), cat2 = add(H / 4, W / 4, c3 + c2), p2 = add(H / 8, W / 8, c2);
+  const int e3a = add(H / 8, W / 8, c3);
+  const int d2a = add(H / 4, W / 4, c2), d1a = add(H / 2, W / 2, c1), d0a = add(H, W, c0);
+  if (ensure(ctx, &ctx->d_act, &ctx->d_act_bytes, total, "activations") != ART_OK) return ART_ERR_OOM;
+  auto P = [&](int i) { return (__nv_bfloat16*)((char*)ctx->d_act + bufs[i].off); };
+  const auto& L = ctx->layers;
+  auto conv = [&](const __nv_bfloat16* in, int cin, int h, int w, int li, __nv_bfloat16* out, int ld, int off,
+                  int up2, float* head_out) {
+    TcConv c;
+    c.in = in;
+    c.cin = cin;
+    c.H = h;
+    c.W = w;
+    c.w = L[li].wbf;
+    c.bias = L[li].b32;
+    c.cout = L[li].cout;
+    c.act = 1;
+    c.out = out;
+    c.ld_out = ld;
+    c.ch_off = off;
+    c.up2 = up2;
+    c.rgba = head_out;
+    c.head_w = head_out ? L[14].w32 : nullptr;
+    c.head_b = head_out ? L[14].b32 : nullptr;
+    return launch_tc_conv(ctx, c);
+  };
+  art_status st = ART_OK;
+#define ART_TRY(x)                  \
+  if ((st = (x)) != ART_OK) return st
+  ART_TRY(conv(F, nd.cin, H, W, 0, P(e0a), c0, 0, 0, nullptr));
+  ART_TRY(conv(P(e0a), c0, H, W, 1, P(cat0), c1 + c0, c1, 0, nullptr));
+  launch_pool_bf16(ctx, P(cat0), c1 + c0, c1, P(p0), H, W, c0);
+  ART_TRY(conv(P(p0), c0, H / 2, W / 2, 2, P(e1a), c1, 0, 0, nullptr));
+  ART_TRY(conv(P(e1a), c1, H / 2, W / 2, 3, P(cat1), c2 + c1, c2, 0, nullptr));
+  launch_pool_bf16(ctx, P(cat1), c2 + c1, c2, P(p1), H / 2, W / 2, c1);
+  ART_TRY(conv(P(p1), c1, H / 4, W / 4, 4, P(e2a), c2, 0, 0, nullptr));
+  ART_TRY(conv(P(e2a), c2, H / 4, W / 4, 5, P(cat2), c3 + c2, c3, 0, nullptr));
+  launch_pool_bf16(ctx, P(cat2), c3 + c2, c3, P(p2), H / 4, W / 4, c2);
+  ART_TRY(conv(P(p2), c2, H / 8, W / 8, 6, P(e3a), c3, 0, 0, nullptr));
+  ART_TRY(conv(P(e3a), c3, H / 8, W / 8, 7, P(cat2), c3 + c2, 0, 1, nullptr));  // up x2 into cat2
+  ART_TRY(conv(P(cat2), c3 + c2, H / 4, W / 4, 8, P(d2a), c2, 0, 0, nullptr));
+  ART_TRY(conv(P(d2a), c2, H / 4, W / 4, 9, P(cat1), c2 + c1, 0, 1, nullptr));  // up x2 into cat1
+  ART_TRY(conv(P(cat1), c2 + c1, H / 2, W / 2, 10, P(d1a), c1, 0, 0, nullptr));
+  ART_TRY(conv(P(d1a), c1, H / 2, W / 2, 11, P(cat0), c1 + c0, 0, 1, nullptr));  // up x2 into cat0
+  ART_TRY(conv(P(cat0), c1 + c0, H, W, 12, P(d0a), c0, 0, 0, nullptr));
+  ART_TRY(conv(P(d0a), c0, H, W, 13, nullptr, 0, 0, 0, rgba));  // + fused 1x1 head, sigmoid
+#undef ART_TRY
+  return ART_OK;
+}
+
+// The tensor-core path covers the U-Net when every layer fits its shapes.
+bool unet_tc_ok(art_ctx* ctx, const ViewParams& v) {
+  const art_net_desc& nd = ctx->net;
+  if (nd.arch != ART_NET_UNET || nd.cout != 4 || v.W % 8 || v.H % 8) return false;
+  for (int i = 0; i < 14; ++i) {
+    TcConv c{};
+    c.cin = ctx->layers[i].cin;
+    c.cout = ctx->layers[i].cout;
+    c.ld_out = 8;
+    c.rgba = i == 13 ? (float*)1 : nullptr;
+    if (ctx->layers[i].k != 3 || !ctx->layers[i].wbf || !tc_conv_ok(c)) return false;
+  }
+  return ctx->layers[14].k == 1;
+}
+
 }  // namespace
 
 art_status run_shader(art_ctx* ctx, const ViewParams& v, const void* F, int F_dtype, float* rgba) {
@@ -242,6 +321,7 @@ art_status run_shader(art_ctx* ctx, const ViewParams& v, const void* F, int F_dt
     return run_typed<float>(ctx, v, F, rgba);
   }
   if (F_dtype != ART_BF16) return fail(ctx, ART_ERR_INVALID_ARG, "shade: BF16 network needs a BF16 feature map");
+  if (unet_tc_ok(ctx, v)) return run_unet_tc(ctx, v, (const __nv_bfloat16*)F, rgba);
   return run_typed<__nv_bfloat16>(ctx, v, F, rgba);
 }
 

@@ -1,10 +1,440 @@
-// Tensor-core (tcgen05) implicit-GEMM convolution for the BF16 shading
-// network.  Placeholder until the tcgen05 kernel lands: reports unsupported so
-// that the CUDA-core kernel runs.
+// Tensor-core (tcgen05) implicit-GEMM 3x3 convolution for the BF16 shading
+// network (arXiv 2202.05628, Sec. 3.1 "Neural Shading"; half-precision
+// network of Sec. 6 "Runtime Analysis").
+//
+// GEMM view: M = pixels (tiles of 128 consecutive pixels of one image row),
+// N = output channels (the whole Cout, <= 256), K = 9 taps x Cin.  For each
+// K chunk (one tap, KC channels) a TMA load brings the 128 x KC input box
+// shifted by the tap (rows / columns outside the image arrive as zeros, which
+// is the convolution's zero padding) and the N x KC weight box into shared
+// memory with the swizzle the UMMA descriptors expect.  One thread issues
+// tcgen05.mma (BF16 x BF16 -> FP32 in TMEM); a double-buffered accumulator
+// lets four epilogue warps drain tile t (tcgen05.ld, bias, ReLU, BF16, store,
+// optional x2 nearest upsampling into a concatenation buffer, optional fused
+// 1x1 head + sigmoid) while tile t+1 accumulates.  The CTA is persistent over
+// the tiles.  Every mbarrier wait is bounded; on time-out the CTA raises an
+// error word, stops its loops, frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 #include "internal.cuh"
 
 namespace art {
-struct ConvArgs;
-bool tc_conv_supported(const ConvArgs&) { return false; }
-void launch_tc_conv(art_ctx*, const ConvArgs&, const __nv_bfloat16*) {}
+namespace {
+
+constexpr int kThreads = 192;  // warp 0 TMA, warp 1 MMA + TMEM, warps 2..5 epilogue
+constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: false when another role aborted or the wait timed out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort_flag) return false;
+    if (clock64() - t0 > kWaitCycles) {
+      *abort_flag = 1;
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, uint64_t* bar, int c0, int c1, int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, uint64_t* bar, int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// UMMA shared-memory descriptor of a K-major tile written by TMA with 128-B
+// (KC = 64 bf16 per row) or 64-B (KC = 32) swizzling: start address, leading
+// byte offset (unused for swizzled K-major, 16 B), stride byte offset between
+// 8-row groups (8 rows x row bytes), descriptor version 1, swizzle mode.
+template <int KC>
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
+  constexpr uint64_t kSbo = (uint64_t)(8 * KC * 2) >> 4;
+  constexpr uint64_t kSwz = KC == 64 ? 2ull : 4ull;  // 2: 128-B swizzle, 4: 64-B swizzle
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | (1ull << 16) | (kSbo << 32) | (1ull << 46) | (kSwz << 61);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+struct TcParams {
+  int H, W, cin, cout;
+  int tiles_per_row, n_tiles;
+  int act;
+  const float* bias;
+  __nv_bfloat16* out;
+  int ld_out, ch_off, up2;
+  float* rgba;           // fused 1x1 head (cout -> 4) + sigmoid when non-null
+  const float* head_w;   // [4][cout]
+  const float* head_b;   // [4]
+  unsigned long long* err;
+};
+
+template <int N, int KC>
+struct TcCfg {
+  static constexpr int kA = 128 * KC * 2;
+  static constexpr int kB = N * KC * 2;
+  static constexpr int kStage = kA + kB;
+  static constexpr int kStagesRaw = 196608 / kStage;
+  static constexpr int kStages = kStagesRaw > 8 ? 8 : kStagesRaw;
+  static constexpr int kTmemCols = 2 * N;  // two accumulators; N in {32, 64, 128, 256}
+  static constexpr uint32_t kIdesc = (1u << 4)                       // D: FP32
+                                     | (1u << 7) | (1u << 10)        // A, B: BF16
+                                     | ((uint32_t)(N >> 3) << 17)    // N / 8
+                                     | ((uint32_t)(128 >> 4) << 24);  // M / 16
+  static constexpr int kSmem = kStages * kStage + 1024 + 8 * (2 * kStages + 4) + 16 + 4 * N + 4 * (4 * 32 + 4);
+};
+
+template <int N, int KC>
+__global__ void __launch_bounds__(kThreads, 1)
+    conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcParams p) {
+  using Cfg = TcCfg<N, KC>;
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  uint8_t* sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
+  uint8_t* stages = sm;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + Cfg::kStages * Cfg::kStage);
+  uint64_t* empty = full + Cfg::kStages;
+  uint64_t* accf = empty + Cfg::kStages;
+  uint64_t* acce = accf + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  float* s_bias = reinterpret_cast<float*>(tmem_slot + 4);
+  float* s_head = s_bias + N;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cpt = p.cin / KC;  // K chunks per tap
+  const int n_chunks = 9 * cpt;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < Cfg::kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accf[b], 1);
+      mbar_init(&acce[b], 128);
+    }
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  for (int i = threadIdx.x; i < N; i += kThreads) s_bias[i] = i < p.cout ? p.bias[i] : 0.0f;
+  if (p.rgba)
+    for (int i = threadIdx.x; i < 4 * N + 4; i += kThreads) s_head[i] = i < 4 * N ? p.head_w[i] : p.head_b[i - 4 * N];
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(Cfg::kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    // ---------------------------------------------------------------- TMA
+    if (lane == 0) {
+      int s = 0;
+      uint32_t ph = 0;
+      for (int tile = blockIdx.x; tile < p.n_tiles && !*abort_flag; tile += gridDim.x) {
+        const int y = tile / p.tiles_per_row, x0 = (tile % p.tiles_per_row) * 128;
+        for (int c = 0; c < n_chunks; ++c) {
+          if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) break;
+          const int tap = c / cpt, cc = c - tap * cpt;
+          const int r = tap / 3, q = tap - 3 * (tap / 3);
+          uint8_t* a = stages + s * Cfg::kStage;
+          mbar_expect_tx(&full[s], Cfg::kStage);
+          tma_load_3d(a, &tmA, &full[s], cc * KC, x0 + q - 1, y + r - 1);
+          tma_load_2d(a + Cfg::kA, &tmB, &full[s], tap * p.cin + cc * KC, 0);
+          if (++s == Cfg::kStages) {
+            s = 0;
+            ph ^= 1u;
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------------------------------------------------------- MMA
+    if (lane == 0) {
+      int s = 0, buf = 0;
+      uint32_t ph = 0, aph = 0;
+      for (int tile = blockIdx.x; tile < p.n_tiles && !*abort_flag; tile += gridDim.x) {
+        if (!mbar_wait(&acce[buf], aph ^ 1u, abort_flag)) break;
+        tc_fence_after();
+        const uint32_t d = tmem_base + (uint32_t)(buf * N);
+        bool ok = true;
+        for (int c = 0; c < n_chunks; ++c) {
+          if (!mbar_wait(&full[s], ph, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a = smem_u32(stages + s * Cfg::kStage), b = a + Cfg::kA;
+#pragma unroll
+          for (int kk = 0; kk < KC / 16; ++kk)
+            umma_bf16(d, umma_desc<KC>(a + kk * 32), umma_desc<KC>(b + kk * 32), Cfg::kIdesc, (c | kk) != 0);
+          umma_commit(&empty[s]);
+          if (++s == Cfg::kStages) {
+            s = 0;
+            ph ^= 1u;
+          }
+        }
+        if (!ok) break;
+        umma_commit(&accf[buf]);
+        if (++buf == 2) {
+          buf = 0;
+          aph ^= 1u;
+        }
+      }
+    }
+    __syncwarp();
+  } else {
+    // ---------------------------------------------------------------- epilogue
+    const int qd = warp & 3;           // TMEM lane quarter this warp may access
+    const int m = qd * 32 + lane;      // row of the tile = pixel offset
+    int buf = 0;
+    uint32_t aph = 0;
+    for (int tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x) {
+      if (!mbar_wait(&accf[buf], aph, abort_flag)) break;
+      tc_fence_after();
+      const int y = tile / p.tiles_per_row, x = (tile % p.tiles_per_row) * 128 + m;
+      const bool valid = x < p.W;
+#pragma unroll 1
+      for (int c0 = 0; c0 < N; c0 += 32) {
+        uint32_t r[32];
+        tmem_ld32(tmem_base + ((uint32_t)(qd * 32) << 16) + (uint32_t)(buf * N + c0), r);
+        float v[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          float t = __uint_as_float(r[j]) + s_bias[c0 + j];
+          v[j] = p.act == 1 ? fmaxf(t, 0.0f) : t;
+        }
+        if (!valid) continue;
+        if (p.rgba) {  // fused 1x1 head (N == 32) + sigmoid -> RGBA FP32
+          float o[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            float acc = s_head[4 * N + k];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) acc = fmaf(s_head[k * N + c0 + j], v[j], acc);
+            o[k] = 1.0f / (1.0f + expf(-acc));
+          }
+          reinterpret_cast<float4*>(p.rgba)[(size_t)y * p.W + x] = make_float4(o[0], o[1], o[2], o[3]);
+          continue;
+        }
+        uint4 pk[4];
+        uint32_t* w = reinterpret_cast<uint32_t*>(pk);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          __nv_bfloat162 b2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+          w[j] = *reinterpret_cast<uint32_t*>(&b2);
+        }
+        if (!p.up2) {
+          uint4* dst = reinterpret_cast<uint4*>(p.out + ((size_t)y * p.W + x) * p.ld_out + p.ch_off + c0);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) dst[k] = pk[k];
+        } else {
+#pragma unroll
+          for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+            for (int dx = 0; dx < 2; ++dx) {
+              const size_t pix = (size_t)(2 * y + dy) * (2 * p.W) + (2 * x + dx);
+              uint4* dst = reinterpret_cast<uint4*>(p.out + pix * p.ld_out + p.ch_off + c0);
+#pragma unroll
+              for (int k = 0; k < 4; ++k) dst[k] = pk[k];
+            }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&acce[buf]);
+      if (++buf == 2) {
+        buf = 0;
+        aph ^= 1u;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                              "r"(Cfg::kTmemCols));
+  if (threadIdx.x == 0 && *abort_flag) atomicAdd(p.err, 1ull);
+}
+
+// 2x2 max pooling of a channel slice [ch_off, ch_off + C) of an NHWC tensor
+// with ld channels per pixel, into a dense [H/2][W/2][C] tensor.
+__global__ void maxpool2_bf16_kernel(const __nv_bfloat16* __restrict__ in, int ld, int ch_off,
+                                     __nv_bfloat16* __restrict__ out, int H, int W, int C) {
+  const int C8 = C / 8;
+  const int64_t total = (int64_t)(H / 2) * (W / 2) * C8;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(idx % C8) * 8;
+    const int64_t pp = idx / C8;
+    const int x = (int)(pp % (W / 2)), y = (int)(pp / (W / 2));
+    const __nv_bfloat16* q = in + (((size_t)(2 * y) * W) + 2 * x) * ld + ch_off + c;
+    uint4 a = *reinterpret_cast<const uint4*>(q);
+    uint4 b = *reinterpret_cast<const uint4*>(q + ld);
+    uint4 cc = *reinterpret_cast<const uint4*>(q + (size_t)W * ld);
+    uint4 d = *reinterpret_cast<const uint4*>(q + (size_t)W * ld + ld);
+    const __nv_bfloat162* pa = reinterpret_cast<const __nv_bfloat162*>(&a);
+    const __nv_bfloat162* pb = reinterpret_cast<const __nv_bfloat162*>(&b);
+    const __nv_bfloat162* pc = reinterpret_cast<const __nv_bfloat162*>(&cc);
+    const __nv_bfloat162* pd = reinterpret_cast<const __nv_bfloat162*>(&d);
+    uint4 o;
+    __nv_bfloat162* po = reinterpret_cast<__nv_bfloat162*>(&o);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) po[k] = __hmax2(__hmax2(pa[k], pb[k]), __hmax2(pc[k], pd[k]));
+    *reinterpret_cast<uint4*>(out + (size_t)pp * C + c) = o;
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+
+bool encode_fn() {
+  std::call_once(g_encode_once, [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  });
+  return g_encode != nullptr;
+}
+
+template <int N, int KC>
+art_status launch_typed(art_ctx* ctx, const TcConv& c) {
+  using Cfg = TcCfg<N, KC>;
+  CUtensorMap tmA, tmB;
+  const CUtensorMapSwizzle swz = KC == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+  {
+    cuuint64_t dims[3] = {(cuuint64_t)c.cin, (cuuint64_t)c.W, (cuuint64_t)c.H};
+    cuuint64_t strides[2] = {(cuuint64_t)c.cin * 2, (cuuint64_t)c.W * c.cin * 2};
+    cuuint32_t box[3] = {(cuuint32_t)KC, 128, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = g_encode(&tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)c.in, dims, strides, box, es,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(ctx, ART_ERR_CUDA, "cuTensorMapEncodeTiled (activations) failed: %d", (int)r);
+  }
+  {
+    cuuint64_t dims[2] = {(cuuint64_t)9 * c.cin, (cuuint64_t)c.cout};
+    cuuint64_t strides[1] = {(cuuint64_t)9 * c.cin * 2};
+    cuuint32_t box[2] = {(cuuint32_t)KC, (cuuint32_t)N};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = g_encode(&tmB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)c.w, dims, strides, box, es,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(ctx, ART_ERR_CUDA, "cuTensorMapEncodeTiled (weights) failed: %d", (int)r);
+  }
+  TcParams p;
+  p.H = c.H;
+  p.W = c.W;
+  p.cin = c.cin;
+  p.cout = c.cout;
+  p.tiles_per_row = (c.W + 127) / 128;
+  p.n_tiles = p.tiles_per_row * c.H;
+  p.act = c.act;
+  p.bias = c.bias;
+  p.out = c.out;
+  p.ld_out = c.ld_out;
+  p.ch_off = c.ch_off;
+  p.up2 = c.up2;
+  p.rgba = c.rgba;
+  p.head_w = c.head_w;
+  p.head_b = c.head_b;
+  p.err = ctx->d_status + kStTcError;
+  auto kfn = conv_tc_kernel<N, KC>;
+  cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "conv_tc shared memory attribute");
+  const int grid = std::min(p.n_tiles, ctx->num_sms);
+  ART_LAUNCH(ctx, "conv_tc", kfn, grid, kThreads, Cfg::kSmem, tmA, tmB, p);
+  return ART_OK;
+}
+
+}  // namespace
+
+bool tc_conv_ok(const TcConv& c) {
+  const bool n_ok = c.cout == 32 || c.cout == 64 || c.cout == 128 || c.cout == 256;
+  return n_ok && (c.cin % 32 == 0) && c.cin >= 32 && (c.ld_out % 8 == 0) && (c.ch_off % 8 == 0) &&
+         (!c.rgba || c.cout == 32) && encode_fn();
+}
+
+art_status launch_tc_conv(art_ctx* ctx, const TcConv& c) {
+  if (!tc_conv_ok(c)) return fail(ctx, ART_ERR_UNSUPPORTED, "tensor-core conv: unsupported shape");
+  const bool k64 = c.cin % 64 == 0;
+  switch (c.cout) {
+    case 32: return k64 ? launch_typed<32, 64>(ctx, c) : launch_typed<32, 32>(ctx, c);
+    case 64: return k64 ? launch_typed<64, 64>(ctx, c) : launch_typed<64, 32>(ctx, c);
+    case 128: return k64 ? launch_typed<128, 64>(ctx, c) : launch_typed<128, 32>(ctx, c);
+    default: return k64 ? launch_typed<256, 64>(ctx, c) : launch_typed<256, 32>(ctx, c);
+  }
+}
+
+void launch_pool_bf16(art_ctx* ctx, const __nv_bfloat16* in, int ld, int ch_off, __nv_bfloat16* out, int H, int W,
+                      int C) {
+  const int64_t total = (int64_t)(H / 2) * (W / 2) * (C / 8);
+  const int grid = (int)std::min<int64_t>((total + 255) / 256, (int64_t)ctx->num_sms * 8);
+  ART_LAUNCH(ctx, "maxpool2_bf16", maxpool2_bf16_kernel, grid, 256, 0, in, ld, ch_off, out, H, W, C);
+}
+
 }  // namespace art

@@ -26,6 +26,7 @@ enum StatusWord {
   kStDegenerate = 1,    // voxels dropped at the last pose
   kStOverflowInst = 2,  // instances beyond capacity (cumulative until cleared)
   kStOverflowOrder = 3, // reorder-buffer overflows (cumulative until cleared)
+  kStTcError = 4,       // tensor-core convolution CTAs that timed out waiting
   kStWords = 8
 };
 
@@ -183,8 +184,30 @@ art_status launch_composite(art_ctx* ctx, const ViewParams& v, void* F, int F_dt
 void* make_hit_log(int32_t* count, uint32_t* ids, float* t0, float* t1, int cap);
 void free_hit_log(void* p);
 
-// ---- shading (cnn.cu)
+// ---- shading (cnn.cu, cnn_tc.cu)
 art_status run_shader(art_ctx* ctx, const ViewParams& v, const void* F, int F_dtype, float* rgba);
+
+// One 3x3 convolution on the tensor cores: input [H][W][cin] BF16 (NHWC,
+// dense), weights [cout][3][3][cin] BF16, bias FP32; output BF16 written at
+// channel offset ch_off of a tensor with ld_out channels per pixel, at the
+// same resolution or (up2) replicated 2x2 into a 2H x 2W tensor; or, with
+// rgba set, the fused 1x1 head (cout -> 4) + sigmoid into FP32 RGBA.
+struct TcConv {
+  const __nv_bfloat16* in;
+  int cin, H, W;
+  const __nv_bfloat16* w;
+  const float* bias;
+  int cout, act;
+  __nv_bfloat16* out;
+  int ld_out, ch_off, up2;
+  float* rgba;
+  const float* head_w;
+  const float* head_b;
+};
+bool tc_conv_ok(const TcConv& c);
+art_status launch_tc_conv(art_ctx* ctx, const TcConv& c);
+void launch_pool_bf16(art_ctx* ctx, const __nv_bfloat16* in, int ld, int ch_off, __nv_bfloat16* out, int H, int W,
+                      int C);
 
 }  // namespace art
 
