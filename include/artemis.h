@@ -143,6 +143,37 @@ art_status art_set_camera(art_ctx* ctx, int view, int W, int H, float fx, float 
  */
 art_status art_render_feature_maps(art_ctx* ctx, int view, void* F_out, int F_dtype, float* A_out);
 
+/* ---------------------------------------------------------- differentiation */
+
+/*
+ * Replace, in place, the voxel features ([n][C] FP32, converted to the storage
+ * dtype), densities ([n]) and/or skinning weights ([n][4]) of the loaded
+ * octree; NULL keeps an array.  Host or device pointers.  After new densities
+ * or weights, call art_set_pose again before rendering (the pose's per-voxel
+ * records carry both).
+ */
+art_status art_update_voxels(art_ctx* ctx, const float* features, const float* density, const float* weights);
+
+/*
+ * Gradients of a loss L through art_render_feature_maps of `view` under the
+ * current pose, with respect to the voxel features f, densities sigma and
+ * skinning weights w (Eq. 4-6; the paper optimises the feature table end to
+ * end, Sec. 3.1 "Training").  Each ray is re-traced (per-ray recomputation;
+ * no per-sample state is stored): hits, their order and the early-stop index
+ * are recomputed exactly as in the forward and held fixed.
+ *   F, A        the forward's outputs for this view and pose: F [H][W][C]
+ *               FP32, A [H][W]
+ *   dF, dA      dL/dF [H][W][C] and dL/dA [H][W] (dA may be NULL = 0); pixels
+ *               with zero upstream gradient are skipped
+ *   d_features  [n][C], d_density [n], d_weights [n][4]: FP32 outputs that
+ *               are ACCUMULATED into (zero them first), so that calls for
+ *               several views sum
+ * All arrays are DEVICE memory.  Gradients accumulate with atomics, so their
+ * last bits depend on the order in which rays finish.
+ */
+art_status art_render_backward(art_ctx* ctx, int view, const float* F, const float* A, const float* dF,
+                               const float* dA, float* d_features, float* d_density, float* d_weights);
+
 /* ----------------------------------------------------------------- shading */
 
 typedef struct {

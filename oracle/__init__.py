@@ -127,7 +127,8 @@ def _cam(c) -> _Cam:
 
 def rodrigues(r) -> np.ndarray:
     out = np.zeros(9)
-    _L().orc_rodrigues(_p(_f64(r)), _p(out))
+    r = _f64(r)  # keep the converted array alive across the call
+    _L().orc_rodrigues(_p(r), _p(out))
     return out.reshape(3, 3)
 
 
@@ -282,8 +283,9 @@ def render_backward(octree, A: np.ndarray, cam, gF: np.ndarray, gA: np.ndarray,
     gfeat = np.zeros((n, C))
     gsig = np.zeros(n)
     gAi = np.zeros((n, 12))
+    gF, gA = _f64(gF), _f64(gA)  # keep the converted arrays alive across the call
     rc = _L().orc_render_backward(ctypes.byref(b.s), ctypes.byref(k), ctypes.c_double(tau),
-                                  _p(_f64(gF)), _p(_f64(gA)), _p(gfeat), _p(gsig), _p(gAi))
+                                  _p(gF), _p(gA), _p(gfeat), _p(gsig), _p(gAi))
     if rc != 0:
         raise MemoryError("orc_render_backward failed")
     return gfeat, gsig, gAi.reshape(n, 3, 4)
@@ -296,8 +298,10 @@ def lbs_backward(octree, G: np.ndarray, A: np.ndarray, gAinv: np.ndarray):
     jidx = np.ascontiguousarray(octree.joint_idx, dtype=np.uint8)
     gA = np.zeros((n, 12))
     gw = np.zeros((n, 4))
-    _L().orc_lbs_backward(ctypes.c_int64(n), ctypes.c_int(G.shape[0]), _p(G), _p(jidx),
-                          _p(_f64(A).reshape(-1, 12)), _p(_f64(gAinv).reshape(-1, 12)), _p(gA), _p(gw))
+    A64 = _f64(A).reshape(-1, 12)
+    gAi64 = _f64(gAinv).reshape(-1, 12)
+    _L().orc_lbs_backward(ctypes.c_int64(n), ctypes.c_int(G.shape[0]), _p(G), _p(jidx), _p(A64), _p(gAi64), _p(gA),
+                          _p(gw))
     return gA.reshape(n, 3, 4), gw
 
 

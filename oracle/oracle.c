@@ -625,6 +625,9 @@ int orc_render_backward(const orc_scene* s, const orc_cam* c, double tau, const 
   double* Fp = (double*)malloc(sizeof(double) * (size_t)C);
   for (int64_t p = 0; p < npx; ++p) {
     int x = (int)(p % c->W), y = (int)(p / c->W);
+    int zero = gA[p] == 0.0;
+    for (int cc = 0; cc < C && zero; ++cc) zero = gF[p * C + cc] == 0.0;
+    if (zero) continue; /* a pixel without upstream gradient contributes nothing */
     int m = pixel_hits(s, c, info, cand.vid + cand.off[p], cand.off[p + 1] - cand.off[p], x, y, &buf, &cap);
     if (m == 0) continue;
     double Ap;

@@ -67,6 +67,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "art_get_kernel_times": [vp, i32, vp, vp, vp, ctypes.POINTER(i32), i32],
         "art_sort_pairs": [vp, vp, vp, i64, i32],
         "art_sort_pairs_static": [vp, vp, i64, i32, vp],
+        "art_update_voxels": [vp, vp, vp, vp],
+        "art_render_backward": [vp, i32, vp, vp, vp, vp, vp, vp, vp],
         "art_debug_buffer": [vp, i32, vp, i64, ctypes.POINTER(i64)],
         "art_debug_hits": [vp, i32, i32, vp, vp, vp, vp, vp, vp],
     }
@@ -183,6 +185,15 @@ class Renderer:
         T = T if hasattr(T, "data_ptr") else _np(T, np.float32)
         self._check(_lib.art_render_frame(self._h, view, _ptr(aa), _ptr(R), _ptr(T), _ptr(rgba_out)))
 
+    def update_voxels(self, features=None, density=None, weights=None):
+        self._check(_lib.art_update_voxels(self._h, _ptr(features), _ptr(density), _ptr(weights)))
+
+    def render_backward(self, view: int, F, A, dF, dA, d_features, d_density, d_weights):
+        """Accumulate dL/df, dL/dsigma, dL/dw (device FP32 tensors) for the
+        current pose and `view`, given the forward's F, A and dL/dF, dL/dA."""
+        self._check(_lib.art_render_backward(self._h, view, _ptr(F), _ptr(A), _ptr(dF), _ptr(dA), _ptr(d_features),
+                                             _ptr(d_density), _ptr(d_weights)))
+
     def sort_pairs(self, keys, vals, key_bits: int = 32):
         self._check(_lib.art_sort_pairs(self._h, _ptr(keys), _ptr(vals), int(keys.numel()), key_bits))
 
@@ -224,6 +235,58 @@ class Renderer:
                                         _ptr(A)))
         return dict(count=count, ids=ids, t0=t0, t1=t1, F=F, A=A)
 
+
+def render_features(renderer: "Renderer", view: int, features, density, weights, pose):
+    """Differentiable render of one view: (F [H,W,C], A [H,W]) as functions of
+    the voxel features [n,C], densities [n] and skinning weights [n,4] (FP32
+    CUDA tensors), through art_update_voxels + art_set_pose +
+    art_render_feature_maps; the backward calls art_render_backward.
+    ``pose`` is (axis_angle [J,3], R [3], T [3])."""
+    return _RenderFn.apply(features, density, weights, renderer, view, pose)
+
+
+def _make_render_fn():
+    import torch
+
+    class RenderFn(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, features, density, weights, renderer, view, pose):
+            features, density, weights = features.contiguous(), density.contiguous(), weights.contiguous()
+            renderer.update_voxels(features, density, weights)
+            renderer.set_pose(*pose)
+            W, H = renderer.views[view]
+            F = torch.empty((H, W, features.shape[1]), dtype=torch.float32, device=features.device)
+            A = torch.empty((H, W), dtype=torch.float32, device=features.device)
+            renderer.render_feature_maps(view, F, A, "f32")
+            ctx.save_for_backward(F, A)
+            ctx.renderer, ctx.view, ctx.shapes = renderer, view, (features.shape, density.shape, weights.shape)
+            return F, A
+
+        @staticmethod
+        def backward(ctx, dF, dA):
+            F, A = ctx.saved_tensors
+            sf, sd, sw = ctx.shapes
+            gf = torch.zeros(sf, dtype=torch.float32, device=F.device)
+            gd = torch.zeros(sd, dtype=torch.float32, device=F.device)
+            gw = torch.zeros(sw, dtype=torch.float32, device=F.device)
+            dF = torch.zeros_like(F) if dF is None else dF.contiguous().float()
+            dA = torch.zeros_like(A) if dA is None else dA.contiguous().float()
+            ctx.renderer.render_backward(ctx.view, F, A, dF, dA, gf, gd, gw)
+            return gf, gd, gw, None, None, None
+
+    return RenderFn
+
+
+class _LazyFn:
+    fn = None
+
+    def apply(self, *a):
+        if _LazyFn.fn is None:
+            _LazyFn.fn = _make_render_fn()
+        return _LazyFn.fn.apply(*a)
+
+
+_RenderFn = _LazyFn()
 
 SORT_STATIC_MAX_PAIRS = 1 << 20
 

@@ -171,7 +171,7 @@ void free_all(art_ctx* ctx) {
                   ctx->d_rec, ctx->d_geo, ctx->d_rect, ctx->d_q, ctx->d_cnt, ctx->d_off, ctx->d_bsum,
                   ctx->d_keys[0], ctx->d_keys[1], ctx->d_vals[0], ctx->d_vals[1], ctx->d_hist, ctx->d_ranges,
                   ctx->d_status, ctx->d_F, ctx->d_A, ctx->d_rgba, ctx->d_act, ctx->d_sk, ctx->d_sv,
-                  ctx->d_shist, ctx->d_sbsum};
+                  ctx->d_shist, ctx->d_sbsum, ctx->d_gN};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& L : ctx->layers) {
@@ -687,6 +687,62 @@ art_status art_sort_pairs(art_ctx* ctx, uint32_t* keys, uint32_t* vals, int64_t 
     cudaMemcpyAsync(vals, ctx->d_sv, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToDevice, ctx->stream);
   }
   return launch_check(ctx, "sort_pairs");
+}
+
+art_status art_update_voxels(art_ctx* ctx, const float* features, const float* density, const float* weights) {
+  if (!ctx) return ART_ERR_INVALID_ARG;
+  if (ctx->n == 0) return fail(ctx, ART_ERR_STATE, "update_voxels before load_octree");
+  const size_t n = (size_t)ctx->n;
+  art_status st;
+  if (density && (st = copy_in(ctx, ctx->d_sigma, density, n * 4, "copy density")) != ART_OK) return st;
+  if (weights && (st = copy_in(ctx, ctx->d_w, weights, n * 16, "copy weights")) != ART_OK) return st;
+  if (features) {
+    if (ctx->feat_dtype == ART_F32) {
+      if ((st = copy_in(ctx, ctx->d_feat, features, n * ctx->C * 4, "copy features")) != ART_OK) return st;
+    } else {
+      float* t = nullptr;
+      if ((st = alloc(ctx, &t, n * ctx->C, "feature staging")) != ART_OK) return st;
+      if ((st = copy_in(ctx, t, features, n * ctx->C * 4, "copy features")) != ART_OK) return st;
+      const int64_t m = (int64_t)n * ctx->C;
+      const unsigned g = (unsigned)((m + 255) / 256);
+      if (ctx->feat_dtype == ART_BF16)
+        convert_kernel<__nv_bfloat16><<<g, 256, 0, ctx->stream>>>(m, t, (__nv_bfloat16*)ctx->d_feat);
+      else
+        convert_kernel<__half><<<g, 256, 0, ctx->stream>>>(m, t, (__half*)ctx->d_feat);
+      st = sync_check(ctx, "update_voxels");
+      cudaFree(t);
+      if (st != ART_OK) return st;
+    }
+  }
+  ctx->posed = ctx->posed && !weights && !density;  // the pose records hold sigma and the blend
+  return launch_check(ctx, "update_voxels");
+}
+
+art_status art_render_backward(art_ctx* ctx, int view, const float* F, const float* A, const float* dF,
+                               const float* dA, float* d_features, float* d_density, float* d_weights) {
+  if (!ctx) return ART_ERR_INVALID_ARG;
+  if (view < 0 || view >= kMaxViews || !ctx->view_set[view]) return fail(ctx, ART_ERR_STATE, "view %d not set", view);
+  if (!ctx->posed) return fail(ctx, ART_ERR_STATE, "render_backward before set_pose");
+  if (!F || !A || !dF || !d_features || !d_density || !d_weights)
+    return fail(ctx, ART_ERR_INVALID_ARG, "null pointer");
+  const void* dev[] = {F, A, dF, d_features, d_density, d_weights};
+  for (const void* p : dev)
+    if (!is_device_ptr(p)) return fail(ctx, ART_ERR_INVALID_ARG, "render_backward takes device arrays");
+  if (dA && !is_device_ptr(dA)) return fail(ctx, ART_ERR_INVALID_ARG, "render_backward takes device arrays");
+  const ViewParams& v = ctx->views[view];
+  art_status st = ensure_bin_buffers(ctx, (int64_t)v.tiles_x * v.tiles_y);
+  if (st != ART_OK) return st;
+  if (ctx->gN_cap < ctx->n) {
+    if ((st = alloc(ctx, &ctx->d_gN, (size_t)ctx->n * 12, "geometry gradient")) != ART_OK) return st;
+    ctx->gN_cap = ctx->n;
+  }
+  cudaMemsetAsync(ctx->d_gN, 0, sizeof(float) * 12 * (size_t)ctx->n, ctx->stream);
+  launch_project(ctx, v);
+  launch_scan_emit(ctx, v);
+  launch_sort(ctx, 32);
+  launch_ranges(ctx, v);
+  if ((st = launch_backward(ctx, v, F, A, dF, dA, d_features, d_density, d_weights)) != ART_OK) return st;
+  return launch_check(ctx, "render_backward");
 }
 
 art_status art_debug_buffer(art_ctx* ctx, int which, void* dst, int64_t bytes, int64_t* needed) {

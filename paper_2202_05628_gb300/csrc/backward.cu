@@ -1,0 +1,324 @@
+// Backward of the dynamic volume rendering (arXiv 2202.05628, Eq. 5-6) and
+// of the LBS warp (Eq. 4) with respect to the voxel features, densities and
+// skinning weights: the gradients the paper's end-to-end optimisation of the
+// feature table needs (Sec. 3.1 "Training").
+//
+// Per-ray recomputation instead of stored sample lists: the backward walks
+// each tile's instance list with exactly the forward's code (staging, masks,
+// slab test, reorder buffer, release rule, early stop), so every pixel
+// revisits the same hits in the same order.  With w_i = T_i a_i,
+// a_i = 1 - exp(-sigma_i delta_i), T_{i+1} = T_i (1 - a_i), g = dL/dF and
+// g_A = dL/dA at the pixel:
+//   dL/df_i      += w_i g
+//   dL/d(s_i)     = T_{i+1} <f_i, g> - <F - P_i, g> + T_final g_A,
+//                   s_i = sigma_i delta_i, P_i = sum_{k<=i} w_k f_k
+//   dL/dsigma_i  += delta_i dL/d(s_i);  dL/ddelta_i = sigma_i dL/d(s_i)
+// and delta_i = t1 - t0 where each clipped-by-a-face end t of the chord
+// solves row_a(N) [o + t d; 1] = const for N = A_i^-1, so
+//   dt/dN[a][0..2] = -(o + t d) / d'_a,  dt/dN[a][3] = -1 / d'_a,
+// d'_a = row_a(N_lin) d.  The per-voxel dL/dN is then mapped to dL/dA by
+// dA = -N^T dN N^T (4x4 affine forms) and to dL/dw_k = <dL/dA, G_{j_k}>.
+// The hit set, the order and the stop index are held fixed (piecewise
+// differentiation, as for any ray-marched renderer).
+#include "raster.cuh"
+
+namespace art {
+namespace {
+
+// Pending hit of the backward: the forward's fields plus what the geometric
+// gradient needs (entry / exit axes and the direction component along them).
+struct PendG {
+  float t0, t1;
+  uint32_t pos;
+  int axes;  // (ax0 + 1) | (ax1 + 1) << 4
+  float e0, e1;
+};
+
+__device__ __forceinline__ bool pless(const PendG& a, const PendG& b) {
+  return a.t0 < b.t0 || (a.t0 == b.t0 && (a.t1 < b.t1 || (a.t1 == b.t1 && a.pos < b.pos)));
+}
+
+__device__ __forceinline__ void atomic_add4(float* p, float a, float b, float c, float d) {
+  atomicAdd(reinterpret_cast<float4*>(p), make_float4(a, b, c, d));
+}
+
+template <int C, typename TF>
+__global__ void __launch_bounds__(32) composite_bwd_kernel(const uint2* __restrict__ ranges,
+                                                           const uint32_t* __restrict__ keys,
+                                                           const uint32_t* __restrict__ vals,
+                                                           const float4* __restrict__ rec,
+                                                           const short4* __restrict__ rect,
+                                                           const TF* __restrict__ feat, ViewParams v, float tau,
+                                                           float h, const float* __restrict__ Ffwd,
+                                                           const float* __restrict__ Afwd,
+                                                           const float* __restrict__ dF, const float* __restrict__ dA,
+                                                           float* __restrict__ gfeat, float* __restrict__ gsig,
+                                                           float* __restrict__ gN,
+                                                           unsigned long long* __restrict__ status) {
+  constexpr int RING = Ring<C, TF>::kChunks;
+  __shared__ float4 s_b0[NT], s_b1[NT], s_b2[NT];
+  __shared__ float s_thr[NT];
+  __shared__ uint32_t s_mask[NT];
+  __shared__ float s_sig[RING][NT];
+  __shared__ uint32_t s_vid[RING][NT];
+  __shared__ __align__(16) TF s_feat[RING][NT][C];
+
+  const int lane = threadIdx.x;
+  const int tile = blockIdx.x;
+  const int tx = tile % v.tiles_x, ty = tile / v.tiles_x;
+  const int sx = tx * TSX, sy = ty * TSY;
+  const int px = sx + (lane & 7), py = sy + (lane >> 3);
+  const bool inside = px < v.W && py < v.H;
+  const size_t pix = inside ? (size_t)py * v.W + px : 0;
+
+  float d0, d1, d2;
+  pixel_dir(v, px, py, d0, d1, d2);
+
+  // upstream gradient of this pixel and the forward's outputs
+  float g[C];
+  float Fg = 0.0f, ga = 0.0f, Tfin = 1.0f;
+  bool any = false;
+#pragma unroll
+  for (int c = 0; c < C; c += 4) {
+    float4 gv = inside ? *reinterpret_cast<const float4*>(dF + pix * C + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 fv = inside ? *reinterpret_cast<const float4*>(Ffwd + pix * C + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+    g[c] = gv.x;
+    g[c + 1] = gv.y;
+    g[c + 2] = gv.z;
+    g[c + 3] = gv.w;
+    Fg += fv.x * gv.x + fv.y * gv.y + fv.z * gv.z + fv.w * gv.w;
+    any = any || gv.x != 0.f || gv.y != 0.f || gv.z != 0.f || gv.w != 0.f;
+  }
+  if (inside) {
+    ga = dA ? dA[pix] : 0.0f;
+    Tfin = 1.0f - Afwd[pix];
+  }
+  any = any || ga != 0.0f;
+
+  float T = 1.0f, pg = 0.0f;  // transmittance before the next hit; <P_i, g>
+  bool done = !(inside && any);
+  PendG buf[kPend];
+#pragma unroll
+  for (int k = 0; k < kPend; ++k) buf[k] = PendG{0.f, 0.f, 0u, 0, 0.f, 0.f};
+  int nb = 0;
+  uint32_t n_over = 0;
+  const uint32_t qmask = (1u << v.depth_bits) - 1u;
+  const float qinv = 1.0f / v.dscale;
+  int cur_chunk = 0;
+  const uint2 rg = ranges[tile];
+
+  auto release_front = [&]() {
+    const PendG hh = buf[0];
+#pragma unroll
+    for (int k = 0; k < kPend - 1; ++k) buf[k] = buf[k + 1];
+    --nb;
+    const int ch = (int)(hh.pos / NT), sl = (int)(hh.pos % NT);
+    float f[C];
+    float sig;
+    uint32_t vid;
+    if (cur_chunk - ch < RING) {
+      sig = s_sig[ch % RING][sl];
+      vid = s_vid[ch % RING][sl];
+      row_to_float<C>(&s_feat[ch % RING][sl][0], f);
+    } else {
+      vid = vals[rg.x + hh.pos];
+      sig = rec[4 * (size_t)vid + 3].x;
+      load_feat<C>(feat + (size_t)vid * C, f);
+    }
+    const float delta = hh.t1 - hh.t0;
+    const float e = expf(-sig * delta);
+    const float w = T * (1.0f - e);
+    float fg = 0.0f;
+#pragma unroll
+    for (int c = 0; c < C; ++c) fg = fmaf(f[c], g[c], fg);
+    pg = fmaf(w, fg, pg);
+    const float core = T * e * fg - (Fg - pg) + Tfin * ga;
+#pragma unroll
+    for (int c = 0; c < C; c += 4)
+      atomic_add4(gfeat + (size_t)vid * C + c, w * g[c], w * g[c + 1], w * g[c + 2], w * g[c + 3]);
+    atomicAdd(gsig + vid, delta * core);
+    const float gdelta = sig * core;
+    const int a0 = (hh.axes & 15) - 1, a1 = (hh.axes >> 4) - 1;
+    if (a0 >= 0) {  // entry end: d(delta)/d(t0) = -1
+      const float gt = -gdelta / (h * hh.e0);
+      atomic_add4(gN + (size_t)vid * 12 + 4 * a0, -gt * (v.o[0] + hh.t0 * d0), -gt * (v.o[1] + hh.t0 * d1),
+                  -gt * (v.o[2] + hh.t0 * d2), -gt);
+    }
+    if (a1 >= 0) {  // exit end: d(delta)/d(t1) = +1
+      const float gt = gdelta / (h * hh.e1);
+      atomic_add4(gN + (size_t)vid * 12 + 4 * a1, -gt * (v.o[0] + hh.t1 * d0), -gt * (v.o[1] + hh.t1 * d1),
+                  -gt * (v.o[2] + hh.t1 * d2), -gt);
+    }
+    T *= e;
+    if (T < tau) done = true;
+  };
+
+  for (uint32_t base = rg.x; base < rg.y; base += NT) {
+    cur_chunk = (int)((base - rg.x) / NT);
+    const int slot = cur_chunk % RING;
+    __syncwarp();
+    {
+      const uint32_t k = base + lane;
+      uint32_t m = 0;
+      float thr = 3.4e38f;
+      if (k < rg.y) {
+        const uint32_t vid = vals[k];
+        const uint32_t key = keys[k];
+        const float4* rp = rec + 4 * (size_t)vid;
+        const float4 r0 = rp[0], r1 = rp[1], r2 = rp[2], r3 = rp[3];
+        const short4 rc = rect[vid];
+        copy_row<C, TF>(feat + (size_t)vid * C, &s_feat[slot][lane][0]);
+        const float ex = v.o[0] - r0.w, ey = v.o[1] - r1.w, ez = v.o[2] - r2.w;
+        s_b0[lane] = make_float4(r0.x, r0.y, r0.z, r0.x * ex + r0.y * ey + r0.z * ez);
+        s_b1[lane] = make_float4(r1.x, r1.y, r1.z, r1.x * ex + r1.y * ey + r1.z * ez);
+        s_b2[lane] = make_float4(r2.x, r2.y, r2.z, r2.x * ex + r2.y * ey + r2.z * ez);
+        s_sig[slot][lane] = r3.x;
+        s_vid[slot][lane] = vid;
+        thr = v.znear + (float)(key & qmask) * qinv;
+        m = rect_mask(rc, sx, sy);
+      }
+      s_mask[lane] = m;
+      s_thr[lane] = thr;
+    }
+    __syncwarp();
+    const float thr0 = s_thr[0];
+    while (!done && nb > 0 && buf[0].t0 < thr0) release_front();
+    uint32_t cand = transpose32(s_mask[lane], lane);
+    if (done) cand = 0;
+    while (cand) {
+      const int idx = __ffs(cand) - 1;
+      cand &= cand - 1;
+      float t0, t1, e[3];
+      int ax0, ax1;
+      if (!slab_hit(s_b0[idx], s_b1[idx], s_b2[idx], d0, d1, d2, v.znear, v.zfar, t0, t1, ax0, ax1, e)) continue;
+      const PendG p{t0, t1, base - rg.x + (uint32_t)idx, (ax0 + 1) | ((ax1 + 1) << 4),
+                    ax0 == 0 ? e[0] : (ax0 == 1 ? e[1] : e[2]), ax1 == 0 ? e[0] : (ax1 == 1 ? e[1] : e[2])};
+      if (nb == kPend) {
+        const float thr = s_thr[idx];
+        while (!done && nb > 0 && buf[0].t0 < thr) release_front();
+        if (!done && nb == kPend) {
+          ++n_over;
+          release_front();
+        }
+        if (done) {
+          cand = 0;
+          break;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < kPend; ++q)
+        if (q == nb) buf[q] = p;
+#pragma unroll
+      for (int q = kPend - 1; q >= 1; --q) {
+        if (q <= nb && pless(buf[q], buf[q - 1])) {
+          const PendG tmp = buf[q];
+          buf[q] = buf[q - 1];
+          buf[q - 1] = tmp;
+        }
+      }
+      ++nb;
+    }
+    if (__all_sync(0xffffffffu, done)) break;
+  }
+  while (nb > 0 && !done) release_front();
+  if (n_over) atomicAdd(status + kStOverflowOrder, (unsigned long long)n_over);
+}
+
+// dL/dA_i = -N^T dL/dN N^T (top 3 rows of the 4x4 affine forms) with
+// N = A_i^-1 = [h Binv | c - h Binv cw]; dL/dw_ik += <dL/dA_i, G_{j_ik}>.
+__global__ void __launch_bounds__(256) lbs_bwd_kernel(int64_t n, const float* __restrict__ G,
+                                                      const uint2* __restrict__ ijk, const uint32_t* __restrict__ jidx,
+                                                      const float4* __restrict__ rec, float ox, float oy, float oz,
+                                                      float h, const float* __restrict__ gN,
+                                                      float* __restrict__ gw) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float4 r3 = rec[4 * i + 3];
+  if (r3.y == 0.0f) return;  // dropped voxel (det < 1e-3): no gradient
+  const uint2 p = ijk[i];
+  const float c[3] = {ox + ((float)(p.x & 0xffffu) + 0.5f) * h, oy + ((float)(p.x >> 16) + 0.5f) * h,
+                      oz + ((float)p.y + 0.5f) * h};
+  float N[3][4], dN[3][4];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const float4 rr = rec[4 * i + r];
+    N[r][0] = h * rr.x;
+    N[r][1] = h * rr.y;
+    N[r][2] = h * rr.z;
+    N[r][3] = 0.0f;  // filled below
+#pragma unroll
+    for (int k = 0; k < 4; ++k) dN[r][k] = gN[12 * i + 4 * r + k];
+  }
+  const float cw[3] = {rec[4 * i].w, rec[4 * i + 1].w, rec[4 * i + 2].w};
+#pragma unroll
+  for (int r = 0; r < 3; ++r) N[r][3] = c[r] - (N[r][0] * cw[0] + N[r][1] * cw[1] + N[r][2] * cw[2]);
+  // T = N^T dN (4x4; dN's and N's bottom rows are 0 and (0,0,0,1))
+  float Tm[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      float s = 0.0f;
+#pragma unroll
+      for (int m = 0; m < 3; ++m) s += N[m][r] * dN[m][k];  // bottom row of dN is zero
+      Tm[r][k] = s;
+    }
+  // dA = -T N^T (rows 0..2): column k < 3 pairs T's row with N's row k (all 4
+  // entries); column 3 meets N's bottom row (0, 0, 0, 1).
+  float dA[3][4];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      dA[r][k] = -(Tm[r][0] * N[k][0] + Tm[r][1] * N[k][1] + Tm[r][2] * N[k][2] + Tm[r][3] * N[k][3]);
+    dA[r][3] = -Tm[r][3];
+  }
+  const uint32_t jj = jidx[i];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int j = (jj >> (8 * q)) & 0xff;
+    const float* Gj = G + 12 * j;
+    float s = 0.0f;
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) s += dA[r][k] * Gj[4 * r + k];
+    gw[4 * i + q] += s;
+  }
+}
+
+template <int C, typename TF>
+void launch_bwd_c(art_ctx* ctx, const ViewParams& v, const float* F, const float* A, const float* dF,
+                  const float* dA, float* gfeat, float* gsig) {
+  auto kfn = composite_bwd_kernel<C, TF>;
+  ART_LAUNCH(ctx, "composite_bwd", kfn, v.tiles_x * v.tiles_y, 32, 0, ctx->d_ranges, ctx->d_keys[0], ctx->d_vals[0],
+             ctx->d_rec, ctx->d_rect, (const TF*)ctx->d_feat, v, ctx->cfg.tau, ctx->h, F, A, dF, dA, gfeat, gsig,
+             ctx->d_gN, ctx->d_status);
+}
+
+template <int C>
+void dispatch_bwd(art_ctx* ctx, const ViewParams& v, const float* F, const float* A, const float* dF, const float* dA,
+                  float* gfeat, float* gsig) {
+  if (ctx->feat_dtype == ART_F32) launch_bwd_c<C, float>(ctx, v, F, A, dF, dA, gfeat, gsig);
+  else if (ctx->feat_dtype == ART_BF16) launch_bwd_c<C, __nv_bfloat16>(ctx, v, F, A, dF, dA, gfeat, gsig);
+  else launch_bwd_c<C, __half>(ctx, v, F, A, dF, dA, gfeat, gsig);
+}
+
+}  // namespace
+
+art_status launch_backward(art_ctx* ctx, const ViewParams& v, const float* F, const float* A, const float* dF,
+                           const float* dA, float* gfeat, float* gsig, float* gw) {
+  switch (ctx->C) {
+    case 4: dispatch_bwd<4>(ctx, v, F, A, dF, dA, gfeat, gsig); break;
+    case 8: dispatch_bwd<8>(ctx, v, F, A, dF, dA, gfeat, gsig); break;
+    case 16: dispatch_bwd<16>(ctx, v, F, A, dF, dA, gfeat, gsig); break;
+    case 32: dispatch_bwd<32>(ctx, v, F, A, dF, dA, gfeat, gsig); break;
+    default: return fail(ctx, ART_ERR_UNSUPPORTED, "backward: C=%d not built", ctx->C);
+  }
+  const int64_t n = ctx->n;
+  ART_LAUNCH(ctx, "lbs_bwd", lbs_bwd_kernel, (unsigned)((n + 255) / 256), 256, 0, n, ctx->d_G, ctx->d_ijk,
+             ctx->d_jidx, ctx->d_rec, ctx->origin[0], ctx->origin[1], ctx->origin[2], ctx->h, ctx->d_gN, gw);
+  return ART_OK;
+}
+
+}  // namespace art

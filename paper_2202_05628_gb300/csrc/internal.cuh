@@ -135,6 +135,10 @@ struct art_ctx {
   void* d_act = nullptr;        // activation arena
   size_t d_act_bytes = 0;
 
+  // ---- backward
+  float* d_gN = nullptr;        // [n][12] dL/d(A_i^-1) accumulator
+  int64_t gN_cap = 0;
+
   // ---- art_sort_pairs scratch
   uint32_t* d_sk = nullptr;
   uint32_t* d_sv = nullptr;
@@ -183,6 +187,10 @@ art_status launch_composite(art_ctx* ctx, const ViewParams& v, void* F, int F_dt
                             const void* hit_log = nullptr);
 void* make_hit_log(int32_t* count, uint32_t* ids, float* t0, float* t1, int cap);
 void free_hit_log(void* p);
+
+// ---- backward (backward.cu)
+art_status launch_backward(art_ctx* ctx, const ViewParams& v, const float* F, const float* A, const float* dF,
+                           const float* dA, float* gfeat, float* gsig, float* gw);
 
 // ---- shading (cnn.cu, cnn_tc.cu)
 art_status run_shader(art_ctx* ctx, const ViewParams& v, const void* F, int F_dtype, float* rgba);

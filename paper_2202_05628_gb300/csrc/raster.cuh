@@ -1,0 +1,248 @@
+// Device helpers shared by the forward composite (composite.cu) and its
+// backward (backward.cu): per-pixel reorder buffer, warp bit-matrix
+// transpose, staged feature ring, vectorised feature loads and the exact
+// ray / warped-voxel slab test.  Both kernels walk a tile's instances with
+// the same code so that they see the same hits in the same order.
+#pragma once
+
+#include "internal.cuh"
+
+namespace art {
+
+constexpr int kPend = 12;  // reorder-buffer depth per pixel
+
+// Optional per-pixel record of the composited hits (inspection only).
+struct HitLog {
+  int32_t* count;
+  uint32_t* ids;
+  float* t0;
+  float* t1;
+  int cap;
+};
+
+// A pending hit: entry and exit ray parameters and its position in the tile's
+// list (which locates the staged density, voxel id and feature row).  Exact
+// (t0, t1) ties, which only coincident voxels produce, fall back to list order.
+struct Pend {
+  float t0, t1;
+  uint32_t pos;
+};
+
+__device__ __forceinline__ bool pless(const Pend& a, const Pend& b) {
+  return a.t0 < b.t0 || (a.t0 == b.t0 && (a.t1 < b.t1 || (a.t1 == b.t1 && a.pos < b.pos)));
+}
+
+// feature row loads (vectorised) --------------------------------------------
+template <int C>
+__device__ __forceinline__ void load_feat(const float* __restrict__ p, float* f) {
+  const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+  for (int k = 0; k < C / 4; ++k) {
+    float4 x = __ldg(q + k);
+    f[4 * k] = x.x;
+    f[4 * k + 1] = x.y;
+    f[4 * k + 2] = x.z;
+    f[4 * k + 3] = x.w;
+  }
+}
+
+__device__ __forceinline__ void unpack2(uint32_t u, float* f, const __nv_bfloat16*) {
+  __nv_bfloat162 b = *reinterpret_cast<__nv_bfloat162*>(&u);
+  float2 x = __bfloat1622float2(b);
+  f[0] = x.x;
+  f[1] = x.y;
+}
+__device__ __forceinline__ void unpack2(uint32_t u, float* f, const __half*) {
+  __half2 b = *reinterpret_cast<__half2*>(&u);
+  float2 x = __half22float2(b);
+  f[0] = x.x;
+  f[1] = x.y;
+}
+
+template <int C, typename T16>
+__device__ __forceinline__ void load_feat16(const T16* __restrict__ p, float* f) {
+  if constexpr (C % 8 == 0) {
+    const uint4* q = reinterpret_cast<const uint4*>(p);
+#pragma unroll
+    for (int k = 0; k < C / 8; ++k) {
+      uint4 x = __ldg(q + k);
+      unpack2(x.x, f + 8 * k, p);
+      unpack2(x.y, f + 8 * k + 2, p);
+      unpack2(x.z, f + 8 * k + 4, p);
+      unpack2(x.w, f + 8 * k + 6, p);
+    }
+  } else {
+    const uint2* q = reinterpret_cast<const uint2*>(p);
+#pragma unroll
+    for (int k = 0; k < C / 4; ++k) {
+      uint2 x = __ldg(q + k);
+      unpack2(x.x, f + 4 * k, p);
+      unpack2(x.y, f + 4 * k + 2, p);
+    }
+  }
+}
+
+template <int C>
+__device__ __forceinline__ void load_feat(const __nv_bfloat16* __restrict__ p, float* f) {
+  load_feat16<C>(p, f);
+}
+template <int C>
+__device__ __forceinline__ void load_feat(const __half* __restrict__ p, float* f) {
+  load_feat16<C>(p, f);
+}
+
+// output row stores ----------------------------------------------------------
+template <int C>
+__device__ __forceinline__ void store_row(float* __restrict__ p, const float* f) {
+  float4* q = reinterpret_cast<float4*>(p);
+#pragma unroll
+  for (int k = 0; k < C / 4; ++k) q[k] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
+}
+
+template <int C>
+__device__ __forceinline__ void store_row(__nv_bfloat16* __restrict__ p, const float* f) {
+  uint32_t u[C / 2];
+#pragma unroll
+  for (int k = 0; k < C / 2; ++k) {
+    __nv_bfloat162 b = __floats2bfloat162_rn(f[2 * k], f[2 * k + 1]);
+    u[k] = *reinterpret_cast<uint32_t*>(&b);
+  }
+  if constexpr (C % 8 == 0) {
+    uint4* q = reinterpret_cast<uint4*>(p);
+#pragma unroll
+    for (int k = 0; k < C / 8; ++k) q[k] = make_uint4(u[4 * k], u[4 * k + 1], u[4 * k + 2], u[4 * k + 3]);
+  } else {
+    uint2* q = reinterpret_cast<uint2*>(p);
+#pragma unroll
+    for (int k = 0; k < C / 4; ++k) q[k] = make_uint2(u[2 * k], u[2 * k + 1]);
+  }
+}
+
+// Transpose of a 32x32 bit matrix held one row per lane: afterwards lane c
+// holds column c (bit r of lane c = bit c of the old row r).
+__device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
+  const uint32_t m[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const int j = 16 >> i;
+    uint32_t y = __shfl_xor_sync(0xffffffffu, x, j);
+    x = (lane & j) ? ((x & ~m[i]) | ((y >> j) & m[i])) : ((x & m[i]) | ((y << j) & ~m[i]));
+  }
+  return x;
+}
+
+constexpr int TSX = 8, TSY = 4;  // tile: 8 x 4 pixels = one warp
+constexpr int NT = 32;           // instances per staged chunk
+
+template <int C, typename TF>
+struct Ring {
+  // chunks of staged feature rows kept in shared memory (<= 32 KB, <= 16)
+  static constexpr int kRaw = 32768 / (NT * C * (int)sizeof(TF));
+  static constexpr int kChunks = kRaw < 16 ? kRaw : 16;
+};
+
+template <int C, typename TF>
+__device__ __forceinline__ void copy_row(const TF* __restrict__ src, TF* dst) {
+  constexpr int kVec = (C * (int)sizeof(TF)) % 16 == 0 ? 16 : 8;
+  constexpr int kN = C * (int)sizeof(TF) / kVec;
+  if constexpr (kVec == 16) {
+    const uint4* s = reinterpret_cast<const uint4*>(src);
+    uint4* d = reinterpret_cast<uint4*>(dst);
+#pragma unroll
+    for (int k = 0; k < kN; ++k) d[k] = __ldg(s + k);
+  } else {
+    const uint2* s = reinterpret_cast<const uint2*>(src);
+    uint2* d = reinterpret_cast<uint2*>(dst);
+#pragma unroll
+    for (int k = 0; k < kN; ++k) d[k] = __ldg(s + k);
+  }
+}
+
+template <int C>
+__device__ __forceinline__ void row_to_float(const float* p, float* f) {
+#pragma unroll
+  for (int c = 0; c < C; c += 4) {
+    float4 x = *reinterpret_cast<const float4*>(p + c);
+    f[c] = x.x;
+    f[c + 1] = x.y;
+    f[c + 2] = x.z;
+    f[c + 3] = x.w;
+  }
+}
+template <int C>
+__device__ __forceinline__ void row_to_float(const __nv_bfloat16* p, float* f) {
+#pragma unroll
+  for (int c = 0; c < C; c += 2) {
+    float2 x = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p + c));
+    f[c] = x.x;
+    f[c + 1] = x.y;
+  }
+}
+template <int C>
+__device__ __forceinline__ void row_to_float(const __half* p, float* f) {
+#pragma unroll
+  for (int c = 0; c < C; c += 2) {
+    float2 x = __half22float2(*reinterpret_cast<const __half2*>(p + c));
+    f[c] = x.x;
+    f[c + 1] = x.y;
+  }
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+
+// Exact hit of the pixel ray (unit direction d) with a staged voxel whose
+// unit-cube map rows are b0, b1, b2 (xyz: rows of A_lin^-1 / h, w: o' = the
+// camera centre in unit-cube coordinates).  t0 / t1 are the entry / exit ray
+// parameters clipped to [near, far]; ax0 / ax1 the axes of the entry / exit
+// planes (-1 when the near / far bound is the active one) and e the ray
+// direction in unit-cube coordinates.  Returns t1 > t0.
+__device__ __forceinline__ bool slab_hit(const float4& b0, const float4& b1, const float4& b2, float d0, float d1,
+                                         float d2, float znear, float zfar, float& t0, float& t1, int& ax0, int& ax1,
+                                         float (&e)[3]) {
+  e[0] = b0.x * d0 + b0.y * d1 + b0.z * d2;
+  e[1] = b1.x * d0 + b1.y * d1 + b1.z * d2;
+  e[2] = b2.x * d0 + b2.y * d1 + b2.z * d2;
+  const float i0 = rcp_approx(e[0]), i1 = rcp_approx(e[1]), i2 = rcp_approx(e[2]);
+  const float a0 = (-0.5f - b0.w) * i0, c0 = (0.5f - b0.w) * i0;
+  const float a1 = (-0.5f - b1.w) * i1, c1 = (0.5f - b1.w) * i1;
+  const float a2 = (-0.5f - b2.w) * i2, c2 = (0.5f - b2.w) * i2;
+  const float l0 = fminf(a0, c0), l1 = fminf(a1, c1), l2 = fminf(a2, c2);
+  const float h0 = fmaxf(a0, c0), h1 = fmaxf(a1, c1), h2 = fmaxf(a2, c2);
+  t0 = fmaxf(fmaxf(znear, l0), fmaxf(l1, l2));
+  t1 = fminf(fminf(zfar, h0), fminf(h1, h2));
+  ax0 = t0 == l0 ? 0 : (t0 == l1 ? 1 : (t0 == l2 ? 2 : -1));
+  ax1 = t1 == h0 ? 0 : (t1 == h1 ? 1 : (t1 == h2 ? 2 : -1));
+  return t1 > t0;
+}
+
+// Pixel-rectangle mask of one instance over a TSX x TSY tile at (sx, sy):
+// bit (y * 8 + x) set when pixel (sx + x, sy + y) lies in the rectangle.
+__device__ __forceinline__ uint32_t rect_mask(short4 rc, int sx, int sy) {
+  const int lx0 = max((int)rc.x - sx, 0), lx1 = min((int)rc.z - sx, TSX - 1);
+  const int ly0 = max((int)rc.y - sy, 0), ly1 = min((int)rc.w - sy, TSY - 1);
+  if (lx0 > lx1 || ly0 > ly1) return 0u;
+  const uint32_t cm = ((2u << lx1) - 1u) & ~((1u << lx0) - 1u);
+  const uint32_t rows = ((2u << ly1) - 1u) & ~((1u << ly0) - 1u);
+  // spread row bits r to byte positions 8r, then replicate the column mask
+  const uint32_t spread = (rows & 1u) | ((rows & 2u) << 7) | ((rows & 4u) << 14) | ((rows & 8u) << 21);
+  return cm * spread;
+}
+
+// Unit-length ray direction through the centre of pixel (px, py).
+__device__ __forceinline__ void pixel_dir(const ViewParams& v, int px, int py, float& d0, float& d1, float& d2) {
+  const float dcx = ((float)px + 0.5f - v.cx) / v.fx, dcy = ((float)py + 0.5f - v.cy) / v.fy;
+  d0 = v.R[0] * dcx + v.R[3] * dcy + v.R[6];
+  d1 = v.R[1] * dcx + v.R[4] * dcy + v.R[7];
+  d2 = v.R[2] * dcx + v.R[5] * dcy + v.R[8];
+  const float inrm = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+  d0 *= inrm;
+  d1 *= inrm;
+  d2 *= inrm;
+}
+
+}  // namespace art

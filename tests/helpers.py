@@ -88,3 +88,4 @@ def tiny_setup(az=0.0, pose_seed=1, res=128):
     sc = sg.preset("tiny")
     cam = sg.orbit_camera(sc.centroid, res, res, az_deg=az)
     return sc, cam, sg.random_pose(pose_seed)
+

@@ -625,3 +625,25 @@ def test_lbs_backward_matrix_inverse_gradient():
             np.testing.assert_allclose(gA[0, r_, c_], fd, rtol=1e-6, atol=1e-9)
     np.testing.assert_allclose(gw[0, 0], np.sum(gA[0] * G[0]), rtol=1e-12)
     np.testing.assert_allclose(gw[0, 1], np.sum(gA[0] * G[1]), rtol=1e-12)
+
+
+def test_wrapper_keeps_converted_inputs_alive():
+    # float32 inputs are converted before the C call; the converted arrays must
+    # stay alive during it (results equal those for the same values in FP64)
+    sc = sg.preset("mini")
+    oc = sc.octree
+    cam = sg.orbit_camera(sc.centroid, 48, 48, az_deg=40.0)
+    G, A, _ = oracle.pose_transforms(sc, sg.random_pose(2))
+    rng = np.random.default_rng(0)
+    g32 = rng.standard_normal((48, 48, oc.C)).astype(np.float32)
+    a32 = rng.standard_normal((48, 48)).astype(np.float32)
+    r1 = oracle.render_backward(oc, A, cam, g32, a32)
+    r2 = oracle.render_backward(oc, A, cam, g32.astype(np.float64), a32.astype(np.float64))
+    for x, y in zip(r1, r2):
+        np.testing.assert_array_equal(x, y)
+    gN = r1[2].astype(np.float32)
+    np.testing.assert_array_equal(oracle.lbs_backward(oc, G, A.astype(np.float32), gN)[1],
+                                  oracle.lbs_backward(oc, G, A.astype(np.float32).astype(np.float64),
+                                                      gN.astype(np.float64))[1])
+    np.testing.assert_array_equal(oracle.rodrigues(np.float32([0.1, 0.2, 0.3])),
+                                  oracle.rodrigues(np.float32([0.1, 0.2, 0.3]).astype(np.float64)))
