@@ -193,8 +193,12 @@ typedef struct {
  * params: float array, for every layer in execution order its weights
  *   [Cout][k][k][Cin] followed by its bias [Cout]; n_params must match.
  * compute_dtype: ART_F32 (CUDA-core FP32), ART_BF16 (tensor cores, BF16
- *   operands, FP32 accumulation) or ART_FP8 (E4M3 operands with per-output-
- *   channel weight scales and per-tensor activation scales).
+ *   operands, FP32 accumulation) or ART_FP8 (U-Net only: E4M3 operands,
+ *   FP32 accumulation, per-output-channel weight scales max|w_co| / 448 and
+ *   per-tensor activation scales; each art_shade quantises with the scales
+ *   measured (max |value| / 448) on the previous call and records its own,
+ *   and the first call after loading runs the network twice to calibrate).
+ *   BF16 and FP8 networks take a BF16 feature map.
  */
 art_status art_load_shader(art_ctx* ctx, const art_net_desc* desc, const float* params, int64_t n_params,
                            int compute_dtype);
@@ -296,7 +300,12 @@ enum {
   ART_BUF_DEPTHKEY = 4,  /* [n] uint32: depth quantum of the last render */
   ART_BUF_KEYS = 5,      /* [instances] uint32 sorted keys (tile << depth_bits | depth) */
   ART_BUF_VALS = 6,      /* [instances] uint32 voxel ids in key order */
-  ART_BUF_RANGES = 7     /* [tiles][2] uint32 [start, end) of each tile */
+  ART_BUF_RANGES = 7,    /* [tiles][2] uint32 [start, end) of each tile */
+  ART_BUF_FP8_SCALES = 8, /* [11] float: FP8 network activation scales used by the next call */
+  ART_BUF_ACTIVATIONS = 9 /* bytes of the tensor-core U-Net's activation arena after the last art_shade:
+                             NHWC tensors, each padded to 256 bytes.  FP8: E4M3 codes of input, e0a,
+                             cat0, p0, e1a, cat1, p1, e2a, cat2, p2, e3a, d2a, d1a, d0a; BF16: the same
+                             tensors without the input.  cat = [upsampled decoder | encoder] */
 };
 
 /*

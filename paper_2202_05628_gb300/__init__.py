@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libartemis_gb.so")
 
 ART_F32, ART_BF16, ART_F16, ART_FP8 = 0, 1, 2, 3
 ART_NET_TINY, ART_NET_UNET = 0, 1
-BUF_JOINT_G, BUF_VOXEL_REC, BUF_VOXEL_GEO, BUF_RECT, BUF_DEPTHKEY, BUF_KEYS, BUF_VALS, BUF_RANGES = range(8)
+BUF_JOINT_G, BUF_VOXEL_REC, BUF_VOXEL_GEO, BUF_RECT, BUF_DEPTHKEY, BUF_KEYS, BUF_VALS, BUF_RANGES, BUF_FP8_SCALES, BUF_ACTIVATIONS = range(10)
 _STATUS = {0: "ART_OK", 1: "ART_ERR_INVALID_ARG", 2: "ART_ERR_CUDA", 3: "ART_ERR_OOM", 4: "ART_ERR_OVERFLOW",
            5: "ART_ERR_STATE", 6: "ART_ERR_UNSUPPORTED"}
 DTYPES = {"f32": ART_F32, "bf16": ART_BF16, "f16": ART_F16, "fp8": ART_FP8}

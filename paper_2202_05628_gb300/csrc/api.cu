@@ -171,7 +171,7 @@ void free_all(art_ctx* ctx) {
                   ctx->d_rec, ctx->d_geo, ctx->d_rect, ctx->d_q, ctx->d_cnt, ctx->d_off, ctx->d_bsum,
                   ctx->d_keys[0], ctx->d_keys[1], ctx->d_vals[0], ctx->d_vals[1], ctx->d_hist, ctx->d_ranges,
                   ctx->d_status, ctx->d_F, ctx->d_A, ctx->d_rgba, ctx->d_act, ctx->d_sk, ctx->d_sv,
-                  ctx->d_shist, ctx->d_sbsum, ctx->d_gN};
+                  ctx->d_shist, ctx->d_sbsum, ctx->d_gN, ctx->d_f8_scale, ctx->d_f8_amax};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& L : ctx->layers) {
@@ -506,7 +506,7 @@ art_status art_load_shader(art_ctx* ctx, const art_net_desc* desc, const float* 
                            int compute_dtype) {
   if (!ctx) return ART_ERR_INVALID_ARG;
   if (!desc || !params) return fail(ctx, ART_ERR_INVALID_ARG, "null descriptor or params");
-  if (compute_dtype != ART_F32 && compute_dtype != ART_BF16)
+  if (compute_dtype != ART_F32 && compute_dtype != ART_BF16 && compute_dtype != ART_FP8)
     return fail(ctx, ART_ERR_UNSUPPORTED, "compute dtype %d not available", compute_dtype);
   std::vector<int> shapes;  // cout, cin, k
   const art_net_desc& d = *desc;
@@ -552,15 +552,26 @@ art_status art_load_shader(art_ctx* ctx, const art_net_desc* desc, const float* 
     off += (int64_t)nw;
     if ((st = copy_in(ctx, L.b32, params + off, (size_t)L.cout * 4, "copy bias")) != ART_OK) break;
     off += L.cout;
-    if (compute_dtype == ART_BF16) {
+    if (compute_dtype == ART_BF16 || compute_dtype == ART_FP8) {
       if ((st = alloc(ctx, &L.wbf, nw, "bf16 weights")) != ART_OK) break;
       round_bf16_kernel<<<(unsigned)((nw + 255) / 256), 256, 0, ctx->stream>>>((int64_t)nw, L.w32, L.wbf);
+    }
+    if (compute_dtype == ART_FP8 && L.k == 3) {  // 1x1 head stays FP32 (fused epilogue)
+      if ((st = alloc(ctx, &L.w8, nw, "fp8 weights")) != ART_OK) break;
+      if ((st = alloc(ctx, &L.wscale, (size_t)L.cout, "fp8 weight scales")) != ART_OK) break;
+      launch_quantize_weights(ctx, L.w32, L.cout, L.k * L.k * L.cin, L.w8, L.wscale);
     }
     ctx->layers.push_back(L);
   }
   if (st != ART_OK) return st;
   ctx->net = d;
   ctx->net_dtype = compute_dtype;
+  if (compute_dtype == ART_FP8) {
+    if ((st = alloc(ctx, &ctx->d_f8_scale, (size_t)kF8Tensors, "fp8 scales")) != ART_OK) return st;
+    if ((st = alloc(ctx, &ctx->d_f8_amax, (size_t)kF8Tensors, "fp8 amax")) != ART_OK) return st;
+    cudaMemsetAsync(ctx->d_f8_amax, 0, sizeof(unsigned int) * kF8Tensors, ctx->stream);
+    ctx->f8_calibrated = false;
+  }
   return sync_check(ctx, "load_shader");
 }
 
@@ -606,7 +617,7 @@ art_status art_render_frame(art_ctx* ctx, int view, const float* axis_angle, con
   art_status st = art_set_pose(ctx, axis_angle, R, T);
   if (st != ART_OK) return st;
   const ViewParams& v = ctx->views[view];
-  int fdt = ctx->net_dtype == ART_F32 ? ART_F32 : ART_BF16;
+  int fdt = ctx->net_dtype == ART_F32 ? ART_F32 : ART_BF16;  // BF16 F feeds the BF16 and FP8 networks
   size_t fbytes = (size_t)v.W * v.H * ctx->C * (fdt == ART_F32 ? 4 : 2);
   if ((st = ensure(ctx, &ctx->d_F, &ctx->d_F_bytes, fbytes, "F buffer")) != ART_OK) return st;
   if ((st = ensure(ctx, (void**)&ctx->d_A, &ctx->d_A_bytes, (size_t)v.W * v.H * 4, "A buffer")) != ART_OK) return st;
@@ -763,6 +774,8 @@ art_status art_debug_buffer(art_ctx* ctx, int which, void* dst, int64_t bytes, i
     case ART_BUF_KEYS: src = ctx->d_keys[0]; sz = (int64_t)ninst * 4; break;
     case ART_BUF_VALS: src = ctx->d_vals[0]; sz = (int64_t)ninst * 4; break;
     case ART_BUF_RANGES: src = ctx->d_ranges; sz = ctx->ranges_cap * 8; break;
+    case ART_BUF_FP8_SCALES: src = ctx->d_f8_scale; sz = ctx->d_f8_scale ? kF8Tensors * 4 : 0; break;
+    case ART_BUF_ACTIVATIONS: src = ctx->d_act; sz = ctx->d_act ? (int64_t)ctx->d_act_bytes : 0; break;
     default: return fail(ctx, ART_ERR_INVALID_ARG, "unknown buffer %d", which);
   }
   if (needed) *needed = sz;

@@ -298,6 +298,105 @@ art_status run_unet_tc(art_ctx* ctx, const ViewParams& v, const __nv_bfloat16* F
   return ART_OK;
 }
 
+// FP8 (E4M3) U-Net on the tensor cores (kind::f8f6f4), same dataflow as
+// run_unet_tc.  Activation tensors carry one scale each (a concatenation
+// buffer and its pooled copy share one); every call quantises with the scales
+// measured on the previous call (delayed per-tensor scaling from max |value|)
+// and records this call's maxima.  The first call after loading calibrates:
+// it runs once with unit scales to measure the maxima, then again.
+art_status run_unet_f8(art_ctx* ctx, const ViewParams& v, const __nv_bfloat16* F, float* rgba) {
+  const int H = v.H, W = v.W;
+  const art_net_desc& nd = ctx->net;
+  const int c0 = nd.ch[0], c1 = nd.ch[1], c2 = nd.ch[2], c3 = nd.ch[3];
+  struct Buf {
+    int h, w, c;
+    size_t off;
+  };
+  std::vector<Buf> bufs;
+  size_t total = 0;
+  auto add = [&](int h, int w, int c) {
+    bufs.push_back(Buf{h, w, c, total});
+    total += ((size_t)h * w * c + 255) & ~(size_t)255;
+    return (int)bufs.size() - 1;
+  };
+  const int fin = add(H, W, nd.cin);
+  const int e0a = add(H, W, c0), cat0 = add(H, W, c1 + c0), p0 = add(H / 2, W / 2, c0);
+  const int e1a = add(H / 2, W / 2, c1), cat1 = add(H / 2, W / 2, c2 + c1), p1 = add(H / 4, W / 4, c1);
+  const int e2a = add(H / 4, W / 4, c2), cat2 = add(H / 4, W / 4, c3 + c2), p2 = add(H / 8, W / 8, c2);
+  const int e3a = add(H / 8, W / 8, c3);
+  const int d2a = add(H / 4, W / 4, c2), d1a = add(H / 2, W / 2, c1), d0a = add(H, W, c0);
+  if (ensure(ctx, &ctx->d_act, &ctx->d_act_bytes, total, "activations") != ART_OK) return ART_ERR_OOM;
+  auto P = [&](int i) { return (uint8_t*)ctx->d_act + bufs[i].off; };
+  // scale slots: 0 input, 1 e0a, 2 cat0/p0, 3 e1a, 4 cat1/p1, 5 e2a, 6 cat2/p2, 7 e3a, 8 d2a, 9 d1a, 10 d0a
+  float* sc = ctx->d_f8_scale;
+  unsigned int* am = ctx->d_f8_amax;
+  const auto& L = ctx->layers;
+  auto conv = [&](int in, int sin, int cin, int h, int w, int li, int out, int sout, int ld, int off, int up2,
+                  float* head_out) {
+    TcConv c;
+    c.in = P(in);
+    c.cin = cin;
+    c.H = h;
+    c.W = w;
+    c.w = L[li].w8;
+    c.bias = L[li].b32;
+    c.cout = L[li].cout;
+    c.act = 1;
+    c.out = out >= 0 ? P(out) : nullptr;
+    c.ld_out = ld;
+    c.ch_off = off;
+    c.up2 = up2;
+    c.rgba = head_out;
+    c.head_w = head_out ? L[14].w32 : nullptr;
+    c.head_b = head_out ? L[14].b32 : nullptr;
+    c.f8 = true;
+    c.in_scale = sc + sin;
+    c.w_scale = L[li].wscale;
+    c.out_scale = out >= 0 ? sc + sout : nullptr;
+    c.out_amax = out >= 0 ? am + sout : nullptr;
+    return launch_tc_conv(ctx, c);
+  };
+  auto network = [&]() -> art_status {
+    art_status st = ART_OK;
+#define ART_TRY(x)                  \
+  if ((st = (x)) != ART_OK) return st
+    launch_quantize_input(ctx, F, (int64_t)H * W * nd.cin, sc + 0, P(fin), am + 0);
+    ART_TRY(conv(fin, 0, nd.cin, H, W, 0, e0a, 1, c0, 0, 0, nullptr));
+    ART_TRY(conv(e0a, 1, c0, H, W, 1, cat0, 2, c1 + c0, c1, 0, nullptr));
+    launch_pool_fp8(ctx, P(cat0), c1 + c0, c1, P(p0), H, W, c0);
+    ART_TRY(conv(p0, 2, c0, H / 2, W / 2, 2, e1a, 3, c1, 0, 0, nullptr));
+    ART_TRY(conv(e1a, 3, c1, H / 2, W / 2, 3, cat1, 4, c2 + c1, c2, 0, nullptr));
+    launch_pool_fp8(ctx, P(cat1), c2 + c1, c2, P(p1), H / 2, W / 2, c1);
+    ART_TRY(conv(p1, 4, c1, H / 4, W / 4, 4, e2a, 5, c2, 0, 0, nullptr));
+    ART_TRY(conv(e2a, 5, c2, H / 4, W / 4, 5, cat2, 6, c3 + c2, c3, 0, nullptr));
+    launch_pool_fp8(ctx, P(cat2), c3 + c2, c3, P(p2), H / 4, W / 4, c2);
+    ART_TRY(conv(p2, 6, c2, H / 8, W / 8, 6, e3a, 7, c3, 0, 0, nullptr));
+    ART_TRY(conv(e3a, 7, c3, H / 8, W / 8, 7, cat2, 6, c3 + c2, 0, 1, nullptr));
+    ART_TRY(conv(cat2, 6, c3 + c2, H / 4, W / 4, 8, d2a, 8, c2, 0, 0, nullptr));
+    ART_TRY(conv(d2a, 8, c2, H / 4, W / 4, 9, cat1, 4, c2 + c1, 0, 1, nullptr));
+    ART_TRY(conv(cat1, 4, c2 + c1, H / 2, W / 2, 10, d1a, 9, c1, 0, 0, nullptr));
+    ART_TRY(conv(d1a, 9, c1, H / 2, W / 2, 11, cat0, 2, c1 + c0, 0, 1, nullptr));
+    ART_TRY(conv(cat0, 2, c1 + c0, H, W, 12, d0a, 10, c0, 0, 0, nullptr));
+    ART_TRY(conv(d0a, 10, c0, H, W, 13, -1, 0, 0, 0, 0, rgba));
+#undef ART_TRY
+    return ART_OK;
+  };
+  art_status st;
+  if (!ctx->f8_calibrated) {  // measure the maxima once with unit scales
+    launch_update_scales(ctx, sc, am, kF8Tensors, 1.0f);
+    if ((st = network()) != ART_OK) return st;
+    launch_update_scales(ctx, sc, am, kF8Tensors, 0.0f);
+    ctx->f8_calibrated = true;
+  }
+  if ((st = network()) != ART_OK) return st;
+  launch_update_scales(ctx, sc, am, kF8Tensors, 0.0f);  // scales of the next call
+  return ART_OK;
+}
+
+// FP8 input quantisation reads BF16 pairs: the input channel count must be even
+// (it is a multiple of 32 whenever unet_tc_ok holds).
+bool f8_input_unusable(art_ctx* ctx) { return (ctx->net.cin % 2) != 0; }
+
 // The tensor-core path covers the U-Net when every layer fits its shapes.
 bool unet_tc_ok(art_ctx* ctx, const ViewParams& v) {
   const art_net_desc& nd = ctx->net;
@@ -306,7 +405,7 @@ bool unet_tc_ok(art_ctx* ctx, const ViewParams& v) {
     TcConv c{};
     c.cin = ctx->layers[i].cin;
     c.cout = ctx->layers[i].cout;
-    c.ld_out = 8;
+    c.ld_out = 16;
     c.rgba = i == 13 ? (float*)1 : nullptr;
     if (ctx->layers[i].k != 3 || !ctx->layers[i].wbf || !tc_conv_ok(c)) return false;
   }
@@ -320,7 +419,12 @@ art_status run_shader(art_ctx* ctx, const ViewParams& v, const void* F, int F_dt
     if (F_dtype != ART_F32) return fail(ctx, ART_ERR_INVALID_ARG, "shade: FP32 network needs an FP32 feature map");
     return run_typed<float>(ctx, v, F, rgba);
   }
-  if (F_dtype != ART_BF16) return fail(ctx, ART_ERR_INVALID_ARG, "shade: BF16 network needs a BF16 feature map");
+  if (F_dtype != ART_BF16) return fail(ctx, ART_ERR_INVALID_ARG, "shade: BF16/FP8 network needs a BF16 feature map");
+  if (ctx->net_dtype == ART_FP8) {
+    if (!unet_tc_ok(ctx, v) || f8_input_unusable(ctx))
+      return fail(ctx, ART_ERR_UNSUPPORTED, "FP8 network: U-Net with tensor-core shapes and W, H multiples of 8 only");
+    return run_unet_f8(ctx, v, (const __nv_bfloat16*)F, rgba);
+  }
   if (unet_tc_ok(ctx, v)) return run_unet_tc(ctx, v, (const __nv_bfloat16*)F, rgba);
   return run_typed<__nv_bfloat16>(ctx, v, F, rgba);
 }

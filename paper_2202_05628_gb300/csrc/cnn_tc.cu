@@ -16,6 +16,7 @@
 // error word, stops its loops, frees its TMEM and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cuda_fp8.h>
 
 #include <mutex>
 
@@ -80,22 +81,32 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, ui
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// UMMA shared-memory descriptor of a K-major tile written by TMA with 128-B
-// (KC = 64 bf16 per row) or 64-B (KC = 32) swizzling: start address, leading
+// UMMA shared-memory descriptor of a K-major tile written by TMA with rows of
+// KCB bytes and the matching swizzle (128, 64 or 32 B): start address, leading
 // byte offset (unused for swizzled K-major, 16 B), stride byte offset between
 // 8-row groups (8 rows x row bytes), descriptor version 1, swizzle mode.
-template <int KC>
+template <int KCB>
 __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
-  constexpr uint64_t kSbo = (uint64_t)(8 * KC * 2) >> 4;
-  constexpr uint64_t kSwz = KC == 64 ? 2ull : 4ull;  // 2: 128-B swizzle, 4: 64-B swizzle
+  constexpr uint64_t kSbo = (uint64_t)(8 * KCB) >> 4;
+  constexpr uint64_t kSwz = KCB == 128 ? 2ull : (KCB == 64 ? 4ull : 6ull);  // 128-, 64-, 32-B swizzle
   return (uint64_t)((saddr >> 4) & 0x3FFFu) | (1ull << 16) | (kSbo << 32) | (1ull << 46) | (kSwz << 61);
 }
 
-__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-          d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+// D (TMEM, FP32) += A x B^T for one K step of 32 bytes: 16 BF16 (kind::f16)
+// or 32 E4M3 (kind::f8f6f4) elements.
+template <bool F8>
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  if constexpr (F8) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+  }
 }
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
@@ -119,7 +130,11 @@ struct TcParams {
   int tiles_per_row, n_tiles;
   int act;
   const float* bias;
-  __nv_bfloat16* out;
+  void* out;             // BF16, or E4M3 for the FP8 network
+  const float* in_scale;   // FP8: dequantisation scale of the input tensor (device scalar)
+  const float* w_scale;    // FP8: per-output-channel weight scales [cout]
+  const float* out_scale;  // FP8: quantisation scale of the output tensor (device scalar)
+  unsigned int* out_amax;  // FP8: running max |output| (float bits) for the next call's scale
   int ld_out, ch_off, up2;
   float* rgba;           // fused 1x1 head (cout -> 4) + sigmoid when non-null
   const float* head_w;   // [4][cout]
@@ -127,25 +142,27 @@ struct TcParams {
   unsigned long long* err;
 };
 
-template <int N, int KC>
+template <int N, int KCB, bool F8>
 struct TcCfg {
-  static constexpr int kA = 128 * KC * 2;
-  static constexpr int kB = N * KC * 2;
+  static constexpr int kA = 128 * KCB;
+  static constexpr int kB = N * KCB;
   static constexpr int kStage = kA + kB;
   static constexpr int kStagesRaw = 196608 / kStage;
   static constexpr int kStages = kStagesRaw > 8 ? 8 : kStagesRaw;
   static constexpr int kTmemCols = 2 * N;  // two accumulators; N in {32, 64, 128, 256}
-  static constexpr uint32_t kIdesc = (1u << 4)                       // D: FP32
-                                     | (1u << 7) | (1u << 10)        // A, B: BF16
-                                     | ((uint32_t)(N >> 3) << 17)    // N / 8
-                                     | ((uint32_t)(128 >> 4) << 24);  // M / 16
-  static constexpr int kSmem = kStages * kStage + 1024 + 8 * (2 * kStages + 4) + 16 + 4 * N + 4 * (4 * 32 + 4);
+  static constexpr uint32_t kFmt = F8 ? 0u : 1u;  // A/B format: E4M3 (kind::f8f6f4) or BF16 (kind::f16)
+  static constexpr uint32_t kIdesc = (1u << 4)                          // D: FP32
+                                     | (kFmt << 7) | (kFmt << 10)       // A, B formats
+                                     | ((uint32_t)(N >> 3) << 17)       // N / 8
+                                     | ((uint32_t)(128 >> 4) << 24);    // M / 16
+  static constexpr int kSmem = kStages * kStage + 1024 + 8 * (2 * kStages + 4) + 16 + 4 * N + 4 * (4 * 32 + 4) + 4 * N;
 };
 
-template <int N, int KC>
+template <int N, int KCB, bool F8>
 __global__ void __launch_bounds__(kThreads, 1)
     conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcParams p) {
-  using Cfg = TcCfg<N, KC>;
+  using Cfg = TcCfg<N, KCB, F8>;
+  constexpr int KC = F8 ? KCB : KCB / 2;  // channels per K chunk
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   uint8_t* sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
@@ -158,6 +175,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   float* s_bias = reinterpret_cast<float*>(tmem_slot + 4);
   float* s_head = s_bias + N;
+  float* s_wsc = s_head + 4 * 32 + 4;  // FP8 per-output-channel weight scales
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int cpt = p.cin / KC;  // K chunks per tap
@@ -178,6 +196,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   for (int i = threadIdx.x; i < N; i += kThreads) s_bias[i] = i < p.cout ? p.bias[i] : 0.0f;
   if (p.rgba)
     for (int i = threadIdx.x; i < 4 * N + 4; i += kThreads) s_head[i] = i < 4 * N ? p.head_w[i] : p.head_b[i - 4 * N];
+  if (F8)
+    for (int i = threadIdx.x; i < N; i += kThreads) s_wsc[i] = i < p.cout ? p.w_scale[i] : 0.0f;
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"(Cfg::kTmemCols));
@@ -187,6 +207,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
+  float amax = 0.0f;  // FP8 epilogue: max |output| seen by this thread
 
   if (warp == 0) {
     // ---------------------------------------------------------------- TMA
@@ -228,8 +249,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           tc_fence_after();
           const uint32_t a = smem_u32(stages + s * Cfg::kStage), b = a + Cfg::kA;
 #pragma unroll
-          for (int kk = 0; kk < KC / 16; ++kk)
-            umma_bf16(d, umma_desc<KC>(a + kk * 32), umma_desc<KC>(b + kk * 32), Cfg::kIdesc, (c | kk) != 0);
+          for (int kk = 0; kk < KCB / 32; ++kk)
+            umma<F8>(d, umma_desc<KCB>(a + kk * 32), umma_desc<KCB>(b + kk * 32), Cfg::kIdesc, (c | kk) != 0);
           umma_commit(&empty[s]);
           if (++s == Cfg::kStages) {
             s = 0;
@@ -249,6 +270,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---------------------------------------------------------------- epilogue
     const int qd = warp & 3;           // TMEM lane quarter this warp may access
     const int m = qd * 32 + lane;      // row of the tile = pixel offset
+    const float in_s = F8 ? *p.in_scale : 1.0f;
+    const float out_inv = (F8 && p.out) ? 1.0f / *p.out_scale : 1.0f;
     int buf = 0;
     uint32_t aph = 0;
     for (int tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x) {
@@ -263,7 +286,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         float v[32];
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
-          float t = __uint_as_float(r[j]) + s_bias[c0 + j];
+          const float acc = F8 ? __uint_as_float(r[j]) * (in_s * s_wsc[c0 + j]) : __uint_as_float(r[j]);
+          const float t = acc + s_bias[c0 + j];
           v[j] = p.act == 1 ? fmaxf(t, 0.0f) : t;
         }
         if (!valid) continue;
@@ -279,26 +303,39 @@ __global__ void __launch_bounds__(kThreads, 1)
           reinterpret_cast<float4*>(p.rgba)[(size_t)y * p.W + x] = make_float4(o[0], o[1], o[2], o[3]);
           continue;
         }
-        uint4 pk[4];
-        uint32_t* w = reinterpret_cast<uint32_t*>(pk);
+        constexpr int kVec = F8 ? 2 : 4;  // 16-B stores of the 32 channels
+        uint4 pk[kVec];
+        if constexpr (F8) {
+          uint16_t* w = reinterpret_cast<uint16_t*>(pk);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          __nv_bfloat162 b2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-          w[j] = *reinterpret_cast<uint32_t*>(&b2);
+          for (int j = 0; j < 16; ++j) {
+            amax = fmaxf(amax, fmaxf(fabsf(v[2 * j]), fabsf(v[2 * j + 1])));
+            w[j] = (uint16_t)__nv_cvt_float2_to_fp8x2(make_float2(v[2 * j] * out_inv, v[2 * j + 1] * out_inv),
+                                                      __NV_SATFINITE, __NV_E4M3);
+          }
+        } else {
+          uint32_t* w = reinterpret_cast<uint32_t*>(pk);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            __nv_bfloat162 b2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+            w[j] = *reinterpret_cast<uint32_t*>(&b2);
+          }
         }
+        constexpr int kEs = F8 ? 1 : 2;
+        uint8_t* outb = reinterpret_cast<uint8_t*>(p.out);
         if (!p.up2) {
-          uint4* dst = reinterpret_cast<uint4*>(p.out + ((size_t)y * p.W + x) * p.ld_out + p.ch_off + c0);
+          uint4* dst = reinterpret_cast<uint4*>(outb + (((size_t)y * p.W + x) * p.ld_out + p.ch_off + c0) * kEs);
 #pragma unroll
-          for (int k = 0; k < 4; ++k) dst[k] = pk[k];
+          for (int k = 0; k < kVec; ++k) dst[k] = pk[k];
         } else {
 #pragma unroll
           for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
             for (int dx = 0; dx < 2; ++dx) {
               const size_t pix = (size_t)(2 * y + dy) * (2 * p.W) + (2 * x + dx);
-              uint4* dst = reinterpret_cast<uint4*>(p.out + pix * p.ld_out + p.ch_off + c0);
+              uint4* dst = reinterpret_cast<uint4*>(outb + (pix * p.ld_out + p.ch_off + c0) * kEs);
 #pragma unroll
-              for (int k = 0; k < 4; ++k) dst[k] = pk[k];
+              for (int k = 0; k < kVec; ++k) dst[k] = pk[k];
             }
         }
       }
@@ -309,6 +346,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         aph ^= 1u;
       }
     }
+  }
+  if (F8 && warp >= 2 && p.out_amax) {  // running max |output| for the next call's scale
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    if (lane == 0) atomicMax(p.out_amax, __float_as_uint(amax));
   }
   tc_fence_before();
   __syncthreads();
@@ -361,29 +403,31 @@ bool encode_fn() {
   return g_encode != nullptr;
 }
 
-template <int N, int KC>
+template <int N, int KCB, bool F8>
 art_status launch_typed(art_ctx* ctx, const TcConv& c) {
-  using Cfg = TcCfg<N, KC>;
+  using Cfg = TcCfg<N, KCB, F8>;
+  constexpr int kEs = F8 ? 1 : 2;
+  constexpr int KC = KCB / kEs;
+  const CUtensorMapDataType dt = F8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  const CUtensorMapSwizzle swz = KCB == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                            : (KCB == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B);
   CUtensorMap tmA, tmB;
-  const CUtensorMapSwizzle swz = KC == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
   {
     cuuint64_t dims[3] = {(cuuint64_t)c.cin, (cuuint64_t)c.W, (cuuint64_t)c.H};
-    cuuint64_t strides[2] = {(cuuint64_t)c.cin * 2, (cuuint64_t)c.W * c.cin * 2};
+    cuuint64_t strides[2] = {(cuuint64_t)c.cin * kEs, (cuuint64_t)c.W * c.cin * kEs};
     cuuint32_t box[3] = {(cuuint32_t)KC, 128, 1};
     cuuint32_t es[3] = {1, 1, 1};
-    CUresult r = g_encode(&tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)c.in, dims, strides, box, es,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r = g_encode(&tmA, dt, 3, (void*)c.in, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(ctx, ART_ERR_CUDA, "cuTensorMapEncodeTiled (activations) failed: %d", (int)r);
   }
   {
     cuuint64_t dims[2] = {(cuuint64_t)9 * c.cin, (cuuint64_t)c.cout};
-    cuuint64_t strides[1] = {(cuuint64_t)9 * c.cin * 2};
+    cuuint64_t strides[1] = {(cuuint64_t)9 * c.cin * kEs};
     cuuint32_t box[2] = {(cuuint32_t)KC, (cuuint32_t)N};
     cuuint32_t es[2] = {1, 1};
-    CUresult r = g_encode(&tmB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)c.w, dims, strides, box, es,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r = g_encode(&tmB, dt, 2, (void*)c.w, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(ctx, ART_ERR_CUDA, "cuTensorMapEncodeTiled (weights) failed: %d", (int)r);
   }
   TcParams p;
@@ -396,6 +440,10 @@ art_status launch_typed(art_ctx* ctx, const TcConv& c) {
   p.act = c.act;
   p.bias = c.bias;
   p.out = c.out;
+  p.in_scale = c.in_scale;
+  p.w_scale = c.w_scale;
+  p.out_scale = c.out_scale;
+  p.out_amax = c.out_amax;
   p.ld_out = c.ld_out;
   p.ch_off = c.ch_off;
   p.up2 = c.up2;
@@ -403,30 +451,69 @@ art_status launch_typed(art_ctx* ctx, const TcConv& c) {
   p.head_w = c.head_w;
   p.head_b = c.head_b;
   p.err = ctx->d_status + kStTcError;
-  auto kfn = conv_tc_kernel<N, KC>;
+  auto kfn = conv_tc_kernel<N, KCB, F8>;
   cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "conv_tc shared memory attribute");
   const int grid = std::min(p.n_tiles, ctx->num_sms);
-  ART_LAUNCH(ctx, "conv_tc", kfn, grid, kThreads, Cfg::kSmem, tmA, tmB, p);
+  ART_LAUNCH(ctx, F8 ? "conv_tc_fp8" : "conv_tc", kfn, grid, kThreads, Cfg::kSmem, tmA, tmB, p);
   return ART_OK;
+}
+
+// 2x2 max pooling of E4M3 activations (non-negative after ReLU, whose bit
+// patterns order like unsigned integers): byte-wise integer maximum.
+__global__ void maxpool2_fp8_kernel(const uint8_t* __restrict__ in, int ld, int ch_off, uint8_t* __restrict__ out,
+                                    int H, int W, int C) {
+  const int C16 = C / 16;
+  const int64_t total = (int64_t)(H / 2) * (W / 2) * C16;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(idx % C16) * 16;
+    const int64_t pp = idx / C16;
+    const int x = (int)(pp % (W / 2)), y = (int)(pp / (W / 2));
+    const uint8_t* q = in + (((size_t)(2 * y) * W) + 2 * x) * ld + ch_off + c;
+    uint4 a = *reinterpret_cast<const uint4*>(q);
+    uint4 b = *reinterpret_cast<const uint4*>(q + ld);
+    uint4 cc = *reinterpret_cast<const uint4*>(q + (size_t)W * ld);
+    uint4 d = *reinterpret_cast<const uint4*>(q + (size_t)W * ld + ld);
+    uint4 o;
+    o.x = __vmaxu4(__vmaxu4(a.x, b.x), __vmaxu4(cc.x, d.x));
+    o.y = __vmaxu4(__vmaxu4(a.y, b.y), __vmaxu4(cc.y, d.y));
+    o.z = __vmaxu4(__vmaxu4(a.z, b.z), __vmaxu4(cc.z, d.z));
+    o.w = __vmaxu4(__vmaxu4(a.w, b.w), __vmaxu4(cc.w, d.w));
+    *reinterpret_cast<uint4*>(out + (size_t)pp * C + c) = o;
+  }
 }
 
 }  // namespace
 
 bool tc_conv_ok(const TcConv& c) {
   const bool n_ok = c.cout == 32 || c.cout == 64 || c.cout == 128 || c.cout == 256;
-  return n_ok && (c.cin % 32 == 0) && c.cin >= 32 && (c.ld_out % 8 == 0) && (c.ch_off % 8 == 0) &&
+  const int al = c.f8 ? 16 : 8;  // 16-byte aligned output rows and channel offsets
+  return n_ok && (c.cin % 32 == 0) && c.cin >= 32 && (c.ld_out % al == 0) && (c.ch_off % al == 0) &&
          (!c.rgba || c.cout == 32) && encode_fn();
 }
 
 art_status launch_tc_conv(art_ctx* ctx, const TcConv& c) {
   if (!tc_conv_ok(c)) return fail(ctx, ART_ERR_UNSUPPORTED, "tensor-core conv: unsupported shape");
-  const bool k64 = c.cin % 64 == 0;
+  if (c.f8) {  // row bytes = channels per K chunk: 128, 64 or 32
+    const int kcb = c.cin % 128 == 0 ? 128 : (c.cin % 64 == 0 ? 64 : 32);
+#define ART_F8(NN)                                                             \
+  return kcb == 128 ? launch_typed<NN, 128, true>(ctx, c)                      \
+                    : (kcb == 64 ? launch_typed<NN, 64, true>(ctx, c) : launch_typed<NN, 32, true>(ctx, c))
+    switch (c.cout) {
+      case 32: ART_F8(32);
+      case 64: ART_F8(64);
+      case 128: ART_F8(128);
+      default: ART_F8(256);
+    }
+#undef ART_F8
+  }
+  const bool k64 = c.cin % 64 == 0;  // BF16: 64 channels = 128-B rows, else 32 = 64-B rows
   switch (c.cout) {
-    case 32: return k64 ? launch_typed<32, 64>(ctx, c) : launch_typed<32, 32>(ctx, c);
-    case 64: return k64 ? launch_typed<64, 64>(ctx, c) : launch_typed<64, 32>(ctx, c);
-    case 128: return k64 ? launch_typed<128, 64>(ctx, c) : launch_typed<128, 32>(ctx, c);
-    default: return k64 ? launch_typed<256, 64>(ctx, c) : launch_typed<256, 32>(ctx, c);
+    case 32: return k64 ? launch_typed<32, 128, false>(ctx, c) : launch_typed<32, 64, false>(ctx, c);
+    case 64: return k64 ? launch_typed<64, 128, false>(ctx, c) : launch_typed<64, 64, false>(ctx, c);
+    case 128: return k64 ? launch_typed<128, 128, false>(ctx, c) : launch_typed<128, 64, false>(ctx, c);
+    default: return k64 ? launch_typed<256, 128, false>(ctx, c) : launch_typed<256, 64, false>(ctx, c);
   }
 }
 
@@ -435,6 +522,83 @@ void launch_pool_bf16(art_ctx* ctx, const __nv_bfloat16* in, int ld, int ch_off,
   const int64_t total = (int64_t)(H / 2) * (W / 2) * (C / 8);
   const int grid = (int)std::min<int64_t>((total + 255) / 256, (int64_t)ctx->num_sms * 8);
   ART_LAUNCH(ctx, "maxpool2_bf16", maxpool2_bf16_kernel, grid, 256, 0, in, ld, ch_off, out, H, W, C);
+}
+
+namespace {
+
+constexpr float kE4M3Max = 448.0f;
+
+// Per-output-channel E4M3 weights: scale_co = max |w_co| / 448, w8 = rn(w / scale_co).
+__global__ void quantize_weights_kernel(const float* __restrict__ w, int K, uint8_t* __restrict__ w8,
+                                        float* __restrict__ scale) {
+  const int co = blockIdx.x;
+  const float* row = w + (size_t)co * K;
+  float m = 0.0f;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) m = fmaxf(m, fabsf(row[k]));
+  __shared__ float red[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) red[0] = m;
+  }
+  __syncthreads();
+  const float s = fmaxf(red[0], 1e-30f) / kE4M3Max;
+  if (threadIdx.x == 0) scale[co] = s;
+  const float inv = 1.0f / s;
+  for (int k = threadIdx.x; k < K; k += blockDim.x)
+    w8[(size_t)co * K + k] = (uint8_t)__nv_cvt_float_to_fp8(row[k] * inv, __NV_SATFINITE, __NV_E4M3);
+}
+
+// BF16 feature map -> E4M3 with the current input scale; records max |F|.
+__global__ void quantize_input_kernel(const __nv_bfloat16* __restrict__ in, int64_t m, const float* __restrict__ scale,
+                                      uint8_t* __restrict__ out, unsigned int* __restrict__ amax) {
+  const float inv = 1.0f / *scale;
+  float a = 0.0f;
+  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 2; i < m; i += (int64_t)gridDim.x * blockDim.x * 2) {
+    const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(in + i));
+    a = fmaxf(a, fmaxf(fabsf(v.x), fabsf(v.y)));
+    *reinterpret_cast<uint16_t*>(out + i) =
+        (uint16_t)__nv_cvt_float2_to_fp8x2(make_float2(v.x * inv, v.y * inv), __NV_SATFINITE, __NV_E4M3);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(amax, __float_as_uint(a));
+}
+
+// Delayed scaling: next call's scale = max |value| of this call / 448; or a
+// fixed value (calibration).
+__global__ void update_scales_kernel(float* __restrict__ scale, unsigned int* __restrict__ amax, int n, float fixed) {
+  const int i = threadIdx.x;
+  if (i >= n) return;
+  scale[i] = fixed > 0.0f ? fixed : fmaxf(__uint_as_float(amax[i]), 1e-12f) / kE4M3Max;
+  amax[i] = 0u;
+}
+
+}  // namespace
+
+void launch_quantize_weights(art_ctx* ctx, const float* w, int cout, int K, uint8_t* w8, float* scale) {
+  ART_LAUNCH(ctx, "quantize_w_fp8", quantize_weights_kernel, cout, 256, 0, w, K, w8, scale);
+}
+
+void launch_quantize_input(art_ctx* ctx, const __nv_bfloat16* in, int64_t m, const float* scale, uint8_t* out,
+                           unsigned int* amax) {
+  const int grid = (int)std::min<int64_t>((m / 2 + 255) / 256, (int64_t)ctx->num_sms * 8);
+  ART_LAUNCH(ctx, "quantize_f_fp8", quantize_input_kernel, grid, 256, 0, in, m, scale, out, amax);
+}
+
+void launch_update_scales(art_ctx* ctx, float* scale, unsigned int* amax, int n, float fixed) {
+  ART_LAUNCH(ctx, "fp8_scales", update_scales_kernel, 1, 32, 0, scale, amax, n, fixed);
+}
+
+void launch_pool_fp8(art_ctx* ctx, const uint8_t* in, int ld, int ch_off, uint8_t* out, int H, int W, int C) {
+  const int64_t total = (int64_t)(H / 2) * (W / 2) * (C / 16);
+  const int grid = (int)std::min<int64_t>((total + 255) / 256, (int64_t)ctx->num_sms * 8);
+  ART_LAUNCH(ctx, "maxpool2_fp8", maxpool2_fp8_kernel, grid, 256, 0, in, ld, ch_off, out, H, W, C);
 }
 
 }  // namespace art

@@ -134,6 +134,9 @@ struct art_ctx {
   std::vector<art::ConvLayer> layers;
   void* d_act = nullptr;        // activation arena
   size_t d_act_bytes = 0;
+  float* d_f8_scale = nullptr;  // FP8 network: per-tensor activation scales
+  unsigned int* d_f8_amax = nullptr;
+  bool f8_calibrated = false;
 
   // ---- backward
   float* d_gN = nullptr;        // [n][12] dL/d(A_i^-1) accumulator
@@ -201,21 +204,35 @@ art_status run_shader(art_ctx* ctx, const ViewParams& v, const void* F, int F_dt
 // same resolution or (up2) replicated 2x2 into a 2H x 2W tensor; or, with
 // rgba set, the fused 1x1 head (cout -> 4) + sigmoid into FP32 RGBA.
 struct TcConv {
-  const __nv_bfloat16* in;
+  const void* in;
   int cin, H, W;
-  const __nv_bfloat16* w;
+  const void* w;
   const float* bias;
   int cout, act;
-  __nv_bfloat16* out;
+  void* out;
   int ld_out, ch_off, up2;
   float* rgba;
   const float* head_w;
   const float* head_b;
+  // FP8 (E4M3) network: operands and output in E4M3; the accumulator is
+  // dequantised by in_scale x w_scale[co], the output quantised by out_scale
+  // and its max |value| recorded in out_amax (float bits).
+  bool f8 = false;
+  const float* in_scale = nullptr;
+  const float* w_scale = nullptr;
+  const float* out_scale = nullptr;
+  unsigned int* out_amax = nullptr;
 };
 bool tc_conv_ok(const TcConv& c);
 art_status launch_tc_conv(art_ctx* ctx, const TcConv& c);
 void launch_pool_bf16(art_ctx* ctx, const __nv_bfloat16* in, int ld, int ch_off, __nv_bfloat16* out, int H, int W,
                       int C);
+void launch_pool_fp8(art_ctx* ctx, const uint8_t* in, int ld, int ch_off, uint8_t* out, int H, int W, int C);
+void launch_quantize_weights(art_ctx* ctx, const float* w, int cout, int K, uint8_t* w8, float* scale);
+void launch_quantize_input(art_ctx* ctx, const __nv_bfloat16* in, int64_t m, const float* scale, uint8_t* out,
+                           unsigned int* amax);
+void launch_update_scales(art_ctx* ctx, float* scale, unsigned int* amax, int n, float fixed);
+constexpr int kF8Tensors = 11;  // FP8 U-Net activation tensors with their own scale
 
 }  // namespace art
 

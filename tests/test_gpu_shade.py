@@ -117,6 +117,125 @@ def test_unet_bf16_tensor_cores_match_emulation(H, W):
     assert psnr(rgba, ref) > 60.0
 
 
+def _e4m3_codes(x32):
+    """Round-to-nearest-even to E4M3 with saturation at +-448: the byte codes."""
+    import torch
+    t = torch.from_numpy(np.clip(np.asarray(x32, np.float32), -448.0, 448.0))
+    return t.to(torch.float8_e4m3fn).view(torch.uint8).numpy()
+
+
+def _e4m3_values(codes):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(codes)).view(torch.float8_e4m3fn).to(torch.float64).numpy()
+
+
+def _f8_weights(w):
+    """Per-output-channel weight quantisation of the BF16-rounded weights
+    (the form every reduced-precision network starts from): scale =
+    max|w| / 448 in FP32."""
+    import torch
+    w = torch.from_numpy(np.asarray(w, np.float32)).to(torch.bfloat16).float().numpy()
+    sw = (np.abs(w).reshape(w.shape[0], -1).max(1) / np.float32(448.0)).astype(np.float32)
+    q = _e4m3_values(_e4m3_codes(w * (np.float32(1.0) / sw)[:, None, None, None]))
+    return q, sw
+
+
+def _f8_conv(x, s_in, layer, s_out=None):
+    """One FP8 3x3 convolution as the path defines it: E4M3 operands (values
+    ``x``, NHWC), products summed exactly (FP64), accumulator dequantised by
+    s_in x s_w, bias and ReLU in FP32, then the output's E4M3 codes with scale
+    ``s_out`` (or the FP32 values when ``s_out`` is None)."""
+    import torch
+    import torch.nn.functional as Fn
+    w8, sw = _f8_weights(layer[0])
+    acc = Fn.conv2d(torch.from_numpy(x).permute(2, 0, 1)[None], torch.from_numpy(w8).permute(0, 3, 1, 2), padding=1)
+    acc = acc[0].permute(1, 2, 0).numpy().astype(np.float32)
+    v = np.maximum(acc * (np.float32(s_in) * sw) + np.asarray(layer[1], np.float32), np.float32(0))
+    return v if s_out is None else _e4m3_codes(v * (np.float32(1.0) / np.float32(s_out)))
+
+
+_F8_TENSORS = ("fin", "e0a", "cat0", "p0", "e1a", "cat1", "p1", "e2a", "cat2", "p2", "e3a", "d2a", "d1a", "d0a")
+
+
+def _f8_arena(raw, H, W, cin, ch):
+    """Split the activation arena (art_debug_buffer ART_BUF_ACTIVATIONS) into
+    its NHWC E4M3 code tensors."""
+    c0, c1, c2, c3 = ch
+    shapes = [(H, W, cin), (H, W, c0), (H, W, c1 + c0), (H // 2, W // 2, c0), (H // 2, W // 2, c1),
+              (H // 2, W // 2, c2 + c1), (H // 4, W // 4, c1), (H // 4, W // 4, c2), (H // 4, W // 4, c3 + c2),
+              (H // 8, W // 8, c2), (H // 8, W // 8, c3), (H // 4, W // 4, c2), (H // 2, W // 2, c1), (H, W, c0)]
+    out, off = {}, 0
+    for name, sh in zip(_F8_TENSORS, shapes):
+        n = int(np.prod(sh))
+        out[name] = raw[off:off + n].reshape(sh)
+        off += (n + 255) & ~255
+    return out
+
+
+def _codes_agree(got, want, what):
+    """Equal E4M3 codes up to rare one-step flips: the accumulation order of
+    the tensor cores differs from the exact sum, which moves values that lie
+    within an FP32 rounding of a rounding midpoint."""
+    d = np.abs(got.astype(np.int32) - want.astype(np.int32))
+    assert d.max() <= 1, (what, int(d.max()))
+    assert (d != 0).mean() < 2e-3, (what, float((d != 0).mean()))
+
+
+@pytest.mark.parametrize("H,W", [(64, 64), (96, 160)])
+def test_unet_fp8_tensor_cores_layer_by_layer(H, W):
+    """The FP8 (E4M3, tcgen05 kind::f8f6f4) network, each layer fed the
+    library's own E4M3 input tensor and compared with its emulation, with the
+    activation scales the library used; the pooling, the upsampling into the
+    concatenations, the input quantisation and the fused head as well."""
+    import paper_2202_05628_gb300 as art
+    rng = np.random.default_rng(H + 3 * W)
+    F = (rng.standard_normal((H, W, 32)) * 0.3).astype(np.float32)
+    layers = sg.unet_weights(6, cin=32)
+    c0, c1, c2, c3 = sg.UNET_CHANNELS
+    sc = sg.preset("mini")
+    r = renderer(sc, profile=True)
+    cam = sg.orbit_camera(sc.centroid, W, H)
+    set_cam(r, 0, cam)
+    r.load_shader(art.ART_NET_UNET, 32, sg.UNET_CHANNELS, 4, art.flat_params(layers), "fp8")
+    _shade(r, 0, F, cam, F_dtype="bf16")  # first call: calibration pass, then the network
+    s = r.debug_buffer(art.BUF_FP8_SCALES, np.float32)[:11].astype(np.float32)
+    assert np.all(np.isfinite(s)) and np.all(s > 0), s
+    r.kernel_times(reset=True)
+    rgba = _shade(r, 0, F, cam, F_dtype="bf16")
+    r.sync_status()
+    assert r.kernel_times().get("conv_tc_fp8", (0, 0))[0] == 14
+    t = _f8_arena(r.debug_buffer(art.BUF_ACTIVATIONS, np.uint8), H, W, 32, sg.UNET_CHANNELS)
+    v = {k: _e4m3_values(x) for k, x in t.items()}
+    import torch
+    Fb = torch.from_numpy(F).to(torch.bfloat16).float().numpy()
+    _codes_agree(t["fin"], _e4m3_codes(Fb * (np.float32(1.0) / s[0])), "input")
+    up = lambda c: np.repeat(np.repeat(c, 2, 0), 2, 1)
+    pool = lambda c: c.reshape(c.shape[0] // 2, 2, c.shape[1] // 2, 2, -1).max((1, 3))
+    # (input, its scale slot, layer, output tensor, channel slice, output scale slot, upsampled)
+    plan = [("fin", 0, 0, "e0a", slice(None), 1, False), ("e0a", 1, 1, "cat0", slice(c1, None), 2, False),
+            ("p0", 2, 2, "e1a", slice(None), 3, False), ("e1a", 3, 3, "cat1", slice(c2, None), 4, False),
+            ("p1", 4, 4, "e2a", slice(None), 5, False), ("e2a", 5, 5, "cat2", slice(c3, None), 6, False),
+            ("p2", 6, 6, "e3a", slice(None), 7, False), ("e3a", 7, 7, "cat2", slice(0, c3), 6, True),
+            ("cat2", 6, 8, "d2a", slice(None), 8, False), ("d2a", 8, 9, "cat1", slice(0, c2), 4, True),
+            ("cat1", 4, 10, "d1a", slice(None), 9, False), ("d1a", 9, 11, "cat0", slice(0, c1), 2, True),
+            ("cat0", 2, 12, "d0a", slice(None), 10, False)]
+    for src, si, li, dst, chs, so, upsampled in plan:
+        want = _f8_conv(v[src], s[si], layers[li], s[so])
+        _codes_agree(t[dst][..., chs], up(want) if upsampled else want, f"layer {li}")
+    # max-pooling acts on the stored codes: exact
+    for cat, lo, p in (("cat0", c1, "p0"), ("cat1", c2, "p1"), ("cat2", c3, "p2")):
+        assert np.array_equal(t[p], pool(t[cat][..., lo:])), p
+    # last convolution with the fused 1x1 head and sigmoid, in FP32
+    d0 = _f8_conv(v["d0a"], s[10], layers[13]).astype(np.float64)
+    wh = torch.from_numpy(layers[14][0].astype(np.float32)).to(torch.bfloat16).double().numpy().reshape(4, -1)
+    emu = 1.0 / (1.0 + np.exp(-(d0 @ wh.T + layers[14][1].astype(np.float64))))
+    assert np.abs(rgba - emu).max() < 1e-5, np.abs(rgba - emu).max()
+    # the variant's distance from the FP64 network (E4M3 keeps 3 mantissa bits)
+    p = psnr(rgba, oracle.shade_unet(F.astype(np.float64), layers))
+    print(f"FP8 U-Net {H}x{W}: PSNR {p:.1f} dB against the FP64 oracle")
+    assert p > 30.0, p
+
+
 def test_unet_bf16_psnr():
     import paper_2202_05628_gb300 as art
     H = W = 128
