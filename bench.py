@@ -38,10 +38,12 @@ def parse():
     p.add_argument("--steps", type=int, default=60)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    p.add_argument("--form", default="bf16", choices=["bf16", "f32"])
+    p.add_argument("--form", default="bf16", choices=["bf16", "f32", "fp8"])
     p.add_argument("--f32-steps", type=int, default=16, help="steps of the FP32 plain form measured beside")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--side-steps", type=int, default=16,
+                   help="frames of the FP8 form and of the backward pass measured beside")
     return p.parse_args()
 
 
@@ -123,7 +125,7 @@ def setup_renderer(sc, cams, layers, form, profile=False):
     import paper_2202_05628_gb300 as art
     oc = sc.octree
     r = art.Renderer()
-    storage = "bf16" if form == "bf16" else "f32"
+    storage = "f32" if form == "f32" else "bf16"
     r.load_octree(oc.depth, oc.origin, oc.extent, oc.ijk, oc.joint_idx, oc.weights, oc.features, oc.density, storage)
     r.load_skeleton(sc.skeleton.parent, sc.skeleton.rest)
     r.load_shader(art.ART_NET_UNET, oc.C, [32, 64, 128, 256], 4, art.flat_params(layers), form)
@@ -202,6 +204,46 @@ def unet_flops(H, W, cin=32, ch=(32, 64, 128, 256)):
     return tot
 
 
+def backward_timing(sc, cams, poses, layers, steps, flush, warmup=3):
+    """Per-frame time of art_render_backward (dL/df, dL/dsigma, dL/dw of the
+    F and A maps) on the workload, BF16 feature storage, with a dense random
+    upstream gradient (every pixel traced again); the forward maps and the
+    zeroing of the gradient buffers are outside the events."""
+    import torch
+    oc = sc.octree
+    r = setup_renderer(sc, cams, layers, "bf16", profile=True)
+    g = torch.Generator(device="cuda").manual_seed(7)
+    Fm = torch.empty((RES, RES, oc.C), dtype=torch.float32, device="cuda")
+    Am = torch.empty((RES, RES), dtype=torch.float32, device="cuda")
+    dF = torch.randn((RES, RES, oc.C), generator=g, device="cuda") * 1e-3
+    dA = torch.randn((RES, RES), generator=g, device="cuda") * 1e-3
+    df = torch.zeros((oc.n, oc.C), dtype=torch.float32, device="cuda")
+    ds = torch.zeros(oc.n, dtype=torch.float32, device="cuda")
+    dw = torch.zeros((oc.n, 4), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    ms = []
+    for k in range(warmup + steps):
+        if k == warmup:
+            r.kernel_times(reset=True)
+        pi, vi = step_indices(k)
+        p = poses[pi]
+        r.set_pose(p.axis_angle, p.R, p.T)
+        r.render_feature_maps(vi, Fm, Am, "f32")
+        df.zero_(), ds.zero_(), dw.zero_(), flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r.render_backward(vi, Fm, Am, dF, dA, df, ds, dw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if k >= warmup:
+            ms.append(e0.elapsed_time(e1))
+    kt = r.kernel_times(reset=True)
+    r.close()
+    return {"ms_per_frame": float(np.mean(ms)), "frames_per_s": 1e3 / float(np.mean(ms)), "steps": steps,
+            "kernels_ms": {k: round(v[1] / steps, 4) for k, v in kt.items() if "bwd" in k},
+            "what": "dL/df, dL/dsigma, dL/dw through the F and A maps, dense upstream gradient"}
+
+
 def gpu_arm(args):
     import torch
     import torch.distributed as dist
@@ -253,14 +295,33 @@ def gpu_arm(args):
         "kernels_ms_per_frame": {k: round(v[1] / args.steps, 4) for k, v in sorted(kt.items(), key=lambda kv: -kv[1][1])},
         "instances": stats["instances"], "overflow": stats["status"],
     }
+    frames = {}  # RGBA of the frame that the oracle also renders, per form
+
+    def first_frame(rr, form):
+        pi, vi = step_indices(0)
+        p = poses[pi]
+        rr.render_frame(vi, p.axis_angle, p.R, p.T, rgba)
+        torch.cuda.synchronize()
+        frames[form] = rgba.cpu().numpy()
+
+    first_frame(r, args.form)
     r.close()
-    # FP32 plain form beside it (same workload, fewer frames)
-    if args.form == "bf16" and args.f32_steps > 0:
-        r32 = setup_renderer(sc, cams, layers, "f32")
-        ms32, _ = timed_region(r32, poses, args.f32_steps, 2, flush, rgba)
-        result["f32_plain"] = {"value": 1e3 * args.f32_steps / float(np.sum(ms32)),
-                               "ms_per_step": float(np.mean(ms32)), "steps": args.f32_steps}
-        r32.close()
+
+    def side(form, steps):
+        rr = setup_renderer(sc, cams, layers, form)
+        ms_s, _ = timed_region(rr, poses, steps, 3, flush, rgba)
+        first_frame(rr, form)
+        rr.close()
+        return {"value": 1e3 * steps / float(np.sum(ms_s)), "ms_per_step": float(np.mean(ms_s)), "steps": steps}
+
+    # the other forms beside it (same workload, fewer frames)
+    if args.form != "f32" and args.f32_steps > 0:
+        result["f32_plain"] = side("f32", args.f32_steps)
+    if args.side_steps > 0:
+        for form in ("bf16", "fp8"):
+            if form != args.form:
+                result[form + "_form"] = side(form, args.side_steps)
+        result["backward"] = backward_timing(sc, cams, poses, layers, args.side_steps, flush)
     # end to end through the public call with host buffers
     if not args.no_e2e:
         r = setup_renderer(sc, cams, layers, args.form)
@@ -282,7 +343,9 @@ def gpu_arm(args):
                          "d2h_bytes_per_step": int(host_out.numel() * 4), "steps": k_e2e}
         r.close()
     if rank == 0 and not args.no_cpu_baseline:
-        result["cpu_baseline"] = cpu_baseline(sc, cams, poses, layers)
+        result["cpu_baseline"], ref = cpu_baseline(sc, cams, poses, layers)
+        result["quality"] = {f: quality(x, ref) for f, x in frames.items()}
+        result["quality"]["frame"] = "pose %d, azimuth %d against the FP64 oracle" % step_indices(0)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -292,43 +355,72 @@ def gpu_arm(args):
 
 # ---------------------------------------------------------------- oracle arm
 
-def cpu_baseline(sc, cams, poses, layers, frames=1):
-    """The FP64 oracle as it stands on the host cores: whole frames (render
-    + U-Net) of the same workload."""
+def cpu_baseline(sc, cams, poses, layers):
+    """The FP64 oracle as it stands on the host cores: one whole frame
+    (FK, LBS, F and A maps, U-Net) of the same workload.  Returns the record
+    and the oracle's RGBA of that frame."""
     import oracle
+    pi, vi = step_indices(0)
     t0 = time.perf_counter()
-    for k in range(frames):
-        pi, vi = step_indices(k)
-        oracle.render_frame(sc, poses[pi], cams[vi], layers)
+    out = oracle.render_frame(sc, poses[pi], cams[vi], layers)
     dt = time.perf_counter() - t0
-    return {"value": frames / dt, "unit": "frames/s", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"{frames} full frame(s) (pose {step_indices(0)[0]}, azimuth 0): FP64 render + U-Net"}
+    rec = {"value": 1.0 / dt, "unit": "frames/s", "cores": oracle.num_threads(), "kind": "oracle",
+           "sample": f"1 full frame (pose {pi}, azimuth {vi}): FP64 render + U-Net"}
+    return rec, out["rgba"]
+
+
+def quality(rgba, ref):
+    """PSNR (peak 1) and largest difference of an RGBA frame against the
+    oracle's."""
+    d = np.asarray(rgba, np.float64) - ref
+    mse = float(np.mean(d * d))
+    return {"psnr_db": 10.0 * np.log10(1.0 / max(mse, 1e-30)), "max_abs": float(np.abs(d).max())}
+
+
+TILE = 256  # side of the oracle arm's sampled square of the view
 
 
 def reference_arm(args):
+    """The FP64 oracle timed on the host cores.  Each step is a bounded
+    sample of the workload: FK and LBS of all voxels, the F and A maps of one
+    256x256 square of the 1024x1024 view (a camera with the principal point
+    shifted, so the rays are those of the full view), and the U-Net over that
+    square; a step counts as 1/16 of a frame.  16 consecutive steps cover
+    the whole view."""
+    import dataclasses
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     sc, cams, poses, layers = workload()
     import oracle
     oracle.build()
-    frames = []
-    for k in range(args.warmup + args.steps if args.steps <= 2 else 2):
-        pass
-    t_all = 0.0
-    K = max(1, min(args.steps, 2))
-    for k in range(K):
+    per = RES // TILE
+
+    def step(k):
         pi, vi = step_indices(k)
-        t0 = time.perf_counter()
-        oracle.render_frame(sc, poses[pi], cams[vi], layers)
-        t_all += time.perf_counter() - t0
-    v = K / t_all
+        c = cams[vi]
+        q = k % (per * per)
+        x0, y0 = TILE * (q % per), TILE * (q // per)
+        crop = dataclasses.replace(c, W=TILE, H=TILE, cx=c.cx - x0, cy=c.cy - y0)
+        oracle.render_frame(sc, poses[pi], crop, layers)
+
+    for k in range(args.warmup):
+        step(k)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        step(args.warmup + k)
+    t_all = time.perf_counter() - t0
+    frac = (TILE * TILE) / float(RES * RES)
+    v = args.steps * frac / t_all
+    sample = (f"{args.steps} steps, each FK + LBS of {sc.octree.n} voxels, F/A maps of one {TILE}x{TILE} square of "
+              f"the {RES}x{RES} view and the U-Net over it (1/{per * per} frame per step)")
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "frames/s", "n_gpus": args.gpus,
-           "steps": K, "warmup": 0, "ms_per_step": 1e3 * t_all / K, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "voxels": sc.octree.n, "resolution": [RES, RES]},
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "voxels": sc.octree.n, "resolution": [RES, RES],
+                      "sample": f"{TILE}x{TILE} squares"},
            "cpu_baseline": {"value": v, "unit": "frames/s", "cores": oracle.num_threads(), "kind": "oracle",
-                            "sample": f"{K} full frame(s) of the workload (FP64 render + U-Net)"},
+                            "sample": sample},
            "e2e": {"value": v, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
