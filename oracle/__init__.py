@@ -18,6 +18,11 @@ convolution primitives.  Every function follows a passage of the paper
   Analysis").
 * :func:`render_backward`, :func:`lbs_backward` - gradients of Eq. 5-6 and
   Eq. 4 (the paper optimises the feature table end to end).
+* :func:`proposal_inputs`, :func:`proposal_mlp`, :func:`proposal_bins`,
+  :func:`render_interval`, :func:`tau_hist`, :func:`coarse_bound`,
+  :func:`skip_render` - the learned ray-interval proposal that lets the
+  composite skip empty depth (project addition; the paper's nearest passage
+  is the early-stop rule of Sec. 3.1).
 
 Pins: each of these is checked in ``tests/test_oracle_pins.py`` against
 closed forms, brute force, invariants and library routines.
@@ -385,3 +390,208 @@ def render_frame(scene, pose, cam, layers=None, tau: float = TAU_DEFAULT) -> dic
     if layers is not None:
         out["rgba"] = shade(out["F"], layers)
     return out
+
+
+# ---------------------------------------------------------------------------
+# Learned ray-interval proposal (project addition, see module docstring)
+# ---------------------------------------------------------------------------
+#
+# Definitions followed by both sides:
+#   input x (107) = [72 pose axis-angles (J = 24 joints x 3, as given to the
+#     pose), 3 unit world ray direction, sin(2^k pi u) k<8, cos(2^k pi u) k<8,
+#     sin(2^k pi v) k<8, cos(2^k pi v) k<8], u = (x + 1/2) / W, v = (y + 1/2) / H;
+#   MLP 107 -> 64 -> 64 -> 64 -> 64 (ReLU) -> 128 logits; parameters flat as
+#     W0 [64][107], b0, W1 [64][64], b1, W2, b2, W3, b3, W4 [128][64], b4
+#     (y = W x + b);
+#   bins: bn = argmax of logits[0:64], bf = argmax of logits[64:128] (first
+#     index on ties); interval [near + bn D, near + (bf + 1) D], D = (far -
+#     near) / 64; bf < bn is the empty interval.
+
+PROPOSAL_IN, PROPOSAL_HIDDEN, PROPOSAL_BINS = 107, 64, 64
+PROPOSAL_SHAPES = [(64, 107), (64, 64), (64, 64), (64, 64), (128, 64)]
+PROPOSAL_PARAMS = sum(o * i + o for o, i in PROPOSAL_SHAPES)
+MISSED_MAX = 1e-3   # coarse-check threshold of lost transmittance mass
+LABEL_WMIN = 1e-6   # a hit is significant when its weight T_i alpha_i exceeds this
+
+
+def round_bf16(x) -> np.ndarray:
+    """Round to the nearest BF16 (ties to even) via FP32; returns FP64."""
+    b = np.ascontiguousarray(np.asarray(x, np.float32)).view(np.uint32).astype(np.uint64)
+    r = ((b + np.uint64(0x7FFF) + ((b >> np.uint64(16)) & np.uint64(1))) >> np.uint64(16)) << np.uint64(16)
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def ray_dirs(cam) -> np.ndarray:
+    """Unit world-space directions of every pixel's ray, [H, W, 3]."""
+    d = np.zeros((cam.H, cam.W, 3))
+    _L().orc_ray_dirs(ctypes.byref(_cam(cam)), _p(d))
+    return d
+
+
+def proposal_inputs(axis_angle, cam) -> np.ndarray:
+    """The 107-dim proposal input of every pixel's ray, [H*W, 107] FP64."""
+    H, W = cam.H, cam.W
+    pose = _f64(axis_angle).reshape(-1)
+    assert pose.size == 72, "the proposal takes the 24 joints' axis-angles"
+    d = ray_dirs(cam).reshape(-1, 3)
+    ys, xs = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+    u = ((xs + 0.5) / W).reshape(-1, 1)
+    v = ((ys + 0.5) / H).reshape(-1, 1)
+    fr = np.pi * (2.0 ** np.arange(8))[None, :]
+    four = np.concatenate([np.sin(fr * u), np.cos(fr * u), np.sin(fr * v), np.cos(fr * v)], 1)
+    return np.concatenate([np.broadcast_to(pose, (H * W, 72)), d, four], 1)
+
+
+def proposal_layers(params):
+    """Split the flat parameter vector into [(W, b)] of the five layers."""
+    p = _f64(params).reshape(-1)
+    assert p.size == PROPOSAL_PARAMS, (p.size, PROPOSAL_PARAMS)
+    out, o = [], 0
+    for n_out, n_in in PROPOSAL_SHAPES:
+        W = p[o:o + n_out * n_in].reshape(n_out, n_in)
+        o += n_out * n_in
+        b = p[o:o + n_out]
+        o += n_out
+        out.append((W, b))
+    return out
+
+
+def proposal_mlp(x, params, bf16: bool = False) -> np.ndarray:
+    """Logits [M, 128].  With ``bf16`` the inputs, weights and hidden
+    activations are rounded to BF16 where the GPU stores them (biases FP32,
+    sums exact): the precision in which the GPU takes the argmax."""
+    h = _f64(x)
+    layers = proposal_layers(params)
+    if bf16:
+        h = round_bf16(h)
+    for li, (W, b) in enumerate(layers):
+        if bf16:
+            W, b = round_bf16(W), np.asarray(b, np.float32).astype(np.float64)
+        h = h @ W.T + b
+        if li < len(layers) - 1:
+            h = np.maximum(h, 0.0)
+            if bf16:
+                h = round_bf16(h)
+    return h
+
+
+def proposal_bins(logits) -> np.ndarray:
+    """(bn, bf) per row: first argmax of each half of the logits, [M, 2] int32."""
+    lg = np.asarray(logits)
+    return np.stack([np.argmax(lg[:, :PROPOSAL_BINS], 1), np.argmax(lg[:, PROPOSAL_BINS:], 1)], 1).astype(np.int32)
+
+
+def label_bins(labels, hist, cam, tsx: int = 8, tsy: int = 4, nb: int = PROPOSAL_BINS,
+               budget: float = 0.4 * MISSED_MAX) -> np.ndarray:
+    """Training label (bn, bf) of every ray, [H*W, 2] int32: the interval
+    that keeps every significant hit and that the coarse check passes.
+    ``labels`` [H, W, 3] = (lo, hi, Ts) of the plain composite (min t1 and
+    max t0 over significant hits, transmittance after the last of them);
+    ``hist`` the tile histogram of :func:`tau_hist`.
+      bn = min(bin(lo), the largest b with 1 - exp(-sum_{b' < b} hist) <= budget)
+      bf = the smallest b >= bin(hi) with Ts (1 - exp(-sum_{b' > b} hist)) <= budget
+    (bin(t) = floor((t - near) / D) clamped to [0, nb - 1]; no significant
+    hit: bin(lo) = nb - 1, bin(hi) = 0, Ts = 1).  With the two budgets at
+    0.4 of the threshold the check passes for these bins."""
+    H, W = cam.H, cam.W
+    lab = np.asarray(labels, np.float64).reshape(-1, 3)
+    D = (cam.far - cam.near) / nb
+    tw = (W + tsx - 1) // tsx
+    ys, xs = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+    tile = ((ys // tsy) * tw + xs // tsx).reshape(-1)
+    Ht = np.asarray(hist, np.float64)[tile]                      # [M, nb]
+    before = np.cumsum(Ht, 1) - Ht                               # sum over b' < b
+    after = Ht.sum(1, keepdims=True) - np.cumsum(Ht, 1)          # sum over b' > b
+    sig = np.isfinite(lab[:, 0])
+    b_lo = np.where(sig, np.clip(np.floor((np.where(sig, lab[:, 0], cam.near) - cam.near) / D), 0, nb - 1), nb - 1)
+    b_hi = np.where(sig, np.clip(np.floor((np.where(sig, lab[:, 1], cam.near) - cam.near) / D), 0, nb - 1), 0)
+    ok_f = (1.0 - np.exp(-before)) <= budget                      # monotone: true up to some b
+    front = np.where(ok_f.all(1), nb - 1, np.argmin(ok_f, 1) - 1)
+    bn = np.minimum(b_lo, front)
+    ok_b = lab[:, 2:3] * (1.0 - np.exp(-after)) <= budget          # monotone: true from some b on
+    bidx = np.arange(nb)[None, :]
+    cand = ok_b & (bidx >= b_hi[:, None])
+    bf = np.argmax(cand, 1)
+    return np.stack([bn, bf], 1).astype(np.int32)
+
+
+def render_interval(octree, A: np.ndarray, cam, bins=None, tau: float = TAU_DEFAULT, nb: int = PROPOSAL_BINS,
+                    wmin: float = LABEL_WMIN, eps: float = 1e-5, labels: bool = False) -> dict:
+    """Composite restricted to the interval of ``bins`` [H*W, 2] (None: the
+    whole [near, far]), its exact lost mass ``missed`` and the ambiguity flag
+    ``amb`` (a hit within ``eps`` of an interval end); with ``labels`` also
+    the plain composite's (min t1, max t0) over significant hits and the
+    transmittance after the last of them, [H, W, 3]."""
+    b = _Bound(octree, np.asarray(A).reshape(-1, 12))
+    k = _cam(cam)
+    H, W, C = cam.H, cam.W, b.feat.shape[1]
+    F = np.zeros((H, W, C))
+    Am = np.zeros((H, W))
+    missed = np.zeros((H, W))
+    amb = np.zeros((H, W), np.int32)
+    lab = np.zeros((H, W, 3)) if labels else None
+    bn = None if bins is None else np.ascontiguousarray(np.asarray(bins).reshape(-1, 2), np.int32)
+    rc = _L().orc_render_interval(ctypes.byref(b.s), ctypes.byref(k), ctypes.c_double(tau), ctypes.c_int(nb),
+                                  _p(bn), ctypes.c_double(wmin), ctypes.c_double(eps), _p(lab), _p(F), _p(Am),
+                                  _p(missed), _p(amb))
+    if rc != 0:
+        raise MemoryError("orc_render_interval failed")
+    out = dict(F=F, A=Am, missed=missed, amb=amb)
+    if labels:
+        out["labels"] = lab
+    return out
+
+
+def tau_hist(octree, A: np.ndarray, cam, tsx: int = 8, tsy: int = 4, nb: int = PROPOSAL_BINS) -> np.ndarray:
+    """Coarse optical-depth bound per (screen tile, depth bin), [tiles, nb]."""
+    b = _Bound(octree, np.asarray(A).reshape(-1, 12))
+    tw, th = (cam.W + tsx - 1) // tsx, (cam.H + tsy - 1) // tsy
+    hist = np.zeros((tw * th, nb))
+    rc = _L().orc_tau_hist(ctypes.byref(b.s), ctypes.byref(_cam(cam)), ctypes.c_int(tsx), ctypes.c_int(tsy),
+                           ctypes.c_int(nb), _p(hist))
+    if rc != 0:
+        raise MemoryError("orc_tau_hist failed")
+    return hist
+
+
+def coarse_bound(hist, bins, T_end, cam, tsx: int = 8, tsy: int = 4) -> np.ndarray:
+    """Per pixel: an upper bound of the lost mass from the tile histogram,
+    (1 - exp(-tau_front)) + T_end (1 - exp(-tau_back)), tau_front = the bins
+    before bn (all bins for an empty interval), tau_back = the bins after bf."""
+    H, W = cam.H, cam.W
+    tw = (W + tsx - 1) // tsx
+    ys, xs = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+    tile = ((ys // tsy) * tw + xs // tsx).reshape(-1)
+    bins = np.asarray(bins).reshape(-1, 2)
+    cs = np.cumsum(hist, 1)[tile]  # inclusive prefix sums of the pixel's tile
+    tot = cs[:, -1]
+    bn, bf = bins[:, 0], bins[:, 1]
+    empty = bf < bn
+    rows = np.arange(H * W)
+    front = np.where(bn > 0, cs[rows, np.maximum(bn - 1, 0)], 0.0)
+    back = tot - cs[rows, np.clip(bf, 0, hist.shape[1] - 1)]
+    front = np.where(empty, tot, front)
+    back = np.where(empty, 0.0, back)
+    T = np.asarray(T_end).reshape(-1)
+    return ((1.0 - np.exp(-front)) + T * (1.0 - np.exp(-back))).reshape(H, W)
+
+
+def skip_render(octree, A: np.ndarray, cam, bins, tau: float = TAU_DEFAULT, nb: int = PROPOSAL_BINS,
+                max_missed: float = MISSED_MAX, tsx: int = 8, tsy: int = 4) -> dict:
+    """The learned-skip render: every pixel composited over its interval; a
+    screen tile in which any pixel's coarse bound exceeds ``max_missed`` is
+    rendered again with the full traversal (the fallback)."""
+    r = render_interval(octree, A, cam, bins, tau, nb)
+    full = render_interval(octree, A, cam, None, tau, nb)
+    hist = tau_hist(octree, A, cam, tsx, tsy, nb)
+    bound = coarse_bound(hist, bins, 1.0 - r["A"], cam, tsx, tsy)
+    H, W = cam.H, cam.W
+    tw, th = (W + tsx - 1) // tsx, (H + tsy - 1) // tsy
+    pad = np.zeros((th * tsy, tw * tsx), bool)
+    pad[:H, :W] = bound > max_missed
+    fail = pad.reshape(th, tsy, tw, tsx).any((1, 3))
+    fb_px = np.repeat(np.repeat(fail, tsy, 0), tsx, 1)[:H, :W]
+    F = np.where(fb_px[..., None], full["F"], r["F"])
+    Am = np.where(fb_px, full["A"], r["A"])
+    return dict(F=F, A=Am, fallback=fail.reshape(-1), bound=bound, missed=r["missed"], amb=r["amb"],
+                restricted=r, full=full, hist=hist)

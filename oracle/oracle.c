@@ -14,6 +14,10 @@
  *     T_i = exp(-sum_{j<i} sigma_j delta_j), A = 1 - T_final,
  *     early stop once T < tau                                  (Eq. 5, Eq. 6, early-stop paragraph)
  *   - direct convolutions of the shading network              (Sec. 3.1, "Neural Shading")
+ *   - the learned ray-interval proposal's labels, the composite restricted to
+ *     a depth interval with the exact transmittance mass it loses, and the
+ *     coarse optical-depth bound per screen tile and depth bin (project
+ *     addition; the paper's nearest passage is the early-stop rule)
  *   - the analytic gradient of the composite with respect to features,
  *     densities and the blended transforms, and of LBS with respect to the
  *     skinning weights (project addition; the paper trains end to end).
@@ -192,6 +196,13 @@ static void cam_ray(const orc_cam* c, int x, int y, double o[3], double d[3]) {
 }
 
 void orc_pixel_ray(const orc_cam* c, int x, int y, double* o, double* d) { cam_ray(c, x, y, o, d); }
+
+/* Unit directions of every pixel's ray, d [H*W][3] (row-major pixels). */
+void orc_ray_dirs(const orc_cam* c, double* d) {
+  double o[3];
+  for (int y = 0; y < c->H; ++y)
+    for (int x = 0; x < c->W; ++x) cam_ray(c, x, y, o, d + 3 * ((size_t)y * c->W + x));
+}
 
 /*
  * Slab test of the ray (o, d) against the canonical cube [lo, lo + h]^3 after
@@ -587,6 +598,162 @@ void orc_voxel_bounds(const orc_scene* s, const orc_cam* c, double* out /*[n][7]
     out[7 * i + 6] = info[i].dmax;
   }
   free(info);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Learned ray-interval proposal (project addition; the nearest passage of  */
+/* the paper is the early-stop rule of Sec. 3.1 "Dynamic Volume Rendering"):  */
+/* labels from the plain composite, compositing restricted to an interval,  */
+/* the exact transmittance mass that the restriction loses, and a coarse    */
+/* per-(tile, depth bin) bound of the optical depth.                         */
+/* ------------------------------------------------------------------------ */
+
+/* Depth interval of the bin pair (bn, bf) over nb uniform bins of [near, far]:
+ * [near + bn D, near + (bf + 1) D], D = (far - near) / nb.  bf < bn is empty. */
+static void bin_interval(const orc_cam* c, int nb, int bn, int bf, double* lo, double* hi) {
+  double D = (c->far_ - c->near_) / nb;
+  *lo = c->near_ + bn * D;
+  *hi = c->near_ + (bf + 1) * D;
+}
+
+/* One ray, ordered hits [0, m).  Restricted set S = hits with t1 >= lo and
+ * t0 <= hi (none when empty); front P = hits with t1 < lo (all hits when
+ * empty); back Q = hits with t0 > hi.  S is composited with the stop rule of
+ * composite().  missed = (1 - exp(-tau_P)) + T_end (1 - exp(-tau_Q)), T_end the
+ * transmittance after S.  *amb is set when a hit lies within eps of the
+ * interval's ends (its membership is decided by rounding). */
+static void composite_interval(const orc_scene* s, const hit_t* hits, int m, double tau, int empty, double lo,
+                               double hi, double eps, double* F, double* Aout, double* missed, int* amb) {
+  for (int c = 0; c < s->C; ++c) F[c] = 0.0;
+  double opt = 0.0, optP = 0.0, optQ = 0.0;
+  int stopped = 0;
+  *amb = 0;
+  for (int i = 0; i < m; ++i) {
+    double sig = s->sigma[hits[i].id];
+    double delta = hits[i].t1 - hits[i].t0;
+    if (!empty && (fabs(hits[i].t1 - lo) < eps || fabs(hits[i].t0 - hi) < eps)) *amb = 1;
+    if (empty || hits[i].t1 < lo) {
+      optP += sig * delta;
+      continue;
+    }
+    if (hits[i].t0 > hi) {
+      optQ += sig * delta;
+      continue;
+    }
+    if (stopped) continue;
+    double Ti = exp(-opt);
+    double alpha = 1.0 - exp(-sig * delta);
+    const double* f = s->feat + (size_t)hits[i].id * s->C;
+    for (int c = 0; c < s->C; ++c) F[c] += Ti * alpha * f[c];
+    opt += sig * delta;
+    if (exp(-opt) < tau) stopped = 1;
+  }
+  *Aout = 1.0 - exp(-opt);
+  *missed = (1.0 - exp(-optP)) + exp(-opt) * (1.0 - exp(-optQ));
+}
+
+/*
+ * Per pixel: the label of the plain composite, and the composite restricted
+ * to the interval of bins [p][0..1] (NULL: no restriction).
+ *   labels [H*W][3] (NULL to skip): (min t1, max t0) over the composited hits
+ *     whose weight T_i alpha_i exceeds wmin, and the transmittance just after
+ *     the last of them; (+inf, -inf, 1) when there is none.
+ *   F [H*W][C], A [H*W]: restricted composite; missed [H*W]: its exact lost
+ *     mass; amb [H*W] (int32): a hit within eps of an interval end.
+ */
+int orc_render_interval(const orc_scene* s, const orc_cam* c, double tau, int nb, const int32_t* bins, double wmin,
+                        double eps, double* labels, double* F, double* Aout, double* missed, int32_t* amb) {
+  vox_info* info = all_info(s, c);
+  if (!info) return -2;
+  cand_t cand = {0, 0};
+  if (build_candidates(s, c, info, &cand) != 0) {
+    free(info);
+    return -2;
+  }
+  int64_t npx = (int64_t)c->W * c->H;
+#pragma omp parallel
+  {
+    hit_t* buf = NULL;
+    int cap = 0;
+    double* tmpF = (double*)malloc(sizeof(double) * (size_t)s->C);
+#pragma omp for schedule(dynamic, 16)
+    for (int64_t p = 0; p < npx; ++p) {
+      int x = (int)(p % c->W), y = (int)(p / c->W);
+      int m = pixel_hits(s, c, info, cand.vid + cand.off[p], cand.off[p + 1] - cand.off[p], x, y, &buf, &cap);
+      if (labels) {
+        double lo = INFINITY, hi = -INFINITY, Ts = 1.0, opt = 0.0;
+        for (int i = 0; i < m; ++i) {
+          double sig = s->sigma[buf[i].id];
+          double delta = buf[i].t1 - buf[i].t0;
+          double w = exp(-opt) * (1.0 - exp(-sig * delta));
+          opt += sig * delta;
+          if (w > wmin) {
+            if (buf[i].t1 < lo) lo = buf[i].t1;
+            if (buf[i].t0 > hi) hi = buf[i].t0;
+            Ts = exp(-opt);
+          }
+          if (exp(-opt) < tau) break;
+        }
+        labels[3 * p] = lo;
+        labels[3 * p + 1] = hi;
+        labels[3 * p + 2] = Ts;
+      }
+      double lo = c->near_, hi = c->far_;
+      int empty = 0;
+      if (bins) {
+        empty = bins[2 * p + 1] < bins[2 * p];
+        bin_interval(c, nb, bins[2 * p], bins[2 * p + 1], &lo, &hi);
+      }
+      int a = 0;
+      double ms = 0.0, Ap = 0.0;
+      composite_interval(s, buf, m, tau, empty, lo, hi, eps, F ? F + p * s->C : tmpF, &Ap, &ms, &a);
+      if (Aout) Aout[p] = Ap;
+      if (missed) missed[p] = ms;
+      if (amb) amb[p] = a;
+    }
+    free(tmpF);
+    free(buf);
+  }
+  free(cand.off);
+  free(cand.vid);
+  free(info);
+  return 0;
+}
+
+/*
+ * Coarse optical-depth bound per (screen tile, depth bin): every voxel that
+ * covers a tile (the coverage rule of orc_tile_pairs) adds sigma_i * 2 r_i,
+ * an upper bound of sigma_i delta_i for any ray (a chord of the box is at most
+ * the diameter of its bounding sphere), to each bin that its distance range
+ * [dmin, dmax] = [|c - o| - r, |c - o| + r] overlaps (bins clamped to
+ * [0, nb - 1]).  hist [tiles][nb] is overwritten.
+ */
+int orc_tau_hist(const orc_scene* s, const orc_cam* c, int tsx, int tsy, int nb, double* hist) {
+  vox_info* info = all_info(s, c);
+  if (!info) return -2;
+  int tw = (c->W + tsx - 1) / tsx, th = (c->H + tsy - 1) / tsy;
+  memset(hist, 0, sizeof(double) * (size_t)tw * th * nb);
+  double D = (c->far_ - c->near_) / nb;
+  for (int64_t i = 0; i < s->n; ++i) {
+    const vox_info* v = info + i;
+    if (!v->ok || v->dmin > c->far_ || v->dmax < c->near_) continue;
+    int x0 = (int)ceil(v->umin - 0.5), x1 = (int)floor(v->umax - 0.5);
+    int y0 = (int)ceil(v->vmin - 0.5), y1 = (int)floor(v->vmax - 0.5);
+    if (x0 < 0) x0 = 0;
+    if (y0 < 0) y0 = 0;
+    if (x1 > c->W - 1) x1 = c->W - 1;
+    if (y1 > c->H - 1) y1 = c->H - 1;
+    if (x0 > x1 || y0 > y1) continue;
+    double taub = s->sigma[i] * (v->dmax - v->dmin);
+    int b0 = (int)floor((v->dmin - c->near_) / D), b1 = (int)floor((v->dmax - c->near_) / D);
+    if (b0 < 0) b0 = 0;
+    if (b1 > nb - 1) b1 = nb - 1;
+    for (int ty = y0 / tsy; ty <= y1 / tsy; ++ty)
+      for (int tx = x0 / tsx; tx <= x1 / tsx; ++tx)
+        for (int b = b0; b <= b1; ++b) hist[((size_t)ty * tw + tx) * nb + b] += taub;
+  }
+  free(info);
+  return 0;
 }
 
 /* ------------------------------------------------------------------------ */

@@ -647,3 +647,182 @@ def test_wrapper_keeps_converted_inputs_alive():
                                                       gN.astype(np.float64))[1])
     np.testing.assert_array_equal(oracle.rodrigues(np.float32([0.1, 0.2, 0.3])),
                                   oracle.rodrigues(np.float32([0.1, 0.2, 0.3]).astype(np.float64)))
+
+
+# ---------------------------------------------------------------------------
+# learned ray-interval proposal (project addition; the paper's nearest
+# passage is the early-stop rule of Sec. 3.1)
+# ---------------------------------------------------------------------------
+
+def _proposal_scene(seed=3):
+    sc = sg.preset("tiny")
+    cam = sg.orbit_camera(sc.centroid, 96, 64, az_deg=30.0, fov_deg=6.0)  # the animal fills the view
+    G, A, _ = oracle.pose_transforms(sc, sg.random_pose(seed))
+    return sc, cam, A
+
+
+def test_proposal_inputs_closed_form():
+    """Pixel (0, 0) of a 2 x 4 image: u = 1/4, v = 1/8; the Fourier features
+    take the values of sin / cos at multiples of pi/4 and pi/8."""
+    cam = sg.orbit_camera(np.zeros(3), 2, 4)
+    aa = np.arange(72, dtype=np.float64).reshape(24, 3) * 0.01
+    x = oracle.proposal_inputs(aa, cam)
+    assert x.shape == (8, 107)
+    np.testing.assert_array_equal(x[:, :72], np.broadcast_to(aa.reshape(-1), (8, 72)))
+    _, d = oracle.pixel_ray(cam, 1, 2)
+    np.testing.assert_allclose(x[2 * 2 + 1, 72:75], d, atol=1e-15)
+    r = math.sqrt(0.5)
+    sin_u = [r, 1, 0, 0, 0, 0, 0, 0]
+    cos_u = [r, 0, -1, 1, 1, 1, 1, 1]
+    s8, c8 = math.sin(math.pi / 8), math.cos(math.pi / 8)
+    sin_v = [s8, r, 1, 0, 0, 0, 0, 0]
+    cos_v = [c8, r, 0, -1, 1, 1, 1, 1]
+    np.testing.assert_allclose(x[0, 75:107], sin_u + cos_u + sin_v + cos_v, atol=1e-12)
+
+
+def test_proposal_mlp_selector_network():
+    """Weights that route input 106 - i to hidden unit i (a transposed or
+    shifted weight layout picks other inputs), identity hidden layers, and an
+    output layer giving +h and 2h + bias on the two halves."""
+    layers = []
+    W0 = np.zeros((64, 107))
+    W0[np.arange(64), 106 - np.arange(64)] = 1.0
+    b0 = np.zeros(64)
+    layers += [W0, b0]
+    for _ in range(3):
+        layers += [np.eye(64), np.zeros(64)]
+    W4 = np.concatenate([np.eye(64), 2 * np.eye(64)])
+    b4 = np.concatenate([np.zeros(64), np.arange(64) * 0.5])
+    layers += [W4, b4]
+    params = np.concatenate([a.reshape(-1) for a in layers])
+    assert params.size == oracle.PROPOSAL_PARAMS
+    rng = np.random.default_rng(0)
+    x = rng.uniform(0.1, 1.0, (5, 107))
+    lg = oracle.proposal_mlp(x, params)
+    h = x[:, 106 - np.arange(64)]
+    np.testing.assert_allclose(lg[:, :64], h, atol=1e-15)
+    np.testing.assert_allclose(lg[:, 64:], 2 * h + np.arange(64) * 0.5, atol=1e-15)
+    # ReLU clips negative routed inputs
+    lg2 = oracle.proposal_mlp(-x, params)
+    np.testing.assert_allclose(lg2[:, :64], 0.0)
+
+
+def test_proposal_bins_first_argmax_and_interval():
+    lg = np.zeros((3, 128))
+    lg[0, [5, 9]] = 1.0         # tie: first index
+    lg[0, 64 + 20] = 3.0
+    lg[1, 63] = 1.0
+    lg[1, 64 + 0] = 1.0         # bf < bn: empty
+    b = oracle.proposal_bins(lg)
+    np.testing.assert_array_equal(b, [[5, 20], [63, 0], [0, 0]])
+
+
+def test_round_bf16_ties_to_even_and_matches_torch():
+    torch = pytest.importorskip("torch")
+    one = 1.0
+    assert oracle.round_bf16(one + 2.0 ** -8) == 1.0                      # tie -> even (1.0)
+    assert oracle.round_bf16(one + 3 * 2.0 ** -8) == 1.0 + 2.0 ** -6      # tie -> even (odd neighbour up)
+    assert oracle.round_bf16(one + 2.0 ** -8 + 2.0 ** -12) == 1.0 + 2.0 ** -7
+    x = np.random.default_rng(1).standard_normal(10000) * 10.0 ** np.random.default_rng(2).integers(-6, 6, 10000)
+    ref = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).double().numpy()
+    np.testing.assert_array_equal(oracle.round_bf16(x), ref)
+
+
+def test_render_interval_whole_range_is_plain_render():
+    sc, cam, A = _proposal_scene()
+    f = oracle.render(sc.octree, A, cam)
+    for bins in (None, np.tile([0, oracle.PROPOSAL_BINS - 1], (cam.H * cam.W, 1))):
+        r = oracle.render_interval(sc.octree, A, cam, bins)
+        np.testing.assert_array_equal(r["F"], f["F"])
+        np.testing.assert_array_equal(r["A"], f["A"])
+        assert r["missed"].max() == 0.0
+
+
+def test_render_interval_empty_loses_all_mass():
+    """An empty interval composites nothing and loses 1 - exp(-sum of
+    sigma delta over all of the ray's hits) (brute force over the hit lists)."""
+    sc, cam, A = _proposal_scene()
+    full = oracle.render(sc.octree, A, cam, hits=True, tau=0.0)
+    bins = np.tile([1, 0], (cam.H * cam.W, 1))
+    r = oracle.render_interval(sc.octree, A, cam, bins)
+    assert np.abs(r["F"]).max() == 0.0 and np.abs(r["A"]).max() == 0.0
+    sig = sc.octree.density.astype(np.float64)
+    off = full["hit_off"]
+    tau_all = np.array([np.sum(sig[full["hit_id"][off[p]:off[p + 1]]] *
+                               (full["hit_t1"][off[p]:off[p + 1]] - full["hit_t0"][off[p]:off[p + 1]]))
+                        for p in range(cam.H * cam.W)])
+    np.testing.assert_allclose(r["missed"].reshape(-1), 1.0 - np.exp(-tau_all), atol=1e-14)
+    assert tau_all.max() > 0.05
+
+
+def test_render_interval_error_within_missed_mass():
+    """For random intervals the restricted feature map differs from the full
+    one by at most (2 m_P + T_end m_Q) max|f| <= 2 missed max|f| (plus the
+    early-stop slack tau), the bound the coarse check relies on; and the tile
+    histogram bound dominates the exact lost mass."""
+    sc, cam, A = _proposal_scene()
+    rng = np.random.default_rng(5)
+    bn = rng.integers(0, 64, cam.H * cam.W)
+    bf = np.minimum(63, bn + rng.integers(-1, 6, cam.H * cam.W))
+    bins = np.stack([bn, bf], 1)
+    f = oracle.render(sc.octree, A, cam)
+    r = oracle.render_interval(sc.octree, A, cam, bins)
+    fmax = np.abs(sc.octree.features).max()
+    err = np.abs(r["F"] - f["F"]).max(-1)
+    assert np.all(err <= (2 * r["missed"] + 2 * oracle.TAU_DEFAULT) * fmax + 1e-12)
+    assert (r["missed"] > 1e-3).mean() > 0.005  # the draw does skip mass somewhere
+    hist = oracle.tau_hist(sc.octree, A, cam)
+    bound = oracle.coarse_bound(hist, bins, 1.0 - r["A"], cam)
+    assert np.all(bound >= r["missed"] - 1e-12)
+
+
+def test_tau_hist_brute_force():
+    """Each voxel adds sigma (dmax - dmin) to the bins its distance range
+    overlaps, in every tile whose pixel centres its box covers."""
+    sc, cam, A = _proposal_scene()
+    hist = oracle.tau_hist(sc.octree, A, cam, 8, 4)
+    vb = oracle.voxel_bounds(sc.octree, A, cam)
+    tile, vid = oracle.tile_pairs(sc.octree, A, cam, 8, 4)
+    D = (cam.far - cam.near) / 64
+    ref = np.zeros_like(hist)
+    for t, i in zip(tile, vid):
+        b0 = int(np.clip(np.floor((vb[i, 5] - cam.near) / D), 0, 63))
+        b1 = int(np.clip(np.floor((vb[i, 6] - cam.near) / D), 0, 63))
+        ref[t, b0:b1 + 1] += sc.octree.density[i] * (vb[i, 6] - vb[i, 5])
+    np.testing.assert_allclose(hist, ref, rtol=1e-12, atol=1e-15)
+
+
+def test_labels_brute_force_and_label_bins_pass_check():
+    """Labels (min t1, max t0 over hits with weight > 1e-6, transmittance
+    after the last) recomputed from the ordered hit lists; the label bins
+    keep every significant hit, pass the coarse check in every tile, and the
+    learned-skip render with them equals the plain render within the
+    lost-mass bound."""
+    sc, cam, A = _proposal_scene()
+    full = oracle.render(sc.octree, A, cam, hits=True)
+    r = oracle.render_interval(sc.octree, A, cam, None, labels=True)
+    lab = r["labels"].reshape(-1, 3)
+    sig = sc.octree.density.astype(np.float64)
+    off = full["hit_off"]
+    for p in range(cam.H * cam.W):
+        lo, hi, Ts, opt = np.inf, -np.inf, 1.0, 0.0
+        for k in range(off[p], off[p + 1]):
+            i, t0, t1 = full["hit_id"][k], full["hit_t0"][k], full["hit_t1"][k]
+            w = math.exp(-opt) * (1.0 - math.exp(-sig[i] * (t1 - t0)))
+            opt += sig[i] * (t1 - t0)
+            if w > oracle.LABEL_WMIN:
+                lo, hi, Ts = min(lo, t1), max(hi, t0), math.exp(-opt)
+            if math.exp(-opt) < oracle.TAU_DEFAULT:
+                break
+        np.testing.assert_allclose(lab[p], [lo, hi, Ts], rtol=0, atol=1e-14)
+    hist = oracle.tau_hist(sc.octree, A, cam)
+    bins = oracle.label_bins(r["labels"], hist, cam)
+    D = (cam.far - cam.near) / 64
+    has = np.isfinite(lab[:, 0])
+    assert has.sum() > 100
+    assert np.all(cam.near + bins[has, 0] * D <= lab[has, 0])
+    assert np.all(cam.near + (bins[has, 1] + 1) * D > lab[has, 1])
+    s = oracle.skip_render(sc.octree, A, cam, bins)
+    assert not s["fallback"].any() and s["bound"].max() <= oracle.MISSED_MAX
+    fmax = np.abs(sc.octree.features).max()
+    assert np.abs(s["F"] - full["F"]).max() <= 2 * oracle.MISSED_MAX * fmax
