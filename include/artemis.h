@@ -214,6 +214,63 @@ art_status art_shade(art_ctx* ctx, int view, const void* F, int F_dtype, float* 
 art_status art_render_frame(art_ctx* ctx, int view, const float* axis_angle, const float R[3], const float T[3],
                             float* rgba_out);
 
+/* ------------------------------------------- learned ray-interval proposal */
+
+/*
+ * A small MLP that predicts, per camera ray, the depth interval in which the
+ * ray's composite takes its mass, so that compositing can skip the rest
+ * (project addition; the paper's nearest passage is the early-stop rule of
+ * Sec. 3.1 "Dynamic Volume Rendering").
+ *   input x (107) = [the 72 joint axis-angles of the current pose (J = 24),
+ *     the unit world direction of the ray, sin(2^k pi u), k < 8, cos(2^k pi u),
+ *     sin(2^k pi v), cos(2^k pi v)], u = (x + 1/2) / W, v = (y + 1/2) / H
+ *   layers 107 -> 64 -> 64 -> 64 -> 64 (ReLU) -> 128 logits, BF16 operands,
+ *     FP32 accumulation (tensor cores), FP32 biases
+ *   bins bn = argmax logits[0:64], bf = argmax logits[64:128] (first index on
+ *     ties) over 64 uniform bins of [znear, zfar] of the view: the interval
+ *     [znear + bn D, znear + (bf + 1) D], D = (zfar - znear) / 64; bf < bn is
+ *     empty.  Each 8 x 4 screen tile takes the union of its rays' non-empty
+ *     intervals (bins min bn .. max bf, widened by config.margin; empty when
+ *     all are empty), and its rays composite the hits with t1 >= the lower end
+ *     and t0 <= the upper end, in the plain order with the plain stop rule.
+ * Coarse check: each voxel adds sigma_i 2 r_i (a bound of its optical depth on
+ * any ray) to every depth bin its distance range |c_i - o| -+ r_i overlaps, in
+ * every screen tile it covers.  A ray's lost mass is bounded by (1 - exp(-sum
+ * of its tile's bins before bn)) + T_end (1 - exp(-sum after bf)) (empty: the
+ * first term over all bins), T_end its transmittance after the interval; if
+ * the bound of any ray of an 8 x 4 tile exceeds config.max_missed, the whole
+ * tile is composited again without the interval (the fallback).
+ */
+
+#define ART_PROPOSAL_PARAMS 27712 /* 64*107+64 + 3*(64*64+64) + 128*64+128 */
+
+/* Load the proposal MLP: params (FP32, host or device) = W0 [64][107], b0,
+ * W1 [64][64], b1, W2, b2, W3, b3, W4 [128][64], b4 (y = W x + b);
+ * n_params must be ART_PROPOSAL_PARAMS.  The skeleton must have 24 joints. */
+art_status art_load_proposal(art_ctx* ctx, const float* params, int64_t n_params);
+
+/*
+ * Run the proposal for every pixel of `view` under the current pose:
+ * bins_out [H][W][2] uint8 (bn, bf) and/or logits_out [H][W][128] float;
+ * DEVICE arrays, either may be NULL.
+ */
+art_status art_run_proposal(art_ctx* ctx, int view, uint8_t* bins_out, float* logits_out);
+
+/*
+ * Training labels from the plain renderer, for the current pose and `view`:
+ *   labels_out [H][W][3] float: (min t1, max t0) over the composited hits whose
+ *     weight T_i alpha_i exceeds 1e-6, and the transmittance just after the
+ *     last of them; (+inf, -inf, 1) when there is none
+ *   bins_out [H][W][2] uint8: the label interval (bn, bf) with
+ *     bn = min(bin(lo), the largest b with 1 - exp(-sum of the tile's bins
+ *     before b) <= 0.4 max_missed), bf = the smallest b >= bin(hi) with
+ *     Ts (1 - exp(-sum after b)) <= 0.4 max_missed (no significant hit:
+ *     bin(lo) = 63, bin(hi) = 0, Ts = 1): it keeps every significant hit and
+ *     passes the coarse check
+ * DEVICE arrays, either may be NULL.  F and A are not written.
+ */
+art_status art_render_labels(art_ctx* ctx, int view, float* labels_out, uint8_t* bins_out);
+
 /* ------------------------------------------------------------ configuration */
 
 typedef struct {
@@ -221,7 +278,15 @@ typedef struct {
   int64_t instance_cap;    /* capacity of (tile, voxel) instances; 0 = 4 n + 65536 */
   int tile_log2;           /* log2 of the screen-tile width: 3 (8 x 4 pixel tiles, the only size built) */
   int profile;             /* 1: time every kernel with CUDA events (art_get_kernel_times) */
+  int skip;                /* ART_SKIP_PLAIN (default) or ART_SKIP_LEARNED: composite each ray only
+                              over the depth interval its proposal predicts (art_load_proposal) */
+  float max_missed;        /* learned skip: coarse-check threshold of lost transmittance mass
+                              (0 = default 1e-3); a tile with a ray above it is traversed again in full */
+  int margin;              /* learned skip: bins added on both sides of the predicted interval (default 0) */
 } art_config;
+
+#define ART_SKIP_PLAIN 0
+#define ART_SKIP_LEARNED 1
 
 /* Replace the configuration (NULL restores the defaults). */
 art_status art_set_config(art_ctx* ctx, const art_config* cfg);
@@ -233,6 +298,7 @@ typedef struct {
   int64_t overflow_order;  /* pixel hits released early because the per-pixel
                               reorder buffer was full (result may be out of order) */
   int64_t kernel_launches; /* kernels launched by this context so far */
+  int64_t fallback_tiles;  /* learned skip: tiles of the last render traversed again in full */
 } art_stats;
 
 /* Synchronise the stream, fill *out (may be NULL) and return
@@ -302,10 +368,15 @@ enum {
   ART_BUF_VALS = 6,      /* [instances] uint32 voxel ids in key order */
   ART_BUF_RANGES = 7,    /* [tiles][2] uint32 [start, end) of each tile */
   ART_BUF_FP8_SCALES = 8, /* [11] float: FP8 network activation scales used by the next call */
-  ART_BUF_ACTIVATIONS = 9 /* bytes of the tensor-core U-Net's activation arena after the last art_shade:
+  ART_BUF_ACTIVATIONS = 9, /* bytes of the tensor-core U-Net's activation arena after the last art_shade:
                              NHWC tensors, each padded to 256 bytes.  FP8: E4M3 codes of input, e0a,
                              cat0, p0, e1a, cat1, p1, e2a, cat2, p2, e3a, d2a, d1a, d0a; BF16: the same
                              tensors without the input.  cat = [upsampled decoder | encoder] */
+  ART_BUF_BINS = 10,      /* [H][W][2] uint8: proposal bins of the last learned-skip render (tiles
+                             without instances are not predicted) */
+  ART_BUF_FALLBACK = 11,  /* [fallback_tiles] uint32: tiles of the last learned-skip render traversed again */
+  ART_BUF_TAU_HIST = 12   /* [tiles][64] float: coarse optical-depth bound per (tile, depth bin) of the
+                             last learned-skip or label render */
 };
 
 /*

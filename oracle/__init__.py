@@ -20,7 +20,7 @@ convolution primitives.  Every function follows a passage of the paper
   Eq. 4 (the paper optimises the feature table end to end).
 * :func:`proposal_inputs`, :func:`proposal_mlp`, :func:`proposal_bins`,
   :func:`render_interval`, :func:`tau_hist`, :func:`coarse_bound`,
-  :func:`skip_render` - the learned ray-interval proposal that lets the
+  :func:`tile_union_bins`, :func:`skip_render` - the learned ray-interval proposal that lets the
   composite skip empty depth (project addition; the paper's nearest passage
   is the early-stop rule of Sec. 3.1).
 
@@ -576,11 +576,35 @@ def coarse_bound(hist, bins, T_end, cam, tsx: int = 8, tsy: int = 4) -> np.ndarr
     return ((1.0 - np.exp(-front)) + T * (1.0 - np.exp(-back))).reshape(H, W)
 
 
+def tile_union_bins(bins, cam, margin: int = 0, tsx: int = 8, tsy: int = 4, nb: int = PROPOSAL_BINS) -> np.ndarray:
+    """Per pixel, the interval its screen tile composites over: the union of
+    the tile's non-empty pixel intervals (min bn .. max bf), widened by
+    ``margin`` bins and clamped; empty (nb, -1) when every pixel's is empty.
+    [H*W, 2] int32."""
+    H, W = cam.H, cam.W
+    tw, th = (W + tsx - 1) // tsx, (H + tsy - 1) // tsy
+    b = np.asarray(bins).reshape(H, W, 2).astype(np.int64)
+    ne = b[..., 1] >= b[..., 0]
+    lo = np.full((th * tsy, tw * tsx), nb, np.int64)
+    hi = np.full((th * tsy, tw * tsx), -1, np.int64)
+    lo[:H, :W] = np.where(ne, b[..., 0], nb)
+    hi[:H, :W] = np.where(ne, b[..., 1], -1)
+    lo_t = lo.reshape(th, tsy, tw, tsx).min((1, 3))
+    hi_t = hi.reshape(th, tsy, tw, tsx).max((1, 3))
+    empty = hi_t < lo_t
+    lo_t = np.where(empty, nb, np.maximum(lo_t - margin, 0))
+    hi_t = np.where(empty, -1, np.minimum(hi_t + margin, nb - 1))
+    up = lambda t: np.repeat(np.repeat(t, tsy, 0), tsx, 1)[:H, :W]
+    return np.stack([up(lo_t), up(hi_t)], -1).reshape(-1, 2).astype(np.int32)
+
+
 def skip_render(octree, A: np.ndarray, cam, bins, tau: float = TAU_DEFAULT, nb: int = PROPOSAL_BINS,
-                max_missed: float = MISSED_MAX, tsx: int = 8, tsy: int = 4) -> dict:
-    """The learned-skip render: every pixel composited over its interval; a
-    screen tile in which any pixel's coarse bound exceeds ``max_missed`` is
-    rendered again with the full traversal (the fallback)."""
+                max_missed: float = MISSED_MAX, margin: int = 0, tsx: int = 8, tsy: int = 4) -> dict:
+    """The learned-skip render: every screen tile composited over the union
+    of its pixels' predicted intervals (:func:`tile_union_bins`); a tile in
+    which any pixel's coarse bound exceeds ``max_missed`` is rendered again
+    with the full traversal (the fallback)."""
+    bins = tile_union_bins(bins, cam, margin, tsx, tsy, nb)
     r = render_interval(octree, A, cam, bins, tau, nb)
     full = render_interval(octree, A, cam, None, tau, nb)
     hist = tau_hist(octree, A, cam, tsx, tsy, nb)
@@ -594,4 +618,4 @@ def skip_render(octree, A: np.ndarray, cam, bins, tau: float = TAU_DEFAULT, nb: 
     F = np.where(fb_px[..., None], full["F"], r["F"])
     Am = np.where(fb_px, full["A"], r["A"])
     return dict(F=F, A=Am, fallback=fail.reshape(-1), bound=bound, missed=r["missed"], amb=r["amb"],
-                restricted=r, full=full, hist=hist)
+                restricted=r, full=full, hist=hist, bins=bins)

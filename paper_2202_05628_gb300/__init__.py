@@ -19,7 +19,10 @@ LIB_PATH = os.path.join(_HERE, "libartemis_gb.so")
 
 ART_F32, ART_BF16, ART_F16, ART_FP8 = 0, 1, 2, 3
 ART_NET_TINY, ART_NET_UNET = 0, 1
-BUF_JOINT_G, BUF_VOXEL_REC, BUF_VOXEL_GEO, BUF_RECT, BUF_DEPTHKEY, BUF_KEYS, BUF_VALS, BUF_RANGES, BUF_FP8_SCALES, BUF_ACTIVATIONS = range(10)
+(BUF_JOINT_G, BUF_VOXEL_REC, BUF_VOXEL_GEO, BUF_RECT, BUF_DEPTHKEY, BUF_KEYS, BUF_VALS, BUF_RANGES, BUF_FP8_SCALES,
+ BUF_ACTIVATIONS, BUF_BINS, BUF_FALLBACK, BUF_TAU_HIST) = range(13)
+SKIP_PLAIN, SKIP_LEARNED = 0, 1
+PROPOSAL_PARAMS = 27712  # 64*107+64 + 3*(64*64+64) + 128*64+128
 _STATUS = {0: "ART_OK", 1: "ART_ERR_INVALID_ARG", 2: "ART_ERR_CUDA", 3: "ART_ERR_OOM", 4: "ART_ERR_OVERFLOW",
            5: "ART_ERR_STATE", 6: "ART_ERR_UNSUPPORTED"}
 DTYPES = {"f32": ART_F32, "bf16": ART_BF16, "f16": ART_F16, "fp8": ART_FP8}
@@ -37,12 +40,14 @@ class NetDesc(ctypes.Structure):
 
 class Config(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_float), ("instance_cap", ctypes.c_int64), ("tile_log2", ctypes.c_int),
-                ("profile", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("skip", ctypes.c_int), ("max_missed", ctypes.c_float),
+                ("margin", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [("instances", ctypes.c_int64), ("degenerate", ctypes.c_int64), ("overflow_inst", ctypes.c_int64),
-                ("overflow_order", ctypes.c_int64), ("kernel_launches", ctypes.c_int64)]
+                ("overflow_order", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
+                ("fallback_tiles", ctypes.c_int64)]
 
 
 def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -71,6 +76,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "art_render_backward": [vp, i32, vp, vp, vp, vp, vp, vp, vp],
         "art_debug_buffer": [vp, i32, vp, i64, ctypes.POINTER(i64)],
         "art_debug_hits": [vp, i32, i32, vp, vp, vp, vp, vp, vp],
+        "art_load_proposal": [vp, vp, i64],
+        "art_run_proposal": [vp, i32, vp, vp],
+        "art_render_labels": [vp, i32, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -136,8 +144,9 @@ class Renderer:
             raise ArtemisError(st, _lib.art_last_error(self._h).decode())
 
     # ----------------------------------------------------------------- setup
-    def set_config(self, tau: float = 1e-4, instance_cap: int = 0, tile_log2: int = 3, profile: bool = False):
-        c = Config(tau, instance_cap, tile_log2, int(profile))
+    def set_config(self, tau: float = 1e-4, instance_cap: int = 0, tile_log2: int = 3, profile: bool = False,
+                   skip: int = SKIP_PLAIN, max_missed: float = 1e-3, margin: int = 0):
+        c = Config(tau, instance_cap, tile_log2, int(profile), int(skip), float(max_missed), int(margin))
         self._check(_lib.art_set_config(self._h, ctypes.byref(c)))
 
     def load_octree(self, depth: int, origin, extent: float, ijk, joint_idx, weights, features, density,
@@ -194,6 +203,20 @@ class Renderer:
         self._check(_lib.art_render_backward(self._h, view, _ptr(F), _ptr(A), _ptr(dF), _ptr(dA), _ptr(d_features),
                                              _ptr(d_density), _ptr(d_weights)))
 
+    # ------------------------------------------------ learned interval skip
+    def load_proposal(self, params):
+        """Load the ray-interval proposal MLP (flat FP32, PROPOSAL_PARAMS values)."""
+        p = params if hasattr(params, "data_ptr") else _np(params, np.float32).reshape(-1)
+        self._check(_lib.art_load_proposal(self._h, _ptr(p), int(p.numel() if hasattr(p, "numel") else p.size)))
+
+    def run_proposal(self, view: int, bins=None, logits=None):
+        """Proposal bins [H,W,2] uint8 and/or logits [H,W,128] float (device tensors)."""
+        self._check(_lib.art_run_proposal(self._h, view, _ptr(bins), _ptr(logits)))
+
+    def render_labels(self, view: int, labels=None, bins=None):
+        """Plain-render training labels [H,W,3] float and label bins [H,W,2] uint8 (device tensors)."""
+        self._check(_lib.art_render_labels(self._h, view, _ptr(labels), _ptr(bins)))
+
     def sort_pairs(self, keys, vals, key_bits: int = 32):
         self._check(_lib.art_sort_pairs(self._h, _ptr(keys), _ptr(vals), int(keys.numel()), key_bits))
 
@@ -204,7 +227,8 @@ class Renderer:
         if st != 0 and (raise_on_overflow or st != 4):
             self._check(st)
         return dict(instances=s.instances, degenerate=s.degenerate, overflow_inst=s.overflow_inst,
-                    overflow_order=s.overflow_order, kernel_launches=s.kernel_launches, status=st)
+                    overflow_order=s.overflow_order, kernel_launches=s.kernel_launches,
+                    fallback_tiles=s.fallback_tiles, status=st)
 
     def kernel_times(self, reset: bool = False) -> dict:
         cap = 64

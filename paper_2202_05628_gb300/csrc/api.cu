@@ -171,7 +171,8 @@ void free_all(art_ctx* ctx) {
                   ctx->d_rec, ctx->d_geo, ctx->d_rect, ctx->d_q, ctx->d_cnt, ctx->d_off, ctx->d_bsum,
                   ctx->d_keys[0], ctx->d_keys[1], ctx->d_vals[0], ctx->d_vals[1], ctx->d_hist, ctx->d_ranges,
                   ctx->d_status, ctx->d_F, ctx->d_A, ctx->d_rgba, ctx->d_act, ctx->d_sk, ctx->d_sv,
-                  ctx->d_shist, ctx->d_sbsum, ctx->d_gN, ctx->d_f8_scale, ctx->d_f8_amax};
+                  ctx->d_shist, ctx->d_sbsum, ctx->d_gN, ctx->d_f8_scale, ctx->d_f8_amax, ctx->d_prop_img,
+                  ctx->d_prop_f32, ctx->d_pose_bias, ctx->d_bins, ctx->d_thist, ctx->d_hbin, ctx->d_htau, ctx->d_fbq};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& L : ctx->layers) {
@@ -195,6 +196,9 @@ art_config default_config() {
   c.instance_cap = 0;
   c.tile_log2 = 3;
   c.profile = 0;
+  c.skip = ART_SKIP_PLAIN;
+  c.max_missed = 1e-3f;
+  c.margin = 0;
   return c;
 }
 
@@ -219,6 +223,26 @@ art_status ensure_bin_buffers(art_ctx* ctx, int64_t ntiles) {
     if (st != ART_OK) return st;
     ctx->ranges_cap = ntiles;
   }
+  return ART_OK;
+}
+
+// Buffers of the coarse check (per-voxel bins and bounds, per-tile histogram,
+// fallback queue) and of the proposal bins, for `view`; the histogram is
+// zeroed on the stream.
+art_status ensure_skip_buffers(art_ctx* ctx, const ViewParams& v) {
+  art_status st;
+  if (ctx->hist_n_cap < ctx->n) {
+    if ((st = alloc(ctx, &ctx->d_hbin, (size_t)ctx->n, "voxel depth bins")) != ART_OK) return st;
+    if ((st = alloc(ctx, &ctx->d_htau, (size_t)ctx->n, "voxel optical-depth bounds")) != ART_OK) return st;
+    ctx->hist_n_cap = ctx->n;
+  }
+  const size_t ntiles = (size_t)v.tiles_x * v.tiles_y;
+  if ((st = ensure(ctx, (void**)&ctx->d_thist, &ctx->d_thist_bytes, ntiles * kPropBins * 4, "tile histogram")) != ART_OK)
+    return st;
+  if ((st = ensure(ctx, (void**)&ctx->d_fbq, &ctx->d_fbq_bytes, ntiles * 4, "fallback queue")) != ART_OK) return st;
+  if ((st = ensure(ctx, (void**)&ctx->d_bins, &ctx->d_bins_bytes, (size_t)v.W * v.H * 2, "proposal bins")) != ART_OK)
+    return st;
+  cudaMemsetAsync(ctx->d_thist, 0, ntiles * kPropBins * 4, ctx->stream);
   return ART_OK;
 }
 
@@ -279,6 +303,10 @@ art_status art_set_config(art_ctx* ctx, const art_config* cfg) {
   if (c.tile_log2 == 0) c.tile_log2 = 3;
   if (c.tile_log2 != 3) return fail(ctx, ART_ERR_UNSUPPORTED, "tile_log2 must be 3 (8x4 tiles)");
   if (c.instance_cap < 0) return fail(ctx, ART_ERR_INVALID_ARG, "instance_cap must be >= 0");
+  if (c.skip != ART_SKIP_PLAIN && c.skip != ART_SKIP_LEARNED) return fail(ctx, ART_ERR_INVALID_ARG, "skip mode %d", c.skip);
+  if (c.max_missed == 0.0f) c.max_missed = 1e-3f;
+  if (!(c.max_missed > 0.0f && c.max_missed < 1.0f)) return fail(ctx, ART_ERR_INVALID_ARG, "max_missed must be in (0, 1)");
+  if (c.margin < 0 || c.margin > 63) return fail(ctx, ART_ERR_INVALID_ARG, "margin must be in [0, 63]");
   ctx->cfg = c;
   return ART_OK;
 }
@@ -408,9 +436,53 @@ art_status art_set_pose(art_ctx* ctx, const float* axis_angle, const float R[3],
   cudaMemsetAsync(ctx->d_status + kStDegenerate, 0, sizeof(unsigned long long), ctx->stream);
   launch_fk(ctx);
   launch_lbs(ctx);
+  if (ctx->prop_loaded) launch_pose_bias(ctx);
   if ((st = launch_check(ctx, "set_pose")) != ART_OK) return st;
   ctx->posed = true;
   return ART_OK;
+}
+
+art_status art_load_proposal(art_ctx* ctx, const float* params, int64_t n_params) {
+  if (!ctx) return ART_ERR_INVALID_ARG;
+  if (!params) return fail(ctx, ART_ERR_INVALID_ARG, "null proposal params");
+  if (n_params != ART_PROPOSAL_PARAMS)
+    return fail(ctx, ART_ERR_INVALID_ARG, "proposal params: %lld given, %d expected", (long long)n_params,
+                ART_PROPOSAL_PARAMS);
+  if (ctx->J != 24) return fail(ctx, ART_ERR_STATE, "the proposal takes a 24-joint pose (load_skeleton first)");
+  art_status st = load_proposal(ctx, params);
+  if (st != ART_OK) return st;
+  if (ctx->posed) launch_pose_bias(ctx);
+  return launch_check(ctx, "load_proposal");
+}
+
+art_status art_run_proposal(art_ctx* ctx, int view, uint8_t* bins_out, float* logits_out) {
+  if (!ctx) return ART_ERR_INVALID_ARG;
+  if (view < 0 || view >= kMaxViews || !ctx->view_set[view]) return fail(ctx, ART_ERR_STATE, "view %d not set", view);
+  if (!ctx->posed) return fail(ctx, ART_ERR_STATE, "run_proposal before set_pose");
+  if (!ctx->prop_loaded) return fail(ctx, ART_ERR_STATE, "run_proposal before load_proposal");
+  if ((bins_out && !is_device_ptr(bins_out)) || (logits_out && !is_device_ptr(logits_out)))
+    return fail(ctx, ART_ERR_INVALID_ARG, "run_proposal writes device arrays");
+  art_status st = launch_proposal(ctx, ctx->views[view], bins_out, logits_out, false);
+  if (st != ART_OK) return st;
+  return launch_check(ctx, "run_proposal");
+}
+
+art_status art_render_labels(art_ctx* ctx, int view, float* labels_out, uint8_t* bins_out) {
+  if (!ctx) return ART_ERR_INVALID_ARG;
+  if (view < 0 || view >= kMaxViews || !ctx->view_set[view]) return fail(ctx, ART_ERR_STATE, "view %d not set", view);
+  if (!ctx->posed) return fail(ctx, ART_ERR_STATE, "render_labels before set_pose");
+  if ((labels_out && !is_device_ptr(labels_out)) || (bins_out && !is_device_ptr(bins_out)))
+    return fail(ctx, ART_ERR_INVALID_ARG, "render_labels writes device arrays");
+  const ViewParams& v = ctx->views[view];
+  art_status st = ensure_bin_buffers(ctx, (int64_t)v.tiles_x * v.tiles_y);
+  if (st != ART_OK) return st;
+  if ((st = ensure_skip_buffers(ctx, v)) != ART_OK) return st;
+  launch_project(ctx, v, ctx->d_hbin, ctx->d_htau);
+  launch_scan_emit(ctx, v, ctx->d_hbin, ctx->d_htau, ctx->d_thist);
+  launch_sort(ctx, 32);
+  launch_ranges(ctx, v);
+  if ((st = launch_composite_labels(ctx, v, labels_out, bins_out)) != ART_OK) return st;
+  return launch_check(ctx, "render_labels");
 }
 
 art_status art_set_camera(art_ctx* ctx, int view, int W, int H, float fx, float fy, float cx, float cy,
@@ -463,6 +535,17 @@ static art_status render_to_device(art_ctx* ctx, int view, void* F, int F_dtype,
   const ViewParams& v = ctx->views[view];
   art_status st = ensure_bin_buffers(ctx, (int64_t)v.tiles_x * v.tiles_y);
   if (st != ART_OK) return st;
+  if (ctx->cfg.skip == ART_SKIP_LEARNED) {  // proposal intervals + coarse check + fallback
+    if (!ctx->prop_loaded) return fail(ctx, ART_ERR_STATE, "learned skip without a proposal (art_load_proposal)");
+    if ((st = ensure_skip_buffers(ctx, v)) != ART_OK) return st;
+    launch_project(ctx, v, ctx->d_hbin, ctx->d_htau);
+    launch_scan_emit(ctx, v, ctx->d_hbin, ctx->d_htau, ctx->d_thist);
+    launch_sort(ctx, 32);
+    launch_ranges(ctx, v);
+    if ((st = launch_proposal(ctx, v, ctx->d_bins, nullptr, true)) != ART_OK) return st;
+    if ((st = launch_composite_skip(ctx, v, F, F_dtype, A)) != ART_OK) return st;
+    return launch_check(ctx, "render_feature_maps");
+  }
   launch_project(ctx, v);
   launch_scan_emit(ctx, v);
   launch_sort(ctx, 32);
@@ -638,6 +721,7 @@ art_status art_sync_status(art_ctx* ctx, art_stats* out) {
     out->overflow_inst = (int64_t)h[kStOverflowInst];
     out->overflow_order = (int64_t)h[kStOverflowOrder];
     out->kernel_launches = ctx->launches;
+    out->fallback_tiles = (int64_t)h[kStFallback];
   }
   if (h[kStTcError]) {
     art_status r = fail(ctx, ART_ERR_CUDA, "tensor-core convolution: %llu CTAs timed out waiting on their pipeline",
@@ -776,6 +860,15 @@ art_status art_debug_buffer(art_ctx* ctx, int which, void* dst, int64_t bytes, i
     case ART_BUF_RANGES: src = ctx->d_ranges; sz = ctx->ranges_cap * 8; break;
     case ART_BUF_FP8_SCALES: src = ctx->d_f8_scale; sz = ctx->d_f8_scale ? kF8Tensors * 4 : 0; break;
     case ART_BUF_ACTIVATIONS: src = ctx->d_act; sz = ctx->d_act ? (int64_t)ctx->d_act_bytes : 0; break;
+    case ART_BUF_BINS: src = ctx->d_bins; sz = ctx->d_bins ? (int64_t)ctx->d_bins_bytes : 0; break;
+    case ART_BUF_FALLBACK: {
+      unsigned long long nf = 0;
+      cudaMemcpy(&nf, ctx->d_status + kStFallback, sizeof(nf), cudaMemcpyDeviceToHost);
+      src = ctx->d_fbq;
+      sz = ctx->d_fbq ? (int64_t)std::min<unsigned long long>(nf, ctx->d_fbq_bytes / 4) * 4 : 0;
+      break;
+    }
+    case ART_BUF_TAU_HIST: src = ctx->d_thist; sz = ctx->d_thist ? (int64_t)ctx->d_thist_bytes : 0; break;
     default: return fail(ctx, ART_ERR_INVALID_ARG, "unknown buffer %d", which);
   }
   if (needed) *needed = sz;

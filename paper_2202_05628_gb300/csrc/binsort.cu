@@ -141,7 +141,10 @@ __global__ void __launch_bounds__(kScanThreads) emit_kernel(int64_t n, const uin
                                                             const uint32_t* __restrict__ q, ViewParams v,
                                                             int64_t cap, uint32_t* __restrict__ keys,
                                                             uint32_t* __restrict__ vals,
-                                                            unsigned long long* __restrict__ status) {
+                                                            unsigned long long* __restrict__ status,
+                                                            const uint32_t* __restrict__ hbin,
+                                                            const float* __restrict__ htau,
+                                                            float* __restrict__ thist) {
   int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * kScanItems;
   uint32_t c[kScanItems];
   uint32_t s = 0;
@@ -158,16 +161,25 @@ __global__ void __launch_bounds__(kScanThreads) emit_kernel(int64_t n, const uin
     short4 r = rect[i];
     uint32_t qq = q[i];
     int tx0 = r.x >> v.tile_wl, tx1 = r.z >> v.tile_wl, ty0 = r.y >> v.tile_hl, ty1 = r.w >> v.tile_hl;
+    int hb0 = 1, hb1 = 0;
+    float ht = 0.0f;
+    if (thist) {
+      const uint32_t hb = hbin[i];
+      hb0 = (int)(hb & 0xFFu);
+      hb1 = (int)(hb >> 8);
+      ht = htau[i];
+    }
     for (int ty = ty0; ty <= ty1; ++ty)
       for (int tx = tx0; tx <= tx1; ++tx) {
+        uint32_t tile = (uint32_t)(ty * v.tiles_x + tx);
         if (off < (uint64_t)cap) {
-          uint32_t tile = (uint32_t)(ty * v.tiles_x + tx);
           keys[off] = (tile << v.depth_bits) | qq;
           vals[off] = (uint32_t)i;
         } else {
           ++over;
         }
         ++off;
+        for (int b = hb0; b <= hb1; ++b) atomicAdd(thist + (size_t)tile * kPropBins + b, ht);
       }
   }
   if (over) atomicAdd(status + kStOverflowInst, (unsigned long long)over);
@@ -270,14 +282,14 @@ size_t sort_hist_words(int64_t inst_cap) {
   return (size_t)(nb * kRadix);
 }
 
-void launch_scan_emit(art_ctx* ctx, const ViewParams& v) {
+void launch_scan_emit(art_ctx* ctx, const ViewParams& v, const uint32_t* hbin, const float* htau, float* thist) {
   int64_t n = ctx->n;
   int nb = (int)((n + kScanBlock - 1) / kScanBlock);
   ART_LAUNCH(ctx, "bin_blocksum", block_sum_kernel, nb, kScanThreads, 0, ctx->d_cnt, n,
              (const unsigned long long*)nullptr, ctx->d_bsum);
   ART_LAUNCH(ctx, "bin_scan", scan_bsum_kernel, 1, 1024, 0, ctx->d_bsum, nb, ctx->d_status + kStInstances);
   ART_LAUNCH(ctx, "bin_emit", emit_kernel, nb, kScanThreads, 0, n, ctx->d_cnt, ctx->d_bsum, ctx->d_rect, ctx->d_q, v,
-             ctx->inst_cap, ctx->d_keys[0], ctx->d_vals[0], ctx->d_status);
+             ctx->inst_cap, ctx->d_keys[0], ctx->d_vals[0], ctx->d_status, hbin, htau, thist);
 }
 
 int launch_sort_bufs(art_ctx* ctx, uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, int64_t cap,

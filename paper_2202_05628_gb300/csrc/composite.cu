@@ -16,21 +16,56 @@
 // (t0 < the distance bound of the next chunk, or of the candidate when the
 // buffer is full).  The walk ends once every pixel of the tile has stopped
 // (T < tau).
+#include <algorithm>
+
 #include "raster.cuh"
 
 namespace art {
 namespace {
 
+enum Mode { kPlain = 0, kDebug = 1, kLabel = 2, kInterval = 3 };
+
+// Inputs and outputs of the learned-skip modes.
+struct SkipArgs {
+  const uchar2* bins;   // kInterval: proposal bins per pixel
+  const float* thist;   // kLabel, kInterval: [tiles][kPropBins] optical-depth bounds
+  float max_missed;     // coarse-check threshold
+  int margin;           // kInterval: bins added on both sides
+  uint32_t* queue;      // kInterval: fallback queue (count in status[kStFallback])
+  float* labels;        // kLabel: [H][W][3]
+  uchar2* lbins;        // kLabel: [H][W]
+};
+
+// Inclusive prefix sums of the tile's depth-bin histogram into pre[64];
+// returns the total.
+__device__ __forceinline__ float tile_hist_prefix(const float* __restrict__ th, float* pre, int lane) {
+  float p0 = th[lane], p1 = th[32 + lane];
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float a = __shfl_up_sync(0xffffffffu, p0, o), b = __shfl_up_sync(0xffffffffu, p1, o);
+    if (lane >= o) {
+      p0 += a;
+      p1 += b;
+    }
+  }
+  const float t0 = __shfl_sync(0xffffffffu, p0, 31);
+  pre[lane] = p0;
+  pre[32 + lane] = p1 + t0;
+  __syncwarp();
+  return pre[63];
+}
+
 // One warp per 8x4 tile, lane = pixel (x = lane & 7, y = lane >> 3).
-template <int C, typename TF, typename TO, bool DBG>
-__global__ void __launch_bounds__(32) composite_kernel(const uint2* __restrict__ ranges,
-                                                       const uint32_t* __restrict__ keys,
-                                                       const uint32_t* __restrict__ vals,
-                                                       const float4* __restrict__ rec,
-                                                       const short4* __restrict__ rect,
-                                                       const TF* __restrict__ feat, ViewParams v, float tau,
-                                                       TO* __restrict__ Fout, float* __restrict__ Aout,
-                                                       unsigned long long* __restrict__ status, HitLog dbg) {
+template <int C, typename TF, typename TO, int MODE>
+__device__ __forceinline__ void composite_tile(const int tile, const uint2* __restrict__ ranges,
+                                               const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals,
+                                               const float4* __restrict__ rec, const short4* __restrict__ rect,
+                                               const TF* __restrict__ feat, const ViewParams& v, float tau,
+                                               TO* __restrict__ Fout, float* __restrict__ Aout,
+                                               unsigned long long* __restrict__ status, const HitLog& dbg,
+                                               const SkipArgs& sk) {
+  constexpr bool DBG = MODE == kDebug;
+  constexpr bool FEAT = MODE != kLabel;  // labels need densities only
   constexpr int RING = Ring<C, TF>::kChunks;
   __shared__ float4 s_b0[NT], s_b1[NT], s_b2[NT];
   __shared__ float s_thr[NT];
@@ -39,8 +74,7 @@ __global__ void __launch_bounds__(32) composite_kernel(const uint2* __restrict__
   __shared__ uint32_t s_vid[RING][NT];
   __shared__ __align__(16) TF s_feat[RING][NT][C];
 
-  const int lane = threadIdx.x;
-  const int tile = blockIdx.x;
+  const int lane = threadIdx.x & 31;
   const int tx = tile % v.tiles_x, ty = tile / v.tiles_x;
   const int sx = tx * TSX, sy = ty * TSY;
   const int px = sx + (lane & 7), py = sy + (lane >> 3);
@@ -65,6 +99,37 @@ __global__ void __launch_bounds__(32) composite_kernel(const uint2* __restrict__
   int n_used = 0;
   int cur_chunk = 0;
   const uint2 rg = ranges[tile];
+  // learned skip: this pixel's interval [t_lo, t_hi] and the deepest end over the warp
+  float t_lo = 0.0f, t_hi = 3.4e38f, hi_w = 3.4e38f;
+  int bn = 0, bf = kPropBins - 1;
+  bool empty = false;
+  if constexpr (MODE == kInterval) {
+    // the tile composites over the union of its pixels' predicted intervals
+    // (empty predictions contribute nothing), widened by the margin
+    int lo_b = kPropBins, hi_b = -1;
+    if (inside) {
+      const uchar2 b = sk.bins[pix];
+      if (b.y >= b.x) {
+        lo_b = b.x;
+        hi_b = b.y;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      lo_b = min(lo_b, __shfl_xor_sync(0xffffffffu, lo_b, o));
+      hi_b = max(hi_b, __shfl_xor_sync(0xffffffffu, hi_b, o));
+    }
+    empty = hi_b < lo_b;
+    bn = empty ? lo_b : max(lo_b - sk.margin, 0);
+    bf = empty ? hi_b : min(hi_b + sk.margin, kPropBins - 1);
+    const float D = (v.zfar - v.znear) / (float)kPropBins;
+    t_lo = v.znear + (float)bn * D;
+    t_hi = v.znear + (float)(bf + 1) * D;
+    if (empty) done = true;
+    hi_w = empty ? -3.4e38f : t_hi;
+  }
+  // labels: span of the significant hits and the transmittance after the last
+  float lab_lo = 3.4e38f, lab_hi = -3.4e38f, lab_T = 1.0f;
 
   auto release_front = [&]() {
     Pend h = buf[0];
@@ -78,11 +143,11 @@ __global__ void __launch_bounds__(32) composite_kernel(const uint2* __restrict__
     if (cur_chunk - ch < RING) {
       sig = s_sig[ch % RING][sl];
       vid = s_vid[ch % RING][sl];
-      row_to_float<C>(&s_feat[ch % RING][sl][0], f);
+      if constexpr (FEAT) row_to_float<C>(&s_feat[ch % RING][sl][0], f);
     } else {  // staged long ago: read the voxel again
       vid = vals[rg.x + h.pos];
       sig = rec[4 * (size_t)vid + 3].x;
-      load_feat<C>(feat + (size_t)vid * C, f);
+      if constexpr (FEAT) load_feat<C>(feat + (size_t)vid * C, f);
     }
     if constexpr (DBG) {
       if (n_used < dbg.cap) {
@@ -94,9 +159,18 @@ __global__ void __launch_bounds__(32) composite_kernel(const uint2* __restrict__
     }
     float e = expf(-sig * (h.t1 - h.t0));
     float w = T * (1.0f - e);
+    if constexpr (FEAT) {
 #pragma unroll
-    for (int c = 0; c < C; ++c) acc[c] = fmaf(w, f[c], acc[c]);
+      for (int c = 0; c < C; ++c) acc[c] = fmaf(w, f[c], acc[c]);
+    }
     T *= e;
+    if constexpr (MODE == kLabel) {
+      if (w > kLabelWmin) {
+        lab_lo = fminf(lab_lo, h.t1);
+        lab_hi = fmaxf(lab_hi, h.t0);
+        lab_T = T;
+      }
+    }
     if (T < tau) done = true;
   };
 
@@ -114,7 +188,7 @@ __global__ void __launch_bounds__(32) composite_kernel(const uint2* __restrict__
         const float4* rp = rec + 4 * (size_t)vid;
         const float4 r0 = rp[0], r1 = rp[1], r2 = rp[2], r3 = rp[3];
         const short4 rc = rect[vid];
-        copy_row<C, TF>(feat + (size_t)vid * C, &s_feat[slot][lane][0]);
+        if constexpr (FEAT) copy_row<C, TF>(feat + (size_t)vid * C, &s_feat[slot][lane][0]);
         const float ex = v.o[0] - r0.w, ey = v.o[1] - r1.w, ez = v.o[2] - r2.w;
         s_b0[lane] = make_float4(r0.x, r0.y, r0.z, r0.x * ex + r0.y * ey + r0.z * ez);
         s_b1[lane] = make_float4(r1.x, r1.y, r1.z, r1.x * ex + r1.y * ey + r1.z * ez);
@@ -123,11 +197,17 @@ __global__ void __launch_bounds__(32) composite_kernel(const uint2* __restrict__
         s_vid[slot][lane] = vid;
         thr = v.znear + (float)(key & qmask) * qinv;
         m = rect_mask(rc, sx, sy);
+        if constexpr (MODE == kInterval) {
+          if (thr > hi_w) m = 0;  // enters beyond every pixel's interval
+        }
       }
       s_mask[lane] = m;
       s_thr[lane] = thr;
     }
     __syncwarp();
+    if constexpr (MODE == kInterval) {
+      if (s_thr[0] > hi_w) break;  // the list is sorted: nothing later can enter an interval
+    }
     // every instance of this chunk and later enters at t >= the first threshold
     const float thr0 = s_thr[0];
     while (!done && nb > 0 && buf[0].t0 < thr0) release_front();
@@ -139,6 +219,9 @@ __global__ void __launch_bounds__(32) composite_kernel(const uint2* __restrict__
       float t0, t1, e[3];
       int ax0, ax1;
       if (!slab_hit(s_b0[idx], s_b1[idx], s_b2[idx], d0, d1, d2, v.znear, v.zfar, t0, t1, ax0, ax1, e)) continue;
+      if constexpr (MODE == kInterval) {
+        if (t1 < t_lo || t0 > t_hi) continue;  // outside this pixel's interval
+      }
       const Pend p{t0, t1, base - rg.x + (uint32_t)idx};
       if (nb == kPend) {
         // buffer full: release what this candidate's own bound allows (still
@@ -171,7 +254,48 @@ __global__ void __launch_bounds__(32) composite_kernel(const uint2* __restrict__
   }
   while (nb > 0 && !done) release_front();
 
-  if (inside) {
+  if constexpr (MODE == kLabel || MODE == kInterval) {
+    __shared__ float s_pre[kPropBins];
+    const float tot = tile_hist_prefix(sk.thist + (size_t)tile * kPropBins, s_pre, lane);
+    if constexpr (MODE == kInterval) {  // coarse check of the lost mass
+      bool fail = false;
+      if (inside) {
+        const float front = empty ? tot : (bn > 0 ? s_pre[bn - 1] : 0.0f);
+        const float back = empty ? 0.0f : tot - s_pre[bf];
+        fail = -expm1f(-front) + T * -expm1f(-back) > sk.max_missed;
+      }
+      if (__any_sync(0xffffffffu, fail) && lane == 0) {
+        const unsigned long long q = atomicAdd(status + kStFallback, 1ull);
+        sk.queue[q] = (uint32_t)tile;
+      }
+    } else {  // label bins: keep the significant hits and pass the check
+      const float budget = kLabelBudget * sk.max_missed;
+      const float tau_b = -log1pf(-budget);
+      const bool c0 = (lane == 0 ? 0.0f : s_pre[lane - 1]) <= tau_b;
+      const bool c1 = s_pre[31 + lane] <= tau_b;
+      const int front = __popc(__ballot_sync(0xffffffffu, c0)) + __popc(__ballot_sync(0xffffffffu, c1)) - 1;
+      if (inside) {
+        const bool sig = lab_lo < 3.0e38f;
+        const float bs = (float)kPropBins / (v.zfar - v.znear);
+        const int blo = sig ? min(max((int)floorf((lab_lo - v.znear) * bs), 0), kPropBins - 1) : kPropBins - 1;
+        const int bhi = sig ? min(max((int)floorf((lab_hi - v.znear) * bs), 0), kPropBins - 1) : 0;
+        const float Ts = sig ? lab_T : 1.0f;
+        int lbf = kPropBins - 1;
+        for (int b = bhi; b < kPropBins; ++b)
+          if (Ts * -expm1f(-(tot - s_pre[b])) <= budget) {
+            lbf = b;
+            break;
+          }
+        if (sk.labels) {
+          sk.labels[3 * pix] = sig ? lab_lo : __int_as_float(0x7f800000);
+          sk.labels[3 * pix + 1] = sig ? lab_hi : __int_as_float(0xff800000);
+          sk.labels[3 * pix + 2] = Ts;
+        }
+        if (sk.lbins) sk.lbins[pix] = make_uchar2((uint8_t)min(blo, front), (uint8_t)lbf);
+      }
+    }
+  }
+  if (inside && MODE != kLabel) {
     if constexpr (DBG) dbg.count[pix] = n_used;
     store_row<C>(Fout + pix * C, acc);
     if (Aout) Aout[pix] = 1.0f - T;
@@ -179,48 +303,118 @@ __global__ void __launch_bounds__(32) composite_kernel(const uint2* __restrict__
   if (n_over) atomicAdd(status + kStOverflowOrder, (unsigned long long)n_over);
 }
 
+template <int C, typename TF, typename TO, int MODE>
+__global__ void __launch_bounds__(32) composite_kernel(const uint2* __restrict__ ranges,
+                                                       const uint32_t* __restrict__ keys,
+                                                       const uint32_t* __restrict__ vals,
+                                                       const float4* __restrict__ rec,
+                                                       const short4* __restrict__ rect,
+                                                       const TF* __restrict__ feat, ViewParams v, float tau,
+                                                       TO* __restrict__ Fout, float* __restrict__ Aout,
+                                                       unsigned long long* __restrict__ status, HitLog dbg,
+                                                       SkipArgs sk) {
+  composite_tile<C, TF, TO, MODE>(blockIdx.x, ranges, keys, vals, rec, rect, feat, v, tau, Fout, Aout, status, dbg,
+                                  sk);
+}
+
+// The plain walk over the tiles queued by the learned-skip pass.
 template <int C, typename TF, typename TO>
-void launch_c(art_ctx* ctx, const ViewParams& v, void* F, float* A, const HitLog* dbg) {
-  int ntiles = v.tiles_x * v.tiles_y;
-  if (dbg) {
-    auto kfn = composite_kernel<C, TF, TO, true>;
+__global__ void __launch_bounds__(32) composite_queue_kernel(const uint2* __restrict__ ranges,
+                                                             const uint32_t* __restrict__ keys,
+                                                             const uint32_t* __restrict__ vals,
+                                                             const float4* __restrict__ rec,
+                                                             const short4* __restrict__ rect,
+                                                             const TF* __restrict__ feat, ViewParams v, float tau,
+                                                             TO* __restrict__ Fout, float* __restrict__ Aout,
+                                                             unsigned long long* __restrict__ status,
+                                                             const uint32_t* __restrict__ queue) {
+  const unsigned long long n = status[kStFallback];
+  for (unsigned long long i = blockIdx.x; i < n; i += gridDim.x)
+    composite_tile<C, TF, TO, kPlain>((int)queue[i], ranges, keys, vals, rec, rect, feat, v, tau, Fout, Aout, status,
+                                      HitLog{}, SkipArgs{});
+}
+
+template <int C, typename TF, typename TO>
+void launch_c(art_ctx* ctx, const ViewParams& v, void* F, float* A, const HitLog* dbg, int mode, const SkipArgs& sk) {
+  const int ntiles = v.tiles_x * v.tiles_y;
+  const TF* feat = (const TF*)ctx->d_feat;
+  if (mode == kDebug) {
+    auto kfn = composite_kernel<C, TF, TO, kDebug>;
     ART_LAUNCH(ctx, "composite_debug", kfn, ntiles, 32, 0, ctx->d_ranges, ctx->d_keys[0], ctx->d_vals[0], ctx->d_rec,
-               ctx->d_rect, (const TF*)ctx->d_feat, v, ctx->cfg.tau, (TO*)F, A, ctx->d_status, *dbg);
+               ctx->d_rect, feat, v, ctx->cfg.tau, (TO*)F, A, ctx->d_status, *dbg, sk);
+  } else if (mode == kLabel) {
+    auto kfn = composite_kernel<C, TF, TO, kLabel>;
+    ART_LAUNCH(ctx, "composite_labels", kfn, ntiles, 32, 0, ctx->d_ranges, ctx->d_keys[0], ctx->d_vals[0], ctx->d_rec,
+               ctx->d_rect, feat, v, ctx->cfg.tau, (TO*)F, A, ctx->d_status, HitLog{}, sk);
+  } else if (mode == kInterval) {
+    auto kfn = composite_kernel<C, TF, TO, kInterval>;
+    ART_LAUNCH(ctx, "composite_skip", kfn, ntiles, 32, 0, ctx->d_ranges, ctx->d_keys[0], ctx->d_vals[0], ctx->d_rec,
+               ctx->d_rect, feat, v, ctx->cfg.tau, (TO*)F, A, ctx->d_status, HitLog{}, sk);
+    auto qfn = composite_queue_kernel<C, TF, TO>;
+    const int qgrid = std::min(ntiles, 16 * ctx->num_sms);
+    ART_LAUNCH(ctx, "composite_fallback", qfn, qgrid, 32, 0, ctx->d_ranges, ctx->d_keys[0], ctx->d_vals[0],
+               ctx->d_rec, ctx->d_rect, feat, v, ctx->cfg.tau, (TO*)F, A, ctx->d_status, sk.queue);
   } else {
-    auto kfn = composite_kernel<C, TF, TO, false>;
+    auto kfn = composite_kernel<C, TF, TO, kPlain>;
     ART_LAUNCH(ctx, "composite", kfn, ntiles, 32, 0, ctx->d_ranges, ctx->d_keys[0], ctx->d_vals[0], ctx->d_rec,
-               ctx->d_rect, (const TF*)ctx->d_feat, v, ctx->cfg.tau, (TO*)F, A, ctx->d_status, HitLog{});
+               ctx->d_rect, feat, v, ctx->cfg.tau, (TO*)F, A, ctx->d_status, HitLog{}, sk);
   }
 }
 
 template <int C>
-art_status dispatch_dtypes(art_ctx* ctx, const ViewParams& v, void* F, int F_dtype, float* A, const HitLog* dbg) {
+art_status dispatch_dtypes(art_ctx* ctx, const ViewParams& v, void* F, int F_dtype, float* A, const HitLog* dbg,
+                           int mode, const SkipArgs& sk) {
   int fd = ctx->feat_dtype;
   if (F_dtype == ART_F32) {
-    if (fd == ART_F32) launch_c<C, float, float>(ctx, v, F, A, dbg);
-    else if (fd == ART_BF16) launch_c<C, __nv_bfloat16, float>(ctx, v, F, A, dbg);
-    else launch_c<C, __half, float>(ctx, v, F, A, dbg);
+    if (fd == ART_F32) launch_c<C, float, float>(ctx, v, F, A, dbg, mode, sk);
+    else if (fd == ART_BF16) launch_c<C, __nv_bfloat16, float>(ctx, v, F, A, dbg, mode, sk);
+    else launch_c<C, __half, float>(ctx, v, F, A, dbg, mode, sk);
   } else {
     if (dbg) return fail(ctx, ART_ERR_INVALID_ARG, "hit logging writes FP32 feature maps");
-    if (fd == ART_F32) launch_c<C, float, __nv_bfloat16>(ctx, v, F, A, nullptr);
-    else if (fd == ART_BF16) launch_c<C, __nv_bfloat16, __nv_bfloat16>(ctx, v, F, A, nullptr);
-    else launch_c<C, __half, __nv_bfloat16>(ctx, v, F, A, nullptr);
+    if (fd == ART_F32) launch_c<C, float, __nv_bfloat16>(ctx, v, F, A, nullptr, mode, sk);
+    else if (fd == ART_BF16) launch_c<C, __nv_bfloat16, __nv_bfloat16>(ctx, v, F, A, nullptr, mode, sk);
+    else launch_c<C, __half, __nv_bfloat16>(ctx, v, F, A, nullptr, mode, sk);
   }
   return ART_OK;
+}
+
+art_status dispatch(art_ctx* ctx, const ViewParams& v, void* F, int F_dtype, float* A, const HitLog* dbg, int mode,
+                    const SkipArgs& sk) {
+  if (v.tile_w != TSX || v.tile_h != TSY) return fail(ctx, ART_ERR_UNSUPPORTED, "composite: tiles must be 8x4");
+  switch (ctx->C) {
+    case 4: return dispatch_dtypes<4>(ctx, v, F, F_dtype, A, dbg, mode, sk);
+    case 8: return dispatch_dtypes<8>(ctx, v, F, F_dtype, A, dbg, mode, sk);
+    case 16: return dispatch_dtypes<16>(ctx, v, F, F_dtype, A, dbg, mode, sk);
+    case 32: return dispatch_dtypes<32>(ctx, v, F, F_dtype, A, dbg, mode, sk);
+    default: return fail(ctx, ART_ERR_UNSUPPORTED, "composite: C=%d not built (4, 8, 16, 32)", ctx->C);
+  }
 }
 
 }  // namespace
 
 art_status launch_composite(art_ctx* ctx, const ViewParams& v, void* F, int F_dtype, float* A, const void* dbg_log) {
   const HitLog* dbg = (const HitLog*)dbg_log;
-  if (v.tile_w != TSX || v.tile_h != TSY) return fail(ctx, ART_ERR_UNSUPPORTED, "composite: tiles must be 8x4");
-  switch (ctx->C) {
-    case 4: return dispatch_dtypes<4>(ctx, v, F, F_dtype, A, dbg);
-    case 8: return dispatch_dtypes<8>(ctx, v, F, F_dtype, A, dbg);
-    case 16: return dispatch_dtypes<16>(ctx, v, F, F_dtype, A, dbg);
-    case 32: return dispatch_dtypes<32>(ctx, v, F, F_dtype, A, dbg);
-    default: return fail(ctx, ART_ERR_UNSUPPORTED, "composite: C=%d not built (4, 8, 16, 32)", ctx->C);
-  }
+  return dispatch(ctx, v, F, F_dtype, A, dbg, dbg ? kDebug : kPlain, SkipArgs{});
+}
+
+art_status launch_composite_skip(art_ctx* ctx, const ViewParams& v, void* F, int F_dtype, float* A) {
+  SkipArgs sk{};
+  sk.bins = reinterpret_cast<const uchar2*>(ctx->d_bins);
+  sk.thist = ctx->d_thist;
+  sk.max_missed = ctx->cfg.max_missed;
+  sk.margin = ctx->cfg.margin;
+  sk.queue = ctx->d_fbq;
+  launch_set_word(ctx, ctx->d_status + kStFallback, 0ull);
+  return dispatch(ctx, v, F, F_dtype, A, nullptr, kInterval, sk);
+}
+
+art_status launch_composite_labels(art_ctx* ctx, const ViewParams& v, float* labels, uint8_t* bins) {
+  SkipArgs sk{};
+  sk.thist = ctx->d_thist;
+  sk.max_missed = ctx->cfg.max_missed;
+  sk.labels = labels;
+  sk.lbins = reinterpret_cast<uchar2*>(bins);
+  return dispatch(ctx, v, nullptr, ART_F32, nullptr, nullptr, kLabel, sk);
 }
 
 // Hit log layout shared with api.cu.

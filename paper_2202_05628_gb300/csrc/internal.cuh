@@ -27,6 +27,7 @@ enum StatusWord {
   kStOverflowInst = 2,  // instances beyond capacity (cumulative until cleared)
   kStOverflowOrder = 3, // reorder-buffer overflows (cumulative until cleared)
   kStTcError = 4,       // tensor-core convolution CTAs that timed out waiting
+  kStFallback = 5,      // learned skip: tiles queued for the full traversal (last render)
   kStWords = 8
 };
 
@@ -138,6 +139,20 @@ struct art_ctx {
   unsigned int* d_f8_amax = nullptr;
   bool f8_calibrated = false;
 
+  // ---- learned ray-interval proposal
+  bool prop_loaded = false;
+  uint8_t* d_prop_img = nullptr;  // BF16 weights of layers 0 (ray part) .. 4 in the UMMA shared-memory image
+  float* d_prop_f32 = nullptr;    // W0 pose columns [64][72] (BF16-rounded), b0, b1, b2, b3, b4
+  float* d_pose_bias = nullptr;   // [64] b0 + W0[:, :72] pose of the current pose
+  uint8_t* d_bins = nullptr;      // [H][W][2] proposal bins of the last learned-skip render
+  size_t d_bins_bytes = 0;
+  float* d_thist = nullptr;       // [tiles][64] optical-depth bound per (tile, depth bin)
+  size_t d_thist_bytes = 0;
+  uint32_t* d_hbin = nullptr;     // [n] per-voxel depth-bin range b0 | b1 << 8 (0xFFFF: none)
+  float* d_htau = nullptr;        // [n] per-voxel optical-depth bound sigma 2 r
+  int64_t hist_n_cap = 0;
+  uint32_t* d_fbq = nullptr;      // [tiles] fallback queue
+  size_t d_fbq_bytes = 0;
   // ---- backward
   float* d_gN = nullptr;        // [n][12] dL/d(A_i^-1) accumulator
   int64_t gN_cap = 0;
@@ -171,10 +186,15 @@ void prof_end(art_ctx* ctx);
 // ---- kernels: LBS (lbs.cu)
 void launch_fk(art_ctx* ctx);
 void launch_lbs(art_ctx* ctx);
-void launch_project(art_ctx* ctx, const ViewParams& v);
+// With hbin / htau set, also the per-voxel depth-bin range and optical-depth
+// bound of the coarse check (64 bins over [znear, zfar]).
+void launch_project(art_ctx* ctx, const ViewParams& v, uint32_t* hbin = nullptr, float* htau = nullptr);
 
 // ---- binning and sorting (binsort.cu)
-void launch_scan_emit(art_ctx* ctx, const ViewParams& v);
+// With thist set (zeroed [tiles][64]), also accumulate the coarse optical-depth
+// bound of every instance into its tile's depth bins.
+void launch_scan_emit(art_ctx* ctx, const ViewParams& v, const uint32_t* hbin = nullptr, const float* htau = nullptr,
+                      float* thist = nullptr);
 void launch_sort(art_ctx* ctx, int key_bits);
 // Radix sort of count (device word) pairs ping-ponging between (k0, v0) and
 // (k1, v1); returns the index (0 or 1) of the buffer holding the result.
@@ -188,6 +208,22 @@ size_t scan_block_words(int64_t n);
 // ---- composite (composite.cu)
 art_status launch_composite(art_ctx* ctx, const ViewParams& v, void* F, int F_dtype, float* A,
                             const void* hit_log = nullptr);
+// Learned skip: composite over the proposal intervals (ctx->d_bins), coarse
+// check against ctx->d_thist, then the full traversal of the queued tiles.
+art_status launch_composite_skip(art_ctx* ctx, const ViewParams& v, void* F, int F_dtype, float* A);
+// Labels of the plain composite (labels [H][W][3], bins [H][W][2]; either may be null).
+art_status launch_composite_labels(art_ctx* ctx, const ViewParams& v, float* labels, uint8_t* bins);
+constexpr int kPropBins = 64;          // proposal depth bins over [znear, zfar]
+constexpr float kLabelWmin = 1e-6f;    // significant hit: weight above this
+constexpr float kLabelBudget = 0.4f;   // label bins keep the coarse bound under this fraction of max_missed
+constexpr float kHistPad = 1e-5f;      // metres added to both ends of a voxel's distance range before binning
+constexpr float kHistSlack = 1e-4f;    // relative growth of the optical-depth bound: covers FP32 rounding of r and sums
+// ---- proposal (proposal.cu)
+art_status load_proposal(art_ctx* ctx, const float* params);
+void launch_pose_bias(art_ctx* ctx);
+// bins [H][W][2] (may be null), logits [H][W][128] (may be null); with
+// active_only, only 4-tile groups with a non-empty tile are predicted.
+art_status launch_proposal(art_ctx* ctx, const ViewParams& v, uint8_t* bins, float* logits, bool active_only);
 void* make_hit_log(int32_t* count, uint32_t* ids, float* t0, float* t1, int cap);
 void free_hit_log(void* p);
 

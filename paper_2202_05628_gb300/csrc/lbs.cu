@@ -160,7 +160,8 @@ __global__ void __launch_bounds__(256) lbs_kernel(int64_t n, int J, const float*
 // which bounds the ray parameter t of any entry point from below.
 __global__ void __launch_bounds__(256) project_kernel(int64_t n, const float4* __restrict__ geo, ViewParams v,
                                                       short4* __restrict__ rect, uint32_t* __restrict__ q,
-                                                      uint32_t* __restrict__ cnt) {
+                                                      uint32_t* __restrict__ cnt, const float* __restrict__ sigma,
+                                                      uint32_t* __restrict__ hbin, float* __restrict__ htau) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   float4 g0 = geo[4 * i], g1 = geo[4 * i + 1], g2 = geo[4 * i + 2], g3 = geo[4 * i + 3];
@@ -217,6 +218,14 @@ __global__ void __launch_bounds__(256) project_kernel(int64_t n, const float4* _
   float qmax = (float)((1u << v.depth_bits) - 1u);
   float qq = fminf(fmaxf(floorf(rel) - 1.0f, 0.0f), qmax);
   q[i] = (uint32_t)qq;
+  if (hbin) {  // coarse check: depth bins [b0, b1] of [dmin, dmax] and the bound sigma (dmax - dmin)
+    // (the range grown by kHistPad so that FP32 rounding never moves a voxel out of a bin it overlaps)
+    const float bs = (float)kPropBins / (v.zfar - v.znear);
+    const int b0 = min(max((int)floorf((dmin - kHistPad - v.znear) * bs), 0), kPropBins - 1);
+    const int b1 = min(max((int)floorf((dmax + kHistPad - v.znear) * bs), 0), kPropBins - 1);
+    hbin[i] = (uint32_t)b0 | ((uint32_t)b1 << 8);
+    htau[i] = sigma[i] * (dmax - dmin) * (1.0f + kHistSlack);
+  }
 }
 
 }  // namespace
@@ -231,10 +240,11 @@ void launch_lbs(art_ctx* ctx) {
              ctx->d_status);
 }
 
-void launch_project(art_ctx* ctx, const ViewParams& v) {
+void launch_project(art_ctx* ctx, const ViewParams& v, uint32_t* hbin, float* htau) {
   int64_t n = ctx->n;
   unsigned grid = (unsigned)((n + 255) / 256);
-  ART_LAUNCH(ctx, "project", project_kernel, grid, 256, 0, n, ctx->d_geo, v, ctx->d_rect, ctx->d_q, ctx->d_cnt);
+  ART_LAUNCH(ctx, "project", project_kernel, grid, 256, 0, n, ctx->d_geo, v, ctx->d_rect, ctx->d_q, ctx->d_cnt,
+             ctx->d_sigma, hbin, htau);
 }
 
 }  // namespace art

@@ -1,0 +1,270 @@
+"""GPU parity of the learned ray-interval proposal against the FP64 oracle:
+the MLP's logits and bins (tensor cores, BF16), the plain renderer's labels,
+the interval-restricted composite with its coarse check and fallback, and a
+proposal trained on the renderer's own labels (project addition; the
+paper's nearest passage is the early-stop rule of Sec. 3.1)."""
+import numpy as np
+import pytest
+
+import oracle
+import scenegen as sg
+from helpers import renderer, set_cam
+
+pytestmark = pytest.mark.gpu
+
+TSX, TSY = 8, 4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _setup(pose_seed=3, W=96, H=64, fov=6.0, az=30.0, storage="f32"):
+    sc = sg.preset("tiny")
+    cam = sg.orbit_camera(sc.centroid, W, H, az_deg=az, fov_deg=fov)  # the animal fills the view
+    pose = sg.random_pose(pose_seed)
+    r = renderer(sc, storage=storage, profile=True)
+    set_cam(r, 0, cam)
+    r.set_pose(pose.axis_angle, pose.R, pose.T)
+    G, A, _ = oracle.pose_transforms(sc, pose)
+    return sc, cam, pose, r, A
+
+
+def _params(seed, scale=1.0):
+    rng = np.random.default_rng(seed)
+    out = []
+    for n_out, n_in in oracle.PROPOSAL_SHAPES:
+        out.append(rng.standard_normal(n_out * n_in) * scale * np.sqrt(2.0 / n_in))
+        out.append(rng.standard_normal(n_out) * 0.1)
+    return np.concatenate(out).astype(np.float32)
+
+
+def _skip_params(seed):
+    """An untrained proposal whose output biases centre the near and far
+    bins on the animal's depth (bins 30 and 33 of the test view), so that
+    some tiles pass the coarse check and some fall back."""
+    p = _params(seed, scale=2.0)
+    k = np.arange(64)
+    p[-128:] = np.concatenate([-0.4 * np.abs(k - 30), -0.4 * np.abs(k - 33)])
+    return p
+
+
+def _tied_pixels(o, n_px, eps=1e-6, face_eps=1e-5):
+    """Pixels whose hit list holds two hits (chords >= face_eps) entering
+    within eps of each other: FP32 may order them either way."""
+    tied = np.zeros(n_px, bool)
+    off = o["hit_off"]
+    for p in range(n_px):
+        t0 = o["hit_t0"][off[p]:off[p + 1]]
+        t1 = o["hit_t1"][off[p]:off[p + 1]]
+        big = (t1 - t0) >= face_eps
+        tied[p] = bool(np.any(np.diff(np.sort(t0[big])) < eps))
+    return tied
+
+
+def _tile_of_pixels(cam):
+    tw = (cam.W + TSX - 1) // TSX
+    ys, xs = np.meshgrid(np.arange(cam.H), np.arange(cam.W), indexing="ij")
+    return (ys // TSY) * tw + xs // TSX
+
+
+@pytest.mark.parametrize("W,H", [(96, 64), (72, 40)])
+def test_proposal_logits_and_bins_match_oracle(W, H):
+    """Logits of every pixel's ray against the oracle MLP with BF16 inputs,
+    weights and hidden activations; bins equal wherever the oracle's top two
+    logits of a half are further apart than the logits' error."""
+    import torch
+    sc, cam, pose, r, A = _setup(W=W, H=H)
+    params = _params(1)
+    r.load_proposal(params)
+    bins = torch.zeros((H, W, 2), dtype=torch.uint8, device="cuda")
+    logits = torch.zeros((H, W, 128), dtype=torch.float32, device="cuda")
+    r.run_proposal(0, bins, logits)
+    r.sync_status()
+    assert r.kernel_times().get("proposal_mlp", (0, 0))[0] == 1
+    x = oracle.proposal_inputs(pose.axis_angle, cam)
+    ref = oracle.proposal_mlp(x, params, bf16=True)
+    got = logits.cpu().numpy().reshape(-1, 128).astype(np.float64)
+    err = np.abs(got - ref)
+    scale = np.abs(ref).max()
+    assert err.max() <= 2e-2 * scale and np.median(err) <= 2e-3 * scale, (err.max(), np.median(err), scale)
+    b_ref = oracle.proposal_bins(ref)
+    b_got = bins.cpu().numpy().reshape(-1, 2).astype(np.int32)
+    tol = 2 * err.max()
+    for h in range(2):
+        half = np.sort(ref[:, 64 * h:64 * (h + 1)], 1)
+        clear = half[:, -1] - half[:, -2] > tol
+        assert clear.mean() > 0.5
+        np.testing.assert_array_equal(b_got[clear, h], b_ref[clear, h])
+    # the 72 pose inputs enter through the per-pose bias: a new pose moves the logits
+    p2 = sg.random_pose(11)
+    r.set_pose(p2.axis_angle, p2.R, p2.T)
+    r.run_proposal(0, None, logits)
+    ref2 = oracle.proposal_mlp(oracle.proposal_inputs(p2.axis_angle, cam), params, bf16=True)
+    err2 = np.abs(logits.cpu().numpy().reshape(-1, 128) - ref2)
+    assert err2.max() <= 2e-2 * np.abs(ref2).max()
+    assert np.abs(ref2 - ref).max() > 10 * err2.max()
+
+
+def test_labels_match_oracle():
+    """Plain-render labels (span of the significant hits, transmittance after
+    the last) and label bins against the oracle's."""
+    import torch
+    sc, cam, pose, r, A = _setup()
+    H, W = cam.H, cam.W
+    lab = torch.zeros((H, W, 3), dtype=torch.float32, device="cuda")
+    bins = torch.zeros((H, W, 2), dtype=torch.uint8, device="cuda")
+    r.render_labels(0, lab, bins)
+    r.sync_status()
+    got = lab.cpu().numpy().reshape(-1, 3).astype(np.float64)
+    ro = oracle.render_interval(sc.octree, A, cam, None, labels=True)
+    ref = ro["labels"].reshape(-1, 3)
+    has = np.isfinite(ref[:, 0])
+    assert has.sum() > 1000
+    np.testing.assert_array_equal(np.isfinite(got[:, 0]), has)
+    d_lo = np.abs(got[has, 0] - ref[has, 0])
+    d_hi = np.abs(got[has, 1] - ref[has, 1])
+    d_T = np.abs(got[has, 2] - ref[has, 2])
+    # a hit whose weight sits at the 1e-6 threshold may be taken on one side only
+    assert (d_lo > 1e-4).mean() < 5e-3 and (d_hi > 1e-4).mean() < 5e-3, ((d_lo > 1e-4).mean(), (d_hi > 1e-4).mean())
+    # T is an FP32 product over some 50 hits, each exp(-sigma delta) with a chord from FP32 slab planes
+    assert np.median(d_T) < 2e-5 and (d_T > 1e-4).mean() < 5e-3, (np.median(d_T), (d_T > 1e-4).mean())
+    hist_g = r.debug_buffer(12, np.float32)
+    hist_o = oracle.tau_hist(sc.octree, A, cam)
+    hg = hist_g[:hist_o.size].reshape(hist_o.shape)
+    # an upper bound of the oracle's: the GPU's pixel boxes are padded by 2e-3 px (a superset of tiles),
+    # its distance ranges by 1e-5 m, and each voxel's bound by a factor 1 + 1e-4 (FP32 rounding)
+    assert np.all(hg >= hist_o * (1 - 1e-6) - 1e-7)
+    assert hg.sum() <= 1.01 * hist_o.sum()
+    nz = hist_o > 0
+    assert np.mean(np.abs(hg[nz] / hist_o[nz] - 1) <= 2e-4) > 0.8
+    b_ref = oracle.label_bins(ro["labels"], hist_o, cam)
+    b_got = bins.cpu().numpy().reshape(-1, 2).astype(np.int32)
+    same = np.all(b_got == b_ref, 1)
+    assert same.mean() > 0.99, same.mean()
+    assert np.abs(b_got - b_ref).max() <= 2
+
+
+@pytest.mark.parametrize("seed,margin", [(2, 0), (5, 1)])
+def test_skip_render_matches_oracle(seed, margin):
+    """Learned-skip render with an untrained proposal (arbitrary intervals):
+    queued tiles equal the plain render bit for bit; tiles that pass the
+    coarse check equal the oracle's interval-restricted composite with the
+    same bins and lose at most the threshold of mass; the queue agrees with
+    the oracle's coarse check."""
+    import torch
+    sc, cam, pose, r, A = _setup(pose_seed=seed)
+    H, W, C = cam.H, cam.W, sc.octree.C
+    r.load_proposal(_skip_params(seed))
+    F0 = torch.zeros((H, W, C), dtype=torch.float32, device="cuda")
+    A0 = torch.zeros((H, W), dtype=torch.float32, device="cuda")
+    r.render_feature_maps(0, F0, A0)  # plain
+    r.set_config(profile=True, skip=1, max_missed=1e-3, margin=margin)
+    F = torch.zeros((H, W, C), dtype=torch.float32, device="cuda")
+    Am = torch.zeros((H, W), dtype=torch.float32, device="cuda")
+    r.kernel_times(reset=True)
+    r.render_feature_maps(0, F, Am)
+    st = r.sync_status()
+    kt = r.kernel_times()
+    assert kt["composite_skip"][0] == 1 and kt["composite_fallback"][0] == 1 and kt["proposal_mlp"][0] == 1
+    bins = r.debug_buffer(10, np.uint8)[:H * W * 2].reshape(-1, 2).astype(np.int32)
+    fb = r.debug_buffer(11, np.uint32)[:st["fallback_tiles"]] if st["fallback_tiles"] else np.zeros(0, np.uint32)
+    assert len(np.unique(fb)) == len(fb) == st["fallback_tiles"]
+    hist_o = oracle.tau_hist(sc.octree, A, cam)
+    active = hist_o.sum(1) > 0
+    tile = _tile_of_pixels(cam).reshape(-1)
+    act_px = active[tile]
+    Fg, Ag = F.cpu().numpy().reshape(-1, C), Am.cpu().numpy().reshape(-1)
+    F0g, A0g = F0.cpu().numpy().reshape(-1, C), A0.cpu().numpy().reshape(-1)
+    in_fb = np.isin(tile, fb)
+    # the fallback is the plain walk
+    np.testing.assert_array_equal(Fg[in_fb], F0g[in_fb])
+    np.testing.assert_array_equal(Ag[in_fb], A0g[in_fb])
+    # bins as the kernel used them (tile union, margin), for the oracle's restricted composite
+    bu = oracle.tile_union_bins(bins, cam, margin)
+    bu[~act_px] = [0, 63]  # tiles without instances were not predicted: nothing to composite there
+    ro = oracle.render_interval(sc.octree, A, cam, bu)
+    full = oracle.render(sc.octree, A, cam)
+    # pixels whose plain FP32 render is well conditioned (no near-tied or grazing hit moves it by 5e-5)
+    good = (np.abs(F0g - full["F"].reshape(-1, C)).max(1) <= 5e-5) & (np.abs(A0g - full["A"].reshape(-1)) <= 5e-5)
+    assert good.mean() > 0.97, good.mean()
+    keep = ~in_fb & good & ~ro["amb"].reshape(-1).astype(bool)
+    assert keep.sum() > 0.5 * (~in_fb).sum()
+    np.testing.assert_allclose(Fg[keep], ro["F"].reshape(-1, C)[keep], atol=1e-4)
+    np.testing.assert_allclose(Ag[keep], ro["A"].reshape(-1)[keep], atol=1e-4)
+    # what passed the check lost no more than the threshold
+    assert ro["missed"].reshape(-1)[~in_fb & act_px].max(initial=0.0) <= 1e-3 * (1 + 1e-3)
+    # the queue is the oracle's coarse check, up to bounds within 1 % of the threshold
+    bound = oracle.coarse_bound(hist_o, bu, 1.0 - ro["A"], cam).reshape(-1)
+    tmax = np.zeros(active.size)
+    np.maximum.at(tmax, tile, bound)
+    fail_o = tmax > 1e-3
+    fail_g = np.zeros(active.size, bool)
+    fail_g[fb] = True
+    clear = np.abs(tmax - 1e-3) > 1e-5
+    # the GPU's tile coverage is a superset (boxes padded by 2e-3 px): it may queue a tile the oracle passes
+    assert np.all(fail_g[clear] >= fail_o[clear])
+    assert np.sum(fail_g[clear] != fail_o[clear]) <= max(1, 0.02 * active.sum())
+    assert 0 < fail_g.sum() < active.sum()  # both branches ran
+
+
+def _train_small(r, cams, n_poses=40, steps=600, seed=0):
+    from paper_2202_05628_gb300 import proposal as prop
+    poses = [sg.random_pose(1000 + k) for k in range(n_poses)]
+    X, Y = prop.collect(r, poses, list(range(len(cams))), cams, rays_per_view=4096, seed=seed)
+    return prop.train(X, Y, steps=steps, batch=4096, lr=3e-3, seed=seed), (X, Y)
+
+
+def test_trained_proposal_skips_with_few_fallbacks():
+    """A proposal trained on the plain renderer's labels over random poses,
+    evaluated on held-out poses: the learned-skip feature maps stay within
+    the lost-mass bound of the plain ones, few tiles fall back, and the
+    skip composite walks fewer list entries than the plain one."""
+    import torch
+    from paper_2202_05628_gb300 import proposal as prop
+    sc = sg.preset("tiny")
+    cams = [sg.orbit_camera(sc.centroid, 96, 64, az_deg=45.0 * k, fov_deg=6.0) for k in range(4)]
+    r = renderer(sc, storage="bf16", profile=True)
+    for k, c in enumerate(cams):
+        set_cam(r, k, c)
+    params, (X, Y) = _train_small(r, cams)
+    acc_n, acc_f, cover = prop.accuracy(params, X, Y)
+    assert acc_n > 0.5 and acc_f > 0.5, (acc_n, acc_f)
+    r.load_proposal(params)
+    fmax = float(np.abs(sc.octree.features).max())
+    n_fb, n_act = 0, 0
+    for k in range(6):  # held-out poses
+        p = sg.random_pose(5000 + k)
+        vi = k % len(cams)
+        cam = cams[vi]
+        F0 = torch.zeros((cam.H, cam.W, sc.octree.C), dtype=torch.float32, device="cuda")
+        F1 = torch.zeros_like(F0)
+        A0 = torch.zeros((cam.H, cam.W), dtype=torch.float32, device="cuda")
+        A1 = torch.zeros_like(A0)
+        r.set_config(profile=True, skip=0)
+        r.set_pose(p.axis_angle, p.R, p.T)
+        r.render_feature_maps(vi, F0, A0)
+        r.set_config(profile=True, skip=1, max_missed=1e-3, margin=1)
+        r.render_feature_maps(vi, F1, A1)
+        st = r.sync_status()
+        ranges = r.debug_buffer(7, np.uint32).reshape(-1, 2)
+        n_act += int(np.sum(ranges[:, 1] > ranges[:, 0]))
+        n_fb += st["fallback_tiles"]
+        assert torch.abs(F1 - F0).max().item() <= 2e-3 * fmax + 1e-4
+        assert torch.abs(A1 - A0).max().item() <= 2e-3 + 1e-4
+    print(f"trained proposal: near/far accuracy {acc_n:.3f}/{acc_f:.3f}, cover {cover:.3f}, "
+          f"fallback {n_fb}/{n_act} active tiles")
+    assert n_fb <= 0.25 * n_act
+
+
+def test_proposal_weights_file_roundtrip(tmp_path):
+    from paper_2202_05628_gb300 import proposal as prop
+    p = prop.init_params(3)
+    f = tmp_path / "w.bin"
+    prop.save(str(f), p, "tiny quadruped")
+    q, meta = prop.load(str(f))
+    np.testing.assert_array_equal(p, q)
+    assert meta == "tiny quadruped"

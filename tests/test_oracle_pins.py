@@ -826,3 +826,20 @@ def test_labels_brute_force_and_label_bins_pass_check():
     assert not s["fallback"].any() and s["bound"].max() <= oracle.MISSED_MAX
     fmax = np.abs(sc.octree.features).max()
     assert np.abs(s["F"] - full["F"]).max() <= 2 * oracle.MISSED_MAX * fmax
+
+
+def test_tile_union_bins_cases():
+    """Union of a tile's non-empty intervals, margin and clamping; a tile of
+    empty intervals stays empty; pixels take their tile's interval."""
+    cam = sg.orbit_camera(np.zeros(3), 16, 4)  # two 8 x 4 tiles
+    b = np.zeros((4, 16, 2), np.int32)
+    b[..., 0], b[..., 1] = 30, 31          # tile 0: all (30, 31) ...
+    b[1, 3] = (27, 29)                      # ... one pixel reaches lower
+    b[2, 5] = (40, 10)                      # ... an empty one is ignored
+    b[:, 8:] = (5, 4)                       # tile 1: all empty
+    u = oracle.tile_union_bins(b, cam).reshape(4, 16, 2)
+    assert np.all(u[:, :8] == (27, 31)) and np.all(u[:, 8:, 1] < u[:, 8:, 0])
+    u2 = oracle.tile_union_bins(b, cam, margin=30).reshape(4, 16, 2)
+    assert np.all(u2[:, :8] == (0, 61))
+    b[..., 0], b[..., 1] = 62, 63
+    assert np.all(oracle.tile_union_bins(b, cam, margin=2).reshape(4, 16, 2) == (60, 63))
