@@ -30,6 +30,14 @@ WORKLOAD = "1M-voxel quadruped octree (depth 10, C=32), 1024x1024 view, 4-level 
 RES = 1024
 N_AZ = 8
 N_POSES = 60
+PROPOSAL = os.path.join(ROOT, "paper_2202_05628_gb300", "weights", "proposal_quadruped_1m_1024.bin")
+# form -> (feature storage, shading network dtype, learned skip, description)
+FORMS = {
+    "bf16_skip": ("bf16", "bf16", True, "BF16 features + learned interval skip + BF16 tensor-core U-Net"),
+    "bf16": ("bf16", "bf16", False, "BF16 features + BF16 tensor-core U-Net (plain traversal)"),
+    "f32": ("f32", "f32", False, "FP32 plain"),
+    "fp8": ("bf16", "fp8", True, "BF16 features + learned interval skip + FP8-E4M3 tensor-core U-Net"),
+}
 
 
 def parse():
@@ -38,7 +46,7 @@ def parse():
     p.add_argument("--steps", type=int, default=60)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    p.add_argument("--form", default="bf16", choices=["bf16", "f32", "fp8"])
+    p.add_argument("--form", default="bf16_skip", choices=list(FORMS))
     p.add_argument("--f32-steps", type=int, default=16, help="steps of the FP32 plain form measured beside")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -121,15 +129,33 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- GPU arm
 
-def setup_renderer(sc, cams, layers, form, profile=False):
+def proposal_params(sc, cams):
+    """Weights of the ray-interval proposal for this workload: the committed
+    file, else trained now from the renderer's own labels (a smaller run)."""
+    from paper_2202_05628_gb300 import proposal as prop
+    if os.path.exists(PROPOSAL):
+        return prop.load(PROPOSAL)[0]
+    import scenegen as sg
+    print("bench: proposal weights missing, training a small one", file=sys.stderr)
+    r = setup_renderer(sc, cams, None, "bf16")
+    X, Y = prop.collect(r, [sg.random_pose(k) for k in range(400)], list(range(len(cams))), cams, 4096,
+                        views_per_pose=2)
+    r.close()
+    return prop.train(X, Y, steps=1500, batch=16384)
+
+
+def setup_renderer(sc, cams, layers, form, profile=False, proposal=None):
     import paper_2202_05628_gb300 as art
+    storage, net, skip, _ = FORMS[form]
     oc = sc.octree
     r = art.Renderer()
-    storage = "f32" if form == "f32" else "bf16"
     r.load_octree(oc.depth, oc.origin, oc.extent, oc.ijk, oc.joint_idx, oc.weights, oc.features, oc.density, storage)
     r.load_skeleton(sc.skeleton.parent, sc.skeleton.rest)
-    r.load_shader(art.ART_NET_UNET, oc.C, [32, 64, 128, 256], 4, art.flat_params(layers), form)
-    r.set_config(tau=1e-4, profile=profile)
+    if layers is not None:
+        r.load_shader(art.ART_NET_UNET, oc.C, [32, 64, 128, 256], 4, art.flat_params(layers), net)
+    if skip:
+        r.load_proposal(proposal if proposal is not None else proposal_params(sc, cams))
+    r.set_config(tau=1e-4, profile=profile, skip=int(skip), max_missed=1e-3, margin=1)
     for v, c in enumerate(cams):
         r.set_camera(v, c.W, c.H, c.fx, c.fy, c.cx, c.cy, c.world_to_cam, c.near, c.far)
     return r
@@ -167,22 +193,28 @@ def timed_region(r, poses, steps, warmup, flush, rgba):
     return ms, launches
 
 
-def roofline(kt, stats, peaks, form, n_vox, C):
-    """Achieved rate of the dominant kernel from its measured launch times."""
+def roofline(kt, stats, peaks, form, n_vox, C, frames):
+    """Achieved rate of the dominant kernel from its measured launch times.
+    Algorithmic work: U-Net FLOPs per frame spread over the convolution
+    launches of a frame; composite bytes = per instance (key, value, 64-B
+    unit-cube record, pixel rectangle, feature row) + per pixel (F row, A)."""
+    storage, net, _, _ = FORMS[form]
     name, (nl, tot) = max(kt.items(), key=lambda kv: kv[1][1])
     avg_ms = tot / max(nl, 1)
     out = {"kernel": name, "launches": nl, "avg_ms": avg_ms}
     if name.startswith("conv"):
-        flops = unet_flops(RES, RES)
-        per_launch = flops / 15.0  # the U-Net issues 15 convolution launches per frame
+        per_launch = unet_flops(RES, RES) * frames / max(nl, 1)
         ach = per_launch / (avg_ms * 1e-3) / 1e12
-        peak = peaks.get("bf16_tflops_sustained" if form == "bf16" else "bf16_tflops", 1713.7)
-        if form == "f32":
-            peak = 2.0 * 152 * 128 * 2.07e9 / 1e12  # FP32 FMA issue rate (CUDA cores)
-        out.update(bound="tensor" if form == "bf16" else "alu", achieved=ach, peak=peak, unit="TFLOP/s",
-                   frac=ach / peak, traffic=None)
+        bf16 = peaks.get("bf16_tflops_sustained", 1713.7)
+        if net == "f32":
+            peak, bound, note = 2.0 * 152 * 128 * 2.07e9 / 1e12, "alu", "FP32 FMA issue rate of the CUDA cores"
+        elif net == "fp8":
+            peak, bound, note = 2.0 * bf16, "tensor", "measured sustained BF16 x 2 (nominal FP8 / BF16 ratio)"
+        else:
+            peak, bound, note = bf16, "tensor", "measured sustained BF16"
+        out.update(bound=bound, achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak, traffic=None, peak_is=note)
     else:
-        fb = 2 if form == "bf16" else 4
+        fb = 2 if storage == "bf16" else 4
         inst = stats["instances"]
         per_inst = 4 + 4 + 64 + 8 + C * fb
         byts = inst * per_inst + RES * RES * (C * fb + 4)
@@ -190,7 +222,8 @@ def roofline(kt, stats, peaks, form, n_vox, C):
             byts = n_vox * 160
         ach = byts / (avg_ms * 1e-3) / 1e9
         peak = peaks.get("hbm_gbs", 6783.5)
-        out.update(bound="hbm", achieved=ach, peak=peak, unit="GB/s", frac=ach / peak, traffic=None)
+        out.update(bound="hbm", achieved=ach, peak=peak, unit="GB/s", frac=ach / peak, traffic=None,
+                   peak_is="measured copy bandwidth")
     return out
 
 
@@ -263,7 +296,8 @@ def gpu_arm(args):
     rgba = torch.empty((RES, RES, 4), dtype=torch.float32, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    r = setup_renderer(sc, cams, layers, args.form, profile=True)
+    prop = proposal_params(sc, cams)
+    r = setup_renderer(sc, cams, layers, args.form, profile=True, proposal=prop)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -280,21 +314,34 @@ def gpu_arm(args):
     else:
         t_max = t_local
     value = world * args.steps / (t_max * 1e-3)
+    storage, net, skip, desc = FORMS[args.form]
     result = {
         "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16" if args.form == "bf16" else "f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": net, "data": "synthetic",
         "config": {"workload": WORKLOAD, "voxels": oc.n, "resolution": [RES, RES], "features": oc.C,
-                   "form": "BF16 features + BF16 tensor-core U-Net (plain traversal)" if args.form == "bf16"
-                   else "FP32 plain", "poses": "60-frame walk cycle x 8 azimuths",
+                   "form": desc, "poses": "60-frame walk cycle x 8 azimuths",
                    "l2": "flushed between timed frames (256 MB write outside the events)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
-        "roofline": roofline(kt, stats, peaks, args.form, oc.n, oc.C),
+        "roofline": roofline(kt, stats, peaks, args.form, oc.n, oc.C, args.steps),
         "kernels_ms_per_frame": {k: round(v[1] / args.steps, 4) for k, v in sorted(kt.items(), key=lambda kv: -kv[1][1])},
         "instances": stats["instances"], "overflow": stats["status"],
     }
+    if skip:  # fallback share over the walk cycle (untimed pass, one status read per frame)
+        n_fb = n_act = 0
+        tw = (RES + 7) // 8
+        for k in range(N_POSES):
+            pi, vi = step_indices(k)
+            p = poses[pi]
+            r.render_frame(vi, p.axis_angle, p.R, p.T, rgba)
+            n_fb += r.sync_status(raise_on_overflow=False)["fallback_tiles"]
+            rg = r.debug_buffer(7, np.uint32).reshape(-1, 2)[:tw * ((RES + 3) // 4)]
+            n_act += int(np.sum(rg[:, 1] > rg[:, 0]))
+        result["skip"] = {"fallback_tiles_per_frame": n_fb / N_POSES, "active_tiles_per_frame": n_act / N_POSES,
+                          "fallback_frac": n_fb / max(n_act, 1), "max_missed": 1e-3, "margin_bins": 1,
+                          "proposal": os.path.relpath(PROPOSAL, ROOT) if os.path.exists(PROPOSAL) else "trained in run"}
     frames = {}  # RGBA of the frame that the oracle also renders, per form
 
     def first_frame(rr, form):
@@ -308,23 +355,26 @@ def gpu_arm(args):
     r.close()
 
     def side(form, steps):
-        rr = setup_renderer(sc, cams, layers, form)
+        rr = setup_renderer(sc, cams, layers, form, proposal=prop, profile=True)
         ms_s, _ = timed_region(rr, poses, steps, 3, flush, rgba)
+        kts = rr.kernel_times(reset=True)
         first_frame(rr, form)
         rr.close()
-        return {"value": 1e3 * steps / float(np.sum(ms_s)), "ms_per_step": float(np.mean(ms_s)), "steps": steps}
+        top = sorted(kts.items(), key=lambda kv: -kv[1][1])[:4]
+        return {"value": 1e3 * steps / float(np.sum(ms_s)), "ms_per_step": float(np.mean(ms_s)), "steps": steps,
+                "form": FORMS[form][3], "top_kernels_ms_per_frame": {k: round(v[1] / steps, 4) for k, v in top}}
 
     # the other forms beside it (same workload, fewer frames)
     if args.form != "f32" and args.f32_steps > 0:
         result["f32_plain"] = side("f32", args.f32_steps)
     if args.side_steps > 0:
-        for form in ("bf16", "fp8"):
-            if form != args.form:
+        for form in FORMS:
+            if form not in (args.form, "f32"):
                 result[form + "_form"] = side(form, args.side_steps)
         result["backward"] = backward_timing(sc, cams, poses, layers, args.side_steps, flush)
     # end to end through the public call with host buffers
     if not args.no_e2e:
-        r = setup_renderer(sc, cams, layers, args.form)
+        r = setup_renderer(sc, cams, layers, args.form, proposal=prop)
         host_out = torch.empty((RES, RES, 4), dtype=torch.float32, pin_memory=True)
         host_pose = [(torch.from_numpy(p.axis_angle).pin_memory(), torch.from_numpy(p.R).pin_memory(),
                       torch.from_numpy(p.T).pin_memory()) for p in poses]

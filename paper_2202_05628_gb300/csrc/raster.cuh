@@ -9,7 +9,7 @@
 
 namespace art {
 
-constexpr int kPend = 12;  // reorder-buffer depth per pixel
+constexpr int kPend = 16;  // reorder-buffer depth per pixel
 
 // Optional per-pixel record of the composited hits (inspection only).
 struct HitLog {

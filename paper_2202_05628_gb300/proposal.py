@@ -31,31 +31,30 @@ N_PARAMS = sum(o * i + o for o, i in SHAPES)
 _MAGIC = b"ARTPROP1"
 
 
-def ray_dirs(cam, device="cuda"):
-    """Unit world-space ray directions of every pixel centre, [H*W, 3]."""
+def encode_rays(axis_angle, cam, pix, device="cuda"):
+    """Proposal inputs of the pixels ``pix`` (flat indices y * W + x) of
+    `cam` under the pose, [len(pix), 107] FP32."""
     import torch
     H, W = cam.H, cam.W
-    ys, xs = torch.meshgrid(torch.arange(H, device=device, dtype=torch.float64),
-                            torch.arange(W, device=device, dtype=torch.float64), indexing="ij")
+    pix = torch.as_tensor(pix, device=device).long()
+    pose = torch.as_tensor(np.asarray(axis_angle, np.float32).reshape(-1), device=device)
+    xs = (pix % W).double()
+    ys = (pix // W).double()
     dc = torch.stack([(xs + 0.5 - cam.cx) / cam.fx, (ys + 0.5 - cam.cy) / cam.fy, torch.ones_like(xs)], -1)
     R = torch.as_tensor(np.asarray(cam.world_to_cam, np.float64)[:, :3], device=device)
-    d = dc.reshape(-1, 3) @ R  # R^T dc for each row
-    return (d / d.norm(dim=1, keepdim=True)).float()
+    d = dc @ R  # R^T dc for each row
+    d = (d / d.norm(dim=1, keepdim=True)).float()
+    u = ((xs.float() + 0.5) / W).reshape(-1, 1)
+    v = ((ys.float() + 0.5) / H).reshape(-1, 1)
+    fr = math.pi * (2.0 ** torch.arange(8, device=device, dtype=torch.float32))[None, :]
+    four = torch.cat([torch.sin(fr * u), torch.cos(fr * u), torch.sin(fr * v), torch.cos(fr * v)], 1)
+    return torch.cat([pose[None, :].expand(pix.numel(), 72), d, four], 1)
 
 
 def encode(axis_angle, cam, device="cuda"):
     """Proposal inputs of every pixel of `cam` under the pose, [H*W, 107] FP32."""
     import torch
-    H, W = cam.H, cam.W
-    pose = torch.as_tensor(np.asarray(axis_angle, np.float32).reshape(-1), device=device)
-    d = ray_dirs(cam, device)
-    ys, xs = torch.meshgrid(torch.arange(H, device=device, dtype=torch.float32),
-                            torch.arange(W, device=device, dtype=torch.float32), indexing="ij")
-    u = ((xs + 0.5) / W).reshape(-1, 1)
-    v = ((ys + 0.5) / H).reshape(-1, 1)
-    fr = math.pi * (2.0 ** torch.arange(8, device=device, dtype=torch.float32))[None, :]
-    four = torch.cat([torch.sin(fr * u), torch.cos(fr * u), torch.sin(fr * v), torch.cos(fr * v)], 1)
-    return torch.cat([pose[None, :].expand(H * W, 72), d, four], 1)
+    return encode_rays(axis_angle, cam, torch.arange(cam.H * cam.W, device=device), device)
 
 
 def init_params(seed: int = 0) -> np.ndarray:
@@ -98,35 +97,39 @@ def _flat(module) -> np.ndarray:
 
 
 def collect(renderer, poses: Sequence, views: Sequence[int], cams: Sequence, rays_per_view: int = 8192,
-            seed: int = 0, active_only: bool = True):
-    """Labels of the plain renderer: for every (pose, view), a random sample
-    of the rays of tiles that hold instances (or all rays), their inputs and
-    label bins.  Returns (X [M,107] FP32, Y [M,2] int64) on the device."""
+            seed: int = 0, views_per_pose: int = 0):
+    """Labels of the plain renderer: for every pose and view (or
+    ``views_per_pose`` random views of each pose), a random sample of the
+    rays of the screen tiles around the animal (tiles holding a significant
+    hit, grown by one tile), their inputs and label bins.  Returns
+    (X [M,107] FP32, Y [M,2] int64) on the device."""
     import torch
+    import torch.nn.functional as Fn
     g = torch.Generator(device="cuda").manual_seed(seed)
+    rng = np.random.default_rng(seed)
     Xs, Ys = [], []
     for p in poses:
         renderer.set_pose(p.axis_angle, p.R, p.T)
-        for vi in views:
+        vsel = list(views) if not views_per_pose else list(rng.choice(list(views), views_per_pose, replace=False))
+        for vi in vsel:
             cam = cams[vi]
-            bins = torch.zeros((cam.H, cam.W, 2), dtype=torch.uint8, device="cuda")
-            lab = torch.empty((cam.H, cam.W, 3), dtype=torch.float32, device="cuda")
+            H, W = cam.H, cam.W
+            bins = torch.zeros((H, W, 2), dtype=torch.uint8, device="cuda")
+            lab = torch.empty((H, W, 3), dtype=torch.float32, device="cuda")
             renderer.render_labels(vi, lab, bins)
-            b = bins.reshape(-1, 2).long()
-            if active_only:
-                hist = torch.as_tensor(renderer.debug_buffer(12, np.float32), device="cuda")
-                tw, th = (cam.W + 7) // 8, (cam.H + 3) // 4
-                act_t = hist[:tw * th * N_BINS].reshape(th, tw, N_BINS).sum(-1) > 0
-                act = act_t.repeat_interleave(4, 0).repeat_interleave(8, 1)[:cam.H, :cam.W].reshape(-1)
-                idx = torch.nonzero(act).reshape(-1)
-            else:
-                idx = torch.arange(cam.H * cam.W, device="cuda")
+            th, tw = (H + 3) // 4, (W + 7) // 8
+            sig = torch.zeros((th * 4, tw * 8), dtype=torch.float32, device="cuda")
+            sig[:H, :W] = torch.isfinite(lab[..., 0]).float()
+            t = sig.reshape(th, 4, tw, 8).amax((1, 3))
+            t = Fn.max_pool2d(t[None, None], 3, stride=1, padding=1)[0, 0] > 0
+            act = t.repeat_interleave(4, 0).repeat_interleave(8, 1)[:H, :W].reshape(-1)
+            idx = torch.nonzero(act).reshape(-1)
             if idx.numel() == 0:
                 continue
             pick = idx[torch.randint(0, idx.numel(), (min(rays_per_view, idx.numel()),), generator=g, device="cuda")]
-            X = encode(p.axis_angle, cam)[pick]
-            Xs.append(X)
-            Ys.append(b[pick])
+            Xs.append(encode_rays(p.axis_angle, cam, pick))
+            Ys.append(bins.reshape(-1, 2)[pick].long())
+    collect.overflow_order = renderer.sync_status(raise_on_overflow=False)["overflow_order"]
     return torch.cat(Xs), torch.cat(Ys)
 
 
@@ -188,3 +191,91 @@ def load(path: str) -> Tuple[np.ndarray, str]:
     if p.size != N_PARAMS:
         raise ValueError(f"{path}: {p.size} parameters, {N_PARAMS} expected")
     return p, meta
+
+
+def evaluate(renderer, params, poses, cams, margin: int = 1, max_missed: float = 1e-3) -> dict:
+    """Learned skip against the plain render on held-out poses (one view per
+    pose, cycling): fallback tiles / active tiles, and the largest
+    difference of F and A."""
+    import torch
+    renderer.load_proposal(params)
+    renderer.sync_status(raise_on_overflow=False)  # clear earlier flags
+    n_fb = n_act = n_over = 0
+    dF = dA = 0.0
+    C = renderer.C
+    for k, p in enumerate(poses):
+        vi = k % len(cams)
+        cam = cams[vi]
+        F0 = torch.empty((cam.H, cam.W, C), dtype=torch.float32, device="cuda")
+        A0 = torch.empty((cam.H, cam.W), dtype=torch.float32, device="cuda")
+        F1, A1 = torch.empty_like(F0), torch.empty_like(A0)
+        renderer.set_pose(p.axis_angle, p.R, p.T)
+        renderer.set_config(skip=0)
+        renderer.render_feature_maps(vi, F0, A0)
+        renderer.set_config(skip=1, max_missed=max_missed, margin=margin)
+        renderer.render_feature_maps(vi, F1, A1)
+        st = renderer.sync_status(raise_on_overflow=False)
+        n_over += st["overflow_order"]
+        rg = renderer.debug_buffer(7, np.uint32).reshape(-1, 2)[:((cam.W + 7) // 8) * ((cam.H + 3) // 4)]
+        n_act += int(np.sum(rg[:, 1] > rg[:, 0]))
+        n_fb += st["fallback_tiles"]
+        dF = max(dF, torch.abs(F1 - F0).max().item())
+        dA = max(dA, torch.abs(A1 - A0).max().item())
+    renderer.set_config(skip=0)
+    return {"fallback_tiles": n_fb, "active_tiles": n_act, "fallback_frac": n_fb / max(n_act, 1), "max_dF": dF,
+            "max_dA": dA, "reorder_overflows": n_over}
+
+
+def main(argv=None) -> None:
+    """Train the proposal for a synthetic workload of ``scenegen`` and write
+    the weights file: labels over random poses (each joint up to 30 deg)
+    seen from the workload's orbit cameras, evaluation on held-out poses."""
+    import argparse
+    import json
+    import os
+    import sys
+    import time
+    p = argparse.ArgumentParser(description=main.__doc__)
+    p.add_argument("--preset", default="paper")
+    p.add_argument("--res", type=int, default=1024)
+    p.add_argument("--azimuths", type=int, default=8)
+    p.add_argument("--poses", type=int, default=2000)
+    p.add_argument("--views-per-pose", type=int, default=2)
+    p.add_argument("--rays", type=int, default=4096, help="rays sampled per (pose, view)")
+    p.add_argument("--steps", type=int, default=4000)
+    p.add_argument("--batch", type=int, default=16384)
+    p.add_argument("--eval-poses", type=int, default=200)
+    p.add_argument("--out", required=True)
+    a = p.parse_args(argv)
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    import scenegen as sg
+    from . import Renderer, flat_params  # noqa: F401  (the library must load)
+    t0 = time.time()
+    sc = sg.preset(a.preset)
+    oc = sc.octree
+    cams = [sg.orbit_camera(sc.centroid, a.res, a.res, az_deg=360.0 / a.azimuths * k) for k in range(a.azimuths)]
+    r = Renderer()
+    r.load_octree(oc.depth, oc.origin, oc.extent, oc.ijk, oc.joint_idx, oc.weights, oc.features, oc.density, "bf16")
+    r.load_skeleton(sc.skeleton.parent, sc.skeleton.rest)
+    r.set_config()
+    for k, c in enumerate(cams):
+        r.set_camera(k, c.W, c.H, c.fx, c.fy, c.cx, c.cy, c.world_to_cam, c.near, c.far)
+    train_poses = [sg.random_pose(k) for k in range(a.poses)]
+    X, Y = collect(r, train_poses, list(range(len(cams))), cams, a.rays, seed=0, views_per_pose=a.views_per_pose)
+    t1 = time.time()
+    params = train(X, Y, steps=a.steps, batch=a.batch, lr=2e-3)
+    t2 = time.time()
+    acc = accuracy(params, X, Y)
+    held = [sg.random_pose(100000 + k) for k in range(a.eval_poses)]
+    ev = evaluate(r, params, held, cams)
+    walk = evaluate(r, params, [sg.walk_pose(f, 60) for f in range(60)], cams)
+    meta = {"preset": a.preset, "res": a.res, "azimuths": a.azimuths, "train_poses": a.poses,
+            "samples": int(X.shape[0]), "label_reorder_overflows": int(collect.overflow_order), "steps": a.steps, "train_acc_near_far_cover": acc,
+            "held_out": ev, "walk_cycle": walk, "label_s": round(t1 - t0, 1), "train_s": round(t2 - t1, 1)}
+    save(a.out, params, json.dumps(meta))
+    print(json.dumps(meta))
+
+
+if __name__ == "__main__":
+    main()
