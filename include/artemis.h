@@ -283,6 +283,8 @@ typedef struct {
   float max_missed;        /* learned skip: coarse-check threshold of lost transmittance mass
                               (0 = default 1e-3); a tile with a ray above it is traversed again in full */
   int margin;              /* learned skip: bins added on both sides of the predicted interval (default 0) */
+  int segment;             /* composite: a tile's list is walked in segments of about this many entries by
+                              separate warps and merged front to back (0 = default 256; >= 32) */
 } art_config;
 
 #define ART_SKIP_PLAIN 0

@@ -172,7 +172,8 @@ void free_all(art_ctx* ctx) {
                   ctx->d_keys[0], ctx->d_keys[1], ctx->d_vals[0], ctx->d_vals[1], ctx->d_hist, ctx->d_ranges,
                   ctx->d_status, ctx->d_F, ctx->d_A, ctx->d_rgba, ctx->d_act, ctx->d_sk, ctx->d_sv,
                   ctx->d_shist, ctx->d_sbsum, ctx->d_gN, ctx->d_f8_scale, ctx->d_f8_amax, ctx->d_prop_img,
-                  ctx->d_prop_f32, ctx->d_pose_bias, ctx->d_bins, ctx->d_thist, ctx->d_hbin, ctx->d_htau, ctx->d_fbq};
+                  ctx->d_prop_f32, ctx->d_pose_bias, ctx->d_bins, ctx->d_thist, ctx->d_hbin, ctx->d_htau, ctx->d_fbq,
+                  ctx->d_seg, ctx->d_items, ctx->d_multi, ctx->d_part};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& L : ctx->layers) {
@@ -199,6 +200,7 @@ art_config default_config() {
   c.skip = ART_SKIP_PLAIN;
   c.max_missed = 1e-3f;
   c.margin = 0;
+  c.segment = 256;
   return c;
 }
 
@@ -243,6 +245,25 @@ art_status ensure_skip_buffers(art_ctx* ctx, const ViewParams& v) {
   if ((st = ensure(ctx, (void**)&ctx->d_bins, &ctx->d_bins_bytes, (size_t)v.W * v.H * 2, "proposal bins")) != ART_OK)
     return st;
   cudaMemsetAsync(ctx->d_thist, 0, ntiles * kPropBins * 4, ctx->stream);
+  return ART_OK;
+}
+
+// Buffers of the split composite walk for `view`: per-tile plan, segment
+// lists and partial sums (segments <= instances / seg_len + tiles).
+art_status ensure_split_buffers(art_ctx* ctx, const ViewParams& v) {
+  art_status st;
+  const size_t ntiles = (size_t)v.tiles_x * v.tiles_y;
+  const size_t items = (size_t)(ctx->inst_cap / ctx->seg_len) + ntiles + 1;
+  if ((st = ensure(ctx, (void**)&ctx->d_seg, &ctx->d_seg_bytes, ntiles * sizeof(uint2), "segment plan")) != ART_OK)
+    return st;
+  if ((st = ensure(ctx, (void**)&ctx->d_multi, &ctx->d_multi_bytes, ntiles * 4, "split tiles")) != ART_OK) return st;
+  if ((st = ensure(ctx, (void**)&ctx->d_items, &ctx->d_items_bytes, items * 4, "segments")) != ART_OK) return st;
+  if ((st = ensure(ctx, (void**)&ctx->d_part, &ctx->d_part_bytes, items * (ctx->C + 1) * 32 * sizeof(float),
+                   "segment partial sums")) != ART_OK)
+    return st;
+  if ((st = ensure(ctx, (void**)&ctx->d_fbq, &ctx->d_fbq_bytes, ntiles * 4, "fallback queue")) != ART_OK) return st;
+  const int fb = ctx->feat_dtype == ART_F32 ? 4 : 2;
+  ctx->composite_blocks = ctx->num_sms * composite_blocks_per_sm(ctx->C, fb);
   return ART_OK;
 }
 
@@ -307,7 +328,10 @@ art_status art_set_config(art_ctx* ctx, const art_config* cfg) {
   if (c.max_missed == 0.0f) c.max_missed = 1e-3f;
   if (!(c.max_missed > 0.0f && c.max_missed < 1.0f)) return fail(ctx, ART_ERR_INVALID_ARG, "max_missed must be in (0, 1)");
   if (c.margin < 0 || c.margin > 63) return fail(ctx, ART_ERR_INVALID_ARG, "margin must be in [0, 63]");
+  if (c.segment == 0) c.segment = 256;
+  if (c.segment < 32 || c.segment > (1 << 24)) return fail(ctx, ART_ERR_INVALID_ARG, "segment must be in [32, 2^24]");
   ctx->cfg = c;
+  ctx->seg_len = c.segment;
   return ART_OK;
 }
 
@@ -434,6 +458,7 @@ art_status art_set_pose(art_ctx* ctx, const float* axis_angle, const float R[3],
     ctx->jidx_ok = true;
   }
   cudaMemsetAsync(ctx->d_status + kStDegenerate, 0, sizeof(unsigned long long), ctx->stream);
+  cudaMemsetAsync(ctx->d_status + kStRmax, 0, sizeof(unsigned long long), ctx->stream);
   launch_fk(ctx);
   launch_lbs(ctx);
   if (ctx->prop_loaded) launch_pose_bias(ctx);
@@ -535,6 +560,7 @@ static art_status render_to_device(art_ctx* ctx, int view, void* F, int F_dtype,
   const ViewParams& v = ctx->views[view];
   art_status st = ensure_bin_buffers(ctx, (int64_t)v.tiles_x * v.tiles_y);
   if (st != ART_OK) return st;
+  if ((st = ensure_split_buffers(ctx, v)) != ART_OK) return st;
   if (ctx->cfg.skip == ART_SKIP_LEARNED) {  // proposal intervals + coarse check + fallback
     if (!ctx->prop_loaded) return fail(ctx, ART_ERR_STATE, "learned skip without a proposal (art_load_proposal)");
     if ((st = ensure_skip_buffers(ctx, v)) != ART_OK) return st;

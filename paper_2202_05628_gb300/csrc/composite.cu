@@ -55,9 +55,18 @@ __device__ __forceinline__ float tile_hist_prefix(const float* __restrict__ th, 
   return pre[63];
 }
 
+// The part of a tile's list one warp walks: list positions [begin, end),
+// hits whose entry t0 lies in [t0_lo, t0_hi); with part set, the walk stores
+// its partial feature sum and transmittance there instead of the outputs.
+struct Seg {
+  uint32_t begin, end;
+  float t0_lo, t0_hi;
+  float* part;  // [C + 1][32]: partial F (per channel), then T
+};
+
 // One warp per 8x4 tile, lane = pixel (x = lane & 7, y = lane >> 3).
 template <int C, typename TF, typename TO, int MODE>
-__device__ __forceinline__ void composite_tile(const int tile, const uint2* __restrict__ ranges,
+__device__ __forceinline__ void composite_tile(const int tile, const Seg& sg,
                                                const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals,
                                                const float4* __restrict__ rec, const short4* __restrict__ rect,
                                                const TF* __restrict__ feat, const ViewParams& v, float tau,
@@ -98,7 +107,7 @@ __device__ __forceinline__ void composite_tile(const int tile, const uint2* __re
   const size_t pix = (size_t)py * v.W + px;
   int n_used = 0;
   int cur_chunk = 0;
-  const uint2 rg = ranges[tile];
+  const uint2 rg = make_uint2(sg.begin, sg.end);
   // learned skip: this pixel's interval [t_lo, t_hi] and the deepest end over the warp
   float t_lo = 0.0f, t_hi = 3.4e38f, hi_w = 3.4e38f;
   int bn = 0, bf = kPropBins - 1;
@@ -219,6 +228,7 @@ __device__ __forceinline__ void composite_tile(const int tile, const uint2* __re
       float t0, t1, e[3];
       int ax0, ax1;
       if (!slab_hit(s_b0[idx], s_b1[idx], s_b2[idx], d0, d1, d2, v.znear, v.zfar, t0, t1, ax0, ax1, e)) continue;
+      if (t0 < sg.t0_lo || t0 >= sg.t0_hi) continue;  // another segment's hit
       if constexpr (MODE == kInterval) {
         if (t1 < t_lo || t0 > t_hi) continue;  // outside this pixel's interval
       }
@@ -254,6 +264,13 @@ __device__ __forceinline__ void composite_tile(const int tile, const uint2* __re
   }
   while (nb > 0 && !done) release_front();
 
+  if (sg.part) {  // a segment of a split tile: partial sums for the merge
+#pragma unroll
+    for (int c = 0; c < C; ++c) sg.part[c * 32 + lane] = acc[c];
+    sg.part[C * 32 + lane] = T;
+    if (n_over) atomicAdd(status + kStOverflowOrder, (unsigned long long)n_over);
+    return;
+  }
   if constexpr (MODE == kLabel || MODE == kInterval) {
     __shared__ float s_pre[kPropBins];
     const float tot = tile_hist_prefix(sk.thist + (size_t)tile * kPropBins, s_pre, lane);
@@ -313,8 +330,200 @@ __global__ void __launch_bounds__(32) composite_kernel(const uint2* __restrict__
                                                        TO* __restrict__ Fout, float* __restrict__ Aout,
                                                        unsigned long long* __restrict__ status, HitLog dbg,
                                                        SkipArgs sk) {
-  composite_tile<C, TF, TO, MODE>(blockIdx.x, ranges, keys, vals, rec, rect, feat, v, tau, Fout, Aout, status, dbg,
-                                  sk);
+  const uint2 rg = ranges[blockIdx.x];
+  const Seg sg{rg.x, rg.y, -3.4e38f, 3.4e38f, nullptr};
+  composite_tile<C, TF, TO, MODE>(blockIdx.x, sg, keys, vals, rec, rect, feat, v, tau, Fout, Aout, status, dbg, sk);
+}
+
+// ------------------------------------------------------------ split walk
+//
+// A tile's list is cut at list positions p_k = start + k len / S into S
+// segments of about seg_len entries.  Segment k composites the hits whose
+// entry t0 lies in [D_k, D_{k+1}), D_k = the depth bound of the entry at p_k,
+// front to back from T = 1.  It walks positions [p'_k, p_{k+1}): an entry can
+// hold such a hit only if its distance range reaches D_k, i.e. its depth bound
+// is at least D_k - (2 r_max + 3 quanta), and p'_k is the first such position.
+// The merge combines the segments in order, F = F_0 + T_0 F_1 + T_0 T_1 F_2 ...,
+// which is the front-to-back sum regrouped.  The stop rule holds exactly in
+// the first segment that a pixel's transmittance enters below tau if that
+// pixel entered it with T = 1; otherwise its tile is queued for the plain walk.
+
+constexpr int kMaxSegs = 255;
+
+// Zero F and A of the tiles without instances (the segments cover the rest).
+template <int C, typename TO>
+__global__ void __launch_bounds__(256) composite_clear_kernel(const uint2* __restrict__ ranges, ViewParams v,
+                                                              TO* __restrict__ Fout, float* __restrict__ Aout) {
+  const int tile = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (tile >= v.tiles_x * v.tiles_y) return;
+  const uint2 rg = ranges[tile];
+  if (rg.y > rg.x) return;
+  const int px = (tile % v.tiles_x) * TSX + (lane & 7), py = (tile / v.tiles_x) * TSY + (lane >> 3);
+  if (px >= v.W || py >= v.H) return;
+  const size_t pix = (size_t)py * v.W + px;
+  float z[C];
+#pragma unroll
+  for (int c = 0; c < C; ++c) z[c] = 0.0f;
+  store_row<C>(Fout + pix * C, z);
+  if (Aout) Aout[pix] = 0.0f;
+}
+
+// Per tile: number of segments and the index of its first one; the segments
+// of all tiles in one list, the tiles with two or more in another.
+__global__ void seg_plan_kernel(int ntiles, const uint2* __restrict__ ranges, int seg_len, uint2* __restrict__ seg,
+                                uint32_t* __restrict__ items, uint32_t* __restrict__ multi,
+                                unsigned long long* __restrict__ status) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ntiles) return;
+  const uint2 rg = ranges[t];
+  const uint32_t len = rg.y - rg.x;
+  uint32_t S = len == 0 ? 0u : (len + seg_len - 1) / seg_len;
+  if (S > kMaxSegs) S = kMaxSegs;
+  uint32_t base = 0;
+  if (S) {
+    base = (uint32_t)atomicAdd(status + kStItems, (unsigned long long)S);
+    for (uint32_t k = 0; k < S; ++k) items[base + k] = (uint32_t)t;
+    if (S > 1) multi[atomicAdd(status + kStMulti, 1ull)] = (uint32_t)t;
+  }
+  seg[t] = make_uint2(base, S);
+}
+
+// First position in [a, b) whose depth quantum is >= qt (b if none): keys are
+// sorted within the tile.  Warp-cooperative: 32 probes per round.
+__device__ __forceinline__ uint32_t lower_bound_q(const uint32_t* __restrict__ keys, uint32_t a, uint32_t b,
+                                                  uint32_t qmask, uint32_t qt, int lane) {
+  while (b - a > 31u) {
+    const uint32_t step = (b - a + 31u) / 32u;
+    const uint32_t idx = a + (uint32_t)lane * step;
+    const bool ge = idx >= b || (keys[idx] & qmask) >= qt;
+    const uint32_t m = __ballot_sync(0xffffffffu, ge);
+    if (m & 1u) return a;
+    const uint32_t f = m ? (uint32_t)(__ffs(m) - 1) : 32u;
+    const uint32_t na = a + (f - 1u) * step + 1u;
+    const uint32_t nb = f < 32u ? min(b, a + f * step) : b;
+    a = na;
+    b = nb;
+  }
+  const uint32_t idx = a + (uint32_t)lane;
+  const bool ge = idx >= b || (keys[idx] & qmask) >= qt;
+  const uint32_t m = __ballot_sync(0xffffffffu, ge);
+  return a + (uint32_t)(__ffs(m) - 1);  // lane b - a (<= 31) is always set
+}
+
+template <int C, typename TF, typename TO, int MODE>
+__global__ void __launch_bounds__(32) composite_split_kernel(
+    const uint2* __restrict__ ranges, const uint2* __restrict__ seg, const uint32_t* __restrict__ items,
+    const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals, const float4* __restrict__ rec,
+    const short4* __restrict__ rect, const TF* __restrict__ feat, ViewParams v, float tau, TO* __restrict__ Fout,
+    float* __restrict__ Aout, unsigned long long* __restrict__ status, float* __restrict__ part, SkipArgs sk) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t qmask = (1u << v.depth_bits) - 1u;
+  const float qinv = 1.0f / v.dscale;
+  const unsigned long long n_items = status[kStItems];
+  // window in depth quanta: 2 r_max + 3 quanta (+ FP32 slack)
+  const float rmax = __uint_as_float((uint32_t)status[kStRmax]);
+  const uint32_t wq = (uint32_t)ceilf((2.0f * rmax + 1e-5f) * v.dscale) + 3u;
+  for (;;) {
+    unsigned long long i = 0;
+    if (lane == 0) i = atomicAdd(status + kStNext, 1ull);
+    i = __shfl_sync(0xffffffffu, i, 0);
+    if (i >= n_items) break;
+    const int tile = (int)items[i];
+    const uint2 sgt = seg[tile];
+    const uint32_t k = (uint32_t)i - sgt.x, S = sgt.y;
+    const uint2 rg = ranges[tile];
+    const uint32_t len = rg.y - rg.x;
+    const uint32_t pk = rg.x + (uint32_t)(((unsigned long long)k * len) / S);
+    const uint32_t pk1 = rg.x + (uint32_t)(((unsigned long long)(k + 1) * len) / S);
+    Seg sg;
+    sg.end = pk1;
+    if (k == 0) {
+      sg.begin = rg.x;
+      sg.t0_lo = -3.4e38f;
+    } else {
+      const uint32_t qk = keys[pk] & qmask;
+      sg.t0_lo = v.znear + (float)qk * qinv;
+      sg.begin = lower_bound_q(keys, rg.x, pk, qmask, qk > wq ? qk - wq : 0u, lane);
+    }
+    sg.t0_hi = k + 1 < S ? v.znear + (float)(keys[pk1] & qmask) * qinv : 3.4e38f;
+    sg.part = S > 1 ? part + (size_t)i * (C + 1) * 32 : nullptr;
+    composite_tile<C, TF, TO, MODE>(tile, sg, keys, vals, rec, rect, feat, v, tau, Fout, Aout, status, HitLog{},
+                                    sk);
+  }
+}
+
+// Merge of the segments of the tiles with two or more: outputs, the coarse
+// check of the learned skip, and the fallback queue.
+template <int C, typename TO, int MODE>
+__global__ void __launch_bounds__(32) composite_merge_kernel(const uint2* __restrict__ seg,
+                                                             const uint32_t* __restrict__ multi, ViewParams v,
+                                                             float tau, TO* __restrict__ Fout,
+                                                             float* __restrict__ Aout,
+                                                             unsigned long long* __restrict__ status,
+                                                             const float* __restrict__ part, SkipArgs sk) {
+  const int lane = threadIdx.x & 31;
+  const unsigned long long n_multi = status[kStMulti];
+  for (;;) {
+    unsigned long long m = 0;
+    if (lane == 0) m = atomicAdd(status + kStNextMerge, 1ull);
+    m = __shfl_sync(0xffffffffu, m, 0);
+    if (m >= n_multi) break;
+    const int tile = (int)multi[m];
+    const uint2 sgt = seg[tile];
+    const int tx = tile % v.tiles_x, ty = tile / v.tiles_x;
+    const int px = tx * TSX + (lane & 7), py = ty * TSY + (lane >> 3);
+    const bool inside = px < v.W && py < v.H;
+    float acc[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) acc[c] = 0.0f;
+    float T = 1.0f;
+    bool stopped = false, redo = false;
+    for (uint32_t k = 0; k < sgt.y; ++k) {
+      const float* pp = part + (size_t)(sgt.x + k) * (C + 1) * 32;
+      const float Tk = pp[C * 32 + lane];
+      if (stopped) break;
+      if (T < 1.0f && T * Tk < tau) redo = true;  // the stop falls inside a later segment
+#pragma unroll
+      for (int c = 0; c < C; ++c) acc[c] = fmaf(T, pp[c * 32 + lane], acc[c]);
+      T *= Tk;
+      if (T < tau) stopped = true;
+    }
+    bool fail = false;
+    if constexpr (MODE == kInterval) {  // coarse check of the lost mass over the tile's union interval
+      __shared__ float s_pre[kPropBins];
+      const float tot = tile_hist_prefix(sk.thist + (size_t)tile * kPropBins, s_pre, lane);
+      int lo_b = kPropBins, hi_b = -1;
+      if (inside) {
+        const uchar2 b = sk.bins[(size_t)py * v.W + px];
+        if (b.y >= b.x) {
+          lo_b = b.x;
+          hi_b = b.y;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        lo_b = min(lo_b, __shfl_xor_sync(0xffffffffu, lo_b, o));
+        hi_b = max(hi_b, __shfl_xor_sync(0xffffffffu, hi_b, o));
+      }
+      const bool empty = hi_b < lo_b;
+      const int bn = empty ? lo_b : max(lo_b - sk.margin, 0);
+      const int bf = empty ? hi_b : min(hi_b + sk.margin, kPropBins - 1);
+      if (inside) {
+        const float front = empty ? tot : (bn > 0 ? s_pre[bn - 1] : 0.0f);
+        const float back = empty ? 0.0f : tot - s_pre[bf];
+        fail = -expm1f(-front) + T * -expm1f(-back) > sk.max_missed;
+      }
+    }
+    if (inside) {
+      const size_t pix = (size_t)py * v.W + px;
+      store_row<C>(Fout + pix * C, acc);
+      if (Aout) Aout[pix] = 1.0f - T;
+    }
+    if (__any_sync(0xffffffffu, (redo || fail) && inside) && lane == 0)
+      sk.queue[atomicAdd(status + kStFallback, 1ull)] = (uint32_t)tile;
+    __syncwarp();
+  }
 }
 
 // The plain walk over the tiles queued by the learned-skip pass.
@@ -329,9 +538,52 @@ __global__ void __launch_bounds__(32) composite_queue_kernel(const uint2* __rest
                                                              unsigned long long* __restrict__ status,
                                                              const uint32_t* __restrict__ queue) {
   const unsigned long long n = status[kStFallback];
-  for (unsigned long long i = blockIdx.x; i < n; i += gridDim.x)
-    composite_tile<C, TF, TO, kPlain>((int)queue[i], ranges, keys, vals, rec, rect, feat, v, tau, Fout, Aout, status,
-                                      HitLog{}, SkipArgs{});
+  for (unsigned long long i = blockIdx.x; i < n; i += gridDim.x) {
+    const int tile = (int)queue[i];
+    const uint2 rg = ranges[tile];
+    const Seg sg{rg.x, rg.y, -3.4e38f, 3.4e38f, nullptr};
+    composite_tile<C, TF, TO, kPlain>(tile, sg, keys, vals, rec, rect, feat, v, tau, Fout, Aout, status, HitLog{},
+                                      SkipArgs{});
+  }
+}
+
+// Plain or learned-skip composite: plan the segments, walk them with
+// persistent warps, merge the split tiles, then walk the queued tiles in full.
+template <int C, typename TF, typename TO>
+void split_walk(art_ctx* ctx, const ViewParams& v, void* F, float* A, int mode, const SkipArgs& sk_in) {
+  const int ntiles = v.tiles_x * v.tiles_y;
+  const TF* feat = (const TF*)ctx->d_feat;
+  SkipArgs sk = sk_in;
+  sk.queue = ctx->d_fbq;
+  cudaMemsetAsync(ctx->d_status + kStItems, 0, 4 * sizeof(unsigned long long), ctx->stream);  // items .. next merge
+  cudaMemsetAsync(ctx->d_status + kStFallback, 0, sizeof(unsigned long long), ctx->stream);
+  ART_LAUNCH(ctx, "composite_plan", seg_plan_kernel, (ntiles + 255) / 256, 256, 0, ntiles, ctx->d_ranges,
+             ctx->seg_len, ctx->d_seg, ctx->d_items, ctx->d_multi, ctx->d_status);
+  auto cfn = composite_clear_kernel<C, TO>;
+  ART_LAUNCH(ctx, "composite_clear", cfn, (ntiles + 7) / 8, 256, 0, ctx->d_ranges, v, (TO*)F, A);
+  const int grid = ctx->composite_blocks;
+  const bool skip = mode == kInterval;
+  if (skip) {
+    auto kfn = composite_split_kernel<C, TF, TO, kInterval>;
+    ART_LAUNCH(ctx, "composite_skip", kfn, grid, 32, 0, ctx->d_ranges, ctx->d_seg, ctx->d_items, ctx->d_keys[0],
+               ctx->d_vals[0], ctx->d_rec, ctx->d_rect, feat, v, ctx->cfg.tau, (TO*)F, A, ctx->d_status, ctx->d_part,
+               sk);
+    auto mfn = composite_merge_kernel<C, TO, kInterval>;
+    ART_LAUNCH(ctx, "composite_merge", mfn, 4 * ctx->num_sms, 32, 0, ctx->d_seg, ctx->d_multi, v, ctx->cfg.tau, (TO*)F,
+               A, ctx->d_status, ctx->d_part, sk);
+  } else {
+    auto kfn = composite_split_kernel<C, TF, TO, kPlain>;
+    ART_LAUNCH(ctx, "composite", kfn, grid, 32, 0, ctx->d_ranges, ctx->d_seg, ctx->d_items, ctx->d_keys[0],
+               ctx->d_vals[0], ctx->d_rec, ctx->d_rect, feat, v, ctx->cfg.tau, (TO*)F, A, ctx->d_status, ctx->d_part,
+               sk);
+    auto mfn = composite_merge_kernel<C, TO, kPlain>;
+    ART_LAUNCH(ctx, "composite_merge", mfn, 4 * ctx->num_sms, 32, 0, ctx->d_seg, ctx->d_multi, v, ctx->cfg.tau, (TO*)F,
+               A, ctx->d_status, ctx->d_part, sk);
+  }
+  auto qfn = composite_queue_kernel<C, TF, TO>;
+  const int qgrid = std::min(ntiles, 16 * ctx->num_sms);
+  ART_LAUNCH(ctx, "composite_fallback", qfn, qgrid, 32, 0, ctx->d_ranges, ctx->d_keys[0], ctx->d_vals[0], ctx->d_rec,
+             ctx->d_rect, feat, v, ctx->cfg.tau, (TO*)F, A, ctx->d_status, sk.queue);
 }
 
 template <int C, typename TF, typename TO>
@@ -346,18 +598,8 @@ void launch_c(art_ctx* ctx, const ViewParams& v, void* F, float* A, const HitLog
     auto kfn = composite_kernel<C, TF, TO, kLabel>;
     ART_LAUNCH(ctx, "composite_labels", kfn, ntiles, 32, 0, ctx->d_ranges, ctx->d_keys[0], ctx->d_vals[0], ctx->d_rec,
                ctx->d_rect, feat, v, ctx->cfg.tau, (TO*)F, A, ctx->d_status, HitLog{}, sk);
-  } else if (mode == kInterval) {
-    auto kfn = composite_kernel<C, TF, TO, kInterval>;
-    ART_LAUNCH(ctx, "composite_skip", kfn, ntiles, 32, 0, ctx->d_ranges, ctx->d_keys[0], ctx->d_vals[0], ctx->d_rec,
-               ctx->d_rect, feat, v, ctx->cfg.tau, (TO*)F, A, ctx->d_status, HitLog{}, sk);
-    auto qfn = composite_queue_kernel<C, TF, TO>;
-    const int qgrid = std::min(ntiles, 16 * ctx->num_sms);
-    ART_LAUNCH(ctx, "composite_fallback", qfn, qgrid, 32, 0, ctx->d_ranges, ctx->d_keys[0], ctx->d_vals[0],
-               ctx->d_rec, ctx->d_rect, feat, v, ctx->cfg.tau, (TO*)F, A, ctx->d_status, sk.queue);
   } else {
-    auto kfn = composite_kernel<C, TF, TO, kPlain>;
-    ART_LAUNCH(ctx, "composite", kfn, ntiles, 32, 0, ctx->d_ranges, ctx->d_keys[0], ctx->d_vals[0], ctx->d_rec,
-               ctx->d_rect, feat, v, ctx->cfg.tau, (TO*)F, A, ctx->d_status, HitLog{}, sk);
+    split_walk<C, TF, TO>(ctx, v, F, A, mode, sk);
   }
 }
 
@@ -403,9 +645,14 @@ art_status launch_composite_skip(art_ctx* ctx, const ViewParams& v, void* F, int
   sk.thist = ctx->d_thist;
   sk.max_missed = ctx->cfg.max_missed;
   sk.margin = ctx->cfg.margin;
-  sk.queue = ctx->d_fbq;
-  launch_set_word(ctx, ctx->d_status + kStFallback, 0ull);
   return dispatch(ctx, v, F, F_dtype, A, nullptr, kInterval, sk);
+}
+
+int composite_blocks_per_sm(int C, int feat_bytes) {
+  // one-warp blocks, limited by the staged-feature ring and the 32-block cap
+  const int ring = std::max(1, std::min(16, 12288 / (NT * C * feat_bytes)));
+  const int smem = ring * NT * (C * feat_bytes + 8) + NT * (3 * 16 + 8) + 4 * kPropBins + 64;
+  return std::max(1, std::min(32, (227 * 1024) / smem));
 }
 
 art_status launch_composite_labels(art_ctx* ctx, const ViewParams& v, float* labels, uint8_t* bins) {

@@ -27,8 +27,13 @@ enum StatusWord {
   kStOverflowInst = 2,  // instances beyond capacity (cumulative until cleared)
   kStOverflowOrder = 3, // reorder-buffer overflows (cumulative until cleared)
   kStTcError = 4,       // tensor-core convolution CTAs that timed out waiting
-  kStFallback = 5,      // learned skip: tiles queued for the full traversal (last render)
-  kStWords = 8
+  kStFallback = 5,      // tiles queued for the full traversal (last render)
+  kStItems = 8,         // composite segments planned (last render)
+  kStMulti = 9,         // tiles split into two or more segments
+  kStNext = 10,         // next segment to walk (work counter)
+  kStNextMerge = 11,    // next split tile to merge (work counter)
+  kStRmax = 12,         // largest voxel bounding radius of the last pose (float bits)
+  kStWords = 16
 };
 
 // Per-view camera, with host-precomputed ray frame.
@@ -153,6 +158,17 @@ struct art_ctx {
   int64_t hist_n_cap = 0;
   uint32_t* d_fbq = nullptr;      // [tiles] fallback queue
   size_t d_fbq_bytes = 0;
+  // ---- split composite walk
+  int seg_len = 256;              // list entries per segment
+  int composite_blocks = 0;       // persistent one-warp blocks of the split walk
+  uint2* d_seg = nullptr;         // [tiles] (first segment, segment count)
+  size_t d_seg_bytes = 0;
+  uint32_t* d_items = nullptr;    // [segments] tile of each segment
+  size_t d_items_bytes = 0;
+  uint32_t* d_multi = nullptr;    // [tiles] tiles with two or more segments
+  size_t d_multi_bytes = 0;
+  float* d_part = nullptr;        // [segments][C + 1][32] partial sums
+  size_t d_part_bytes = 0;
   // ---- backward
   float* d_gN = nullptr;        // [n][12] dL/d(A_i^-1) accumulator
   int64_t gN_cap = 0;
@@ -213,6 +229,8 @@ art_status launch_composite(art_ctx* ctx, const ViewParams& v, void* F, int F_dt
 art_status launch_composite_skip(art_ctx* ctx, const ViewParams& v, void* F, int F_dtype, float* A);
 // Labels of the plain composite (labels [H][W][3], bins [H][W][2]; either may be null).
 art_status launch_composite_labels(art_ctx* ctx, const ViewParams& v, float* labels, uint8_t* bins);
+// One-warp blocks of the composite walk that fit on an SM (C channels of feat_bytes).
+int composite_blocks_per_sm(int C, int feat_bytes);
 constexpr int kPropBins = 64;          // proposal depth bins over [znear, zfar]
 constexpr float kLabelWmin = 1e-6f;    // significant hit: weight above this
 constexpr float kLabelBudget = 0.4f;   // label bins keep the coarse bound under this fraction of max_missed

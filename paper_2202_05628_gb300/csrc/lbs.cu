@@ -83,6 +83,7 @@ __global__ void __launch_bounds__(256) lbs_kernel(int64_t n, int J, const float*
   __syncthreads();
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   bool degenerate = false;
+  float rmax = 0.0f;
   if (i < n) {
     uint2 p = ijk[i];
     float c[3] = {ox + ((float)(p.x & 0xffffu) + 0.5f) * h, oy + ((float)(p.x >> 16) + 0.5f) * h,
@@ -139,6 +140,7 @@ __global__ void __launch_bounds__(256) lbs_kernel(int64_t n, int J, const float*
       }
       // slight growth keeps the radius a bound under FP32 rounding
       float r = sqrtf(r2) * (1.0f + 1e-6f) + 1e-9f;
+      rmax = fmaxf(rmax, r);
       out_geo[0] = make_float4(cw[0], cw[1], cw[2], r);
       out_geo[1] = make_float4(ax[0], ax[1], ax[2], 0.f);
       out_geo[2] = make_float4(ay[0], ay[1], ay[2], 0.f);
@@ -152,6 +154,10 @@ __global__ void __launch_bounds__(256) lbs_kernel(int64_t n, int J, const float*
   }
   unsigned bal = __ballot_sync(0xffffffffu, degenerate);
   if ((threadIdx.x & 31) == 0 && bal) atomicAdd(status + kStDegenerate, (unsigned long long)__popc(bal));
+  // largest bounding radius of the pose (positive floats order as their bits)
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+  if ((threadIdx.x & 31) == 0 && rmax > 0.0f) atomicMax(status + kStRmax, (unsigned long long)__float_as_uint(rmax));
 }
 
 // Per voxel and view: projected-corner pixel rectangle (grown by kBboxPad),

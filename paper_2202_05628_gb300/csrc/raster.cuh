@@ -136,9 +136,11 @@ constexpr int NT = 32;           // instances per staged chunk
 
 template <int C, typename TF>
 struct Ring {
-  // chunks of staged feature rows kept in shared memory (<= 32 KB, <= 16)
-  static constexpr int kRaw = 32768 / (NT * C * (int)sizeof(TF));
-  static constexpr int kChunks = kRaw < 16 ? kRaw : 16;
+  // chunks of staged feature rows kept in shared memory (<= 12 KB, 1 .. 16):
+  // small enough for many resident one-warp blocks; a hit released after its
+  // chunk left the ring reads its voxel again from global memory
+  static constexpr int kRaw = 12288 / (NT * C * (int)sizeof(TF));
+  static constexpr int kChunks = kRaw < 1 ? 1 : (kRaw < 16 ? kRaw : 16);
 };
 
 template <int C, typename TF>

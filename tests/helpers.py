@@ -5,14 +5,14 @@ import numpy as np
 import scenegen as sg
 
 
-def renderer(scene, storage="f32", tau=1e-4, profile=False, instance_cap=0):
+def renderer(scene, storage="f32", tau=1e-4, profile=False, instance_cap=0, segment=256):
     import paper_2202_05628_gb300 as art
     r = art.Renderer()
     oc = scene.octree
     r.load_octree(oc.depth, oc.origin, oc.extent, oc.ijk, oc.joint_idx, oc.weights, oc.features, oc.density,
                   storage)
     r.load_skeleton(scene.skeleton.parent, scene.skeleton.rest)
-    r.set_config(tau=tau, profile=profile, instance_cap=instance_cap)
+    r.set_config(tau=tau, profile=profile, instance_cap=instance_cap, segment=segment)
     return r
 
 

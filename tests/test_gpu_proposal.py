@@ -151,7 +151,7 @@ def test_labels_match_oracle():
 @pytest.mark.parametrize("seed,margin", [(2, 0), (5, 1)])
 def test_skip_render_matches_oracle(seed, margin):
     """Learned-skip render with an untrained proposal (arbitrary intervals):
-    queued tiles equal the plain render bit for bit; tiles that pass the
+    queued tiles equal the plain render up to FP32 regrouping; tiles that pass the
     coarse check equal the oracle's interval-restricted composite with the
     same bins and lose at most the threshold of mass; the queue agrees with
     the oracle's coarse check."""
@@ -180,9 +180,9 @@ def test_skip_render_matches_oracle(seed, margin):
     Fg, Ag = F.cpu().numpy().reshape(-1, C), Am.cpu().numpy().reshape(-1)
     F0g, A0g = F0.cpu().numpy().reshape(-1, C), A0.cpu().numpy().reshape(-1)
     in_fb = np.isin(tile, fb)
-    # the fallback is the plain walk
-    np.testing.assert_array_equal(Fg[in_fb], F0g[in_fb])
-    np.testing.assert_array_equal(Ag[in_fb], A0g[in_fb])
+    # the fallback is the plain walk (sequential; the plain render regroups the same sum by segments)
+    np.testing.assert_allclose(Fg[in_fb], F0g[in_fb], atol=1e-6)
+    np.testing.assert_allclose(Ag[in_fb], A0g[in_fb], atol=1e-6)
     # bins as the kernel used them (tile union, margin), for the oracle's restricted composite
     bu = oracle.tile_union_bins(bins, cam, margin)
     bu[~act_px] = [0, 63]  # tiles without instances were not predicted: nothing to composite there

@@ -167,18 +167,51 @@ def _stop_case(dens_scale, tau, tol):
     assert np.abs(g["F"] - o["F"])[ok].max() < tol
     assert np.abs(g["A"] - o["A"])[ok].max() < tol
     assert np.array_equal(g["count"][ok & stopped], o["nused"][ok & stopped])
+    # the split walk (segments of 32 entries): a stop inside a later segment
+    # sends the tile to the plain walk, so the stop rule holds exactly
+    r.set_config(tau=tau, segment=32)
+    F, A = render_maps(r, 0, cam, oc.C)
+    st = r.sync_status()
+    assert np.abs(F - o["F"])[ok].max() < tol
+    assert np.abs(A - o["A"])[ok].max() < tol
+    return st
 
 
 def test_early_stop_matches_oracle():
     # tau = 0.7 fires inside the animal at the workload's densities: FP32 tolerance
-    _stop_case(1.0, 0.7, TOL_F32)
+    st = _stop_case(1.0, 0.7, TOL_F32)
+    assert st["fallback_tiles"] > 0
 
 
 def test_early_stop_opaque_voxels():
     # sigma x 60 (up to ~3000 / m) with tau = 1e-4: the FP32 ray parameter carries
     # ~2e-7 m of rounding at 2 m, i.e. up to sigma * 2e-7 * 4 ~ 3e-3 of alpha per
     # hit; the bound below is that per-hit figure times max|f|.
-    _stop_case(60.0, 1e-4, 3e-3 * 2.0)
+    st = _stop_case(60.0, 1e-4, 3e-3 * 2.0)
+    assert st["fallback_tiles"] > 0
+
+
+@pytest.mark.parametrize("segment,az,pose_seed", [(32, 80.0, 4), (96, 215.0, 7)])
+def test_split_walk_matches_oracle(segment, az, pose_seed):
+    """Tiles walked in segments by separate warps and merged front to back
+    (F = F_0 + T_0 F_1 + ...) against the oracle, and against one segment
+    per tile (the same sum, grouped differently)."""
+    sc, cam, pose = tiny_setup(az=az, pose_seed=pose_seed)
+    r = renderer(sc, segment=segment, profile=True)
+    set_pose(r, pose)
+    set_cam(r, 0, cam)
+    F, A = render_maps(r, 0, cam, sc.octree.C)
+    kt = r.kernel_times(reset=True)
+    assert kt["composite_merge"][0] == 1 and kt["composite"][0] == 1
+    rg = r.debug_buffer(7, np.uint32).reshape(-1, 2)[: ((cam.W + 7) // 8) * ((cam.H + 3) // 4)]
+    assert (rg[:, 1] - rg[:, 0]).max() >= 4 * segment  # some tiles split in four or more
+    _, A_or, _ = oracle.pose_transforms(sc, pose)
+    o = oracle.render(sc.octree, A_or, cam)
+    assert np.abs(F - o["F"]).max() < TOL_F32 and np.abs(A - o["A"]).max() < TOL_F32
+    r.set_config(segment=1 << 24)
+    F1, A1 = render_maps(r, 0, cam, sc.octree.C)
+    assert np.abs(F - F1).max() < 1e-6 and np.abs(A - A1).max() < 1e-6
+    assert r.sync_status()["fallback_tiles"] == 0
 
 
 def test_bf16_and_f16_feature_storage():
