@@ -44,13 +44,84 @@ struct TcParams {
   unsigned long long* err;
 };
 
+// Epilogue of one 128-pixel output row segment: this thread's pixel x of
+// row y; the accumulator's N columns start at TMEM address taddr (lane
+// quarter included).  Bias, ReLU, then BF16 / E4M3 store (optionally 2x2
+// replicated into the upsampled concatenation), or the fused 1x1 head.
+template <int N, bool F8>
+__device__ __forceinline__ void epi_row(const TcParams& p, uint32_t taddr, int y, int x, const float* s_bias,
+                                        const float* s_head, const float* s_wsc, float in_s, float out_inv,
+                                        float& amax) {
+  const bool valid = x < p.W;
+#pragma unroll 1
+  for (int c0 = 0; c0 < N; c0 += 32) {
+    uint32_t r[32];
+    tmem_ld32(taddr + (uint32_t)c0, r);
+    float v[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const float acc = F8 ? __uint_as_float(r[j]) * (in_s * s_wsc[c0 + j]) : __uint_as_float(r[j]);
+      const float t = acc + s_bias[c0 + j];
+      v[j] = p.act == 1 ? fmaxf(t, 0.0f) : t;
+    }
+    if (!valid) continue;
+    if (p.rgba) {  // fused 1x1 head (N == 32) + sigmoid -> RGBA FP32
+      float o[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        float acc = s_head[4 * N + k];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) acc = fmaf(s_head[k * N + c0 + j], v[j], acc);
+        o[k] = 1.0f / (1.0f + expf(-acc));
+      }
+      reinterpret_cast<float4*>(p.rgba)[(size_t)y * p.W + x] = make_float4(o[0], o[1], o[2], o[3]);
+      continue;
+    }
+    constexpr int kVec = F8 ? 2 : 4;  // 16-B stores of the 32 channels
+    uint4 pk[kVec];
+    if constexpr (F8) {
+      uint16_t* w = reinterpret_cast<uint16_t*>(pk);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        amax = fmaxf(amax, fmaxf(fabsf(v[2 * j]), fabsf(v[2 * j + 1])));
+        w[j] = (uint16_t)__nv_cvt_float2_to_fp8x2(make_float2(v[2 * j] * out_inv, v[2 * j + 1] * out_inv),
+                                                  __NV_SATFINITE, __NV_E4M3);
+      }
+    } else {
+      uint32_t* w = reinterpret_cast<uint32_t*>(pk);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        __nv_bfloat162 b2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+        w[j] = *reinterpret_cast<uint32_t*>(&b2);
+      }
+    }
+    constexpr int kEs = F8 ? 1 : 2;
+    uint8_t* outb = reinterpret_cast<uint8_t*>(p.out);
+    if (!p.up2) {
+      uint4* dst = reinterpret_cast<uint4*>(outb + (((size_t)y * p.W + x) * p.ld_out + p.ch_off + c0) * kEs);
+#pragma unroll
+      for (int k = 0; k < kVec; ++k) dst[k] = pk[k];
+    } else {
+#pragma unroll
+      for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 2; ++dx) {
+          const size_t pix = (size_t)(2 * y + dy) * (2 * p.W) + (2 * x + dx);
+          uint4* dst = reinterpret_cast<uint4*>(outb + (pix * p.ld_out + p.ch_off + c0) * kEs);
+#pragma unroll
+          for (int k = 0; k < kVec; ++k) dst[k] = pk[k];
+        }
+    }
+  }
+}
+
 template <int N, int KCB, bool F8>
 struct TcCfg {
   static constexpr int kA = 128 * KCB;
   static constexpr int kB = N * KCB;
   static constexpr int kStage = kA + kB;
   static constexpr int kStagesRaw = 196608 / kStage;
-  static constexpr int kStages = kStagesRaw > 8 ? 8 : kStagesRaw;
+  static constexpr int kStages = kStagesRaw > 24 ? 24 : kStagesRaw;  // more bytes in flight per SM
   static constexpr int kTmemCols = 2 * N;  // two accumulators; N in {32, 64, 128, 256}
   static constexpr uint32_t kFmt = F8 ? 0u : 1u;  // A/B format: E4M3 (kind::f8f6f4) or BF16 (kind::f16)
   static constexpr uint32_t kIdesc = (1u << 4)                          // D: FP32
@@ -177,70 +248,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     int buf = 0;
     uint32_t aph = 0;
     for (int tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x) {
-      if (!mbar_wait(&accf[buf], aph, abort_flag)) break;
+      if (!mbar_wait(&accf[buf], aph, abort_flag, 256)) break;
       tc_fence_after();
       const int y = tile / p.tiles_per_row, x = (tile % p.tiles_per_row) * 128 + m;
-      const bool valid = x < p.W;
-#pragma unroll 1
-      for (int c0 = 0; c0 < N; c0 += 32) {
-        uint32_t r[32];
-        tmem_ld32(tmem_base + ((uint32_t)(qd * 32) << 16) + (uint32_t)(buf * N + c0), r);
-        float v[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const float acc = F8 ? __uint_as_float(r[j]) * (in_s * s_wsc[c0 + j]) : __uint_as_float(r[j]);
-          const float t = acc + s_bias[c0 + j];
-          v[j] = p.act == 1 ? fmaxf(t, 0.0f) : t;
-        }
-        if (!valid) continue;
-        if (p.rgba) {  // fused 1x1 head (N == 32) + sigmoid -> RGBA FP32
-          float o[4];
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            float acc = s_head[4 * N + k];
-#pragma unroll
-            for (int j = 0; j < 32; ++j) acc = fmaf(s_head[k * N + c0 + j], v[j], acc);
-            o[k] = 1.0f / (1.0f + expf(-acc));
-          }
-          reinterpret_cast<float4*>(p.rgba)[(size_t)y * p.W + x] = make_float4(o[0], o[1], o[2], o[3]);
-          continue;
-        }
-        constexpr int kVec = F8 ? 2 : 4;  // 16-B stores of the 32 channels
-        uint4 pk[kVec];
-        if constexpr (F8) {
-          uint16_t* w = reinterpret_cast<uint16_t*>(pk);
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            amax = fmaxf(amax, fmaxf(fabsf(v[2 * j]), fabsf(v[2 * j + 1])));
-            w[j] = (uint16_t)__nv_cvt_float2_to_fp8x2(make_float2(v[2 * j] * out_inv, v[2 * j + 1] * out_inv),
-                                                      __NV_SATFINITE, __NV_E4M3);
-          }
-        } else {
-          uint32_t* w = reinterpret_cast<uint32_t*>(pk);
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            __nv_bfloat162 b2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-            w[j] = *reinterpret_cast<uint32_t*>(&b2);
-          }
-        }
-        constexpr int kEs = F8 ? 1 : 2;
-        uint8_t* outb = reinterpret_cast<uint8_t*>(p.out);
-        if (!p.up2) {
-          uint4* dst = reinterpret_cast<uint4*>(outb + (((size_t)y * p.W + x) * p.ld_out + p.ch_off + c0) * kEs);
-#pragma unroll
-          for (int k = 0; k < kVec; ++k) dst[k] = pk[k];
-        } else {
-#pragma unroll
-          for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-            for (int dx = 0; dx < 2; ++dx) {
-              const size_t pix = (size_t)(2 * y + dy) * (2 * p.W) + (2 * x + dx);
-              uint4* dst = reinterpret_cast<uint4*>(outb + (pix * p.ld_out + p.ch_off + c0) * kEs);
-#pragma unroll
-              for (int k = 0; k < kVec; ++k) dst[k] = pk[k];
-            }
-        }
-      }
+      epi_row<N, F8>(p, tmem_base + ((uint32_t)(qd * 32) << 16) + (uint32_t)(buf * N), y, x, s_bias, s_head, s_wsc,
+                     in_s, out_inv, amax);
       tc_fence_before();
       mbar_arrive(&acce[buf]);
       if (++buf == 2) {
@@ -259,6 +271,188 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
                               "r"(Cfg::kTmemCols));
+  if (threadIdx.x == 0 && *abort_flag) atomicAdd(p.err, 1ull);
+}
+
+// Row-blocked variant for the narrow layers (N = 32 or 64 output channels,
+// BF16): the weights of all nine taps stay in shared memory for the whole
+// persistent loop, and a work unit is R = 4 output rows of one 128-pixel
+// segment.  The producer brings each of the R + 2 input rows in three
+// horizontal shifts (x - 1, x, x + 1) and channel chunks; every such box
+// serves the up to three output rows it neighbours vertically (one MMA per
+// row into that row's accumulator).  Per output row that is 3 (R + 2) / R
+// boxes instead of 9, and no weight traffic.  Accumulators: R x N TMEM
+// columns per unit, two units in flight.
+constexpr int kRows = 4;
+
+template <int N, int KCB>
+struct RowCfg {
+  static constexpr int KC = KCB / 2;  // channels per chunk
+  static constexpr int kA = 128 * KCB;
+  static constexpr int kTmemCols = 2 * kRows * N;  // 256 or 512
+  static constexpr uint32_t kIdesc = idesc_bf16(128, N);
+};
+
+struct RowParams {
+  TcParams p;
+  int cpt;        // channel chunks per tap
+  int n_units;    // ceil(H / R) x tiles per row
+  int n_stages;   // stages in flight (three boxes each)
+  int w_bytes;    // resident weights: 9 x cpt blocks of N x KCB bytes
+};
+
+template <int N, int KCB>
+__global__ void __launch_bounds__(kThreads, 1)
+    conv_rows_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, RowParams rp) {
+  using Cfg = RowCfg<N, KCB>;
+  const TcParams& p = rp.p;
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  uint8_t* sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
+  uint8_t* wsm = sm;
+  uint8_t* stages = sm + rp.w_bytes;
+  const int S = rp.n_stages;
+  uint64_t* full = reinterpret_cast<uint64_t*>(stages + (size_t)S * 3 * Cfg::kA);
+  uint64_t* empty = full + S;
+  uint64_t* accf = empty + S;
+  uint64_t* acce = accf + 2;
+  uint64_t* wbar = acce + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(wbar + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  float* s_bias = reinterpret_cast<float*>(tmem_slot + 4);
+  float* s_head = s_bias + N;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cpt = rp.cpt;
+  const int n_stage_unit = (kRows + 2) * cpt;  // stages per unit
+  const int kStage = 3 * Cfg::kA;              // three horizontal shifts
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accf[b], 1);
+      mbar_init(&acce[b], 128);
+    }
+    mbar_init(wbar, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  for (int i = threadIdx.x; i < N; i += kThreads) s_bias[i] = i < p.cout ? p.bias[i] : 0.0f;
+  if (p.rgba)
+    for (int i = threadIdx.x; i < 4 * N + 4; i += kThreads) s_head[i] = i < 4 * N ? p.head_w[i] : p.head_b[i - 4 * N];
+  if (warp == 1) tmem_alloc(tmem_slot, Cfg::kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  float amax = 0.0f;
+
+  // A stage is one input row and channel chunk in its three horizontal
+  // shifts (three boxes, one barrier round trip).
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA
+    if (lane == 0) {
+      mbar_expect_tx(wbar, (uint32_t)rp.w_bytes);
+      for (int tap = 0; tap < 9; ++tap)
+        for (int c = 0; c < cpt; ++c)
+          tma_load_2d(wsm + (size_t)(tap * cpt + c) * N * KCB, &tmB, wbar, tap * p.cin + c * Cfg::KC, 0);
+      int s = 0;
+      uint32_t ph = 0;
+      for (int u = blockIdx.x; u < rp.n_units && !*abort_flag; u += gridDim.x) {
+        const int y0 = (u / p.tiles_per_row) * kRows, x0 = (u % p.tiles_per_row) * 128;
+        for (int st = 0; st < n_stage_unit; ++st) {
+          if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) break;
+          const int j = st / cpt, c = st - j * cpt;
+          uint8_t* dst = stages + (size_t)s * kStage;
+          mbar_expect_tx(&full[s], (uint32_t)kStage);
+#pragma unroll
+          for (int dx = 0; dx < 3; ++dx)
+            tma_load_3d(dst + dx * Cfg::kA, &tmA, &full[s], c * Cfg::KC, x0 + dx - 1, y0 - 1 + j);
+          if (++s == S) {
+            s = 0;
+            ph ^= 1u;
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA
+    if (lane == 0) {
+      int s = 0, buf = 0;
+      uint32_t ph = 0, aph = 0;
+      bool ok = mbar_wait(wbar, 0u, abort_flag);
+      const uint32_t wbase = smem_u32(wsm);
+      for (int u = blockIdx.x; ok && u < rp.n_units && !*abort_flag; u += gridDim.x) {
+        if (!mbar_wait(&acce[buf], aph ^ 1u, abort_flag)) break;
+        tc_fence_after();
+        const uint32_t d0 = tmem_base + (uint32_t)(buf * kRows * N);
+        for (int st = 0; st < n_stage_unit; ++st) {
+          if (!mbar_wait(&full[s], ph, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const int j = st / cpt, c = st - j * cpt;
+          const uint32_t a0 = smem_u32(stages + (size_t)s * kStage);
+#pragma unroll
+          for (int dxi = 0; dxi < 3; ++dxi)
+#pragma unroll
+            for (int kk = 0; kk < KCB / 32; ++kk)
+#pragma unroll
+              for (int r = 0; r < kRows; ++r) {  // rows interleaved: independent accumulators back to back
+                const int dyi = j - r;             // dy + 1
+                if (dyi < 0 || dyi > 2) continue;
+                const int tap = dyi * 3 + dxi;
+                const uint32_t bw = wbase + (uint32_t)((tap * cpt + c) * N * KCB);
+                const bool first = dyi == 0 && dxi == 0 && c == 0 && kk == 0;
+                umma<false>(d0 + (uint32_t)(r * N), umma_desc<KCB>(a0 + dxi * Cfg::kA + kk * 32),
+                            umma_desc<KCB>(bw + kk * 32), Cfg::kIdesc, first ? 0u : 1u);
+              }
+          umma_commit(&empty[s]);
+          if (++s == S) {
+            s = 0;
+            ph ^= 1u;
+          }
+        }
+        if (!ok) break;
+        umma_commit(&accf[buf]);
+        if (++buf == 2) {
+          buf = 0;
+          aph ^= 1u;
+        }
+      }
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int qd = warp & 3;
+    const int m = qd * 32 + lane;
+    int buf = 0;
+    uint32_t aph = 0;
+    for (int u = blockIdx.x; u < rp.n_units; u += gridDim.x) {
+      if (!mbar_wait(&accf[buf], aph, abort_flag, 256)) break;
+      tc_fence_after();
+      const int y0 = (u / p.tiles_per_row) * kRows, x = (u % p.tiles_per_row) * 128 + m;
+      for (int r = 0; r < kRows; ++r) {
+        if (y0 + r >= p.H) break;
+        epi_row<N, false>(p, tmem_base + ((uint32_t)(qd * 32) << 16) + (uint32_t)((buf * kRows + r) * N), y0 + r, x,
+                          s_bias, s_head, nullptr, 1.0f, 1.0f, amax);
+      }
+      tc_fence_before();
+      mbar_arrive(&acce[buf]);
+      if (++buf == 2) {
+        buf = 0;
+        aph ^= 1u;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(tmem_base, Cfg::kTmemCols);
   if (threadIdx.x == 0 && *abort_flag) atomicAdd(p.err, 1ull);
 }
 
@@ -388,6 +582,72 @@ __global__ void maxpool2_fp8_kernel(const uint8_t* __restrict__ in, int ld, int 
 
 }  // namespace
 
+namespace {
+
+constexpr int kRowsMaxWeights = 80 * 1024;  // resident weights of the row-blocked kernel
+
+template <int N, int KCB>
+art_status launch_rows(art_ctx* ctx, const TcConv& c) {
+  using Cfg = RowCfg<N, KCB>;
+  CUtensorMap tmA, tmB;
+  const CUtensorMapSwizzle swz = KCB == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+  {
+    cuuint64_t dims[3] = {(cuuint64_t)c.cin, (cuuint64_t)c.W, (cuuint64_t)c.H};
+    cuuint64_t strides[2] = {(cuuint64_t)c.cin * 2, (cuuint64_t)c.W * c.cin * 2};
+    cuuint32_t box[3] = {(cuuint32_t)Cfg::KC, 128, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = g_encode(&tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)c.in, dims, strides, box, es,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(ctx, ART_ERR_CUDA, "cuTensorMapEncodeTiled (activations) failed: %d", (int)r);
+  }
+  {
+    cuuint64_t dims[2] = {(cuuint64_t)9 * c.cin, (cuuint64_t)c.cout};
+    cuuint64_t strides[1] = {(cuuint64_t)9 * c.cin * 2};
+    cuuint32_t box[2] = {(cuuint32_t)Cfg::KC, (cuuint32_t)N};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = g_encode(&tmB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)c.w, dims, strides, box, es,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(ctx, ART_ERR_CUDA, "cuTensorMapEncodeTiled (weights) failed: %d", (int)r);
+  }
+  RowParams rp;
+  TcParams& p = rp.p;
+  p = TcParams{};
+  p.H = c.H;
+  p.W = c.W;
+  p.cin = c.cin;
+  p.cout = c.cout;
+  p.tiles_per_row = (c.W + 127) / 128;
+  p.n_tiles = p.tiles_per_row * c.H;
+  p.act = c.act;
+  p.bias = c.bias;
+  p.out = c.out;
+  p.ld_out = c.ld_out;
+  p.ch_off = c.ch_off;
+  p.up2 = c.up2;
+  p.rgba = c.rgba;
+  p.head_w = c.head_w;
+  p.head_b = c.head_b;
+  p.err = ctx->d_status + kStTcError;
+  rp.cpt = c.cin / Cfg::KC;
+  rp.n_units = ((c.H + kRows - 1) / kRows) * p.tiles_per_row;
+  rp.w_bytes = 9 * rp.cpt * N * KCB;
+  const int tail = 8 * (2 * 24 + 5) + 16 + 4 * N + 4 * (4 * 32 + 4);
+  const int avail = 232448 - 1024 - rp.w_bytes - tail;
+  rp.n_stages = std::min(24, avail / (3 * Cfg::kA));
+  if (rp.n_stages < 2) return fail(ctx, ART_ERR_UNSUPPORTED, "row-blocked conv: weights too large");
+  const int smem = 1024 + rp.w_bytes + rp.n_stages * 3 * Cfg::kA + tail;
+  auto kfn = conv_rows_kernel<N, KCB>;
+  cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "conv_rows shared memory attribute");
+  const int grid = std::min(rp.n_units, ctx->num_sms);
+  ART_LAUNCH(ctx, "conv_tc", kfn, grid, kThreads, smem, tmA, tmB, rp);
+  return ART_OK;
+}
+
+}  // namespace
+
 bool tc_conv_ok(const TcConv& c) {
   const bool n_ok = c.cout == 32 || c.cout == 64 || c.cout == 128 || c.cout == 256;
   const int al = c.f8 ? 16 : 8;  // 16-byte aligned output rows and channel offsets
@@ -411,6 +671,10 @@ art_status launch_tc_conv(art_ctx* ctx, const TcConv& c) {
 #undef ART_F8
   }
   const bool k64 = c.cin % 64 == 0;  // BF16: 64 channels = 128-B rows, else 32 = 64-B rows
+  if ((c.cout == 32 || c.cout == 64) && 9 * c.cin * c.cout * 2 <= kRowsMaxWeights && ctx->conv_rows) {
+    if (c.cout == 32) return k64 ? launch_rows<32, 128>(ctx, c) : launch_rows<32, 64>(ctx, c);
+    return k64 ? launch_rows<64, 128>(ctx, c) : launch_rows<64, 64>(ctx, c);
+  }
   switch (c.cout) {
     case 32: return k64 ? launch_typed<32, 128, false>(ctx, c) : launch_typed<32, 64, false>(ctx, c);
     case 64: return k64 ? launch_typed<64, 128, false>(ctx, c) : launch_typed<64, 64, false>(ctx, c);

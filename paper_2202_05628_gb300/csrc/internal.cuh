@@ -140,6 +140,7 @@ struct art_ctx {
   std::vector<art::ConvLayer> layers;
   void* d_act = nullptr;        // activation arena
   size_t d_act_bytes = 0;
+  bool conv_rows = true;        // row-blocked kernel for the narrow BF16 convolutions
   float* d_f8_scale = nullptr;  // FP8 network: per-tensor activation scales
   unsigned int* d_f8_amax = nullptr;
   bool f8_calibrated = false;

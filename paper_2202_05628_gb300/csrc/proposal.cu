@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(128) proposal_kernel(PropParams p) {
           umma<false>(tmem, umma_desc<128>(a_addr + kk * 32), umma_desc<128>(wb + kk * 32), id, kk != 0);
         umma_commit(bar);
       }
-      const bool ok = mbar_wait(bar, phase, abort_flag);
+      const bool ok = mbar_wait(bar, phase, abort_flag, tid == 0 ? 0u : 64u);
       phase ^= 1u;
       if (__syncthreads_or(!ok)) {
         failed = true;
