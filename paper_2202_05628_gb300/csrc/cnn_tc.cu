@@ -285,12 +285,20 @@ __global__ void __launch_bounds__(kThreads, 1)
 // columns per unit, two units in flight.
 constexpr int kRows = 4;
 
+// With 32 output channels the three vertical taps are stacked into one
+// N = 96 operand: the accumulators of consecutive output rows sit in
+// consecutive TMEM column slots in reverse row order (slot of row y =
+// y0 + R + 1 - y; two slots of spare on each side), so that one MMA per
+// input-row box accumulates into the three rows it touches.  Every MMA then
+// accumulates; the epilogue zeroes each real slot after reading it.
 template <int N, int KCB>
 struct RowCfg {
   static constexpr int KC = KCB / 2;  // channels per chunk
   static constexpr int kA = 128 * KCB;
-  static constexpr int kTmemCols = 2 * kRows * N;  // 256 or 512
-  static constexpr uint32_t kIdesc = idesc_bf16(128, N);
+  static constexpr bool kStack = N == 32;
+  static constexpr int kSlots = kStack ? kRows + 4 : kRows;
+  static constexpr int kTmemCols = 2 * kSlots * N;  // 512
+  static constexpr uint32_t kIdesc = idesc_bf16(128, kStack ? 3 * N : N);
 };
 
 struct RowParams {
@@ -326,6 +334,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int cpt = rp.cpt;
   const int n_stage_unit = (kRows + 2) * cpt;  // stages per unit
   const int kStage = 3 * Cfg::kA;              // three horizontal shifts
+  // resident weight block of (dy + 1, dx + 1, chunk); stacked form: the three
+  // vertical taps of one (dx, chunk) are adjacent (one N = 96 operand)
+  auto wblk = [&](int dyi, int dxi, int c) { return Cfg::kStack ? (dxi * cpt + c) * 3 + dyi : (dyi * 3 + dxi) * cpt + c; };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
@@ -358,7 +369,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_expect_tx(wbar, (uint32_t)rp.w_bytes);
       for (int tap = 0; tap < 9; ++tap)
         for (int c = 0; c < cpt; ++c)
-          tma_load_2d(wsm + (size_t)(tap * cpt + c) * N * KCB, &tmB, wbar, tap * p.cin + c * Cfg::KC, 0);
+          tma_load_2d(wsm + (size_t)wblk(tap / 3, tap % 3, c) * N * KCB, &tmB, wbar, tap * p.cin + c * Cfg::KC, 0);
       int s = 0;
       uint32_t ph = 0;
       for (int u = blockIdx.x; u < rp.n_units && !*abort_flag; u += gridDim.x) {
@@ -386,9 +397,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool ok = mbar_wait(wbar, 0u, abort_flag);
       const uint32_t wbase = smem_u32(wsm);
       for (int u = blockIdx.x; ok && u < rp.n_units && !*abort_flag; u += gridDim.x) {
-        if (!mbar_wait(&acce[buf], aph ^ 1u, abort_flag)) break;
+        // stacked form: the epilogue clears the accumulators (phase 0 = the initial clear)
+        if (!mbar_wait(&acce[buf], Cfg::kStack ? aph : aph ^ 1u, abort_flag)) break;
         tc_fence_after();
-        const uint32_t d0 = tmem_base + (uint32_t)(buf * kRows * N);
+        const uint32_t d0 = tmem_base + (uint32_t)(buf * Cfg::kSlots * N);
         for (int st = 0; st < n_stage_unit; ++st) {
           if (!mbar_wait(&full[s], ph, abort_flag)) {
             ok = false;
@@ -397,20 +409,32 @@ __global__ void __launch_bounds__(kThreads, 1)
           tc_fence_after();
           const int j = st / cpt, c = st - j * cpt;
           const uint32_t a0 = smem_u32(stages + (size_t)s * kStage);
+          if constexpr (Cfg::kStack) {
+            // input row j feeds output rows j, j - 1, j - 2 of the unit (slots R + 1 - j .. R + 3 - j)
+            const uint32_t dj = d0 + (uint32_t)((kRows + 1 - j) * N);
 #pragma unroll
-          for (int dxi = 0; dxi < 3; ++dxi)
+            for (int dxi = 0; dxi < 3; ++dxi) {
+              const uint32_t bw = wbase + (uint32_t)(wblk(0, dxi, c) * N * KCB);
 #pragma unroll
-            for (int kk = 0; kk < KCB / 32; ++kk)
+              for (int kk = 0; kk < KCB / 32; ++kk)
+                umma<false>(dj, umma_desc<KCB>(a0 + dxi * Cfg::kA + kk * 32), umma_desc<KCB>(bw + kk * 32),
+                            Cfg::kIdesc, 1u);
+            }
+          } else {
 #pragma unroll
-              for (int r = 0; r < kRows; ++r) {  // rows interleaved: independent accumulators back to back
-                const int dyi = j - r;             // dy + 1
-                if (dyi < 0 || dyi > 2) continue;
-                const int tap = dyi * 3 + dxi;
-                const uint32_t bw = wbase + (uint32_t)((tap * cpt + c) * N * KCB);
-                const bool first = dyi == 0 && dxi == 0 && c == 0 && kk == 0;
-                umma<false>(d0 + (uint32_t)(r * N), umma_desc<KCB>(a0 + dxi * Cfg::kA + kk * 32),
-                            umma_desc<KCB>(bw + kk * 32), Cfg::kIdesc, first ? 0u : 1u);
-              }
+            for (int dxi = 0; dxi < 3; ++dxi)
+#pragma unroll
+              for (int kk = 0; kk < KCB / 32; ++kk)
+#pragma unroll
+                for (int r = 0; r < kRows; ++r) {  // rows interleaved: independent accumulators back to back
+                  const int dyi = j - r;             // dy + 1
+                  if (dyi < 0 || dyi > 2) continue;
+                  const uint32_t bw = wbase + (uint32_t)(wblk(dyi, dxi, c) * N * KCB);
+                  const bool first = dyi == 0 && dxi == 0 && c == 0 && kk == 0;
+                  umma<false>(d0 + (uint32_t)(r * N), umma_desc<KCB>(a0 + dxi * Cfg::kA + kk * 32),
+                              umma_desc<KCB>(bw + kk * 32), Cfg::kIdesc, first ? 0u : 1u);
+                }
+          }
           umma_commit(&empty[s]);
           if (++s == S) {
             s = 0;
@@ -430,17 +454,30 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ------------------------------------------------------------ epilogue
     const int qd = warp & 3;
     const int m = qd * 32 + lane;
+    const uint32_t tq = tmem_base + ((uint32_t)(qd * 32) << 16);  // this warp's lane quarter
     int buf = 0;
     uint32_t aph = 0;
+    if constexpr (Cfg::kStack) {  // zero every slot of both buffers, then release them to the MMA
+      for (int c0 = 0; c0 < Cfg::kTmemCols; c0 += 32) tmem_zero32(tq + (uint32_t)c0);
+      tmem_wait_st();
+      tc_fence_before();
+      mbar_arrive(&acce[0]);
+      mbar_arrive(&acce[1]);
+    }
     for (int u = blockIdx.x; u < rp.n_units; u += gridDim.x) {
       if (!mbar_wait(&accf[buf], aph, abort_flag, 256)) break;
       tc_fence_after();
       const int y0 = (u / p.tiles_per_row) * kRows, x = (u % p.tiles_per_row) * 128 + m;
       for (int r = 0; r < kRows; ++r) {
-        if (y0 + r >= p.H) break;
-        epi_row<N, false>(p, tmem_base + ((uint32_t)(qd * 32) << 16) + (uint32_t)((buf * kRows + r) * N), y0 + r, x,
-                          s_bias, s_head, nullptr, 1.0f, 1.0f, amax);
+        const int slot = Cfg::kStack ? kRows + 1 - r : r;
+        const uint32_t ta = tq + (uint32_t)((buf * Cfg::kSlots + slot) * N);
+        if (y0 + r < p.H) epi_row<N, false>(p, ta, y0 + r, x, s_bias, s_head, nullptr, 1.0f, 1.0f, amax);
+        if constexpr (Cfg::kStack) {
+#pragma unroll
+          for (int c0 = 0; c0 < N; c0 += 32) tmem_zero32(ta + (uint32_t)c0);
+        }
       }
+      if constexpr (Cfg::kStack) tmem_wait_st();
       tc_fence_before();
       mbar_arrive(&acce[buf]);
       if (++buf == 2) {
