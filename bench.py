@@ -50,6 +50,7 @@ def parse():
     p.add_argument("--f32-steps", type=int, default=16, help="steps of the FP32 plain form measured beside")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--segment", type=int, default=256, help="list entries per composite segment")
     p.add_argument("--side-steps", type=int, default=16,
                    help="frames of the FP8 form and of the backward pass measured beside")
     return p.parse_args()
@@ -144,6 +145,9 @@ def proposal_params(sc, cams):
     return prop.train(X, Y, steps=1500, batch=16384)
 
 
+SEGMENT = 256
+
+
 def setup_renderer(sc, cams, layers, form, profile=False, proposal=None):
     import paper_2202_05628_gb300 as art
     storage, net, skip, _ = FORMS[form]
@@ -155,7 +159,7 @@ def setup_renderer(sc, cams, layers, form, profile=False, proposal=None):
         r.load_shader(art.ART_NET_UNET, oc.C, [32, 64, 128, 256], 4, art.flat_params(layers), net)
     if skip:
         r.load_proposal(proposal if proposal is not None else proposal_params(sc, cams))
-    r.set_config(tau=1e-4, profile=profile, skip=int(skip), max_missed=1e-3, margin=1)
+    r.set_config(tau=1e-4, profile=profile, skip=int(skip), max_missed=1e-3, margin=1, segment=SEGMENT)
     for v, c in enumerate(cams):
         r.set_camera(v, c.W, c.H, c.fx, c.fy, c.cx, c.cy, c.world_to_cam, c.near, c.far)
     return r
@@ -476,7 +480,9 @@ def reference_arm(args):
 
 
 def main():
+    global SEGMENT
     args = parse()
+    SEGMENT = args.segment
     if args.impl == "reference":
         reference_arm(args)
     else:

@@ -173,7 +173,7 @@ void free_all(art_ctx* ctx) {
                   ctx->d_status, ctx->d_F, ctx->d_A, ctx->d_rgba, ctx->d_act, ctx->d_sk, ctx->d_sv,
                   ctx->d_shist, ctx->d_sbsum, ctx->d_gN, ctx->d_f8_scale, ctx->d_f8_amax, ctx->d_prop_img,
                   ctx->d_prop_f32, ctx->d_pose_bias, ctx->d_bins, ctx->d_thist, ctx->d_hbin, ctx->d_htau, ctx->d_fbq,
-                  ctx->d_seg, ctx->d_items, ctx->d_multi, ctx->d_part};
+                  ctx->d_seg, ctx->d_items, ctx->d_multi, ctx->d_part, ctx->d_fbq2};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& L : ctx->layers) {
@@ -253,7 +253,7 @@ art_status ensure_skip_buffers(art_ctx* ctx, const ViewParams& v) {
 art_status ensure_split_buffers(art_ctx* ctx, const ViewParams& v) {
   art_status st;
   const size_t ntiles = (size_t)v.tiles_x * v.tiles_y;
-  const size_t items = (size_t)(ctx->inst_cap / ctx->seg_len) + ntiles + 1;
+  const size_t items = (size_t)(ctx->inst_cap / std::max(32, ctx->seg_len / 4)) + ntiles + 1;  // re-walks: seg_len / 4
   if ((st = ensure(ctx, (void**)&ctx->d_seg, &ctx->d_seg_bytes, ntiles * sizeof(uint2), "segment plan")) != ART_OK)
     return st;
   if ((st = ensure(ctx, (void**)&ctx->d_multi, &ctx->d_multi_bytes, ntiles * 4, "split tiles")) != ART_OK) return st;
@@ -262,6 +262,8 @@ art_status ensure_split_buffers(art_ctx* ctx, const ViewParams& v) {
                    "segment partial sums")) != ART_OK)
     return st;
   if ((st = ensure(ctx, (void**)&ctx->d_fbq, &ctx->d_fbq_bytes, ntiles * 4, "fallback queue")) != ART_OK) return st;
+  if ((st = ensure(ctx, (void**)&ctx->d_fbq2, &ctx->d_fbq2_bytes, ntiles * 4, "second fallback queue")) != ART_OK)
+    return st;
   const int fb = ctx->feat_dtype == ART_F32 ? 4 : 2;
   ctx->composite_blocks = ctx->num_sms * composite_blocks_per_sm(ctx->C, fb);
   return ART_OK;

@@ -31,7 +31,8 @@ struct SkipArgs {
   const float* thist;   // kLabel, kInterval: [tiles][kPropBins] optical-depth bounds
   float max_missed;     // coarse-check threshold
   int margin;           // kInterval: bins added on both sides
-  uint32_t* queue;      // kInterval: fallback queue (count in status[kStFallback])
+  uint32_t* queue;      // tiles queued for a later walk (count in status[qword])
+  int qword;            // status word counting the queue
   float* labels;        // kLabel: [H][W][3]
   uchar2* lbins;        // kLabel: [H][W]
 };
@@ -282,7 +283,7 @@ __device__ __forceinline__ void composite_tile(const int tile, const Seg& sg,
         fail = -expm1f(-front) + T * -expm1f(-back) > sk.max_missed;
       }
       if (__any_sync(0xffffffffu, fail) && lane == 0) {
-        const unsigned long long q = atomicAdd(status + kStFallback, 1ull);
+        const unsigned long long q = atomicAdd(status + sk.qword, 1ull);
         sk.queue[q] = (uint32_t)tile;
       }
     } else {  // label bins: keep the significant hits and pass the check
@@ -371,10 +372,17 @@ __global__ void __launch_bounds__(256) composite_clear_kernel(const uint2* __res
 
 // Per tile: number of segments and the index of its first one; the segments
 // of all tiles in one list, the tiles with two or more in another.
+// With tiles_in set, only the tiles listed there (count in status[in_word]).
 __global__ void seg_plan_kernel(int ntiles, const uint2* __restrict__ ranges, int seg_len, uint2* __restrict__ seg,
                                 uint32_t* __restrict__ items, uint32_t* __restrict__ multi,
-                                unsigned long long* __restrict__ status) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+                                unsigned long long* __restrict__ status, const uint32_t* __restrict__ tiles_in,
+                                int in_word) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int t = i;
+  if (tiles_in) {
+    if ((unsigned long long)i >= status[in_word]) return;
+    t = (int)tiles_in[i];
+  }
   if (t >= ntiles) return;
   const uint2 rg = ranges[t];
   const uint32_t len = rg.y - rg.x;
@@ -455,6 +463,16 @@ __global__ void __launch_bounds__(32) composite_split_kernel(
 
 // Merge of the segments of the tiles with two or more: outputs, the coarse
 // check of the learned skip, and the fallback queue.
+// Channels merged by one warp: a split tile is merged by C / kMergeCh warps,
+// each owning a channel group (the transmittance and the flags are computed
+// by all of them; group 0 writes A and queues the tile).
+constexpr int kMergeCh = 8;
+
+template <int C, typename TO>
+__device__ __forceinline__ void store_group(TO* __restrict__ p, const float* f) {
+  store_row<(C >= kMergeCh ? kMergeCh : C)>(p, f);
+}
+
 template <int C, typename TO, int MODE>
 __global__ void __launch_bounds__(32) composite_merge_kernel(const uint2* __restrict__ seg,
                                                              const uint32_t* __restrict__ multi, ViewParams v,
@@ -462,66 +480,99 @@ __global__ void __launch_bounds__(32) composite_merge_kernel(const uint2* __rest
                                                              float* __restrict__ Aout,
                                                              unsigned long long* __restrict__ status,
                                                              const float* __restrict__ part, SkipArgs sk) {
+  constexpr int G = C >= kMergeCh ? C / kMergeCh : 1;  // channel groups
+  constexpr int CG = C / G;
   const int lane = threadIdx.x & 31;
-  const unsigned long long n_multi = status[kStMulti];
+  const unsigned long long n_items = status[kStMulti] * G;
   for (;;) {
     unsigned long long m = 0;
     if (lane == 0) m = atomicAdd(status + kStNextMerge, 1ull);
     m = __shfl_sync(0xffffffffu, m, 0);
-    if (m >= n_multi) break;
-    const int tile = (int)multi[m];
+    if (m >= n_items) break;
+    const int tile = (int)multi[m / G];
+    const int grp = (int)(m % G);
     const uint2 sgt = seg[tile];
     const int tx = tile % v.tiles_x, ty = tile / v.tiles_x;
     const int px = tx * TSX + (lane & 7), py = ty * TSY + (lane >> 3);
     const bool inside = px < v.W && py < v.H;
-    float acc[C];
-#pragma unroll
-    for (int c = 0; c < C; ++c) acc[c] = 0.0f;
+    const float* pbase = part + (size_t)sgt.x * (C + 1) * 32;
+    // the segments this pixel composites (front to back until the stop) and the stop check
     float T = 1.0f;
-    bool stopped = false, redo = false;
+    uint32_t kend = sgt.y;
+    bool redo = false;
     for (uint32_t k = 0; k < sgt.y; ++k) {
-      const float* pp = part + (size_t)(sgt.x + k) * (C + 1) * 32;
-      const float Tk = pp[C * 32 + lane];
-      if (stopped) break;
+      const float Tk = pbase[(size_t)k * (C + 1) * 32 + C * 32 + lane];
       if (T < 1.0f && T * Tk < tau) redo = true;  // the stop falls inside a later segment
-#pragma unroll
-      for (int c = 0; c < C; ++c) acc[c] = fmaf(T, pp[c * 32 + lane], acc[c]);
       T *= Tk;
-      if (T < tau) stopped = true;
+      if (T < tau) {
+        kend = k + 1;
+        break;
+      }
+    }
+    // F = sum_k (T_0 ... T_{k-1}) F_k over this warp's channels; loads of two
+    // segments in flight together
+    float acc[CG];
+#pragma unroll
+    for (int c = 0; c < CG; ++c) acc[c] = 0.0f;
+    float P = 1.0f;
+    uint32_t k = 0;
+    for (; k + 1 < kend; k += 2) {
+      const float* p0 = pbase + (size_t)k * (C + 1) * 32;
+      const float* p1 = p0 + (C + 1) * 32;
+      float f0[CG], f1[CG];
+#pragma unroll
+      for (int c = 0; c < CG; ++c) {
+        f0[c] = p0[(grp * CG + c) * 32 + lane];
+        f1[c] = p1[(grp * CG + c) * 32 + lane];
+      }
+      const float T0 = p0[C * 32 + lane], T1 = p1[C * 32 + lane];
+#pragma unroll
+      for (int c = 0; c < CG; ++c) acc[c] = fmaf(P, f0[c], acc[c]);
+      P *= T0;
+#pragma unroll
+      for (int c = 0; c < CG; ++c) acc[c] = fmaf(P, f1[c], acc[c]);
+      P *= T1;
+    }
+    if (k < kend) {
+      const float* p0 = pbase + (size_t)k * (C + 1) * 32;
+#pragma unroll
+      for (int c = 0; c < CG; ++c) acc[c] = fmaf(P, p0[(grp * CG + c) * 32 + lane], acc[c]);
     }
     bool fail = false;
     if constexpr (MODE == kInterval) {  // coarse check of the lost mass over the tile's union interval
-      __shared__ float s_pre[kPropBins];
-      const float tot = tile_hist_prefix(sk.thist + (size_t)tile * kPropBins, s_pre, lane);
-      int lo_b = kPropBins, hi_b = -1;
-      if (inside) {
-        const uchar2 b = sk.bins[(size_t)py * v.W + px];
-        if (b.y >= b.x) {
-          lo_b = b.x;
-          hi_b = b.y;
+      if (grp == 0) {
+        __shared__ float s_pre[kPropBins];
+        const float tot = tile_hist_prefix(sk.thist + (size_t)tile * kPropBins, s_pre, lane);
+        int lo_b = kPropBins, hi_b = -1;
+        if (inside) {
+          const uchar2 b = sk.bins[(size_t)py * v.W + px];
+          if (b.y >= b.x) {
+            lo_b = b.x;
+            hi_b = b.y;
+          }
         }
-      }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        lo_b = min(lo_b, __shfl_xor_sync(0xffffffffu, lo_b, o));
-        hi_b = max(hi_b, __shfl_xor_sync(0xffffffffu, hi_b, o));
-      }
-      const bool empty = hi_b < lo_b;
-      const int bn = empty ? lo_b : max(lo_b - sk.margin, 0);
-      const int bf = empty ? hi_b : min(hi_b + sk.margin, kPropBins - 1);
-      if (inside) {
-        const float front = empty ? tot : (bn > 0 ? s_pre[bn - 1] : 0.0f);
-        const float back = empty ? 0.0f : tot - s_pre[bf];
-        fail = -expm1f(-front) + T * -expm1f(-back) > sk.max_missed;
+        for (int o = 16; o > 0; o >>= 1) {
+          lo_b = min(lo_b, __shfl_xor_sync(0xffffffffu, lo_b, o));
+          hi_b = max(hi_b, __shfl_xor_sync(0xffffffffu, hi_b, o));
+        }
+        const bool empty = hi_b < lo_b;
+        const int bn = empty ? lo_b : max(lo_b - sk.margin, 0);
+        const int bf = empty ? hi_b : min(hi_b + sk.margin, kPropBins - 1);
+        if (inside) {
+          const float front = empty ? tot : (bn > 0 ? s_pre[bn - 1] : 0.0f);
+          const float back = empty ? 0.0f : tot - s_pre[bf];
+          fail = -expm1f(-front) + T * -expm1f(-back) > sk.max_missed;
+        }
       }
     }
     if (inside) {
       const size_t pix = (size_t)py * v.W + px;
-      store_row<C>(Fout + pix * C, acc);
-      if (Aout) Aout[pix] = 1.0f - T;
+      store_group<C, TO>(Fout + pix * C + grp * CG, acc);
+      if (grp == 0 && Aout) Aout[pix] = 1.0f - T;
     }
-    if (__any_sync(0xffffffffu, (redo || fail) && inside) && lane == 0)
-      sk.queue[atomicAdd(status + kStFallback, 1ull)] = (uint32_t)tile;
+    if (grp == 0 && __any_sync(0xffffffffu, (redo || fail) && inside) && lane == 0)
+      sk.queue[atomicAdd(status + sk.qword, 1ull)] = (uint32_t)tile;
     __syncwarp();
   }
 }
@@ -536,8 +587,8 @@ __global__ void __launch_bounds__(32) composite_queue_kernel(const uint2* __rest
                                                              const TF* __restrict__ feat, ViewParams v, float tau,
                                                              TO* __restrict__ Fout, float* __restrict__ Aout,
                                                              unsigned long long* __restrict__ status,
-                                                             const uint32_t* __restrict__ queue) {
-  const unsigned long long n = status[kStFallback];
+                                                             const uint32_t* __restrict__ queue, int qword) {
+  const unsigned long long n = status[qword];
   for (unsigned long long i = blockIdx.x; i < n; i += gridDim.x) {
     const int tile = (int)queue[i];
     const uint2 rg = ranges[tile];
@@ -547,23 +598,27 @@ __global__ void __launch_bounds__(32) composite_queue_kernel(const uint2* __rest
   }
 }
 
-// Plain or learned-skip composite: plan the segments, walk them with
-// persistent warps, merge the split tiles, then walk the queued tiles in full.
+// One split pass, plain or learned-skip, over all tiles or the tiles listed
+// in `list` (count in status[list_word]): plan the segments, walk them with
+// persistent warps, merge the split tiles; tiles that need the sequential
+// walk go to sk.queue (count in status[sk.qword]).
 template <int C, typename TF, typename TO>
-void split_walk(art_ctx* ctx, const ViewParams& v, void* F, float* A, int mode, const SkipArgs& sk_in) {
+void split_pass(art_ctx* ctx, const ViewParams& v, void* F, float* A, int mode, const SkipArgs& sk,
+                const uint32_t* list, int list_word) {
   const int ntiles = v.tiles_x * v.tiles_y;
   const TF* feat = (const TF*)ctx->d_feat;
-  SkipArgs sk = sk_in;
-  sk.queue = ctx->d_fbq;
   cudaMemsetAsync(ctx->d_status + kStItems, 0, 4 * sizeof(unsigned long long), ctx->stream);  // items .. next merge
-  cudaMemsetAsync(ctx->d_status + kStFallback, 0, sizeof(unsigned long long), ctx->stream);
-  ART_LAUNCH(ctx, "composite_plan", seg_plan_kernel, (ntiles + 255) / 256, 256, 0, ntiles, ctx->d_ranges,
-             ctx->seg_len, ctx->d_seg, ctx->d_items, ctx->d_multi, ctx->d_status);
-  auto cfn = composite_clear_kernel<C, TO>;
-  ART_LAUNCH(ctx, "composite_clear", cfn, (ntiles + 7) / 8, 256, 0, ctx->d_ranges, v, (TO*)F, A);
+  cudaMemsetAsync(ctx->d_status + sk.qword, 0, sizeof(unsigned long long), ctx->stream);
+  // a re-walk covers a few tiles: shorter segments put more warps on them
+  const int seg_len = list ? std::max(32, ctx->seg_len / 4) : ctx->seg_len;
+  ART_LAUNCH(ctx, list ? "composite_replan" : "composite_plan", seg_plan_kernel, (ntiles + 255) / 256, 256, 0, ntiles,
+             ctx->d_ranges, seg_len, ctx->d_seg, ctx->d_items, ctx->d_multi, ctx->d_status, list, list_word);
+  if (!list) {
+    auto cfn = composite_clear_kernel<C, TO>;
+    ART_LAUNCH(ctx, "composite_clear", cfn, (ntiles + 7) / 8, 256, 0, ctx->d_ranges, v, (TO*)F, A);
+  }
   const int grid = ctx->composite_blocks;
-  const bool skip = mode == kInterval;
-  if (skip) {
+  if (mode == kInterval) {
     auto kfn = composite_split_kernel<C, TF, TO, kInterval>;
     ART_LAUNCH(ctx, "composite_skip", kfn, grid, 32, 0, ctx->d_ranges, ctx->d_seg, ctx->d_items, ctx->d_keys[0],
                ctx->d_vals[0], ctx->d_rec, ctx->d_rect, feat, v, ctx->cfg.tau, (TO*)F, A, ctx->d_status, ctx->d_part,
@@ -573,17 +628,41 @@ void split_walk(art_ctx* ctx, const ViewParams& v, void* F, float* A, int mode, 
                A, ctx->d_status, ctx->d_part, sk);
   } else {
     auto kfn = composite_split_kernel<C, TF, TO, kPlain>;
-    ART_LAUNCH(ctx, "composite", kfn, grid, 32, 0, ctx->d_ranges, ctx->d_seg, ctx->d_items, ctx->d_keys[0],
-               ctx->d_vals[0], ctx->d_rec, ctx->d_rect, feat, v, ctx->cfg.tau, (TO*)F, A, ctx->d_status, ctx->d_part,
-               sk);
+    ART_LAUNCH(ctx, list ? "composite_refill" : "composite", kfn, grid, 32, 0, ctx->d_ranges, ctx->d_seg, ctx->d_items,
+               ctx->d_keys[0], ctx->d_vals[0], ctx->d_rec, ctx->d_rect, feat, v, ctx->cfg.tau, (TO*)F, A,
+               ctx->d_status, ctx->d_part, sk);
     auto mfn = composite_merge_kernel<C, TO, kPlain>;
     ART_LAUNCH(ctx, "composite_merge", mfn, 4 * ctx->num_sms, 32, 0, ctx->d_seg, ctx->d_multi, v, ctx->cfg.tau, (TO*)F,
                A, ctx->d_status, ctx->d_part, sk);
   }
+}
+
+// Plain composite: one split pass, then the sequential walk of the tiles
+// whose stop fell inside a later segment.  Learned skip: the interval pass,
+// then a plain split pass over the tiles that failed the coarse check, then
+// the sequential walk of that pass's stop cases.
+template <int C, typename TF, typename TO>
+void split_walk(art_ctx* ctx, const ViewParams& v, void* F, float* A, int mode, const SkipArgs& sk_in) {
+  const int ntiles = v.tiles_x * v.tiles_y;
+  const TF* feat = (const TF*)ctx->d_feat;
+  SkipArgs sk = sk_in;
+  sk.queue = ctx->d_fbq;
+  sk.qword = kStFallback;
+  split_pass<C, TF, TO>(ctx, v, F, A, mode, sk, nullptr, 0);
+  const uint32_t* seq = ctx->d_fbq;
+  int seq_word = kStFallback;
+  if (mode == kInterval) {  // the tiles that failed the check, walked in full (split again)
+    SkipArgs sp{};
+    sp.queue = ctx->d_fbq2;
+    sp.qword = kStFallback2;
+    split_pass<C, TF, TO>(ctx, v, F, A, kPlain, sp, ctx->d_fbq, kStFallback);
+    seq = ctx->d_fbq2;
+    seq_word = kStFallback2;
+  }
   auto qfn = composite_queue_kernel<C, TF, TO>;
   const int qgrid = std::min(ntiles, 16 * ctx->num_sms);
   ART_LAUNCH(ctx, "composite_fallback", qfn, qgrid, 32, 0, ctx->d_ranges, ctx->d_keys[0], ctx->d_vals[0], ctx->d_rec,
-             ctx->d_rect, feat, v, ctx->cfg.tau, (TO*)F, A, ctx->d_status, sk.queue);
+             ctx->d_rect, feat, v, ctx->cfg.tau, (TO*)F, A, ctx->d_status, seq, seq_word);
 }
 
 template <int C, typename TF, typename TO>

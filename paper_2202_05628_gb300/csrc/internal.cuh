@@ -33,6 +33,7 @@ enum StatusWord {
   kStNext = 10,         // next segment to walk (work counter)
   kStNextMerge = 11,    // next split tile to merge (work counter)
   kStRmax = 12,         // largest voxel bounding radius of the last pose (float bits)
+  kStFallback2 = 13,    // learned skip: tiles of the full pass whose stop needs the sequential walk
   kStWords = 16
 };
 
@@ -159,6 +160,8 @@ struct art_ctx {
   int64_t hist_n_cap = 0;
   uint32_t* d_fbq = nullptr;      // [tiles] fallback queue
   size_t d_fbq_bytes = 0;
+  uint32_t* d_fbq2 = nullptr;     // [tiles] second queue (sequential walk after a refill pass)
+  size_t d_fbq2_bytes = 0;
   // ---- split composite walk
   int seg_len = 256;              // list entries per segment
   int composite_blocks = 0;       // persistent one-warp blocks of the split walk
