@@ -120,8 +120,10 @@ struct TcCfg {
   static constexpr int kA = 128 * KCB;
   static constexpr int kB = N * KCB;
   static constexpr int kStage = kA + kB;
-  static constexpr int kStagesRaw = 196608 / kStage;
-  static constexpr int kStages = kStagesRaw > 24 ? 24 : kStagesRaw;  // more bytes in flight per SM
+  // two CTAs per SM (two issuing threads) where the accumulators fit twice in TMEM
+  static constexpr int kCtas = (N <= 128 && !F8) ? 2 : 1;
+  static constexpr int kStagesRaw = 196608 / kCtas / kStage;
+  static constexpr int kStages = kStagesRaw > 24 ? 24 : kStagesRaw;
   static constexpr int kTmemCols = 2 * N;  // two accumulators; N in {32, 64, 128, 256}
   static constexpr uint32_t kFmt = F8 ? 0u : 1u;  // A/B format: E4M3 (kind::f8f6f4) or BF16 (kind::f16)
   static constexpr uint32_t kIdesc = (1u << 4)                          // D: FP32
@@ -297,7 +299,7 @@ struct RowCfg {
   static constexpr int kA = 128 * KCB;
   static constexpr bool kStack = N == 32;
   static constexpr int kSlots = kStack ? kRows + 4 : kRows;
-  static constexpr int kTmemCols = 2 * kSlots * N;  // 512
+  static constexpr int kBufCols = kSlots * N;  // columns of one accumulator buffer (256 or 512 ... x2)
   static constexpr uint32_t kIdesc = idesc_bf16(128, kStack ? 3 * N : N);
 };
 
@@ -307,6 +309,7 @@ struct RowParams {
   int n_units;    // ceil(H / R) x tiles per row
   int n_stages;   // stages in flight (three boxes each)
   int w_bytes;    // resident weights: 9 x cpt blocks of N x KCB bytes
+  int nbuf;       // accumulator buffers (2, or 1 when two CTAs share an SM's TMEM)
 };
 
 template <int N, int KCB>
@@ -354,7 +357,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   for (int i = threadIdx.x; i < N; i += kThreads) s_bias[i] = i < p.cout ? p.bias[i] : 0.0f;
   if (p.rgba)
     for (int i = threadIdx.x; i < 4 * N + 4; i += kThreads) s_head[i] = i < 4 * N ? p.head_w[i] : p.head_b[i - 4 * N];
-  if (warp == 1) tmem_alloc(tmem_slot, Cfg::kTmemCols);
+  const int nbuf = rp.nbuf;
+  const uint32_t tmem_cols = (uint32_t)(nbuf * Cfg::kBufCols);
+  if (warp == 1) tmem_alloc(tmem_slot, tmem_cols);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -400,7 +405,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // stacked form: the epilogue clears the accumulators (phase 0 = the initial clear)
         if (!mbar_wait(&acce[buf], Cfg::kStack ? aph : aph ^ 1u, abort_flag)) break;
         tc_fence_after();
-        const uint32_t d0 = tmem_base + (uint32_t)(buf * Cfg::kSlots * N);
+        const uint32_t d0 = tmem_base + (uint32_t)(buf * Cfg::kBufCols);
         for (int st = 0; st < n_stage_unit; ++st) {
           if (!mbar_wait(&full[s], ph, abort_flag)) {
             ok = false;
@@ -443,7 +448,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         if (!ok) break;
         umma_commit(&accf[buf]);
-        if (++buf == 2) {
+        if (++buf == nbuf) {
           buf = 0;
           aph ^= 1u;
         }
@@ -458,11 +463,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     int buf = 0;
     uint32_t aph = 0;
     if constexpr (Cfg::kStack) {  // zero every slot of both buffers, then release them to the MMA
-      for (int c0 = 0; c0 < Cfg::kTmemCols; c0 += 32) tmem_zero32(tq + (uint32_t)c0);
+      for (int c0 = 0; c0 < (int)tmem_cols; c0 += 32) tmem_zero32(tq + (uint32_t)c0);
       tmem_wait_st();
       tc_fence_before();
-      mbar_arrive(&acce[0]);
-      mbar_arrive(&acce[1]);
+      for (int b = 0; b < nbuf; ++b) mbar_arrive(&acce[b]);
     }
     for (int u = blockIdx.x; u < rp.n_units; u += gridDim.x) {
       if (!mbar_wait(&accf[buf], aph, abort_flag, 256)) break;
@@ -470,7 +474,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int y0 = (u / p.tiles_per_row) * kRows, x = (u % p.tiles_per_row) * 128 + m;
       for (int r = 0; r < kRows; ++r) {
         const int slot = Cfg::kStack ? kRows + 1 - r : r;
-        const uint32_t ta = tq + (uint32_t)((buf * Cfg::kSlots + slot) * N);
+        const uint32_t ta = tq + (uint32_t)(buf * Cfg::kBufCols + slot * N);
         if (y0 + r < p.H) epi_row<N, false>(p, ta, y0 + r, x, s_bias, s_head, nullptr, 1.0f, 1.0f, amax);
         if constexpr (Cfg::kStack) {
 #pragma unroll
@@ -480,7 +484,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if constexpr (Cfg::kStack) tmem_wait_st();
       tc_fence_before();
       mbar_arrive(&acce[buf]);
-      if (++buf == 2) {
+      if (++buf == nbuf) {
         buf = 0;
         aph ^= 1u;
       }
@@ -489,7 +493,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 1) tmem_dealloc(tmem_base, Cfg::kTmemCols);
+  if (warp == 1) tmem_dealloc(tmem_base, tmem_cols);
   if (threadIdx.x == 0 && *abort_flag) atomicAdd(p.err, 1ull);
 }
 
@@ -587,7 +591,7 @@ art_status launch_typed(art_ctx* ctx, const TcConv& c) {
   auto kfn = conv_tc_kernel<N, KCB, F8>;
   cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "conv_tc shared memory attribute");
-  const int grid = std::min(p.n_tiles, ctx->num_sms);
+  const int grid = std::min(p.n_tiles, Cfg::kCtas * ctx->num_sms);
   ART_LAUNCH(ctx, F8 ? "conv_tc_fp8" : "conv_tc", kfn, grid, kThreads, Cfg::kSmem, tmA, tmB, p);
   return ART_OK;
 }
@@ -671,14 +675,19 @@ art_status launch_rows(art_ctx* ctx, const TcConv& c) {
   rp.n_units = ((c.H + kRows - 1) / kRows) * p.tiles_per_row;
   rp.w_bytes = 9 * rp.cpt * N * KCB;
   const int tail = 8 * (2 * 24 + 5) + 16 + 4 * N + 4 * (4 * 32 + 4);
-  const int avail = 232448 - 1024 - rp.w_bytes - tail;
+  // two CTAs per SM (two issuing threads, one accumulator buffer each) when
+  // the resident weights and three stages fit in half the shared memory
+  const int half = 232448 / 2 - 1024 - rp.w_bytes - tail;
+  const int ctas = half >= 3 * 3 * Cfg::kA ? 2 : 1;
+  const int avail = 232448 / ctas - 1024 - rp.w_bytes - tail;
+  rp.nbuf = ctas == 2 ? 1 : 2;
   rp.n_stages = std::min(24, avail / (3 * Cfg::kA));
   if (rp.n_stages < 2) return fail(ctx, ART_ERR_UNSUPPORTED, "row-blocked conv: weights too large");
   const int smem = 1024 + rp.w_bytes + rp.n_stages * 3 * Cfg::kA + tail;
   auto kfn = conv_rows_kernel<N, KCB>;
   cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "conv_rows shared memory attribute");
-  const int grid = std::min(rp.n_units, ctx->num_sms);
+  const int grid = std::min(rp.n_units, ctas * ctx->num_sms);
   ART_LAUNCH(ctx, "conv_tc", kfn, grid, kThreads, smem, tmA, tmB, rp);
   return ART_OK;
 }
