@@ -855,6 +855,7 @@ art_status art_render_backward(art_ctx* ctx, int view, const float* F, const flo
   const ViewParams& v = ctx->views[view];
   art_status st = ensure_bin_buffers(ctx, (int64_t)v.tiles_x * v.tiles_y);
   if (st != ART_OK) return st;
+  if ((st = ensure_split_buffers(ctx, v)) != ART_OK) return st;
   if (ctx->gN_cap < ctx->n) {
     if ((st = alloc(ctx, &ctx->d_gN, (size_t)ctx->n * 12, "geometry gradient")) != ART_OK) return st;
     ctx->gN_cap = ctx->n;

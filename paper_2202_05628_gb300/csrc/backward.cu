@@ -6,7 +6,11 @@
 // Per-ray recomputation instead of stored sample lists: the backward walks
 // each tile's instance list with exactly the forward's code (staging, masks,
 // slab test, reorder buffer, release rule, early stop), so every pixel
-// revisits the same hits in the same order.  With w_i = T_i a_i,
+// revisits the same hits in the same order.  Long lists are split into the
+// forward's depth segments, walked by separate warps: a first pass gives each
+// segment's own transmittance product and sum of w <f, g>, a prefix over the
+// segments the values each is entered with, and the gradient pass walks every
+// segment from those (exact stop rule: the true transmittance is carried).  With w_i = T_i a_i,
 // a_i = 1 - exp(-sigma_i delta_i), T_{i+1} = T_i (1 - a_i), g = dL/dF and
 // g_A = dL/dA at the pixel:
 //   dL/df_i      += w_i g
@@ -42,19 +46,21 @@ __device__ __forceinline__ void atomic_add4(float* p, float a, float b, float c,
   atomicAdd(reinterpret_cast<float4*>(p), make_float4(a, b, c, d));
 }
 
-template <int C, typename TF>
-__global__ void __launch_bounds__(32) composite_bwd_kernel(const uint2* __restrict__ ranges,
-                                                           const uint32_t* __restrict__ keys,
-                                                           const uint32_t* __restrict__ vals,
-                                                           const float4* __restrict__ rec,
-                                                           const short4* __restrict__ rect,
-                                                           const TF* __restrict__ feat, ViewParams v, float tau,
-                                                           float h, const float* __restrict__ Ffwd,
-                                                           const float* __restrict__ Afwd,
-                                                           const float* __restrict__ dF, const float* __restrict__ dA,
-                                                           float* __restrict__ gfeat, float* __restrict__ gsig,
-                                                           float* __restrict__ gN,
-                                                           unsigned long long* __restrict__ status) {
+// One segment of a tile's list (the forward's split walk: Seg, make_seg),
+// entered with the pixel's transmittance T_in and <P, g>_in of everything
+// composited before it.  PASS 0 walks the segment from T = 1, <P, g> = 0 and
+// stores its own product of (1 - a) and sum of w <f, g> ([2][32] at out);
+// PASS 1 walks it with the true incoming values and accumulates the
+// gradients.  One segment per tile is the sequential walk.
+template <int C, typename TF, int PASS>
+__device__ __forceinline__ void bwd_tile(const int tile, const Seg& sg, float T_in, float pg_in, float* out,
+                                         const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals,
+                                         const float4* __restrict__ rec, const short4* __restrict__ rect,
+                                         const TF* __restrict__ feat, const ViewParams& v, float tau, float h,
+                                         const float* __restrict__ Ffwd, const float* __restrict__ Afwd,
+                                         const float* __restrict__ dF, const float* __restrict__ dA,
+                                         float* __restrict__ gfeat, float* __restrict__ gsig, float* __restrict__ gN,
+                                         unsigned long long* __restrict__ status) {
   constexpr int RING = Ring<C, TF>::kChunks;
   __shared__ float4 s_b0[NT], s_b1[NT], s_b2[NT];
   __shared__ float s_thr[NT];
@@ -63,8 +69,7 @@ __global__ void __launch_bounds__(32) composite_bwd_kernel(const uint2* __restri
   __shared__ uint32_t s_vid[RING][NT];
   __shared__ __align__(16) TF s_feat[RING][NT][C];
 
-  const int lane = threadIdx.x;
-  const int tile = blockIdx.x;
+  const int lane = threadIdx.x & 31;
   const int tx = tile % v.tiles_x, ty = tile / v.tiles_x;
   const int sx = tx * TSX, sy = ty * TSY;
   const int px = sx + (lane & 7), py = sy + (lane >> 3);
@@ -95,8 +100,8 @@ __global__ void __launch_bounds__(32) composite_bwd_kernel(const uint2* __restri
   }
   any = any || ga != 0.0f;
 
-  float T = 1.0f, pg = 0.0f;  // transmittance before the next hit; <P_i, g>
-  bool done = !(inside && any);
+  float T = T_in, pg = pg_in;  // transmittance before the next hit; <P_i, g>
+  bool done = !(inside && any) || T < tau;
   PendG buf[kPend];
 #pragma unroll
   for (int k = 0; k < kPend; ++k) buf[k] = PendG{0.f, 0.f, 0u, 0, 0.f, 0.f};
@@ -105,7 +110,7 @@ __global__ void __launch_bounds__(32) composite_bwd_kernel(const uint2* __restri
   const uint32_t qmask = (1u << v.depth_bits) - 1u;
   const float qinv = 1.0f / v.dscale;
   int cur_chunk = 0;
-  const uint2 rg = ranges[tile];
+  const uint2 rg = make_uint2(sg.begin, sg.end);
 
   auto release_front = [&]() {
     const PendG hh = buf[0];
@@ -132,6 +137,11 @@ __global__ void __launch_bounds__(32) composite_bwd_kernel(const uint2* __restri
 #pragma unroll
     for (int c = 0; c < C; ++c) fg = fmaf(f[c], g[c], fg);
     pg = fmaf(w, fg, pg);
+    if constexpr (PASS == 0) {  // the segment's own product and sum only
+      T *= e;
+      if (T < tau) done = true;
+      return;
+    }
     const float core = T * e * fg - (Fg - pg) + Tfin * ga;
 #pragma unroll
     for (int c = 0; c < C; c += 4)
@@ -191,6 +201,7 @@ __global__ void __launch_bounds__(32) composite_bwd_kernel(const uint2* __restri
       float t0, t1, e[3];
       int ax0, ax1;
       if (!slab_hit(s_b0[idx], s_b1[idx], s_b2[idx], d0, d1, d2, v.znear, v.zfar, t0, t1, ax0, ax1, e)) continue;
+      if (t0 < sg.t0_lo || t0 >= sg.t0_hi) continue;  // another segment's hit
       const PendG p{t0, t1, base - rg.x + (uint32_t)idx, (ax0 + 1) | ((ax1 + 1) << 4),
                     ax0 == 0 ? e[0] : (ax0 == 1 ? e[1] : e[2]), ax1 == 0 ? e[0] : (ax1 == 1 ? e[1] : e[2])};
       if (nb == kPend) {
@@ -221,7 +232,64 @@ __global__ void __launch_bounds__(32) composite_bwd_kernel(const uint2* __restri
     if (__all_sync(0xffffffffu, done)) break;
   }
   while (nb > 0 && !done) release_front();
+  if constexpr (PASS == 0) {
+    out[lane] = T;
+    out[32 + lane] = pg;
+  }
   if (n_over) atomicAdd(status + kStOverflowOrder, (unsigned long long)n_over);
+}
+
+// The segments of every tile, pulled by persistent one-warp blocks.  PASS 0
+// runs only the segments of split tiles; PASS 1 every segment.
+template <int C, typename TF, int PASS>
+__global__ void __launch_bounds__(32) bwd_split_kernel(
+    const uint2* __restrict__ ranges, const uint2* __restrict__ seg, const uint32_t* __restrict__ items,
+    const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals, const float4* __restrict__ rec,
+    const short4* __restrict__ rect, const TF* __restrict__ feat, ViewParams v, float tau, float h,
+    const float* __restrict__ Ffwd, const float* __restrict__ Afwd, const float* __restrict__ dF,
+    const float* __restrict__ dA, float* __restrict__ gfeat, float* __restrict__ gsig, float* __restrict__ gN,
+    unsigned long long* __restrict__ status, float* __restrict__ part) {
+  const int lane = threadIdx.x & 31;
+  const unsigned long long n_items = status[kStItems];
+  const uint32_t wq = seg_window(v, status);
+  for (;;) {
+    unsigned long long i = 0;
+    if (lane == 0) i = atomicAdd(status + kStNext, 1ull);
+    i = __shfl_sync(0xffffffffu, i, 0);
+    if (i >= n_items) break;
+    const int tile = (int)items[i];
+    const uint2 sgt = seg[tile];
+    if (PASS == 0 && sgt.y < 2) continue;
+    const Seg sg = make_seg(v, ranges[tile], sgt, (uint32_t)i, keys, wq, lane);
+    float* pp = part + (size_t)i * 64;
+    const float T_in = (PASS == 1 && sgt.y > 1) ? pp[lane] : 1.0f;
+    const float pg_in = (PASS == 1 && sgt.y > 1) ? pp[32 + lane] : 0.0f;
+    bwd_tile<C, TF, PASS>(tile, sg, T_in, pg_in, pp, keys, vals, rec, rect, feat, v, tau, h, Ffwd, Afwd, dF, dA, gfeat,
+                          gsig, gN, status);
+  }
+}
+
+// Per split tile and pixel, in segment order: replace each segment's own
+// (product T, sum w <f, g>) by the values it is entered with,
+// T_in(s) = prod_{r<s} T_r and <P, g>_in(s) = sum_{r<s} T_in(r) sum_r.
+__global__ void __launch_bounds__(32) bwd_prefix_kernel(const uint2* __restrict__ seg,
+                                                        const uint32_t* __restrict__ multi,
+                                                        unsigned long long* __restrict__ status,
+                                                        float* __restrict__ part) {
+  const int lane = threadIdx.x & 31;
+  const unsigned long long n = status[kStMulti];
+  for (unsigned long long m = blockIdx.x; m < n; m += gridDim.x) {
+    const uint2 sgt = seg[multi[m]];
+    float T = 1.0f, pg = 0.0f;
+    for (uint32_t k = 0; k < sgt.y; ++k) {
+      float* pp = part + (size_t)(sgt.x + k) * 64;
+      const float Tk = pp[lane], sk = pp[32 + lane];
+      pp[lane] = T;
+      pp[32 + lane] = pg;
+      pg = fmaf(T, sk, pg);
+      T *= Tk;
+    }
+  }
 }
 
 // dL/dA_i = -N^T dL/dN N^T (top 3 rows of the 4x4 affine forms) with
@@ -290,10 +358,23 @@ __global__ void __launch_bounds__(256) lbs_bwd_kernel(int64_t n, const float* __
 template <int C, typename TF>
 void launch_bwd_c(art_ctx* ctx, const ViewParams& v, const float* F, const float* A, const float* dF,
                   const float* dA, float* gfeat, float* gsig) {
-  auto kfn = composite_bwd_kernel<C, TF>;
-  ART_LAUNCH(ctx, "composite_bwd", kfn, v.tiles_x * v.tiles_y, 32, 0, ctx->d_ranges, ctx->d_keys[0], ctx->d_vals[0],
-             ctx->d_rec, ctx->d_rect, (const TF*)ctx->d_feat, v, ctx->cfg.tau, ctx->h, F, A, dF, dA, gfeat, gsig,
-             ctx->d_gN, ctx->d_status);
+  const int ntiles = v.tiles_x * v.tiles_y;
+  const TF* feat = (const TF*)ctx->d_feat;
+  cudaMemsetAsync(ctx->d_status + kStItems, 0, 4 * sizeof(unsigned long long), ctx->stream);  // items .. next merge
+  ART_LAUNCH(ctx, "composite_plan", seg_plan_kernel, (ntiles + 255) / 256, 256, 0, ntiles, ctx->d_ranges,
+             ctx->seg_len, ctx->d_seg, ctx->d_items, ctx->d_multi, ctx->d_status, (const uint32_t*)nullptr, 0);
+  const int grid = ctx->composite_blocks;
+  auto k0 = bwd_split_kernel<C, TF, 0>;
+  ART_LAUNCH(ctx, "composite_bwd_scan", k0, grid, 32, 0, ctx->d_ranges, ctx->d_seg, ctx->d_items, ctx->d_keys[0],
+             ctx->d_vals[0], ctx->d_rec, ctx->d_rect, feat, v, ctx->cfg.tau, ctx->h, F, A, dF, dA, gfeat, gsig,
+             ctx->d_gN, ctx->d_status, ctx->d_part);
+  ART_LAUNCH(ctx, "composite_bwd_prefix", bwd_prefix_kernel, 4 * ctx->num_sms, 32, 0, ctx->d_seg, ctx->d_multi,
+             ctx->d_status, ctx->d_part);
+  cudaMemsetAsync(ctx->d_status + kStNext, 0, sizeof(unsigned long long), ctx->stream);
+  auto k1 = bwd_split_kernel<C, TF, 1>;
+  ART_LAUNCH(ctx, "composite_bwd", k1, grid, 32, 0, ctx->d_ranges, ctx->d_seg, ctx->d_items, ctx->d_keys[0],
+             ctx->d_vals[0], ctx->d_rec, ctx->d_rect, feat, v, ctx->cfg.tau, ctx->h, F, A, dF, dA, gfeat, gsig,
+             ctx->d_gN, ctx->d_status, ctx->d_part);
 }
 
 template <int C>

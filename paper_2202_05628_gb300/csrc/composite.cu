@@ -56,15 +56,6 @@ __device__ __forceinline__ float tile_hist_prefix(const float* __restrict__ th, 
   return pre[63];
 }
 
-// The part of a tile's list one warp walks: list positions [begin, end),
-// hits whose entry t0 lies in [t0_lo, t0_hi); with part set, the walk stores
-// its partial feature sum and transmittance there instead of the outputs.
-struct Seg {
-  uint32_t begin, end;
-  float t0_lo, t0_hi;
-  float* part;  // [C + 1][32]: partial F (per channel), then T
-};
-
 // One warp per 8x4 tile, lane = pixel (x = lane & 7, y = lane >> 3).
 template <int C, typename TF, typename TO, int MODE>
 __device__ __forceinline__ void composite_tile(const int tile, const Seg& sg,
@@ -349,7 +340,6 @@ __global__ void __launch_bounds__(32) composite_kernel(const uint2* __restrict__
 // the first segment that a pixel's transmittance enters below tau if that
 // pixel entered it with T = 1; otherwise its tile is queued for the plain walk.
 
-constexpr int kMaxSegs = 255;
 
 // Zero F and A of the tiles without instances (the segments cover the rest).
 template <int C, typename TO>
@@ -370,55 +360,6 @@ __global__ void __launch_bounds__(256) composite_clear_kernel(const uint2* __res
   if (Aout) Aout[pix] = 0.0f;
 }
 
-// Per tile: number of segments and the index of its first one; the segments
-// of all tiles in one list, the tiles with two or more in another.
-// With tiles_in set, only the tiles listed there (count in status[in_word]).
-__global__ void seg_plan_kernel(int ntiles, const uint2* __restrict__ ranges, int seg_len, uint2* __restrict__ seg,
-                                uint32_t* __restrict__ items, uint32_t* __restrict__ multi,
-                                unsigned long long* __restrict__ status, const uint32_t* __restrict__ tiles_in,
-                                int in_word) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  int t = i;
-  if (tiles_in) {
-    if ((unsigned long long)i >= status[in_word]) return;
-    t = (int)tiles_in[i];
-  }
-  if (t >= ntiles) return;
-  const uint2 rg = ranges[t];
-  const uint32_t len = rg.y - rg.x;
-  uint32_t S = len == 0 ? 0u : (len + seg_len - 1) / seg_len;
-  if (S > kMaxSegs) S = kMaxSegs;
-  uint32_t base = 0;
-  if (S) {
-    base = (uint32_t)atomicAdd(status + kStItems, (unsigned long long)S);
-    for (uint32_t k = 0; k < S; ++k) items[base + k] = (uint32_t)t;
-    if (S > 1) multi[atomicAdd(status + kStMulti, 1ull)] = (uint32_t)t;
-  }
-  seg[t] = make_uint2(base, S);
-}
-
-// First position in [a, b) whose depth quantum is >= qt (b if none): keys are
-// sorted within the tile.  Warp-cooperative: 32 probes per round.
-__device__ __forceinline__ uint32_t lower_bound_q(const uint32_t* __restrict__ keys, uint32_t a, uint32_t b,
-                                                  uint32_t qmask, uint32_t qt, int lane) {
-  while (b - a > 31u) {
-    const uint32_t step = (b - a + 31u) / 32u;
-    const uint32_t idx = a + (uint32_t)lane * step;
-    const bool ge = idx >= b || (keys[idx] & qmask) >= qt;
-    const uint32_t m = __ballot_sync(0xffffffffu, ge);
-    if (m & 1u) return a;
-    const uint32_t f = m ? (uint32_t)(__ffs(m) - 1) : 32u;
-    const uint32_t na = a + (f - 1u) * step + 1u;
-    const uint32_t nb = f < 32u ? min(b, a + f * step) : b;
-    a = na;
-    b = nb;
-  }
-  const uint32_t idx = a + (uint32_t)lane;
-  const bool ge = idx >= b || (keys[idx] & qmask) >= qt;
-  const uint32_t m = __ballot_sync(0xffffffffu, ge);
-  return a + (uint32_t)(__ffs(m) - 1);  // lane b - a (<= 31) is always set
-}
-
 template <int C, typename TF, typename TO, int MODE>
 __global__ void __launch_bounds__(32) composite_split_kernel(
     const uint2* __restrict__ ranges, const uint2* __restrict__ seg, const uint32_t* __restrict__ items,
@@ -426,12 +367,8 @@ __global__ void __launch_bounds__(32) composite_split_kernel(
     const short4* __restrict__ rect, const TF* __restrict__ feat, ViewParams v, float tau, TO* __restrict__ Fout,
     float* __restrict__ Aout, unsigned long long* __restrict__ status, float* __restrict__ part, SkipArgs sk) {
   const int lane = threadIdx.x & 31;
-  const uint32_t qmask = (1u << v.depth_bits) - 1u;
-  const float qinv = 1.0f / v.dscale;
   const unsigned long long n_items = status[kStItems];
-  // window in depth quanta: 2 r_max + 3 quanta (+ FP32 slack)
-  const float rmax = __uint_as_float((uint32_t)status[kStRmax]);
-  const uint32_t wq = (uint32_t)ceilf((2.0f * rmax + 1e-5f) * v.dscale) + 3u;
+  const uint32_t wq = seg_window(v, status);
   for (;;) {
     unsigned long long i = 0;
     if (lane == 0) i = atomicAdd(status + kStNext, 1ull);
@@ -439,23 +376,8 @@ __global__ void __launch_bounds__(32) composite_split_kernel(
     if (i >= n_items) break;
     const int tile = (int)items[i];
     const uint2 sgt = seg[tile];
-    const uint32_t k = (uint32_t)i - sgt.x, S = sgt.y;
-    const uint2 rg = ranges[tile];
-    const uint32_t len = rg.y - rg.x;
-    const uint32_t pk = rg.x + (uint32_t)(((unsigned long long)k * len) / S);
-    const uint32_t pk1 = rg.x + (uint32_t)(((unsigned long long)(k + 1) * len) / S);
-    Seg sg;
-    sg.end = pk1;
-    if (k == 0) {
-      sg.begin = rg.x;
-      sg.t0_lo = -3.4e38f;
-    } else {
-      const uint32_t qk = keys[pk] & qmask;
-      sg.t0_lo = v.znear + (float)qk * qinv;
-      sg.begin = lower_bound_q(keys, rg.x, pk, qmask, qk > wq ? qk - wq : 0u, lane);
-    }
-    sg.t0_hi = k + 1 < S ? v.znear + (float)(keys[pk1] & qmask) * qinv : 3.4e38f;
-    sg.part = S > 1 ? part + (size_t)i * (C + 1) * 32 : nullptr;
+    Seg sg = make_seg(v, ranges[tile], sgt, (uint32_t)i, keys, wq, lane);
+    sg.part = sgt.y > 1 ? part + (size_t)i * (C + 1) * 32 : nullptr;
     composite_tile<C, TF, TO, MODE>(tile, sg, keys, vals, rec, rect, feat, v, tau, Fout, Aout, status, HitLog{},
                                     sk);
   }

@@ -247,4 +247,101 @@ __device__ __forceinline__ void pixel_dir(const ViewParams& v, int px, int py, f
   d2 *= inrm;
 }
 
+
+// ------------------------------------------------------------ split walk
+
+// The part of a tile's list one warp walks: list positions [begin, end),
+// hits whose entry t0 lies in [t0_lo, t0_hi); with part set, the walk stores
+// its partial feature sum and transmittance there instead of the outputs.
+struct Seg {
+  uint32_t begin, end;
+  float t0_lo, t0_hi;
+  float* part;  // [C + 1][32]: partial F (per channel), then T
+};
+
+constexpr int kMaxSegs = 255;
+
+// Per tile: number of segments and the index of its first one; the segments
+// of all tiles in one list, the tiles with two or more in another.
+// With tiles_in set, only the tiles listed there (count in status[in_word]).
+static __global__ void seg_plan_kernel(int ntiles, const uint2* __restrict__ ranges, int seg_len, uint2* __restrict__ seg,
+                                uint32_t* __restrict__ items, uint32_t* __restrict__ multi,
+                                unsigned long long* __restrict__ status, const uint32_t* __restrict__ tiles_in,
+                                int in_word) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int t = i;
+  if (tiles_in) {
+    if ((unsigned long long)i >= status[in_word]) return;
+    t = (int)tiles_in[i];
+  }
+  if (t >= ntiles) return;
+  const uint2 rg = ranges[t];
+  const uint32_t len = rg.y - rg.x;
+  uint32_t S = len == 0 ? 0u : (len + seg_len - 1) / seg_len;
+  if (S > kMaxSegs) S = kMaxSegs;
+  uint32_t base = 0;
+  if (S) {
+    base = (uint32_t)atomicAdd(status + kStItems, (unsigned long long)S);
+    for (uint32_t k = 0; k < S; ++k) items[base + k] = (uint32_t)t;
+    if (S > 1) multi[atomicAdd(status + kStMulti, 1ull)] = (uint32_t)t;
+  }
+  seg[t] = make_uint2(base, S);
+}
+
+// First position in [a, b) whose depth quantum is >= qt (b if none): keys are
+// sorted within the tile.  Warp-cooperative: 32 probes per round.
+__device__ __forceinline__ uint32_t lower_bound_q(const uint32_t* __restrict__ keys, uint32_t a, uint32_t b,
+                                                  uint32_t qmask, uint32_t qt, int lane) {
+  while (b - a > 31u) {
+    const uint32_t step = (b - a + 31u) / 32u;
+    const uint32_t idx = a + (uint32_t)lane * step;
+    const bool ge = idx >= b || (keys[idx] & qmask) >= qt;
+    const uint32_t m = __ballot_sync(0xffffffffu, ge);
+    if (m & 1u) return a;
+    const uint32_t f = m ? (uint32_t)(__ffs(m) - 1) : 32u;
+    const uint32_t na = a + (f - 1u) * step + 1u;
+    const uint32_t nb = f < 32u ? min(b, a + f * step) : b;
+    a = na;
+    b = nb;
+  }
+  const uint32_t idx = a + (uint32_t)lane;
+  const bool ge = idx >= b || (keys[idx] & qmask) >= qt;
+  const uint32_t m = __ballot_sync(0xffffffffu, ge);
+  return a + (uint32_t)(__ffs(m) - 1);  // lane b - a (<= 31) is always set
+}
+
+// Window of a segment's scan before its first depth bound, in depth quanta:
+// 2 r_max + 3 quanta (+ FP32 slack); r_max of the pose is status[kStRmax].
+__device__ __forceinline__ uint32_t seg_window(const ViewParams& v, const unsigned long long* status) {
+  const float rmax = __uint_as_float((uint32_t)status[kStRmax]);
+  return (uint32_t)ceilf((2.0f * rmax + 1e-5f) * v.dscale) + 3u;
+}
+
+// Segment k = i - first of a tile with S segments: list positions
+// p_k = start + k len / S; it composites the hits with entry t0 in
+// [D_k, D_{k+1}) (D_k the depth bound at p_k) and walks from the first entry
+// whose bound lies within the window before D_k up to p_{k+1}.
+__device__ __forceinline__ Seg make_seg(const ViewParams& v, uint2 rg, uint2 sgt, uint32_t i,
+                                        const uint32_t* __restrict__ keys, uint32_t wq, int lane) {
+  const uint32_t qmask = (1u << v.depth_bits) - 1u;
+  const float qinv = 1.0f / v.dscale;
+  const uint32_t k = i - sgt.x, S = sgt.y;
+  const uint32_t len = rg.y - rg.x;
+  const uint32_t pk = rg.x + (uint32_t)(((unsigned long long)k * len) / S);
+  const uint32_t pk1 = rg.x + (uint32_t)(((unsigned long long)(k + 1) * len) / S);
+  Seg sg;
+  sg.end = pk1;
+  if (k == 0) {
+    sg.begin = rg.x;
+    sg.t0_lo = -3.4e38f;
+  } else {
+    const uint32_t qk = keys[pk] & qmask;
+    sg.t0_lo = v.znear + (float)qk * qinv;
+    sg.begin = lower_bound_q(keys, rg.x, pk, qmask, qk > wq ? qk - wq : 0u, lane);
+  }
+  sg.t0_hi = k + 1 < S ? v.znear + (float)(keys[pk1] & qmask) * qinv : 3.4e38f;
+  sg.part = nullptr;
+  return sg;
+}
+
 }  // namespace art

@@ -19,10 +19,10 @@ def _cuda():
         pytest.skip("no CUDA device")
 
 
-def _gpu_grads(sc, pose, cams, gFs, gAs, storage="f32"):
+def _gpu_grads(sc, pose, cams, gFs, gAs, storage="f32", segment=256, tau=1e-4):
     import torch
     oc = sc.octree
-    r = renderer(sc, storage=storage)
+    r = renderer(sc, storage=storage, segment=segment, tau=tau)
     set_pose(r, pose)
     gf = torch.zeros((oc.n, oc.C), dtype=torch.float32, device="cuda")
     gd = torch.zeros(oc.n, dtype=torch.float32, device="cuda")
@@ -40,14 +40,14 @@ def _gpu_grads(sc, pose, cams, gFs, gAs, storage="f32"):
     return gf.cpu().numpy().astype(np.float64), gd.cpu().numpy().astype(np.float64), gw.cpu().numpy().astype(np.float64)
 
 
-def _oracle_grads(sc, pose, cams, gFs, gAs, features=None):
+def _oracle_grads(sc, pose, cams, gFs, gAs, features=None, tau=1e-4):
     oc = sc.octree
     G, A, _ = oracle.pose_transforms(sc, pose)
     gf = np.zeros((oc.n, oc.C))
     gd = np.zeros(oc.n)
     gN = np.zeros((oc.n, 3, 4))
     for cam, gF, gA in zip(cams, gFs, gAs):
-        a, b, c = oracle.render_backward(oc, A, cam, gF, gA, features=features)
+        a, b, c = oracle.render_backward(oc, A, cam, gF, gA, tau=tau, features=features)
         gf += a
         gd += b
         gN += c
@@ -75,6 +75,28 @@ def test_backward_matches_oracle_small():
     gAs = [rng.standard_normal((96, 96)) for _ in cams]
     g = _gpu_grads(sc, pose, cams, gFs, gAs)
     o = _oracle_grads(sc, pose, cams, gFs, gAs)
+    _close(g[0], o[0], 3e-4, "dL/df")
+    _close(g[1], o[1], 1e-3, "dL/dsigma")
+    _close(g[2], o[2], 5e-3, "dL/dw")
+
+
+@pytest.mark.parametrize("segment,tau", [(32, 1e-4), (96, 0.7)])
+def test_backward_split_walk_matches_oracle(segment, tau):
+    """Lists walked in short depth segments by separate warps (a pass for
+    each segment's own transmittance and <P, g>, a prefix over segments, the
+    gradient pass) against the oracle and against one segment per tile; with
+    tau = 0.7 the stop falls inside later segments."""
+    sc = sg.preset("tiny")
+    pose = sg.random_pose(17)
+    cams = [sg.orbit_camera(sc.centroid, 64, 64, az_deg=a, fov_deg=8.0) for a in (40.0, 200.0)]
+    rng = np.random.default_rng(2)
+    gFs = [rng.standard_normal((64, 64, sc.octree.C)) for _ in cams]
+    gAs = [rng.standard_normal((64, 64)) for _ in cams]
+    g = _gpu_grads(sc, pose, cams, gFs, gAs, segment=segment, tau=tau)
+    g1 = _gpu_grads(sc, pose, cams, gFs, gAs, segment=1 << 24, tau=tau)
+    o = _oracle_grads(sc, pose, cams, gFs, gAs, tau=tau)
+    for a, b, what in zip(g, g1, ("dL/df", "dL/dsigma", "dL/dw")):
+        _close(a, b, 1e-5, what + " split vs one segment")  # the same sums, atomics in another order
     _close(g[0], o[0], 3e-4, "dL/df")
     _close(g[1], o[1], 1e-3, "dL/dsigma")
     _close(g[2], o[2], 5e-3, "dL/dw")
