@@ -168,12 +168,13 @@ art_status launch_check(art_ctx* ctx, const char* what) {
 
 void free_all(art_ctx* ctx) {
   void* ptrs[] = {ctx->d_ijk, ctx->d_jidx, ctx->d_w, ctx->d_feat, ctx->d_sigma, ctx->d_skel, ctx->d_pose, ctx->d_G,
-                  ctx->d_rec, ctx->d_geo, ctx->d_rect, ctx->d_q, ctx->d_cnt, ctx->d_off, ctx->d_bsum,
-                  ctx->d_keys[0], ctx->d_keys[1], ctx->d_vals[0], ctx->d_vals[1], ctx->d_hist, ctx->d_ranges,
+                  ctx->d_rec, ctx->d_geo, ctx->d_rect, ctx->d_q, ctx->d_cnt, ctx->d_keys,
+                  ctx->d_vals, ctx->d_sort_tmp, ctx->d_ranges,
                   ctx->d_status, ctx->d_F, ctx->d_A, ctx->d_rgba, ctx->d_act, ctx->d_sk, ctx->d_sv,
                   ctx->d_shist, ctx->d_sbsum, ctx->d_gN, ctx->d_f8_scale, ctx->d_f8_amax, ctx->d_prop_img,
                   ctx->d_prop_f32, ctx->d_pose_bias, ctx->d_bins, ctx->d_thist, ctx->d_hbin, ctx->d_htau, ctx->d_fbq,
-                  ctx->d_seg, ctx->d_items, ctx->d_multi, ctx->d_part, ctx->d_fbq2};
+                  ctx->d_seg, ctx->d_items, ctx->d_multi, ctx->d_part, ctx->d_fbq2, ctx->d_tcount, ctx->d_toff,
+                  ctx->d_sortlist};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& L : ctx->layers) {
@@ -208,21 +209,19 @@ art_config default_config() {
 art_status ensure_bin_buffers(art_ctx* ctx, int64_t ntiles) {
   int64_t cap = ctx->cfg.instance_cap > 0 ? ctx->cfg.instance_cap : 4 * ctx->n + 65536;
   if (cap > (int64_t)0xFFFFFFF0LL) cap = (int64_t)0xFFFFFFF0LL;
-  if (cap != ctx->inst_cap) {
-    art_status st;
-    for (int k = 0; k < 2; ++k) {
-      if ((st = alloc(ctx, &ctx->d_keys[k], (size_t)cap, "instance keys")) != ART_OK) return st;
-      if ((st = alloc(ctx, &ctx->d_vals[k], (size_t)cap, "instance values")) != ART_OK) return st;
-    }
-    size_t hw = sort_hist_words(cap);
-    if ((st = alloc(ctx, &ctx->d_hist, hw, "sort histogram")) != ART_OK) return st;
-    size_t bw = std::max(scan_block_words(ctx->n), scan_block_words((int64_t)hw));
-    if ((st = alloc(ctx, &ctx->d_bsum, bw, "scan block sums")) != ART_OK) return st;
+  const bool new_cap = cap != ctx->inst_cap, more_tiles = ntiles > ctx->ranges_cap;
+  art_status st;
+  if (new_cap) {
+    if ((st = alloc(ctx, &ctx->d_keys, (size_t)cap, "instance keys")) != ART_OK) return st;
+    if ((st = alloc(ctx, &ctx->d_vals, (size_t)cap, "instance values")) != ART_OK) return st;
+    if ((st = alloc(ctx, &ctx->d_sort_tmp, (size_t)cap, "bucket staging")) != ART_OK) return st;
     ctx->inst_cap = cap;
   }
-  if (ntiles > ctx->ranges_cap) {
-    art_status st = alloc(ctx, &ctx->d_ranges, (size_t)ntiles, "tile ranges");
-    if (st != ART_OK) return st;
+  if (more_tiles) {
+    if ((st = alloc(ctx, &ctx->d_ranges, (size_t)ntiles, "tile ranges")) != ART_OK) return st;
+    if ((st = alloc(ctx, &ctx->d_tcount, (size_t)ntiles, "tile counts")) != ART_OK) return st;
+    if ((st = alloc(ctx, &ctx->d_toff, (size_t)ntiles, "tile offsets")) != ART_OK) return st;
+    if ((st = alloc(ctx, &ctx->d_sortlist, (size_t)ntiles, "tile sort list")) != ART_OK) return st;
     ctx->ranges_cap = ntiles;
   }
   return ART_OK;
@@ -505,9 +504,7 @@ art_status art_render_labels(art_ctx* ctx, int view, float* labels_out, uint8_t*
   if (st != ART_OK) return st;
   if ((st = ensure_skip_buffers(ctx, v)) != ART_OK) return st;
   launch_project(ctx, v, ctx->d_hbin, ctx->d_htau);
-  launch_scan_emit(ctx, v, ctx->d_hbin, ctx->d_htau, ctx->d_thist);
-  launch_sort(ctx, 32);
-  launch_ranges(ctx, v);
+  launch_bin(ctx, v, ctx->d_hbin, ctx->d_htau, ctx->d_thist);
   if ((st = launch_composite_labels(ctx, v, labels_out, bins_out)) != ART_OK) return st;
   return launch_check(ctx, "render_labels");
 }
@@ -567,17 +564,13 @@ static art_status render_to_device(art_ctx* ctx, int view, void* F, int F_dtype,
     if (!ctx->prop_loaded) return fail(ctx, ART_ERR_STATE, "learned skip without a proposal (art_load_proposal)");
     if ((st = ensure_skip_buffers(ctx, v)) != ART_OK) return st;
     launch_project(ctx, v, ctx->d_hbin, ctx->d_htau);
-    launch_scan_emit(ctx, v, ctx->d_hbin, ctx->d_htau, ctx->d_thist);
-    launch_sort(ctx, 32);
-    launch_ranges(ctx, v);
+    launch_bin(ctx, v, ctx->d_hbin, ctx->d_htau, ctx->d_thist);
     if ((st = launch_proposal(ctx, v, ctx->d_bins, nullptr, true)) != ART_OK) return st;
     if ((st = launch_composite_skip(ctx, v, F, F_dtype, A)) != ART_OK) return st;
     return launch_check(ctx, "render_feature_maps");
   }
   launch_project(ctx, v);
-  launch_scan_emit(ctx, v);
-  launch_sort(ctx, 32);
-  launch_ranges(ctx, v);
+  launch_bin(ctx, v);
   if ((st = launch_composite(ctx, v, F, F_dtype, A)) != ART_OK) return st;
   return launch_check(ctx, "render_feature_maps");
 }
@@ -862,9 +855,7 @@ art_status art_render_backward(art_ctx* ctx, int view, const float* F, const flo
   }
   cudaMemsetAsync(ctx->d_gN, 0, sizeof(float) * 12 * (size_t)ctx->n, ctx->stream);
   launch_project(ctx, v);
-  launch_scan_emit(ctx, v);
-  launch_sort(ctx, 32);
-  launch_ranges(ctx, v);
+  launch_bin(ctx, v);
   if ((st = launch_backward(ctx, v, F, A, dF, dA, d_features, d_density, d_weights)) != ART_OK) return st;
   return launch_check(ctx, "render_backward");
 }
@@ -884,8 +875,8 @@ art_status art_debug_buffer(art_ctx* ctx, int which, void* dst, int64_t bytes, i
     case ART_BUF_VOXEL_GEO: src = ctx->d_geo; sz = ctx->n * 64; break;
     case ART_BUF_RECT: src = ctx->d_rect; sz = ctx->n * 8; break;
     case ART_BUF_DEPTHKEY: src = ctx->d_q; sz = ctx->n * 4; break;
-    case ART_BUF_KEYS: src = ctx->d_keys[0]; sz = (int64_t)ninst * 4; break;
-    case ART_BUF_VALS: src = ctx->d_vals[0]; sz = (int64_t)ninst * 4; break;
+    case ART_BUF_KEYS: src = ctx->d_keys; sz = (int64_t)ninst * 4; break;
+    case ART_BUF_VALS: src = ctx->d_vals; sz = (int64_t)ninst * 4; break;
     case ART_BUF_RANGES: src = ctx->d_ranges; sz = ctx->ranges_cap * 8; break;
     case ART_BUF_FP8_SCALES: src = ctx->d_f8_scale; sz = ctx->d_f8_scale ? kF8Tensors * 4 : 0; break;
     case ART_BUF_ACTIVATIONS: src = ctx->d_act; sz = ctx->d_act ? (int64_t)ctx->d_act_bytes : 0; break;
@@ -930,9 +921,7 @@ art_status art_debug_hits(art_ctx* ctx, int view, int cap, int32_t* count, uint3
     if (st == ART_OK) {
       void* log = make_hit_log(dc, di, d0, d1, cap);
       launch_project(ctx, v);
-      launch_scan_emit(ctx, v);
-      launch_sort(ctx, 32);
-      launch_ranges(ctx, v);
+      launch_bin(ctx, v);
       st = launch_composite(ctx, v, dF, ART_F32, dA, log);
       free_hit_log(log);
     }

@@ -365,15 +365,15 @@ void launch_bwd_c(art_ctx* ctx, const ViewParams& v, const float* F, const float
              ctx->seg_len, ctx->d_seg, ctx->d_items, ctx->d_multi, ctx->d_status, (const uint32_t*)nullptr, 0);
   const int grid = ctx->composite_blocks;
   auto k0 = bwd_split_kernel<C, TF, 0>;
-  ART_LAUNCH(ctx, "composite_bwd_scan", k0, grid, 32, 0, ctx->d_ranges, ctx->d_seg, ctx->d_items, ctx->d_keys[0],
-             ctx->d_vals[0], ctx->d_rec, ctx->d_rect, feat, v, ctx->cfg.tau, ctx->h, F, A, dF, dA, gfeat, gsig,
+  ART_LAUNCH(ctx, "composite_bwd_scan", k0, grid, 32, 0, ctx->d_ranges, ctx->d_seg, ctx->d_items, ctx->d_keys,
+             ctx->d_vals, ctx->d_rec, ctx->d_rect, feat, v, ctx->cfg.tau, ctx->h, F, A, dF, dA, gfeat, gsig,
              ctx->d_gN, ctx->d_status, ctx->d_part);
   ART_LAUNCH(ctx, "composite_bwd_prefix", bwd_prefix_kernel, 4 * ctx->num_sms, 32, 0, ctx->d_seg, ctx->d_multi,
              ctx->d_status, ctx->d_part);
   cudaMemsetAsync(ctx->d_status + kStNext, 0, sizeof(unsigned long long), ctx->stream);
   auto k1 = bwd_split_kernel<C, TF, 1>;
-  ART_LAUNCH(ctx, "composite_bwd", k1, grid, 32, 0, ctx->d_ranges, ctx->d_seg, ctx->d_items, ctx->d_keys[0],
-             ctx->d_vals[0], ctx->d_rec, ctx->d_rect, feat, v, ctx->cfg.tau, ctx->h, F, A, dF, dA, gfeat, gsig,
+  ART_LAUNCH(ctx, "composite_bwd", k1, grid, 32, 0, ctx->d_ranges, ctx->d_seg, ctx->d_items, ctx->d_keys,
+             ctx->d_vals, ctx->d_rec, ctx->d_rect, feat, v, ctx->cfg.tau, ctx->h, F, A, dF, dA, gfeat, gsig,
              ctx->d_gN, ctx->d_status, ctx->d_part);
 }
 

@@ -1,7 +1,7 @@
-// Screen-tile binning of the warped voxels and a device LSD radix sort of the
-// (tile, depth) keys.  This per-frame indexing step plays the role of the
-// paper's per-frame octree rebuild before the ray-voxel test (arXiv
-// 2202.05628, Sec. 3.1 "Dynamic Volume Rendering").
+// Screen-tile binning of the warped voxels into (tile, depth)-ordered lists,
+// and a device LSD radix sort of key/value pairs.  The per-frame binning
+// plays the role of the paper's per-frame octree rebuild before the ray-voxel
+// test (arXiv 2202.05628, Sec. 3.1 "Dynamic Volume Rendering").
 #include <mutex>
 
 #include "internal.cuh"
@@ -133,58 +133,6 @@ __global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const uint32_t
   }
 }
 
-// Scan the per-voxel tile counts and emit (key, voxel) instances:
-// key = tile << depth_bits | depth quantum.
-__global__ void __launch_bounds__(kScanThreads) emit_kernel(int64_t n, const uint32_t* __restrict__ cnt,
-                                                            const uint32_t* __restrict__ bsum,
-                                                            const short4* __restrict__ rect,
-                                                            const uint32_t* __restrict__ q, ViewParams v,
-                                                            int64_t cap, uint32_t* __restrict__ keys,
-                                                            uint32_t* __restrict__ vals,
-                                                            unsigned long long* __restrict__ status,
-                                                            const uint32_t* __restrict__ hbin,
-                                                            const float* __restrict__ htau,
-                                                            float* __restrict__ thist) {
-  int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * kScanItems;
-  uint32_t c[kScanItems];
-  uint32_t s = 0;
-#pragma unroll
-  for (int k = 0; k < kScanItems; ++k) {
-    c[k] = (base + k < n) ? cnt[base + k] : 0u;
-    s += c[k];
-  }
-  uint64_t off = (uint64_t)block_exclusive_scan(s, nullptr) + bsum[blockIdx.x];
-  uint32_t over = 0;
-  for (int k = 0; k < kScanItems; ++k) {
-    if (c[k] == 0) continue;
-    int64_t i = base + k;
-    short4 r = rect[i];
-    uint32_t qq = q[i];
-    int tx0 = r.x >> v.tile_wl, tx1 = r.z >> v.tile_wl, ty0 = r.y >> v.tile_hl, ty1 = r.w >> v.tile_hl;
-    int hb0 = 1, hb1 = 0;
-    float ht = 0.0f;
-    if (thist) {
-      const uint32_t hb = hbin[i];
-      hb0 = (int)(hb & 0xFFu);
-      hb1 = (int)(hb >> 8);
-      ht = htau[i];
-    }
-    for (int ty = ty0; ty <= ty1; ++ty)
-      for (int tx = tx0; tx <= tx1; ++tx) {
-        uint32_t tile = (uint32_t)(ty * v.tiles_x + tx);
-        if (off < (uint64_t)cap) {
-          keys[off] = (tile << v.depth_bits) | qq;
-          vals[off] = (uint32_t)i;
-        } else {
-          ++over;
-        }
-        ++off;
-        for (int b = hb0; b <= hb1; ++b) atomicAdd(thist + (size_t)tile * kPropBins + b, ht);
-      }
-  }
-  if (over) atomicAdd(status + kStOverflowInst, (unsigned long long)over);
-}
-
 // ---------------------------------------------------------------- radix sort
 
 // number of keys: the device count word, clamped to the capacity
@@ -262,14 +210,381 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(
   }
 }
 
-// Tile ranges [start, end) in the sorted instance list.
-__global__ void ranges_kernel(const uint32_t* __restrict__ keys, int64_t cap, const unsigned long long* __restrict__ st,
-                              int depth_bits, uint2* __restrict__ ranges) {
-  int64_t n = num_keys(st, cap);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    uint32_t tile = keys[i] >> depth_bits;
-    if (i == 0 || (keys[i - 1] >> depth_bits) != tile) ranges[tile].x = (uint32_t)i;
-    if (i == n - 1 || (keys[i + 1] >> depth_bits) != tile) ranges[tile].y = (uint32_t)(i + 1);
+// ---------------------------------------------------- binning by tile buckets
+//
+// The frame's (tile, depth) order without a global sort: count the instances
+// of every tile, scan the counts (the tile ranges), scatter every instance
+// into its tile's bucket, then sort each bucket by (depth quantum, voxel id).
+// That is the order of a stable sort of the keys emitted in voxel order, so
+// the result does not depend on the order in which the atomics land.
+
+constexpr int kTileScanThreads = 1024;
+constexpr int kTileScanItems = 16;       // tiles per thread and chunk
+constexpr int kTileSortThreads = 512;
+constexpr int kTileSortWarps = kTileSortThreads / 32;
+constexpr int kSortPer = 16;             // bucket entries per thread held in registers
+constexpr int kTileSortSmem = kTileSortThreads * kSortPer;  // buckets staged in shared memory (8192)
+constexpr int kWarpSortCap = 256;        // buckets up to this size: one warp each
+constexpr int kSortBins = 4096;          // depth bins of a block-sorted bucket
+constexpr int kRankMax = 64;             // bins up to this size: entries ranked by counting
+
+// The tiles x0..x1 by y0..y1 of a pixel rectangle, the k-th in row-major order.
+__device__ __forceinline__ uint32_t rect_tile(const ViewParams& v, int tx0, int ty0, int w, uint32_t k) {
+  return (uint32_t)((ty0 + (int)(k / (uint32_t)w)) * v.tiles_x + tx0 + (int)(k % (uint32_t)w));
+}
+
+// Per voxel: one count for every tile its pixel rectangle covers.  Lanes of a
+// warp that hit the same tile in the same step add together.
+__global__ void __launch_bounds__(256) tile_count_kernel(int64_t n, const uint32_t* __restrict__ cnt,
+                                                         const short4* __restrict__ rect, ViewParams v,
+                                                         uint32_t* __restrict__ tcount) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  uint32_t c = 0;
+  int tx0 = 0, ty0 = 0, w = 1;
+  if (i < n && (c = cnt[i]) != 0) {
+    const short4 r = rect[i];
+    tx0 = r.x >> v.tile_wl;
+    ty0 = r.y >> v.tile_hl;
+    w = (r.z >> v.tile_wl) - tx0 + 1;
+  }
+  const uint32_t steps = __reduce_max_sync(0xFFFFFFFFu, c);
+  for (uint32_t k = 0; k < steps; ++k) {
+    const uint32_t tile = k < c ? rect_tile(v, tx0, ty0, w, k) : 0xFFFFFFFFu;
+    const unsigned grp = __match_any_sync(0xFFFFFFFFu, tile);
+    if (tile != 0xFFFFFFFFu && lane == __ffs(grp) - 1) atomicAdd(tcount + tile, (uint32_t)__popc(grp));
+  }
+}
+
+// Shared-memory slot of element i of a chunk: one pad word per 32 so that
+// threads reading consecutive runs of kTileScanItems hit distinct banks.
+__device__ __forceinline__ int scan_slot(int i) { return i + (i >> 5); }
+constexpr int kTileScanChunk = kTileScanThreads * kTileScanItems;
+constexpr int kTileScanSmem = 4 * (kTileScanChunk + kTileScanChunk / 32 + 1);
+
+// One block: exclusive scan of the tile counts into the bucket cursors and
+// the tile ranges (clamped to the capacity), the total into kStInstances,
+// and the tiles whose bucket needs sorting: those of 2..kWarpSortCap
+// instances from the front of sort_list, longer ones from its end
+// (kStSortTiles and kStSortBig of them; both work counters reset).  Chunks
+// pass through shared memory so that every global access is coalesced.
+__global__ void __launch_bounds__(kTileScanThreads) tile_scan_kernel(int ntiles, const uint32_t* __restrict__ tcount,
+                                                                     int64_t cap, uint32_t* __restrict__ toff,
+                                                                     uint2* __restrict__ ranges,
+                                                                     uint32_t* __restrict__ sort_list,
+                                                                     unsigned long long* __restrict__ status) {
+  extern __shared__ uint32_t sbuf[];
+  uint64_t carry = 0;
+  uint32_t n_small = 0, n_big = 0;
+  for (int base0 = 0; base0 < ntiles; base0 += kTileScanChunk) {
+    const int len = min(kTileScanChunk, ntiles - base0);
+    for (int i = threadIdx.x; i < kTileScanChunk; i += kTileScanThreads)
+      sbuf[scan_slot(i)] = i < len ? tcount[base0 + i] : 0u;
+    __syncthreads();
+    const int i0 = (int)threadIdx.x * kTileScanItems;
+    uint32_t c[kTileScanItems], s = 0, lists = 0;  // lists: small | big << 16
+#pragma unroll
+    for (int k = 0; k < kTileScanItems; ++k) {
+      c[k] = sbuf[scan_slot(i0 + k)];
+      s += c[k];
+      lists += c[k] > (uint32_t)kWarpSortCap ? 0x10000u : (c[k] > 1u ? 1u : 0u);
+    }
+    uint32_t tot = 0, lt = 0;
+    uint64_t off = carry + block_exclusive_scan(s, &tot);  // (ends with a barrier)
+    const uint32_t lp = block_exclusive_scan(lists, &lt);
+    uint32_t ps = n_small + (lp & 0xFFFFu), pb = n_big + (lp >> 16);
+#pragma unroll
+    for (int k = 0; k < kTileScanItems; ++k) {
+      sbuf[scan_slot(i0 + k)] = (uint32_t)min(off, (uint64_t)cap);
+      if (c[k] > (uint32_t)kWarpSortCap)
+        sort_list[ntiles - 1 - (int)pb++] = (uint32_t)(base0 + i0 + k);
+      else if (c[k] > 1u && i0 + k < len)
+        sort_list[ps++] = (uint32_t)(base0 + i0 + k);
+      off += c[k];
+    }
+    carry += tot;
+    if (threadIdx.x == 0) sbuf[scan_slot(kTileScanChunk)] = (uint32_t)min(carry, (uint64_t)cap);
+    __syncthreads();
+    for (int i = threadIdx.x; i < len; i += kTileScanThreads) {
+      const uint32_t a = sbuf[scan_slot(i)];
+      toff[base0 + i] = a;
+      ranges[base0 + i] = make_uint2(a, i + 1 < len ? sbuf[scan_slot(i + 1)] : sbuf[scan_slot(kTileScanChunk)]);
+    }
+    n_small += lt & 0xFFFFu;
+    n_big += lt >> 16;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    status[kStInstances] = carry;
+    status[kStSortTiles] = n_small;
+    status[kStSortBig] = n_big;
+    status[kStSortNext] = 0;
+    status[kStSortBigNext] = 0;
+  }
+}
+
+// Per voxel: its instances, each at the next free place of its tile's bucket
+// (toff: the buckets' starts on entry, their ends on exit); and with thist,
+// the coarse optical-depth bound of every instance in its tile's depth bins.
+// Lanes of a warp that hit the same tile in the same step take one atomic.
+__global__ void __launch_bounds__(256) bucket_emit_kernel(int64_t n, const uint32_t* __restrict__ cnt,
+                                                          const short4* __restrict__ rect,
+                                                          const uint32_t* __restrict__ q, ViewParams v, int64_t cap,
+                                                          uint32_t* __restrict__ toff, uint32_t* __restrict__ keys,
+                                                          uint32_t* __restrict__ vals,
+                                                          unsigned long long* __restrict__ status,
+                                                          const uint32_t* __restrict__ hbin,
+                                                          const float* __restrict__ htau, float* __restrict__ thist) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  uint32_t c = 0, qq = 0;
+  int tx0 = 0, ty0 = 0, w = 1, hb0 = 1, hb1 = 0;
+  float ht = 0.0f;
+  if (i < n && (c = cnt[i]) != 0) {
+    const short4 r = rect[i];
+    tx0 = r.x >> v.tile_wl;
+    ty0 = r.y >> v.tile_hl;
+    w = (r.z >> v.tile_wl) - tx0 + 1;
+    qq = q[i];
+    if (thist) {
+      const uint32_t hb = hbin[i];
+      hb0 = (int)(hb & 0xFFu);
+      hb1 = (int)(hb >> 8);
+      ht = htau[i];
+    }
+  }
+  uint32_t over = 0;
+  const uint32_t steps = __reduce_max_sync(0xFFFFFFFFu, c);
+  for (uint32_t k = 0; k < steps; ++k) {
+    const uint32_t tile = k < c ? rect_tile(v, tx0, ty0, w, k) : 0xFFFFFFFFu;
+    const unsigned grp = __match_any_sync(0xFFFFFFFFu, tile);
+    const int leader = __ffs(grp) - 1;
+    uint32_t pos = 0;
+    if (tile != 0xFFFFFFFFu && lane == leader) pos = atomicAdd(toff + tile, (uint32_t)__popc(grp));
+    pos = __shfl_sync(0xFFFFFFFFu, pos, leader) + (uint32_t)__popc(grp & ((1u << lane) - 1u));
+    if (tile == 0xFFFFFFFFu) continue;
+    if (pos < (uint64_t)cap) {
+      keys[pos] = (tile << v.depth_bits) | qq;
+      vals[pos] = (uint32_t)i;
+    } else {
+      ++over;
+    }
+    for (int b = hb0; b <= hb1; ++b) atomicAdd(thist + (size_t)tile * kPropBins + b, ht);
+  }
+  if (over) atomicAdd(status + kStOverflowInst, (unsigned long long)over);
+}
+
+// Bitonic sorting network with every comparator ascending (the first step of
+// each merge compares mirrored positions): entries at positions >= n act as
+// +infinity and are never touched, so any n works.  Lanes t0, t0 + 32, ...
+// of one warp share the comparators of s[0, n).
+__device__ void warp_bitonic(unsigned long long* s, uint32_t n, uint32_t t0) {
+  uint32_t P = 1;
+  while (P < n) P <<= 1;
+  for (uint32_t k = 2; k <= P; k <<= 1) {
+    const uint32_t half = k >> 1;
+    for (uint32_t i = t0; i < P / 2; i += 32) {  // merge: mirrored pairs
+      const uint32_t a = (i / half) * k + i % half, b = (i / half) * k + k - 1 - i % half;
+      if (b < n) {
+        const unsigned long long x = s[a], y = s[b];
+        if (y < x) {
+          s[a] = y;
+          s[b] = x;
+        }
+      }
+    }
+    __syncwarp();
+    for (uint32_t j = k >> 2; j > 0; j >>= 1) {  // half-cleaners
+      for (uint32_t i = t0; i < P / 2; i += 32) {
+        const uint32_t a = (i / j) * 2 * j + i % j, b = a + j;
+        if (b < n) {
+          const unsigned long long x = s[a], y = s[b];
+          if (y < x) {
+            s[a] = y;
+            s[b] = x;
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+__device__ __forceinline__ unsigned long long bucket_entry(uint32_t key, uint32_t val, uint32_t qmask) {
+  return ((unsigned long long)(key & qmask) << 32) | val;
+}
+
+// Block-wide sort of one bucket of n >= 2 entries (keys, vals: the bucket)
+// by (depth quantum, voxel id) through the staging array S (shared memory
+// for n <= kTileSortSmem, the entries then held in registers; else the
+// bucket's own stretch of a global scratch).  A counting sort on the depth
+// bin (q - lo) >> shift, with kSortBins bins over the bucket's quanta
+// [lo, hi], stages the entries bin by bin; an entry of a bin of up to
+// kRankMax entries then goes straight to its place, the number of smaller
+// (quantum, voxel id) pairs in its bin; larger bins are sorted by one warp.
+__device__ void block_sort_bucket(uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, uint32_t n,
+                                  uint32_t qmask, uint32_t thi, unsigned long long* S) {
+  __shared__ uint32_t s_start[kSortBins], s_cur[kSortBins];
+  __shared__ uint32_t s_lo[kTileSortWarps], s_hi[kTileSortWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool regs = n <= (uint32_t)kTileSortSmem;
+  uint32_t kq[kSortPer], kv[kSortPer];
+  uint32_t lo = 0xFFFFFFFFu, hi = 0;
+  if (regs) {
+#pragma unroll
+    for (int e = 0; e < kSortPer; ++e) {
+      const uint32_t k = (uint32_t)e * kTileSortThreads + threadIdx.x;
+      kq[e] = 0;
+      kv[e] = 0;
+      if (k < n) {
+        kq[e] = keys[k] & qmask;
+        kv[e] = vals[k];
+        lo = min(lo, kq[e]);
+        hi = max(hi, kq[e]);
+      }
+    }
+  } else {
+    for (uint32_t k = threadIdx.x; k < n; k += kTileSortThreads) {
+      const uint32_t q = keys[k] & qmask;
+      lo = min(lo, q);
+      hi = max(hi, q);
+    }
+  }
+  lo = __reduce_min_sync(0xFFFFFFFFu, lo);
+  hi = __reduce_max_sync(0xFFFFFFFFu, hi);
+  if (lane == 0) {
+    s_lo[warp] = lo;
+    s_hi[warp] = hi;
+  }
+  for (int b = threadIdx.x; b < kSortBins; b += kTileSortThreads) s_cur[b] = 0;
+  __syncthreads();
+  lo = s_lo[0];
+  hi = s_hi[0];
+#pragma unroll
+  for (int w = 1; w < kTileSortWarps; ++w) {
+    lo = min(lo, s_lo[w]);
+    hi = max(hi, s_hi[w]);
+  }
+  uint32_t shift = 0;
+  while (((hi - lo) >> shift) >= (uint32_t)kSortBins) ++shift;
+  // histogram of the bins
+  if (regs) {
+#pragma unroll
+    for (int e = 0; e < kSortPer; ++e)
+      if ((uint32_t)e * kTileSortThreads + threadIdx.x < n) atomicAdd(&s_cur[(kq[e] - lo) >> shift], 1u);
+  } else {
+    for (uint32_t k = threadIdx.x; k < n; k += kTileSortThreads)
+      atomicAdd(&s_cur[((keys[k] & qmask) - lo) >> shift], 1u);
+  }
+  __syncthreads();
+  {  // exclusive scan of the bin counts
+    constexpr int kPer = kSortBins / kTileSortThreads;
+    uint32_t c[kPer], t = 0;
+    const int b0 = threadIdx.x * kPer;
+#pragma unroll
+    for (int e = 0; e < kPer; ++e) {
+      c[e] = s_cur[b0 + e];
+      t += c[e];
+    }
+    uint32_t run = block_exclusive_scan(t, nullptr);
+#pragma unroll
+    for (int e = 0; e < kPer; ++e) {
+      s_start[b0 + e] = run;
+      s_cur[b0 + e] = run;
+      run += c[e];
+    }
+  }
+  __syncthreads();
+  // stage bin by bin (s_cur: each bin's end afterwards)
+  if (regs) {
+#pragma unroll
+    for (int e = 0; e < kSortPer; ++e)
+      if ((uint32_t)e * kTileSortThreads + threadIdx.x < n)
+        S[atomicAdd(&s_cur[(kq[e] - lo) >> shift], 1u)] = ((unsigned long long)kq[e] << 32) | kv[e];
+  } else {
+    for (uint32_t k = threadIdx.x; k < n; k += kTileSortThreads) {
+      const uint32_t key = keys[k];
+      S[atomicAdd(&s_cur[((key & qmask) - lo) >> shift], 1u)] = bucket_entry(key, vals[k], qmask);
+    }
+  }
+  __syncthreads();
+  // entries of small bins: rank within the bin
+  for (uint32_t p = threadIdx.x; p < n; p += kTileSortThreads) {
+    const unsigned long long x = S[p];
+    const uint32_t q = (uint32_t)(x >> 32), b = (q - lo) >> shift;
+    const uint32_t a = s_start[b], m = s_cur[b] - a;
+    if (m > (uint32_t)kRankMax) continue;
+    uint32_t r = 0;
+    for (uint32_t j = 0; j < m; ++j) r += S[a + j] < x ? 1u : 0u;
+    keys[a + r] = thi | q;
+    vals[a + r] = (uint32_t)x;
+  }
+  // large bins: one warp each
+  for (int b0 = warp * 32; b0 < kSortBins; b0 += kTileSortThreads) {
+    unsigned big = __ballot_sync(0xFFFFFFFFu, s_cur[b0 + lane] - s_start[b0 + lane] > (uint32_t)kRankMax);
+    while (big) {
+      const int b = b0 + __ffs(big) - 1;
+      big &= big - 1;
+      const uint32_t a = s_start[b], m = s_cur[b] - a;
+      warp_bitonic(S + a, m, lane);
+      for (uint32_t k = lane; k < m; k += 32) {
+        const unsigned long long x = S[a + k];
+        keys[a + k] = thi | (uint32_t)(x >> 32);
+        vals[a + k] = (uint32_t)x;
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+}
+
+// Sort each listed tile's bucket by (depth quantum, voxel id).  Persistent
+// blocks take the buckets of more than kWarpSortCap entries first, one block
+// each, then the others, one warp each.
+__global__ void __launch_bounds__(kTileSortThreads) tile_sort_kernel(const uint2* __restrict__ ranges,
+                                                                     const uint32_t* __restrict__ sort_list,
+                                                                     int ntiles, int depth_bits,
+                                                                     uint32_t* __restrict__ keys,
+                                                                     uint32_t* __restrict__ vals,
+                                                                     unsigned long long* __restrict__ scratch,
+                                                                     unsigned long long* __restrict__ status) {
+  extern __shared__ unsigned long long sk[];
+  __shared__ unsigned long long s_item;
+  const uint32_t qmask = (1u << depth_bits) - 1u;
+  const unsigned long long n_big = status[kStSortBig], n_small = status[kStSortTiles];
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(status + kStSortBigNext, 1ull);
+    __syncthreads();
+    const unsigned long long it = s_item;
+    __syncthreads();
+    if (it >= n_big) break;
+    const uint32_t tile = sort_list[ntiles - 1 - (int)it];
+    const uint2 rg = ranges[tile];
+    const uint32_t n = rg.y - rg.x;
+    if (n > 1)
+      block_sort_bucket(keys + rg.x, vals + rg.x, n, qmask, tile << depth_bits,
+                        n <= (uint32_t)kTileSortSmem ? sk : scratch + rg.x);
+  }
+  const uint32_t lane = threadIdx.x & 31u;
+  unsigned long long* ws = sk + (threadIdx.x >> 5) * kWarpSortCap;
+  for (;;) {
+    unsigned long long it = 0;
+    if (lane == 0) it = atomicAdd(status + kStSortNext, 1ull);
+    it = __shfl_sync(0xFFFFFFFFu, it, 0);
+    if (it >= n_small) break;
+    const uint32_t tile = sort_list[it];
+    const uint2 rg = ranges[tile];
+    const uint32_t n = rg.y - rg.x;
+    uint32_t* kp = keys + rg.x;
+    uint32_t* vp = vals + rg.x;
+    for (uint32_t k = lane; k < n; k += 32) ws[k] = bucket_entry(kp[k], vp[k], qmask);
+    __syncwarp();
+    warp_bitonic(ws, n, lane);
+    for (uint32_t k = lane; k < n; k += 32) {
+      kp[k] = (tile << depth_bits) | (uint32_t)(ws[k] >> 32);
+      vp[k] = (uint32_t)ws[k];
+    }
+    __syncwarp();
   }
 }
 
@@ -282,14 +597,24 @@ size_t sort_hist_words(int64_t inst_cap) {
   return (size_t)(nb * kRadix);
 }
 
-void launch_scan_emit(art_ctx* ctx, const ViewParams& v, const uint32_t* hbin, const float* htau, float* thist) {
-  int64_t n = ctx->n;
-  int nb = (int)((n + kScanBlock - 1) / kScanBlock);
-  ART_LAUNCH(ctx, "bin_blocksum", block_sum_kernel, nb, kScanThreads, 0, ctx->d_cnt, n,
-             (const unsigned long long*)nullptr, ctx->d_bsum);
-  ART_LAUNCH(ctx, "bin_scan", scan_bsum_kernel, 1, 1024, 0, ctx->d_bsum, nb, ctx->d_status + kStInstances);
-  ART_LAUNCH(ctx, "bin_emit", emit_kernel, nb, kScanThreads, 0, n, ctx->d_cnt, ctx->d_bsum, ctx->d_rect, ctx->d_q, v,
-             ctx->inst_cap, ctx->d_keys[0], ctx->d_vals[0], ctx->d_status, hbin, htau, thist);
+void launch_bin(art_ctx* ctx, const ViewParams& v, const uint32_t* hbin, const float* htau, float* thist) {
+  const int64_t n = ctx->n;
+  const int ntiles = v.tiles_x * v.tiles_y;
+  const unsigned vb = (unsigned)((n + 255) / 256);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(tile_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileScanSmem);
+    cudaFuncSetAttribute(tile_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileSortSmem * 8);
+    attr = true;
+  }
+  cudaMemsetAsync(ctx->d_tcount, 0, sizeof(uint32_t) * (size_t)ntiles, ctx->stream);
+  ART_LAUNCH(ctx, "bin_count", tile_count_kernel, vb, 256, 0, n, ctx->d_cnt, ctx->d_rect, v, ctx->d_tcount);
+  ART_LAUNCH(ctx, "bin_scan", tile_scan_kernel, 1, kTileScanThreads, kTileScanSmem, ntiles, ctx->d_tcount, ctx->inst_cap,
+             ctx->d_toff, ctx->d_ranges, ctx->d_sortlist, ctx->d_status);
+  ART_LAUNCH(ctx, "bin_emit", bucket_emit_kernel, vb, 256, 0, n, ctx->d_cnt, ctx->d_rect, ctx->d_q, v, ctx->inst_cap,
+             ctx->d_toff, ctx->d_keys, ctx->d_vals, ctx->d_status, hbin, htau, thist);
+  ART_LAUNCH(ctx, "tile_sort", tile_sort_kernel, 2 * ctx->num_sms, kTileSortThreads, kTileSortSmem * 8, ctx->d_ranges,
+             ctx->d_sortlist, ntiles, v.depth_bits, ctx->d_keys, ctx->d_vals, ctx->d_sort_tmp, ctx->d_status);
 }
 
 int launch_sort_bufs(art_ctx* ctx, uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, int64_t cap,
@@ -314,25 +639,12 @@ int launch_sort_bufs(art_ctx* ctx, uint32_t* k0, uint32_t* v0, uint32_t* k1, uin
   return src;
 }
 
-void launch_sort(art_ctx* ctx, int key_bits) {
-  launch_sort_bufs(ctx, ctx->d_keys[0], ctx->d_vals[0], ctx->d_keys[1], ctx->d_vals[1], ctx->inst_cap,
-                   ctx->d_status + kStInstances, key_bits, ctx->d_hist, ctx->d_bsum);
-}
-
 namespace {
 __global__ void set_word_kernel(unsigned long long* p, unsigned long long value) { *p = value; }
 }  // namespace
 
 void launch_set_word(art_ctx* ctx, unsigned long long* p, unsigned long long value) {
   ART_LAUNCH(ctx, "set_word", set_word_kernel, 1, 1, 0, p, value);
-}
-
-void launch_ranges(art_ctx* ctx, const ViewParams& v) {
-  int64_t ntiles = (int64_t)v.tiles_x * v.tiles_y;
-  cudaMemsetAsync(ctx->d_ranges, 0, sizeof(uint2) * (size_t)ntiles, ctx->stream);
-  int grid = ctx->num_sms * 4;
-  ART_LAUNCH(ctx, "tile_ranges", ranges_kernel, grid, 256, 0, ctx->d_keys[0], ctx->inst_cap,
-             ctx->d_status + kStInstances, v.depth_bits, ctx->d_ranges);
 }
 
 // ------------------------------------------------ sort without allocation

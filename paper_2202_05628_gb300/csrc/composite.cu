@@ -542,8 +542,8 @@ void split_pass(art_ctx* ctx, const ViewParams& v, void* F, float* A, int mode, 
   const int grid = ctx->composite_blocks;
   if (mode == kInterval) {
     auto kfn = composite_split_kernel<C, TF, TO, kInterval>;
-    ART_LAUNCH(ctx, "composite_skip", kfn, grid, 32, 0, ctx->d_ranges, ctx->d_seg, ctx->d_items, ctx->d_keys[0],
-               ctx->d_vals[0], ctx->d_rec, ctx->d_rect, feat, v, ctx->cfg.tau, (TO*)F, A, ctx->d_status, ctx->d_part,
+    ART_LAUNCH(ctx, "composite_skip", kfn, grid, 32, 0, ctx->d_ranges, ctx->d_seg, ctx->d_items, ctx->d_keys,
+               ctx->d_vals, ctx->d_rec, ctx->d_rect, feat, v, ctx->cfg.tau, (TO*)F, A, ctx->d_status, ctx->d_part,
                sk);
     auto mfn = composite_merge_kernel<C, TO, kInterval>;
     ART_LAUNCH(ctx, "composite_merge", mfn, 4 * ctx->num_sms, 32, 0, ctx->d_seg, ctx->d_multi, v, ctx->cfg.tau, (TO*)F,
@@ -551,7 +551,7 @@ void split_pass(art_ctx* ctx, const ViewParams& v, void* F, float* A, int mode, 
   } else {
     auto kfn = composite_split_kernel<C, TF, TO, kPlain>;
     ART_LAUNCH(ctx, list ? "composite_refill" : "composite", kfn, grid, 32, 0, ctx->d_ranges, ctx->d_seg, ctx->d_items,
-               ctx->d_keys[0], ctx->d_vals[0], ctx->d_rec, ctx->d_rect, feat, v, ctx->cfg.tau, (TO*)F, A,
+               ctx->d_keys, ctx->d_vals, ctx->d_rec, ctx->d_rect, feat, v, ctx->cfg.tau, (TO*)F, A,
                ctx->d_status, ctx->d_part, sk);
     auto mfn = composite_merge_kernel<C, TO, kPlain>;
     ART_LAUNCH(ctx, "composite_merge", mfn, 4 * ctx->num_sms, 32, 0, ctx->d_seg, ctx->d_multi, v, ctx->cfg.tau, (TO*)F,
@@ -583,7 +583,7 @@ void split_walk(art_ctx* ctx, const ViewParams& v, void* F, float* A, int mode, 
   }
   auto qfn = composite_queue_kernel<C, TF, TO>;
   const int qgrid = std::min(ntiles, 16 * ctx->num_sms);
-  ART_LAUNCH(ctx, "composite_fallback", qfn, qgrid, 32, 0, ctx->d_ranges, ctx->d_keys[0], ctx->d_vals[0], ctx->d_rec,
+  ART_LAUNCH(ctx, "composite_fallback", qfn, qgrid, 32, 0, ctx->d_ranges, ctx->d_keys, ctx->d_vals, ctx->d_rec,
              ctx->d_rect, feat, v, ctx->cfg.tau, (TO*)F, A, ctx->d_status, seq, seq_word);
 }
 
@@ -593,11 +593,11 @@ void launch_c(art_ctx* ctx, const ViewParams& v, void* F, float* A, const HitLog
   const TF* feat = (const TF*)ctx->d_feat;
   if (mode == kDebug) {
     auto kfn = composite_kernel<C, TF, TO, kDebug>;
-    ART_LAUNCH(ctx, "composite_debug", kfn, ntiles, 32, 0, ctx->d_ranges, ctx->d_keys[0], ctx->d_vals[0], ctx->d_rec,
+    ART_LAUNCH(ctx, "composite_debug", kfn, ntiles, 32, 0, ctx->d_ranges, ctx->d_keys, ctx->d_vals, ctx->d_rec,
                ctx->d_rect, feat, v, ctx->cfg.tau, (TO*)F, A, ctx->d_status, *dbg, sk);
   } else if (mode == kLabel) {
     auto kfn = composite_kernel<C, TF, TO, kLabel>;
-    ART_LAUNCH(ctx, "composite_labels", kfn, ntiles, 32, 0, ctx->d_ranges, ctx->d_keys[0], ctx->d_vals[0], ctx->d_rec,
+    ART_LAUNCH(ctx, "composite_labels", kfn, ntiles, 32, 0, ctx->d_ranges, ctx->d_keys, ctx->d_vals, ctx->d_rec,
                ctx->d_rect, feat, v, ctx->cfg.tau, (TO*)F, A, ctx->d_status, HitLog{}, sk);
   } else {
     split_walk<C, TF, TO>(ctx, v, F, A, mode, sk);

@@ -34,7 +34,11 @@ enum StatusWord {
   kStNextMerge = 11,    // next split tile to merge (work counter)
   kStRmax = 12,         // largest voxel bounding radius of the last pose (float bits)
   kStFallback2 = 13,    // learned skip: tiles of the full pass whose stop needs the sequential walk
-  kStWords = 16
+  kStSortTiles = 14,    // binning: tiles whose bucket needs sorting
+  kStSortNext = 15,     // binning: next bucket to sort (work counter)
+  kStSortBig = 16,      // binning: buckets sorted by a whole block
+  kStSortBigNext = 17,  // binning: next such bucket (work counter)
+  kStWords = 18
 };
 
 // Per-view camera, with host-precomputed ray frame.
@@ -117,13 +121,14 @@ struct art_ctx {
   short4* d_rect = nullptr;     // [n] pixel rect (x0, y0, x1, y1), empty if x0 > x1
   uint32_t* d_q = nullptr;      // [n] depth quantum
   uint32_t* d_cnt = nullptr;    // [n] tile count
-  uint32_t* d_off = nullptr;    // [n] exclusive offsets
-  uint32_t* d_bsum = nullptr;   // block sums for scans
-  uint32_t* d_keys[2] = {nullptr, nullptr};
-  uint32_t* d_vals[2] = {nullptr, nullptr};
-  uint32_t* d_hist = nullptr;   // radix histograms
+  uint32_t* d_keys = nullptr;   // instances in (tile, depth, voxel) order: tile << depth_bits | depth quantum
+  uint32_t* d_vals = nullptr;   // ... and their voxel ids
+  unsigned long long* d_sort_tmp = nullptr;  // staging of the buckets too long for shared memory
   uint2* d_ranges = nullptr;    // per tile [start, end)
   int64_t ranges_cap = 0;
+  uint32_t* d_tcount = nullptr;  // per tile instance count
+  uint32_t* d_toff = nullptr;    // per tile bucket cursor
+  uint32_t* d_sortlist = nullptr;  // tiles whose bucket needs sorting
   unsigned long long* d_status = nullptr;
   unsigned long long* h_status = nullptr;  // pinned
 
@@ -213,16 +218,20 @@ void launch_project(art_ctx* ctx, const ViewParams& v, uint32_t* hbin = nullptr,
 // ---- binning and sorting (binsort.cu)
 // With thist set (zeroed [tiles][64]), also accumulate the coarse optical-depth
 // bound of every instance into its tile's depth bins.
-void launch_scan_emit(art_ctx* ctx, const ViewParams& v, const uint32_t* hbin = nullptr, const float* htau = nullptr,
-                      float* thist = nullptr);
-void launch_sort(art_ctx* ctx, int key_bits);
+// Binning of the projected voxels: per-tile instance counts, their scan (the
+// tile ranges), the scatter of every instance into its tile's bucket and the
+// sort of each bucket by (depth quantum, voxel id).  With thist set, the
+// scatter also adds each voxel's optical-depth bound htau to the depth bins
+// hbin of each of its tiles (thist: zeroed [tiles][64]; the coarse check of
+// the learned skip).
+void launch_bin(art_ctx* ctx, const ViewParams& v, const uint32_t* hbin = nullptr, const float* htau = nullptr,
+                float* thist = nullptr);
 // Radix sort of count (device word) pairs ping-ponging between (k0, v0) and
 // (k1, v1); returns the index (0 or 1) of the buffer holding the result.
 int launch_sort_bufs(art_ctx* ctx, uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, int64_t cap,
                      const unsigned long long* count, int key_bits, uint32_t* hist, uint32_t* bsum);
 void launch_set_word(art_ctx* ctx, unsigned long long* p, unsigned long long value);
-void launch_ranges(art_ctx* ctx, const ViewParams& v);
-size_t sort_hist_words(int64_t inst_cap);
+size_t sort_hist_words(int64_t n);
 size_t scan_block_words(int64_t n);
 
 // ---- composite (composite.cu)

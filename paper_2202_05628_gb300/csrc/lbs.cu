@@ -29,43 +29,80 @@ __device__ void rodrigues(const float* r, float* R) {
     }
 }
 
-// One thread walks the joint tree (parents precede children).
+// One thread per joint forms its local transform L_j = [R(r_j) | rest_j -
+// rest_parent] (the root's premultiplied by the global [R | T]); one thread
+// then walks the tree (parents precede children), M_j = M_parent L_j, and
+// every joint writes G_j = M_j [I | -rest_j].
 // skel: J parent indices stored as floats, then rest[J][3]; pose: r[J][3], R[3], T[3].
-__global__ void fk_kernel(int J, const float* __restrict__ skel, const float* __restrict__ pose,
-                          float* __restrict__ G) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  __shared__ float M[kMaxJoints * 12];
-  const float* rest = skel + J;
-  float Rg[9];
-  rodrigues(pose + 3 * J, Rg);
-  const float* Tg = pose + 3 * J + 3;
-  for (int j = 0; j < J; ++j) {
-    int p = (int)skel[j];
+__global__ void __launch_bounds__(kMaxJoints) fk_kernel(int J, const float* __restrict__ skel,
+                                                        const float* __restrict__ pose, float* __restrict__ G) {
+  __shared__ float sL[kMaxJoints][12];
+  __shared__ float sM[kMaxJoints][12];
+  __shared__ int sp[kMaxJoints];
+  __shared__ float srest[kMaxJoints][3];
+  const int j = threadIdx.x;
+  const bool on = j < J;
+  int p = -1;
+  float r[3] = {0.f, 0.f, 0.f}, rg[3], Tg[3];
+  if (on) {
+    p = (int)skel[j];
+    sp[j] = p;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      srest[j][a] = skel[J + 3 * j + a];
+      r[a] = pose[3 * j + a];
+      rg[a] = pose[3 * J + a];
+      Tg[a] = pose[3 * J + 3 + a];
+    }
+  }
+  __syncthreads();
+  if (on) {
     float Rl[9];
-    rodrigues(pose + 3 * j, Rl);
-    float tl[3];
-    for (int a = 0; a < 3; ++a) tl[a] = rest[3 * j + a] - (p >= 0 ? rest[3 * p + a] : 0.0f);
-    // parent transform P (3x4)
-    float P[12];
-    if (p >= 0) {
-      for (int m = 0; m < 12; ++m) P[m] = M[12 * p + m];
-    } else {
+    rodrigues(r, Rl);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+#pragma unroll
+      for (int b = 0; b < 3; ++b) sL[j][a * 4 + b] = Rl[a * 3 + b];
+      sL[j][a * 4 + 3] = srest[j][a] - (p >= 0 ? srest[p][a] : 0.0f);
+    }
+    if (p < 0) {  // the global transform stands in as the root's parent
+      float Rg[9];
+      rodrigues(rg, Rg);
+#pragma unroll
       for (int a = 0; a < 3; ++a) {
-        for (int b = 0; b < 3; ++b) P[a * 4 + b] = Rg[a * 3 + b];
-        P[a * 4 + 3] = Tg[a];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) sM[j][a * 4 + b] = Rg[a * 3 + b];
+        sM[j][a * 4 + 3] = Tg[a];
       }
     }
-    float* Mj = M + 12 * j;
-    for (int a = 0; a < 3; ++a) {
-      for (int b = 0; b < 3; ++b)
-        Mj[a * 4 + b] = P[a * 4 + 0] * Rl[0 * 3 + b] + P[a * 4 + 1] * Rl[1 * 3 + b] + P[a * 4 + 2] * Rl[2 * 3 + b];
-      Mj[a * 4 + 3] = P[a * 4 + 0] * tl[0] + P[a * 4 + 1] * tl[1] + P[a * 4 + 2] * tl[2] + P[a * 4 + 3];
+  }
+  __syncthreads();
+  if (j == 0) {
+    for (int k = 0; k < J; ++k) {
+      const int q = sp[k];
+      float P[12];
+#pragma unroll
+      for (int m = 0; m < 12; ++m) P[m] = sM[q >= 0 ? q : k][m];
+      const float* L = sL[k];
+      float* Mk = sM[k];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+          Mk[a * 4 + b] = P[a * 4 + 0] * L[0 * 4 + b] + P[a * 4 + 1] * L[1 * 4 + b] + P[a * 4 + 2] * L[2 * 4 + b];
+        Mk[a * 4 + 3] = P[a * 4 + 0] * L[3] + P[a * 4 + 1] * L[7] + P[a * 4 + 2] * L[11] + P[a * 4 + 3];
+      }
     }
-    // G_j = M_j [I | -rest_j]
+  }
+  __syncthreads();
+  if (on) {
+    const float* M = sM[j];
+#pragma unroll
     for (int a = 0; a < 3; ++a) {
-      for (int b = 0; b < 3; ++b) G[12 * j + a * 4 + b] = Mj[a * 4 + b];
+#pragma unroll
+      for (int b = 0; b < 3; ++b) G[12 * j + a * 4 + b] = M[a * 4 + b];
       G[12 * j + a * 4 + 3] =
-          Mj[a * 4 + 3] - (Mj[a * 4 + 0] * rest[3 * j] + Mj[a * 4 + 1] * rest[3 * j + 1] + Mj[a * 4 + 2] * rest[3 * j + 2]);
+          M[a * 4 + 3] - (M[a * 4 + 0] * srest[j][0] + M[a * 4 + 1] * srest[j][1] + M[a * 4 + 2] * srest[j][2]);
     }
   }
 }
@@ -236,7 +273,7 @@ __global__ void __launch_bounds__(256) project_kernel(int64_t n, const float4* _
 
 }  // namespace
 
-void launch_fk(art_ctx* ctx) { ART_LAUNCH(ctx, "fk", fk_kernel, 1, 32, 0, ctx->J, ctx->d_skel, ctx->d_pose, ctx->d_G); }
+void launch_fk(art_ctx* ctx) { ART_LAUNCH(ctx, "fk", fk_kernel, 1, kMaxJoints, 0, ctx->J, ctx->d_skel, ctx->d_pose, ctx->d_G); }
 
 void launch_lbs(art_ctx* ctx) {
   int64_t n = ctx->n;
