@@ -279,12 +279,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 // Row-blocked variant for the narrow layers (N = 32 or 64 output channels,
 // BF16): the weights of all nine taps stay in shared memory for the whole
 // persistent loop, and a work unit is R = 4 output rows of one 128-pixel
-// segment.  The producer brings each of the R + 2 input rows in three
-// horizontal shifts (x - 1, x, x + 1) and channel chunks; every such box
-// serves the up to three output rows it neighbours vertically (one MMA per
-// row into that row's accumulator).  Per output row that is 3 (R + 2) / R
-// boxes instead of 9, and no weight traffic.  Accumulators: R x N TMEM
-// columns per unit, two units in flight.
+// segment.  The producer brings each of the R + 2 input rows, per channel
+// chunk, as one box of 130 pixels (x - 1 .. x + 128); the three horizontal
+// taps read it from row 0, 1 or 2 of the box, and every box serves the up to
+// three output rows it neighbours vertically (one MMA per row into that
+// row's accumulator).  Per output row that is (R + 2) / R boxes instead of
+// 9, and no weight traffic.  Accumulators: R x N TMEM columns per unit, two
+// units in flight.
 constexpr int kRows = 4;
 
 // With 32 output channels the three vertical taps are stacked into one
@@ -301,6 +302,9 @@ struct RowCfg {
   static constexpr int kSlots = kStack ? kRows + 4 : kRows;
   static constexpr int kBufCols = kSlots * N;  // columns of one accumulator buffer (256 or 512 ... x2)
   static constexpr uint32_t kIdesc = idesc_bf16(128, kStack ? 3 * N : N);
+  static constexpr int kHalo = 130;                                   // input pixels of a row box (128 + 2)
+  static constexpr int kBoxBytes = kHalo * KCB;
+  static constexpr int kStageBytes = (kBoxBytes + 1023) / 1024 * 1024;  // stages stay on swizzle-atom boundaries
 };
 
 struct RowParams {
@@ -323,7 +327,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint8_t* wsm = sm;
   uint8_t* stages = sm + rp.w_bytes;
   const int S = rp.n_stages;
-  uint64_t* full = reinterpret_cast<uint64_t*>(stages + (size_t)S * 3 * Cfg::kA);
+  uint64_t* full = reinterpret_cast<uint64_t*>(stages + (size_t)S * Cfg::kStageBytes);
   uint64_t* empty = full + S;
   uint64_t* accf = empty + S;
   uint64_t* acce = accf + 2;
@@ -336,7 +340,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int cpt = rp.cpt;
   const int n_stage_unit = (kRows + 2) * cpt;  // stages per unit
-  const int kStage = 3 * Cfg::kA;              // three horizontal shifts
+  const int kStage = Cfg::kStageBytes;         // one box of 130 pixels: the three shifts are row offsets
+  // the swizzle follows the absolute shared-memory address, so a descriptor
+  // may start at any row of the box: shift dx is the box from row dx on
   // resident weight block of (dy + 1, dx + 1, chunk); stacked form: the three
   // vertical taps of one (dx, chunk) are adjacent (one N = 96 operand)
   auto wblk = [&](int dyi, int dxi, int c) { return Cfg::kStack ? (dxi * cpt + c) * 3 + dyi : (dyi * 3 + dxi) * cpt + c; };
@@ -383,10 +389,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) break;
           const int j = st / cpt, c = st - j * cpt;
           uint8_t* dst = stages + (size_t)s * kStage;
-          mbar_expect_tx(&full[s], (uint32_t)kStage);
-#pragma unroll
-          for (int dx = 0; dx < 3; ++dx)
-            tma_load_3d(dst + dx * Cfg::kA, &tmA, &full[s], c * Cfg::KC, x0 + dx - 1, y0 - 1 + j);
+          mbar_expect_tx(&full[s], (uint32_t)Cfg::kBoxBytes);
+          tma_load_3d(dst, &tmA, &full[s], c * Cfg::KC, x0 - 1, y0 - 1 + j);
           if (++s == S) {
             s = 0;
             ph ^= 1u;
@@ -422,7 +426,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               const uint32_t bw = wbase + (uint32_t)(wblk(0, dxi, c) * N * KCB);
 #pragma unroll
               for (int kk = 0; kk < KCB / 32; ++kk)
-                umma<false>(dj, umma_desc<KCB>(a0 + dxi * Cfg::kA + kk * 32), umma_desc<KCB>(bw + kk * 32),
+                umma<false>(dj, umma_desc<KCB>(a0 + dxi * KCB + kk * 32), umma_desc<KCB>(bw + kk * 32),
                             Cfg::kIdesc, 1u);
             }
           } else {
@@ -436,7 +440,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                   if (dyi < 0 || dyi > 2) continue;
                   const uint32_t bw = wbase + (uint32_t)(wblk(dyi, dxi, c) * N * KCB);
                   const bool first = dyi == 0 && dxi == 0 && c == 0 && kk == 0;
-                  umma<false>(d0 + (uint32_t)(r * N), umma_desc<KCB>(a0 + dxi * Cfg::kA + kk * 32),
+                  umma<false>(d0 + (uint32_t)(r * N), umma_desc<KCB>(a0 + dxi * KCB + kk * 32),
                               umma_desc<KCB>(bw + kk * 32), Cfg::kIdesc, first ? 0u : 1u);
                 }
           }
@@ -635,7 +639,7 @@ art_status launch_rows(art_ctx* ctx, const TcConv& c) {
   {
     cuuint64_t dims[3] = {(cuuint64_t)c.cin, (cuuint64_t)c.W, (cuuint64_t)c.H};
     cuuint64_t strides[2] = {(cuuint64_t)c.cin * 2, (cuuint64_t)c.W * c.cin * 2};
-    cuuint32_t box[3] = {(cuuint32_t)Cfg::KC, 128, 1};
+    cuuint32_t box[3] = {(cuuint32_t)Cfg::KC, (cuuint32_t)Cfg::kHalo, 1};
     cuuint32_t es[3] = {1, 1, 1};
     CUresult r = g_encode(&tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)c.in, dims, strides, box, es,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -678,12 +682,12 @@ art_status launch_rows(art_ctx* ctx, const TcConv& c) {
   // two CTAs per SM (two issuing threads, one accumulator buffer each) when
   // the resident weights and three stages fit in half the shared memory
   const int half = 232448 / 2 - 1024 - rp.w_bytes - tail;
-  const int ctas = half >= 3 * 3 * Cfg::kA ? 2 : 1;
+  const int ctas = half >= 3 * Cfg::kStageBytes ? 2 : 1;
   const int avail = 232448 / ctas - 1024 - rp.w_bytes - tail;
   rp.nbuf = ctas == 2 ? 1 : 2;
-  rp.n_stages = std::min(24, avail / (3 * Cfg::kA));
+  rp.n_stages = std::min(24, avail / Cfg::kStageBytes);
   if (rp.n_stages < 2) return fail(ctx, ART_ERR_UNSUPPORTED, "row-blocked conv: weights too large");
-  const int smem = 1024 + rp.w_bytes + rp.n_stages * 3 * Cfg::kA + tail;
+  const int smem = 1024 + rp.w_bytes + rp.n_stages * Cfg::kStageBytes + tail;
   auto kfn = conv_rows_kernel<N, KCB>;
   cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "conv_rows shared memory attribute");
