@@ -278,8 +278,16 @@ __global__ void __launch_bounds__(kTileScanThreads) tile_scan_kernel(int ntiles,
   uint32_t n_small = 0, n_big = 0;
   for (int base0 = 0; base0 < ntiles; base0 += kTileScanChunk) {
     const int len = min(kTileScanChunk, ntiles - base0);
-    for (int i = threadIdx.x; i < kTileScanChunk; i += kTileScanThreads)
-      sbuf[scan_slot(i)] = i < len ? tcount[base0 + i] : 0u;
+    {
+      uint32_t x[kTileScanItems];  // all loads in flight before the first store
+#pragma unroll
+      for (int k = 0; k < kTileScanItems; ++k) {
+        const int i = k * kTileScanThreads + (int)threadIdx.x;
+        x[k] = i < len ? tcount[base0 + i] : 0u;
+      }
+#pragma unroll
+      for (int k = 0; k < kTileScanItems; ++k) sbuf[scan_slot(k * kTileScanThreads + (int)threadIdx.x)] = x[k];
+    }
     __syncthreads();
     const int i0 = (int)threadIdx.x * kTileScanItems;
     uint32_t c[kTileScanItems], s = 0, lists = 0;  // lists: small | big << 16

@@ -288,20 +288,21 @@ __global__ void __launch_bounds__(kThreads, 1)
 // units in flight.
 constexpr int kRows = 4;
 
-// With 32 output channels the three vertical taps are stacked into one
-// N = 96 operand: the accumulators of consecutive output rows sit in
-// consecutive TMEM column slots in reverse row order (slot of row y =
-// y0 + R + 1 - y; two slots of spare on each side), so that one MMA per
-// input-row box accumulates into the three rows it touches.  Every MMA then
-// accumulates; the epilogue zeroes each real slot after reading it.
+// With 32 output channels the vertical taps are stacked into one operand:
+// the accumulators of the unit's R output rows sit in consecutive TMEM
+// column slots in reverse row order (slot of output row r = R - 1 - r), so
+// that one MMA per input-row box, N = 32 x (the taps whose output row lies
+// in the unit: 3 inside, 2 or 1 at the unit's edge rows), accumulates into
+// every row it touches.  Every MMA accumulates; the epilogue zeroes each
+// slot after reading it.
 template <int N, int KCB>
 struct RowCfg {
   static constexpr int KC = KCB / 2;  // channels per chunk
   static constexpr int kA = 128 * KCB;
   static constexpr bool kStack = N == 32;
-  static constexpr int kSlots = kStack ? kRows + 4 : kRows;
-  static constexpr int kBufCols = kSlots * N;  // columns of one accumulator buffer (256 or 512 ... x2)
-  static constexpr uint32_t kIdesc = idesc_bf16(128, kStack ? 3 * N : N);
+  static constexpr int kSlots = kRows;
+  static constexpr int kBufCols = kSlots * N;  // columns of one accumulator buffer
+  static constexpr uint32_t kIdesc = idesc_bf16(128, N);
   static constexpr int kHalo = 130;                                   // input pixels of a row box (128 + 2)
   static constexpr int kBoxBytes = kHalo * KCB;
   static constexpr int kStageBytes = (kBoxBytes + 1023) / 1024 * 1024;  // stages stay on swizzle-atom boundaries
@@ -419,15 +420,17 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int j = st / cpt, c = st - j * cpt;
           const uint32_t a0 = smem_u32(stages + (size_t)s * kStage);
           if constexpr (Cfg::kStack) {
-            // input row j feeds output rows j, j - 1, j - 2 of the unit (slots R + 1 - j .. R + 3 - j)
-            const uint32_t dj = d0 + (uint32_t)((kRows + 1 - j) * N);
+            // input row j feeds output rows j - dyi of the unit for the taps dyi in [lo, hi]
+            // (slots R - 1 - j + lo ..., consecutive like the stacked taps' weight blocks)
+            const int lo = max(0, j - kRows + 1), hi = min(2, j);
+            const uint32_t dj = d0 + (uint32_t)((kRows - 1 - j + lo) * N);
+            const uint32_t idesc = idesc_bf16(128, (hi - lo + 1) * N);
 #pragma unroll
             for (int dxi = 0; dxi < 3; ++dxi) {
-              const uint32_t bw = wbase + (uint32_t)(wblk(0, dxi, c) * N * KCB);
+              const uint32_t bw = wbase + (uint32_t)((wblk(0, dxi, c) + lo) * N * KCB);
 #pragma unroll
               for (int kk = 0; kk < KCB / 32; ++kk)
-                umma<false>(dj, umma_desc<KCB>(a0 + dxi * KCB + kk * 32), umma_desc<KCB>(bw + kk * 32),
-                            Cfg::kIdesc, 1u);
+                umma<false>(dj, umma_desc<KCB>(a0 + dxi * KCB + kk * 32), umma_desc<KCB>(bw + kk * 32), idesc, 1u);
             }
           } else {
 #pragma unroll
@@ -477,7 +480,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc_fence_after();
       const int y0 = (u / p.tiles_per_row) * kRows, x = (u % p.tiles_per_row) * 128 + m;
       for (int r = 0; r < kRows; ++r) {
-        const int slot = Cfg::kStack ? kRows + 1 - r : r;
+        const int slot = Cfg::kStack ? kRows - 1 - r : r;
         const uint32_t ta = tq + (uint32_t)(buf * Cfg::kBufCols + slot * N);
         if (y0 + r < p.H) epi_row<N, false>(p, ta, y0 + r, x, s_bias, s_head, nullptr, 1.0f, 1.0f, amax);
         if constexpr (Cfg::kStack) {
@@ -684,7 +687,7 @@ art_status launch_rows(art_ctx* ctx, const TcConv& c) {
   const int half = 232448 / 2 - 1024 - rp.w_bytes - tail;
   const int ctas = half >= 3 * Cfg::kStageBytes ? 2 : 1;
   const int avail = 232448 / ctas - 1024 - rp.w_bytes - tail;
-  rp.nbuf = ctas == 2 ? 1 : 2;
+  rp.nbuf = (ctas == 2 && Cfg::kBufCols > 128) ? 1 : 2;  // 512 TMEM columns per SM
   rp.n_stages = std::min(24, avail / Cfg::kStageBytes);
   if (rp.n_stages < 2) return fail(ctx, ART_ERR_UNSUPPORTED, "row-blocked conv: weights too large");
   const int smem = 1024 + rp.w_bytes + rp.n_stages * Cfg::kStageBytes + tail;
