@@ -255,7 +255,7 @@ art_status run_unet_tc(art_ctx* ctx, const ViewParams& v, const __nv_bfloat16* F
   auto P = [&](int i) { return (__nv_bfloat16*)((char*)ctx->d_act + bufs[i].off); };
   const auto& L = ctx->layers;
   auto conv = [&](const __nv_bfloat16* in, int cin, int h, int w, int li, __nv_bfloat16* out, int ld, int off,
-                  int up2, float* head_out) {
+                  int up2, float* head_out, __nv_bfloat16* pooled = nullptr) {
     TcConv c;
     c.in = in;
     c.cin = cin;
@@ -272,20 +272,18 @@ art_status run_unet_tc(art_ctx* ctx, const ViewParams& v, const __nv_bfloat16* F
     c.rgba = head_out;
     c.head_w = head_out ? L[14].w32 : nullptr;
     c.head_b = head_out ? L[14].b32 : nullptr;
+    c.pool = pooled;
     return launch_tc_conv(ctx, c);
   };
   art_status st = ART_OK;
 #define ART_TRY(x)                  \
   if ((st = (x)) != ART_OK) return st
   ART_TRY(conv(F, nd.cin, H, W, 0, P(e0a), c0, 0, 0, nullptr));
-  ART_TRY(conv(P(e0a), c0, H, W, 1, P(cat0), c1 + c0, c1, 0, nullptr));
-  launch_pool_bf16(ctx, P(cat0), c1 + c0, c1, P(p0), H, W, c0);
+  ART_TRY(conv(P(e0a), c0, H, W, 1, P(cat0), c1 + c0, c1, 0, nullptr, P(p0)));  // + 2x2 max pooling
   ART_TRY(conv(P(p0), c0, H / 2, W / 2, 2, P(e1a), c1, 0, 0, nullptr));
-  ART_TRY(conv(P(e1a), c1, H / 2, W / 2, 3, P(cat1), c2 + c1, c2, 0, nullptr));
-  launch_pool_bf16(ctx, P(cat1), c2 + c1, c2, P(p1), H / 2, W / 2, c1);
+  ART_TRY(conv(P(e1a), c1, H / 2, W / 2, 3, P(cat1), c2 + c1, c2, 0, nullptr, P(p1)));
   ART_TRY(conv(P(p1), c1, H / 4, W / 4, 4, P(e2a), c2, 0, 0, nullptr));
-  ART_TRY(conv(P(e2a), c2, H / 4, W / 4, 5, P(cat2), c3 + c2, c3, 0, nullptr));
-  launch_pool_bf16(ctx, P(cat2), c3 + c2, c3, P(p2), H / 4, W / 4, c2);
+  ART_TRY(conv(P(e2a), c2, H / 4, W / 4, 5, P(cat2), c3 + c2, c3, 0, nullptr, P(p2)));
   ART_TRY(conv(P(p2), c2, H / 8, W / 8, 6, P(e3a), c3, 0, 0, nullptr));
   ART_TRY(conv(P(e3a), c3, H / 8, W / 8, 7, P(cat2), c3 + c2, 0, 1, nullptr));  // up x2 into cat2
   ART_TRY(conv(P(cat2), c3 + c2, H / 4, W / 4, 8, P(d2a), c2, 0, 0, nullptr));

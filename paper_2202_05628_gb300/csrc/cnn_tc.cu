@@ -41,6 +41,7 @@ struct TcParams {
   float* rgba;           // fused 1x1 head (cout -> 4) + sigmoid when non-null
   const float* head_w;   // [4][cout]
   const float* head_b;   // [4]
+  __nv_bfloat16* pool;   // row-blocked kernel: fused 2x2 max pooling, dense [H/2][W/2][cout]
   unsigned long long* err;
 };
 
@@ -111,6 +112,64 @@ __device__ __forceinline__ void epi_row(const TcParams& p, uint32_t taddr, int y
 #pragma unroll
           for (int k = 0; k < kVec; ++k) dst[k] = pk[k];
         }
+    }
+  }
+}
+
+// Epilogue of one output row of the row-blocked kernel with the 2x2 max
+// pooling fused: the row is stored as by epi_row (BF16, no upsampling), and
+// its packed values are kept (first row of a pair) or pooled with the kept
+// row and the neighbouring pixel's lane (second row), the pooled pixel stored
+// by the even lane.  Max and BF16 rounding commute, so this equals pooling
+// the stored tensor.
+template <int N>
+__device__ __forceinline__ void epi_row_pool(const TcParams& p, uint32_t taddr, int y, int x, const float* s_bias,
+                                             uint32_t (&keep)[N / 2], bool second) {
+  const bool valid = x < p.W;
+#pragma unroll
+  for (int c0 = 0; c0 < N; c0 += 32) {
+    uint32_t r[32];
+    tmem_ld32(taddr + (uint32_t)c0, r);
+    uint4 pk[4];
+    uint32_t* w = reinterpret_cast<uint32_t*>(pk);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      float t0 = __uint_as_float(r[2 * j]) + s_bias[c0 + 2 * j];
+      float t1 = __uint_as_float(r[2 * j + 1]) + s_bias[c0 + 2 * j + 1];
+      if (p.act == 1) {
+        t0 = fmaxf(t0, 0.0f);
+        t1 = fmaxf(t1, 0.0f);
+      }
+      __nv_bfloat162 b2 = __floats2bfloat162_rn(t0, t1);
+      w[j] = *reinterpret_cast<uint32_t*>(&b2);
+    }
+    if (valid) {
+      uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(p.out) +
+                                            ((size_t)y * p.W + x) * p.ld_out + p.ch_off + c0);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) dst[k] = pk[k];
+    }
+    if (!second) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) keep[c0 / 2 + j] = w[j];
+    } else {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        __nv_bfloat162 a = *reinterpret_cast<__nv_bfloat162*>(&keep[c0 / 2 + j]);
+        __nv_bfloat162 b = *reinterpret_cast<__nv_bfloat162*>(&w[j]);
+        __nv_bfloat162 m = __hmax2(a, b);
+        uint32_t mu = *reinterpret_cast<uint32_t*>(&m);
+        uint32_t nu = __shfl_xor_sync(0xffffffffu, mu, 1);
+        __nv_bfloat162 n = *reinterpret_cast<__nv_bfloat162*>(&nu);
+        m = __hmax2(m, n);
+        w[j] = *reinterpret_cast<uint32_t*>(&m);
+      }
+      const int Wp = p.W / 2, Hp = p.H / 2;
+      if (!(x & 1) && (x >> 1) < Wp && (y >> 1) < Hp) {
+        uint4* dst = reinterpret_cast<uint4*>(p.pool + ((size_t)(y >> 1) * Wp + (x >> 1)) * N + c0);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) dst[k] = pk[k];
+      }
     }
   }
 }
@@ -288,21 +347,19 @@ __global__ void __launch_bounds__(kThreads, 1)
 // units in flight.
 constexpr int kRows = 4;
 
-// With 32 output channels the vertical taps are stacked into one operand:
+// The vertical taps are stacked into one operand:
 // the accumulators of the unit's R output rows sit in consecutive TMEM
 // column slots in reverse row order (slot of output row r = R - 1 - r), so
-// that one MMA per input-row box, N = 32 x (the taps whose output row lies
-// in the unit: 3 inside, 2 or 1 at the unit's edge rows), accumulates into
+// that one MMA per input-row box, N x (the taps whose output row lies in
+// the unit: 3 inside, 2 or 1 at the unit's edge rows) columns, accumulates into
 // every row it touches.  Every MMA accumulates; the epilogue zeroes each
 // slot after reading it.
 template <int N, int KCB>
 struct RowCfg {
   static constexpr int KC = KCB / 2;  // channels per chunk
   static constexpr int kA = 128 * KCB;
-  static constexpr bool kStack = N == 32;
   static constexpr int kSlots = kRows;
   static constexpr int kBufCols = kSlots * N;  // columns of one accumulator buffer
-  static constexpr uint32_t kIdesc = idesc_bf16(128, N);
   static constexpr int kHalo = 130;                                   // input pixels of a row box (128 + 2)
   static constexpr int kBoxBytes = kHalo * KCB;
   static constexpr int kStageBytes = (kBoxBytes + 1023) / 1024 * 1024;  // stages stay on swizzle-atom boundaries
@@ -344,9 +401,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int kStage = Cfg::kStageBytes;         // one box of 130 pixels: the three shifts are row offsets
   // the swizzle follows the absolute shared-memory address, so a descriptor
   // may start at any row of the box: shift dx is the box from row dx on
-  // resident weight block of (dy + 1, dx + 1, chunk); stacked form: the three
-  // vertical taps of one (dx, chunk) are adjacent (one N = 96 operand)
-  auto wblk = [&](int dyi, int dxi, int c) { return Cfg::kStack ? (dxi * cpt + c) * 3 + dyi : (dyi * 3 + dxi) * cpt + c; };
+  // resident weight block of (dy + 1, dx + 1, chunk): the three vertical
+  // taps of one (dx, chunk) are adjacent (one stacked operand of up to 3 N rows)
+  auto wblk = [&](int dyi, int dxi, int c) { return (dxi * cpt + c) * 3 + dyi; };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
@@ -407,8 +464,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool ok = mbar_wait(wbar, 0u, abort_flag);
       const uint32_t wbase = smem_u32(wsm);
       for (int u = blockIdx.x; ok && u < rp.n_units && !*abort_flag; u += gridDim.x) {
-        // stacked form: the epilogue clears the accumulators (phase 0 = the initial clear)
-        if (!mbar_wait(&acce[buf], Cfg::kStack ? aph : aph ^ 1u, abort_flag)) break;
+        // the epilogue clears the accumulators (phase 0 = the initial clear)
+        if (!mbar_wait(&acce[buf], aph, abort_flag)) break;
         tc_fence_after();
         const uint32_t d0 = tmem_base + (uint32_t)(buf * Cfg::kBufCols);
         for (int st = 0; st < n_stage_unit; ++st) {
@@ -419,33 +476,17 @@ __global__ void __launch_bounds__(kThreads, 1)
           tc_fence_after();
           const int j = st / cpt, c = st - j * cpt;
           const uint32_t a0 = smem_u32(stages + (size_t)s * kStage);
-          if constexpr (Cfg::kStack) {
-            // input row j feeds output rows j - dyi of the unit for the taps dyi in [lo, hi]
-            // (slots R - 1 - j + lo ..., consecutive like the stacked taps' weight blocks)
-            const int lo = max(0, j - kRows + 1), hi = min(2, j);
-            const uint32_t dj = d0 + (uint32_t)((kRows - 1 - j + lo) * N);
-            const uint32_t idesc = idesc_bf16(128, (hi - lo + 1) * N);
+          // input row j feeds output rows j - dyi of the unit for the taps dyi in [lo, hi]
+          // (slots R - 1 - j + lo ..., consecutive like the stacked taps' weight blocks)
+          const int lo = max(0, j - kRows + 1), hi = min(2, j);
+          const uint32_t dj = d0 + (uint32_t)((kRows - 1 - j + lo) * N);
+          const uint32_t idesc = idesc_bf16(128, (hi - lo + 1) * N);
 #pragma unroll
-            for (int dxi = 0; dxi < 3; ++dxi) {
-              const uint32_t bw = wbase + (uint32_t)((wblk(0, dxi, c) + lo) * N * KCB);
+          for (int dxi = 0; dxi < 3; ++dxi) {
+            const uint32_t bw = wbase + (uint32_t)((wblk(0, dxi, c) + lo) * N * KCB);
 #pragma unroll
-              for (int kk = 0; kk < KCB / 32; ++kk)
-                umma<false>(dj, umma_desc<KCB>(a0 + dxi * KCB + kk * 32), umma_desc<KCB>(bw + kk * 32), idesc, 1u);
-            }
-          } else {
-#pragma unroll
-            for (int dxi = 0; dxi < 3; ++dxi)
-#pragma unroll
-              for (int kk = 0; kk < KCB / 32; ++kk)
-#pragma unroll
-                for (int r = 0; r < kRows; ++r) {  // rows interleaved: independent accumulators back to back
-                  const int dyi = j - r;             // dy + 1
-                  if (dyi < 0 || dyi > 2) continue;
-                  const uint32_t bw = wbase + (uint32_t)(wblk(dyi, dxi, c) * N * KCB);
-                  const bool first = dyi == 0 && dxi == 0 && c == 0 && kk == 0;
-                  umma<false>(d0 + (uint32_t)(r * N), umma_desc<KCB>(a0 + dxi * KCB + kk * 32),
-                              umma_desc<KCB>(bw + kk * 32), Cfg::kIdesc, first ? 0u : 1u);
-                }
+            for (int kk = 0; kk < KCB / 32; ++kk)
+              umma<false>(dj, umma_desc<KCB>(a0 + dxi * KCB + kk * 32), umma_desc<KCB>(bw + kk * 32), idesc, 1u);
           }
           umma_commit(&empty[s]);
           if (++s == S) {
@@ -467,9 +508,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int qd = warp & 3;
     const int m = qd * 32 + lane;
     const uint32_t tq = tmem_base + ((uint32_t)(qd * 32) << 16);  // this warp's lane quarter
+    uint32_t keep[N / 2];  // fused pooling: the first row of the pair, packed BF16
     int buf = 0;
     uint32_t aph = 0;
-    if constexpr (Cfg::kStack) {  // zero every slot of both buffers, then release them to the MMA
+    {  // zero every slot of both buffers, then release them to the MMA
       for (int c0 = 0; c0 < (int)tmem_cols; c0 += 32) tmem_zero32(tq + (uint32_t)c0);
       tmem_wait_st();
       tc_fence_before();
@@ -480,15 +522,18 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc_fence_after();
       const int y0 = (u / p.tiles_per_row) * kRows, x = (u % p.tiles_per_row) * 128 + m;
       for (int r = 0; r < kRows; ++r) {
-        const int slot = Cfg::kStack ? kRows - 1 - r : r;
+        const int slot = kRows - 1 - r;
         const uint32_t ta = tq + (uint32_t)(buf * Cfg::kBufCols + slot * N);
-        if (y0 + r < p.H) epi_row<N, false>(p, ta, y0 + r, x, s_bias, s_head, nullptr, 1.0f, 1.0f, amax);
-        if constexpr (Cfg::kStack) {
-#pragma unroll
-          for (int c0 = 0; c0 < N; c0 += 32) tmem_zero32(ta + (uint32_t)c0);
+        if (y0 + r < p.H) {
+          if (p.pool)
+            epi_row_pool<N>(p, ta, y0 + r, x, s_bias, keep, (r & 1) != 0);
+          else
+            epi_row<N, false>(p, ta, y0 + r, x, s_bias, s_head, nullptr, 1.0f, 1.0f, amax);
         }
+#pragma unroll
+        for (int c0 = 0; c0 < N; c0 += 32) tmem_zero32(ta + (uint32_t)c0);
       }
-      if constexpr (Cfg::kStack) tmem_wait_st();
+      tmem_wait_st();
       tc_fence_before();
       mbar_arrive(&acce[buf]);
       if (++buf == nbuf) {
@@ -594,6 +639,7 @@ art_status launch_typed(art_ctx* ctx, const TcConv& c) {
   p.rgba = c.rgba;
   p.head_w = c.head_w;
   p.head_b = c.head_b;
+  p.pool = nullptr;  // pooled by a pass of its own
   p.err = ctx->d_status + kStTcError;
   auto kfn = conv_tc_kernel<N, KCB, F8>;
   cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem);
@@ -677,6 +723,7 @@ art_status launch_rows(art_ctx* ctx, const TcConv& c) {
   p.rgba = c.rgba;
   p.head_w = c.head_w;
   p.head_b = c.head_b;
+  p.pool = (__nv_bfloat16*)c.pool;
   p.err = ctx->d_status + kStTcError;
   rp.cpt = c.cin / Cfg::KC;
   rp.n_units = ((c.H + kRows - 1) / kRows) * p.tiles_per_row;
@@ -724,16 +771,21 @@ art_status launch_tc_conv(art_ctx* ctx, const TcConv& c) {
 #undef ART_F8
   }
   const bool k64 = c.cin % 64 == 0;  // BF16: 64 channels = 128-B rows, else 32 = 64-B rows
-  if ((c.cout == 32 || c.cout == 64) && 9 * c.cin * c.cout * 2 <= kRowsMaxWeights && ctx->conv_rows) {
+  if ((c.cout == 32 || c.cout == 64) && 9 * c.cin * c.cout * 2 <= kRowsMaxWeights && ctx->conv_rows &&
+      (!c.pool || (!c.up2 && !c.rgba))) {
     if (c.cout == 32) return k64 ? launch_rows<32, 128>(ctx, c) : launch_rows<32, 64>(ctx, c);
     return k64 ? launch_rows<64, 128>(ctx, c) : launch_rows<64, 64>(ctx, c);
   }
+  art_status st;
   switch (c.cout) {
-    case 32: return k64 ? launch_typed<32, 128, false>(ctx, c) : launch_typed<32, 64, false>(ctx, c);
-    case 64: return k64 ? launch_typed<64, 128, false>(ctx, c) : launch_typed<64, 64, false>(ctx, c);
-    case 128: return k64 ? launch_typed<128, 128, false>(ctx, c) : launch_typed<128, 64, false>(ctx, c);
-    default: return k64 ? launch_typed<256, 128, false>(ctx, c) : launch_typed<256, 64, false>(ctx, c);
+    case 32: st = k64 ? launch_typed<32, 128, false>(ctx, c) : launch_typed<32, 64, false>(ctx, c); break;
+    case 64: st = k64 ? launch_typed<64, 128, false>(ctx, c) : launch_typed<64, 64, false>(ctx, c); break;
+    case 128: st = k64 ? launch_typed<128, 128, false>(ctx, c) : launch_typed<128, 64, false>(ctx, c); break;
+    default: st = k64 ? launch_typed<256, 128, false>(ctx, c) : launch_typed<256, 64, false>(ctx, c); break;
   }
+  if (st == ART_OK && c.pool)
+    launch_pool_bf16(ctx, (const __nv_bfloat16*)c.out, c.ld_out, c.ch_off, (__nv_bfloat16*)c.pool, c.H, c.W, c.cout);
+  return st;
 }
 
 void launch_pool_bf16(art_ctx* ctx, const __nv_bfloat16* in, int ld, int ch_off, __nv_bfloat16* out, int H, int W,

@@ -74,6 +74,8 @@ __device__ __forceinline__ void composite_tile(const int tile, const Seg& sg,
   __shared__ float s_sig[RING][NT];
   __shared__ uint32_t s_vid[RING][NT];
   __shared__ __align__(16) TF s_feat[RING][NT][C];
+  __shared__ __align__(16) float4 s_rec[2][NT][4];  // raw voxel records of this chunk and the next
+  __shared__ short4 s_rc[2][NT];
 
   const int lane = threadIdx.x & 31;
   const int tx = tile % v.tiles_x, ty = tile / v.tiles_x;
@@ -141,7 +143,7 @@ __device__ __forceinline__ void composite_tile(const int tile, const Seg& sg,
     float f[C];
     float sig;
     uint32_t vid;
-    if (cur_chunk - ch < RING) {
+    if (cur_chunk - ch < RING - 1) {  // (the ring's last slot takes the next chunk's rows)
       sig = s_sig[ch % RING][sl];
       vid = s_vid[ch % RING][sl];
       if constexpr (FEAT) row_to_float<C>(&s_feat[ch % RING][sl][0], f);
@@ -175,21 +177,52 @@ __device__ __forceinline__ void composite_tile(const int tile, const Seg& sg,
     if (T < tau) done = true;
   };
 
+  // Staging pipeline: the records and feature rows of chunk i + 1 are copied
+  // asynchronously while chunk i is walked, and the list entries of chunk
+  // i + 2 are loaded into registers meanwhile.
+  auto issue = [&](uint32_t cbase, int cslot, int b, uint32_t vid) {
+    if (cbase + lane < rg.y) {
+      const float4* rp = rec + 4 * (size_t)vid;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) cp_async16(&s_rec[b][lane][q], rp + q);
+      cp_async8(&s_rc[b][lane], rect + vid);
+      if constexpr (FEAT) copy_row_async<C, TF>(feat + (size_t)vid * C, &s_feat[cslot][lane][0]);
+    }
+    cp_async_commit();
+  };
+  uint32_t vid_c = 0, key_c = 0, vid_n = 0, key_n = 0;  // list entries of the current and the next chunk
+  if (rg.x + lane < rg.y) {
+    vid_c = vals[rg.x + lane];
+    key_c = keys[rg.x + lane];
+  }
+  issue(rg.x, 0, 0, vid_c);
+  if (rg.x + NT + lane < rg.y) {
+    vid_n = vals[rg.x + NT + lane];
+    key_n = keys[rg.x + NT + lane];
+  }
+
   for (uint32_t base = rg.x; base < rg.y; base += NT) {
     cur_chunk = (int)((base - rg.x) / NT);
     const int slot = cur_chunk % RING;
+    const int b = cur_chunk & 1;
     __syncwarp();
+    issue(base + NT, (cur_chunk + 1) % RING, b ^ 1, vid_n);
+    const uint32_t vid = vid_c, key = key_c;
+    vid_c = vid_n;
+    key_c = key_n;
+    if (base + 2 * NT + lane < rg.y) {
+      vid_n = vals[base + 2 * NT + lane];
+      key_n = keys[base + 2 * NT + lane];
+    }
+    cp_async_wait<1>();  // this chunk's copies (the next chunk's may be in flight)
     {  // stage one instance per lane
       const uint32_t k = base + lane;
       uint32_t m = 0;
       float thr = 3.4e38f;
       if (k < rg.y) {
-        const uint32_t vid = vals[k];
-        const uint32_t key = keys[k];
-        const float4* rp = rec + 4 * (size_t)vid;
-        const float4 r0 = rp[0], r1 = rp[1], r2 = rp[2], r3 = rp[3];
-        const short4 rc = rect[vid];
-        if constexpr (FEAT) copy_row<C, TF>(feat + (size_t)vid * C, &s_feat[slot][lane][0]);
+        const float4 r0 = s_rec[b][lane][0], r1 = s_rec[b][lane][1], r2 = s_rec[b][lane][2],
+                     r3 = s_rec[b][lane][3];
+        const short4 rc = s_rc[b][lane];
         const float ex = v.o[0] - r0.w, ey = v.o[1] - r1.w, ez = v.o[2] - r2.w;
         s_b0[lane] = make_float4(r0.x, r0.y, r0.z, r0.x * ex + r0.y * ey + r0.z * ez);
         s_b1[lane] = make_float4(r1.x, r1.y, r1.z, r1.x * ex + r1.y * ey + r1.z * ez);
@@ -255,6 +288,8 @@ __device__ __forceinline__ void composite_tile(const int tile, const Seg& sg,
     if (__all_sync(0xffffffffu, done)) break;
   }
   while (nb > 0 && !done) release_front();
+  cp_async_wait<0>();  // no copy may land in a later segment's staging
+  __syncwarp();
 
   if (sg.part) {  // a segment of a split tile: partial sums for the merge
 #pragma unroll
@@ -361,7 +396,7 @@ __global__ void __launch_bounds__(256) composite_clear_kernel(const uint2* __res
 }
 
 template <int C, typename TF, typename TO, int MODE>
-__global__ void __launch_bounds__(32) composite_split_kernel(
+__global__ void __launch_bounds__(32, 12) composite_split_kernel(
     const uint2* __restrict__ ranges, const uint2* __restrict__ seg, const uint32_t* __restrict__ items,
     const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals, const float4* __restrict__ rec,
     const short4* __restrict__ rect, const TF* __restrict__ feat, ViewParams v, float tau, TO* __restrict__ Fout,

@@ -281,6 +281,9 @@ struct TcConv {
   float* rgba;
   const float* head_w;
   const float* head_b;
+  // BF16: also the 2x2 max pooling of the output, a dense [H/2][W/2][cout]
+  // tensor (fused into the row-blocked kernel's epilogue, else a pass of its own)
+  void* pool = nullptr;
   // FP8 (E4M3) network: operands and output in E4M3; the accumulator is
   // dequantised by in_scale x w_scale[co], the output quantised by out_scale
   // and its max |value| recorded in out_amax (float bits).

@@ -136,12 +136,44 @@ constexpr int NT = 32;           // instances per staged chunk
 
 template <int C, typename TF>
 struct Ring {
-  // chunks of staged feature rows kept in shared memory (<= 12 KB, 1 .. 16):
+  // chunks of staged feature rows kept in shared memory (<= 10 KB, 1 .. 16):
   // small enough for many resident one-warp blocks; a hit released after its
   // chunk left the ring reads its voxel again from global memory
-  static constexpr int kRaw = 12288 / (NT * C * (int)sizeof(TF));
+  static constexpr int kRaw = 10240 / (NT * C * (int)sizeof(TF));
   static constexpr int kChunks = kRaw < 1 ? 1 : (kRaw < 16 ? kRaw : 16);
 };
+
+// Asynchronous global -> shared copies (cp.async): issued, grouped per
+// commit, and waited for by group; a thread sees its own copies after the
+// wait, the other lanes after a __syncwarp that follows it.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// A feature row into shared memory, asynchronously.
+template <int C, typename TF>
+__device__ __forceinline__ void copy_row_async(const TF* __restrict__ src, TF* dst) {
+  constexpr int kBytes = C * (int)sizeof(TF);
+  if constexpr (kBytes % 16 == 0) {
+#pragma unroll
+    for (int k = 0; k < kBytes / 16; ++k)
+      cp_async16(reinterpret_cast<uint8_t*>(dst) + 16 * k, reinterpret_cast<const uint8_t*>(src) + 16 * k);
+  } else {
+#pragma unroll
+    for (int k = 0; k < kBytes / 8; ++k)
+      cp_async8(reinterpret_cast<uint8_t*>(dst) + 8 * k, reinterpret_cast<const uint8_t*>(src) + 8 * k);
+  }
+}
 
 template <int C, typename TF>
 __device__ __forceinline__ void copy_row(const TF* __restrict__ src, TF* dst) {
