@@ -218,8 +218,10 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(
 // That is the order of a stable sort of the keys emitted in voxel order, so
 // the result does not depend on the order in which the atomics land.
 
-constexpr int kTileScanThreads = 1024;
-constexpr int kTileScanItems = 16;       // tiles per thread and chunk
+constexpr int kTileScanThreads = 256;
+constexpr int kTileScanItems = 4;        // tiles per thread
+constexpr int kTileScanBlock = kTileScanThreads * kTileScanItems;  // tiles per block
+constexpr long long kScanSpin = 1 << 22;  // look-back polls before a block gives up
 constexpr int kTileSortThreads = 512;
 constexpr int kTileSortWarps = kTileSortThreads / 32;
 constexpr int kSortPer = 16;             // bucket entries per thread held in registers
@@ -235,9 +237,16 @@ __device__ __forceinline__ uint32_t rect_tile(const ViewParams& v, int tx0, int 
 
 // Per voxel: one count for every tile its pixel rectangle covers.  Lanes of a
 // warp that hit the same tile in the same step add together.
+// Block 0 also clears the tile scan's look-back words and block ticket.
 __global__ void __launch_bounds__(256) tile_count_kernel(int64_t n, const uint32_t* __restrict__ cnt,
                                                          const short4* __restrict__ rect, ViewParams v,
-                                                         uint32_t* __restrict__ tcount) {
+                                                         uint32_t* __restrict__ tcount,
+                                                         unsigned long long* __restrict__ scan_state, int scan_words,
+                                                         unsigned long long* __restrict__ status) {
+  if (blockIdx.x == 0) {
+    for (int k = threadIdx.x; k < scan_words; k += blockDim.x) scan_state[k] = 0ull;
+    if (threadIdx.x == 0) status[kStScanTicket] = 0ull;
+  }
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
   uint32_t c = 0;
@@ -256,76 +265,161 @@ __global__ void __launch_bounds__(256) tile_count_kernel(int64_t n, const uint32
   }
 }
 
-// Shared-memory slot of element i of a chunk: one pad word per 32 so that
-// threads reading consecutive runs of kTileScanItems hit distinct banks.
-__device__ __forceinline__ int scan_slot(int i) { return i + (i >> 5); }
-constexpr int kTileScanChunk = kTileScanThreads * kTileScanItems;
-constexpr int kTileScanSmem = 4 * (kTileScanChunk + kTileScanChunk / 32 + 1);
+// Single-pass tile scan with decoupled look-back.  Blocks take consecutive
+// runs of kTileScanBlock tiles in the order they start (a ticket), so every
+// predecessor of a block is already running.  A block publishes its totals
+// (instances; list entries small | big << 31) as soon as it has them, then
+// its warp 0 looks back over up to 32 predecessors per round: the nearest one
+// that published its inclusive prefix ends the walk, the others contribute
+// their totals.  Words carry their value shifted left by one with bit 0 set
+// once written (zeroed by tile_count_kernel).  A poll that does not end within
+// kScanSpin tries counts the block in kStScanError and reads zero.
+//
+// Outputs: bucket cursors and tile ranges (clamped to the capacity), the
+// total into kStInstances, and the tiles whose bucket needs sorting: those of
+// 2..kWarpSortCap instances from the front of sort_list, longer ones from its
+// end (kStSortTiles and kStSortBig of them, written by the last block, which
+// also resets both work counters).
+struct ScanWords {  // per block: aggregate and inclusive prefix, each (instances, lists)
+  unsigned long long agg_i, agg_l, inc_i, inc_l;
+};
 
-// One block: exclusive scan of the tile counts into the bucket cursors and
-// the tile ranges (clamped to the capacity), the total into kStInstances,
-// and the tiles whose bucket needs sorting: those of 2..kWarpSortCap
-// instances from the front of sort_list, longer ones from its end
-// (kStSortTiles and kStSortBig of them; both work counters reset).  Chunks
-// pass through shared memory so that every global access is coalesced.
+__device__ __forceinline__ unsigned long long ld_volatile(const unsigned long long* p) {
+  return *reinterpret_cast<const volatile unsigned long long*>(p);
+}
+__device__ __forceinline__ void st_volatile(unsigned long long* p, unsigned long long x) {
+  *reinterpret_cast<volatile unsigned long long*>(p) = x;
+}
+
 __global__ void __launch_bounds__(kTileScanThreads) tile_scan_kernel(int ntiles, const uint32_t* __restrict__ tcount,
                                                                      int64_t cap, uint32_t* __restrict__ toff,
                                                                      uint2* __restrict__ ranges,
                                                                      uint32_t* __restrict__ sort_list,
+                                                                     ScanWords* __restrict__ sw,
                                                                      unsigned long long* __restrict__ status) {
-  extern __shared__ uint32_t sbuf[];
-  uint64_t carry = 0;
-  uint32_t n_small = 0, n_big = 0;
-  for (int base0 = 0; base0 < ntiles; base0 += kTileScanChunk) {
-    const int len = min(kTileScanChunk, ntiles - base0);
-    {
-      uint32_t x[kTileScanItems];  // all loads in flight before the first store
+  __shared__ unsigned long long s_b, s_pi, s_pl;
+  if (threadIdx.x == 0) s_b = atomicAdd(status + kStScanTicket, 1ull);
+  __syncthreads();
+  const int b = (int)s_b;
+  const int nblocks = (ntiles + kTileScanBlock - 1) / kTileScanBlock;
+  const int base = b * kTileScanBlock + (int)threadIdx.x * kTileScanItems;
+  uint32_t c[kTileScanItems];
+  if (base + kTileScanItems <= ntiles) {
+    const uint4 x = *reinterpret_cast<const uint4*>(tcount + base);
+    c[0] = x.x;
+    c[1] = x.y;
+    c[2] = x.z;
+    c[3] = x.w;
+  } else {
 #pragma unroll
-      for (int k = 0; k < kTileScanItems; ++k) {
-        const int i = k * kTileScanThreads + (int)threadIdx.x;
-        x[k] = i < len ? tcount[base0 + i] : 0u;
+    for (int k = 0; k < kTileScanItems; ++k) c[k] = base + k < ntiles ? tcount[base + k] : 0u;
+  }
+  uint32_t s = 0, lists = 0;  // lists: small | big << 16 (per block < 2^16 each)
+#pragma unroll
+  for (int k = 0; k < kTileScanItems; ++k) {
+    s += c[k];
+    lists += c[k] > (uint32_t)kWarpSortCap ? 0x10000u : (c[k] > 1u ? 1u : 0u);
+  }
+  uint32_t tot = 0, lt = 0;
+  const uint32_t ps = block_exclusive_scan(s, &tot);
+  const uint32_t lp = block_exclusive_scan(lists, &lt);
+  const unsigned long long agg_l = (unsigned long long)(lt & 0xFFFFu) | ((unsigned long long)(lt >> 16) << 31);
+  if (threadIdx.x == 0) {
+    if (b == 0) {
+      st_volatile(&sw[0].inc_i, ((unsigned long long)tot << 1) | 1ull);
+      st_volatile(&sw[0].inc_l, (agg_l << 1) | 1ull);
+    } else {
+      st_volatile(&sw[b].agg_i, ((unsigned long long)tot << 1) | 1ull);
+      st_volatile(&sw[b].agg_l, (agg_l << 1) | 1ull);
+    }
+  }
+  if (threadIdx.x < 32) {  // look back
+    const int lane = threadIdx.x;
+    unsigned long long pi = 0, pl = 0;
+    for (int p = b - 1; p >= 0; p -= 32) {
+      const int q = p - lane;
+      unsigned long long vi = 0, vl = 0;
+      bool inc = q < 0;
+      if (q >= 0) {
+        long long spin = 0;
+        for (;;) {
+          const unsigned long long ii = ld_volatile(&sw[q].inc_i), il = ld_volatile(&sw[q].inc_l);
+          if ((ii & 1ull) && (il & 1ull)) {
+            vi = ii >> 1;
+            vl = il >> 1;
+            inc = true;
+            break;
+          }
+          const unsigned long long ai = ld_volatile(&sw[q].agg_i), al = ld_volatile(&sw[q].agg_l);
+          if ((ai & 1ull) && (al & 1ull)) {
+            vi = ai >> 1;
+            vl = al >> 1;
+            break;
+          }
+          if (++spin > kScanSpin) {
+            atomicAdd(status + kStScanError, 1ull);
+            break;
+          }
+          __nanosleep(64);
+        }
+      }
+      const unsigned incm = __ballot_sync(0xffffffffu, inc);
+      const int stop = incm ? __ffs(incm) - 1 : 32;  // nearest predecessor with its inclusive prefix
+      if (lane > stop) {
+        vi = 0;
+        vl = 0;
       }
 #pragma unroll
-      for (int k = 0; k < kTileScanItems; ++k) sbuf[scan_slot(k * kTileScanThreads + (int)threadIdx.x)] = x[k];
+      for (int o = 16; o > 0; o >>= 1) {
+        vi += __shfl_xor_sync(0xffffffffu, vi, o);
+        vl += __shfl_xor_sync(0xffffffffu, vl, o);
+      }
+      pi += vi;
+      pl += vl;
+      if (stop < 32) break;
     }
-    __syncthreads();
-    const int i0 = (int)threadIdx.x * kTileScanItems;
-    uint32_t c[kTileScanItems], s = 0, lists = 0;  // lists: small | big << 16
-#pragma unroll
-    for (int k = 0; k < kTileScanItems; ++k) {
-      c[k] = sbuf[scan_slot(i0 + k)];
-      s += c[k];
-      lists += c[k] > (uint32_t)kWarpSortCap ? 0x10000u : (c[k] > 1u ? 1u : 0u);
+    if (lane == 0) {
+      s_pi = pi;
+      s_pl = pl;
+      if (b > 0) {
+        st_volatile(&sw[b].inc_i, ((pi + tot) << 1) | 1ull);
+        st_volatile(&sw[b].inc_l, ((pl + agg_l) << 1) | 1ull);
+      }
     }
-    uint32_t tot = 0, lt = 0;
-    uint64_t off = carry + block_exclusive_scan(s, &tot);  // (ends with a barrier)
-    const uint32_t lp = block_exclusive_scan(lists, &lt);
-    uint32_t ps = n_small + (lp & 0xFFFFu), pb = n_big + (lp >> 16);
-#pragma unroll
-    for (int k = 0; k < kTileScanItems; ++k) {
-      sbuf[scan_slot(i0 + k)] = (uint32_t)min(off, (uint64_t)cap);
-      if (c[k] > (uint32_t)kWarpSortCap)
-        sort_list[ntiles - 1 - (int)pb++] = (uint32_t)(base0 + i0 + k);
-      else if (c[k] > 1u && i0 + k < len)
-        sort_list[ps++] = (uint32_t)(base0 + i0 + k);
-      off += c[k];
-    }
-    carry += tot;
-    if (threadIdx.x == 0) sbuf[scan_slot(kTileScanChunk)] = (uint32_t)min(carry, (uint64_t)cap);
-    __syncthreads();
-    for (int i = threadIdx.x; i < len; i += kTileScanThreads) {
-      const uint32_t a = sbuf[scan_slot(i)];
-      toff[base0 + i] = a;
-      ranges[base0 + i] = make_uint2(a, i + 1 < len ? sbuf[scan_slot(i + 1)] : sbuf[scan_slot(kTileScanChunk)]);
-    }
-    n_small += lt & 0xFFFFu;
-    n_big += lt >> 16;
-    __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    status[kStInstances] = carry;
-    status[kStSortTiles] = n_small;
-    status[kStSortBig] = n_big;
+  __syncthreads();
+  const unsigned long long pi = s_pi, pl = s_pl;
+  uint64_t off = pi + ps;
+  uint32_t nsm = (uint32_t)(pl & 0x7FFFFFFFull) + (lp & 0xFFFFu), nbg = (uint32_t)(pl >> 31) + (lp >> 16);
+  uint32_t a4[kTileScanItems];
+  uint2 r4[kTileScanItems];
+#pragma unroll
+  for (int k = 0; k < kTileScanItems; ++k) {
+    const uint64_t a = min(off, (uint64_t)cap), e = min(off + c[k], (uint64_t)cap);
+    a4[k] = (uint32_t)a;
+    r4[k] = make_uint2((uint32_t)a, (uint32_t)e);
+    if (c[k] > (uint32_t)kWarpSortCap)
+      sort_list[ntiles - 1 - (int)nbg++] = (uint32_t)(base + k);
+    else if (c[k] > 1u)
+      sort_list[nsm++] = (uint32_t)(base + k);
+    off += c[k];
+  }
+  if (base + kTileScanItems <= ntiles) {
+    *reinterpret_cast<uint4*>(toff + base) = make_uint4(a4[0], a4[1], a4[2], a4[3]);
+    *reinterpret_cast<uint4*>(ranges + base) = make_uint4(r4[0].x, r4[0].y, r4[1].x, r4[1].y);
+    *reinterpret_cast<uint4*>(ranges + base + 2) = make_uint4(r4[2].x, r4[2].y, r4[3].x, r4[3].y);
+  } else {
+#pragma unroll
+    for (int k = 0; k < kTileScanItems; ++k)
+      if (base + k < ntiles) {
+        toff[base + k] = a4[k];
+        ranges[base + k] = r4[k];
+      }
+  }
+  if (b == nblocks - 1 && threadIdx.x == 0) {
+    status[kStInstances] = pi + tot;
+    status[kStSortTiles] = (pl & 0x7FFFFFFFull) + (lt & 0xFFFFu);
+    status[kStSortBig] = (pl >> 31) + (lt >> 16);
     status[kStSortNext] = 0;
     status[kStSortBigNext] = 0;
   }
@@ -600,6 +694,8 @@ __global__ void __launch_bounds__(kTileSortThreads) tile_sort_kernel(const uint2
 
 size_t scan_block_words(int64_t n) { return (size_t)((n + kScanBlock - 1) / kScanBlock) + 1; }
 
+size_t tile_scan_state_words(int64_t ntiles) { return 4 * (size_t)((ntiles + kTileScanBlock - 1) / kTileScanBlock); }
+
 size_t sort_hist_words(int64_t inst_cap) {
   int64_t nb = (inst_cap + kSortBlock - 1) / kSortBlock;
   return (size_t)(nb * kRadix);
@@ -611,14 +707,16 @@ void launch_bin(art_ctx* ctx, const ViewParams& v, const uint32_t* hbin, const f
   const unsigned vb = (unsigned)((n + 255) / 256);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(tile_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileScanSmem);
     cudaFuncSetAttribute(tile_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileSortSmem * 8);
     attr = true;
   }
+  const int nsb = (ntiles + kTileScanBlock - 1) / kTileScanBlock;
   cudaMemsetAsync(ctx->d_tcount, 0, sizeof(uint32_t) * (size_t)ntiles, ctx->stream);
-  ART_LAUNCH(ctx, "bin_count", tile_count_kernel, vb, 256, 0, n, ctx->d_cnt, ctx->d_rect, v, ctx->d_tcount);
-  ART_LAUNCH(ctx, "bin_scan", tile_scan_kernel, 1, kTileScanThreads, kTileScanSmem, ntiles, ctx->d_tcount, ctx->inst_cap,
-             ctx->d_toff, ctx->d_ranges, ctx->d_sortlist, ctx->d_status);
+  ART_LAUNCH(ctx, "bin_count", tile_count_kernel, vb, 256, 0, n, ctx->d_cnt, ctx->d_rect, v, ctx->d_tcount,
+             ctx->d_scan_state, 4 * nsb, ctx->d_status);
+  ART_LAUNCH(ctx, "bin_scan", tile_scan_kernel, nsb, kTileScanThreads, 0, ntiles, ctx->d_tcount, ctx->inst_cap,
+             ctx->d_toff, ctx->d_ranges, ctx->d_sortlist, reinterpret_cast<ScanWords*>(ctx->d_scan_state),
+             ctx->d_status);
   ART_LAUNCH(ctx, "bin_emit", bucket_emit_kernel, vb, 256, 0, n, ctx->d_cnt, ctx->d_rect, ctx->d_q, v, ctx->inst_cap,
              ctx->d_toff, ctx->d_keys, ctx->d_vals, ctx->d_status, hbin, htau, thist);
   ART_LAUNCH(ctx, "tile_sort", tile_sort_kernel, 2 * ctx->num_sms, kTileSortThreads, kTileSortSmem * 8, ctx->d_ranges,

@@ -357,7 +357,6 @@ constexpr int kRows = 4;
 template <int N, int KCB>
 struct RowCfg {
   static constexpr int KC = KCB / 2;  // channels per chunk
-  static constexpr int kA = 128 * KCB;
   static constexpr int kSlots = kRows;
   static constexpr int kBufCols = kSlots * N;  // columns of one accumulator buffer
   static constexpr int kHalo = 130;                                   // input pixels of a row box (128 + 2)

@@ -385,14 +385,25 @@ __global__ void __launch_bounds__(256) composite_clear_kernel(const uint2* __res
   if (tile >= v.tiles_x * v.tiles_y) return;
   const uint2 rg = ranges[tile];
   if (rg.y > rg.x) return;
-  const int px = (tile % v.tiles_x) * TSX + (lane & 7), py = (tile / v.tiles_x) * TSY + (lane >> 3);
-  if (px >= v.W || py >= v.H) return;
-  const size_t pix = (size_t)py * v.W + px;
-  float z[C];
+  const int sx = (tile % v.tiles_x) * TSX, sy = (tile / v.tiles_x) * TSY;
+  const int px = sx + (lane & 7), py = sy + (lane >> 3);
+  if constexpr ((C * sizeof(TO)) % 16 == 0) {  // each tile row is one contiguous run: 16-B chunks across the lanes
+    const int npx = min(TSX, v.W - sx);
+    const int chunks = npx * C * (int)sizeof(TO) / 16;
+    for (int r = 0; r < TSY && sy + r < v.H; ++r) {
+      uint4* row = reinterpret_cast<uint4*>(Fout + ((size_t)(sy + r) * v.W + sx) * C);
+      for (int k = lane; k < chunks; k += 32) row[k] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    if (Aout && px < v.W && py < v.H) Aout[(size_t)py * v.W + px] = 0.0f;
+  } else {
+    if (px >= v.W || py >= v.H) return;
+    const size_t pix = (size_t)py * v.W + px;
+    float z[C];
 #pragma unroll
-  for (int c = 0; c < C; ++c) z[c] = 0.0f;
-  store_row<C>(Fout + pix * C, z);
-  if (Aout) Aout[pix] = 0.0f;
+    for (int c = 0; c < C; ++c) z[c] = 0.0f;
+    store_row<C>(Fout + pix * C, z);
+    if (Aout) Aout[pix] = 0.0f;
+  }
 }
 
 template <int C, typename TF, typename TO, int MODE>
@@ -581,7 +592,7 @@ void split_pass(art_ctx* ctx, const ViewParams& v, void* F, float* A, int mode, 
                ctx->d_vals, ctx->d_rec, ctx->d_rect, feat, v, ctx->cfg.tau, (TO*)F, A, ctx->d_status, ctx->d_part,
                sk);
     auto mfn = composite_merge_kernel<C, TO, kInterval>;
-    ART_LAUNCH(ctx, "composite_merge", mfn, 4 * ctx->num_sms, 32, 0, ctx->d_seg, ctx->d_multi, v, ctx->cfg.tau, (TO*)F,
+    ART_LAUNCH(ctx, "composite_merge", mfn, 32 * ctx->num_sms, 32, 0, ctx->d_seg, ctx->d_multi, v, ctx->cfg.tau, (TO*)F,
                A, ctx->d_status, ctx->d_part, sk);
   } else {
     auto kfn = composite_split_kernel<C, TF, TO, kPlain>;
@@ -589,7 +600,7 @@ void split_pass(art_ctx* ctx, const ViewParams& v, void* F, float* A, int mode, 
                ctx->d_keys, ctx->d_vals, ctx->d_rec, ctx->d_rect, feat, v, ctx->cfg.tau, (TO*)F, A,
                ctx->d_status, ctx->d_part, sk);
     auto mfn = composite_merge_kernel<C, TO, kPlain>;
-    ART_LAUNCH(ctx, "composite_merge", mfn, 4 * ctx->num_sms, 32, 0, ctx->d_seg, ctx->d_multi, v, ctx->cfg.tau, (TO*)F,
+    ART_LAUNCH(ctx, "composite_merge", mfn, 32 * ctx->num_sms, 32, 0, ctx->d_seg, ctx->d_multi, v, ctx->cfg.tau, (TO*)F,
                A, ctx->d_status, ctx->d_part, sk);
   }
 }
@@ -685,10 +696,11 @@ art_status launch_composite_skip(art_ctx* ctx, const ViewParams& v, void* F, int
 }
 
 int composite_blocks_per_sm(int C, int feat_bytes) {
-  // one-warp blocks, limited by the staged-feature ring and the 32-block cap
-  const int ring = std::max(1, std::min(16, 12288 / (NT * C * feat_bytes)));
-  const int smem = ring * NT * (C * feat_bytes + 8) + NT * (3 * 16 + 8) + 4 * kPropBins + 64;
-  return std::max(1, std::min(32, (227 * 1024) / smem));
+  // one-warp blocks, limited by shared memory (staged-feature ring, chunk
+  // geometry, double-buffered records) and by registers (12 blocks)
+  const int ring = std::max(1, std::min(16, 10240 / (NT * C * feat_bytes)));
+  const int smem = ring * NT * (C * feat_bytes + 8) + NT * (3 * 16 + 8) + 2 * NT * (64 + 8) + 4 * kPropBins + 64;
+  return std::max(1, std::min(12, (227 * 1024) / smem));
 }
 
 art_status launch_composite_labels(art_ctx* ctx, const ViewParams& v, float* labels, uint8_t* bins) {

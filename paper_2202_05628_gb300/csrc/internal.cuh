@@ -38,7 +38,9 @@ enum StatusWord {
   kStSortNext = 15,     // binning: next bucket to sort (work counter)
   kStSortBig = 16,      // binning: buckets sorted by a whole block
   kStSortBigNext = 17,  // binning: next such bucket (work counter)
-  kStWords = 18
+  kStScanTicket = 18,   // binning: blocks of the tile scan started (their order)
+  kStScanError = 19,    // binning: tile-scan blocks that timed out waiting for a predecessor
+  kStWords = 20
 };
 
 // Per-view camera, with host-precomputed ray frame.
@@ -129,6 +131,7 @@ struct art_ctx {
   uint32_t* d_tcount = nullptr;  // per tile instance count
   uint32_t* d_toff = nullptr;    // per tile bucket cursor
   uint32_t* d_sortlist = nullptr;  // tiles whose bucket needs sorting
+  unsigned long long* d_scan_state = nullptr;  // tile scan: per block aggregate and inclusive prefix words
   unsigned long long* d_status = nullptr;
   unsigned long long* h_status = nullptr;  // pinned
 
@@ -233,6 +236,7 @@ int launch_sort_bufs(art_ctx* ctx, uint32_t* k0, uint32_t* v0, uint32_t* k1, uin
 void launch_set_word(art_ctx* ctx, unsigned long long* p, unsigned long long value);
 size_t sort_hist_words(int64_t n);
 size_t scan_block_words(int64_t n);
+size_t tile_scan_state_words(int64_t ntiles);  // look-back words of the tile scan
 
 // ---- composite (composite.cu)
 art_status launch_composite(art_ctx* ctx, const ViewParams& v, void* F, int F_dtype, float* A,

@@ -115,8 +115,9 @@ __global__ void __launch_bounds__(256) lbs_kernel(int64_t n, int J, const float*
                                                   const float4* __restrict__ wts, const float* __restrict__ sigma,
                                                   float ox, float oy, float oz, float h, float4* __restrict__ rec,
                                                   float4* __restrict__ geo, unsigned long long* __restrict__ status) {
-  __shared__ float sG[kMaxJoints * 12];
-  for (int k = threadIdx.x; k < J * 12; k += blockDim.x) sG[k] = G[k];
+  __shared__ float4 sG[kMaxJoints * 3];  // G_j as three float4 rows
+  for (int k = threadIdx.x; k < J * 3; k += blockDim.x)
+    sG[k] = make_float4(G[4 * k], G[4 * k + 1], G[4 * k + 2], G[4 * k + 3]);
   __syncthreads();
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   bool degenerate = false;
@@ -133,10 +134,15 @@ __global__ void __launch_bounds__(256) lbs_kernel(int64_t n, int J, const float*
     for (int m = 0; m < 12; ++m) A[m] = 0.0f;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      int j = (jj >> (8 * k)) & 0xff;
-      const float* g = sG + 12 * j;
+      const int j = (jj >> (8 * k)) & 0xff;
 #pragma unroll
-      for (int m = 0; m < 12; ++m) A[m] = fmaf(wk[k], g[m], A[m]);
+      for (int m = 0; m < 3; ++m) {
+        const float4 g = sG[3 * j + m];
+        A[4 * m] = fmaf(wk[k], g.x, A[4 * m]);
+        A[4 * m + 1] = fmaf(wk[k], g.y, A[4 * m + 1]);
+        A[4 * m + 2] = fmaf(wk[k], g.z, A[4 * m + 2]);
+        A[4 * m + 3] = fmaf(wk[k], g.w, A[4 * m + 3]);
+      }
     }
     float a = A[0], b = A[1], cc = A[2], d = A[4], e = A[5], f = A[6], g = A[8], hh = A[9], k2 = A[10];
     float c00 = e * k2 - f * hh, c01 = f * g - d * k2, c02 = d * hh - e * g;
@@ -189,12 +195,27 @@ __global__ void __launch_bounds__(256) lbs_kernel(int64_t n, int J, const float*
       geo[4 * i + m] = out_geo[m];
     }
   }
-  unsigned bal = __ballot_sync(0xffffffffu, degenerate);
-  if ((threadIdx.x & 31) == 0 && bal) atomicAdd(status + kStDegenerate, (unsigned long long)__popc(bal));
-  // largest bounding radius of the pose (positive floats order as their bits)
+  // block totals: degenerate voxels and the largest bounding radius of the
+  // pose (positive floats order as their bits), one atomic each per block
+  __shared__ unsigned s_deg;
+  __shared__ unsigned s_rmax;
+  if (threadIdx.x == 0) {
+    s_deg = 0;
+    s_rmax = 0;
+  }
+  __syncthreads();
+  const unsigned bal = __ballot_sync(0xffffffffu, degenerate);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
-  if ((threadIdx.x & 31) == 0 && rmax > 0.0f) atomicMax(status + kStRmax, (unsigned long long)__float_as_uint(rmax));
+  if ((threadIdx.x & 31) == 0) {
+    if (bal) atomicAdd(&s_deg, (unsigned)__popc(bal));
+    if (rmax > 0.0f) atomicMax(&s_rmax, __float_as_uint(rmax));
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (s_deg) atomicAdd(status + kStDegenerate, (unsigned long long)s_deg);
+    if (s_rmax) atomicMax(status + kStRmax, (unsigned long long)s_rmax);
+  }
 }
 
 // Per voxel and view: projected-corner pixel rectangle (grown by kBboxPad),
