@@ -174,7 +174,7 @@ void free_all(art_ctx* ctx) {
                   ctx->d_shist, ctx->d_sbsum, ctx->d_gN, ctx->d_f8_scale, ctx->d_f8_amax, ctx->d_prop_img,
                   ctx->d_prop_f32, ctx->d_pose_bias, ctx->d_bins, ctx->d_thist, ctx->d_hbin, ctx->d_htau, ctx->d_fbq,
                   ctx->d_seg, ctx->d_items, ctx->d_multi, ctx->d_part, ctx->d_fbq2, ctx->d_tcount, ctx->d_toff,
-                  ctx->d_sortlist, ctx->d_scan_state};
+                  ctx->d_sortlist, ctx->d_scan_state, ctx->d_agroups};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& L : ctx->layers) {
@@ -223,6 +223,7 @@ art_status ensure_bin_buffers(art_ctx* ctx, int64_t ntiles) {
     if ((st = alloc(ctx, &ctx->d_toff, (size_t)ntiles, "tile offsets")) != ART_OK) return st;
     if ((st = alloc(ctx, &ctx->d_sortlist, (size_t)ntiles, "tile sort list")) != ART_OK) return st;
     if ((st = alloc(ctx, &ctx->d_scan_state, tile_scan_state_words(ntiles), "tile scan state")) != ART_OK) return st;
+    if ((st = alloc(ctx, &ctx->d_agroups, (size_t)(ntiles + 3) / 4, "active tile groups")) != ART_OK) return st;
     ctx->ranges_cap = ntiles;
   }
   return ART_OK;

@@ -235,36 +235,6 @@ __device__ __forceinline__ uint32_t rect_tile(const ViewParams& v, int tx0, int 
   return (uint32_t)((ty0 + (int)(k / (uint32_t)w)) * v.tiles_x + tx0 + (int)(k % (uint32_t)w));
 }
 
-// Per voxel: one count for every tile its pixel rectangle covers.  Lanes of a
-// warp that hit the same tile in the same step add together.
-// Block 0 also clears the tile scan's look-back words and block ticket.
-__global__ void __launch_bounds__(256) tile_count_kernel(int64_t n, const uint32_t* __restrict__ cnt,
-                                                         const short4* __restrict__ rect, ViewParams v,
-                                                         uint32_t* __restrict__ tcount,
-                                                         unsigned long long* __restrict__ scan_state, int scan_words,
-                                                         unsigned long long* __restrict__ status) {
-  if (blockIdx.x == 0) {
-    for (int k = threadIdx.x; k < scan_words; k += blockDim.x) scan_state[k] = 0ull;
-    if (threadIdx.x == 0) status[kStScanTicket] = 0ull;
-  }
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int lane = threadIdx.x & 31;
-  uint32_t c = 0;
-  int tx0 = 0, ty0 = 0, w = 1;
-  if (i < n && (c = cnt[i]) != 0) {
-    const short4 r = rect[i];
-    tx0 = r.x >> v.tile_wl;
-    ty0 = r.y >> v.tile_hl;
-    w = (r.z >> v.tile_wl) - tx0 + 1;
-  }
-  const uint32_t steps = __reduce_max_sync(0xFFFFFFFFu, c);
-  for (uint32_t k = 0; k < steps; ++k) {
-    const uint32_t tile = k < c ? rect_tile(v, tx0, ty0, w, k) : 0xFFFFFFFFu;
-    const unsigned grp = __match_any_sync(0xFFFFFFFFu, tile);
-    if (tile != 0xFFFFFFFFu && lane == __ffs(grp) - 1) atomicAdd(tcount + tile, (uint32_t)__popc(grp));
-  }
-}
-
 // Single-pass tile scan with decoupled look-back.  Blocks take consecutive
 // runs of kTileScanBlock tiles in the order they start (a ticket), so every
 // predecessor of a block is already running.  A block publishes its totals
@@ -272,7 +242,7 @@ __global__ void __launch_bounds__(256) tile_count_kernel(int64_t n, const uint32
 // its warp 0 looks back over up to 32 predecessors per round: the nearest one
 // that published its inclusive prefix ends the walk, the others contribute
 // their totals.  Words carry their value shifted left by one with bit 0 set
-// once written (zeroed by tile_count_kernel).  A poll that does not end within
+// once written (zeroed by the projection kernel).  A poll that does not end within
 // kScanSpin tries counts the block in kStScanError and reads zero.
 //
 // Outputs: bucket cursors and tile ranges (clamped to the capacity), the
@@ -296,6 +266,7 @@ __global__ void __launch_bounds__(kTileScanThreads) tile_scan_kernel(int ntiles,
                                                                      uint2* __restrict__ ranges,
                                                                      uint32_t* __restrict__ sort_list,
                                                                      ScanWords* __restrict__ sw,
+                                                                     uint32_t* __restrict__ agroups,
                                                                      unsigned long long* __restrict__ status) {
   __shared__ unsigned long long s_b, s_pi, s_pl;
   if (threadIdx.x == 0) s_b = atomicAdd(status + kStScanTicket, 1ull);
@@ -319,6 +290,15 @@ __global__ void __launch_bounds__(kTileScanThreads) tile_scan_kernel(int ntiles,
   for (int k = 0; k < kTileScanItems; ++k) {
     s += c[k];
     lists += c[k] > (uint32_t)kWarpSortCap ? 0x10000u : (c[k] > 1u ? 1u : 0u);
+  }
+  {  // this thread's four tiles are one group: listed when any has instances
+    static_assert(kTileScanItems == 4, "one group of four tiles per thread");
+    const bool act = s > 0;
+    const unsigned am = __ballot_sync(0xffffffffu, act);
+    unsigned long long g0 = 0;
+    if ((threadIdx.x & 31) == 0 && am) g0 = atomicAdd(status + kStActiveGroups, (unsigned long long)__popc(am));
+    g0 = __shfl_sync(0xffffffffu, g0, 0);
+    if (act) agroups[g0 + __popc(am & ((1u << (threadIdx.x & 31)) - 1u))] = (uint32_t)(base / 4);
   }
   uint32_t tot = 0, lt = 0;
   const uint32_t ps = block_exclusive_scan(s, &tot);
@@ -711,12 +691,9 @@ void launch_bin(art_ctx* ctx, const ViewParams& v, const uint32_t* hbin, const f
     attr = true;
   }
   const int nsb = (ntiles + kTileScanBlock - 1) / kTileScanBlock;
-  cudaMemsetAsync(ctx->d_tcount, 0, sizeof(uint32_t) * (size_t)ntiles, ctx->stream);
-  ART_LAUNCH(ctx, "bin_count", tile_count_kernel, vb, 256, 0, n, ctx->d_cnt, ctx->d_rect, v, ctx->d_tcount,
-             ctx->d_scan_state, 4 * nsb, ctx->d_status);
   ART_LAUNCH(ctx, "bin_scan", tile_scan_kernel, nsb, kTileScanThreads, 0, ntiles, ctx->d_tcount, ctx->inst_cap,
              ctx->d_toff, ctx->d_ranges, ctx->d_sortlist, reinterpret_cast<ScanWords*>(ctx->d_scan_state),
-             ctx->d_status);
+             ctx->d_agroups, ctx->d_status);
   ART_LAUNCH(ctx, "bin_emit", bucket_emit_kernel, vb, 256, 0, n, ctx->d_cnt, ctx->d_rect, ctx->d_q, v, ctx->inst_cap,
              ctx->d_toff, ctx->d_keys, ctx->d_vals, ctx->d_status, hbin, htau, thist);
   ART_LAUNCH(ctx, "tile_sort", tile_sort_kernel, 2 * ctx->num_sms, kTileSortThreads, kTileSortSmem * 8, ctx->d_ranges,

@@ -467,14 +467,20 @@ __global__ void __launch_bounds__(32) composite_merge_kernel(const uint2* __rest
     // the segments this pixel composites (front to back until the stop) and the stop check
     float T = 1.0f;
     uint32_t kend = sgt.y;
-    bool redo = false;
-    for (uint32_t k = 0; k < sgt.y; ++k) {
-      const float Tk = pbase[(size_t)k * (C + 1) * 32 + C * 32 + lane];
-      if (T < 1.0f && T * Tk < tau) redo = true;  // the stop falls inside a later segment
-      T *= Tk;
-      if (T < tau) {
-        kend = k + 1;
-        break;
+    bool redo = false, stopped = false;
+    for (uint32_t k0 = 0; k0 < sgt.y && !stopped; k0 += 8) {  // eight segments' loads in flight
+      float tk[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) tk[j] = k0 + j < sgt.y ? pbase[(size_t)(k0 + j) * (C + 1) * 32 + C * 32 + lane] : 1.0f;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        if (stopped || k0 + j >= sgt.y) continue;
+        if (T < 1.0f && T * tk[j] < tau) redo = true;  // the stop falls inside a later segment
+        T *= tk[j];
+        if (T < tau) {
+          kend = k0 + j + 1;
+          stopped = true;
+        }
       }
     }
     // F = sum_k (T_0 ... T_{k-1}) F_k over this warp's channels; loads of two
@@ -483,28 +489,22 @@ __global__ void __launch_bounds__(32) composite_merge_kernel(const uint2* __rest
 #pragma unroll
     for (int c = 0; c < CG; ++c) acc[c] = 0.0f;
     float P = 1.0f;
-    uint32_t k = 0;
-    for (; k + 1 < kend; k += 2) {
-      const float* p0 = pbase + (size_t)k * (C + 1) * 32;
-      const float* p1 = p0 + (C + 1) * 32;
-      float f0[CG], f1[CG];
+    for (uint32_t k0 = 0; k0 < kend; k0 += 4) {  // four segments' loads in flight
+      float f[4][CG], tq[4];
 #pragma unroll
-      for (int c = 0; c < CG; ++c) {
-        f0[c] = p0[(grp * CG + c) * 32 + lane];
-        f1[c] = p1[(grp * CG + c) * 32 + lane];
+      for (int j = 0; j < 4; ++j) {
+        const bool in = k0 + j < kend;
+        const float* pj = pbase + (size_t)(k0 + j) * (C + 1) * 32;
+#pragma unroll
+        for (int c = 0; c < CG; ++c) f[j][c] = in ? pj[(grp * CG + c) * 32 + lane] : 0.0f;
+        tq[j] = in ? pj[C * 32 + lane] : 1.0f;
       }
-      const float T0 = p0[C * 32 + lane], T1 = p1[C * 32 + lane];
 #pragma unroll
-      for (int c = 0; c < CG; ++c) acc[c] = fmaf(P, f0[c], acc[c]);
-      P *= T0;
+      for (int j = 0; j < 4; ++j) {
 #pragma unroll
-      for (int c = 0; c < CG; ++c) acc[c] = fmaf(P, f1[c], acc[c]);
-      P *= T1;
-    }
-    if (k < kend) {
-      const float* p0 = pbase + (size_t)k * (C + 1) * 32;
-#pragma unroll
-      for (int c = 0; c < CG; ++c) acc[c] = fmaf(P, p0[(grp * CG + c) * 32 + lane], acc[c]);
+        for (int c = 0; c < CG; ++c) acc[c] = fmaf(P, f[j][c], acc[c]);
+        P *= tq[j];
+      }
     }
     bool fail = false;
     if constexpr (MODE == kInterval) {  // coarse check of the lost mass over the tile's union interval

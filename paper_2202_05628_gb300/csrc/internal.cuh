@@ -40,7 +40,8 @@ enum StatusWord {
   kStSortBigNext = 17,  // binning: next such bucket (work counter)
   kStScanTicket = 18,   // binning: blocks of the tile scan started (their order)
   kStScanError = 19,    // binning: tile-scan blocks that timed out waiting for a predecessor
-  kStWords = 20
+  kStActiveGroups = 20, // binning: groups of four consecutive tiles with instances (listed in d_agroups)
+  kStWords = 21
 };
 
 // Per-view camera, with host-precomputed ray frame.
@@ -132,6 +133,7 @@ struct art_ctx {
   uint32_t* d_toff = nullptr;    // per tile bucket cursor
   uint32_t* d_sortlist = nullptr;  // tiles whose bucket needs sorting
   unsigned long long* d_scan_state = nullptr;  // tile scan: per block aggregate and inclusive prefix words
+  uint32_t* d_agroups = nullptr;  // groups of four consecutive tiles with instances (unordered)
   unsigned long long* d_status = nullptr;
   unsigned long long* h_status = nullptr;  // pinned
 
@@ -215,15 +217,17 @@ void prof_end(art_ctx* ctx);
 void launch_fk(art_ctx* ctx);
 void launch_lbs(art_ctx* ctx);
 // With hbin / htau set, also the per-voxel depth-bin range and optical-depth
-// bound of the coarse check (64 bins over [znear, zfar]).
+// bound of the coarse check (64 bins over [znear, zfar]).  Also counts each
+// tile's instances and resets the tile scan: launch_bin follows it.
 void launch_project(art_ctx* ctx, const ViewParams& v, uint32_t* hbin = nullptr, float* htau = nullptr);
 
 // ---- binning and sorting (binsort.cu)
 // With thist set (zeroed [tiles][64]), also accumulate the coarse optical-depth
 // bound of every instance into its tile's depth bins.
-// Binning of the projected voxels: per-tile instance counts, their scan (the
-// tile ranges), the scatter of every instance into its tile's bucket and the
-// sort of each bucket by (depth quantum, voxel id).  With thist set, the
+// Binning of the projected voxels (after launch_project, which counts the
+// instances of every tile): the scan of the counts (the tile ranges), the
+// scatter of every instance into its tile's bucket and the sort of each
+// bucket by (depth quantum, voxel id).  With thist set, the
 // scatter also adds each voxel's optical-depth bound htau to the depth bins
 // hbin of each of its tiles (thist: zeroed [tiles][64]; the coarse check of
 // the learned skip).

@@ -222,12 +222,16 @@ __global__ void __launch_bounds__(256) lbs_kernel(int64_t n, int J, const float*
 // screen-tile count, and the depth key: a floor-quantised lower bound of the
 // distance from the camera centre to any point of the voxel (|cw - o| - r),
 // which bounds the ray parameter t of any entry point from below.
-__global__ void __launch_bounds__(256) project_kernel(int64_t n, const float4* __restrict__ geo, ViewParams v,
-                                                      short4* __restrict__ rect, uint32_t* __restrict__ q,
-                                                      uint32_t* __restrict__ cnt, const float* __restrict__ sigma,
-                                                      uint32_t* __restrict__ hbin, float* __restrict__ htau) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+//
+// Each voxel then adds one to the instance count of every tile its rectangle
+// covers (lanes of a warp that hit the same tile in the same step add
+// together), the first step of the binning; block 0 also clears the tile
+// scan's look-back words and its block ticket and the active-group count.
+__device__ __forceinline__ void project_voxel(int64_t i, const float4* __restrict__ geo, const ViewParams& v,
+                                              short4* __restrict__ rect, uint32_t* __restrict__ q,
+                                              uint32_t* __restrict__ cnt, const float* __restrict__ sigma,
+                                              uint32_t* __restrict__ hbin, float* __restrict__ htau, short4& rc,
+                                              uint32_t& c) {
   float4 g0 = geo[4 * i], g1 = geo[4 * i + 1], g2 = geo[4 * i + 2], g3 = geo[4 * i + 3];
   short4 empty = make_short4(1, 1, 0, 0);
   if (!(g0.w >= 0.0f)) {
@@ -276,8 +280,10 @@ __global__ void __launch_bounds__(256) project_kernel(int64_t n, const float4* _
     q[i] = 0;
     return;
   }
-  rect[i] = make_short4((short)x0, (short)y0, (short)x1, (short)y1);
-  cnt[i] = (uint32_t)(((x1 >> v.tile_wl) - (x0 >> v.tile_wl) + 1) * ((y1 >> v.tile_hl) - (y0 >> v.tile_hl) + 1));
+  rc = make_short4((short)x0, (short)y0, (short)x1, (short)y1);
+  c = (uint32_t)(((x1 >> v.tile_wl) - (x0 >> v.tile_wl) + 1) * ((y1 >> v.tile_hl) - (y0 >> v.tile_hl) + 1));
+  rect[i] = rc;
+  cnt[i] = c;
   float rel = (fmaxf(dmin, v.znear) - v.znear) * v.dscale;
   float qmax = (float)((1u << v.depth_bits) - 1u);
   float qq = fminf(fmaxf(floorf(rel) - 1.0f, 0.0f), qmax);
@@ -289,6 +295,35 @@ __global__ void __launch_bounds__(256) project_kernel(int64_t n, const float4* _
     const int b1 = min(max((int)floorf((dmax + kHistPad - v.znear) * bs), 0), kPropBins - 1);
     hbin[i] = (uint32_t)b0 | ((uint32_t)b1 << 8);
     htau[i] = sigma[i] * (dmax - dmin) * (1.0f + kHistSlack);
+  }
+}
+
+__global__ void __launch_bounds__(256) project_kernel(int64_t n, const float4* __restrict__ geo, ViewParams v,
+                                                      short4* __restrict__ rect, uint32_t* __restrict__ q,
+                                                      uint32_t* __restrict__ cnt, const float* __restrict__ sigma,
+                                                      uint32_t* __restrict__ hbin, float* __restrict__ htau,
+                                                      uint32_t* __restrict__ tcount,
+                                                      unsigned long long* __restrict__ scan_state, int scan_words,
+                                                      unsigned long long* __restrict__ status) {
+  if (blockIdx.x == 0) {
+    for (int k = threadIdx.x; k < scan_words; k += blockDim.x) scan_state[k] = 0ull;
+    if (threadIdx.x == 0) {
+      status[kStScanTicket] = 0ull;
+      status[kStActiveGroups] = 0ull;
+    }
+  }
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  short4 rc = make_short4(1, 1, 0, 0);
+  uint32_t c = 0;
+  if (i < n) project_voxel(i, geo, v, rect, q, cnt, sigma, hbin, htau, rc, c);
+  const int lane = threadIdx.x & 31;
+  const int tx0 = rc.x >> v.tile_wl, ty0 = rc.y >> v.tile_hl, w = (rc.z >> v.tile_wl) - tx0 + 1;
+  const uint32_t steps = __reduce_max_sync(0xFFFFFFFFu, c);
+  for (uint32_t k = 0; k < steps; ++k) {
+    const uint32_t tile =
+        k < c ? (uint32_t)((ty0 + (int)(k / (uint32_t)w)) * v.tiles_x + tx0 + (int)(k % (uint32_t)w)) : 0xFFFFFFFFu;
+    const unsigned grp = __match_any_sync(0xFFFFFFFFu, tile);
+    if (tile != 0xFFFFFFFFu && lane == __ffs(grp) - 1) atomicAdd(tcount + tile, (uint32_t)__popc(grp));
   }
 }
 
@@ -307,8 +342,11 @@ void launch_lbs(art_ctx* ctx) {
 void launch_project(art_ctx* ctx, const ViewParams& v, uint32_t* hbin, float* htau) {
   int64_t n = ctx->n;
   unsigned grid = (unsigned)((n + 255) / 256);
+  const int ntiles = v.tiles_x * v.tiles_y;
+  cudaMemsetAsync(ctx->d_tcount, 0, sizeof(uint32_t) * (size_t)ntiles, ctx->stream);
   ART_LAUNCH(ctx, "project", project_kernel, grid, 256, 0, n, ctx->d_geo, v, ctx->d_rect, ctx->d_q, ctx->d_cnt,
-             ctx->d_sigma, hbin, htau);
+             ctx->d_sigma, hbin, htau, ctx->d_tcount, ctx->d_scan_state, (int)tile_scan_state_words(ntiles),
+             ctx->d_status);
 }
 
 }  // namespace art

@@ -50,7 +50,9 @@ struct PropParams {
   ViewParams v;
   const uint2* ranges;     // per tile [start, end)
   int ngroups;             // groups of four screen tiles
-  int active_only;
+  int active_only;         // only the groups listed in agroups (count: *n_active)
+  const uint32_t* agroups;
+  const unsigned long long* n_active;
   uint8_t* bins;           // [H][W][2] or null
   float* logits;           // [H][W][128] or null
   unsigned long long* err;
@@ -62,13 +64,23 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 }
 
 // b0 + W0[:, :72] x, x = the current pose's axis-angles rounded to BF16; FP32.
-__global__ void pose_bias_kernel(const float* __restrict__ f32, const float* __restrict__ pose, float* __restrict__ out) {
-  const int j = threadIdx.x;
-  if (j >= 64) return;
-  float acc = f32[64 * kPoseIn + j];
-  for (int k = 0; k < kPoseIn; ++k)
-    acc = fmaf(f32[j * kPoseIn + k], __bfloat162float(__float2bfloat16_rn(pose[k])), acc);
-  out[j] = acc;
+// 256 threads: the weights and the pose come in with coalesced loads, four
+// threads share an output (k = q, q + 4, ...), summed in a fixed order.
+__global__ void __launch_bounds__(256) pose_bias_kernel(const float* __restrict__ f32, const float* __restrict__ pose,
+                                                        float* __restrict__ out) {
+  __shared__ float sx[kPoseIn];
+  const int j = threadIdx.x >> 2, q = threadIdx.x & 3;
+  float w[kPoseIn / 4];  // this thread's weights, loaded together
+#pragma unroll
+  for (int i = 0; i < kPoseIn / 4; ++i) w[i] = f32[j * kPoseIn + q + 4 * i];
+  if (threadIdx.x < kPoseIn) sx[threadIdx.x] = __bfloat162float(__float2bfloat16_rn(pose[threadIdx.x]));
+  __syncthreads();
+  float acc = 0.0f;
+#pragma unroll
+  for (int i = 0; i < kPoseIn / 4; ++i) acc = fmaf(w[i], sx[q + 4 * i], acc);
+  acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+  acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+  if (q == 0) out[j] = f32[64 * kPoseIn + j] + acc;
 }
 
 __global__ void __launch_bounds__(128) proposal_kernel(PropParams p) {
@@ -82,8 +94,12 @@ __global__ void __launch_bounds__(128) proposal_kernel(PropParams p) {
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int n_items = p.active_only ? (int)*p.n_active : p.ngroups;
+  if ((int)blockIdx.x >= n_items) return;  // no group for this CTA
 
-  for (int i = tid; i < kImgBytes / 16; i += 128) reinterpret_cast<uint4*>(s_img)[i] = p.img[i];
+  // the weight image: all copies in flight at once
+  for (int i = tid; i < kImgBytes / 16; i += 128) cp_async16(s_img + 16 * i, p.img + i);
+  cp_async_commit();
   if (tid < 64) s_bias[tid] = p.pose_bias[tid];
   for (int i = tid; i < 320; i += 128) s_bias[64 + i] = p.f32[64 * kPoseIn + 64 + i];
   if (tid == 0) {
@@ -92,6 +108,7 @@ __global__ void __launch_bounds__(128) proposal_kernel(PropParams p) {
     fence_mbar_init();
   }
   if (warp == 0) tmem_alloc(tmem_slot, 128);
+  cp_async_wait<0>();
   fence_proxy_async_smem();
   tc_fence_before();
   __syncthreads();
@@ -104,7 +121,8 @@ __global__ void __launch_bounds__(128) proposal_kernel(PropParams p) {
   uint32_t phase = 0;
   bool failed = false;
 
-  for (int g = blockIdx.x; g < p.ngroups && !failed; g += gridDim.x) {
+  for (int it = blockIdx.x; it < n_items && !failed; it += gridDim.x) {
+    const int g = p.active_only ? (int)p.agroups[it] : it;
     const int tile = 4 * g + warp;
     bool act = tile < ntiles;
     if (act && p.active_only) {
@@ -261,7 +279,7 @@ art_status load_proposal(art_ctx* ctx, const float* params) {
 }
 
 void launch_pose_bias(art_ctx* ctx) {
-  ART_LAUNCH(ctx, "proposal_pose_bias", pose_bias_kernel, 1, 64, 0, ctx->d_prop_f32, ctx->d_pose, ctx->d_pose_bias);
+  ART_LAUNCH(ctx, "proposal_pose_bias", pose_bias_kernel, 1, 256, 0, ctx->d_prop_f32, ctx->d_pose, ctx->d_pose_bias);
 }
 
 art_status launch_proposal(art_ctx* ctx, const ViewParams& v, uint8_t* bins, float* logits, bool active_only) {
@@ -280,6 +298,8 @@ art_status launch_proposal(art_ctx* ctx, const ViewParams& v, uint8_t* bins, flo
   const int ntiles = v.tiles_x * v.tiles_y;
   p.ngroups = (ntiles + 3) / 4;
   p.active_only = active_only ? 1 : 0;
+  p.agroups = ctx->d_agroups;
+  p.n_active = ctx->d_status + kStActiveGroups;
   p.bins = bins;
   p.logits = logits;
   p.err = ctx->d_status + kStTcError;
