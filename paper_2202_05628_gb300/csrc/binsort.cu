@@ -225,7 +225,8 @@ constexpr long long kScanSpin = 1 << 22;  // look-back polls before a block give
 constexpr int kTileSortThreads = 512;
 constexpr int kTileSortWarps = kTileSortThreads / 32;
 constexpr int kSortPer = 16;             // bucket entries per thread held in registers
-constexpr int kTileSortSmem = kTileSortThreads * kSortPer;  // buckets staged in shared memory (8192)
+constexpr int kSortRegs = kTileSortThreads * kSortPer;  // buckets held in registers (8192)
+constexpr int kTileSortSmem = 9216;                      // buckets staged in shared memory (72 KB)
 constexpr int kWarpSortCap = 256;        // buckets up to this size: one warp each
 constexpr int kSortBins = 4096;          // depth bins of a block-sorted bucket
 constexpr int kRankMax = 64;             // bins up to this size: entries ranked by counting
@@ -498,8 +499,8 @@ __device__ __forceinline__ unsigned long long bucket_entry(uint32_t key, uint32_
 
 // Block-wide sort of one bucket of n >= 2 entries (keys, vals: the bucket)
 // by (depth quantum, voxel id) through the staging array S (shared memory
-// for n <= kTileSortSmem, the entries then held in registers; else the
-// bucket's own stretch of a global scratch).  A counting sort on the depth
+// for n <= kTileSortSmem, else the bucket's own stretch of a global scratch;
+// the entries are held in registers for n <= kSortRegs).  A counting sort on the depth
 // bin (q - lo) >> shift, with kSortBins bins over the bucket's quanta
 // [lo, hi], stages the entries bin by bin; an entry of a bin of up to
 // kRankMax entries then goes straight to its place, the number of smaller
@@ -509,7 +510,7 @@ __device__ void block_sort_bucket(uint32_t* __restrict__ keys, uint32_t* __restr
   __shared__ uint32_t s_start[kSortBins], s_cur[kSortBins];
   __shared__ uint32_t s_lo[kTileSortWarps], s_hi[kTileSortWarps];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const bool regs = n <= (uint32_t)kTileSortSmem;
+  const bool regs = n <= (uint32_t)kSortRegs;
   uint32_t kq[kSortPer], kv[kSortPer];
   uint32_t lo = 0xFFFFFFFFu, hi = 0;
   if (regs) {
