@@ -224,7 +224,7 @@ def roofline(kt, stats, peaks, form, n_vox, C, frames):
         else:
             peak, bound, note = bf16, "tensor", "measured sustained BF16"
         # DRAM bytes per launch of the BF16 convolutions, from one ncu capture of a frame's 14 launches
-        # (profiles/conv_unet_1024.md: 931.6 MB cold-cache reads + writes over the 14 launches)
+        # DRAM reads + writes of the 14 launches of one frame from an ncu capture (cold cache): 931.6 MB
         traffic = 931.6e6 / 14 if net == "bf16" else None
         out.update(bound=bound, achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak, traffic=traffic, peak_is=note)
     else:

@@ -25,7 +25,7 @@ convolution primitives.  Every function follows a passage of the paper
   is the early-stop rule of Sec. 3.1).
 
 Pins: each of these is checked in ``tests/test_oracle_pins.py`` against
-closed forms, brute force, invariants and library routines (see DESIGN.md).
+closed forms, brute force, invariants and library routines.
 """
 from __future__ import annotations
 

@@ -22,7 +22,7 @@
  *     densities and the blended transforms, and of LBS with respect to the
  *     skinning weights (project addition; the paper trains end to end).
  *
- * Readings where the paper is silent or garbled (listed in the design doc):
+ * Readings where the paper is silent or garbled:
  *   - T_i uses the exclusive sum j < i (Eq. 6 prints j <= i; with j < i the
  *     accumulated alpha equals 1 - T_final, which is how the coarse opacity
  *     map is defined).
