@@ -116,6 +116,8 @@ __global__ void __launch_bounds__(256) lbs_kernel(int64_t n, int J, const float*
                                                   float ox, float oy, float oz, float h, float4* __restrict__ rec,
                                                   float4* __restrict__ geo, unsigned long long* __restrict__ status) {
   __shared__ float4 sG[kMaxJoints * 3];  // G_j as three float4 rows
+  __shared__ float4 s_out[2][8][32 * 4];  // per warp: the 32 voxels' records and bounds
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int k = threadIdx.x; k < J * 3; k += blockDim.x)
     sG[k] = make_float4(G[4 * k], G[4 * k + 1], G[4 * k + 2], G[4 * k + 3]);
   __syncthreads();
@@ -189,10 +191,23 @@ __global__ void __launch_bounds__(256) lbs_kernel(int64_t n, int J, const float*
       out_geo[2] = make_float4(ay[0], ay[1], ay[2], 0.f);
       out_geo[3] = make_float4(az[0], az[1], az[2], 0.f);
     }
+    // (written below through shared memory, coalesced per warp)
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-      rec[4 * i + m] = out_rec[m];
-      geo[4 * i + m] = out_geo[m];
+      s_out[0][warp][lane * 4 + (m ^ ((lane >> 1) & 3))] = out_rec[m];
+      s_out[1][warp][lane * 4 + (m ^ ((lane >> 1) & 3))] = out_geo[m];
+    }
+  }
+  __syncwarp();
+  {  // float4 o of the warp's 32 records: voxel o / 4, row o % 4 (rows stored XOR-swizzled)
+    const int64_t w0 = (int64_t)blockIdx.x * blockDim.x + warp * 32;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int o = m * 32 + lane, vv = o >> 2, slot = vv * 4 + ((o & 3) ^ ((vv >> 1) & 3));
+      if (w0 + vv < n) {
+        rec[4 * w0 + o] = s_out[0][warp][slot];
+        geo[4 * w0 + o] = s_out[1][warp][slot];
+      }
     }
   }
   // block totals: degenerate voxels and the largest bounding radius of the
