@@ -226,7 +226,7 @@ constexpr int kTileSortThreads = 512;
 constexpr int kTileSortWarps = kTileSortThreads / 32;
 constexpr int kSortPer = 16;             // bucket entries per thread held in registers
 constexpr int kSortRegs = kTileSortThreads * kSortPer;  // buckets held in registers (8192)
-constexpr int kTileSortSmem = 9216;                      // buckets staged in shared memory (72 KB)
+constexpr int kTileSortSmem = kSortRegs;                 // ... and staged in shared memory (64 KB)
 constexpr int kWarpSortCap = 256;        // buckets up to this size: one warp each
 constexpr int kSortBins = 4096;          // depth bins of a block-sorted bucket
 constexpr int kRankMax = 64;             // bins up to this size: entries ranked by counting

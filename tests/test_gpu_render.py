@@ -40,6 +40,44 @@ def test_fk_and_lbs_match_oracle():
     np.testing.assert_array_equal(rec[:, 3, 0], sc.octree.density)
 
 
+TS, TSY = 8, 4  # screen tile
+
+
+def _check_tile_order(r, n, cam):
+    """The instance list is exactly the stable sort of the (tile << depth_bits
+    | depth quantum, voxel id) pairs emitted in voxel order from the rectangles
+    and quanta the projection recorded, and the tile ranges delimit it.
+    Returns keys, vals, depth_bits and the tile counts."""
+    st = r.sync_status()
+    keys = r.debug_buffer(5, np.uint32)
+    vals = r.debug_buffer(6, np.uint32)
+    assert st["instances"] == len(keys) and st["overflow_inst"] == 0
+    rect = r.debug_buffer(3, np.int16).reshape(-1, 4).astype(np.int64)
+    q = r.debug_buffer(4, np.uint32).astype(np.uint64)
+    tw, th = (cam.W + TS - 1) // TS, (cam.H + TSY - 1) // TSY
+    tb = max(1, int(np.ceil(np.log2(tw * th))))
+    db = min(32 - tb, 20)
+    vis = np.nonzero((rect[:, 0] <= rect[:, 2]) & (rect[:, 1] <= rect[:, 3]))[0]
+    tx0, ty0 = rect[vis, 0] // TS, rect[vis, 1] // TSY
+    nx, ny = rect[vis, 2] // TS - tx0 + 1, rect[vis, 3] // TSY - ty0 + 1
+    per = nx * ny  # instances of each visible voxel, emitted row by row
+    idx = np.repeat(np.arange(len(vis)), per)
+    k = np.arange(per.sum()) - np.repeat(np.cumsum(per) - per, per)
+    t = ((ty0[idx] + k // nx[idx]) * tw + tx0[idx] + k % nx[idx]).astype(np.uint64)
+    ek = (t << np.uint64(db)) | q[vis[idx]]
+    ev = vis[idx].astype(np.uint64)
+    order = np.lexsort((ev, ek))
+    np.testing.assert_array_equal(keys, ek[order].astype(np.uint32))
+    np.testing.assert_array_equal(vals, ev[order].astype(np.uint32))
+    rng_ = r.debug_buffer(7, np.uint32).reshape(-1, 2)[: tw * th]
+    tiles = (keys >> db).astype(np.int64)
+    counts = np.bincount(tiles, minlength=tw * th)
+    starts = np.concatenate([[0], np.cumsum(counts)[:-1]])
+    np.testing.assert_array_equal(rng_[:, 0], starts)
+    np.testing.assert_array_equal(rng_[:, 1], starts + counts)
+    return keys, vals, db, counts
+
+
 @pytest.mark.parametrize("az,pose_seed", [(0.0, 1), (135.0, 2)])
 def test_tile_lists_sorted_and_cover_oracle(az, pose_seed):
     sc, cam, pose = tiny_setup(az=az, pose_seed=pose_seed)
@@ -47,30 +85,9 @@ def test_tile_lists_sorted_and_cover_oracle(az, pose_seed):
     set_pose(r, pose)
     set_cam(r, 0, cam)
     render_maps(r, 0, cam, sc.octree.C)
-    st = r.sync_status()
-    keys = r.debug_buffer(5, np.uint32)
-    vals = r.debug_buffer(6, np.uint32)
-    assert st["instances"] == len(keys) and st["overflow_inst"] == 0
     # 1. the sort: exactly the stable sort of the emitted (key, voxel) pairs
-    rect = r.debug_buffer(3, np.int16).reshape(-1, 4)
-    q = r.debug_buffer(4, np.uint32)
-    TS, TSY = 8, 4
+    keys, vals, db, _ = _check_tile_order(r, sc.octree.n, cam)
     tw, th = (cam.W + TS - 1) // TS, (cam.H + TSY - 1) // TSY
-    tb = max(1, int(np.ceil(np.log2(tw * th))))
-    db = min(32 - tb, 20)
-    ek, ev = [], []
-    for i in range(sc.octree.n):
-        x0, y0, x1, y1 = rect[i]
-        if x0 > x1 or y0 > y1:
-            continue
-        for ty in range(y0 // TSY, y1 // TSY + 1):
-            for tx in range(x0 // TS, x1 // TS + 1):
-                ek.append(((ty * tw + tx) << db) | int(q[i]))
-                ev.append(i)
-    ek, ev = np.array(ek, np.uint64), np.array(ev, np.uint64)
-    order = np.lexsort((ev, ek))
-    np.testing.assert_array_equal(keys, ek[order].astype(np.uint32))
-    np.testing.assert_array_equal(vals, ev[order].astype(np.uint32))
     # 2. the tiles: a superset of the oracle's coverage, extras only at bbox edges
     _, A_or, _ = oracle.pose_transforms(sc, pose)
     ot, ov = oracle.tile_pairs(sc.octree, A_or, cam, TS, TSY)
@@ -85,12 +102,25 @@ def test_tile_lists_sorted_and_cover_oracle(az, pose_seed):
         ys = np.arange(ty * TSY, min(ty * TSY + TSY, cam.H)) + 0.5
         e = 1e-2
         assert ok and np.any((xs >= u0 - e) & (xs <= u1 + e)) and np.any((ys >= v0 - e) & (ys <= v1 + e))
-    # 3. tile ranges
-    rng_ = r.debug_buffer(7, np.uint32).reshape(-1, 2)[: tw * th]
-    tiles = keys >> db
-    for t in np.unique(tiles):
-        s, e = rng_[t]
-        assert np.all(tiles[s:e] == t) and (s == 0 or tiles[s - 1] != t) and (e == len(tiles) or tiles[e] != t)
+
+
+# Views chosen so that the binning takes each of its paths: the ~20k-voxel
+# scene at 512^2 (8192 tiles: a tile scan of eight blocks chained by
+# look-back; buckets of a few entries, warp sort, and of hundreds, block
+# sort with the entries in registers), and the 1M-voxel scene at 1024^2
+# seen from the side (buckets of up to ~8.6k entries: staged in global
+# memory past 8192).
+@pytest.mark.parametrize("preset,res,az,min_bucket", [("tiny", 512, 60.0, 257), ("paper", 1024, 90.0, 8193)])
+def test_bucket_sort_regimes(preset, res, az, min_bucket):
+    sc = sg.preset(preset)
+    cam = sg.orbit_camera(sc.centroid, res, res, az_deg=az)
+    pose = sg.walk_pose(5, 60)
+    r = renderer(sc)
+    set_pose(r, pose)
+    set_cam(r, 0, cam)
+    render_maps(r, 0, cam, sc.octree.C)
+    _, _, _, counts = _check_tile_order(r, sc.octree.n, cam)
+    assert counts.max() >= min_bucket  # the regime this view is meant to reach
 
 
 @pytest.mark.parametrize("az,pose_seed", [(0.0, 1), (80.0, 4), (215.0, 7)])
