@@ -212,11 +212,14 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(
 
 // ---------------------------------------------------- binning by tile buckets
 //
-// The frame's (tile, depth) order without a global sort: count the instances
-// of every tile, scan the counts (the tile ranges), scatter every instance
-// into its tile's bucket, then sort each bucket by (depth quantum, voxel id).
-// That is the order of a stable sort of the keys emitted in voxel order, so
-// the result does not depend on the order in which the atomics land.
+// The frame's (tile, depth) order as a most-significant-digit radix sort:
+// the first digit is the tile (a counting sort: count the instances of
+// every tile, scan the counts into the tile ranges, scatter every instance
+// into its tile's bucket), the second a depth bin within the tile (a
+// counting sort in shared memory), finished by comparisons of (depth
+// quantum, voxel id).  That is the order of a stable sort of the keys
+// emitted in voxel order, so the result does not depend on the order in
+// which the atomics land.
 
 constexpr int kTileScanThreads = 256;
 constexpr int kTileScanItems = 4;        // tiles per thread
