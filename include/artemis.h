@@ -322,8 +322,11 @@ art_status art_get_kernel_times(art_ctx* ctx, int cap, const char** names, int64
 
 /*
  * Stable LSD radix sort of (key, value) pairs by the low key_bits bits of
- * the keys (key_bits in {8, 16, 24, 32}), the sort that orders the screen-tile
- * instances by (tile, depth).  keys, vals: DEVICE arrays of n uint32 each
+ * the keys (key_bits in {8, 16, 24, 32}).  Given the screen-tile instances
+ * (tile << depth_bits | depth quantum, voxel id) in voxel order it yields the
+ * (tile, depth) order that the render computes internally with a
+ * most-significant-digit sort (tile buckets, then depth bins per tile).
+ * keys, vals: DEVICE arrays of n uint32 each
  * (0 <= n <= 2^31 - 1), sorted in place.  Scratch (2 n pairs plus histograms)
  * is allocated by the context on first use and kept for later calls.
  */
