@@ -215,6 +215,20 @@ def render(octree, A: np.ndarray, cam, tau: float = TAU_DEFAULT, hits: bool = Fa
     return out
 
 
+def depth(octree, A: np.ndarray, cam, sigma_min: float, density=None) -> dict:
+    """Depth buffer (Sec. 3.1 "Hybrid Rendering"): per pixel the entry distance
+    of the first hit (compositing order, all hits in [near, far]) whose density
+    exceeds ``sigma_min``, +inf where there is none; ``chord`` = t1 - t0 of
+    that hit.  [H, W] each."""
+    b = _Bound(octree, np.asarray(A).reshape(-1, 12), None, density)
+    k = _cam(cam)
+    D = np.zeros((cam.H, cam.W))
+    ch = np.zeros((cam.H, cam.W))
+    if _L().orc_depth(ctypes.byref(b.s), ctypes.byref(k), ctypes.c_double(sigma_min), _p(D), _p(ch)) != 0:
+        raise MemoryError("orc_depth failed")
+    return dict(depth=D, chord=ch)
+
+
 def pixels(octree, A: np.ndarray, cam, px: Sequence[int], py: Sequence[int],
            tau: float = TAU_DEFAULT, features=None, density=None) -> dict:
     """Sampled pixels, each by brute force over every voxel."""

@@ -14,6 +14,8 @@
  *     T_i = exp(-sum_{j<i} sigma_j delta_j), A = 1 - T_final,
  *     early stop once T < tau                                  (Eq. 5, Eq. 6, early-stop paragraph)
  *   - direct convolutions of the shading network              (Sec. 3.1, "Neural Shading")
+ *   - the depth buffer: entry distance of the first voxel along a ray denser
+ *     than a threshold                                          (Sec. 3.1, "Hybrid Rendering")
  *   - the learned ray-interval proposal's labels, the composite restricted to
  *     a depth interval with the exact transmittance mass it loses, and the
  *     coarse optical-depth bound per screen tile and depth bin (project
@@ -30,6 +32,11 @@
  *     mapped into the canonical frame by A_i^-1 (not renormalised, so the ray
  *     parameter t is preserved) and slab-tested against the cube.
  *   - hits are ordered by (t0, t1, voxel id); the stop test follows each hit.
+ *   - the depth buffer's "first voxel ... with a density larger than a
+ *     threshold" is the first such hit in that order among all of the ray's
+ *     hits in [near, far] (the early stop does not cut the search), its depth
+ *     the entry distance t0 from the camera centre along the unit ray, +inf
+ *     where the ray meets no such voxel.
  *   - a voxel whose blended linear part has det < 1e-3, or any of whose eight
  *     warped corners has camera z <= 1e-6, is not rendered.
  */
@@ -498,6 +505,50 @@ int64_t orc_render(const orc_scene* s, const orc_cam* c, double tau, double* F, 
   free(cand.vid);
   free(info);
   return ret;
+}
+
+/*
+ * Depth buffer (Sec. 3.1 "Hybrid Rendering": the first voxel along a pixel
+ * ray whose density is larger than a threshold gives the pixel its depth).
+ * Per pixel: the entry distance t0 of the first hit, in the compositing
+ * order (t0, t1, voxel id), whose density exceeds sigma_min — over all of the
+ * ray's hits inside [near, far], not only those composited before the early
+ * stop — and +inf where there is none.  depth, chord: [H*W]; chord (may be
+ * NULL) gets t1 - t0 of that hit (+inf where none).  Returns 0, or -1 on
+ * allocation failure.
+ */
+int orc_depth(const orc_scene* s, const orc_cam* c, double sigma_min, double* depth, double* chord) {
+  vox_info* info = all_info(s, c);
+  if (!info) return -1;
+  cand_t cand = {0, 0};
+  if (build_candidates(s, c, info, &cand) != 0) {
+    free(info);
+    return -1;
+  }
+  int64_t npx = (int64_t)c->W * c->H;
+#pragma omp parallel
+  {
+    hit_t* buf = NULL;
+    int cap = 0;
+#pragma omp for schedule(dynamic, 16)
+    for (int64_t p = 0; p < npx; ++p) {
+      int x = (int)(p % c->W), y = (int)(p / c->W);
+      int m = pixel_hits(s, c, info, cand.vid + cand.off[p], cand.off[p + 1] - cand.off[p], x, y, &buf, &cap);
+      depth[p] = INFINITY;
+      if (chord) chord[p] = INFINITY;
+      for (int k = 0; k < m; ++k)
+        if (s->sigma[buf[k].id] > sigma_min) {
+          depth[p] = buf[k].t0;
+          if (chord) chord[p] = buf[k].t1 - buf[k].t0;
+          break;
+        }
+    }
+    free(buf);
+  }
+  free(cand.off);
+  free(cand.vid);
+  free(info);
+  return 0;
 }
 
 /*

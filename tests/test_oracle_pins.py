@@ -843,3 +843,72 @@ def test_tile_union_bins_cases():
     assert np.all(u2[:, :8] == (0, 61))
     b[..., 0], b[..., 1] = 62, 63
     assert np.all(oracle.tile_union_bins(b, cam, margin=2).reshape(4, 16, 2) == (60, 63))
+
+
+# ---------------------------------------------------------------------------
+# Sec. 3.1 "Hybrid Rendering": the depth buffer
+# ---------------------------------------------------------------------------
+
+def test_depth_single_voxel_front_face():
+    # The centre ray of an axis-aligned cube, seen from distance D along an
+    # axis, enters it at D - h/2; along a diagonal through the centre the
+    # entry is at D - h / (2 max_a |d_a|).
+    oc = make_octree([[7, 8, 9]], dens=[5.0], C=2)
+    c = voxel_center(oc, 0)
+    for direction in [(0, 0, 1), (1, 0, 0), (1, 1, 1), (0.3, -0.5, 1.0)]:
+        d = np.asarray(direction, float) / np.linalg.norm(direction)
+        cam = axis_camera(c, direction, dist=1.2)
+        r = oracle.depth(oc, identity_A(1), cam, 1.0)
+        half = 0.5 * oc.h / np.max(np.abs(d))
+        np.testing.assert_allclose(r["depth"][0, 0], 1.2 - half, rtol=1e-12)
+        np.testing.assert_allclose(r["chord"][0, 0], 2 * half, rtol=1e-12)
+    # denser threshold than the voxel: no depth
+    assert np.isinf(oracle.depth(oc, identity_A(1), cam, 5.0)["depth"][0, 0])
+
+
+def test_depth_skips_thin_voxels_and_ignores_the_stop():
+    # Three voxels stacked along the ray, densities 1, 50, 9: with threshold 2
+    # the depth is the second voxel's front face even where an opaque first
+    # voxel would have stopped the composite (tau = 1: stop after the first hit).
+    oc = make_octree([[5, 5, 5], [5, 5, 6], [5, 5, 7]], dens=[1.0, 50.0, 9.0], C=1)
+    c0 = voxel_center(oc, 0)
+    cam = axis_camera(c0, (0, 0, 1), dist=1.0)
+    r = oracle.depth(oc, identity_A(3), cam, 2.0)
+    np.testing.assert_allclose(r["depth"][0, 0], 1.0 + 0.5 * oc.h, rtol=1e-12)
+    assert oracle.render(oc, identity_A(3), cam, tau=1.0)["nused"][0, 0] == 1
+    np.testing.assert_allclose(oracle.depth(oc, identity_A(3), cam, 0.5)["depth"][0, 0], 1.0 - 0.5 * oc.h,
+                               rtol=1e-12)
+    np.testing.assert_allclose(oracle.depth(oc, identity_A(3), cam, 20.0)["depth"][0, 0], 1.0 + 0.5 * oc.h,
+                               rtol=1e-12)
+    np.testing.assert_allclose(oracle.depth(oc, identity_A(3), cam, 50.0)["depth"][0, 0], np.inf)
+    # the near plane clips the entry: the depth is where the ray enters [near, far]
+    cam = axis_camera(c0, (0, 0, 1), dist=1.0, near=1.0)
+    np.testing.assert_allclose(oracle.depth(oc, identity_A(3), cam, 0.5)["depth"][0, 0], 1.0, rtol=1e-12)
+
+
+def test_depth_is_first_dense_hit_of_the_brute_force_lists():
+    # Brute force: the first entry of each pixel's full hit list (every voxel
+    # tested) whose density exceeds the threshold; raising the threshold never
+    # brings the depth closer.
+    sc = sg.preset("mini")
+    cam = sg.orbit_camera(sc.centroid, 24, 16, az_deg=30.0, fov_deg=8.0)
+    pose = sg.random_pose(4)
+    _, A, _ = oracle.pose_transforms(sc, pose)
+    dens = sc.octree.density.astype(np.float64)
+    thr = float(np.median(dens))
+    r = oracle.depth(sc.octree, A, cam, thr)
+    n_some = 0
+    for y in range(cam.H):
+        for x in range(cam.W):
+            b = oracle.pixel_brute(sc.octree, A, cam, x, y, tau=0.0)
+            want = np.inf
+            for i, t0 in zip(b["ids"], b["t0"]):
+                if dens[i] > thr:
+                    want = t0
+                    break
+            n_some += np.isfinite(want)
+            np.testing.assert_allclose(r["depth"][y, x], want, rtol=1e-12)
+    assert n_some > 20
+    r2 = oracle.depth(sc.octree, A, cam, 2 * thr)
+    assert np.all(r2["depth"] >= r["depth"])
+    assert np.all(r["depth"][np.isfinite(r["depth"])] >= cam.near)
