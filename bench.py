@@ -406,6 +406,22 @@ def gpu_arm(args):
         frames[form] = rgba.cpu().numpy()
 
     first_frame(r, args.form)
+    # depth buffer (Sec. 3.1 "Hybrid Rendering"): projection, binning and the
+    # depth walk of one view at the median density as threshold, per call
+    Dbuf = torch.empty((RES, RES), dtype=torch.float32, device="cuda")
+    thr = float(np.median(oc.density))
+    vi0 = step_indices(0)[1]
+    r.render_depth(vi0, thr, Dbuf)
+    dev_ = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(10)]
+    for a, b in dev_:
+        flush.zero_()
+        a.record(torch.cuda.current_stream())
+        r.render_depth(vi0, thr, Dbuf)
+        b.record(torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    result["depth_buffer"] = {"ms_per_call": float(np.mean([a.elapsed_time(b) for a, b in dev_])),
+                              "sigma_min": thr, "covered_pixels": int(torch.isfinite(Dbuf).sum().item()),
+                              "what": "art_render_depth of one 1024^2 view: projection, binning, depth walk"}
     r.close()
 
     def side(form, steps):

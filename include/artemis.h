@@ -143,6 +143,21 @@ art_status art_set_camera(art_ctx* ctx, int view, int W, int H, float fx, float 
  */
 art_status art_render_feature_maps(art_ctx* ctx, int view, void* F_out, int F_dtype, float* A_out);
 
+/*
+ * Depth buffer of `view` under the current pose (Sec. 3.1 "Hybrid
+ * Rendering": each pixel ray is traced to the first voxel whose density is
+ * larger than a threshold, whose distance becomes the pixel's depth): the
+ * entry distance t0 (from the camera centre along the unit pixel ray,
+ * clipped to [znear, zfar]) of the first hit, in order of entry distance,
+ * with sigma > sigma_min among all of the ray's hits — not cut by the early
+ * stop of the compositing — and +infinity where the ray meets none.
+ *   sigma_min  density threshold (>= 0; 1/m)
+ *   depth_out  [H][W] float; device or host
+ * Errors: ART_ERR_STATE before the camera or the pose is set,
+ * ART_ERR_INVALID_ARG for a null output or a negative threshold.
+ */
+art_status art_render_depth(art_ctx* ctx, int view, float sigma_min, float* depth_out);
+
 /* ---------------------------------------------------------- differentiation */
 
 /*

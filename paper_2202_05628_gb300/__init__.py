@@ -64,6 +64,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "art_set_pose": [vp, vp, vp, vp],
         "art_set_camera": [vp, i32, i32, i32, f32, f32, f32, f32, vp, f32, f32],
         "art_render_feature_maps": [vp, i32, vp, i32, vp],
+        "art_render_depth": [vp, i32, f32, vp],
         "art_load_shader": [vp, ctypes.POINTER(NetDesc), vp, i64, i32],
         "art_shade": [vp, i32, vp, i32, vp],
         "art_render_frame": [vp, i32, vp, vp, vp, vp],
@@ -185,6 +186,10 @@ class Renderer:
     # ------------------------------------------------------------- rendering
     def render_feature_maps(self, view: int, F_out, A_out=None, F_dtype: str = "f32"):
         self._check(_lib.art_render_feature_maps(self._h, view, _ptr(F_out), DTYPES[F_dtype], _ptr(A_out)))
+
+    def render_depth(self, view: int, sigma_min: float, depth_out):
+        """Depth buffer: entry distance of the first hit denser than sigma_min (+inf where none)."""
+        self._check(_lib.art_render_depth(self._h, view, float(sigma_min), _ptr(depth_out)))
 
     def shade(self, view: int, F, rgba_out, F_dtype: str = "f32"):
         self._check(_lib.art_shade(self._h, view, _ptr(F), DTYPES[F_dtype], _ptr(rgba_out)))

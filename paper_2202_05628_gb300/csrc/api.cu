@@ -608,6 +608,33 @@ art_status art_render_feature_maps(art_ctx* ctx, int view, void* F_out, int F_dt
   return ART_OK;
 }
 
+art_status art_render_depth(art_ctx* ctx, int view, float sigma_min, float* depth_out) {
+  if (!ctx) return ART_ERR_INVALID_ARG;
+  if (view < 0 || view >= kMaxViews || !ctx->view_set[view]) return fail(ctx, ART_ERR_STATE, "view %d not set", view);
+  if (!ctx->posed) return fail(ctx, ART_ERR_STATE, "render_depth before set_pose");
+  if (!depth_out) return fail(ctx, ART_ERR_INVALID_ARG, "depth_out is null");
+  if (!(sigma_min >= 0.0f)) return fail(ctx, ART_ERR_INVALID_ARG, "sigma_min must be >= 0");
+  const ViewParams& v = ctx->views[view];
+  const size_t npx = (size_t)v.W * v.H;
+  const bool dev = is_device_ptr(depth_out);
+  float* D = depth_out;
+  art_status st;
+  if (!dev) {
+    if ((st = ensure(ctx, (void**)&ctx->d_A, &ctx->d_A_bytes, npx * 4, "depth buffer")) != ART_OK) return st;
+    D = ctx->d_A;
+  }
+  if ((st = ensure_bin_buffers(ctx, (int64_t)v.tiles_x * v.tiles_y)) != ART_OK) return st;
+  launch_project(ctx, v);
+  launch_bin(ctx, v);
+  launch_depth(ctx, v, sigma_min, D);
+  if ((st = launch_check(ctx, "render_depth")) != ART_OK) return st;
+  if (!dev) {
+    cudaMemcpyAsync(depth_out, D, npx * 4, cudaMemcpyDeviceToHost, ctx->stream);
+    return sync_check(ctx, "render_depth (copy out)");
+  }
+  return ART_OK;
+}
+
 art_status art_load_shader(art_ctx* ctx, const art_net_desc* desc, const float* params, int64_t n_params,
                            int compute_dtype) {
   if (!ctx) return ART_ERR_INVALID_ARG;

@@ -242,6 +242,11 @@ size_t sort_hist_words(int64_t n);
 size_t scan_block_words(int64_t n);
 size_t tile_scan_state_words(int64_t ntiles);  // look-back words of the tile scan
 
+// ---- depth buffer (depth.cu): after launch_project + launch_bin of the view,
+// depth [H][W] = entry distance of the nearest hit denser than sigma_min
+// (+inf where none)
+void launch_depth(art_ctx* ctx, const ViewParams& v, float sigma_min, float* depth);
+
 // ---- composite (composite.cu)
 art_status launch_composite(art_ctx* ctx, const ViewParams& v, void* F, int F_dtype, float* A,
                             const void* hit_log = nullptr);
