@@ -32,8 +32,8 @@
  *     mapped into the canonical frame by A_i^-1 (not renormalised, so the ray
  *     parameter t is preserved) and slab-tested against the cube.
  *   - hits are ordered by (t0, t1, voxel id); the stop test follows each hit.
- *   - the depth buffer's "first voxel ... with a density larger than a
- *     threshold" is the first such hit in that order among all of the ray's
+ *   - the depth buffer's voxel (the nearest along the ray denser than the
+ *     threshold) is the first such hit in that order among all of the ray's
  *     hits in [near, far] (the early stop does not cut the search), its depth
  *     the entry distance t0 from the camera centre along the unit ray, +inf
  *     where the ray meets no such voxel.
@@ -508,8 +508,8 @@ int64_t orc_render(const orc_scene* s, const orc_cam* c, double tau, double* F, 
 }
 
 /*
- * Depth buffer (Sec. 3.1 "Hybrid Rendering": the first voxel along a pixel
- * ray whose density is larger than a threshold gives the pixel its depth).
+ * Depth buffer (Sec. 3.1 "Hybrid Rendering": a pixel's depth is how far
+ * along its ray the nearest voxel denser than a set threshold lies).
  * Per pixel: the entry distance t0 of the first hit, in the compositing
  * order (t0, t1, voxel id), whose density exceeds sigma_min — over all of the
  * ray's hits inside [near, far], not only those composited before the early

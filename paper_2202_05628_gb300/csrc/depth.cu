@@ -1,6 +1,6 @@
 // Depth buffer of the rendered animal (arXiv 2202.05628, Sec. 3.1 "Hybrid
-// Rendering": each pixel ray is traced to the first voxel whose density is
-// larger than a threshold, and its distance is the pixel's depth).  Here:
+// Rendering": a pixel's depth is how far along its ray the nearest voxel
+// denser than a set threshold lies).  Here:
 // the entry distance t0 (from the camera centre along the unit ray, inside
 // [near, far]) of the nearest hit with sigma > sigma_min among all of the
 // ray's hits, +inf where there is none.
