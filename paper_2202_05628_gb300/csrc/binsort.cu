@@ -689,10 +689,9 @@ void launch_bin(art_ctx* ctx, const ViewParams& v, const uint32_t* hbin, const f
   const int64_t n = ctx->n;
   const int ntiles = v.tiles_x * v.tiles_y;
   const unsigned vb = (unsigned)((n + 255) / 256);
-  static bool attr = false;
-  if (!attr) {
+  if (!ctx->attr_tile_sort) {  // (a function attribute holds per device: set once per context)
     cudaFuncSetAttribute(tile_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileSortSmem * 8);
-    attr = true;
+    ctx->attr_tile_sort = true;
   }
   const int nsb = (ntiles + kTileScanBlock - 1) / kTileScanBlock;
   ART_LAUNCH(ctx, "bin_scan", tile_scan_kernel, nsb, kTileScanThreads, 0, ntiles, ctx->d_tcount, ctx->inst_cap,

@@ -136,6 +136,8 @@ struct art_ctx {
   uint32_t* d_agroups = nullptr;  // groups of four consecutive tiles with instances (unordered)
   unsigned long long* d_status = nullptr;
   unsigned long long* h_status = nullptr;  // pinned
+  bool attr_tile_sort = false;  // large shared-memory attributes set on this context's device
+  bool attr_proposal = false;
 
   // ---- frame buffers (art_render_frame)
   void* d_F = nullptr;

@@ -283,11 +283,10 @@ void launch_pose_bias(art_ctx* ctx) {
 }
 
 art_status launch_proposal(art_ctx* ctx, const ViewParams& v, uint8_t* bins, float* logits, bool active_only) {
-  static bool attr = false;
-  if (!attr) {
+  if (!ctx->attr_proposal) {  // (a function attribute holds per device: set once per context)
     cudaError_t e = cudaFuncSetAttribute(proposal_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "proposal smem attribute");
-    attr = true;
+    ctx->attr_proposal = true;
   }
   PropParams p;
   p.img = reinterpret_cast<const uint4*>(ctx->d_prop_img);
