@@ -1,7 +1,7 @@
 """Frame-rate benchmark of the GB300 ARTEMIS rendering path.
 
 One step = one frame of one view: pose -> LBS warp of ~1M leaf voxels ->
-screen-tile binning + radix sort -> exact-hit front-to-back compositing of
+screen-tile binning (by tile, then by depth) -> exact-hit front-to-back compositing of
 F (32 channels) and A at 1024x1024 -> 4-level U-Net shading -> RGBA.
 Poses follow a 60-frame walk cycle; the camera orbits 8 azimuths.
 
@@ -360,13 +360,8 @@ def gpu_arm(args):
             conv_launch_ms = unet_ms(r, step_indices(args.warmup + args.steps - 1)[1], oc.C, rgba, flush) / 14
             r.kernel_times(reset=True)
     t_local = float(np.sum(ms))
-    if world > 1:
-        t = torch.tensor([t_local], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    else:
-        t_max = t_local
-    value = world * args.steps / (t_max * 1e-3)
+    t_max = max_over_ranks(t_local, world, "cuda")
+    value = job_value(world, args.steps, t_max)
     storage, net, skip, desc = FORMS[args.form]
     result = {
         "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
@@ -501,6 +496,22 @@ def quality(rgba, ref):
 
 
 TILE = 256  # side of the oracle arm's sampled square of the view
+
+
+def max_over_ranks(t_local: float, world: int, device) -> float:
+    """Duration of the whole job's timed region: the max over the ranks (ms)."""
+    if world == 1:
+        return t_local
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([t_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world: int, steps: int, t_max_ms: float) -> float:
+    """Frames of all replicas per second of the slowest one."""
+    return world * steps / (t_max_ms * 1e-3)
 
 
 def reference_arm(args):
