@@ -229,6 +229,59 @@ def depth(octree, A: np.ndarray, cam, sigma_min: float, density=None) -> dict:
     return dict(depth=D, chord=ch)
 
 
+# ---------------------------------------------------------------------------
+# Eq. 2: view-dependent features (spherical harmonics)
+# ---------------------------------------------------------------------------
+
+SH_LMAX = 9
+
+
+def sh_basis(L: int, dirs) -> np.ndarray:
+    """Real orthonormal spherical harmonics of degree <= L at unit directions
+    ``dirs`` [m, 3]: [m, (L+1)^2], index l^2 + l + m."""
+    d = _f64(np.atleast_2d(dirs))
+    H = (L + 1) ** 2
+    out = np.zeros((d.shape[0], H))
+    row = np.zeros(H)
+    for k in range(d.shape[0]):
+        dk = np.ascontiguousarray(d[k])
+        if _L().orc_sh_basis(ctypes.c_int(L), _p(dk), _p(row)) != 0:
+            raise ValueError(f"degree {L} out of range [0, {SH_LMAX}]")
+        out[k] = row
+    return out
+
+
+def polar_rotation(A) -> np.ndarray:
+    """Rotation factor of the polar decomposition of each 3x4 transform's
+    linear part: [n, 3, 3]."""
+    A = _f64(A).reshape(-1, 12)
+    R = np.zeros((A.shape[0], 9))
+    for i in range(A.shape[0]):
+        a = np.ascontiguousarray(A[i])
+        r = np.zeros(9)
+        if _L().orc_polar_rotation(_p(a), _p(r)) != 0:
+            raise ValueError("polar_rotation: det <= 0")
+        R[i] = r
+    return R.reshape(-1, 3, 3)
+
+
+def render_sh(octree, A: np.ndarray, cam, L: int, coef, tau: float = TAU_DEFAULT, density=None) -> dict:
+    """F [H,W,C] and A [H,W] with view-dependent features (Eq. 2): hit i's
+    feature is sum_h coef[i, h] Y_h(R_i^T d), R_i the rotation factor of its
+    transform, d the unit ray direction.  coef: [n, (L+1)^2, C]."""
+    coef = _f64(coef)
+    n, H, C = coef.shape
+    assert n == octree.n and H == (L + 1) ** 2
+    b = _Bound(octree, np.asarray(A).reshape(-1, 12), np.zeros((n, C)), density)
+    k = _cam(cam)
+    F = np.zeros((cam.H, cam.W, C))
+    Am = np.zeros((cam.H, cam.W))
+    if _L().orc_render_sh(ctypes.byref(b.s), ctypes.byref(k), ctypes.c_double(tau), ctypes.c_int(L), _p(coef),
+                          _p(F), _p(Am)) != 0:
+        raise ValueError("orc_render_sh failed (degree out of range or allocation)")
+    return dict(F=F, A=Am)
+
+
 def pixels(octree, A: np.ndarray, cam, px: Sequence[int], py: Sequence[int],
            tau: float = TAU_DEFAULT, features=None, density=None) -> dict:
     """Sampled pixels, each by brute force over every voxel."""

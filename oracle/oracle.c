@@ -16,6 +16,8 @@
  *   - direct convolutions of the shading network              (Sec. 3.1, "Neural Shading")
  *   - the depth buffer: entry distance of the first voxel along a ray denser
  *     than a threshold                                          (Sec. 3.1, "Hybrid Rendering")
+ *   - view-dependent features: spherical-harmonics coefficients evaluated at
+ *     the ray direction in the voxel's canonical frame          (Eq. 2, Sec. 3.1)
  *   - the learned ray-interval proposal's labels, the composite restricted to
  *     a depth interval with the exact transmittance mass it loses, and the
  *     coarse optical-depth bound per screen tile and depth bin (project
@@ -37,6 +39,13 @@
  *     hits in [near, far] (the early stop does not cut the search), its depth
  *     the entry distance t0 from the camera centre along the unit ray, +inf
  *     where the ray meets no such voxel.
+ *   - Eq. 2's spherical harmonics are the real orthonormal ones (without the
+ *     Condon-Shortley phase in the real basis), indexed h = l^2 + l + m; the
+ *     paper's 91 bases is not a square (l <= 8 gives 81, l <= 9 gives 100):
+ *     the degree is a parameter (<= 9).  The rotation R_i^t that maps a ray
+ *     into voxel i's canonical frame is read, for a blend of joint
+ *     transforms (not a rotation), as the rotation factor of the polar
+ *     decomposition of its linear part.
  *   - a voxel whose blended linear part has det < 1e-3, or any of whose eight
  *     warped corners has camera z <= 1e-6, is not rendered.
  */
@@ -547,6 +556,147 @@ int orc_depth(const orc_scene* s, const orc_cam* c, double sigma_min, double* de
   }
   free(cand.off);
   free(cand.vid);
+  free(info);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* View-dependent features (Eq. 2): per voxel, spherical-harmonics           */
+/* coefficient vectors k_h in R^C evaluated at the ray direction mapped into  */
+/* the voxel's canonical frame, d^c = R_i^-1 d (Sec. 3.1, "Dynamic Volume     */
+/* Rendering"), S = sum_h k_h Y_h(d^c).                                       */
+/* ------------------------------------------------------------------------ */
+
+#define ORC_SH_LMAX 9
+#define ORC_PI 3.14159265358979323846
+
+/* Real orthonormal spherical harmonics of degree <= L (L <= ORC_SH_LMAX) at
+ * the unit direction d, Y[l*l + l + m] for -l <= m <= l:
+ *   Y_{l,0} = K_l^0 P_l^0(z),
+ *   Y_{l,m} = sqrt(2) K_l^m P_l^m(z) cos(m phi),  Y_{l,-m} = sqrt(2) K_l^m P_l^m(z) sin(m phi)  (m > 0),
+ *   K_l^m = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!),
+ * P_l^m the associated Legendre functions without the Condon-Shortley
+ * phase, z = cos(theta) = d_z, phi = atan2(d_y, d_x).  Returns 0, or -1 for
+ * a degree out of range. */
+int orc_sh_basis(int L, const double d[3], double* Y) {
+  if (L < 0 || L > ORC_SH_LMAX) return -1;
+  const int S = ORC_SH_LMAX + 1;
+  double P[(ORC_SH_LMAX + 1) * (ORC_SH_LMAX + 1)];
+  const double z = d[2], st = hypot(d[0], d[1]), phi = atan2(d[1], d[0]);
+  for (int m = 0; m <= L; ++m) {
+    double pmm = 1.0;
+    for (int k = 1; k <= m; ++k) pmm *= (double)(2 * k - 1) * st;
+    P[m * S + m] = pmm;
+    if (m + 1 <= L) P[(m + 1) * S + m] = z * (double)(2 * m + 1) * pmm;
+    for (int l = m + 2; l <= L; ++l)
+      P[l * S + m] = ((double)(2 * l - 1) * z * P[(l - 1) * S + m] - (double)(l + m - 1) * P[(l - 2) * S + m]) /
+                     (double)(l - m);
+  }
+  for (int l = 0; l <= L; ++l)
+    for (int m = 0; m <= l; ++m) {
+      double ratio = 1.0; /* (l-m)! / (l+m)! */
+      for (int k = l - m + 1; k <= l + m; ++k) ratio /= (double)k;
+      const double K = sqrt((double)(2 * l + 1) / (4.0 * ORC_PI) * ratio);
+      if (m == 0) {
+        Y[l * l + l] = K * P[l * S];
+      } else {
+        Y[l * l + l + m] = sqrt(2.0) * K * P[l * S + m] * cos((double)m * phi);
+        Y[l * l + l - m] = sqrt(2.0) * K * P[l * S + m] * sin((double)m * phi);
+      }
+    }
+  return 0;
+}
+
+/* Rotation factor R of the polar decomposition A_lin = R S (S symmetric
+ * positive definite) of the 3x3 block of a 3x4 affine matrix with a positive
+ * determinant, by Newton's iteration X <- (X + X^-T) / 2 from X = A_lin
+ * (Higham 1986).  R: [9] row-major.  Returns 0, or -1 when det <= 0. */
+int orc_polar_rotation(const double A[12], double R[9]) {
+  double X[9];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) X[r * 3 + c] = A[r * 4 + c];
+  if (det3(X, 3) <= 0.0) return -1;
+  for (int it = 0; it < 100; ++it) {
+    const double d = det3(X, 3);
+    /* X^-T = cofactor(X) / det */
+    const double cof[9] = {X[4] * X[8] - X[5] * X[7], X[5] * X[6] - X[3] * X[8], X[3] * X[7] - X[4] * X[6],
+                           X[2] * X[7] - X[1] * X[8], X[0] * X[8] - X[2] * X[6], X[1] * X[6] - X[0] * X[7],
+                           X[1] * X[5] - X[2] * X[4], X[2] * X[3] - X[0] * X[5], X[0] * X[4] - X[1] * X[3]};
+    double diff = 0.0;
+    for (int k = 0; k < 9; ++k) {
+      const double xn = 0.5 * (X[k] + cof[k] / d);
+      diff = fmax(diff, fabs(xn - X[k]));
+      X[k] = xn;
+    }
+    if (diff < 1e-15) break;
+  }
+  memcpy(R, X, sizeof(X));
+  return 0;
+}
+
+/*
+ * Feature map and coarse opacity with view-dependent features: as orc_render
+ * (Eq. 5, Eq. 6, early stop) but each hit's feature is
+ * S = sum_h coef[i][h][:] Y_h(R_i^T d), R_i the rotation factor of voxel i's
+ * blended transform, d the unit pixel ray direction, H = (L+1)^2.
+ * coef: [n][H][C] (C = the scene's channel count; the scene's own features
+ * are not used).  F [H*W][C], A [H*W].  Returns 0, or -1 on allocation
+ * failure or a degree out of range.
+ */
+int orc_render_sh(const orc_scene* s, const orc_cam* c, double tau, int L, const double* coef, double* F,
+                  double* Aout) {
+  if (L < 0 || L > ORC_SH_LMAX) return -1;
+  const int H = (L + 1) * (L + 1), C = s->C;
+  vox_info* info = all_info(s, c);
+  if (!info) return -1;
+  double* rot = (double*)malloc(sizeof(double) * 9 * (size_t)(s->n > 0 ? s->n : 1));
+  cand_t cand = {0, 0};
+  if (!rot || build_candidates(s, c, info, &cand) != 0) {
+    free(rot);
+    free(info);
+    return -1;
+  }
+  for (int64_t i = 0; i < s->n; ++i)
+    if (!info[i].ok || orc_polar_rotation(s->A + 12 * i, rot + 9 * i) != 0) info[i].ok = 0;
+  const int64_t npx = (int64_t)c->W * c->H;
+#pragma omp parallel
+  {
+    hit_t* buf = NULL;
+    int cap = 0;
+    double Y[(ORC_SH_LMAX + 1) * (ORC_SH_LMAX + 1)];
+#pragma omp for schedule(dynamic, 16)
+    for (int64_t p = 0; p < npx; ++p) {
+      const int x = (int)(p % c->W), y = (int)(p / c->W);
+      int m = pixel_hits(s, c, info, cand.vid + cand.off[p], cand.off[p + 1] - cand.off[p], x, y, &buf, &cap);
+      double o[3], d[3];
+      cam_ray(c, x, y, o, d);
+      double* Fp = F + p * C;
+      for (int k = 0; k < C; ++k) Fp[k] = 0.0;
+      double optical = 0.0;
+      for (int q = 0; q < m; ++q) {
+        const int64_t id = buf[q].id;
+        const double* R = rot + 9 * id;
+        const double dc[3] = {R[0] * d[0] + R[3] * d[1] + R[6] * d[2], R[1] * d[0] + R[4] * d[1] + R[7] * d[2],
+                              R[2] * d[0] + R[5] * d[1] + R[8] * d[2]};
+        orc_sh_basis(L, dc, Y);
+        const double sig = s->sigma[id], delta = buf[q].t1 - buf[q].t0;
+        const double w = exp(-optical) * (1.0 - exp(-sig * delta));
+        const double* kq = coef + (size_t)id * H * C;
+        for (int k = 0; k < C; ++k) {
+          double f = 0.0;
+          for (int h = 0; h < H; ++h) f += kq[(size_t)h * C + k] * Y[h];
+          Fp[k] += w * f;
+        }
+        optical += sig * delta;
+        if (exp(-optical) < tau) break;
+      }
+      Aout[p] = 1.0 - exp(-optical);
+    }
+    free(buf);
+  }
+  free(cand.off);
+  free(cand.vid);
+  free(rot);
   free(info);
   return 0;
 }

@@ -912,3 +912,139 @@ def test_depth_is_first_dense_hit_of_the_brute_force_lists():
     r2 = oracle.depth(sc.octree, A, cam, 2 * thr)
     assert np.all(r2["depth"] >= r["depth"])
     assert np.all(r["depth"][np.isfinite(r["depth"])] >= cam.near)
+
+
+# ---------------------------------------------------------------------------
+# Eq. 2: view-dependent features (spherical harmonics)
+# ---------------------------------------------------------------------------
+
+def _real_sh_scipy(L, d):
+    """Real orthonormal SH from scipy's complex ones (which carry the
+    Condon-Shortley phase): sqrt(2) (-1)^m Re / Im of Y_l^|m|."""
+    sp = pytest.importorskip("scipy.special")
+    th = np.arccos(np.clip(d[:, 2], -1, 1))
+    ph = np.mod(np.arctan2(d[:, 1], d[:, 0]), 2 * np.pi)
+    out = np.zeros((d.shape[0], (L + 1) ** 2))
+    for l in range(L + 1):
+        for m in range(-l, l + 1):
+            y = sp.sph_harm_y(l, abs(m), th, ph)
+            if m < 0:
+                v = math.sqrt(2) * (-1) ** m * y.imag
+            elif m == 0:
+                v = y.real
+            else:
+                v = math.sqrt(2) * (-1) ** m * y.real
+            out[:, l * l + l + m] = v
+    return out
+
+
+def test_sh_basis_matches_scipy():
+    rng = np.random.default_rng(0)
+    d = rng.standard_normal((40, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    d = np.concatenate([d, [[0, 0, 1.0], [0, 0, -1.0], [1.0, 0, 0]]])
+    for L in (0, 1, 3, 6, 9):
+        np.testing.assert_allclose(oracle.sh_basis(L, d), _real_sh_scipy(L, d), atol=1e-11)
+    # degree 1 in closed form: sqrt(3 / 4pi) (y, z, x)
+    c1 = math.sqrt(3.0 / (4 * math.pi))
+    np.testing.assert_allclose(oracle.sh_basis(1, d)[:, 1:], c1 * d[:, [1, 2, 0]], atol=1e-14)
+    with pytest.raises(ValueError):
+        oracle.sh_basis(10, d[:1])
+
+
+def test_sh_basis_orthonormal_on_the_sphere():
+    # Gauss-Legendre in cos(theta) x uniform phi integrates products of
+    # degree <= 7 harmonics exactly: the Gram matrix is the identity.
+    L = 7
+    x, wx = np.polynomial.legendre.leggauss(24)
+    nphi = 48
+    phi = 2 * np.pi * np.arange(nphi) / nphi
+    ct, ph = np.meshgrid(x, phi, indexing="ij")
+    st = np.sqrt(1 - ct ** 2)
+    d = np.stack([st * np.cos(ph), st * np.sin(ph), ct], -1).reshape(-1, 3)
+    w = (wx[:, None] * np.full(nphi, 2 * np.pi / nphi)[None, :]).reshape(-1)
+    Y = oracle.sh_basis(L, d)
+    G = (Y * w[:, None]).T @ Y
+    np.testing.assert_allclose(G, np.eye((L + 1) ** 2), atol=1e-12)
+
+
+def test_polar_rotation_factors():
+    rng = np.random.default_rng(3)
+    for k in range(5):
+        Q = oracle.rodrigues(rng.standard_normal(3))
+        M = rng.standard_normal((3, 3))
+        S = M @ M.T + 0.5 * np.eye(3)  # symmetric positive definite
+        for lin in (Q, 2.5 * Q, Q @ S):
+            A = np.concatenate([lin, rng.standard_normal((3, 1))], 1)
+            np.testing.assert_allclose(oracle.polar_rotation(A)[0], Q, atol=1e-12)
+    # a blend of two rotations: orthonormal, det +1, and R^T A_lin symmetric positive definite
+    R1, R2 = oracle.rodrigues([0.3, -0.2, 0.5]), oracle.rodrigues([-0.4, 0.1, 0.2])
+    lin = 0.7 * R1 + 0.3 * R2
+    R = oracle.polar_rotation(np.concatenate([lin, np.zeros((3, 1))], 1))[0]
+    np.testing.assert_allclose(R.T @ R, np.eye(3), atol=1e-13)
+    assert abs(np.linalg.det(R) - 1) < 1e-13
+    P = R.T @ lin
+    np.testing.assert_allclose(P, P.T, atol=1e-13)
+    assert np.all(np.linalg.eigvalsh(0.5 * (P + P.T)) > 0)
+
+
+def test_render_sh_degree_zero_is_the_plain_render():
+    sc = sg.preset("mini")
+    oc = sc.octree
+    cam = sg.orbit_camera(sc.centroid, 32, 24, az_deg=70.0, fov_deg=10.0)
+    _, A, _ = oracle.pose_transforms(sc, sg.random_pose(2))
+    rng = np.random.default_rng(1)
+    k0 = rng.standard_normal((oc.n, 1, 5))
+    r = oracle.render_sh(oc, A, cam, 0, k0)
+    y00 = 0.5 / math.sqrt(math.pi)
+    p = oracle.render(oc, A, cam, features=k0[:, 0, :] * y00)
+    assert (p["A"] > 0).sum() > 50
+    np.testing.assert_allclose(r["A"], p["A"], atol=1e-14)
+    np.testing.assert_allclose(r["F"], p["F"], atol=1e-13)
+
+
+def test_render_sh_single_voxel_closed_form():
+    # One voxel under a rigid transform [Q | t], seen along direction d through
+    # its centre: S = sum_h k_h Y_h(Q^T d), weighted by its alpha.
+    oc = make_octree([[6, 7, 8]], dens=[4.0], C=2)
+    Q = oracle.rodrigues([0.3, 0.9, -0.4])
+    t = np.array([0.02, -0.05, 0.04])
+    A = np.zeros((1, 3, 4))
+    A[0, :, :3], A[0, :, 3] = Q, t
+    cw = Q @ voxel_center(oc, 0) + t
+    L = 3
+    k = np.random.default_rng(5).standard_normal((1, (L + 1) ** 2, 2))
+    for direction in [(0, 0, 1), (0.4, -0.3, 1.0), (-1, 0.2, 0.1)]:
+        d = np.asarray(direction, float) / np.linalg.norm(direction)
+        cam = axis_camera(cw, direction, dist=1.1)
+        r = oracle.render_sh(oc, A, cam, L, k)
+        dl = Q.T @ d
+        chord = oc.h / np.max(np.abs(dl))
+        a = 1 - math.exp(-4.0 * chord)
+        S = _real_sh_scipy(L, dl[None, :])[0] @ k[0]
+        np.testing.assert_allclose(r["F"][0, 0], a * S, rtol=1e-10, atol=1e-13)
+
+
+def test_render_sh_rigid_joint_equals_moved_camera():
+    # All voxels bound to one joint (a rigid G_j): the canonical ray direction
+    # R_j^T d is the direction seen by the camera world_to_cam * G_j looking at
+    # the unposed animal, so the two renders agree.
+    sc = sg.preset("mini")
+    oc = sc.octree
+    w = np.zeros_like(oc.weights)
+    w[:, 0] = 1.0
+    jidx = np.full_like(oc.joint_idx, 4)
+    oc1 = sg.Octree(oc.depth, oc.origin, oc.extent, oc.ijk, jidx, w, oc.features, oc.density, oc.sdf)
+    sc1 = sg.Scene(oc1, sc.skeleton, sc.centroid, sc.scale, sc.bones, sc.capsules)
+    G, A, _ = oracle.pose_transforms(sc1, sg.random_pose(7))
+    cam = _cam64(sg.orbit_camera(sc.centroid, 40, 30, az_deg=-25, fov_deg=10.0))
+    L = 4
+    k = np.random.default_rng(8).standard_normal((oc.n, (L + 1) ** 2, 3))
+    r1 = oracle.render_sh(oc1, A, cam, L, k)
+    M, Gj = cam.world_to_cam, G[4]
+    M2 = np.concatenate([M[:, :3] @ Gj[:, :3], (M[:, :3] @ Gj[:, 3] + M[:, 3])[:, None]], 1)
+    cam2 = sg.Camera(cam.W, cam.H, cam.fx, cam.fy, cam.cx, cam.cy, M2, cam.near, cam.far)
+    r2 = oracle.render_sh(oc1, identity_A(oc.n), cam2, L, k)
+    assert (r1["A"] > 0).sum() > 50
+    np.testing.assert_allclose(r1["A"], r2["A"], atol=1e-10)
+    np.testing.assert_allclose(r1["F"], r2["F"], atol=1e-9)
