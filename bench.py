@@ -451,16 +451,19 @@ def gpu_arm(args):
             pi, vi = step_indices(k)
             r.render_frame(vi, *host_pose[pi], host_out)
         torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
         t0 = time.perf_counter()
         for k in range(k_e2e):
             pi, vi = step_indices(k)
             r.render_frame(vi, *host_pose[pi], host_out)  # synchronous: copies RGBA back to the host
         t1 = time.perf_counter()
-        result["e2e"] = {"value": k_e2e / (t1 - t0), "unit": "frames/s",
+        t_e2e = max_over_ranks(1e3 * (t1 - t0), world, "cuda")  # ms, the slowest replica
+        result["e2e"] = {"value": job_value(world, k_e2e, t_e2e), "unit": "frames/s",
                          "h2d_bytes_per_step": int(sum(x.numel() * 4 for x in host_pose[0])),
                          "d2h_bytes_per_step": int(host_out.numel() * 4), "steps": k_e2e}
         r.close()
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:  # the oracle baseline: one GPU runs only
         result["cpu_baseline"], ref = cpu_baseline(sc, cams, poses, layers)
         result["quality"] = {f: quality(x, ref) for f, x in frames.items()}
         result["quality"]["frame"] = "pose %d, azimuth %d against the FP64 oracle" % step_indices(0)
