@@ -1048,3 +1048,68 @@ def test_render_sh_rigid_joint_equals_moved_camera():
     assert (r1["A"] > 0).sum() > 50
     np.testing.assert_allclose(r1["A"], r2["A"], atol=1e-10)
     np.testing.assert_allclose(r1["F"], r2["F"], atol=1e-9)
+
+
+# ---------------------------------------------------------------------------
+# remaining entry points: the tiny network, the whole frame, ray directions,
+# sampled pixels
+# ---------------------------------------------------------------------------
+
+def test_tiny_net_matches_torch_and_shade_dispatches():
+    torch = pytest.importorskip("torch")
+    import torch.nn.functional as Fn
+    layers = sg.tiny_net_weights(4, cin=5, mid=7, cout=4)
+    x = np.random.default_rng(2).standard_normal((11, 13, 5))
+    t = torch.from_numpy(x).permute(2, 0, 1)[None]
+    for k, (w, b) in enumerate(layers):
+        t = Fn.conv2d(t, torch.from_numpy(w.astype(np.float64)).permute(0, 3, 1, 2),
+                      torch.from_numpy(b.astype(np.float64)), padding=1)
+        t = torch.sigmoid(t) if k == 2 else torch.relu(t)
+    ref = t[0].permute(1, 2, 0).numpy()
+    np.testing.assert_allclose(oracle.shade_tiny(x, layers), ref, atol=1e-12)
+    np.testing.assert_array_equal(oracle.shade(x, layers), oracle.shade_tiny(x, layers))
+    ul = sg.unet_weights(3, cin=5, ch=(4, 6, 8, 10))
+    xu = np.random.default_rng(3).standard_normal((16, 24, 5))
+    np.testing.assert_array_equal(oracle.shade(xu, ul), oracle.shade_unet(xu, ul))
+
+
+def test_render_frame_is_pose_render_and_shade():
+    sc = sg.preset("mini")
+    cam = sg.orbit_camera(sc.centroid, 24, 16, az_deg=10.0, fov_deg=10.0)
+    pose = sg.random_pose(6)
+    layers = sg.tiny_net_weights(1, cin=sc.octree.C, mid=6)
+    out = oracle.render_frame(sc, pose, cam, layers)
+    G, A, det = oracle.pose_transforms(sc, pose)
+    r = oracle.render(sc.octree, A, cam)
+    np.testing.assert_array_equal(out["F"], r["F"])
+    np.testing.assert_array_equal(out["A"], r["A"])
+    np.testing.assert_array_equal(out["rgba"], oracle.shade(r["F"], layers))
+    np.testing.assert_array_equal(out["G"], G)
+
+
+def test_ray_dirs_equal_pixel_rays():
+    cam = sg.orbit_camera(np.array([0.1, 0.2, -0.3]), 7, 5, az_deg=33.0, elev_deg=-20.0)
+    D = oracle.ray_dirs(cam)
+    for y in range(cam.H):
+        for x in range(cam.W):
+            _, d = oracle.pixel_ray(cam, x, y)
+            np.testing.assert_allclose(D[y, x], d, atol=1e-15)
+    np.testing.assert_allclose(np.linalg.norm(D, axis=2), 1.0, atol=1e-14)
+
+
+def test_sampled_pixels_equal_the_full_render():
+    # pixels() tests every voxel for each sampled pixel; render() only the
+    # candidates of the projected boxes: the same F and A wherever sampled.
+    sc = sg.preset("mini")
+    cam = sg.orbit_camera(sc.centroid, 32, 24, az_deg=140.0, fov_deg=10.0)
+    _, A, _ = oracle.pose_transforms(sc, sg.random_pose(9))
+    full = oracle.render(sc.octree, A, cam)
+    rng = np.random.default_rng(4)
+    px, py = rng.integers(0, cam.W, 60), rng.integers(0, cam.H, 60)
+    cov = np.argwhere(full["A"] > 0)
+    px = np.concatenate([px, cov[:40, 1]])
+    py = np.concatenate([py, cov[:40, 0]])
+    o = oracle.pixels(sc.octree, A, cam, px, py)
+    np.testing.assert_allclose(o["F"], full["F"][py, px], atol=1e-14)
+    np.testing.assert_allclose(o["A"], full["A"][py, px], atol=1e-14)
+    assert np.all(o["nhit"] == full["nhit"][py, px])
