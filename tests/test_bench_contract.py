@@ -1,0 +1,46 @@
+"""The benchmark's JSON fields that are pure arithmetic, checked on the CPU:
+the U-Net's FLOP count and the roofline object built from kernel times."""
+import math
+
+import bench
+
+
+def test_unet_flops_by_hand():
+    # 3x3 convolutions per level (H, W halve per level): 2 H W Cout 9 Cin each,
+    # plus the 1x1 head; the 1024^2, 32-64-128-256 network is ~357 GFLOP.
+    H = W = 1024
+    convs = [(0, 32, 32), (0, 32, 32), (1, 64, 32), (1, 64, 64), (2, 128, 64), (2, 128, 128), (3, 256, 128),
+             (3, 256, 256), (2, 128, 384), (2, 128, 128), (1, 64, 192), (1, 64, 64), (0, 32, 96), (0, 32, 32)]
+    want = sum(2 * (H >> l) * (W >> l) * co * ci * 9 for l, co, ci in convs) + 2 * H * W * 4 * 32
+    assert bench.unet_flops(H, W) == want
+    assert abs(want / 1e9 - 357.4) < 0.5
+
+
+def test_roofline_of_the_convolutions():
+    frames = 10
+    kt = {"conv_tc": (14 * frames, 14 * frames * 0.05), "composite_skip": (2 * frames, 0.3 * frames)}
+    peaks = {"hbm_gbs": 6783.5, "bf16_tflops_sustained": 1713.7}
+    r = bench.roofline(kt, {"instances": 900000}, peaks, "bf16_skip", 1000000, 32, frames)
+    per_launch = bench.unet_flops(1024, 1024) / 14
+    assert r["kernel"] == "conv_tc" and r["bound"] == "tensor" and r["unit"] == "TFLOP/s"
+    assert math.isclose(r["achieved"], per_launch / 0.05e-3 / 1e12, rel_tol=1e-12)
+    assert math.isclose(r["frac"], r["achieved"] / 1713.7, rel_tol=1e-12)
+    assert r["peak_is"] == "measured sustained BF16" and r["traffic"] > 0
+    # the back-to-back launch time replaces the event time when given
+    r2 = bench.roofline(kt, {"instances": 900000}, peaks, "bf16_skip", 1000000, 32, frames, conv_launch_ms=0.04)
+    assert math.isclose(r2["avg_ms"], 0.04) and math.isclose(r2["achieved"], per_launch / 0.04e-3 / 1e12)
+    # no measured peaks: the fallback figures, labelled so
+    r3 = bench.roofline(kt, {"instances": 900000}, {}, "bf16_skip", 1000000, 32, frames)
+    assert r3["peak"] == 1700.0 and r3["peak_is"].startswith("fallback")
+    # the FP8 form against twice the BF16 peak
+    r4 = bench.roofline(kt, {"instances": 900000}, peaks, "fp8", 1000000, 32, frames)
+    assert math.isclose(r4["peak"], 2 * 1713.7) and r4["traffic"] is None
+
+
+def test_roofline_of_a_bandwidth_bound_kernel():
+    kt = {"lbs": (10, 10 * 0.035)}
+    r = bench.roofline(kt, {"instances": 900000}, {"hbm_gbs": 6783.5}, "bf16_skip", 1000000, 32, 10)
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert math.isclose(r["achieved"], 1000000 * 160 / 0.035e-3 / 1e9, rel_tol=1e-12)
+    assert r["peak_is"] == "measured copy bandwidth"
+    assert bench.roofline({}, {}, {}, "bf16_skip", 1, 32, 1) is None
