@@ -419,6 +419,26 @@ def gpu_arm(args):
     result["depth_buffer"] = {"ms_per_call": float(np.mean([a.elapsed_time(b) for a, b in dev_])),
                               "sigma_min": thr, "covered_pixels": int(torch.isfinite(Dbuf).sum().item()),
                               "what": "art_render_depth of one 1024^2 view: projection, binning, depth walk"}
+    # view-dependent features (Eq. 2) of degree 2: 9 coefficient vectors per voxel, plain traversal
+    configure(r, "bf16", False)
+    sh_deg = 2
+    coef = 0.3 * torch.randn((oc.n, (sh_deg + 1) ** 2, oc.C), dtype=torch.float32, device="cuda")
+    r.load_sh_features(sh_deg, coef)
+    Fs = torch.empty((RES, RES, oc.C), dtype=torch.bfloat16, device="cuda")
+    As = torch.empty((RES, RES), dtype=torch.float32, device="cuda")
+    r.render_feature_maps(vi0, Fs, As, "bf16")
+    sev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+    for a, b in sev:
+        flush.zero_()
+        a.record(torch.cuda.current_stream())
+        r.render_feature_maps(vi0, Fs, As, "bf16")
+        b.record(torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    result["sh_features"] = {"ms_per_call": float(np.mean([a.elapsed_time(b) for a, b in sev])), "degree": sh_deg,
+                             "what": "art_render_feature_maps of one 1024^2 view with SH features: projection, "
+                                     "binning, one warp per tile evaluating each hit's harmonics"}
+    r.load_sh_features(-1)
+    del coef
     r.close()
 
     def side(form, steps):

@@ -144,6 +144,23 @@ art_status art_set_camera(art_ctx* ctx, int view, int W, int H, float fx, float 
 art_status art_render_feature_maps(art_ctx* ctx, int view, void* F_out, int F_dtype, float* A_out);
 
 /*
+ * View-dependent features (Eq. 2 and the canonical ray direction of
+ * Sec. 3.1): each voxel's feature becomes a set of spherical-harmonics
+ * coefficient vectors k_h (h = l^2 + l + m, l <= degree), and a hit's
+ * feature S = sum_h k_h Y_h(R_i^T d) with Y_h the real orthonormal harmonics
+ * (no Condon-Shortley phase in the real basis), d the unit pixel ray and
+ * R_i the rotation factor of voxel i's blended transform (polar
+ * decomposition).  Later art_render_feature_maps / art_render_frame calls
+ * composite these features (plain traversal only).
+ *   degree  0 .. 3; -1 returns to the per-voxel features of art_load_octree
+ *   coef    [n][(degree+1)^2][C] float, host or device; copied
+ * Errors: ART_ERR_STATE before art_load_octree, ART_ERR_UNSUPPORTED for a
+ * degree above 3; art_render_backward and the learned skip then return
+ * ART_ERR_UNSUPPORTED.  A new art_load_octree returns to the plain features.
+ */
+art_status art_load_sh_features(art_ctx* ctx, int degree, const float* coef);
+
+/*
  * Depth buffer of `view` under the current pose (Sec. 3.1 "Hybrid
  * Rendering": each pixel ray is traced to the first voxel whose density is
  * larger than a threshold, whose distance becomes the pixel's depth): the

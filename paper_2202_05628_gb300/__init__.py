@@ -65,6 +65,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "art_set_camera": [vp, i32, i32, i32, f32, f32, f32, f32, vp, f32, f32],
         "art_render_feature_maps": [vp, i32, vp, i32, vp],
         "art_render_depth": [vp, i32, f32, vp],
+        "art_load_sh_features": [vp, i32, vp],
         "art_load_shader": [vp, ctypes.POINTER(NetDesc), vp, i64, i32],
         "art_shade": [vp, i32, vp, i32, vp],
         "art_render_frame": [vp, i32, vp, vp, vp, vp],
@@ -186,6 +187,11 @@ class Renderer:
     # ------------------------------------------------------------- rendering
     def render_feature_maps(self, view: int, F_out, A_out=None, F_dtype: str = "f32"):
         self._check(_lib.art_render_feature_maps(self._h, view, _ptr(F_out), DTYPES[F_dtype], _ptr(A_out)))
+
+    def load_sh_features(self, degree: int, coef=None):
+        """View-dependent features: coef [n][(degree+1)^2][C] float32 (degree -1: back to plain)."""
+        c = None if coef is None else (coef if hasattr(coef, "data_ptr") else _np(coef, np.float32))
+        self._check(_lib.art_load_sh_features(self._h, int(degree), _ptr(c)))
 
     def render_depth(self, view: int, sigma_min: float, depth_out):
         """Depth buffer: entry distance of the first hit denser than sigma_min (+inf where none)."""

@@ -174,7 +174,7 @@ void free_all(art_ctx* ctx) {
                   ctx->d_shist, ctx->d_sbsum, ctx->d_gN, ctx->d_f8_scale, ctx->d_f8_amax, ctx->d_prop_img,
                   ctx->d_prop_f32, ctx->d_pose_bias, ctx->d_bins, ctx->d_thist, ctx->d_hbin, ctx->d_htau, ctx->d_fbq,
                   ctx->d_seg, ctx->d_items, ctx->d_multi, ctx->d_part, ctx->d_fbq2, ctx->d_tcount, ctx->d_toff,
-                  ctx->d_sortlist, ctx->d_scan_state, ctx->d_agroups};
+                  ctx->d_sortlist, ctx->d_scan_state, ctx->d_agroups, ctx->d_sh, ctx->d_sh_rot};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& L : ctx->layers) {
@@ -342,6 +342,7 @@ art_status art_load_octree(art_ctx* ctx, int64_t n, int depth, const float origi
                            const uint16_t* ijk, const uint8_t* joint_idx, const float* weights,
                            const float* features, int C, int storage_dtype, const float* density) {
   if (!ctx) return ART_ERR_INVALID_ARG;
+  ctx->sh_degree = -1;  // coefficients belong to the previous octree
   if (n <= 0 || n > (int64_t)1 << 25) return fail(ctx, ART_ERR_INVALID_ARG, "n=%lld out of range [1, 2^25]", (long long)n);
   if (depth < 1 || depth > 16) return fail(ctx, ART_ERR_INVALID_ARG, "depth=%d out of range [1, 16]", depth);
   if (!origin || !(extent > 0.0f)) return fail(ctx, ART_ERR_INVALID_ARG, "origin/extent invalid");
@@ -563,6 +564,8 @@ static art_status render_to_device(art_ctx* ctx, int view, void* F, int F_dtype,
   if (st != ART_OK) return st;
   if ((st = ensure_split_buffers(ctx, v)) != ART_OK) return st;
   if (ctx->cfg.skip == ART_SKIP_LEARNED) {  // proposal intervals + coarse check + fallback
+    if (ctx->sh_degree >= 0)
+      return fail(ctx, ART_ERR_UNSUPPORTED, "view-dependent (SH) features use the plain traversal (skip = 0)");
     if (!ctx->prop_loaded) return fail(ctx, ART_ERR_STATE, "learned skip without a proposal (art_load_proposal)");
     if ((st = ensure_skip_buffers(ctx, v)) != ART_OK) return st;
     launch_project(ctx, v, ctx->d_hbin, ctx->d_htau);
@@ -573,6 +576,10 @@ static art_status render_to_device(art_ctx* ctx, int view, void* F, int F_dtype,
   }
   launch_project(ctx, v);
   launch_bin(ctx, v);
+  if (ctx->sh_degree >= 0) {  // view-dependent features (Eq. 2)
+    if ((st = launch_composite_sh(ctx, v, F, F_dtype, A)) != ART_OK) return st;
+    return launch_check(ctx, "render_feature_maps (SH)");
+  }
   if ((st = launch_composite(ctx, v, F, F_dtype, A)) != ART_OK) return st;
   return launch_check(ctx, "render_feature_maps");
 }
@@ -605,6 +612,27 @@ art_status art_render_feature_maps(art_ctx* ctx, int view, void* F_out, int F_dt
     if (A_out && !a_dev) cudaMemcpyAsync(A_out, A, npx * 4, cudaMemcpyDeviceToHost, ctx->stream);
     return sync_check(ctx, "render_feature_maps (copy out)");
   }
+  return ART_OK;
+}
+
+art_status art_load_sh_features(art_ctx* ctx, int degree, const float* coef) {
+  if (!ctx) return ART_ERR_INVALID_ARG;
+  if (ctx->n == 0) return fail(ctx, ART_ERR_STATE, "load_sh_features before load_octree");
+  if (degree < 0) {  // back to the plain per-voxel features
+    ctx->sh_degree = -1;
+    return ART_OK;
+  }
+  if (degree > kShMaxDegree)
+    return fail(ctx, ART_ERR_UNSUPPORTED, "SH degree %d: degrees 0 .. %d are built", degree, kShMaxDegree);
+  if (!coef) return fail(ctx, ART_ERR_INVALID_ARG, "coef is null");
+  const size_t count = (size_t)ctx->n * (size_t)((degree + 1) * (degree + 1)) * (size_t)ctx->C;
+  art_status st;
+  if ((st = alloc(ctx, &ctx->d_sh, count, "SH coefficients")) != ART_OK) return st;
+  if ((st = alloc(ctx, &ctx->d_sh_rot, 9 * (size_t)ctx->n, "SH rotations")) != ART_OK) return st;
+  cudaError_t e = cudaMemcpyAsync(ctx->d_sh, coef, sizeof(float) * count, cudaMemcpyDefault, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "copy SH coefficients");
+  if ((st = sync_check(ctx, "load_sh_features")) != ART_OK) return st;
+  ctx->sh_degree = degree;
   return ART_OK;
 }
 
@@ -875,6 +903,7 @@ art_status art_render_backward(art_ctx* ctx, int view, const float* F, const flo
   if (!ctx) return ART_ERR_INVALID_ARG;
   if (view < 0 || view >= kMaxViews || !ctx->view_set[view]) return fail(ctx, ART_ERR_STATE, "view %d not set", view);
   if (!ctx->posed) return fail(ctx, ART_ERR_STATE, "render_backward before set_pose");
+  if (ctx->sh_degree >= 0) return fail(ctx, ART_ERR_UNSUPPORTED, "render_backward: view-dependent (SH) features");
   if (!F || !A || !dF || !d_features || !d_density || !d_weights)
     return fail(ctx, ART_ERR_INVALID_ARG, "null pointer");
   const void* dev[] = {F, A, dF, d_features, d_density, d_weights};

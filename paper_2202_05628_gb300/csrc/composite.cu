@@ -23,7 +23,7 @@
 namespace art {
 namespace {
 
-enum Mode { kPlain = 0, kDebug = 1, kLabel = 2, kInterval = 3 };
+enum Mode { kPlain = 0, kDebug = 1, kLabel = 2, kInterval = 3, kSH = 4 };
 
 // Inputs and outputs of the learned-skip modes.
 struct SkipArgs {
@@ -35,7 +35,85 @@ struct SkipArgs {
   int qword;            // status word counting the queue
   float* labels;        // kLabel: [H][W][3]
   uchar2* lbins;        // kLabel: [H][W]
+  const float* sh_coef; // kSH: [n][(L+1)^2][C] spherical-harmonics coefficients
+  const float* sh_rot;  // kSH: [n][9] per voxel the map of world directions into its canonical frame
+  int sh_degree;        // kSH: L (0 .. kShMaxDegree)
 };
+
+// Real orthonormal spherical harmonics of degree <= L (<= kShMaxDegree) at
+// the unit direction (x, y, z) (Eq. 2): Y[l*l + l + m],
+//   Y_{l,0} = K_l^0 Q_l^0(z),  Y_{l,+-m} = sqrt(2) K_l^m Q_l^m(z) {Re, Im}((x + i y)^m)  (m > 0),
+// K_l^m = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!), Q_l^m the associated Legendre
+// function without the Condon-Shortley phase divided by sin(theta)^m:
+// Q_m^m = (2m-1)!!, Q_{m+1}^m = (2m+1) z Q_m^m,
+// Q_l^m = ((2l-1) z Q_{l-1}^m - (l+m-1) Q_{l-2}^m) / (l-m).
+__device__ __forceinline__ void sh_basis(int L, float x, float y, float z, float (&Y)[kShMaxBases]) {
+  float cr = 1.0f, ci = 0.0f;  // (x + i y)^m
+  float qmm = 1.0f;            // (2m-1)!!
+#pragma unroll
+  for (int m = 0; m <= kShMaxDegree; ++m) {
+    if (m > 0) {
+      const float r = cr * x - ci * y, i = cr * y + ci * x;
+      cr = r;
+      ci = i;
+      qmm *= (float)(2 * m - 1);
+    }
+    float q2 = 0.0f, q1 = qmm;  // Q_{l-2}^m, Q_{l-1}^m
+#pragma unroll
+    for (int l = m; l <= kShMaxDegree; ++l) {
+      float q;
+      if (l == m) {
+        q = qmm;
+      } else if (l == m + 1) {
+        q = (float)(2 * m + 1) * z * qmm;
+      } else {
+        q = ((float)(2 * l - 1) * z * q1 - (float)(l + m - 1) * q2) / (float)(l - m);
+      }
+      if (l > m) {
+        q2 = q1;
+        q1 = q;
+      }
+      float ratio = 1.0f;  // (l-m)! / (l+m)!
+#pragma unroll
+      for (int k = l - m + 1; k <= l + m; ++k) ratio /= (float)k;
+      const float K = sqrtf((float)(2 * l + 1) * 0.0795774715459476678f * ratio);  // 1 / (4 pi)
+      if (l <= L) {
+        if (m == 0) {
+          Y[l * l + l] = K * q;
+        } else {
+          Y[l * l + l + m] = 1.41421356237309505f * K * q * cr;
+          Y[l * l + l - m] = 1.41421356237309505f * K * q * ci;
+        }
+      }
+    }
+  }
+}
+
+// The view-dependent feature of voxel vid along the unit ray d (Eq. 2):
+// S = sum_h k_h Y_h(P d), P the voxel's map of world directions into its
+// canonical frame.
+template <int C>
+__device__ __forceinline__ void sh_feature(const SkipArgs& sk, uint32_t vid, float d0, float d1, float d2, float* f) {
+  const float* P = sk.sh_rot + 9 * (size_t)vid;
+  const float x = P[0] * d0 + P[1] * d1 + P[2] * d2;
+  const float y = P[3] * d0 + P[4] * d1 + P[5] * d2;
+  const float z = P[6] * d0 + P[7] * d1 + P[8] * d2;
+  float Y[kShMaxBases];
+#pragma unroll
+  for (int h = 0; h < kShMaxBases; ++h) Y[h] = 0.0f;
+  sh_basis(sk.sh_degree, x, y, z, Y);
+  const int H = (sk.sh_degree + 1) * (sk.sh_degree + 1);
+  const float* k = sk.sh_coef + (size_t)vid * H * C;
+#pragma unroll
+  for (int c = 0; c < C; ++c) f[c] = 0.0f;
+#pragma unroll
+  for (int h = 0; h < kShMaxBases; ++h) {
+    if (h < H) {
+#pragma unroll
+      for (int c = 0; c < C; ++c) f[c] = fmaf(__ldg(k + h * C + c), Y[h], f[c]);
+    }
+  }
+}
 
 // Inclusive prefix sums of the tile's depth-bin histogram into pre[64];
 // returns the total.
@@ -66,7 +144,8 @@ __device__ __forceinline__ void composite_tile(const int tile, const Seg& sg,
                                                unsigned long long* __restrict__ status, const HitLog& dbg,
                                                const SkipArgs& sk) {
   constexpr bool DBG = MODE == kDebug;
-  constexpr bool FEAT = MODE != kLabel;  // labels need densities only
+  constexpr bool SH = MODE == kSH;                 // features evaluated per hit from SH coefficients
+  constexpr bool FEAT = MODE != kLabel && !SH;  // staged feature rows (labels need densities only)
   constexpr int RING = Ring<C, TF>::kChunks;
   __shared__ float4 s_b0[NT], s_b1[NT], s_b2[NT];
   __shared__ float s_thr[NT];
@@ -147,10 +226,12 @@ __device__ __forceinline__ void composite_tile(const int tile, const Seg& sg,
       sig = s_sig[ch % RING][sl];
       vid = s_vid[ch % RING][sl];
       if constexpr (FEAT) row_to_float<C>(&s_feat[ch % RING][sl][0], f);
+      if constexpr (SH) sh_feature<C>(sk, vid, d0, d1, d2, f);
     } else {  // staged long ago: read the voxel again
       vid = vals[rg.x + h.pos];
       sig = rec[4 * (size_t)vid + 3].x;
       if constexpr (FEAT) load_feat<C>(feat + (size_t)vid * C, f);
+      if constexpr (SH) sh_feature<C>(sk, vid, d0, d1, d2, f);
     }
     if constexpr (DBG) {
       if (n_used < dbg.cap) {
@@ -162,7 +243,7 @@ __device__ __forceinline__ void composite_tile(const int tile, const Seg& sg,
     }
     float e = expf(-sig * (h.t1 - h.t0));
     float w = T * (1.0f - e);
-    if constexpr (FEAT) {
+    if constexpr (FEAT || SH) {
 #pragma unroll
       for (int c = 0; c < C; ++c) acc[c] = fmaf(w, f[c], acc[c]);
     }
@@ -645,6 +726,10 @@ void launch_c(art_ctx* ctx, const ViewParams& v, void* F, float* A, const HitLog
     auto kfn = composite_kernel<C, TF, TO, kLabel>;
     ART_LAUNCH(ctx, "composite_labels", kfn, ntiles, 32, 0, ctx->d_ranges, ctx->d_keys, ctx->d_vals, ctx->d_rec,
                ctx->d_rect, feat, v, ctx->cfg.tau, (TO*)F, A, ctx->d_status, HitLog{}, sk);
+  } else if (mode == kSH) {  // sequential walk, one warp per tile
+    auto kfn = composite_kernel<C, TF, TO, kSH>;
+    ART_LAUNCH(ctx, "composite_sh", kfn, ntiles, 32, 0, ctx->d_ranges, ctx->d_keys, ctx->d_vals, ctx->d_rec,
+               ctx->d_rect, feat, v, ctx->cfg.tau, (TO*)F, A, ctx->d_status, HitLog{}, sk);
   } else {
     split_walk<C, TF, TO>(ctx, v, F, A, mode, sk);
   }
@@ -684,6 +769,44 @@ art_status dispatch(art_ctx* ctx, const ViewParams& v, void* F, int F_dtype, flo
 art_status launch_composite(art_ctx* ctx, const ViewParams& v, void* F, int F_dtype, float* A, const void* dbg_log) {
   const HitLog* dbg = (const HitLog*)dbg_log;
   return dispatch(ctx, v, F, F_dtype, A, dbg, dbg ? kDebug : kPlain, SkipArgs{});
+}
+
+// Per voxel, the rotation that maps world directions into its canonical
+// frame: the orthogonal polar factor of its unit-cube map A_lin^-1 / h
+// (A_lin = R S gives A_lin^-1 = S^-1 R^T, whose orthogonal factor is R^T),
+// by scaled Newton steps X <- (g X + (g X)^-T) / 2, g = |det X|^(-1/3).
+__global__ void __launch_bounds__(256) sh_rot_kernel(int64_t n, const float4* __restrict__ rec, float* __restrict__ rot) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float4 r0 = rec[4 * i], r1 = rec[4 * i + 1], r2 = rec[4 * i + 2], r3 = rec[4 * i + 3];
+  float X[9] = {r0.x, r0.y, r0.z, r1.x, r1.y, r1.z, r2.x, r2.y, r2.z};
+  if (r3.y == 0.0f) {  // dropped voxel: never listed
+#pragma unroll
+    for (int k = 0; k < 9; ++k) X[k] = (k % 4 == 0) ? 1.0f : 0.0f;
+  } else {
+#pragma unroll 1
+    for (int it = 0; it < 12; ++it) {
+      const float cof[9] = {X[4] * X[8] - X[5] * X[7], X[5] * X[6] - X[3] * X[8], X[3] * X[7] - X[4] * X[6],
+                            X[2] * X[7] - X[1] * X[8], X[0] * X[8] - X[2] * X[6], X[1] * X[6] - X[0] * X[7],
+                            X[1] * X[5] - X[2] * X[4], X[2] * X[3] - X[0] * X[5], X[0] * X[4] - X[1] * X[3]};
+      const float det = X[0] * cof[0] + X[1] * cof[1] + X[2] * cof[2];
+      const float g = it < 6 ? 1.0f / cbrtf(fabsf(det)) : 1.0f;  // scaling speeds the first steps
+#pragma unroll
+      for (int k = 0; k < 9; ++k) X[k] = 0.5f * (g * X[k] + cof[k] / (g * det));
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 9; ++k) rot[9 * i + k] = X[k];
+}
+
+art_status launch_composite_sh(art_ctx* ctx, const ViewParams& v, void* F, int F_dtype, float* A) {
+  ART_LAUNCH(ctx, "sh_rot", sh_rot_kernel, (unsigned)((ctx->n + 255) / 256), 256, 0, ctx->n,
+             (const float4*)ctx->d_rec, ctx->d_sh_rot);
+  SkipArgs sk{};
+  sk.sh_coef = ctx->d_sh;
+  sk.sh_rot = ctx->d_sh_rot;
+  sk.sh_degree = ctx->sh_degree;
+  return dispatch(ctx, v, F, F_dtype, A, nullptr, kSH, sk);
 }
 
 art_status launch_composite_skip(art_ctx* ctx, const ViewParams& v, void* F, int F_dtype, float* A) {

@@ -136,6 +136,9 @@ struct art_ctx {
   uint32_t* d_agroups = nullptr;  // groups of four consecutive tiles with instances (unordered)
   unsigned long long* d_status = nullptr;
   unsigned long long* h_status = nullptr;  // pinned
+  float* d_sh = nullptr;        // [n][(L+1)^2][C] spherical-harmonics coefficients (view-dependent features)
+  float* d_sh_rot = nullptr;    // [n][9] world -> canonical direction map per voxel
+  int sh_degree = -1;           // L, or -1: plain features
   bool attr_tile_sort = false;  // large shared-memory attributes set on this context's device
   bool attr_proposal = false;
 
@@ -252,6 +255,9 @@ void launch_depth(art_ctx* ctx, const ViewParams& v, float sigma_min, float* dep
 // ---- composite (composite.cu)
 art_status launch_composite(art_ctx* ctx, const ViewParams& v, void* F, int F_dtype, float* A,
                             const void* hit_log = nullptr);
+// View-dependent features (Eq. 2): each hit's feature from its SH
+// coefficients at the ray direction in its canonical frame (sequential walk).
+art_status launch_composite_sh(art_ctx* ctx, const ViewParams& v, void* F, int F_dtype, float* A);
 // Learned skip: composite over the proposal intervals (ctx->d_bins), coarse
 // check against ctx->d_thist, then the full traversal of the queued tiles.
 art_status launch_composite_skip(art_ctx* ctx, const ViewParams& v, void* F, int F_dtype, float* A);
@@ -259,6 +265,8 @@ art_status launch_composite_skip(art_ctx* ctx, const ViewParams& v, void* F, int
 art_status launch_composite_labels(art_ctx* ctx, const ViewParams& v, float* labels, uint8_t* bins);
 // One-warp blocks of the composite walk that fit on an SM (C channels of feat_bytes).
 int composite_blocks_per_sm(int C, int feat_bytes);
+constexpr int kShMaxDegree = 3;  // view-dependent features: spherical harmonics up to this degree
+constexpr int kShMaxBases = (kShMaxDegree + 1) * (kShMaxDegree + 1);
 constexpr int kPropBins = 64;          // proposal depth bins over [znear, zfar]
 constexpr float kLabelWmin = 1e-6f;    // significant hit: weight above this
 constexpr float kLabelBudget = 0.4f;   // label bins keep the coarse bound under this fraction of max_missed
