@@ -282,6 +282,21 @@ def render_sh(octree, A: np.ndarray, cam, L: int, coef, tau: float = TAU_DEFAULT
     return dict(F=F, A=Am)
 
 
+def render_sh_backward(octree, A: np.ndarray, cam, L: int, gF, tau: float = TAU_DEFAULT, density=None,
+                       C: Optional[int] = None) -> np.ndarray:
+    """dL/dcoef [n, (L+1)^2, C] of render_sh's feature map for dL/dF = gF [H, W, C]."""
+    gF = _f64(gF)
+    C = gF.shape[2] if C is None else C
+    n, H = octree.n, (L + 1) ** 2
+    b = _Bound(octree, np.asarray(A).reshape(-1, 12), np.zeros((n, C)), density)
+    k = _cam(cam)
+    g = np.zeros((n, H, C))
+    if _L().orc_render_sh_backward(ctypes.byref(b.s), ctypes.byref(k), ctypes.c_double(tau), ctypes.c_int(L),
+                                   _p(gF), _p(g)) != 0:
+        raise ValueError("orc_render_sh_backward failed (degree out of range or allocation)")
+    return g
+
+
 def pixels(octree, A: np.ndarray, cam, px: Sequence[int], py: Sequence[int],
            tau: float = TAU_DEFAULT, features=None, density=None) -> dict:
     """Sampled pixels, each by brute force over every voxel."""

@@ -23,8 +23,9 @@
  *     coarse optical-depth bound per screen tile and depth bin (project
  *     addition; the paper's nearest passage is the early-stop rule)
  *   - the analytic gradient of the composite with respect to features,
- *     densities and the blended transforms, and of LBS with respect to the
- *     skinning weights (project addition; the paper trains end to end).
+ *     densities and the blended transforms, of LBS with respect to the
+ *     skinning weights, and of the view-dependent feature map with respect
+ *     to the SH coefficients (project addition; the paper trains end to end).
  *
  * Readings where the paper is silent or garbled:
  *   - T_i uses the exclusive sum j < i (Eq. 6 prints j <= i; with j < i the
@@ -694,6 +695,64 @@ int orc_render_sh(const orc_scene* s, const orc_cam* c, double tau, int L, const
     }
     free(buf);
   }
+  free(cand.off);
+  free(cand.vid);
+  free(rot);
+  free(info);
+  return 0;
+}
+
+/*
+ * Gradient of the view-dependent feature map with respect to the SH
+ * coefficients: for dL/dF = gF [H*W][C], accumulates
+ *   dL/dcoef[i][h][c] = sum over the pixels whose composite uses hit i of
+ *                        w_i Y_h(R_i^T d) gF[c],   w_i = T_i (1 - exp(-sigma_i delta_i)),
+ * over the hits composited before the early stop (F is linear in the
+ * coefficients).  gcoef [n][(L+1)^2][C], zeroed here.  Serial over pixels.
+ * Returns 0, or -1 on allocation failure or a degree out of range.
+ */
+int orc_render_sh_backward(const orc_scene* s, const orc_cam* c, double tau, int L, const double* gF,
+                           double* gcoef) {
+  if (L < 0 || L > ORC_SH_LMAX) return -1;
+  const int H = (L + 1) * (L + 1), C = s->C;
+  vox_info* info = all_info(s, c);
+  if (!info) return -1;
+  double* rot = (double*)malloc(sizeof(double) * 9 * (size_t)(s->n > 0 ? s->n : 1));
+  cand_t cand = {0, 0};
+  if (!rot || build_candidates(s, c, info, &cand) != 0) {
+    free(rot);
+    free(info);
+    return -1;
+  }
+  for (int64_t i = 0; i < s->n; ++i)
+    if (!info[i].ok || orc_polar_rotation(s->A + 12 * i, rot + 9 * i) != 0) info[i].ok = 0;
+  memset(gcoef, 0, sizeof(double) * (size_t)s->n * H * C);
+  hit_t* buf = NULL;
+  int cap = 0;
+  double Y[(ORC_SH_LMAX + 1) * (ORC_SH_LMAX + 1)];
+  const int64_t npx = (int64_t)c->W * c->H;
+  for (int64_t p = 0; p < npx; ++p) {
+    const int x = (int)(p % c->W), y = (int)(p / c->W);
+    int m = pixel_hits(s, c, info, cand.vid + cand.off[p], cand.off[p + 1] - cand.off[p], x, y, &buf, &cap);
+    double o[3], d[3];
+    cam_ray(c, x, y, o, d);
+    double optical = 0.0;
+    for (int q = 0; q < m; ++q) {
+      const int64_t id = buf[q].id;
+      const double* R = rot + 9 * id;
+      const double dc[3] = {R[0] * d[0] + R[3] * d[1] + R[6] * d[2], R[1] * d[0] + R[4] * d[1] + R[7] * d[2],
+                            R[2] * d[0] + R[5] * d[1] + R[8] * d[2]};
+      orc_sh_basis(L, dc, Y);
+      const double sig = s->sigma[id], delta = buf[q].t1 - buf[q].t0;
+      const double w = exp(-optical) * (1.0 - exp(-sig * delta));
+      double* gk = gcoef + (size_t)id * H * C;
+      for (int h = 0; h < H; ++h)
+        for (int k = 0; k < C; ++k) gk[(size_t)h * C + k] += w * Y[h] * gF[p * C + k];
+      optical += sig * delta;
+      if (exp(-optical) < tau) break;
+    }
+  }
+  free(buf);
   free(cand.off);
   free(cand.vid);
   free(rot);

@@ -1113,3 +1113,37 @@ def test_sampled_pixels_equal_the_full_render():
     np.testing.assert_allclose(o["F"], full["F"][py, px], atol=1e-14)
     np.testing.assert_allclose(o["A"], full["A"][py, px], atol=1e-14)
     assert np.all(o["nhit"] == full["nhit"][py, px])
+
+
+def test_render_sh_is_linear_and_its_coefficient_gradient():
+    # F is linear in the coefficients: F(a k1 + b k2) = a F(k1) + b F(k2), and
+    # the gradient of <gF, F> is exact under a central difference; at degree
+    # 0 it is Y_00 times the plain render's feature gradient.
+    sc = sg.preset("mini")
+    oc = sc.octree
+    cam = sg.orbit_camera(sc.centroid, 16, 12, az_deg=40.0, fov_deg=8.0)
+    _, A, _ = oracle.pose_transforms(sc, sg.random_pose(5))
+    rng = np.random.default_rng(11)
+    L, C = 2, 3
+    k1 = rng.standard_normal((oc.n, 9, C))
+    k2 = rng.standard_normal((oc.n, 9, C))
+    F1 = oracle.render_sh(oc, A, cam, L, k1)["F"]
+    F2 = oracle.render_sh(oc, A, cam, L, k2)["F"]
+    F12 = oracle.render_sh(oc, A, cam, L, 0.7 * k1 - 1.3 * k2)["F"]
+    np.testing.assert_allclose(F12, 0.7 * F1 - 1.3 * F2, atol=1e-13)
+    gF = rng.standard_normal((cam.H, cam.W, C))
+    g = oracle.render_sh_backward(oc, A, cam, L, gF)
+    hit = np.argwhere(np.abs(g).sum((1, 2)) > 0)[:, 0]
+    assert len(hit) > 20
+    eps = 1e-3
+    for i in hit[:: max(1, len(hit) // 6)][:6]:
+        for h, c in [(0, 0), (4, 1), (8, 2)]:
+            kp, km = k1.copy(), k1.copy()
+            kp[i, h, c] += eps
+            km[i, h, c] -= eps
+            fd = (np.sum(gF * oracle.render_sh(oc, A, cam, L, kp)["F"]) -
+                  np.sum(gF * oracle.render_sh(oc, A, cam, L, km)["F"])) / (2 * eps)
+            np.testing.assert_allclose(g[i, h, c], fd, rtol=1e-7, atol=1e-10)
+    g0 = oracle.render_sh_backward(oc, A, cam, 0, gF)
+    gfeat, _, _ = oracle.render_backward(oc, A, cam, gF, np.zeros((cam.H, cam.W)), features=np.zeros((oc.n, C)))
+    np.testing.assert_allclose(g0[:, 0, :], gfeat * (0.5 / math.sqrt(math.pi)), atol=1e-13)
