@@ -69,6 +69,8 @@ def _L():
             _lib = ctypes.CDLL(_LIB_PATH)
             _lib.orc_render.restype = ctypes.c_int64
             _lib.orc_tile_pairs.restype = ctypes.c_int64
+            _lib.orc_grid_snap.restype = ctypes.c_int64
+            _lib.orc_render_grid.restype = ctypes.c_int64
     return _lib
 
 
@@ -227,6 +229,50 @@ def depth(octree, A: np.ndarray, cam, sigma_min: float, density=None) -> dict:
     if _L().orc_depth(ctypes.byref(b.s), ctypes.byref(k), ctypes.c_double(sigma_min), _p(D), _p(ch)) != 0:
         raise MemoryError("orc_depth failed")
     return dict(depth=D, chord=ch)
+
+
+# ---------------------------------------------------------------------------
+# The paper's per-frame index: warped centres snapped to the leaf lattice
+# ---------------------------------------------------------------------------
+
+def grid_snap(octree, A: np.ndarray) -> dict:
+    """Each voxel's lattice cell floor((A_i p_i^c - origin) / h) [n, 3], the
+    survivor of its cell [n] (smallest id; -1 = not placed) and the number of
+    occupied cells."""
+    b = _Bound(octree, np.asarray(A).reshape(-1, 12), np.zeros((octree.n, 1)))
+    cell = np.zeros((octree.n, 3), np.int64)
+    win = np.zeros(octree.n, np.int64)
+    nc = _L().orc_grid_snap(ctypes.byref(b.s), _p(cell), _p(win))
+    if nc < 0:
+        raise MemoryError("orc_grid_snap failed")
+    return dict(cell=cell, winner=win, n_cells=int(nc))
+
+
+def render_grid(octree, A: np.ndarray, cam, tau: float = TAU_DEFAULT, features=None, density=None) -> dict:
+    """F [H,W,C], A [H,W], hit counts [H,W] of the snapped index: the occupied
+    lattice cells as axis-aligned boxes carrying their survivors' features and
+    densities, composited as the voxel path does."""
+    b = _Bound(octree, np.asarray(A).reshape(-1, 12), features, density)
+    k = _cam(cam)
+    F = np.zeros((cam.H, cam.W, b.feat.shape[1]))
+    Am = np.zeros((cam.H, cam.W))
+    nhit = np.zeros((cam.H, cam.W), np.int32)
+    nc = _L().orc_render_grid(ctypes.byref(b.s), ctypes.byref(k), ctypes.c_double(tau), _p(F), _p(Am), _p(nhit))
+    if nc < 0:
+        raise MemoryError("orc_render_grid failed")
+    return dict(F=F, A=Am, nhit=nhit, n_cells=int(nc))
+
+
+def vrt_loss(octree, A: np.ndarray, features=None, lam: float = 1.0) -> float:
+    """The voxel regularisation term (Sec. 3.1, "Training"): lam times the mean
+    over the placed voxels of || Q(p_i^t, T^t) - f_i ||_1, Q returning the
+    feature of the survivor of the cell that p_i^t falls in."""
+    f = _f64(octree.features if features is None else features)
+    win = grid_snap(octree, A)["winner"]
+    placed = win >= 0
+    if not placed.any():
+        return 0.0
+    return float(lam * np.abs(f[win[placed]] - f[placed]).sum(1).mean())
 
 
 # ---------------------------------------------------------------------------

@@ -18,6 +18,10 @@
  *     than a threshold                                          (Sec. 3.1, "Hybrid Rendering")
  *   - view-dependent features: spherical-harmonics coefficients evaluated at
  *     the ray direction in the voxel's canonical frame          (Eq. 2, Sec. 3.1)
+ *   - the paper's own per-frame index: warped voxel centres snapped to the
+ *     lattice of the canonical leaves, collisions resolved, the query Q of
+ *     the voxel regularisation term, and the render of the occupied cells
+ *                                                              (Sec. 3.1, "Dynamic Volume Rendering", "Training")
  *   - the learned ray-interval proposal's labels, the composite restricted to
  *     a depth interval with the exact transmittance mass it loses, and the
  *     coarse optical-depth bound per screen tile and depth bin (project
@@ -49,6 +53,12 @@
  *     decomposition of its linear part.
  *   - a voxel whose blended linear part has det < 1e-3, or any of whose eight
  *     warped corners has camera z <= 1e-6, is not rendered.
+ *   - the per-frame index is the lattice of the canonical octree's leaves
+ *     (same origin and leaf size, unbounded); a voxel goes to the cell
+ *     holding its warped centre; of the voxels that collide in one cell the
+ *     smallest id survives (the paper says features are overwritten, not
+ *     which); a ray composites the occupied cells it crosses, each an
+ *     axis-aligned leaf box with its survivor's feature and density.
  */
 #include <math.h>
 #include <stdint.h>
@@ -281,9 +291,10 @@ typedef struct {
   double dmin, dmax;      /* distance bounds |c - o| -+ r */
 } vox_info;
 
-static void voxel_info(const orc_scene* s, const orc_cam* c, int64_t i, vox_info* v) {
-  const double* A = s->A + 12 * i;
-  for (int a = 0; a < 3; ++a) v->lo[a] = s->origin[a] + (double)s->ijk[3 * i + a] * s->h;
+/* The box A * [lo, lo + h]^3 seen from camera c: inverse transform, validity,
+ * projected bounding box and distance bounds. */
+static void box_info(const double A[12], const double lo[3], double h, const orc_cam* c, vox_info* v) {
+  for (int a = 0; a < 3; ++a) v->lo[a] = lo[a];
   v->ok = det3(A, 4) >= ORC_DET_MIN && affine_inv(A, v->Ainv);
   if (!v->ok) return;
   double o[3];
@@ -291,15 +302,15 @@ static void voxel_info(const orc_scene* s, const orc_cam* c, int64_t i, vox_info
     o[a] = -(c->w2c[0 * 4 + a] * c->w2c[3] + c->w2c[1 * 4 + a] * c->w2c[7] + c->w2c[2 * 4 + a] * c->w2c[11]);
   double cw[3], corners[8][3];
   for (int a = 0; a < 3; ++a) {
-    double cc[3] = {v->lo[0] + 0.5 * s->h, v->lo[1] + 0.5 * s->h, v->lo[2] + 0.5 * s->h};
+    double cc[3] = {v->lo[0] + 0.5 * h, v->lo[1] + 0.5 * h, v->lo[2] + 0.5 * h};
     cw[a] = A[a * 4] * cc[0] + A[a * 4 + 1] * cc[1] + A[a * 4 + 2] * cc[2] + A[a * 4 + 3];
   }
   v->umin = v->vmin = INFINITY;
   v->umax = v->vmax = -INFINITY;
   double r = 0.0;
   for (int q = 0; q < 8; ++q) {
-    double p[3] = {v->lo[0] + ((q & 1) ? s->h : 0.0), v->lo[1] + ((q & 2) ? s->h : 0.0),
-                   v->lo[2] + ((q & 4) ? s->h : 0.0)};
+    double p[3] = {v->lo[0] + ((q & 1) ? h : 0.0), v->lo[1] + ((q & 2) ? h : 0.0),
+                   v->lo[2] + ((q & 4) ? h : 0.0)};
     double dd = 0;
     for (int a = 0; a < 3; ++a) {
       corners[q][a] = A[a * 4] * p[0] + A[a * 4 + 1] * p[1] + A[a * 4 + 2] * p[2] + A[a * 4 + 3];
@@ -323,6 +334,12 @@ static void voxel_info(const orc_scene* s, const orc_cam* c, int64_t i, vox_info
                    (cw[2] - o[2]) * (cw[2] - o[2]));
   v->dmin = dc - r;
   v->dmax = dc + r;
+}
+
+static void voxel_info(const orc_scene* s, const orc_cam* c, int64_t i, vox_info* v) {
+  double lo[3];
+  for (int a = 0; a < 3; ++a) lo[a] = s->origin[a] + (double)s->ijk[3 * i + a] * s->h;
+  box_info(s->A + 12 * i, lo, s->h, c, v);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -559,6 +576,135 @@ int orc_depth(const orc_scene* s, const orc_cam* c, double sigma_min, double* de
   free(cand.vid);
   free(info);
   return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The paper's own per-frame index (Sec. 3.1, "Dynamic Volume Rendering",     */
+/* and the query operator Q of the voxel regularisation term, "Training").   */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  int64_t c[3];
+  int64_t id;
+} snap_t;
+
+static int snap_cmp(const void* a, const void* b) {
+  const snap_t* x = (const snap_t*)a;
+  const snap_t* y = (const snap_t*)b;
+  for (int k = 0; k < 3; ++k)
+    if (x->c[k] != y->c[k]) return x->c[k] < y->c[k] ? -1 : 1;
+  return (x->id > y->id) - (x->id < y->id);
+}
+
+/*
+ * Places each voxel's warped centre p_i^t = A_i p_i^c (Eq. 4, p_i^c the centre
+ * of its canonical cube) in the cell floor((p_i^t - origin) / h) of the
+ * lattice of the canonical octree's leaves: the index the paper rebuilds
+ * under every pose.  Voxels that land in one cell collide and one survives;
+ * Q(p, T^t) returns the survivor of the cell holding p.  Readings: the lattice
+ * is the canonical octree's (origin, leaf size h) without bounds; the
+ * survivor of a collision is the smallest voxel id; a voxel whose blend has
+ * det < 1e-3 (or a centre beyond 2^40 cells) is not placed.
+ * cell [n][3]: lattice coordinates (any sign; 0 when not placed);
+ * winner [n]: the survivor of voxel i's cell, -1 when i is not placed.
+ * Returns the number of occupied cells, or -1 on allocation failure.
+ */
+int64_t orc_grid_snap(const orc_scene* s, int64_t* cell, int64_t* winner) {
+  snap_t* e = (snap_t*)malloc(sizeof(snap_t) * (size_t)(s->n > 0 ? s->n : 1));
+  if (!e) return -1;
+  int64_t m = 0;
+  for (int64_t i = 0; i < s->n; ++i) {
+    const double* A = s->A + 12 * i;
+    winner[i] = -1;
+    cell[3 * i] = cell[3 * i + 1] = cell[3 * i + 2] = 0;
+    if (det3(A, 4) < ORC_DET_MIN) continue;
+    double pc[3], q[3];
+    for (int a = 0; a < 3; ++a) pc[a] = s->origin[a] + ((double)s->ijk[3 * i + a] + 0.5) * s->h;
+    int ok = 1;
+    for (int a = 0; a < 3; ++a) {
+      double p = A[a * 4] * pc[0] + A[a * 4 + 1] * pc[1] + A[a * 4 + 2] * pc[2] + A[a * 4 + 3];
+      q[a] = floor((p - s->origin[a]) / s->h);
+      if (!(fabs(q[a]) <= 1099511627776.0)) ok = 0;
+    }
+    if (!ok) continue;
+    for (int a = 0; a < 3; ++a) e[m].c[a] = cell[3 * i + a] = (int64_t)q[a];
+    e[m].id = i;
+    ++m;
+  }
+  qsort(e, (size_t)m, sizeof(snap_t), snap_cmp);
+  int64_t cells = 0;
+  for (int64_t k = 0; k < m;) {
+    int64_t j = k;
+    while (j < m && e[j].c[0] == e[k].c[0] && e[j].c[1] == e[k].c[1] && e[j].c[2] == e[k].c[2]) {
+      winner[e[j].id] = e[k].id;
+      ++j;
+    }
+    ++cells;
+    k = j;
+  }
+  free(e);
+  return cells;
+}
+
+/*
+ * Renders the snapped index: each occupied cell is the axis-aligned box
+ * origin + h [cell, cell + 1]^3 with its survivor's feature and density, and
+ * each pixel's ray composites the cells it crosses front to back as the
+ * voxel path does (Eq. 5, Eq. 6, early stop), in the order (t0, t1,
+ * survivor id).  A cell with a corner at camera z <= 1e-6 is not rendered.
+ * F [H*W][C], Aout [H*W], nhit [H*W] (may be NULL).  Returns the number of
+ * occupied cells, or -1 on allocation failure.
+ */
+int64_t orc_render_grid(const orc_scene* s, const orc_cam* c, double tau, double* F, double* Aout,
+                        int32_t* nhit) {
+  static const double I[12] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0};
+  const size_t n1 = (size_t)(s->n > 0 ? s->n : 1);
+  int64_t* cell = (int64_t*)malloc(sizeof(int64_t) * 3 * n1);
+  int64_t* win = (int64_t*)malloc(sizeof(int64_t) * n1);
+  vox_info* info = (vox_info*)malloc(sizeof(vox_info) * n1);
+  double* sig = (double*)malloc(sizeof(double) * n1);
+  double* feat = (double*)malloc(sizeof(double) * n1 * (size_t)s->C);
+  int64_t nc = (cell && win && info && sig && feat) ? orc_grid_snap(s, cell, win) : -1;
+  cand_t cand = {0, 0};
+  if (nc >= 0) {
+    int64_t k = 0;
+    for (int64_t i = 0; i < s->n; ++i) {
+      if (win[i] != i) continue;
+      double lo[3];
+      for (int a = 0; a < 3; ++a) lo[a] = s->origin[a] + (double)cell[3 * i + a] * s->h;
+      box_info(I, lo, s->h, c, info + k);
+      sig[k] = s->sigma[i];
+      memcpy(feat + (size_t)k * s->C, s->feat + (size_t)i * s->C, sizeof(double) * (size_t)s->C);
+      ++k;
+    }
+    orc_scene g = {nc, s->C, s->h, {s->origin[0], s->origin[1], s->origin[2]}, NULL, NULL, feat, sig};
+    if (build_candidates(&g, c, info, &cand) != 0) {
+      nc = -1;
+    } else {
+      const int64_t npx = (int64_t)c->W * c->H;
+#pragma omp parallel
+      {
+        hit_t* buf = NULL;
+        int cap = 0;
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t p = 0; p < npx; ++p) {
+          int x = (int)(p % c->W), y = (int)(p / c->W);
+          int m = pixel_hits(&g, c, info, cand.vid + cand.off[p], cand.off[p + 1] - cand.off[p], x, y, &buf, &cap);
+          composite(&g, buf, m, tau, F + p * s->C, Aout + p);
+          if (nhit) nhit[p] = m;
+        }
+        free(buf);
+      }
+    }
+  }
+  free(cand.off);
+  free(cand.vid);
+  free(feat);
+  free(sig);
+  free(info);
+  free(win);
+  free(cell);
+  return nc;
 }
 
 /* ------------------------------------------------------------------------ */

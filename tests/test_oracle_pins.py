@@ -1147,3 +1147,104 @@ def test_render_sh_is_linear_and_its_coefficient_gradient():
     g0 = oracle.render_sh_backward(oc, A, cam, 0, gF)
     gfeat, _, _ = oracle.render_backward(oc, A, cam, gF, np.zeros((cam.H, cam.W)), features=np.zeros((oc.n, C)))
     np.testing.assert_allclose(g0[:, 0, :], gfeat * (0.5 / math.sqrt(math.pi)), atol=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# The paper's per-frame index: warped centres snapped to the leaf lattice
+# ---------------------------------------------------------------------------
+
+def _snap_brute(oc, A):
+    """Python loop: lattice cell of each warped centre, survivors by dict."""
+    h = oc.extent / (1 << oc.depth)
+    org = oc.origin.astype(np.float64)
+    A = np.asarray(A, np.float64).reshape(-1, 3, 4)
+    cells, owner = [], {}
+    for i in range(oc.n):
+        if np.linalg.det(A[i, :, :3]) < 1e-3:
+            cells.append(None)
+            continue
+        pc = org + (oc.ijk[i].astype(np.float64) + 0.5) * h
+        p = A[i, :, :3] @ pc + A[i, :, 3]
+        c = tuple(int(math.floor(v)) for v in (p - org) / h)
+        cells.append(c)
+        owner.setdefault(c, i)  # ids ascend: the first is the smallest
+    win = np.array([-1 if c is None else owner[c] for c in cells])
+    return cells, win, len(owner)
+
+
+def test_grid_snap_matches_brute_force_under_a_pose():
+    sc = sg.preset("mini")
+    oc = sc.octree
+    _, A, _ = oracle.pose_transforms(sc, sg.random_pose(9))
+    A = np.asarray(A, np.float64).reshape(-1, 3, 4).copy()
+    A[7, :, :3] *= 0.05  # det 1.25e-4 < 1e-3: not placed
+    g = oracle.grid_snap(oc, A)
+    cells, win, nc = _snap_brute(oc, A)
+    np.testing.assert_array_equal(g["winner"], win)
+    assert g["n_cells"] == nc and g["winner"][7] == -1
+    for i in range(oc.n):
+        if cells[i] is not None:
+            assert tuple(g["cell"][i]) == cells[i]
+    assert nc < int(np.sum(win >= 0))  # the pose makes some voxels collide
+
+
+def test_grid_at_identity_is_the_voxel_render():
+    # with every A_i = I each centre lands in its own leaf: no collision, the
+    # cells are the canonical cubes and the two renders are the same numbers
+    sc = sg.preset("tiny")
+    oc = sc.octree
+    A = identity_A(oc.n)
+    g = oracle.grid_snap(oc, A)
+    np.testing.assert_array_equal(g["winner"], np.arange(oc.n))
+    np.testing.assert_array_equal(g["cell"], oc.ijk.astype(np.int64))
+    cam = sg.orbit_camera(sc.centroid, 64, 48, az_deg=30.0, fov_deg=10.0)
+    r = oracle.render(oc, A, cam)
+    q = oracle.render_grid(oc, A, cam)
+    assert q["n_cells"] == oc.n and np.count_nonzero(r["A"]) > 200
+    np.testing.assert_array_equal(q["F"], r["F"])
+    np.testing.assert_array_equal(q["A"], r["A"])
+    np.testing.assert_array_equal(q["nhit"], r["nhit"])
+    assert oracle.vrt_loss(oc, A) == 0.0
+
+
+def test_grid_render_is_the_voxel_render_of_the_survivors_moved_to_their_cells():
+    # under any pose: the survivors, each translated from its canonical cube
+    # onto its cell, rendered by the exact voxel path
+    sc = sg.preset("mini")
+    oc = sc.octree
+    cam = sg.orbit_camera(sc.centroid, 40, 32, az_deg=75.0, fov_deg=8.0)
+    _, A, _ = oracle.pose_transforms(sc, sg.random_pose(4))
+    g = oracle.grid_snap(oc, A)
+    keep = np.flatnonzero(g["winner"] == np.arange(oc.n))
+    h = oc.extent / (1 << oc.depth)
+    At = identity_A(keep.size)
+    At[:, :, 3] = (g["cell"][keep] - oc.ijk[keep].astype(np.int64)) * h
+    r = oracle.render(oc.subset(keep), At, cam)
+    q = oracle.render_grid(oc, A, cam)
+    assert q["n_cells"] == keep.size and np.count_nonzero(q["A"]) > 100
+    np.testing.assert_allclose(q["F"], r["F"], atol=1e-10)
+    np.testing.assert_allclose(q["A"], r["A"], atol=1e-10)
+    np.testing.assert_array_equal(q["nhit"], r["nhit"])
+
+
+def test_grid_collision_keeps_the_smallest_id():
+    # voxel 3 is moved onto voxel 1's leaf: both centres share one cell, voxel
+    # 1 survives, the picture is the scene without voxel 3, and the
+    # regularisation term is |f_1 - f_3|_1 over the placed voxels
+    ijk = [(4, 4, 4), (6, 4, 4), (8, 4, 4), (10, 8, 4)]
+    oc = make_octree(ijk, depth=4, extent=1.0, C=3, seed=5)
+    h = 1.0 / 16
+    A = identity_A(4)
+    A[3, :, 3] = (np.array([6, 4, 4]) - np.array([10, 8, 4])) * h + 0.3 * h  # inside the same leaf
+    g = oracle.grid_snap(oc, A)
+    np.testing.assert_array_equal(g["winner"], [0, 1, 2, 1])
+    assert g["n_cells"] == 3
+    f = oc.features.astype(np.float64)
+    assert math.isclose(oracle.vrt_loss(oc, A, lam=2.0), 2.0 * np.abs(f[1] - f[3]).sum() / 4, rel_tol=1e-14)
+    cam = axis_camera(oc.centers()[1], (0.2, 0.1, 1.0), dist=1.0, W=9, H=9, f=60.0, near=0.05, far=3.0)
+    keep = np.array([0, 1, 2])
+    r = oracle.render(oc.subset(keep), identity_A(3), cam)
+    q = oracle.render_grid(oc, A, cam)
+    assert np.count_nonzero(q["A"]) > 0
+    np.testing.assert_array_equal(q["F"], r["F"])
+    np.testing.assert_array_equal(q["A"], r["A"])
