@@ -483,10 +483,11 @@ def shade_tiny(F: np.ndarray, layers) -> np.ndarray:
     return conv2d(x, w2, b2, ACT_SIGMOID)
 
 
-def shade_unet(F: np.ndarray, layers) -> np.ndarray:
-    """4-level U-Net: per level two conv3x3 + ReLU; 2x2 max-pool down; nearest
-    x2 up, concatenation [upsampled, skip] on channels, two conv3x3 + ReLU;
-    1x1 head + sigmoid -> RGBA [H,W,4]."""
+def unet(x: np.ndarray, layers, levels: int) -> np.ndarray:
+    """U-Net of ``levels`` levels: per level two conv3x3 + ReLU; 2x2 max-pool
+    down; nearest x2 up, concatenation [upsampled, skip] on channels, two
+    conv3x3 + ReLU; 1x1 head + sigmoid.  x [H,W,Cin], H and W divisible by
+    2^(levels-1)."""
     it = iter(layers)
 
     def block(x):
@@ -495,15 +496,30 @@ def shade_unet(F: np.ndarray, layers) -> np.ndarray:
         w, b = next(it)
         return conv2d(x, w, b, ACT_RELU)
 
-    e0 = block(F)
-    e1 = block(maxpool2(e0))
-    e2 = block(maxpool2(e1))
-    e3 = block(maxpool2(e2))
-    d2 = block(np.concatenate([upsample2(e3), e2], axis=2))
-    d1 = block(np.concatenate([upsample2(d2), e1], axis=2))
-    d0 = block(np.concatenate([upsample2(d1), e0], axis=2))
+    skips = [block(x)]
+    for _ in range(levels - 1):
+        skips.append(block(maxpool2(skips[-1])))
+    d = skips.pop()
+    while skips:
+        d = block(np.concatenate([upsample2(d), skips.pop()], axis=2))
     w, b = next(it)
-    return conv2d(d0, w, b, ACT_SIGMOID)
+    return conv2d(d, w, b, ACT_SIGMOID)
+
+
+def shade_unet(F: np.ndarray, layers) -> np.ndarray:
+    """The 4-level U-Net shading F -> RGBA [H,W,4]."""
+    return unet(F, layers, 4)
+
+
+def shade_two_branch(F: np.ndarray, A: np.ndarray, rgb_layers, alpha_layers, rgb_levels: int = 4,
+                     alpha_levels: int = 2) -> np.ndarray:
+    """The paper's two-branch shading network G (Sec. 3.1 "Neural Shading",
+    Fig. 4): the appearance branch turns the feature map F into the texture
+    image I_f [H,W,3]; the opacity branch refines the coarse opacity map A
+    from [A, I_f] (4 channels) into alpha [H,W,1].  Returns [I_f, alpha]."""
+    I_f = unet(F, rgb_layers, rgb_levels)
+    alpha = unet(np.concatenate([_f64(A)[..., None], I_f], axis=2), alpha_layers, alpha_levels)
+    return np.concatenate([I_f, alpha], axis=2)
 
 
 def shade(F: np.ndarray, layers) -> np.ndarray:

@@ -26,7 +26,7 @@ __all__ = [
     "Skeleton", "Octree", "Pose", "Camera", "Scene",
     "quadruped_skeleton", "make_octree", "random_pose", "walk_pose",
     "rest_pose", "orbit_camera", "tiny_net_weights", "unet_weights",
-    "UNET_CHANNELS", "preset", "PRESETS",
+    "UNET_CHANNELS", "unet_layer_shapes", "two_branch_weights", "ALPHA_CHANNELS", "preset", "PRESETS",
 ]
 
 J_JOINTS = 24
@@ -432,25 +432,33 @@ def tiny_net_weights(seed: int, cin: int = 16, mid: int = 32, cout: int = 4):
 
 
 def unet_layer_shapes(cin: int = 32, ch=UNET_CHANNELS, cout: int = 4):
-    """(Cout, Cin, k) of every layer of the 4-level U-Net, in execution order:
-    enc0 a/b, enc1 a/b, enc2 a/b, enc3 a/b (bottleneck), dec2 a/b, dec1 a/b,
-    dec0 a/b, head (1x1)."""
-    c0, c1, c2, c3 = ch
-    return [
-        (c0, cin, 3), (c0, c0, 3),
-        (c1, c0, 3), (c1, c1, 3),
-        (c2, c1, 3), (c2, c2, 3),
-        (c3, c2, 3), (c3, c3, 3),
-        (c2, c3 + c2, 3), (c2, c2, 3),
-        (c1, c2 + c1, 3), (c1, c1, 3),
-        (c0, c1 + c0, 3), (c0, c0, 3),
-        (cout, c0, 1),
-    ]
+    """(Cout, Cin, k) of every layer of a len(ch)-level U-Net, in execution
+    order: enc0 a/b, ..., enc(L-1) a/b (bottleneck), dec(L-2) a/b, ...,
+    dec0 a/b, head (1x1).  A decoder level's first layer takes the upsampled
+    level below concatenated with the skip."""
+    L = len(ch)
+    shapes, prev = [], cin
+    for c in ch:
+        shapes += [(c, prev, 3), (c, c, 3)]
+        prev = c
+    for l in range(L - 2, -1, -1):
+        shapes += [(ch[l], ch[l + 1] + ch[l], 3), (ch[l], ch[l], 3)]
+    return shapes + [(cout, ch[0], 1)]
 
 
 def unet_weights(seed: int, cin: int = 32, ch=UNET_CHANNELS, cout: int = 4):
     rng = np.random.default_rng(seed)
     return [_conv_w(rng, co, ci, k) for co, ci, k in unet_layer_shapes(cin, ch, cout)]
+
+
+ALPHA_CHANNELS = (16, 32)
+
+
+def two_branch_weights(seed: int, cin: int = 32, rgb_ch=UNET_CHANNELS, alpha_ch=ALPHA_CHANNELS):
+    """The two-branch shading network's weights: an RGB U-Net cin -> 3 with
+    len(rgb_ch) levels and an alpha U-Net (1 + 3) -> 1 with len(alpha_ch)
+    levels (its input is the coarse opacity and the RGB branch's image)."""
+    return unet_weights(seed, cin, rgb_ch, 3), unet_weights(seed + 1, 4, alpha_ch, 1)
 
 
 # ---------------------------------------------------------------------------

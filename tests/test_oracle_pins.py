@@ -1248,3 +1248,56 @@ def test_grid_collision_keeps_the_smallest_id():
     assert np.count_nonzero(q["A"]) > 0
     np.testing.assert_array_equal(q["F"], r["F"])
     np.testing.assert_array_equal(q["A"], r["A"])
+
+
+# ---------------------------------------------------------------------------
+# The two-branch shading network (Sec. 3.1 "Neural Shading", Fig. 4)
+# ---------------------------------------------------------------------------
+
+def _torch_unet(torch, t, layers, levels):
+    """The U-Net written recursively with torch's FP64 ops."""
+    import torch.nn.functional as Fn
+    L = iter(layers)
+
+    def conv(z, act):
+        w, b = next(L)
+        y = Fn.conv2d(z, torch.from_numpy(w.astype(np.float64)).permute(0, 3, 1, 2),
+                      torch.from_numpy(b.astype(np.float64)), padding=w.shape[1] // 2)
+        return torch.relu(y) if act else torch.sigmoid(y)
+
+    def level(z, l):
+        e = conv(conv(z, True), True)
+        if l == levels - 1:
+            return e
+        below = level(Fn.max_pool2d(e, 2), l + 1)
+        up = Fn.interpolate(below, scale_factor=2, mode="nearest")
+        return conv(conv(torch.cat([up, e], 1), True), True)
+
+    return conv(level(t, 0), False)
+
+
+def test_two_branch_net_matches_torch_and_its_structure():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(7)
+    F = rng.standard_normal((16, 24, 5))
+    A = rng.uniform(0, 1, (16, 24))
+    rgb, alpha = sg.two_branch_weights(2, cin=5, rgb_ch=(4, 6, 8, 10), alpha_ch=(3, 5))
+    assert [w.shape for w, _ in sg.unet_weights(3, cin=5, ch=(4, 6, 8, 10))] == \
+        [(co, k, k, ci) for co, ci, k in [(4, 5, 3), (4, 4, 3), (6, 4, 3), (6, 6, 3), (8, 6, 3), (8, 8, 3),
+                                          (10, 8, 3), (10, 10, 3), (8, 18, 3), (8, 8, 3), (6, 14, 3),
+                                          (6, 6, 3), (4, 10, 3), (4, 4, 3), (4, 4, 1)]]
+    got = oracle.shade_two_branch(F, A, rgb, alpha)
+    assert got.shape == (16, 24, 4)
+    tF = torch.from_numpy(F).permute(2, 0, 1)[None]
+    I_f = _torch_unet(torch, tF, rgb, 4)
+    a = _torch_unet(torch, torch.cat([torch.from_numpy(A)[None, None], I_f], 1), alpha, 2)
+    ref = torch.cat([I_f, a], 1)[0].permute(1, 2, 0).numpy()
+    np.testing.assert_allclose(got, ref, atol=1e-12)
+    # the appearance branch does not see A; the opacity branch does
+    got2 = oracle.shade_two_branch(F, 1.0 - A, rgb, alpha)
+    np.testing.assert_array_equal(got2[..., :3], got[..., :3])
+    assert np.abs(got2[..., 3] - got[..., 3]).max() > 1e-6
+    # an opacity branch with a zero head returns sigmoid of the head's bias
+    alpha0 = [(w, b) for w, b in alpha[:-1]] + [(np.zeros_like(alpha[-1][0]), np.array([0.3], np.float32))]
+    np.testing.assert_allclose(oracle.shade_two_branch(F, A, rgb, alpha0)[..., 3],
+                               1.0 / (1.0 + math.exp(-float(np.float32(0.3)))), atol=1e-15)
