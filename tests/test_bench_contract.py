@@ -44,3 +44,37 @@ def test_roofline_of_a_bandwidth_bound_kernel():
     assert math.isclose(r["achieved"], 1000000 * 160 / 0.035e-3 / 1e9, rel_tol=1e-12)
     assert r["peak_is"] == "measured copy bandwidth"
     assert bench.roofline({}, {}, {}, "bf16_skip", 1, 32, 1) is None
+
+
+def test_clock_summary_of_sampled_lines():
+    cs = bench.ClockSampler(0)
+    cs.lines = [
+        "0, 1965, 2070, 900.5, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 1980, 2070, 950.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 2010, 2070, 1010.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "garbled line",
+        "0, [N/A], 2070, 1.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+    ]
+    s = cs.summary()
+    assert s == {"sm_mhz": 1980.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    cs.lines = ["0, 1200, 2070, 700, 0x8, Not Active, Active, Not Active, Not Active"]
+    assert cs.summary()["reasons"] == ["hw_thermal_slowdown"]
+    cs.lines = []
+    assert cs.summary()["reasons"] == ["unsampled"]
+
+
+def test_step_schedule_covers_every_pose_and_azimuth():
+    seen = {bench.step_indices(k) for k in range(bench.N_POSES * bench.N_AZ)}
+    assert {p for p, _ in seen} == set(range(bench.N_POSES))
+    assert {v for _, v in seen} == set(range(bench.N_AZ))
+    # consecutive steps change both the pose and the view
+    for k in range(50):
+        a, b = bench.step_indices(k), bench.step_indices(k + 1)
+        assert a[0] != b[0] and a[1] != b[1]
+
+
+def test_quality_psnr():
+    import numpy as np
+    ref = np.zeros((4, 4, 4))
+    q = bench.quality(ref + 0.01, ref)
+    assert math.isclose(q["psnr_db"], 40.0, rel_tol=1e-12) and math.isclose(q["max_abs"], 0.01)
