@@ -21,7 +21,10 @@
  *   - Pointer arguments may be host or device memory unless stated; the
  *     library tells them apart with cudaPointerGetAttributes.  Inputs are
  *     copied into library-owned device memory; the caller keeps ownership of
- *     everything it passes.
+ *     everything it passes.  A pageable host input may be reused as soon as
+ *     the call returns; a page-locked (pinned) host input, and any device
+ *     input, is read asynchronously and must stay unchanged until the stream
+ *     has passed the call.
  *   - All arrays are dense, row-major, with the layouts given per argument.
  *   - A context is not thread-safe; use one per host thread / stream.
  */
