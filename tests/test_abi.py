@@ -55,3 +55,18 @@ def test_flat_params_layout():
     n = sum(w.size + b.size for w, b in layers)
     assert p.shape == (n,)
     np.testing.assert_array_equal(p[:layers[0][0].size], layers[0][0].ravel())
+
+
+def test_no_gpu_means_no_context(lib_path):
+    # the library has no CPU path: without a CUDA device art_create returns
+    # ART_ERR_CUDA and no context, and the Python binding raises
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    lib = ctypes.CDLL(lib_path)
+    lib.art_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p]
+    h = ctypes.c_void_p()
+    assert lib.art_create(ctypes.byref(h), None) == 2 and h.value is None
+    import paper_2202_05628_gb300 as art
+    with pytest.raises((RuntimeError, art.ArtemisError)):
+        art.Renderer()
