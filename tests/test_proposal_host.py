@@ -10,13 +10,21 @@ import oracle
 import scenegen as sg
 
 torch = pytest.importorskip("torch")
-from paper_2202_05628_gb300 import proposal as prop  # noqa: E402
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 WEIGHTS = os.path.join(ROOT, "paper_2202_05628_gb300", "weights", "proposal_quadruped_1m_1024.bin")
 
 
-def test_encoding_equals_the_oracle_inputs():
+@pytest.fixture(scope="module")
+def prop():
+    # the package loads its library on import: build it first (a no-op when current)
+    import __graft_entry__
+    __graft_entry__._build_module().build()
+    from paper_2202_05628_gb300 import proposal
+    return proposal
+
+
+def test_encoding_equals_the_oracle_inputs(prop):
     cam = sg.orbit_camera(np.array([0.05, 0.1, -0.02]), 24, 16, az_deg=70.0, elev_deg=-5.0)
     pose = sg.random_pose(4)
     x = prop.encode(pose.axis_angle, cam, device="cpu").double().numpy()
@@ -32,7 +40,7 @@ def test_encoding_equals_the_oracle_inputs():
     np.testing.assert_array_equal(xs, x[pix])
 
 
-def test_network_equals_the_oracle_mlp():
+def test_network_equals_the_oracle_mlp(prop):
     p = prop.init_params(7)
     p[64 * 107:64 * 107 + 64] = np.random.default_rng(1).standard_normal(64).astype(np.float32) * 0.1  # a bias
     x = np.random.default_rng(2).standard_normal((50, 107)).astype(np.float32)
@@ -43,7 +51,7 @@ def test_network_equals_the_oracle_mlp():
     np.testing.assert_array_equal(prop._flat(prop._module(p, "cpu")), p)
 
 
-def test_weights_file_round_trip_and_checks(tmp_path):
+def test_weights_file_round_trip_and_checks(prop, tmp_path):
     p = prop.init_params(3)
     f = tmp_path / "w.bin"
     prop.save(str(f), p, "tiny quadruped")
@@ -56,7 +64,7 @@ def test_weights_file_round_trip_and_checks(tmp_path):
         prop.load(str(bad))
 
 
-def test_committed_weights_load():
+def test_committed_weights_load(prop):
     if not os.path.exists(WEIGHTS):
         pytest.skip("trained proposal weights missing")
     p, meta = prop.load(WEIGHTS)
