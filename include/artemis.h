@@ -387,10 +387,14 @@ art_status art_sort_pairs(art_ctx* ctx, uint32_t* keys, uint32_t* vals, int64_t 
  * of it that it reads, so no state carries over between calls; but all calls
  * share it, so calls that overlap on the GPU (other streams, other host
  * threads) race: order them on one stream or with events.
- * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  Returns ART_ERR_CUDA if that lookup or a launch
- * fails.
+ * keys and vals must be device (or managed) memory of the current device,
+ * else ART_ERR_INVALID_ARG is returned without launching.
+ * The first call on each device (and again after a cudaDeviceReset) looks up
+ * the array's device address (cudaGetSymbolAddress, with that device
+ * current); make that first call before any stream capture.  If a CUDA error
+ * is already pending when the call starts (left by an earlier call), it
+ * returns ART_ERR_CUDA without launching and leaves that error pending.
+ * Returns ART_ERR_CUDA if the lookup or a launch fails.
  */
 #define ART_SORT_STATIC_MAX_PAIRS (1 << 20)
 art_status art_sort_pairs_static(uint32_t* keys, uint32_t* vals, int64_t n, int key_bits, void* cuda_stream);

@@ -344,8 +344,12 @@ def render_sh_backward(octree, A: np.ndarray, cam, L: int, gF, tau: float = TAU_
 
 
 def pixels(octree, A: np.ndarray, cam, px: Sequence[int], py: Sequence[int],
-           tau: float = TAU_DEFAULT, features=None, density=None) -> dict:
-    """Sampled pixels, each by brute force over every voxel."""
+           tau: float = TAU_DEFAULT, features=None, density=None, tie_eps: float = 1e-6) -> dict:
+    """Sampled pixels, each by brute force over every voxel.  ``tie`` is, per
+    pixel, the largest change of a feature channel that swapping two
+    consecutive composited hits with entry distances within ``tie_eps`` would
+    cause (T_i alpha_i alpha_j |f_i - f_j|; 0 without such a pair): the part
+    of F that rounding of the entry distances can decide."""
     b = _Bound(octree, np.asarray(A).reshape(-1, 12), features, density)
     k = _cam(cam)
     px = np.ascontiguousarray(px, np.int32)
@@ -354,9 +358,10 @@ def pixels(octree, A: np.ndarray, cam, px: Sequence[int], py: Sequence[int],
     F = np.zeros((m, b.feat.shape[1]))
     Am = np.zeros(m)
     nh = np.zeros(m, np.int32)
+    tie = np.zeros(m)
     _L().orc_pixels(ctypes.byref(b.s), ctypes.byref(k), ctypes.c_int64(m), _p(px), _p(py),
-                    ctypes.c_double(tau), _p(F), _p(Am), _p(nh))
-    return dict(F=F, A=Am, nhit=nh)
+                    ctypes.c_double(tau), _p(F), _p(Am), _p(nh), ctypes.c_double(tie_eps), _p(tie))
+    return dict(F=F, A=Am, nhit=nh, tie=tie)
 
 
 def pixel_brute(octree, A: np.ndarray, cam, x: int, y: int, tau: float = TAU_DEFAULT,

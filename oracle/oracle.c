@@ -934,7 +934,7 @@ int orc_pixel_brute(const orc_scene* s, const orc_cam* c, int x, int y, double t
  * all voxels.  Used to check sampled outputs of full-size frames.
  */
 int orc_pixels(const orc_scene* s, const orc_cam* c, int64_t np, const int32_t* px, const int32_t* py,
-               double tau, double* F, double* Aout, int32_t* nhit) {
+               double tau, double* F, double* Aout, int32_t* nhit, double tie_eps, double* tie) {
   vox_info* info = all_info(s, c);
   if (!info) return -1;
 #pragma omp parallel
@@ -944,8 +944,31 @@ int orc_pixels(const orc_scene* s, const orc_cam* c, int64_t np, const int32_t* 
 #pragma omp for schedule(dynamic, 1)
     for (int64_t k = 0; k < np; ++k) {
       int m = pixel_hits(s, c, info, NULL, s->n, px[k], py[k], &buf, &bcap);
-      composite(s, buf, m, tau, F + k * s->C, Aout + k);
+      int used = composite(s, buf, m, tau, F + k * s->C, Aout + k);
       if (nhit) nhit[k] = m;
+      if (tie) {
+        /* Order-ambiguous pairs: consecutive hits among the composited ones
+         * (and the first after the stop) whose entry distances differ by less
+         * than tie_eps.  Swapping such a pair i, i+1 changes F by
+         * T_i alpha_i alpha_{i+1} (f_i - f_{i+1}); the largest channel change
+         * over the pixel's pairs is reported (0 when there is none). */
+        double worst = 0.0, optical = 0.0;
+        for (int i = 0; i + 1 < m && i <= used; ++i) {
+          const double si = s->sigma[buf[i].id], sj = s->sigma[buf[i + 1].id];
+          const double ai = 1.0 - exp(-si * (buf[i].t1 - buf[i].t0));
+          if (buf[i + 1].t0 - buf[i].t0 < tie_eps) {
+            const double aj = 1.0 - exp(-sj * (buf[i + 1].t1 - buf[i + 1].t0));
+            const double* fi = s->feat + (size_t)buf[i].id * s->C;
+            const double* fj = s->feat + (size_t)buf[i + 1].id * s->C;
+            double df = 0.0;
+            for (int ch = 0; ch < s->C; ++ch) df = fmax(df, fabs(fi[ch] - fj[ch]));
+            const double e = exp(-optical) * ai * aj * df;
+            if (e > worst) worst = e;
+          }
+          optical += si * (buf[i].t1 - buf[i].t0);
+        }
+        tie[k] = worst;
+      }
     }
     free(buf);
   }

@@ -230,6 +230,7 @@ class Renderer:
         self._check(_lib.art_render_labels(self._h, view, _ptr(labels), _ptr(bins)))
 
     def sort_pairs(self, keys, vals, key_bits: int = 32):
+        _check_pairs(keys, vals)
         self._check(_lib.art_sort_pairs(self._h, _ptr(keys), _ptr(vals), int(keys.numel()), key_bits))
 
     # ------------------------------------------------------------ inspection
@@ -327,11 +328,25 @@ _RenderFn = _LazyFn()
 SORT_STATIC_MAX_PAIRS = 1 << 20
 
 
+def _check_pairs(keys, vals):
+    """keys and vals of a device sort: contiguous 4-byte CUDA tensors of the
+    same length on the current device."""
+    import torch
+    for t in (keys, vals):
+        if not (t.is_cuda and t.element_size() == 4 and t.is_contiguous()):
+            raise ValueError("sort: keys and vals must be contiguous 4-byte CUDA tensors")
+        if t.device.index != torch.cuda.current_device():
+            raise ValueError("sort: keys and vals must be on the current CUDA device")
+    if keys.numel() != vals.numel():
+        raise ValueError(f"sort: {keys.numel()} keys but {vals.numel()} values")
+
+
 def sort_pairs_static(keys, vals, key_bits: int = 32, stream=None) -> int:
     """art_sort_pairs_static: the radix sort without any device allocation
     (scratch in a fixed array inside the library; see include/artemis.h).
     Returns the library status (0 = ART_OK)."""
     import torch
+    _check_pairs(keys, vals)
     s = torch.cuda.current_stream() if stream is None else stream
     return int(_lib.art_sort_pairs_static(_ptr(keys), _ptr(vals), int(keys.numel()), key_bits,
                                           ctypes.c_void_p(s.cuda_stream)))

@@ -537,6 +537,7 @@ art_status art_set_camera(art_ctx* ctx, int view, int W, int H, float fx, float 
     double s = 0;
     for (int r = 0; r < 3; ++r) s -= (double)M[r * 4 + a] * (double)M[r * 4 + 3];
     v.o[a] = (float)s;
+    v.o_lo[a] = (float)(s - (double)v.o[a]);
   }
   v.znear = znear;
   v.zfar = zfar;

@@ -32,14 +32,14 @@ namespace {
 // Pending hit of the backward: the forward's fields plus what the geometric
 // gradient needs (entry / exit axes and the direction component along them).
 struct PendG {
-  float t0, t1;
+  float t0, dl;  // entry distance and chord (the exit is t0 + dl)
   uint32_t pos;
   int axes;  // (ax0 + 1) | (ax1 + 1) << 4
   float e0, e1;
 };
 
 __device__ __forceinline__ bool pless(const PendG& a, const PendG& b) {
-  return a.t0 < b.t0 || (a.t0 == b.t0 && (a.t1 < b.t1 || (a.t1 == b.t1 && a.pos < b.pos)));
+  return a.t0 < b.t0 || (a.t0 == b.t0 && (a.dl < b.dl || (a.dl == b.dl && a.pos < b.pos)));
 }
 
 __device__ __forceinline__ void atomic_add4(float* p, float a, float b, float c, float d) {
@@ -62,7 +62,7 @@ __device__ __forceinline__ void bwd_tile(const int tile, const Seg& sg, float T_
                                          float* __restrict__ gfeat, float* __restrict__ gsig, float* __restrict__ gN,
                                          unsigned long long* __restrict__ status) {
   constexpr int RING = Ring<C, TF>::kChunks;
-  __shared__ float4 s_b0[NT], s_b1[NT], s_b2[NT];
+  __shared__ float4 s_b0[NT], s_b1[NT], s_b2[NT], s_xl[NT];
   __shared__ float s_thr[NT];
   __shared__ uint32_t s_mask[NT];
   __shared__ float s_sig[RING][NT];
@@ -76,8 +76,8 @@ __device__ __forceinline__ void bwd_tile(const int tile, const Seg& sg, float T_
   const bool inside = px < v.W && py < v.H;
   const size_t pix = inside ? (size_t)py * v.W + px : 0;
 
-  float d0, d1, d2;
-  pixel_dir(v, px, py, d0, d1, d2);
+  const RayDir rd = pixel_ray(v, px, py);
+  const float d0 = rd.h[0], d1 = rd.h[1], d2 = rd.h[2];
 
   // upstream gradient of this pixel and the forward's outputs
   float g[C];
@@ -130,7 +130,8 @@ __device__ __forceinline__ void bwd_tile(const int tile, const Seg& sg, float T_
       sig = rec[4 * (size_t)vid + 3].x;
       load_feat<C>(feat + (size_t)vid * C, f);
     }
-    const float delta = hh.t1 - hh.t0;
+    const float delta = hh.dl;
+    const float t1 = hh.t0 + hh.dl;
     const float e = expf(-sig * delta);
     const float w = T * (1.0f - e);
     float fg = 0.0f;
@@ -156,8 +157,8 @@ __device__ __forceinline__ void bwd_tile(const int tile, const Seg& sg, float T_
     }
     if (a1 >= 0) {  // exit end: d(delta)/d(t1) = +1
       const float gt = gdelta / (h * hh.e1);
-      atomic_add4(gN + (size_t)vid * 12 + 4 * a1, -gt * (v.o[0] + hh.t1 * d0), -gt * (v.o[1] + hh.t1 * d1),
-                  -gt * (v.o[2] + hh.t1 * d2), -gt);
+      atomic_add4(gN + (size_t)vid * 12 + 4 * a1, -gt * (v.o[0] + t1 * d0), -gt * (v.o[1] + t1 * d1),
+                  -gt * (v.o[2] + t1 * d2), -gt);
     }
     T *= e;
     if (T < tau) done = true;
@@ -178,10 +179,7 @@ __device__ __forceinline__ void bwd_tile(const int tile, const Seg& sg, float T_
         const float4 r0 = rp[0], r1 = rp[1], r2 = rp[2], r3 = rp[3];
         const short4 rc = rect[vid];
         copy_row<C, TF>(feat + (size_t)vid * C, &s_feat[slot][lane][0]);
-        const float ex = v.o[0] - r0.w, ey = v.o[1] - r1.w, ez = v.o[2] - r2.w;
-        s_b0[lane] = make_float4(r0.x, r0.y, r0.z, r0.x * ex + r0.y * ey + r0.z * ez);
-        s_b1[lane] = make_float4(r1.x, r1.y, r1.z, r1.x * ex + r1.y * ey + r1.z * ez);
-        s_b2[lane] = make_float4(r2.x, r2.y, r2.z, r2.x * ex + r2.y * ey + r2.z * ez);
+        stage_voxel(r0, r1, r2, v, s_b0[lane], s_b1[lane], s_b2[lane], s_xl[lane]);
         s_sig[slot][lane] = r3.x;
         s_vid[slot][lane] = vid;
         thr = v.znear + (float)(key & qmask) * qinv;
@@ -198,11 +196,11 @@ __device__ __forceinline__ void bwd_tile(const int tile, const Seg& sg, float T_
     while (cand) {
       const int idx = __ffs(cand) - 1;
       cand &= cand - 1;
-      float t0, t1, e[3];
+      float t0, dl, e[3];
       int ax0, ax1;
-      if (!slab_hit(s_b0[idx], s_b1[idx], s_b2[idx], d0, d1, d2, v.znear, v.zfar, t0, t1, ax0, ax1, e)) continue;
+      if (!slab_hit(s_b0[idx], s_b1[idx], s_b2[idx], s_xl[idx], rd, v.znear, v.zfar, t0, dl, ax0, ax1, e)) continue;
       if (t0 < sg.t0_lo || t0 >= sg.t0_hi) continue;  // another segment's hit
-      const PendG p{t0, t1, base - rg.x + (uint32_t)idx, (ax0 + 1) | ((ax1 + 1) << 4),
+      const PendG p{t0, dl, base - rg.x + (uint32_t)idx, (ax0 + 1) | ((ax1 + 1) << 4),
                     ax0 == 0 ? e[0] : (ax0 == 1 ? e[1] : e[2]), ax1 == 0 ? e[0] : (ax1 == 1 ? e[1] : e[2])};
       if (nb == kPend) {
         const float thr = s_thr[idx];

@@ -2,6 +2,9 @@
 // and a device LSD radix sort of key/value pairs.  The per-frame binning
 // plays the role of the paper's per-frame octree rebuild before the ray-voxel
 // test (arXiv 2202.05628, Sec. 3.1 "Dynamic Volume Rendering").
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <mutex>
 
 #include "internal.cuh"
@@ -765,24 +768,61 @@ static __device__ __align__(256) unsigned char g_sort_scratch[kStaticBytes];
 namespace {
 
 std::mutex g_scratch_mu;
-void* g_scratch_addr[kMaxDevices] = {};
+struct ScratchAddr {
+  unsigned long long ctx_id;  // the context the address belongs to (unique per process, never reused)
+  void* addr;
+};
+ScratchAddr g_scratch_addr[kMaxDevices] = {};
 
-// Device address of g_sort_scratch on the current device (looked up once per
-// device; in host code the symbol itself is only a host-side stand-in).
-cudaError_t static_scratch(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
+// Device address of g_sort_scratch on the current device.  In host code the
+// symbol itself is only a host-side stand-in, so the address is looked up
+// with cudaGetSymbolAddress, once per device and context: after a
+// cudaDeviceReset the device gets a new primary context (a new id), and the
+// next call looks the address up again.
+cudaError_t static_scratch(int dev, void** out) {
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  cudaError_t e = cudaFree(nullptr);  // makes the device's primary context current (frees nothing)
+  if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_addr[dev]) {
+  // the driver's context calls, found through the runtime (the library does
+  // not link the driver library, so that it loads on machines without one)
+  static PFN_cuCtxGetCurrent_v4000 get_current = nullptr;
+  static PFN_cuCtxGetId_v12000 get_id = nullptr;
+  if (!get_current || !get_id) {
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", (void**)&get_current, 4000, cudaEnableDefault, &q1) !=
+            cudaSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", (void**)&get_id, 12000, cudaEnableDefault, &q2) !=
+            cudaSuccess ||
+        q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess) {
+      get_current = nullptr;
+      get_id = nullptr;
+      return cudaErrorNotSupported;
+    }
+  }
+  CUcontext cu = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&cu) != CUDA_SUCCESS || !cu || get_id(cu, &id) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+  if (!g_scratch_addr[dev].addr || g_scratch_addr[dev].ctx_id != id) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_sort_scratch);
     if (e != cudaSuccess) return e;
-    g_scratch_addr[dev] = p;
+    g_scratch_addr[dev] = ScratchAddr{id, p};
   }
-  *out = g_scratch_addr[dev];
+  *out = g_scratch_addr[dev].addr;
   return cudaSuccess;
+}
+
+// keys / vals must be device (or managed) memory of the device the scratch
+// belongs to.
+bool on_device(const void* p, int dev) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();  // the query's own error on a pointer CUDA does not know
+    return false;
+  }
+  if (at.type == cudaMemoryTypeManaged) return true;
+  return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 }  // namespace
@@ -796,8 +836,14 @@ extern "C" art_status art_sort_pairs_static(uint32_t* keys, uint32_t* vals, int6
   if (key_bits != 8 && key_bits != 16 && key_bits != 24 && key_bits != 32) return ART_ERR_INVALID_ARG;
   if (n == 0) return ART_OK;
   if (!keys || !vals) return ART_ERR_INVALID_ARG;
+  // an error left pending by an earlier, unrelated call is neither cleared
+  // nor reported as this call's: the call refuses to run instead
+  if (cudaPeekAtLastError() != cudaSuccess) return ART_ERR_CUDA;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return ART_ERR_CUDA;
+  if (!on_device(keys, dev) || !on_device(vals, dev)) return ART_ERR_INVALID_ARG;
   void* base = nullptr;
-  if (static_scratch(&base) != cudaSuccess) {
+  if (static_scratch(dev, &base) != cudaSuccess) {
     cudaGetLastError();
     return ART_ERR_CUDA;
   }
@@ -814,6 +860,7 @@ extern "C" art_status art_sort_pairs_static(uint32_t* keys, uint32_t* vals, int6
   uint32_t* K[2] = {keys, sk};
   uint32_t* V[2] = {vals, sv};
   set_word_kernel<<<1, 1, 0, s>>>(count, (unsigned long long)n);
+  if (cudaPeekAtLastError() != cudaSuccess) return (cudaGetLastError(), ART_ERR_CUDA);
   int src = 0;
   for (int shift = 0; shift < key_bits; shift += kRadixBits) {
     radix_hist_kernel<<<nb, kSortThreads, 0, s>>>(K[src], n, count, shift, nb, hist);
@@ -822,11 +869,13 @@ extern "C" art_status art_sort_pairs_static(uint32_t* keys, uint32_t* vals, int6
     scan_apply_kernel<<<hb, kScanThreads, 0, s>>>(hist, hist, hn, bsum);
     radix_scatter_kernel<<<nb, kSortThreads, 0, s>>>(K[src], V[src], K[src ^ 1], V[src ^ 1], n, count, shift, nb,
                                                      hist);
+    if (cudaPeekAtLastError() != cudaSuccess) return (cudaGetLastError(), ART_ERR_CUDA);
     src ^= 1;
   }
   if (src == 1) {
-    cudaMemcpyAsync(keys, sk, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s);
-    cudaMemcpyAsync(vals, sv, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s);
+    if (cudaMemcpyAsync(keys, sk, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(vals, sv, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return (cudaGetLastError(), ART_ERR_CUDA);
   }
-  return cudaGetLastError() == cudaSuccess ? ART_OK : ART_ERR_CUDA;
+  return ART_OK;
 }

@@ -147,7 +147,7 @@ __device__ __forceinline__ void composite_tile(const int tile, const Seg& sg,
   constexpr bool SH = MODE == kSH;                 // features evaluated per hit from SH coefficients
   constexpr bool FEAT = MODE != kLabel && !SH;  // staged feature rows (labels need densities only)
   constexpr int RING = Ring<C, TF>::kChunks;
-  __shared__ float4 s_b0[NT], s_b1[NT], s_b2[NT];
+  __shared__ float4 s_b0[NT], s_b1[NT], s_b2[NT], s_xl[NT];
   __shared__ float s_thr[NT];
   __shared__ uint32_t s_mask[NT];
   __shared__ float s_sig[RING][NT];
@@ -162,8 +162,7 @@ __device__ __forceinline__ void composite_tile(const int tile, const Seg& sg,
   const int px = sx + (lane & 7), py = sy + (lane >> 3);
   const bool inside = px < v.W && py < v.H;
 
-  float d0, d1, d2;
-  pixel_dir(v, px, py, d0, d1, d2);
+  const RayDir rd = pixel_ray(v, px, py);
 
   float acc[C];
 #pragma unroll
@@ -226,22 +225,22 @@ __device__ __forceinline__ void composite_tile(const int tile, const Seg& sg,
       sig = s_sig[ch % RING][sl];
       vid = s_vid[ch % RING][sl];
       if constexpr (FEAT) row_to_float<C>(&s_feat[ch % RING][sl][0], f);
-      if constexpr (SH) sh_feature<C>(sk, vid, d0, d1, d2, f);
+      if constexpr (SH) sh_feature<C>(sk, vid, rd.h[0], rd.h[1], rd.h[2], f);
     } else {  // staged long ago: read the voxel again
       vid = vals[rg.x + h.pos];
       sig = rec[4 * (size_t)vid + 3].x;
       if constexpr (FEAT) load_feat<C>(feat + (size_t)vid * C, f);
-      if constexpr (SH) sh_feature<C>(sk, vid, d0, d1, d2, f);
+      if constexpr (SH) sh_feature<C>(sk, vid, rd.h[0], rd.h[1], rd.h[2], f);
     }
     if constexpr (DBG) {
       if (n_used < dbg.cap) {
         dbg.ids[pix * dbg.cap + n_used] = vid;
         dbg.t0[pix * dbg.cap + n_used] = h.t0;
-        dbg.t1[pix * dbg.cap + n_used] = h.t1;
+        dbg.t1[pix * dbg.cap + n_used] = h.t0 + h.dl;
       }
       ++n_used;
     }
-    float e = expf(-sig * (h.t1 - h.t0));
+    float e = expf(-sig * h.dl);
     float w = T * (1.0f - e);
     if constexpr (FEAT || SH) {
 #pragma unroll
@@ -250,7 +249,7 @@ __device__ __forceinline__ void composite_tile(const int tile, const Seg& sg,
     T *= e;
     if constexpr (MODE == kLabel) {
       if (w > kLabelWmin) {
-        lab_lo = fminf(lab_lo, h.t1);
+        lab_lo = fminf(lab_lo, h.t0 + h.dl);
         lab_hi = fmaxf(lab_hi, h.t0);
         lab_T = T;
       }
@@ -304,10 +303,7 @@ __device__ __forceinline__ void composite_tile(const int tile, const Seg& sg,
         const float4 r0 = s_rec[b][lane][0], r1 = s_rec[b][lane][1], r2 = s_rec[b][lane][2],
                      r3 = s_rec[b][lane][3];
         const short4 rc = s_rc[b][lane];
-        const float ex = v.o[0] - r0.w, ey = v.o[1] - r1.w, ez = v.o[2] - r2.w;
-        s_b0[lane] = make_float4(r0.x, r0.y, r0.z, r0.x * ex + r0.y * ey + r0.z * ez);
-        s_b1[lane] = make_float4(r1.x, r1.y, r1.z, r1.x * ex + r1.y * ey + r1.z * ez);
-        s_b2[lane] = make_float4(r2.x, r2.y, r2.z, r2.x * ex + r2.y * ey + r2.z * ez);
+        stage_voxel(r0, r1, r2, v, s_b0[lane], s_b1[lane], s_b2[lane], s_xl[lane]);
         s_sig[slot][lane] = r3.x;
         s_vid[slot][lane] = vid;
         thr = v.znear + (float)(key & qmask) * qinv;
@@ -331,14 +327,14 @@ __device__ __forceinline__ void composite_tile(const int tile, const Seg& sg,
     while (cand) {
       const int idx = __ffs(cand) - 1;
       cand &= cand - 1;
-      float t0, t1, e[3];
+      float t0, dl, e[3];
       int ax0, ax1;
-      if (!slab_hit(s_b0[idx], s_b1[idx], s_b2[idx], d0, d1, d2, v.znear, v.zfar, t0, t1, ax0, ax1, e)) continue;
+      if (!slab_hit(s_b0[idx], s_b1[idx], s_b2[idx], s_xl[idx], rd, v.znear, v.zfar, t0, dl, ax0, ax1, e)) continue;
       if (t0 < sg.t0_lo || t0 >= sg.t0_hi) continue;  // another segment's hit
       if constexpr (MODE == kInterval) {
-        if (t1 < t_lo || t0 > t_hi) continue;  // outside this pixel's interval
+        if (t0 + dl < t_lo || t0 > t_hi) continue;  // outside this pixel's interval
       }
-      const Pend p{t0, t1, base - rg.x + (uint32_t)idx};
+      const Pend p{t0, dl, base - rg.x + (uint32_t)idx};
       if (nb == kPend) {
         // buffer full: release what this candidate's own bound allows (still
         // exact), and only if nothing can go, the earliest hit (counted)
@@ -822,7 +818,7 @@ int composite_blocks_per_sm(int C, int feat_bytes) {
   // one-warp blocks, limited by shared memory (staged-feature ring, chunk
   // geometry, double-buffered records) and by registers (12 blocks)
   const int ring = std::max(1, std::min(16, 10240 / (NT * C * feat_bytes)));
-  const int smem = ring * NT * (C * feat_bytes + 8) + NT * (3 * 16 + 8) + 2 * NT * (64 + 8) + 4 * kPropBins + 64;
+  const int smem = ring * NT * (C * feat_bytes + 8) + NT * (4 * 16 + 8) + 2 * NT * (64 + 8) + 4 * kPropBins + 64;
   return std::max(1, std::min(12, (227 * 1024) / smem));
 }
 

@@ -20,15 +20,14 @@ __global__ void __launch_bounds__(32) depth_kernel(const uint2* __restrict__ ran
                                                    const uint32_t* __restrict__ vals, const float4* __restrict__ rec,
                                                    const short4* __restrict__ rect, ViewParams v, float sigma_min,
                                                    float* __restrict__ depth) {
-  __shared__ float4 s_b0[NT], s_b1[NT], s_b2[NT];
+  __shared__ float4 s_b0[NT], s_b1[NT], s_b2[NT], s_xl[NT];
   __shared__ uint32_t s_mask[NT];
   __shared__ float s_bound;
   const int tile = blockIdx.x, lane = threadIdx.x & 31;
   const int sx = (tile % v.tiles_x) * TSX, sy = (tile / v.tiles_x) * TSY;
   const int px = sx + (lane & 7), py = sy + (lane >> 3);
   const bool inside = px < v.W && py < v.H;
-  float d0, d1, d2;
-  pixel_dir(v, px, py, d0, d1, d2);
+  const RayDir rd = pixel_ray(v, px, py);
   float best = __int_as_float(0x7f800000);  // +inf
   const uint2 rg = ranges[tile];
   const uint32_t qmask = (1u << v.depth_bits) - 1u;
@@ -43,10 +42,7 @@ __global__ void __launch_bounds__(32) depth_kernel(const uint2* __restrict__ ran
       const float4 r3 = rp[3];
       if (r3.x > sigma_min) {
         const float4 r0 = rp[0], r1 = rp[1], r2 = rp[2];
-        const float ex = v.o[0] - r0.w, ey = v.o[1] - r1.w, ez = v.o[2] - r2.w;
-        s_b0[lane] = make_float4(r0.x, r0.y, r0.z, r0.x * ex + r0.y * ey + r0.z * ez);
-        s_b1[lane] = make_float4(r1.x, r1.y, r1.z, r1.x * ex + r1.y * ey + r1.z * ez);
-        s_b2[lane] = make_float4(r2.x, r2.y, r2.z, r2.x * ex + r2.y * ey + r2.z * ez);
+        stage_voxel(r0, r1, r2, v, s_b0[lane], s_b1[lane], s_b2[lane], s_xl[lane]);
         m = rect_mask(rect[vid], sx, sy);
       }
     }
@@ -59,9 +55,9 @@ __global__ void __launch_bounds__(32) depth_kernel(const uint2* __restrict__ ran
     while (cand) {
       const int idx = __ffs(cand) - 1;
       cand &= cand - 1;
-      float t0, t1, e[3];
+      float t0, dl, e[3];
       int ax0, ax1;
-      if (slab_hit(s_b0[idx], s_b1[idx], s_b2[idx], d0, d1, d2, v.znear, v.zfar, t0, t1, ax0, ax1, e))
+      if (slab_hit(s_b0[idx], s_b1[idx], s_b2[idx], s_xl[idx], rd, v.znear, v.zfar, t0, dl, ax0, ax1, e))
         best = fminf(best, t0);
     }
   }

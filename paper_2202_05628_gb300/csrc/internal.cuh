@@ -50,7 +50,8 @@ struct ViewParams {
   float fx, fy, cx, cy;
   float R[9];      // world_to_cam rotation (row-major)
   float t[3];
-  float o[3];      // camera centre -R^T t
+  float o[3];      // camera centre -R^T t (FP32 rounding of the FP64 value)
+  float o_lo[3];   // its rounding error: o + o_lo is the centre to ~48 bits
   float znear, zfar;
   int tiles_x, tiles_y;
   int tile_w, tile_h;  // screen tile size in pixels (powers of two)

@@ -20,16 +20,18 @@ struct HitLog {
   int cap;
 };
 
-// A pending hit: entry and exit ray parameters and its position in the tile's
-// list (which locates the staged density, voxel id and feature row).  Exact
-// (t0, t1) ties, which only coincident voxels produce, fall back to list order.
+// A pending hit: entry distance t0, chord length dl (the exit is t0 + dl)
+// and its position in the tile's list (which locates the staged density,
+// voxel id and feature row).  Ordered by (t0, exit, position): at equal t0 the
+// exit order is the chord order.  Exact ties, which only coincident voxels
+// produce, fall back to list order.
 struct Pend {
-  float t0, t1;
+  float t0, dl;
   uint32_t pos;
 };
 
 __device__ __forceinline__ bool pless(const Pend& a, const Pend& b) {
-  return a.t0 < b.t0 || (a.t0 == b.t0 && (a.t1 < b.t1 || (a.t1 == b.t1 && a.pos < b.pos)));
+  return a.t0 < b.t0 || (a.t0 == b.t0 && (a.dl < b.dl || (a.dl == b.dl && a.pos < b.pos)));
 }
 
 // feature row loads (vectorised) --------------------------------------------
@@ -229,29 +231,95 @@ __device__ __forceinline__ float rcp_approx(float x) {
 }
 
 
-// Exact hit of the pixel ray (unit direction d) with a staged voxel whose
-// unit-cube map rows are b0, b1, b2 (xyz: rows of A_lin^-1 / h, w: o' = the
-// camera centre in unit-cube coordinates).  t0 / t1 are the entry / exit ray
-// parameters clipped to [near, far]; ax0 / ax1 the axes of the entry / exit
-// planes (-1 when the near / far bound is the active one) and e the ray
-// direction in unit-cube coordinates.  Returns t1 > t0.
-__device__ __forceinline__ bool slab_hit(const float4& b0, const float4& b1, const float4& b2, float d0, float d1,
-                                         float d2, float znear, float zfar, float& t0, float& t1, int& ax0, int& ax1,
-                                         float (&e)[3]) {
-  e[0] = b0.x * d0 + b0.y * d1 + b0.z * d2;
-  e[1] = b1.x * d0 + b1.y * d1 + b1.z * d2;
-  e[2] = b2.x * d0 + b2.y * d1 + b2.z * d2;
+// The pixel ray's unit direction held to ~48 bits as the sum of two FP32
+// vectors (hi + lo).  The hit test below works at metre scale 2 m from the
+// voxels; there a plain FP32 direction (~1e-7 relative error) moves the ray by
+// ~3e-7 m sideways, which misplaces the chord of a ray that meets a face at a
+// shallow angle by micrometres.  The direction is formed in FP64 exactly as
+// Sec. 3.1's camera rays are defined (through the pixel centre, normalised
+// after the rotation) and split.
+struct RayDir {
+  float h[3], l[3];
+};
+
+__device__ __forceinline__ RayDir pixel_ray(const ViewParams& v, int px, int py) {
+  const double dcx = ((double)px + 0.5 - (double)v.cx) / (double)v.fx;
+  const double dcy = ((double)py + 0.5 - (double)v.cy) / (double)v.fy;
+  double d[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) d[a] = (double)v.R[a] * dcx + (double)v.R[3 + a] * dcy + (double)v.R[6 + a];
+  const double inrm = rsqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  RayDir r;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const double x = d[a] * inrm;
+    r.h[a] = (float)x;
+    r.l[a] = (float)(x - (double)r.h[a]);
+  }
+  return r;
+}
+
+// Staged form of a voxel record for the hit test: rows of its unit-cube map
+// A_lin^-1 / h in b0..b2 (.xyz) with x = o - cw, the camera centre relative to
+// the warped centre, split into hi (b0..b2 .w) and lo (xl.xyz) parts: the hi
+// part is the FP32 difference, the lo part its exact rounding error (two-sum)
+// plus the low part of the camera centre.
+__device__ __forceinline__ void stage_voxel(const float4& r0, const float4& r1, const float4& r2, const ViewParams& v,
+                                            float4& b0, float4& b1, float4& b2, float4& xl) {
+  const float cw[3] = {r0.w, r1.w, r2.w};
+  float xh[3], xo[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float p = v.o[a], q = -cw[a];
+    const float s = __fadd_rn(p, q);
+    const float qq = __fsub_rn(s, p);
+    const float err = __fadd_rn(__fsub_rn(p, __fsub_rn(s, qq)), __fsub_rn(q, qq));
+    xh[a] = s;
+    xo[a] = __fadd_rn(err, v.o_lo[a]);
+  }
+  b0 = make_float4(r0.x, r0.y, r0.z, xh[0]);
+  b1 = make_float4(r1.x, r1.y, r1.z, xh[1]);
+  b2 = make_float4(r2.x, r2.y, r2.z, xh[2]);
+  xl = make_float4(xo[0], xo[1], xo[2], 0.0f);
+}
+
+// Exact hit of the pixel ray with a staged voxel (stage_voxel), anchored at
+// the voxel: s = <cw - o, d> is the ray parameter of the point nearest the
+// warped centre and q = (o - cw) + s d that point relative to the centre
+// (millimetres, formed with one rounding from the split parts, so ~1e-10 m);
+// u = local ray parameters of the entry / exit planes of the unit cube, from
+// A_lin^-1 q / h and the direction e = A_lin^-1 d / h.  The chord delta
+// (Eq. 5's distance travelled through the voxel) is the difference of the
+// small local parameters; the entry distance t0 = s + u_entry (for ordering
+// only).  Both are clipped to [near, far].  ax0 / ax1 are the axes of the
+// entry / exit planes (-1 when the near / far bound is the active one) and e
+// the direction in unit-cube coordinates.  Returns delta > 0.
+__device__ __forceinline__ bool slab_hit(const float4& b0, const float4& b1, const float4& b2, const float4& xl,
+                                         const RayDir& d, float znear, float zfar, float& t0, float& delta, int& ax0,
+                                         int& ax1, float (&e)[3]) {
+  const float s = -(b0.w * d.h[0] + b1.w * d.h[1] + b2.w * d.h[2]);
+  const float q0 = fmaf(s, d.h[0], b0.w) + fmaf(s, d.l[0], xl.x);
+  const float q1 = fmaf(s, d.h[1], b1.w) + fmaf(s, d.l[1], xl.y);
+  const float q2 = fmaf(s, d.h[2], b2.w) + fmaf(s, d.l[2], xl.z);
+  const float p0 = b0.x * q0 + b0.y * q1 + b0.z * q2;
+  const float p1 = b1.x * q0 + b1.y * q1 + b1.z * q2;
+  const float p2 = b2.x * q0 + b2.y * q1 + b2.z * q2;
+  e[0] = b0.x * d.h[0] + b0.y * d.h[1] + b0.z * d.h[2];
+  e[1] = b1.x * d.h[0] + b1.y * d.h[1] + b1.z * d.h[2];
+  e[2] = b2.x * d.h[0] + b2.y * d.h[1] + b2.z * d.h[2];
   const float i0 = rcp_approx(e[0]), i1 = rcp_approx(e[1]), i2 = rcp_approx(e[2]);
-  const float a0 = (-0.5f - b0.w) * i0, c0 = (0.5f - b0.w) * i0;
-  const float a1 = (-0.5f - b1.w) * i1, c1 = (0.5f - b1.w) * i1;
-  const float a2 = (-0.5f - b2.w) * i2, c2 = (0.5f - b2.w) * i2;
+  const float a0 = (-0.5f - p0) * i0, c0 = (0.5f - p0) * i0;
+  const float a1 = (-0.5f - p1) * i1, c1 = (0.5f - p1) * i1;
+  const float a2 = (-0.5f - p2) * i2, c2 = (0.5f - p2) * i2;
   const float l0 = fminf(a0, c0), l1 = fminf(a1, c1), l2 = fminf(a2, c2);
   const float h0 = fmaxf(a0, c0), h1 = fmaxf(a1, c1), h2 = fmaxf(a2, c2);
-  t0 = fmaxf(fmaxf(znear, l0), fmaxf(l1, l2));
-  t1 = fminf(fminf(zfar, h0), fminf(h1, h2));
-  ax0 = t0 == l0 ? 0 : (t0 == l1 ? 1 : (t0 == l2 ? 2 : -1));
-  ax1 = t1 == h0 ? 0 : (t1 == h1 ? 1 : (t1 == h2 ? 2 : -1));
-  return t1 > t0;
+  const float ul = fmaxf(fmaxf(znear - s, l0), fmaxf(l1, l2));
+  const float uh = fminf(fminf(zfar - s, h0), fminf(h1, h2));
+  ax0 = ul == l0 ? 0 : (ul == l1 ? 1 : (ul == l2 ? 2 : -1));
+  ax1 = uh == h0 ? 0 : (uh == h1 ? 1 : (uh == h2 ? 2 : -1));
+  t0 = s + ul;
+  delta = uh - ul;
+  return delta > 0.0f;
 }
 
 // Pixel-rectangle mask of one instance over a TSX x TSY tile at (sx, sy):

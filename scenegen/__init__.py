@@ -111,6 +111,14 @@ class Camera:
     near: float
     far: float
 
+    def __post_init__(self):
+        # The library takes the intrinsics as FP32: they are kept at their
+        # FP32 rounding, so that any consumer (the FP64 oracle included) sees
+        # exactly the camera the library renders.  (orbit_camera's matrix is
+        # FP32 already; hand-made FP64 matrices stay exact for closed forms.)
+        for k in ("fx", "fy", "cx", "cy"):
+            setattr(self, k, float(np.float32(getattr(self, k))))
+
 
 @dataclasses.dataclass
 class Scene:

@@ -89,3 +89,31 @@ def tiny_setup(az=0.0, pose_seed=1, res=128):
     cam = sg.orbit_camera(sc.centroid, res, res, az_deg=az)
     return sc, cam, sg.random_pose(pose_seed)
 
+
+
+def order_ambiguous(o, octree, H, W, tie_eps=1e-6, effect=1e-5, features=None):
+    """Pixels of an oracle render (``hits=True``) whose F the rounding of
+    entry distances decides: two consecutive composited hits (or the last
+    composited one and the next) with entry distances within ``tie_eps`` whose
+    swap changes a channel by more than ``effect`` (T_i alpha_i alpha_j
+    |f_i - f_j|, the difference of the two orders' sums)."""
+    feat = np.asarray(octree.features if features is None else features, np.float64)
+    sig = np.asarray(octree.density, np.float64)
+    off, ids, t0, t1 = o["hit_off"], o["hit_id"], o["hit_t0"], o["hit_t1"]
+    used = o["nused"].ravel()
+    out = np.zeros(H * W, bool)
+    for p in np.flatnonzero(o["nhit"].ravel() > 1):
+        a, b = off[p], off[p + 1]
+        last = min(b - a - 1, int(used[p]))
+        optical = 0.0
+        for i in range(last):
+            k = a + i
+            ai = 1.0 - np.exp(-sig[ids[k]] * (t1[k] - t0[k]))
+            if t0[k + 1] - t0[k] < tie_eps:
+                aj = 1.0 - np.exp(-sig[ids[k + 1]] * (t1[k + 1] - t0[k + 1]))
+                df = np.abs(feat[ids[k]] - feat[ids[k + 1]]).max()
+                if np.exp(-optical) * ai * aj * df > effect:
+                    out[p] = True
+                    break
+            optical += sig[ids[k]] * (t1[k] - t0[k])
+    return out.reshape(H, W)

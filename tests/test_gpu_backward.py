@@ -1,7 +1,9 @@
 """GPU parity of the hand-written backward (composite + LBS) against the FP64
 oracle's analytic gradient, which tests/test_oracle_pins.py pins to central
 finite differences.  Gradients w.r.t. voxel features, densities and skinning
-weights, through the C ABI and through torch.autograd."""
+weights, through the C ABI and through torch.autograd, compared element by
+element (with a bound widened only where the oracle's own gradient moves
+under an FP32-sized perturbation of the blended transforms) and by norm."""
 import numpy as np
 import pytest
 
@@ -40,9 +42,10 @@ def _gpu_grads(sc, pose, cams, gFs, gAs, storage="f32", segment=256, tau=1e-4):
     return gf.cpu().numpy().astype(np.float64), gd.cpu().numpy().astype(np.float64), gw.cpu().numpy().astype(np.float64)
 
 
-def _oracle_grads(sc, pose, cams, gFs, gAs, features=None, tau=1e-4):
+def _oracle_grads(sc, pose, cams, gFs, gAs, features=None, tau=1e-4, A=None):
     oc = sc.octree
-    G, A, _ = oracle.pose_transforms(sc, pose)
+    G, A0, _ = oracle.pose_transforms(sc, pose)
+    A = A0 if A is None else A
     gf = np.zeros((oc.n, oc.C))
     gd = np.zeros(oc.n)
     gN = np.zeros((oc.n, 3, 4))
@@ -55,15 +58,57 @@ def _oracle_grads(sc, pose, cams, gFs, gAs, features=None, tau=1e-4):
     return gf, gd, gw
 
 
-# FP32 ray parameters carry ~2.4e-7 m of rounding at 2 m; chords are a few
-# mm, so alpha = 1 - exp(-sigma delta) and with it every gradient term carries
-# ~1e-4 relative error (more for grazing chords and, through 1 / d'_a, for the
-# geometric terms of the skinning weights).
+def _conditioning(sc, pose, cams, gFs, gAs, base, features=None, tau=1e-4, trials=3):
+    """Per element, how far the oracle's own FP64 gradient moves under
+    perturbations of the size of the library's FP32 rounding of the geometry:
+    each joint transform G_j by up to 8 units in the last FP32 place (the
+    forward-kinematics chain, a rigid error per bone), then each blended
+    transform A_i by up to 2 (LBS).  Large where a chord is grazing, a ray
+    leaves near an edge of a voxel (the derivative switches faces) or two
+    entry distances nearly tie (the order flips); those elements get a
+    proportionally wider bound."""
+    G, _, _ = oracle.pose_transforms(sc, pose)
+    rng = np.random.default_rng(123)
+    cond = [np.zeros_like(b) for b in base]
+    for _ in range(trials):
+        Gp = G * (1.0 + 8.0 * 2.0 ** -24 * rng.uniform(-1.0, 1.0, G.shape))
+        Ap, _ = oracle.lbs(sc.octree, Gp)
+        Ap = Ap * (1.0 + 2.0 * 2.0 ** -24 * rng.uniform(-1.0, 1.0, Ap.shape))
+        g = _oracle_grads(sc, pose, cams, gFs, gAs, features=features, tau=tau, A=Ap)
+        cond = [np.maximum(c, np.abs(x - b)) for c, x, b in zip(cond, g, base)]
+    return cond
+
+
+def _elementwise(g, o, cond, what, rtol=2e-4, atol_frac=1e-5, max_wide=0.02):
+    """Per element |g - o| <= 2 cond + rtol |o| + atol_frac max|o|.  The FP32
+    chord error left once the ray is held in double-float is that of the LBS
+    rounding (~5e-8 m), ~1e-5 relative on a millimetre chord: 2e-4 leaves a
+    margin of 20.  At most max_wide of the elements may owe their pass to the
+    conditioning term."""
+    tol_plain = rtol * np.abs(o) + atol_frac * np.abs(o).max()
+    err = np.abs(g - o)
+    bad = err > 2.0 * cond + tol_plain
+    wide = (err > tol_plain) & ~bad
+    i = np.unravel_index(np.argmax(err - 2.0 * cond - tol_plain), err.shape)
+    msg = (f"{what}: {int(bad.sum())} of {bad.size} elements outside the bound (worst at {i}: gpu {g[i]:.6e}, "
+           f"oracle {o[i]:.6e}, conditioning {cond[i]:.2e}); {int(wide.sum())} inside only through conditioning")
+    print(msg)
+    assert not bad.any(), msg
+    assert wide.mean() <= max_wide, msg
+
+
+# Norm check beside the element-wise one: a blanket relative L2 bound.
 def _close(g, o, rel_l2, what):
     scale = np.linalg.norm(o)
     assert scale > 0, what
     err = np.linalg.norm(g - o) / scale
     assert err < rel_l2, f"{what}: relative L2 error {err:.2e} (max abs {np.abs(g - o).max():.2e}, scale {np.abs(o).max():.2e})"
+
+
+def _compare(g, o, cond, rel=(3e-4, 1e-3, 5e-3)):
+    for k, what in enumerate(("dL/df", "dL/dsigma", "dL/dw")):
+        _elementwise(g[k], o[k], cond[k], what)
+        _close(g[k], o[k], rel[k], what)
 
 
 def test_backward_matches_oracle_small():
@@ -75,9 +120,7 @@ def test_backward_matches_oracle_small():
     gAs = [rng.standard_normal((96, 96)) for _ in cams]
     g = _gpu_grads(sc, pose, cams, gFs, gAs)
     o = _oracle_grads(sc, pose, cams, gFs, gAs)
-    _close(g[0], o[0], 3e-4, "dL/df")
-    _close(g[1], o[1], 1e-3, "dL/dsigma")
-    _close(g[2], o[2], 5e-3, "dL/dw")
+    _compare(g, o, _conditioning(sc, pose, cams, gFs, gAs, o))
 
 
 @pytest.mark.parametrize("segment,tau", [(32, 1e-4), (96, 0.7)])
@@ -97,9 +140,7 @@ def test_backward_split_walk_matches_oracle(segment, tau):
     o = _oracle_grads(sc, pose, cams, gFs, gAs, tau=tau)
     for a, b, what in zip(g, g1, ("dL/df", "dL/dsigma", "dL/dw")):
         _close(a, b, 1e-5, what + " split vs one segment")  # the same sums, atomics in another order
-    _close(g[0], o[0], 3e-4, "dL/df")
-    _close(g[1], o[1], 1e-3, "dL/dsigma")
-    _close(g[2], o[2], 5e-3, "dL/dw")
+    _compare(g, o, _conditioning(sc, pose, cams, gFs, gAs, o, tau=tau))
 
 
 def test_backward_config4_random_rays():
@@ -126,19 +167,7 @@ def test_backward_config4_random_rays():
         gAs.append(np.zeros((cam.H, cam.W)))
     g = _gpu_grads(sc, pose, cams, gFs, gAs)
     o = _oracle_grads(sc, pose, cams, gFs, gAs)
-    _close(g[0], o[0], 3e-4, "dL/df")
-    _close(g[1], o[1], 1e-3, "dL/dsigma")
-    # Skinning weights: each chord's derivative is piecewise smooth.  A hit
-    # within rounding of a piece boundary (a ray leaving near an edge, a
-    # vanishing chord, entry distances of overlapping warped voxels that tie,
-    # which flips the compositing order and with it the feature mass behind
-    # every earlier hit) takes the other piece in FP32 for a few voxels and
-    # changes their gradient by O(1); FP64 finite differences land on either
-    # side there.  Checked: nearly all voxels agree tightly, and the aggregate.
-    carried = np.abs(o[2]).max(1) > 0
-    per_voxel = np.abs(g[2] - o[2]).max(1) <= 2e-2 * np.abs(o[2]).max(1) + 1e-3 * np.abs(o[2]).max()
-    assert per_voxel[carried].mean() > 0.99, per_voxel[carried].mean()
-    _close(g[2], o[2], 0.1, "dL/dw (aggregate)")
+    _compare(g, o, _conditioning(sc, pose, cams, gFs, gAs, o))
     del torch
 
 
@@ -162,9 +191,8 @@ def test_autograd_function_equals_direct_call():
     gF = (2 * (F - tgt)).detach().cpu().numpy()
     gA = (2 * A).detach().cpu().numpy()
     o = _oracle_grads(sc, pose, [cam], [gF], [gA])
-    _close(f.grad.cpu().numpy().astype(np.float64), o[0], 3e-4, "autograd dL/df")
-    _close(d.grad.cpu().numpy().astype(np.float64), o[1], 1e-3, "autograd dL/dsigma")
-    _close(w.grad.cpu().numpy().astype(np.float64), o[2], 5e-3, "autograd dL/dw")
+    g = [t.grad.cpu().numpy().astype(np.float64) for t in (f, d, w)]
+    _compare(g, o, _conditioning(sc, pose, [cam], [gF], [gA], o))
     o_F = oracle.render(oc, oracle.pose_transforms(sc, pose)[1], cam)
     assert np.abs(F.detach().cpu().numpy() - o_F["F"]).max() < 1e-4
 
@@ -180,6 +208,4 @@ def test_backward_bf16_storage_uses_rounded_features():
     g = _gpu_grads(sc, pose, [cam], [gF], [gA], storage="bf16")
     fb = torch.from_numpy(sc.octree.features).to(torch.bfloat16).to(torch.float64).numpy()
     o = _oracle_grads(sc, pose, [cam], [gF], [gA], features=fb)
-    _close(g[0], o[0], 3e-4, "dL/df (bf16 storage)")
-    _close(g[1], o[1], 1e-3, "dL/dsigma (bf16 storage)")
-    _close(g[2], o[2], 5e-3, "dL/dw (bf16 storage)")
+    _compare(g, o, _conditioning(sc, pose, [cam], [gF], [gA], o, features=fb))

@@ -3,17 +3,16 @@ oracle computes one by one (brute force over every voxel), in the launch
 configuration the benchmark times.
 
 - 1M voxels, FP32 features, one 1024x1024 view of the walk cycle: the plain
-  FP32 form, within 1e-4.
+  FP32 form, within 1e-4 on every sampled pixel except those whose F the
+  rounding of entry distances decides: two consecutive composited hits with
+  entry distances within 1e-6 m (2.5x the FP32 error of a difference of two
+  entry distances at 2 m) whose swap would move a channel by more than
+  1e-5 (the oracle reports T alpha_i alpha_j |f_i - f_j| per pixel).
 - 1M voxels, BF16 features, the stereo pair of 1920x1080 views (6.4 cm
-  baseline) with the learned interval skip and the trained proposal: within
-  the skip's lost-mass bound (max_missed = 1e-3 of the feature scale and of
-  alpha) of the oracle run on the same BF16-rounded features.
-
-A pixel whose FP32 render is ill-conditioned (a grazing hit decided by
-rounding) can sit outside these bounds; such pixels are a few percent of the
-covered ones at the small sizes (tests/test_gpu_proposal.py), so the tests
-require 97 % of the sampled pixels within the bound and bound the rest
-loosely.
+  baseline) with the learned interval skip and the trained proposal: every
+  sampled pixel within the skip's lost-mass bound (max_missed = 1e-3 of the
+  feature scale and of alpha) of the oracle run on the same BF16-rounded
+  features.
 """
 import os
 
@@ -48,15 +47,16 @@ def _samples(A, n_cov, n_bg, seed):
     return pick % W, pick // W
 
 
-def _check(F, A, o, px, py, tol_f, tol_a, what):
+def _check(F, A, o, px, py, tol_f, tol_a, what, exclude=None):
     dF = np.abs(F[py, px] - o["F"]).max(1)
     dA = np.abs(A[py, px] - o["A"])
+    keep = np.ones(dF.shape, bool) if exclude is None else ~exclude
     ok = (dF <= tol_f) & (dA <= tol_a)
-    msg = (f"{what}: {ok.mean():.4f} of {ok.size} sampled pixels within ({tol_f:.2e}, {tol_a:.2e}); "
-           f"max |dF| {dF.max():.3e}, max |dA| {dA.max():.3e}")
+    msg = (f"{what}: {int(ok[keep].sum())} of {int(keep.sum())} compared pixels within ({tol_f:.2e}, {tol_a:.2e}) "
+           f"({int((~keep).sum())} order-ambiguous left out); max |dF| {dF[keep].max():.3e}, "
+           f"max |dA| {dA[keep].max():.3e}; over all samples max |dF| {dF.max():.3e}")
     print(msg)
-    assert ok.mean() >= 0.97, msg
-    assert dF.max() <= 5e-2 and dA.max() <= 5e-2, msg
+    assert ok[keep].all(), msg
 
 
 def test_fullsize_plain_f32_1024_sampled():
@@ -76,8 +76,10 @@ def test_fullsize_plain_f32_1024_sampled():
     F, A = F.cpu().numpy(), A.cpu().numpy()
     px, py = _samples(A, 384, 64, seed=11)
     _, A_or, _ = oracle.pose_transforms(sc, pose)
-    o = oracle.pixels(oc, A_or, cam, px, py)
-    _check(F, A, o, px, py, 1e-4, 1e-4, "1M voxels, FP32 plain, 1024^2")
+    o = oracle.pixels(oc, A_or, cam, px, py, tie_eps=1e-6)
+    tied = o["tie"] > 1e-5
+    assert tied.mean() <= 0.1, tied.mean()
+    _check(F, A, o, px, py, 1e-4, 1e-4, "1M voxels, FP32 plain, 1024^2", exclude=tied)
 
 
 def test_fullsize_stereo_1080p_bf16_learned_skip_sampled():

@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 import scenegen as sg
-from helpers import renderer, set_cam
+from helpers import order_ambiguous, renderer, set_cam
 
 pytestmark = pytest.mark.gpu
 
@@ -187,10 +187,12 @@ def test_skip_render_matches_oracle(seed, margin):
     bu = oracle.tile_union_bins(bins, cam, margin)
     bu[~act_px] = [0, 63]  # tiles without instances were not predicted: nothing to composite there
     ro = oracle.render_interval(sc.octree, A, cam, bu)
-    full = oracle.render(sc.octree, A, cam)
-    # pixels whose plain FP32 render is well conditioned (no near-tied or grazing hit moves it by 5e-5)
-    good = (np.abs(F0g - full["F"].reshape(-1, C)).max(1) <= 5e-5) & (np.abs(A0g - full["A"].reshape(-1)) <= 5e-5)
-    assert good.mean() > 0.97, good.mean()
+    full = oracle.render(sc.octree, A, cam, hits=True)
+    # pixels whose F the rounding of entry distances does not decide; there
+    # the plain FP32 render is the oracle's within 1e-4
+    good = ~order_ambiguous(full, sc.octree, H, W).reshape(-1)
+    np.testing.assert_allclose(F0g[good], full["F"].reshape(-1, C)[good], atol=1e-4)
+    np.testing.assert_allclose(A0g[good], full["A"].reshape(-1)[good], atol=1e-4)
     keep = ~in_fb & good & ~ro["amb"].reshape(-1).astype(bool)
     assert keep.sum() > 0.5 * (~in_fb).sum()
     np.testing.assert_allclose(Fg[keep], ro["F"].reshape(-1, C)[keep], atol=1e-4)

@@ -239,6 +239,30 @@ def test_two_stacked_voxels_closed_form():
     assert list(r["hit_id"]) == [1, 0]
 
 
+def test_pixels_tie_effect_closed_form():
+    # Two coincident voxels (the same cell, different features and
+    # densities) are entered at the same distance: their order is a tie, and
+    # swapping them changes F by alpha_1 alpha_2 (f_1 - f_2) (T = 1 before
+    # them); a third voxel stacked behind is no tie.  The oracle's per-pixel
+    # report is the largest channel of that change, 0 for tie_eps below every
+    # gap, and 0 for a pixel with a single hit.
+    oc = make_octree([[5, 5, 5], [5, 5, 5], [5, 5, 6]], dens=[7.0, 11.0, 5.0], C=3)
+    c0 = voxel_center(oc, 0)
+    cam = axis_camera(c0, (0, 0, 1))
+    a1 = 1 - math.exp(-7.0 * oc.h)
+    a2 = 1 - math.exp(-11.0 * oc.h)
+    f = oc.features.astype(float)
+    o = oracle.pixels(oc, identity_A(3), cam, [0], [0], tie_eps=1e-6)
+    np.testing.assert_allclose(o["tie"][0], a1 * a2 * np.abs(f[0] - f[1]).max(), rtol=1e-12)
+    # the two orders' sums, written out
+    F01 = a1 * f[0] + (1 - a1) * a2 * f[1]
+    F10 = a2 * f[1] + (1 - a2) * a1 * f[0]
+    np.testing.assert_allclose(np.abs(F01 - F10).max(), o["tie"][0], rtol=1e-12)
+    assert oracle.pixels(oc, identity_A(3), cam, [0], [0], tie_eps=0.0)["tie"][0] == 0.0
+    one = make_octree([[5, 5, 5]], C=3)
+    assert oracle.pixels(one, identity_A(1), cam, [0], [0])["tie"][0] == 0.0
+
+
 def test_near_far_clip():
     oc = make_octree([[8, 8, 8]], C=1)
     c = voxel_center(oc, 0)

@@ -59,3 +59,25 @@ def test_static_sort_rejects_more_than_its_maximum():
     v = torch.zeros(n, dtype=torch.int32, device="cuda")
     assert art.sort_pairs_static(k, v, 32) == 1  # ART_ERR_INVALID_ARG, nothing launched
     assert art.sort_pairs_static(k[:10], v[:10], 12) == 1  # key_bits not a multiple of 8
+
+
+def test_static_sort_rejects_host_memory_and_mismatched_arrays():
+    import ctypes
+
+    import torch
+    import paper_2202_05628_gb300 as art
+    # host arrays: refused by the library's pointer check before any launch
+    k = np.zeros(64, np.uint32)
+    v = np.zeros(64, np.uint32)
+    st = art.library().art_sort_pairs_static(k.ctypes.data, v.ctypes.data, 64, 32,
+                                             ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == 1  # ART_ERR_INVALID_ARG
+    # the binding refuses arrays of different lengths or widths
+    kd = torch.zeros(64, dtype=torch.int32, device="cuda")
+    with pytest.raises(ValueError):
+        art.sort_pairs_static(kd, torch.zeros(63, dtype=torch.int32, device="cuda"))
+    with pytest.raises(ValueError):
+        art.sort_pairs_static(kd, torch.zeros(64, dtype=torch.int64, device="cuda"))
+    # and a valid call still works afterwards
+    assert art.sort_pairs_static(kd, torch.arange(64, dtype=torch.int32, device="cuda"), 32) == 0
+    torch.cuda.synchronize()
