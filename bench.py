@@ -321,6 +321,185 @@ def backward_timing(sc, cams, poses, layers, steps, flush, warmup=3):
             "what": "dL/df, dL/dsigma, dL/dw through the F and A maps, dense upstream gradient"}
 
 
+STEREO = (1920, 1080, 0.032)  # config 5: two 1920x1080 eyes, 6.4 cm baseline
+
+
+def stereo_cams(sc, az_index):
+    import scenegen as sg
+    W, H, b = STEREO
+    return [sg.orbit_camera(sc.centroid, W, H, az_deg=45.0 * az_index, shift_x=s) for s in (-b, b)]
+
+
+def stereo_timing(sc, poses, layers, prop, flush, steps, warmup=3, oracle_psnr=True):
+    """Stereo frames (both eyes of one pose) of the 1M-voxel octree at
+    1920x1080 per eye: pose, both eyes' F and A maps, the U-Net on each.
+    Forms: the BF16 plain traversal with both eyes in one pass
+    (art_render_views: one tile space, one scan, scatter, sort and composite
+    walk) and the same as two single-view passes; BF16 + learned skip (per
+    eye); FP32 plain.  Cameras are set per frame (an orbit azimuth per step,
+    as a moving head would); CUDA events around each stereo frame, the L2
+    flushed between frames outside them."""
+    import torch
+    import paper_2202_05628_gb300 as art
+    W, H, _ = STEREO
+    oc = sc.octree
+    out = {"resolution": [W, H], "baseline_m": 2 * STEREO[2], "steps": steps}
+    Fe = [torch.empty((H, W, oc.C), dtype=torch.bfloat16, device="cuda") for _ in range(2)]
+    F32 = [torch.empty((H, W, oc.C), dtype=torch.float32, device="cuda") for _ in range(2)]
+    Ae = [torch.empty((H, W), dtype=torch.float32, device="cuda") for _ in range(2)]
+    rgba = [torch.empty((H, W, 4), dtype=torch.float32, device="cuda") for _ in range(2)]
+    first = {}
+
+    def run(form, joint):
+        storage, net, skip, desc = FORMS[form]
+        rr = setup_renderer(sc, stereo_cams(sc, 0), layers, form, proposal=prop)
+        Fo = F32 if storage == "f32" and net == "f32" else Fe
+        fdt = "f32" if net == "f32" else "bf16"
+        stream = torch.cuda.current_stream()
+
+        def frame(k):
+            pi, vi = step_indices(k)
+            p = poses[pi]
+            for v, c in enumerate(stereo_cams(sc, vi)):
+                rr.set_camera(v, c.W, c.H, c.fx, c.fy, c.cx, c.cy, c.world_to_cam, c.near, c.far)
+            rr.set_pose(p.axis_angle, p.R, p.T)
+            if joint:
+                rr.render_views([0, 1], Fo, Ae, fdt)
+            else:
+                for v in range(2):
+                    rr.render_feature_maps(v, Fo[v], Ae[v], fdt)
+            for v in range(2):
+                rr.shade(v, Fo[v], rgba[v], fdt)
+
+        n = steps if net != "f32" else max(2, steps // 8)
+        for k in range(warmup):
+            frame(k)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        for k in range(n):
+            flush.zero_()
+            ev[k][0].record(stream)
+            frame(warmup + k)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+        frame(0)
+        torch.cuda.synchronize()
+        first[form + ("_joint" if joint else "")] = rgba[0].cpu().numpy()
+        rr.close()
+        return {"stereo_frames_per_s": 1e3 / ms, "ms_per_stereo_frame": ms, "steps": n, "form": desc,
+                "eyes": ("art_render_views: the eyes one after another (learned skip)" if skip else
+                         "one pass (art_render_views)") if joint else "two single-view passes"}
+
+    out["bf16_one_pass"] = run("bf16", True)
+    out["bf16_two_passes"] = run("bf16", False)
+    out["bf16_skip"] = run("bf16_skip", True)
+    out["f32_plain"] = run("f32", True)
+    if oracle_psnr:
+        import oracle
+        pi, vi = step_indices(0)
+        cam = stereo_cams(sc, vi)[0]
+        ref = oracle.render_frame(sc, poses[pi], cam, layers)["rgba"]
+        out["quality_left_eye"] = {k: quality(x, ref) for k, x in first.items()}
+        out["quality_left_eye"]["frame"] = "pose %d, azimuth %d, left eye, against the FP64 oracle" % (pi, vi)
+    return out
+
+
+def two_branch_timing(sc, cams, poses, flush, reps=10):
+    """The paper's two-branch shading network (appearance U-Net F -> I_f,
+    opacity U-Net [A, I_f] -> alpha, both BF16 on the tensor cores) on one
+    1024^2 frame's maps, per call, beside the single network."""
+    import torch
+    import paper_2202_05628_gb300 as art
+    import scenegen as sg
+    oc = sc.octree
+    rgb, alpha = sg.two_branch_weights(0, cin=oc.C)
+    r = setup_renderer(sc, cams, None, "bf16")
+    r.load_shader(art.ART_NET_TWO_BRANCH, oc.C, sg.UNET_CHANNELS, 4, art.flat_params(rgb + alpha), "bf16",
+                  ach=sg.ALPHA_CHANNELS)
+    p = poses[0]
+    r.set_pose(p.axis_angle, p.R, p.T)
+    F = torch.empty((RES, RES, oc.C), dtype=torch.bfloat16, device="cuda")
+    A = torch.empty((RES, RES), dtype=torch.float32, device="cuda")
+    out = torch.empty((RES, RES, 4), dtype=torch.float32, device="cuda")
+    r.render_feature_maps(0, F, A, "bf16")
+    for _ in range(3):
+        r.shade_with_opacity(0, F, A, out, "bf16")
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for a, b in ev:
+        flush.zero_()
+        a.record(stream)
+        r.shade_with_opacity(0, F, A, out, "bf16")
+        b.record(stream)
+    torch.cuda.synchronize()
+    r.close()
+    return {"ms_per_call": float(np.mean([a.elapsed_time(b) for a, b in ev])),
+            "what": "art_shade_with_opacity, BF16 tensor cores: appearance U-Net 32-64-128-256 + opacity U-Net "
+                    + "-".join(str(c) for c in sg.ALPHA_CHANNELS) + " at 1024^2"}
+
+
+def walk_quality(sc, cams, poses, layers, prop, psnr_frames=(20, 40), n_cov=48, n_bg=16):
+    """Error against the FP64 oracle per frame over the 60-frame walk cycle
+    (each frame at its azimuth of the timed schedule): max-abs of F and A on
+    seeded sampled pixels (n_cov the animal covers, n_bg others; the oracle
+    brute-forces each over all voxels, on the unrounded FP32 features) for
+    the FP32 plain form and the BF16 + learned-skip form; pixels whose F the
+    rounding of entry distances decides are left out of the FP32 figure and
+    counted.  RGBA PSNR of the BF16 + learned-skip frame on psnr_frames
+    (full oracle frames)."""
+    import torch
+    import oracle
+    oc = sc.octree
+    rf = setup_renderer(sc, cams, layers, "f32", proposal=prop)
+    rs = setup_renderer(sc, cams, layers, "bf16_skip", proposal=prop)
+    F32 = torch.empty((RES, RES, oc.C), dtype=torch.float32, device="cuda")
+    A32 = torch.empty((RES, RES), dtype=torch.float32, device="cuda")
+    Fb = torch.empty((RES, RES, oc.C), dtype=torch.bfloat16, device="cuda")
+    Ab = torch.empty((RES, RES), dtype=torch.float32, device="cuda")
+    rng = np.random.default_rng(1234)
+    per = {"f32_plain": {"F_max_abs": [], "A_max_abs": [], "order_ambiguous_left_out": 0},
+           "bf16_skip": {"F_max_abs": [], "A_max_abs": []}}
+    for f in range(N_POSES):
+        pi, vi = step_indices(f)
+        p = poses[pi]
+        for rr in (rf, rs):
+            rr.set_pose(p.axis_angle, p.R, p.T)
+        rf.render_feature_maps(vi, F32, A32, "f32")
+        rs.render_feature_maps(vi, Fb, Ab, "bf16")
+        torch.cuda.synchronize()
+        a = A32.cpu().numpy().reshape(-1)
+        cov, bg = np.flatnonzero(a > 0), np.flatnonzero(a <= 0)
+        pick = np.concatenate([rng.choice(cov, min(n_cov, cov.size), replace=False),
+                               rng.choice(bg, min(n_bg, bg.size), replace=False)])
+        px, py = pick % RES, pick // RES
+        _, A, _ = oracle.pose_transforms(sc, p)
+        o = oracle.pixels(oc, A, cams[vi], px, py, tie_eps=1e-6)
+        keep = o["tie"] <= 1e-5
+        for name, Fm, Am, k in (("f32_plain", F32, A32, keep), ("bf16_skip", Fb, Ab, np.ones_like(keep))):
+            Fg = Fm.float().cpu().numpy()[py, px]
+            Ag = Am.cpu().numpy()[py, px]
+            per[name]["F_max_abs"].append(float(np.abs(Fg - o["F"]).max(1)[k].max()))
+            per[name]["A_max_abs"].append(float(np.abs(Ag - o["A"])[k].max()))
+        per["f32_plain"]["order_ambiguous_left_out"] += int((~keep).sum())
+    for v in per.values():
+        v["worst_F"] = max(v["F_max_abs"])
+        v["worst_A"] = max(v["A_max_abs"])
+    rgba = torch.empty((RES, RES, 4), dtype=torch.float32, device="cuda")
+    ps = {}
+    for f in psnr_frames:
+        pi, vi = step_indices(f)
+        p = poses[pi]
+        rs.render_frame(vi, p.axis_angle, p.R, p.T, rgba)
+        torch.cuda.synchronize()
+        ref = oracle.render_frame(sc, p, cams[vi], layers)["rgba"]
+        ps[str(f)] = quality(rgba.cpu().numpy(), ref)
+    rf.close()
+    rs.close()
+    return {"frames": N_POSES, "samples_per_frame": n_cov + n_bg, **per, "bf16_skip_rgba_by_frame": ps,
+            "what": "per walk-cycle frame (pose f, azimuth of step f) against the FP64 oracle"}
+
+
 def gpu_arm(args):
     import torch
     import torch.distributed as dist
@@ -462,6 +641,9 @@ def gpu_arm(args):
             if form not in (args.form, "f32"):
                 result[form + "_form"] = side(form, args.side_steps)
         result["backward"] = backward_timing(sc, cams, poses, layers, args.side_steps, flush)
+        result["two_branch"] = two_branch_timing(sc, cams, poses, flush)
+        result["stereo_1080p"] = stereo_timing(sc, poses, layers, prop, flush, max(4, args.side_steps // 2),
+                                               oracle_psnr=(rank == 0 and world == 1 and not args.no_cpu_baseline))
     # end to end through the public call with host buffers
     if not args.no_e2e:
         r = setup_renderer(sc, cams, layers, args.form, proposal=prop)
@@ -489,6 +671,7 @@ def gpu_arm(args):
         result["cpu_baseline"], ref = cpu_baseline(sc, cams, poses, layers)
         result["quality"] = {f: quality(x, ref) for f, x in frames.items()}
         result["quality"]["frame"] = "pose %d, azimuth %d against the FP64 oracle" % step_indices(0)
+        result["quality"]["walk_cycle"] = walk_quality(sc, cams, poses, layers, prop)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -555,24 +738,34 @@ def reference_arm(args):
     oracle.build()
     per = RES // TILE
 
+    posed = {}
+
     def step(k):
-        pi, vi = step_indices(k)
+        # 16 consecutive steps are one frame: its FK + LBS once (in the
+        # frame's first step), the F / A maps and the U-Net of one square each
+        f = k // (per * per)
+        pi, vi = step_indices(f)
         c = cams[vi]
         q = k % (per * per)
         x0, y0 = TILE * (q % per), TILE * (q // per)
         crop = dataclasses.replace(c, W=TILE, H=TILE, cx=c.cx - x0, cy=c.cy - y0)
-        oracle.render_frame(sc, poses[pi], crop, layers)
+        if posed.get("frame") != f:
+            posed["frame"], posed["A"] = f, oracle.pose_transforms(sc, poses[pi])[1]
+        F = oracle.render(sc.octree, posed["A"], crop)["F"]
+        oracle.shade_unet(F, layers)
 
+    w0 = per * per * ((args.warmup + per * per - 1) // (per * per))  # timed steps start on a frame
     for k in range(args.warmup):
         step(k)
     t0 = time.perf_counter()
     for k in range(args.steps):
-        step(args.warmup + k)
+        step(w0 + k)
     t_all = time.perf_counter() - t0
     frac = (TILE * TILE) / float(RES * RES)
     v = args.steps * frac / t_all
-    sample = (f"{args.steps} steps, each FK + LBS of {sc.octree.n} voxels, F/A maps of one {TILE}x{TILE} square of "
-              f"the {RES}x{RES} view and the U-Net over it (1/{per * per} frame per step)")
+    sample = (f"{args.steps} steps, each the F/A maps of one {TILE}x{TILE} square of the {RES}x{RES} view and the "
+              f"U-Net over it (1/{per * per} frame per step), FK + LBS of {sc.octree.n} voxels once per frame "
+              f"({per * per} steps)")
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "frames/s", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",

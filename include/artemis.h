@@ -55,7 +55,7 @@ enum { ART_F32 = 0, ART_BF16 = 1, ART_F16 = 2, ART_FP8 = 3 };
 
 /* shading network architectures (Sec. 3.1 "Neural Shading"; the single-branch
  * "Light" form of Sec. 6 "Runtime Analysis", RGB and alpha from one net) */
-enum { ART_NET_TINY = 0, ART_NET_UNET = 1 };
+enum { ART_NET_TINY = 0, ART_NET_UNET = 1, ART_NET_TWO_BRANCH = 2 };
 
 /* ---------------------------------------------------------------- context */
 
@@ -212,10 +212,11 @@ art_status art_render_backward(art_ctx* ctx, int view, const float* F, const flo
 /* ----------------------------------------------------------------- shading */
 
 typedef struct {
-  int arch;     /* ART_NET_TINY or ART_NET_UNET */
+  int arch;     /* ART_NET_TINY, ART_NET_UNET or ART_NET_TWO_BRANCH */
   int cin;      /* input channels (= C of the feature map) */
-  int ch[4];    /* TINY: ch[0] hidden width; UNET: widths of the 4 levels */
-  int cout;     /* output channels (4 = RGBA) */
+  int ch[4];    /* TINY: ch[0] hidden width; UNET, TWO_BRANCH: widths of the 4 levels (appearance branch) */
+  int cout;     /* output channels (4 = RGBA; TWO_BRANCH: 4) */
+  int ach[2];   /* TWO_BRANCH: widths of the opacity branch's 2 levels */
 } art_net_desc;
 
 /*
@@ -225,6 +226,13 @@ typedef struct {
  * UNET: 4 levels; per level two conv3x3 + ReLU; 2x2 max-pool between
  *       levels; decoder: nearest x2 upsample, channel concat [upsampled,
  *       skip], two conv3x3 + ReLU; head conv1x1 -> cout, sigmoid.
+ * TWO_BRANCH: the paper's two-branch G (Sec. 3.1 "Neural Shading", Fig. 4):
+ *       an appearance UNET (widths ch) from F to the texture image I_f
+ *       (3 channels, sigmoid head), then an opacity U-Net of 2 levels
+ *       (widths ach) from [A, I_f] (4 channels, the coarse opacity map
+ *       first) to alpha (1 channel, sigmoid head); RGBA = [I_f, alpha].
+ *       params: the appearance layers, then the opacity layers.  Shaded
+ *       with art_shade_with_opacity (it needs A); F32 or BF16 only.
  * params: float array, for every layer in execution order its weights
  *   [Cout][k][k][Cin] followed by its bias [Cout]; n_params must match.
  * compute_dtype: ART_F32 (CUDA-core FP32), ART_BF16 (tensor cores, BF16
@@ -243,6 +251,30 @@ art_status art_load_shader(art_ctx* ctx, const art_net_desc* desc, const float* 
  * multiples of 8 for UNET) into rgba_out [H][W][cout] float (device or host).
  */
 art_status art_shade(art_ctx* ctx, int view, const void* F, int F_dtype, float* rgba_out);
+
+/*
+ * Shade with a network that also reads the coarse opacity map A [H][W]
+ * float (host or device; Eq. 5's accumulated alpha, as written by
+ * art_render_feature_maps): the TWO_BRANCH network (Sec. 3.1 "Neural
+ * Shading").  Other networks ignore A.  F and rgba_out as in art_shade.
+ */
+art_status art_shade_with_opacity(art_ctx* ctx, int view, const void* F, int F_dtype, const float* A, float* rgba_out);
+
+/*
+ * Several views of the current pose in one pass (the paper's stereo VR
+ * pairs and multi-view rendering, Sec. 5-6): one projection per view into
+ * one tile space (the views' screen tiles end to end), one scan, scatter and
+ * sort of all their instances, one composite walk over all their tiles.
+ *   nv       1 .. 8 distinct views (set with art_set_camera), listed in views
+ *   F_out    nv DEVICE arrays [H_k][W_k][C] in F_dtype (F32 or BF16)
+ *   A_out    NULL, or nv DEVICE arrays [H_k][W_k] float (entries may be NULL)
+ * Each view's maps equal those of art_render_feature_maps up to the
+ * regrouping of FP32 sums (the joint tile space has its own depth-key
+ * layout, hence other segment cuts).  With the learned skip or SH features
+ * configured, the views are rendered one after another instead.
+ */
+art_status art_render_views(art_ctx* ctx, int nv, const int* views, void* const* F_out, int F_dtype,
+                            float* const* A_out);
 
 /* One frame of one view: art_set_pose + art_render_feature_maps into
  * library-owned buffers + art_shade.  rgba_out as in art_shade. */
@@ -332,10 +364,12 @@ typedef struct {
   int64_t instances;       /* (tile, voxel) instances of the last render */
   int64_t degenerate;      /* voxels dropped at the last pose (det < 1e-3) */
   int64_t overflow_inst;   /* instances that did not fit instance_cap */
-  int64_t overflow_order;  /* pixel hits released early because the per-pixel
-                              reorder buffer was full (result may be out of order) */
+  int64_t overflow_order;  /* pixels whose hits could not all be put in order: more than
+                              1024 hits on one ray (result may be out of order) */
   int64_t kernel_launches; /* kernels launched by this context so far */
   int64_t fallback_tiles;  /* learned skip: tiles of the last render traversed again in full */
+  int64_t exact_tiles;     /* tiles of the last render walked again exactly because a pixel
+                              had more pending hits than its 16-entry reorder buffer holds */
 } art_stats;
 
 /* Synchronise the stream, fill *out (may be NULL) and return

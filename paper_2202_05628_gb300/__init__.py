@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libartemis_gb.so")
 
 ART_F32, ART_BF16, ART_F16, ART_FP8 = 0, 1, 2, 3
-ART_NET_TINY, ART_NET_UNET = 0, 1
+ART_NET_TINY, ART_NET_UNET, ART_NET_TWO_BRANCH = 0, 1, 2
 (BUF_JOINT_G, BUF_VOXEL_REC, BUF_VOXEL_GEO, BUF_RECT, BUF_DEPTHKEY, BUF_KEYS, BUF_VALS, BUF_RANGES, BUF_FP8_SCALES,
  BUF_ACTIVATIONS, BUF_BINS, BUF_FALLBACK, BUF_TAU_HIST) = range(13)
 SKIP_PLAIN, SKIP_LEARNED = 0, 1
@@ -35,7 +35,8 @@ class ArtemisError(RuntimeError):
 
 
 class NetDesc(ctypes.Structure):
-    _fields_ = [("arch", ctypes.c_int), ("cin", ctypes.c_int), ("ch", ctypes.c_int * 4), ("cout", ctypes.c_int)]
+    _fields_ = [("arch", ctypes.c_int), ("cin", ctypes.c_int), ("ch", ctypes.c_int * 4), ("cout", ctypes.c_int),
+                ("ach", ctypes.c_int * 2)]
 
 
 class Config(ctypes.Structure):
@@ -47,7 +48,7 @@ class Config(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("instances", ctypes.c_int64), ("degenerate", ctypes.c_int64), ("overflow_inst", ctypes.c_int64),
                 ("overflow_order", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
-                ("fallback_tiles", ctypes.c_int64)]
+                ("fallback_tiles", ctypes.c_int64), ("exact_tiles", ctypes.c_int64)]
 
 
 def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -73,6 +74,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "art_sync_status": [vp, ctypes.POINTER(Stats)],
         "art_get_kernel_times": [vp, i32, vp, vp, vp, ctypes.POINTER(i32), i32],
         "art_sort_pairs": [vp, vp, vp, i64, i32],
+        "art_shade_with_opacity": [vp, i32, vp, i32, vp, vp],
+        "art_render_views": [vp, i32, vp, vp, i32, vp],
         "art_sort_pairs_static": [vp, vp, i64, i32, vp],
         "art_update_voxels": [vp, vp, vp, vp],
         "art_render_backward": [vp, i32, vp, vp, vp, vp, vp, vp, vp],
@@ -179,8 +182,10 @@ class Renderer:
         self._check(_lib.art_set_camera(self._h, view, W, H, fx, fy, cx, cy, _ptr(M), near, far))
         self.views[view] = (W, H)
 
-    def load_shader(self, arch: int, cin: int, ch: Sequence[int], cout: int, params, dtype: str = "f32"):
-        d = NetDesc(arch, cin, (ctypes.c_int * 4)(*(list(ch) + [0] * (4 - len(ch)))), cout)
+    def load_shader(self, arch: int, cin: int, ch: Sequence[int], cout: int, params, dtype: str = "f32",
+                    ach: Sequence[int] = (0, 0)):
+        d = NetDesc(arch, cin, (ctypes.c_int * 4)(*(list(ch) + [0] * (4 - len(ch)))), cout,
+                    (ctypes.c_int * 2)(*list(ach)))
         p = _np(params, np.float32).reshape(-1)
         self._check(_lib.art_load_shader(self._h, ctypes.byref(d), _ptr(p), p.size, DTYPES[dtype]))
 
@@ -199,6 +204,16 @@ class Renderer:
 
     def shade(self, view: int, F, rgba_out, F_dtype: str = "f32"):
         self._check(_lib.art_shade(self._h, view, _ptr(F), DTYPES[F_dtype], _ptr(rgba_out)))
+
+    def render_views(self, views: Sequence[int], F_outs, A_outs=None, F_dtype: str = "f32"):
+        nv = len(views)
+        vv = (ctypes.c_int * nv)(*views)
+        fp = (ctypes.c_void_p * nv)(*[_ptr(f) for f in F_outs])
+        ap = None if A_outs is None else (ctypes.c_void_p * nv)(*[_ptr(a) for a in A_outs])
+        self._check(_lib.art_render_views(self._h, nv, vv, fp, DTYPES[F_dtype], ap))
+
+    def shade_with_opacity(self, view: int, F, A, rgba_out, F_dtype: str = "f32"):
+        self._check(_lib.art_shade_with_opacity(self._h, view, _ptr(F), DTYPES[F_dtype], _ptr(A), _ptr(rgba_out)))
 
     def render_frame(self, view: int, axis_angle, R, T, rgba_out):
         aa = axis_angle if hasattr(axis_angle, "data_ptr") else _np(axis_angle, np.float32)
@@ -241,7 +256,7 @@ class Renderer:
             self._check(st)
         return dict(instances=s.instances, degenerate=s.degenerate, overflow_inst=s.overflow_inst,
                     overflow_order=s.overflow_order, kernel_launches=s.kernel_launches,
-                    fallback_tiles=s.fallback_tiles, status=st)
+                    fallback_tiles=s.fallback_tiles, exact_tiles=s.exact_tiles, status=st)
 
     def kernel_times(self, reset: bool = False) -> dict:
         cap = 64

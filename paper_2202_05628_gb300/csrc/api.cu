@@ -143,12 +143,22 @@ __global__ void convert_kernel<__half>(int64_t m, const float* __restrict__ in, 
   if (i < m) out[i] = __float2half_rn(in[i]);
 }
 
-__global__ void round_bf16_kernel(int64_t m, float* __restrict__ w, __nv_bfloat16* __restrict__ wb) {
+// BF16 copy wb [..][cin_pad] of the FP32 weights w [..][cin] (input channels
+// innermost; channels cin .. cin_pad - 1 zero); w is rounded in place so
+// that its FP32 values are the BF16 ones.
+__global__ void round_bf16_kernel(int64_t m, int cin, int cin_pad, float* __restrict__ w,
+                                  __nv_bfloat16* __restrict__ wb) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < m) {
-    __nv_bfloat16 b = __float2bfloat16_rn(w[i]);
+    const int ci = (int)(i % cin_pad);
+    if (ci >= cin) {
+      wb[i] = __float2bfloat16_rn(0.0f);
+      return;
+    }
+    const int64_t j = (i / cin_pad) * cin + ci;
+    __nv_bfloat16 b = __float2bfloat16_rn(w[j]);
     wb[i] = b;
-    w[i] = __bfloat162float(b);
+    w[j] = __bfloat162float(b);
   }
 }
 
@@ -174,7 +184,8 @@ void free_all(art_ctx* ctx) {
                   ctx->d_shist, ctx->d_sbsum, ctx->d_gN, ctx->d_f8_scale, ctx->d_f8_amax, ctx->d_prop_img,
                   ctx->d_prop_f32, ctx->d_pose_bias, ctx->d_bins, ctx->d_thist, ctx->d_hbin, ctx->d_htau, ctx->d_fbq,
                   ctx->d_seg, ctx->d_items, ctx->d_multi, ctx->d_part, ctx->d_fbq2, ctx->d_tcount, ctx->d_toff,
-                  ctx->d_sortlist, ctx->d_scan_state, ctx->d_agroups, ctx->d_sh, ctx->d_sh_rot};
+                  ctx->d_sortlist, ctx->d_scan_state, ctx->d_agroups, ctx->d_sh, ctx->d_sh_rot, ctx->d_rect_v,
+                  ctx->d_q_v, ctx->d_cnt_v, ctx->d_vset, ctx->d_xflag, ctx->d_xqueue, ctx->d_xhit, ctx->d_xpos};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& L : ctx->layers) {
@@ -251,9 +262,8 @@ art_status ensure_skip_buffers(art_ctx* ctx, const ViewParams& v) {
 
 // Buffers of the split composite walk for `view`: per-tile plan, segment
 // lists and partial sums (segments <= instances / seg_len + tiles).
-art_status ensure_split_buffers(art_ctx* ctx, const ViewParams& v) {
+art_status ensure_split_buffers(art_ctx* ctx, size_t ntiles) {
   art_status st;
-  const size_t ntiles = (size_t)v.tiles_x * v.tiles_y;
   const size_t items = (size_t)(ctx->inst_cap / std::max(32, ctx->seg_len / 4)) + ntiles + 1;  // re-walks: seg_len / 4
   if ((st = ensure(ctx, (void**)&ctx->d_seg, &ctx->d_seg_bytes, ntiles * sizeof(uint2), "segment plan")) != ART_OK)
     return st;
@@ -265,6 +275,15 @@ art_status ensure_split_buffers(art_ctx* ctx, const ViewParams& v) {
   if ((st = ensure(ctx, (void**)&ctx->d_fbq, &ctx->d_fbq_bytes, ntiles * 4, "fallback queue")) != ART_OK) return st;
   if ((st = ensure(ctx, (void**)&ctx->d_fbq2, &ctx->d_fbq2_bytes, ntiles * 4, "second fallback queue")) != ART_OK)
     return st;
+  if ((st = ensure(ctx, (void**)&ctx->d_xflag, &ctx->d_xflag_bytes, ntiles * 4, "exact re-walk flags")) != ART_OK)
+    return st;
+  if ((st = ensure(ctx, (void**)&ctx->d_xqueue, &ctx->d_xqueue_bytes, ntiles * 4, "exact re-walk queue")) != ART_OK)
+    return st;
+  if (!ctx->d_xhit) {
+    const size_t m = (size_t)kExactBlocks * 32 * kExactCap;
+    if ((st = alloc(ctx, &ctx->d_xhit, m, "exact re-walk hit lists")) != ART_OK) return st;
+    if ((st = alloc(ctx, &ctx->d_xpos, m, "exact re-walk list positions")) != ART_OK) return st;
+  }
   const int fb = ctx->feat_dtype == ART_F32 ? 4 : 2;
   ctx->composite_blocks = ctx->num_sms * composite_blocks_per_sm(ctx->C, fb);
   return ART_OK;
@@ -563,7 +582,7 @@ static art_status render_to_device(art_ctx* ctx, int view, void* F, int F_dtype,
   const ViewParams& v = ctx->views[view];
   art_status st = ensure_bin_buffers(ctx, (int64_t)v.tiles_x * v.tiles_y);
   if (st != ART_OK) return st;
-  if ((st = ensure_split_buffers(ctx, v)) != ART_OK) return st;
+  if ((st = ensure_split_buffers(ctx, (size_t)v.tiles_x * v.tiles_y)) != ART_OK) return st;
   if (ctx->cfg.skip == ART_SKIP_LEARNED) {  // proposal intervals + coarse check + fallback
     if (ctx->sh_degree >= 0)
       return fail(ctx, ART_ERR_UNSUPPORTED, "view-dependent (SH) features use the plain traversal (skip = 0)");
@@ -583,6 +602,72 @@ static art_status render_to_device(art_ctx* ctx, int view, void* F, int F_dtype,
   }
   if ((st = launch_composite(ctx, v, F, F_dtype, A)) != ART_OK) return st;
   return launch_check(ctx, "render_feature_maps");
+}
+
+art_status art_render_views(art_ctx* ctx, int nv, const int* views, void* const* F_out, int F_dtype,
+                            float* const* A_out) {
+  if (!ctx) return ART_ERR_INVALID_ARG;
+  if (nv < 1 || nv > kMaxViews || !views || !F_out) return fail(ctx, ART_ERR_INVALID_ARG, "need 1..%d views", kMaxViews);
+  if (!ctx->posed) return fail(ctx, ART_ERR_STATE, "render before set_pose");
+  if (F_dtype != ART_F32 && F_dtype != ART_BF16) return fail(ctx, ART_ERR_INVALID_ARG, "F_dtype must be F32 or BF16");
+  for (int k = 0; k < nv; ++k) {
+    const int vk = views[k];
+    if (vk < 0 || vk >= kMaxViews || !ctx->view_set[vk]) return fail(ctx, ART_ERR_STATE, "view %d not set", vk);
+    for (int j = 0; j < k; ++j)
+      if (views[j] == vk) return fail(ctx, ART_ERR_INVALID_ARG, "view %d listed twice", vk);
+    if (!F_out[k] || !is_device_ptr(F_out[k]) || (A_out && A_out[k] && !is_device_ptr(A_out[k])))
+      return fail(ctx, ART_ERR_INVALID_ARG, "render_views writes device arrays (view %d)", vk);
+  }
+  art_status st;
+  if (ctx->cfg.skip == ART_SKIP_LEARNED || ctx->sh_degree >= 0) {  // per-view passes
+    for (int k = 0; k < nv; ++k)
+      if ((st = render_to_device(ctx, views[k], F_out[k], F_dtype, A_out ? A_out[k] : nullptr)) != ART_OK) return st;
+    return ART_OK;
+  }
+  // one tile space: view k's tiles after the first k views'; one depth-key layout
+  ViewSet& vs = ctx->h_vset;
+  vs = ViewSet{};
+  vs.nv = nv;
+  int64_t total = 0;
+  for (int k = 0; k < nv; ++k) {
+    const ViewParams& v = ctx->views[views[k]];
+    vs.toff[k] = (uint32_t)total;
+    total += (int64_t)v.tiles_x * v.tiles_y;
+  }
+  vs.toff[nv] = (uint32_t)total;
+  int tb = 1;
+  while (((int64_t)1 << tb) < total) ++tb;
+  const int depth_bits = std::min(32 - tb, 20);
+  if (depth_bits < 12) return fail(ctx, ART_ERR_UNSUPPORTED, "too many tiles over the views for 32-bit keys");
+  for (int k = 0; k < nv; ++k) {
+    ViewParams v = ctx->views[views[k]];
+    v.depth_bits = depth_bits;
+    v.dscale = (float)((double)(1u << depth_bits) / ((double)v.zfar - (double)v.znear));
+    vs.v[k] = v;
+    vs.F[k] = F_out[k];
+    vs.A[k] = A_out ? A_out[k] : nullptr;
+  }
+  if ((st = ensure_bin_buffers(ctx, total)) != ART_OK) return st;
+  if ((st = ensure_split_buffers(ctx, (size_t)total)) != ART_OK) return st;
+  const int64_t need = (int64_t)nv * ctx->n;
+  if (ctx->views_cap < need) {
+    if ((st = alloc(ctx, &ctx->d_rect_v, (size_t)need, "batch voxel rects")) != ART_OK) return st;
+    if ((st = alloc(ctx, &ctx->d_q_v, (size_t)need, "batch depth keys")) != ART_OK) return st;
+    if ((st = alloc(ctx, &ctx->d_cnt_v, (size_t)need, "batch tile counts")) != ART_OK) return st;
+    ctx->views_cap = need;
+  }
+  if (!ctx->d_vset && (st = alloc(ctx, &ctx->d_vset, 1, "view table")) != ART_OK) return st;
+  vs.rect_stride = ctx->n;
+  if ((st = copy_in(ctx, ctx->d_vset, &vs, sizeof(ViewSet), "copy view table")) != ART_OK) return st;
+  cudaMemsetAsync(ctx->d_tcount, 0, sizeof(uint32_t) * (size_t)total, ctx->stream);
+  for (int k = 0; k < nv; ++k) {
+    const int64_t o = (int64_t)k * ctx->n;
+    launch_project_view(ctx, vs.v[k], ctx->d_rect_v + o, ctx->d_q_v + o, ctx->d_cnt_v + o, ctx->d_tcount + vs.toff[k],
+                        k == 0);
+  }
+  launch_bin_views(ctx, vs, total);
+  if ((st = launch_composite_views(ctx, vs, F_dtype)) != ART_OK) return st;
+  return launch_check(ctx, "render_views");
 }
 
 art_status art_render_feature_maps(art_ctx* ctx, int view, void* F_out, int F_dtype, float* A_out) {
@@ -672,18 +757,35 @@ art_status art_load_shader(art_ctx* ctx, const art_net_desc* desc, const float* 
     return fail(ctx, ART_ERR_UNSUPPORTED, "compute dtype %d not available", compute_dtype);
   std::vector<int> shapes;  // cout, cin, k
   const art_net_desc& d = *desc;
+  // (cout, cin, k) of a U-Net's layers in execution order: enc0 a/b, ...,
+  // bottleneck a/b, dec(levels-2) a/b, ..., dec0 a/b, 1x1 head
+  auto unet_shapes = [&](int cin, int levels, const int* ch, int cout) {
+    int prev = cin;
+    for (int l = 0; l < levels; ++l) {
+      shapes.insert(shapes.end(), {ch[l], prev, 3, ch[l], ch[l], 3});
+      prev = ch[l];
+    }
+    for (int l = levels - 2; l >= 0; --l) shapes.insert(shapes.end(), {ch[l], ch[l + 1] + ch[l], 3, ch[l], ch[l], 3});
+    shapes.insert(shapes.end(), {cout, ch[0], 1});
+  };
   if (d.cin < 1 || d.cout < 1 || d.cin > 256 || d.cout > 256) return fail(ctx, ART_ERR_INVALID_ARG, "cin/cout range");
   if (d.arch == ART_NET_TINY) {
     int c = d.ch[0];
     if (c < 1 || c > 256) return fail(ctx, ART_ERR_INVALID_ARG, "hidden width range");
     shapes = {c, d.cin, 3, c, c, 3, d.cout, c, 3};
-  } else if (d.arch == ART_NET_UNET) {
-    const int* ch = d.ch;
+  } else if (d.arch == ART_NET_UNET || d.arch == ART_NET_TWO_BRANCH) {
     for (int k = 0; k < 4; ++k)
-      if (ch[k] < 1 || ch[k] > 512) return fail(ctx, ART_ERR_INVALID_ARG, "channel range");
-    shapes = {ch[0], d.cin, 3, ch[0], ch[0], 3, ch[1], ch[0], 3, ch[1], ch[1], 3, ch[2], ch[1], 3, ch[2], ch[2], 3,
-              ch[3], ch[2], 3, ch[3], ch[3], 3, ch[2], ch[3] + ch[2], 3, ch[2], ch[2], 3, ch[1], ch[2] + ch[1], 3,
-              ch[1], ch[1], 3, ch[0], ch[1] + ch[0], 3, ch[0], ch[0], 3, d.cout, ch[0], 1};
+      if (d.ch[k] < 1 || d.ch[k] > 512) return fail(ctx, ART_ERR_INVALID_ARG, "channel range");
+    if (d.arch == ART_NET_UNET) {
+      unet_shapes(d.cin, 4, d.ch, d.cout);
+    } else {
+      if (d.cout != 4) return fail(ctx, ART_ERR_INVALID_ARG, "two-branch network: cout must be 4 (RGB + alpha)");
+      if (compute_dtype == ART_FP8) return fail(ctx, ART_ERR_UNSUPPORTED, "two-branch network: F32 or BF16 only");
+      for (int k = 0; k < 2; ++k)
+        if (d.ach[k] < 1 || d.ach[k] > 512) return fail(ctx, ART_ERR_INVALID_ARG, "opacity channel range");
+      unet_shapes(d.cin, 4, d.ch, 3);  // appearance: F -> I_f
+      unet_shapes(4, 2, d.ach, 1);     // opacity: [A, I_f] -> alpha
+    }
   } else {
     return fail(ctx, ART_ERR_INVALID_ARG, "unknown arch %d", d.arch);
   }
@@ -707,6 +809,9 @@ art_status art_load_shader(art_ctx* ctx, const art_net_desc* desc, const float* 
     L.cout = shapes[3 * l];
     L.cin = shapes[3 * l + 1];
     L.k = shapes[3 * l + 2];
+    // the opacity branch's first layer reads the packed [A, I_f, 0 ...] tensor on the tensor cores
+    const bool padded = d.arch == ART_NET_TWO_BRANCH && l == 15 && compute_dtype == ART_BF16;
+    L.cin_pad = padded ? kOpacityPad : L.cin;
     size_t nw = (size_t)L.cout * L.k * L.k * L.cin;
     if ((st = alloc(ctx, &L.w32, nw, "weights")) != ART_OK) break;
     if ((st = alloc(ctx, &L.b32, (size_t)L.cout, "bias")) != ART_OK) break;
@@ -715,8 +820,10 @@ art_status art_load_shader(art_ctx* ctx, const art_net_desc* desc, const float* 
     if ((st = copy_in(ctx, L.b32, params + off, (size_t)L.cout * 4, "copy bias")) != ART_OK) break;
     off += L.cout;
     if (compute_dtype == ART_BF16 || compute_dtype == ART_FP8) {
-      if ((st = alloc(ctx, &L.wbf, nw, "bf16 weights")) != ART_OK) break;
-      round_bf16_kernel<<<(unsigned)((nw + 255) / 256), 256, 0, ctx->stream>>>((int64_t)nw, L.w32, L.wbf);
+      const size_t nwp = (size_t)L.cout * L.k * L.k * L.cin_pad;
+      if ((st = alloc(ctx, &L.wbf, nwp, "bf16 weights")) != ART_OK) break;
+      round_bf16_kernel<<<(unsigned)((nwp + 255) / 256), 256, 0, ctx->stream>>>((int64_t)nwp, L.cin, L.cin_pad,
+                                                                                 L.w32, L.wbf);
     }
     if (compute_dtype == ART_FP8 && L.k == 3) {  // 1x1 head stays FP32 (fused epilogue)
       if ((st = alloc(ctx, &L.w8, nw, "fp8 weights")) != ART_OK) break;
@@ -737,13 +844,18 @@ art_status art_load_shader(art_ctx* ctx, const art_net_desc* desc, const float* 
   return sync_check(ctx, "load_shader");
 }
 
-art_status art_shade(art_ctx* ctx, int view, const void* F, int F_dtype, float* rgba_out) {
+namespace art {
+namespace {
+
+art_status shade_impl(art_ctx* ctx, int view, const void* F, int F_dtype, const float* A, float* rgba_out) {
   if (!ctx) return ART_ERR_INVALID_ARG;
   if (ctx->layers.empty()) return fail(ctx, ART_ERR_STATE, "shade before load_shader");
   if (view < 0 || view >= kMaxViews || !ctx->view_set[view]) return fail(ctx, ART_ERR_STATE, "view %d not set", view);
   if (!F || !rgba_out) return fail(ctx, ART_ERR_INVALID_ARG, "null pointer");
   const ViewParams& v = ctx->views[view];
-  if (ctx->net.arch == ART_NET_UNET && ((v.W % 8) || (v.H % 8)))
+  const bool two = ctx->net.arch == ART_NET_TWO_BRANCH;
+  if (two && !A) return fail(ctx, ART_ERR_INVALID_ARG, "the two-branch network needs A: art_shade_with_opacity");
+  if (ctx->net.arch != ART_NET_TINY && ((v.W % 8) || (v.H % 8)))
     return fail(ctx, ART_ERR_INVALID_ARG, "U-Net needs W and H multiples of 8");
   size_t npx = (size_t)v.W * v.H;
   size_t fbytes = npx * ctx->net.cin * (F_dtype == ART_F32 ? 4 : 2);
@@ -754,6 +866,12 @@ art_status art_shade(art_ctx* ctx, int view, const void* F, int F_dtype, float* 
     if ((st = copy_in(ctx, ctx->d_F, F, fbytes, "copy F")) != ART_OK) return st;
     Fd = ctx->d_F;
   }
+  const float* Ad = two ? A : nullptr;
+  if (two && !is_device_ptr(A)) {
+    if ((st = ensure(ctx, (void**)&ctx->d_A, &ctx->d_A_bytes, npx * 4, "A buffer")) != ART_OK) return st;
+    if ((st = copy_in(ctx, ctx->d_A, A, npx * 4, "copy A")) != ART_OK) return st;
+    Ad = ctx->d_A;
+  }
   bool out_dev = is_device_ptr(rgba_out);
   float* out = rgba_out;
   size_t obytes = npx * ctx->net.cout * 4;
@@ -761,13 +879,25 @@ art_status art_shade(art_ctx* ctx, int view, const void* F, int F_dtype, float* 
     if ((st = ensure(ctx, (void**)&ctx->d_rgba, &ctx->d_rgba_bytes, obytes, "rgba buffer")) != ART_OK) return st;
     out = ctx->d_rgba;
   }
-  if ((st = run_shader(ctx, v, Fd, F_dtype, out)) != ART_OK) return st;
+  if ((st = run_shader(ctx, v, Fd, F_dtype, Ad, out)) != ART_OK) return st;
   if ((st = launch_check(ctx, "shade")) != ART_OK) return st;
   if (!out_dev) {
     cudaMemcpyAsync(rgba_out, out, obytes, cudaMemcpyDeviceToHost, ctx->stream);
     return sync_check(ctx, "shade (copy out)");
   }
   return ART_OK;
+}
+
+}  // namespace
+}  // namespace art
+
+art_status art_shade(art_ctx* ctx, int view, const void* F, int F_dtype, float* rgba_out) {
+  return shade_impl(ctx, view, F, F_dtype, nullptr, rgba_out);
+}
+
+art_status art_shade_with_opacity(art_ctx* ctx, int view, const void* F, int F_dtype, const float* A, float* rgba_out) {
+  if (ctx && !A) return fail(ctx, ART_ERR_INVALID_ARG, "null A");
+  return shade_impl(ctx, view, F, F_dtype, A, rgba_out);
 }
 
 art_status art_render_frame(art_ctx* ctx, int view, const float* axis_angle, const float R[3], const float T[3],
@@ -784,7 +914,7 @@ art_status art_render_frame(art_ctx* ctx, int view, const float* axis_angle, con
   if ((st = ensure(ctx, &ctx->d_F, &ctx->d_F_bytes, fbytes, "F buffer")) != ART_OK) return st;
   if ((st = ensure(ctx, (void**)&ctx->d_A, &ctx->d_A_bytes, (size_t)v.W * v.H * 4, "A buffer")) != ART_OK) return st;
   if ((st = render_to_device(ctx, view, ctx->d_F, fdt, ctx->d_A)) != ART_OK) return st;
-  return art_shade(ctx, view, ctx->d_F, fdt, rgba_out);
+  return shade_impl(ctx, view, ctx->d_F, fdt, ctx->d_A, rgba_out);
 }
 
 art_status art_sync_status(art_ctx* ctx, art_stats* out) {
@@ -801,6 +931,7 @@ art_status art_sync_status(art_ctx* ctx, art_stats* out) {
     out->overflow_order = (int64_t)h[kStOverflowOrder];
     out->kernel_launches = ctx->launches;
     out->fallback_tiles = (int64_t)h[kStFallback];
+    out->exact_tiles = (int64_t)h[kStExactQ];
   }
   if (h[kStTcError]) {
     art_status r = fail(ctx, ART_ERR_CUDA, "tensor-core convolution: %llu CTAs timed out waiting on their pipeline",
@@ -914,7 +1045,7 @@ art_status art_render_backward(art_ctx* ctx, int view, const float* F, const flo
   const ViewParams& v = ctx->views[view];
   art_status st = ensure_bin_buffers(ctx, (int64_t)v.tiles_x * v.tiles_y);
   if (st != ART_OK) return st;
-  if ((st = ensure_split_buffers(ctx, v)) != ART_OK) return st;
+  if ((st = ensure_split_buffers(ctx, (size_t)v.tiles_x * v.tiles_y)) != ART_OK) return st;
   if (ctx->gN_cap < ctx->n) {
     if ((st = alloc(ctx, &ctx->d_gN, (size_t)ctx->n * 12, "geometry gradient")) != ART_OK) return st;
     ctx->gN_cap = ctx->n;

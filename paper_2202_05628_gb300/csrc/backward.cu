@@ -77,7 +77,7 @@ __device__ __forceinline__ void bwd_tile(const int tile, const Seg& sg, float T_
   const size_t pix = inside ? (size_t)py * v.W + px : 0;
 
   const RayDir rd = pixel_ray(v, px, py);
-  const float d0 = rd.h[0], d1 = rd.h[1], d2 = rd.h[2];
+  const float d0 = rd.h[0] * rd.inv_n, d1 = rd.h[1] * rd.inv_n, d2 = rd.h[2] * rd.inv_n;  // unit direction
 
   // upstream gradient of this pixel and the forward's outputs
   float g[C];

@@ -419,6 +419,7 @@ __global__ void __launch_bounds__(kTileScanThreads) tile_scan_kernel(int ntiles,
 __global__ void __launch_bounds__(256) bucket_emit_kernel(int64_t n, const uint32_t* __restrict__ cnt,
                                                           const short4* __restrict__ rect,
                                                           const uint32_t* __restrict__ q, ViewParams v, int64_t cap,
+                                                          uint32_t tile_base,
                                                           uint32_t* __restrict__ toff, uint32_t* __restrict__ keys,
                                                           uint32_t* __restrict__ vals,
                                                           unsigned long long* __restrict__ status,
@@ -445,7 +446,7 @@ __global__ void __launch_bounds__(256) bucket_emit_kernel(int64_t n, const uint3
   uint32_t over = 0;
   const uint32_t steps = __reduce_max_sync(0xFFFFFFFFu, c);
   for (uint32_t k = 0; k < steps; ++k) {
-    const uint32_t tile = k < c ? rect_tile(v, tx0, ty0, w, k) : 0xFFFFFFFFu;
+    const uint32_t tile = k < c ? tile_base + rect_tile(v, tx0, ty0, w, k) : 0xFFFFFFFFu;
     const unsigned grp = __match_any_sync(0xFFFFFFFFu, tile);
     const int leader = __ffs(grp) - 1;
     uint32_t pos = 0;
@@ -701,9 +702,31 @@ void launch_bin(art_ctx* ctx, const ViewParams& v, const uint32_t* hbin, const f
              ctx->d_toff, ctx->d_ranges, ctx->d_sortlist, reinterpret_cast<ScanWords*>(ctx->d_scan_state),
              ctx->d_agroups, ctx->d_status);
   ART_LAUNCH(ctx, "bin_emit", bucket_emit_kernel, vb, 256, 0, n, ctx->d_cnt, ctx->d_rect, ctx->d_q, v, ctx->inst_cap,
-             ctx->d_toff, ctx->d_keys, ctx->d_vals, ctx->d_status, hbin, htau, thist);
+             0u, ctx->d_toff, ctx->d_keys, ctx->d_vals, ctx->d_status, hbin, htau, thist);
   ART_LAUNCH(ctx, "tile_sort", tile_sort_kernel, 2 * ctx->num_sms, kTileSortThreads, kTileSortSmem * 8, ctx->d_ranges,
              ctx->d_sortlist, ntiles, v.depth_bits, ctx->d_keys, ctx->d_vals, ctx->d_sort_tmp, ctx->d_status);
+}
+
+void launch_bin_views(art_ctx* ctx, const ViewSet& vs, int64_t ntiles) {
+  const int64_t n = ctx->n;
+  const unsigned vb = (unsigned)((n + 255) / 256);
+  if (!ctx->attr_tile_sort) {
+    cudaFuncSetAttribute(tile_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileSortSmem * 8);
+    ctx->attr_tile_sort = true;
+  }
+  const int nt = (int)ntiles;
+  const int nsb = (nt + kTileScanBlock - 1) / kTileScanBlock;
+  ART_LAUNCH(ctx, "bin_scan", tile_scan_kernel, nsb, kTileScanThreads, 0, nt, ctx->d_tcount, ctx->inst_cap,
+             ctx->d_toff, ctx->d_ranges, ctx->d_sortlist, reinterpret_cast<ScanWords*>(ctx->d_scan_state),
+             ctx->d_agroups, ctx->d_status);
+  for (int k = 0; k < vs.nv; ++k) {
+    const int64_t o = (int64_t)k * vs.rect_stride;
+    ART_LAUNCH(ctx, "bin_emit", bucket_emit_kernel, vb, 256, 0, n, ctx->d_cnt_v + o, ctx->d_rect_v + o,
+               ctx->d_q_v + o, vs.v[k], ctx->inst_cap, vs.toff[k], ctx->d_toff, ctx->d_keys, ctx->d_vals,
+               ctx->d_status, (const uint32_t*)nullptr, (const float*)nullptr, (float*)nullptr);
+  }
+  ART_LAUNCH(ctx, "tile_sort", tile_sort_kernel, 2 * ctx->num_sms, kTileSortThreads, kTileSortSmem * 8, ctx->d_ranges,
+             ctx->d_sortlist, nt, vs.v[0].depth_bits, ctx->d_keys, ctx->d_vals, ctx->d_sort_tmp, ctx->d_status);
 }
 
 int launch_sort_bufs(art_ctx* ctx, uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, int64_t cap,

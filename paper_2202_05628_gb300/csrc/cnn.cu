@@ -18,8 +18,9 @@ struct ConvArgs {
   int cout, k, act;
   const float* w;  // [cout][k][k][cin] FP32
   const float* b;  // [cout]
-  void* out;       // [H][W][cout]
+  void* out;       // [H][W][out_ld], channels [out_off, out_off + cout)
   int out_f32;     // output element type FP32 (else the activation type)
+  int out_ld, out_off;
 };
 
 namespace {
@@ -107,7 +108,7 @@ __global__ void __launch_bounds__(256) conv_simt_kernel(ConvArgs a) {
       int co = co0 + tn + 16 * j;
       if (co >= a.cout) continue;
       float v = activate(acc[i][j] + a.b[co], a.act);
-      size_t o = ((size_t)y * a.W + x) * a.cout + co;
+      size_t o = ((size_t)y * a.W + x) * a.out_ld + a.out_off + co;
       if (a.out_f32)
         ((float*)a.out)[o] = v;
       else
@@ -148,29 +149,127 @@ void pool(art_ctx* ctx, const void* in, void* out, int H, int W, int C) {
 }
 
 template <typename TI>
-art_status run_typed(art_ctx* ctx, const ViewParams& v, const void* F, float* rgba) {
+ConvArgs conv_args(const void* s0, int c0, int up0, const void* s1, int c1, int h, int w, const ConvLayer& l,
+                   void* out, int act, int out_f32, int out_ld = -1, int out_off = 0) {
+  ConvArgs a;
+  a.src0 = s0;
+  a.c0 = c0;
+  a.up0 = up0;
+  a.src1 = s1;
+  a.c1 = c1;
+  a.H = h;
+  a.W = w;
+  a.cout = l.cout;
+  a.k = l.k;
+  a.act = act;
+  a.w = l.w32;
+  a.b = l.b32;
+  a.out = out;
+  a.out_f32 = out_f32;
+  a.out_ld = out_ld < 0 ? l.cout : out_ld;
+  a.out_off = out_off;
+  return a;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Bytes of the CUDA-core U-Net's activations: per level two block outputs
+// and the pooled copy, per decoder level two block outputs.
+size_t unet_simt_bytes(int H, int W, int levels, const int* ch, size_t es) {
+  size_t t = 0;
+  for (int l = 0; l < levels; ++l) {
+    const size_t px = (size_t)(H >> l) * (W >> l);
+    t += 2 * align256(px * ch[l] * es);
+    if (l + 1 < levels) t += align256(px / 4 * ch[l] * es) + 2 * align256(px * ch[l] * es);
+  }
+  return t;
+}
+
+// U-Net of `levels` levels on the CUDA cores, layers[lb ...] in the order
+// enc0 a/b, ..., bottleneck a/b, dec(levels-2) a/b, ..., dec0 a/b, 1x1 head
+// (Sec. 3.1 "Neural Shading"; per level two conv3x3 + ReLU, 2x2 max pooling
+// down, nearest x2 up with the concatenation [upsampled, skip], sigmoid
+// head).  The head writes its cout channels at out_off of out_ld FP32 values
+// per pixel.  Activations live in the arena from byte arena_off on.
+template <typename TI>
+art_status unet_simt(art_ctx* ctx, int H, int W, const void* in, int cin, int lb, int levels, const int* ch,
+                     float* out, int out_ld, int out_off, size_t arena_off) {
+  const size_t es = sizeof(TI);
+  const size_t need = arena_off + unet_simt_bytes(H, W, levels, ch, es);
+  if (ensure(ctx, &ctx->d_act, &ctx->d_act_bytes, need, "activations") != ART_OK) return ART_ERR_OOM;
+  size_t off = arena_off;
+  auto take = [&](int l, int c, int shift) {
+    void* p = (char*)ctx->d_act + off;
+    off += align256((size_t)(H >> (l + shift)) * (W >> (l + shift)) * c * es);
+    return p;
+  };
+  auto L = [&](int i) -> const ConvLayer& { return ctx->layers[lb + i]; };
+  void* skip[4] = {};
+  const void* x = in;
+  int xc = cin;
+  int li = 0;
+  for (int l = 0; l < levels; ++l) {  // encoder
+    const int h = H >> l, w = W >> l;
+    void* a = take(l, ch[l], 0);
+    void* b = take(l, ch[l], 0);
+    conv<TI>(ctx, conv_args<TI>(x, xc, 0, nullptr, 0, h, w, L(li), a, 1, 0), L(li));
+    conv<TI>(ctx, conv_args<TI>(a, ch[l], 0, nullptr, 0, h, w, L(li + 1), b, 1, 0), L(li + 1));
+    li += 2;
+    skip[l] = b;
+    if (l + 1 < levels) {
+      void* pooled = take(l, ch[l], 1);
+      pool<TI>(ctx, b, pooled, h, w, ch[l]);
+      x = pooled;
+      xc = ch[l];
+    }
+  }
+  const void* d = skip[levels - 1];
+  for (int l = levels - 2; l >= 0; --l) {  // decoder: [up(d), skip_l]
+    const int h = H >> l, w = W >> l;
+    void* a = take(l, ch[l], 0);
+    void* b = take(l, ch[l], 0);
+    conv<TI>(ctx, conv_args<TI>(d, ch[l + 1], 1, skip[l], ch[l], h, w, L(li), a, 1, 0), L(li));
+    conv<TI>(ctx, conv_args<TI>(a, ch[l], 0, nullptr, 0, h, w, L(li + 1), b, 1, 0), L(li + 1));
+    li += 2;
+    d = b;
+  }
+  conv<TI>(ctx, conv_args<TI>(d, ch[0], 0, nullptr, 0, H, W, L(li), out, 2, 1, out_ld, out_off), L(li));
+  return ART_OK;
+}
+
+// The opacity branch's input [A, I_f] of the two-branch network: channel 0
+// the coarse opacity A, channels 1..3 the appearance branch's image (FP32
+// RGB of rgba [H][W][4]), channels 4 .. C-1 zero (padding for the tensor
+// cores' K granularity).
+template <typename TI, int C>
+__global__ void __launch_bounds__(256) pack_opacity_input_kernel(int64_t npx, const float* __restrict__ A,
+                                                                 const float* __restrict__ rgba, TI* __restrict__ x) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= npx) return;
+  const float4 c = reinterpret_cast<const float4*>(rgba)[i];
+  float v[C];
+#pragma unroll
+  for (int k = 0; k < C; ++k) v[k] = 0.0f;
+  v[0] = A[i];
+  v[1] = c.x;
+  v[2] = c.y;
+  v[3] = c.z;
+  TI* o = x + i * C;
+#pragma unroll
+  for (int k = 0; k < C; ++k) st_act(o + k, v[k]);
+}
+
+template <typename TI, int C>
+void pack_opacity_input(art_ctx* ctx, int64_t npx, const float* A, const float* rgba, TI* x) {
+  auto kfn = pack_opacity_input_kernel<TI, C>;
+  ART_LAUNCH(ctx, "pack_opacity_input", kfn, (unsigned)((npx + 255) / 256), 256, 0, npx, A, rgba, x);
+}
+
+template <typename TI>
+art_status run_typed(art_ctx* ctx, const ViewParams& v, const void* F, const float* A, float* rgba) {
   const int H = v.H, W = v.W;
   const art_net_desc& nd = ctx->net;
   auto L = [&](int i) -> const ConvLayer& { return ctx->layers[i]; };
-  auto mk = [&](const void* s0, int c0, int up0, const void* s1, int c1, int h, int w, const ConvLayer& l, void* out,
-                int act, int out_f32) {
-    ConvArgs a;
-    a.src0 = s0;
-    a.c0 = c0;
-    a.up0 = up0;
-    a.src1 = s1;
-    a.c1 = c1;
-    a.H = h;
-    a.W = w;
-    a.cout = l.cout;
-    a.k = l.k;
-    a.act = act;
-    a.w = l.w32;
-    a.b = l.b32;
-    a.out = out;
-    a.out_f32 = out_f32;
-    return a;
-  };
   const size_t es = sizeof(TI);
   if (nd.arch == ART_NET_TINY) {
     int c = nd.ch[0];
@@ -178,126 +277,133 @@ art_status run_typed(art_ctx* ctx, const ViewParams& v, const void* F, float* rg
     if (ensure(ctx, &ctx->d_act, &ctx->d_act_bytes, need, "activations") != ART_OK) return ART_ERR_OOM;
     char* b0 = (char*)ctx->d_act;
     char* b1 = b0 + (size_t)H * W * c * es;
-    conv<TI>(ctx, mk(F, nd.cin, 0, nullptr, 0, H, W, L(0), b0, 1, 0), L(0));
-    conv<TI>(ctx, mk(b0, c, 0, nullptr, 0, H, W, L(1), b1, 1, 0), L(1));
-    conv<TI>(ctx, mk(b1, c, 0, nullptr, 0, H, W, L(2), rgba, 2, 1), L(2));
+    conv<TI>(ctx, conv_args<TI>(F, nd.cin, 0, nullptr, 0, H, W, L(0), b0, 1, 0), L(0));
+    conv<TI>(ctx, conv_args<TI>(b0, c, 0, nullptr, 0, H, W, L(1), b1, 1, 0), L(1));
+    conv<TI>(ctx, conv_args<TI>(b1, c, 0, nullptr, 0, H, W, L(2), rgba, 2, 1), L(2));
     return ART_OK;
   }
-  // U-Net
-  const int c0 = nd.ch[0], c1 = nd.ch[1], c2 = nd.ch[2], c3 = nd.ch[3];
-  struct Buf {
-    int h, w, c;
-    size_t off;
-  };
-  std::vector<Buf> bufs;
-  size_t total = 0;
-  auto add = [&](int h, int w, int c) {
-    bufs.push_back(Buf{h, w, c, total});
-    total += ((size_t)h * w * c * es + 255) & ~(size_t)255;
-    return (int)bufs.size() - 1;
-  };
-  int e0a = add(H, W, c0), e0 = add(H, W, c0), p0 = add(H / 2, W / 2, c0);
-  int e1a = add(H / 2, W / 2, c1), e1 = add(H / 2, W / 2, c1), p1 = add(H / 4, W / 4, c1);
-  int e2a = add(H / 4, W / 4, c2), e2 = add(H / 4, W / 4, c2), p2 = add(H / 8, W / 8, c2);
-  int e3a = add(H / 8, W / 8, c3), e3 = add(H / 8, W / 8, c3);
-  int d2a = add(H / 4, W / 4, c2), d2 = add(H / 4, W / 4, c2);
-  int d1a = add(H / 2, W / 2, c1), d1 = add(H / 2, W / 2, c1);
-  int d0a = add(H, W, c0), d0 = add(H, W, c0);
-  if (ensure(ctx, &ctx->d_act, &ctx->d_act_bytes, total, "activations") != ART_OK) return ART_ERR_OOM;
-  auto P = [&](int i) { return (void*)((char*)ctx->d_act + bufs[i].off); };
-  conv<TI>(ctx, mk(F, nd.cin, 0, nullptr, 0, H, W, L(0), P(e0a), 1, 0), L(0));
-  conv<TI>(ctx, mk(P(e0a), c0, 0, nullptr, 0, H, W, L(1), P(e0), 1, 0), L(1));
-  pool<TI>(ctx, P(e0), P(p0), H, W, c0);
-  conv<TI>(ctx, mk(P(p0), c0, 0, nullptr, 0, H / 2, W / 2, L(2), P(e1a), 1, 0), L(2));
-  conv<TI>(ctx, mk(P(e1a), c1, 0, nullptr, 0, H / 2, W / 2, L(3), P(e1), 1, 0), L(3));
-  pool<TI>(ctx, P(e1), P(p1), H / 2, W / 2, c1);
-  conv<TI>(ctx, mk(P(p1), c1, 0, nullptr, 0, H / 4, W / 4, L(4), P(e2a), 1, 0), L(4));
-  conv<TI>(ctx, mk(P(e2a), c2, 0, nullptr, 0, H / 4, W / 4, L(5), P(e2), 1, 0), L(5));
-  pool<TI>(ctx, P(e2), P(p2), H / 4, W / 4, c2);
-  conv<TI>(ctx, mk(P(p2), c2, 0, nullptr, 0, H / 8, W / 8, L(6), P(e3a), 1, 0), L(6));
-  conv<TI>(ctx, mk(P(e3a), c3, 0, nullptr, 0, H / 8, W / 8, L(7), P(e3), 1, 0), L(7));
-  conv<TI>(ctx, mk(P(e3), c3, 1, P(e2), c2, H / 4, W / 4, L(8), P(d2a), 1, 0), L(8));
-  conv<TI>(ctx, mk(P(d2a), c2, 0, nullptr, 0, H / 4, W / 4, L(9), P(d2), 1, 0), L(9));
-  conv<TI>(ctx, mk(P(d2), c2, 1, P(e1), c1, H / 2, W / 2, L(10), P(d1a), 1, 0), L(10));
-  conv<TI>(ctx, mk(P(d1a), c1, 0, nullptr, 0, H / 2, W / 2, L(11), P(d1), 1, 0), L(11));
-  conv<TI>(ctx, mk(P(d1), c1, 1, P(e0), c0, H, W, L(12), P(d0a), 1, 0), L(12));
-  conv<TI>(ctx, mk(P(d0a), c0, 0, nullptr, 0, H, W, L(13), P(d0), 1, 0), L(13));
-  conv<TI>(ctx, mk(P(d0), c0, 0, nullptr, 0, H, W, L(14), rgba, 2, 1), L(14));
-  return ART_OK;
+  if (nd.arch == ART_NET_UNET) return unet_simt<TI>(ctx, H, W, F, nd.cin, 0, 4, nd.ch, rgba, nd.cout, 0, 0);
+  // two branches: appearance F -> I_f (rgba channels 0..2), opacity [A, I_f] -> alpha (channel 3)
+  art_status st = unet_simt<TI>(ctx, H, W, F, nd.cin, 0, 4, nd.ch, rgba, 4, 0, 0);
+  if (st != ART_OK) return st;
+  const int64_t npx = (int64_t)H * W;
+  const size_t xb = align256((size_t)npx * 4 * es);
+  if (ensure(ctx, &ctx->d_act, &ctx->d_act_bytes, xb + unet_simt_bytes(H, W, 2, nd.ach, es), "activations") != ART_OK)
+    return ART_ERR_OOM;
+  pack_opacity_input<TI, 4>(ctx, npx, A, rgba, (TI*)ctx->d_act);
+  return unet_simt<TI>(ctx, H, W, ctx->d_act, 4, 15, 2, nd.ach, rgba, 4, 3, xb);
 }
 
-// BF16 U-Net on the tensor cores.  Skip connections and upsampled decoder
-// inputs are written straight into per-level concatenation buffers
+// Bytes of the tensor-core U-Net's activations (unet_tc's tensors).
+size_t unet_tc_bytes(int H, int W, int levels, const int* ch) {
+  size_t t = 0;
+  for (int l = 0; l + 1 < levels; ++l) {
+    const size_t px = (size_t)(H >> l) * (W >> l);
+    t += align256(px * ch[l] * 2) + align256(px * (ch[l + 1] + ch[l]) * 2) + align256(px / 4 * ch[l] * 2);
+  }
+  t += align256((size_t)(H >> (levels - 1)) * (W >> (levels - 1)) * ch[levels - 1] * 2);
+  for (int l = levels - 2; l >= 0; --l) t += align256((size_t)(H >> l) * (W >> l) * ch[l] * 2);
+  return t;
+}
+
+// BF16 U-Net of `levels` levels on the tensor cores, layers[lb ...] in the
+// order of unet_simt.  Skip connections and upsampled decoder inputs are
+// written straight into per-level concatenation buffers
 // cat_l = [up(decoder below) | encoder skip] by the producing convolutions'
 // epilogues, so every decoder convolution reads one dense tensor; the last
-// convolution carries the 1x1 head + sigmoid in its epilogue.
-art_status run_unet_tc(art_ctx* ctx, const ViewParams& v, const __nv_bfloat16* F, float* rgba) {
-  const int H = v.H, W = v.W;
-  const art_net_desc& nd = ctx->net;
-  const int c0 = nd.ch[0], c1 = nd.ch[1], c2 = nd.ch[2], c3 = nd.ch[3];
-  struct Buf {
-    int h, w, c;
-    size_t off;
+// convolution carries the 1x1 head + sigmoid in its epilogue, into head_n
+// FP32 channels at head_off of head_ld per pixel.  Arena order (from
+// arena_off): e0a, cat0, p0, e1a, cat1, p1, ..., bottleneck a, then the
+// decoders' first outputs from the deepest level up.
+art_status unet_tc(art_ctx* ctx, int H, int W, const __nv_bfloat16* in, int cin, int lb, int levels, const int* ch,
+                   float* out, int head_n, int head_ld, int head_off, size_t arena_off) {
+  const size_t need = arena_off + unet_tc_bytes(H, W, levels, ch);
+  if (ensure(ctx, &ctx->d_act, &ctx->d_act_bytes, need, "activations") != ART_OK) return ART_ERR_OOM;
+  size_t off = arena_off;
+  auto take = [&](int l, int c, int shift) {
+    __nv_bfloat16* p = (__nv_bfloat16*)((char*)ctx->d_act + off);
+    off += align256((size_t)(H >> (l + shift)) * (W >> (l + shift)) * c * 2);
+    return p;
   };
-  std::vector<Buf> bufs;
-  size_t total = 0;
-  auto add = [&](int h, int w, int c) {
-    bufs.push_back(Buf{h, w, c, total});
-    total += ((size_t)h * w * c * 2 + 255) & ~(size_t)255;
-    return (int)bufs.size() - 1;
-  };
-  const int e0a = add(H, W, c0), cat0 = add(H, W, c1 + c0), p0 = add(H / 2, W / 2, c0);
-  const int e1a = add(H / 2, W / 2, c1), cat1 = add(H / 2, W / 2, c2 + c1), p1 = add(H / 4, W / 4, c1);
-  const int e2a = add(H / 4, W / 4, c2), cat2 = add(H / 4, W / 4, c3 + c2), p2 = add(H / 8, W / 8, c2);
-  const int e3a = add(H / 8, W / 8, c3);
-  const int d2a = add(H / 4, W / 4, c2), d1a = add(H / 2, W / 2, c1), d0a = add(H, W, c0);
-  if (ensure(ctx, &ctx->d_act, &ctx->d_act_bytes, total, "activations") != ART_OK) return ART_ERR_OOM;
-  auto P = [&](int i) { return (__nv_bfloat16*)((char*)ctx->d_act + bufs[i].off); };
-  const auto& L = ctx->layers;
-  auto conv = [&](const __nv_bfloat16* in, int cin, int h, int w, int li, __nv_bfloat16* out, int ld, int off,
-                  int up2, float* head_out, __nv_bfloat16* pooled = nullptr) {
+  __nv_bfloat16 *ea[4] = {}, *cat[4] = {}, *pl[4] = {}, *da[4] = {};
+  for (int l = 0; l + 1 < levels; ++l) {
+    ea[l] = take(l, ch[l], 0);
+    cat[l] = take(l, ch[l + 1] + ch[l], 0);
+    pl[l] = take(l, ch[l], 1);
+  }
+  ea[levels - 1] = take(levels - 1, ch[levels - 1], 0);
+  for (int l = levels - 2; l >= 0; --l) da[l] = take(l, ch[l], 0);
+  const auto& Ls = ctx->layers;
+  const int head = lb + 4 * levels - 2;
+  auto conv = [&](const __nv_bfloat16* x, int xc, int l, int li, __nv_bfloat16* o, int ld, int o_off, int up2,
+                  bool to_head, __nv_bfloat16* pooled) {
     TcConv c;
-    c.in = in;
-    c.cin = cin;
-    c.H = h;
-    c.W = w;
-    c.w = L[li].wbf;
-    c.bias = L[li].b32;
-    c.cout = L[li].cout;
+    c.in = x;
+    c.cin = xc;
+    c.H = H >> l;
+    c.W = W >> l;
+    c.w = Ls[lb + li].wbf;
+    c.bias = Ls[lb + li].b32;
+    c.cout = Ls[lb + li].cout;
     c.act = 1;
-    c.out = out;
+    c.out = o;
     c.ld_out = ld;
-    c.ch_off = off;
+    c.ch_off = o_off;
     c.up2 = up2;
-    c.rgba = head_out;
-    c.head_w = head_out ? L[14].w32 : nullptr;
-    c.head_b = head_out ? L[14].b32 : nullptr;
+    c.rgba = to_head ? out : nullptr;
+    c.head_w = to_head ? Ls[head].w32 : nullptr;
+    c.head_b = to_head ? Ls[head].b32 : nullptr;
+    c.head_n = head_n;
+    c.head_ld = head_ld;
+    c.head_off = head_off;
     c.pool = pooled;
     return launch_tc_conv(ctx, c);
   };
   art_status st = ART_OK;
 #define ART_TRY(x)                  \
   if ((st = (x)) != ART_OK) return st
-  ART_TRY(conv(F, nd.cin, H, W, 0, P(e0a), c0, 0, 0, nullptr));
-  ART_TRY(conv(P(e0a), c0, H, W, 1, P(cat0), c1 + c0, c1, 0, nullptr, P(p0)));  // + 2x2 max pooling
-  ART_TRY(conv(P(p0), c0, H / 2, W / 2, 2, P(e1a), c1, 0, 0, nullptr));
-  ART_TRY(conv(P(e1a), c1, H / 2, W / 2, 3, P(cat1), c2 + c1, c2, 0, nullptr, P(p1)));
-  ART_TRY(conv(P(p1), c1, H / 4, W / 4, 4, P(e2a), c2, 0, 0, nullptr));
-  ART_TRY(conv(P(e2a), c2, H / 4, W / 4, 5, P(cat2), c3 + c2, c3, 0, nullptr, P(p2)));
-  ART_TRY(conv(P(p2), c2, H / 8, W / 8, 6, P(e3a), c3, 0, 0, nullptr));
-  ART_TRY(conv(P(e3a), c3, H / 8, W / 8, 7, P(cat2), c3 + c2, 0, 1, nullptr));  // up x2 into cat2
-  ART_TRY(conv(P(cat2), c3 + c2, H / 4, W / 4, 8, P(d2a), c2, 0, 0, nullptr));
-  ART_TRY(conv(P(d2a), c2, H / 4, W / 4, 9, P(cat1), c2 + c1, 0, 1, nullptr));  // up x2 into cat1
-  ART_TRY(conv(P(cat1), c2 + c1, H / 2, W / 2, 10, P(d1a), c1, 0, 0, nullptr));
-  ART_TRY(conv(P(d1a), c1, H / 2, W / 2, 11, P(cat0), c1 + c0, 0, 1, nullptr));  // up x2 into cat0
-  ART_TRY(conv(P(cat0), c1 + c0, H, W, 12, P(d0a), c0, 0, 0, nullptr));
-  ART_TRY(conv(P(d0a), c0, H, W, 13, nullptr, 0, 0, 0, rgba));  // + fused 1x1 head, sigmoid
+  const __nv_bfloat16* x = in;
+  int xc = cin;
+  for (int l = 0; l + 1 < levels; ++l) {  // encoder: the block output goes into cat_l as the skip, + 2x2 pooling
+    ART_TRY(conv(x, xc, l, 2 * l, ea[l], ch[l], 0, 0, false, nullptr));
+    ART_TRY(conv(ea[l], ch[l], l, 2 * l + 1, cat[l], ch[l + 1] + ch[l], ch[l + 1], 0, false, pl[l]));
+    x = pl[l];
+    xc = ch[l];
+  }
+  const int lL = levels - 1;  // bottleneck: its block output goes up x2 into cat of the level above
+  ART_TRY(conv(x, xc, lL, 2 * lL, ea[lL], ch[lL], 0, 0, false, nullptr));
+  ART_TRY(conv(ea[lL], ch[lL], lL, 2 * lL + 1, cat[lL - 1], ch[lL] + ch[lL - 1], 0, 1, false, nullptr));
+  int li = 2 * levels;
+  for (int l = levels - 2; l >= 0; --l, li += 2) {
+    ART_TRY(conv(cat[l], ch[l + 1] + ch[l], l, li, da[l], ch[l], 0, 0, false, nullptr));
+    if (l > 0) {
+      ART_TRY(conv(da[l], ch[l], l, li + 1, cat[l - 1], ch[l] + ch[l - 1], 0, 1, false, nullptr));  // up x2
+    } else {
+      ART_TRY(conv(da[0], ch[0], 0, li + 1, nullptr, 0, 0, 0, true, nullptr));  // + fused 1x1 head, sigmoid
+    }
+  }
 #undef ART_TRY
   return ART_OK;
 }
 
+// Both branches of the two-branch network on the tensor cores; the
+// opacity branch's first layer carries BF16 weights padded to 32 input
+// channels (the packed [A, I_f, 0 ...] tensor).
+art_status run_two_branch_tc(art_ctx* ctx, const ViewParams& v, const __nv_bfloat16* F, const float* A, float* rgba) {
+  const int H = v.H, W = v.W;
+  const art_net_desc& nd = ctx->net;
+  art_status st = unet_tc(ctx, H, W, F, nd.cin, 0, 4, nd.ch, rgba, 3, 4, 0, 0);
+  if (st != ART_OK) return st;
+  const int64_t npx = (int64_t)H * W;
+  const size_t xb = align256((size_t)npx * kOpacityPad * 2);
+  if (ensure(ctx, &ctx->d_act, &ctx->d_act_bytes, xb + unet_tc_bytes(H, W, 2, nd.ach), "activations") != ART_OK)
+    return ART_ERR_OOM;
+  pack_opacity_input<__nv_bfloat16, kOpacityPad>(ctx, npx, A, rgba, (__nv_bfloat16*)ctx->d_act);
+  return unet_tc(ctx, H, W, (const __nv_bfloat16*)ctx->d_act, kOpacityPad, 15, 2, nd.ach, rgba, 1, 4, 3, xb);
+}
+
 // FP8 (E4M3) U-Net on the tensor cores (kind::f8f6f4), same dataflow as
-// run_unet_tc.  Activation tensors carry one scale each (a concatenation
+// unet_tc.  Activation tensors carry one scale each (a concatenation
 // buffer and its pooled copy share one); every call quantises with the scales
 // measured on the previous call (delayed per-tensor scaling from max |value|)
 // and records this call's maxima.  The first call after loading calibrates:
@@ -395,27 +501,45 @@ art_status run_unet_f8(art_ctx* ctx, const ViewParams& v, const __nv_bfloat16* F
 // (it is a multiple of 32 whenever unet_tc_ok holds).
 bool f8_input_unusable(art_ctx* ctx) { return (ctx->net.cin % 2) != 0; }
 
-// The tensor-core path covers the U-Net when every layer fits its shapes.
+// The tensor-core path covers a U-Net (levels levels, layers[lb ...]) when
+// every layer fits its shapes (a padded first layer counts with its padded
+// input channels) and the head is a 1x1 layer of at most 4 outputs fused
+// into a last convolution of 32 channels.
+bool unet_layers_tc_ok(art_ctx* ctx, int lb, int levels) {
+  const int nl = 4 * levels - 1;
+  if ((int)ctx->layers.size() < lb + nl) return false;
+  for (int i = 0; i < nl - 1; ++i) {
+    const ConvLayer& l = ctx->layers[lb + i];
+    TcConv c{};
+    c.cin = l.cin_pad;
+    c.cout = l.cout;
+    c.ld_out = 16;
+    c.rgba = i == nl - 2 ? (float*)1 : nullptr;
+    if (l.k != 3 || !l.wbf || !tc_conv_ok(c)) return false;
+  }
+  const ConvLayer& hd = ctx->layers[lb + nl - 1];
+  return hd.k == 1 && hd.cout <= 4;
+}
+
 bool unet_tc_ok(art_ctx* ctx, const ViewParams& v) {
   const art_net_desc& nd = ctx->net;
   if (nd.arch != ART_NET_UNET || nd.cout != 4 || v.W % 8 || v.H % 8) return false;
-  for (int i = 0; i < 14; ++i) {
-    TcConv c{};
-    c.cin = ctx->layers[i].cin;
-    c.cout = ctx->layers[i].cout;
-    c.ld_out = 16;
-    c.rgba = i == 13 ? (float*)1 : nullptr;
-    if (ctx->layers[i].k != 3 || !ctx->layers[i].wbf || !tc_conv_ok(c)) return false;
-  }
-  return ctx->layers[14].k == 1;
+  return unet_layers_tc_ok(ctx, 0, 4);
+}
+
+bool two_branch_tc_ok(art_ctx* ctx, const ViewParams& v) {
+  if (ctx->net.arch != ART_NET_TWO_BRANCH || v.W % 8 || v.H % 8) return false;
+  return unet_layers_tc_ok(ctx, 0, 4) && unet_layers_tc_ok(ctx, 15, 2);
 }
 
 }  // namespace
 
-art_status run_shader(art_ctx* ctx, const ViewParams& v, const void* F, int F_dtype, float* rgba) {
+art_status run_shader(art_ctx* ctx, const ViewParams& v, const void* F, int F_dtype, const float* A, float* rgba) {
+  if (ctx->net.arch == ART_NET_TWO_BRANCH && !A)
+    return fail(ctx, ART_ERR_INVALID_ARG, "the two-branch network needs the coarse opacity map A");
   if (ctx->net_dtype == ART_F32) {
     if (F_dtype != ART_F32) return fail(ctx, ART_ERR_INVALID_ARG, "shade: FP32 network needs an FP32 feature map");
-    return run_typed<float>(ctx, v, F, rgba);
+    return run_typed<float>(ctx, v, F, A, rgba);
   }
   if (F_dtype != ART_BF16) return fail(ctx, ART_ERR_INVALID_ARG, "shade: BF16/FP8 network needs a BF16 feature map");
   if (ctx->net_dtype == ART_FP8) {
@@ -423,8 +547,10 @@ art_status run_shader(art_ctx* ctx, const ViewParams& v, const void* F, int F_dt
       return fail(ctx, ART_ERR_UNSUPPORTED, "FP8 network: U-Net with tensor-core shapes and W, H multiples of 8 only");
     return run_unet_f8(ctx, v, (const __nv_bfloat16*)F, rgba);
   }
-  if (unet_tc_ok(ctx, v)) return run_unet_tc(ctx, v, (const __nv_bfloat16*)F, rgba);
-  return run_typed<__nv_bfloat16>(ctx, v, F, rgba);
+  const __nv_bfloat16* Fb = (const __nv_bfloat16*)F;
+  if (unet_tc_ok(ctx, v)) return unet_tc(ctx, v.H, v.W, Fb, ctx->net.cin, 0, 4, ctx->net.ch, rgba, 4, 4, 0, 0);
+  if (two_branch_tc_ok(ctx, v)) return run_two_branch_tc(ctx, v, Fb, A, rgba);
+  return run_typed<__nv_bfloat16>(ctx, v, F, A, rgba);
 }
 
 }  // namespace art

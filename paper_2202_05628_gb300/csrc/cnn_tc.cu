@@ -38,9 +38,10 @@ struct TcParams {
   const float* out_scale;  // FP8: quantisation scale of the output tensor (device scalar)
   unsigned int* out_amax;  // FP8: running max |output| (float bits) for the next call's scale
   int ld_out, ch_off, up2;
-  float* rgba;           // fused 1x1 head (cout -> 4) + sigmoid when non-null
-  const float* head_w;   // [4][cout]
-  const float* head_b;   // [4]
+  float* rgba;           // fused 1x1 head (cout -> head_n <= 4) + sigmoid when non-null
+  const float* head_w;   // [head_n][cout]
+  const float* head_b;   // [head_n]
+  int head_n, head_ld, head_off;  // head outputs, FP32 values per output pixel, channel of the first
   __nv_bfloat16* pool;   // row-blocked kernel: fused 2x2 max pooling, dense [H/2][W/2][cout]
   unsigned long long* err;
 };
@@ -66,7 +67,7 @@ __device__ __forceinline__ void epi_row(const TcParams& p, uint32_t taddr, int y
       v[j] = p.act == 1 ? fmaxf(t, 0.0f) : t;
     }
     if (!valid) continue;
-    if (p.rgba) {  // fused 1x1 head (N == 32) + sigmoid -> RGBA FP32
+    if (p.rgba) {  // fused 1x1 head (N == 32) + sigmoid -> head_n FP32 channels of the output
       float o[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
@@ -75,7 +76,14 @@ __device__ __forceinline__ void epi_row(const TcParams& p, uint32_t taddr, int y
         for (int j = 0; j < 32; ++j) acc = fmaf(s_head[k * N + c0 + j], v[j], acc);
         o[k] = 1.0f / (1.0f + expf(-acc));
       }
-      reinterpret_cast<float4*>(p.rgba)[(size_t)y * p.W + x] = make_float4(o[0], o[1], o[2], o[3]);
+      float* dst = p.rgba + (size_t)(y * p.W + x) * p.head_ld + p.head_off;
+      if (p.head_n == 4 && p.head_ld == 4) {
+        *reinterpret_cast<float4*>(dst) = make_float4(o[0], o[1], o[2], o[3]);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (k < p.head_n) dst[k] = o[k];
+      }
       continue;
     }
     constexpr int kVec = F8 ? 2 : 4;  // 16-B stores of the 32 channels
@@ -229,7 +237,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   for (int i = threadIdx.x; i < N; i += kThreads) s_bias[i] = i < p.cout ? p.bias[i] : 0.0f;
   if (p.rgba)
-    for (int i = threadIdx.x; i < 4 * N + 4; i += kThreads) s_head[i] = i < 4 * N ? p.head_w[i] : p.head_b[i - 4 * N];
+    for (int i = threadIdx.x; i < 4 * N + 4; i += kThreads)  // rows beyond head_n are zero
+      s_head[i] = i < 4 * N ? (i < p.head_n * N ? p.head_w[i] : 0.0f) : (i - 4 * N < p.head_n ? p.head_b[i - 4 * N] : 0.0f);
   if (F8)
     for (int i = threadIdx.x; i < N; i += kThreads) s_wsc[i] = i < p.cout ? p.w_scale[i] : 0.0f;
   if (warp == 1) {
@@ -419,7 +428,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   for (int i = threadIdx.x; i < N; i += kThreads) s_bias[i] = i < p.cout ? p.bias[i] : 0.0f;
   if (p.rgba)
-    for (int i = threadIdx.x; i < 4 * N + 4; i += kThreads) s_head[i] = i < 4 * N ? p.head_w[i] : p.head_b[i - 4 * N];
+    for (int i = threadIdx.x; i < 4 * N + 4; i += kThreads)  // rows beyond head_n are zero
+      s_head[i] = i < 4 * N ? (i < p.head_n * N ? p.head_w[i] : 0.0f) : (i - 4 * N < p.head_n ? p.head_b[i - 4 * N] : 0.0f);
   const int nbuf = rp.nbuf;
   const uint32_t tmem_cols = (uint32_t)(nbuf * Cfg::kBufCols);
   if (warp == 1) tmem_alloc(tmem_slot, tmem_cols);
@@ -638,6 +648,9 @@ art_status launch_typed(art_ctx* ctx, const TcConv& c) {
   p.rgba = c.rgba;
   p.head_w = c.head_w;
   p.head_b = c.head_b;
+  p.head_n = c.head_n;
+  p.head_ld = c.head_ld;
+  p.head_off = c.head_off;
   p.pool = nullptr;  // pooled by a pass of its own
   p.err = ctx->d_status + kStTcError;
   auto kfn = conv_tc_kernel<N, KCB, F8>;
@@ -722,6 +735,9 @@ art_status launch_rows(art_ctx* ctx, const TcConv& c) {
   p.rgba = c.rgba;
   p.head_w = c.head_w;
   p.head_b = c.head_b;
+  p.head_n = c.head_n;
+  p.head_ld = c.head_ld;
+  p.head_off = c.head_off;
   p.pool = (__nv_bfloat16*)c.pool;
   p.err = ctx->d_status + kStTcError;
   rp.cpt = c.cin / Cfg::KC;

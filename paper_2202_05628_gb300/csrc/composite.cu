@@ -38,6 +38,9 @@ struct SkipArgs {
   const float* sh_coef; // kSH: [n][(L+1)^2][C] spherical-harmonics coefficients
   const float* sh_rot;  // kSH: [n][9] per voxel the map of world directions into its canonical frame
   int sh_degree;        // kSH: L (0 .. kShMaxDegree)
+  uint32_t* xflag;      // kPlain, kInterval: per global tile, queued for the exact re-walk already
+  uint32_t* xqueue;     // ... the queue (count in status[kStExactQ])
+  int gtile;            // the walked tile's index in the (joint) tile space
 };
 
 // Real orthonormal spherical harmonics of degree <= L (<= kShMaxDegree) at
@@ -134,6 +137,22 @@ __device__ __forceinline__ float tile_hist_prefix(const float* __restrict__ th, 
   return pre[63];
 }
 
+// A pixel whose reorder buffer was full released a hit that a later list
+// entry may still precede.  With an exact re-walk queue (the composite of F
+// and A) the tile is queued once for the exact walk, which rewrites it; else
+// the releases are counted (overflow_order).
+__device__ __forceinline__ void report_overflow(uint32_t n_over, const SkipArgs& sk,
+                                                unsigned long long* __restrict__ status, int lane) {
+  const bool any = __any_sync(0xffffffffu, n_over != 0);
+  if (!any) return;
+  if (sk.xqueue) {
+    if (lane == 0 && atomicExch(sk.xflag + sk.gtile, 1u) == 0u)
+      sk.xqueue[atomicAdd(status + kStExactQ, 1ull)] = (uint32_t)sk.gtile;
+  } else if (n_over) {
+    atomicAdd(status + kStOverflowOrder, (unsigned long long)n_over);
+  }
+}
+
 // One warp per 8x4 tile, lane = pixel (x = lane & 7, y = lane >> 3).
 template <int C, typename TF, typename TO, int MODE>
 __device__ __forceinline__ void composite_tile(const int tile, const Seg& sg,
@@ -225,12 +244,12 @@ __device__ __forceinline__ void composite_tile(const int tile, const Seg& sg,
       sig = s_sig[ch % RING][sl];
       vid = s_vid[ch % RING][sl];
       if constexpr (FEAT) row_to_float<C>(&s_feat[ch % RING][sl][0], f);
-      if constexpr (SH) sh_feature<C>(sk, vid, rd.h[0], rd.h[1], rd.h[2], f);
+      if constexpr (SH) sh_feature<C>(sk, vid, rd.h[0] * rd.inv_n, rd.h[1] * rd.inv_n, rd.h[2] * rd.inv_n, f);
     } else {  // staged long ago: read the voxel again
       vid = vals[rg.x + h.pos];
       sig = rec[4 * (size_t)vid + 3].x;
       if constexpr (FEAT) load_feat<C>(feat + (size_t)vid * C, f);
-      if constexpr (SH) sh_feature<C>(sk, vid, rd.h[0], rd.h[1], rd.h[2], f);
+      if constexpr (SH) sh_feature<C>(sk, vid, rd.h[0] * rd.inv_n, rd.h[1] * rd.inv_n, rd.h[2] * rd.inv_n, f);
     }
     if constexpr (DBG) {
       if (n_used < dbg.cap) {
@@ -372,7 +391,7 @@ __device__ __forceinline__ void composite_tile(const int tile, const Seg& sg,
 #pragma unroll
     for (int c = 0; c < C; ++c) sg.part[c * 32 + lane] = acc[c];
     sg.part[C * 32 + lane] = T;
-    if (n_over) atomicAdd(status + kStOverflowOrder, (unsigned long long)n_over);
+    report_overflow(n_over, sk, status, lane);
     return;
   }
   if constexpr (MODE == kLabel || MODE == kInterval) {
@@ -421,7 +440,7 @@ __device__ __forceinline__ void composite_tile(const int tile, const Seg& sg,
     store_row<C>(Fout + pix * C, acc);
     if (Aout) Aout[pix] = 1.0f - T;
   }
-  if (n_over) atomicAdd(status + kStOverflowOrder, (unsigned long long)n_over);
+  report_overflow(n_over, sk, status, lane);
 }
 
 template <int C, typename TF, typename TO, int MODE>
@@ -501,8 +520,42 @@ __global__ void __launch_bounds__(32, 12) composite_split_kernel(
     const uint2 sgt = seg[tile];
     Seg sg = make_seg(v, ranges[tile], sgt, (uint32_t)i, keys, wq, lane);
     sg.part = sgt.y > 1 ? part + (size_t)i * (C + 1) * 32 : nullptr;
+    SkipArgs skt = sk;
+    skt.gtile = tile;
     composite_tile<C, TF, TO, MODE>(tile, sg, keys, vals, rec, rect, feat, v, tau, Fout, Aout, status, HitLog{},
-                                    sk);
+                                    skt);
+  }
+}
+
+// The split walk over a batch of views in one tile space: a segment's global
+// tile names its view (vs->toff), whose parameters, rectangles and output
+// maps it composites with.
+template <int C, typename TF, typename TO>
+__global__ void __launch_bounds__(32, 12) composite_split_views_kernel(
+    const ViewSet* __restrict__ vs, const uint2* __restrict__ ranges, const uint2* __restrict__ seg,
+    const uint32_t* __restrict__ items, const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals,
+    const float4* __restrict__ rec, const short4* __restrict__ rect, const TF* __restrict__ feat, float tau,
+    unsigned long long* __restrict__ status, float* __restrict__ part, uint32_t* __restrict__ xflag,
+    uint32_t* __restrict__ xqueue) {
+  const int lane = threadIdx.x & 31;
+  const unsigned long long n_items = status[kStItems];
+  for (;;) {
+    unsigned long long i = 0;
+    if (lane == 0) i = atomicAdd(status + kStNext, 1ull);
+    i = __shfl_sync(0xffffffffu, i, 0);
+    if (i >= n_items) break;
+    const uint32_t tile = items[i];
+    const int k = view_of(*vs, tile);
+    const ViewParams v = vs->v[k];
+    const uint2 sgt = seg[tile];
+    Seg sg = make_seg(v, ranges[tile], sgt, (uint32_t)i, keys, seg_window(v, status), lane);
+    sg.part = sgt.y > 1 ? part + (size_t)i * (C + 1) * 32 : nullptr;
+    SkipArgs sk{};
+    sk.xflag = xflag;
+    sk.xqueue = xqueue;
+    sk.gtile = (int)tile;
+    composite_tile<C, TF, TO, kPlain>((int)(tile - vs->toff[k]), sg, keys, vals, rec, rect + k * vs->rect_stride, feat,
+                                      v, tau, (TO*)vs->F[k], vs->A[k], status, HitLog{}, sk);
   }
 }
 
@@ -519,6 +572,97 @@ __device__ __forceinline__ void store_group(TO* __restrict__ p, const float* f) 
 }
 
 template <int C, typename TO, int MODE>
+__device__ __forceinline__ void merge_tile(int tile, int tl, int grp, int lane, const uint2* __restrict__ seg,
+                                           const ViewParams& v, float tau, TO* __restrict__ Fout,
+                                           float* __restrict__ Aout, unsigned long long* __restrict__ status,
+                                           const float* __restrict__ part, const SkipArgs& sk) {
+  constexpr int G = C >= kMergeCh ? C / kMergeCh : 1;  // channel groups
+  constexpr int CG = C / G;
+  const uint2 sgt = seg[tile];
+  const int tx = tl % v.tiles_x, ty = tl / v.tiles_x;
+  const int px = tx * TSX + (lane & 7), py = ty * TSY + (lane >> 3);
+  const bool inside = px < v.W && py < v.H;
+  const float* pbase = part + (size_t)sgt.x * (C + 1) * 32;
+  // the segments this pixel composites (front to back until the stop) and the stop check
+  float T = 1.0f;
+  uint32_t kend = sgt.y;
+  bool redo = false, stopped = false;
+  for (uint32_t k0 = 0; k0 < sgt.y && !stopped; k0 += 8) {  // eight segments' loads in flight
+    float tk[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) tk[j] = k0 + j < sgt.y ? pbase[(size_t)(k0 + j) * (C + 1) * 32 + C * 32 + lane] : 1.0f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      if (stopped || k0 + j >= sgt.y) continue;
+      if (T < 1.0f && T * tk[j] < tau) redo = true;  // the stop falls inside a later segment
+      T *= tk[j];
+      if (T < tau) {
+        kend = k0 + j + 1;
+        stopped = true;
+      }
+    }
+  }
+  // F = sum_k (T_0 ... T_{k-1}) F_k over this warp's channels; loads of two
+  // segments in flight together
+  float acc[CG];
+#pragma unroll
+  for (int c = 0; c < CG; ++c) acc[c] = 0.0f;
+  float P = 1.0f;
+  for (uint32_t k0 = 0; k0 < kend; k0 += 4) {  // four segments' loads in flight
+    float f[4][CG], tq[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const bool in = k0 + j < kend;
+      const float* pj = pbase + (size_t)(k0 + j) * (C + 1) * 32;
+#pragma unroll
+      for (int c = 0; c < CG; ++c) f[j][c] = in ? pj[(grp * CG + c) * 32 + lane] : 0.0f;
+      tq[j] = in ? pj[C * 32 + lane] : 1.0f;
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+#pragma unroll
+      for (int c = 0; c < CG; ++c) acc[c] = fmaf(P, f[j][c], acc[c]);
+      P *= tq[j];
+    }
+  }
+  bool fail = false;
+  if constexpr (MODE == kInterval) {  // coarse check of the lost mass over the tile's union interval
+    if (grp == 0) {
+      __shared__ float s_pre[kPropBins];
+      const float tot = tile_hist_prefix(sk.thist + (size_t)tile * kPropBins, s_pre, lane);
+      int lo_b = kPropBins, hi_b = -1;
+      if (inside) {
+        const uchar2 b = sk.bins[(size_t)py * v.W + px];
+        if (b.y >= b.x) {
+          lo_b = b.x;
+          hi_b = b.y;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        lo_b = min(lo_b, __shfl_xor_sync(0xffffffffu, lo_b, o));
+        hi_b = max(hi_b, __shfl_xor_sync(0xffffffffu, hi_b, o));
+      }
+      const bool empty = hi_b < lo_b;
+      const int bn = empty ? lo_b : max(lo_b - sk.margin, 0);
+      const int bf = empty ? hi_b : min(hi_b + sk.margin, kPropBins - 1);
+      if (inside) {
+        const float front = empty ? tot : (bn > 0 ? s_pre[bn - 1] : 0.0f);
+        const float back = empty ? 0.0f : tot - s_pre[bf];
+        fail = -expm1f(-front) + T * -expm1f(-back) > sk.max_missed;
+      }
+    }
+  }
+  if (inside) {
+    const size_t pix = (size_t)py * v.W + px;
+    store_group<C, TO>(Fout + pix * C + grp * CG, acc);
+    if (grp == 0 && Aout) Aout[pix] = 1.0f - T;
+  }
+  if (grp == 0 && __any_sync(0xffffffffu, (redo || fail) && inside) && lane == 0)
+    sk.queue[atomicAdd(status + sk.qword, 1ull)] = (uint32_t)tile;
+}
+
+template <int C, typename TO, int MODE>
 __global__ void __launch_bounds__(32) composite_merge_kernel(const uint2* __restrict__ seg,
                                                              const uint32_t* __restrict__ multi, ViewParams v,
                                                              float tau, TO* __restrict__ Fout,
@@ -526,7 +670,6 @@ __global__ void __launch_bounds__(32) composite_merge_kernel(const uint2* __rest
                                                              unsigned long long* __restrict__ status,
                                                              const float* __restrict__ part, SkipArgs sk) {
   constexpr int G = C >= kMergeCh ? C / kMergeCh : 1;  // channel groups
-  constexpr int CG = C / G;
   const int lane = threadIdx.x & 31;
   const unsigned long long n_items = status[kStMulti] * G;
   for (;;) {
@@ -535,89 +678,32 @@ __global__ void __launch_bounds__(32) composite_merge_kernel(const uint2* __rest
     m = __shfl_sync(0xffffffffu, m, 0);
     if (m >= n_items) break;
     const int tile = (int)multi[m / G];
-    const int grp = (int)(m % G);
-    const uint2 sgt = seg[tile];
-    const int tx = tile % v.tiles_x, ty = tile / v.tiles_x;
-    const int px = tx * TSX + (lane & 7), py = ty * TSY + (lane >> 3);
-    const bool inside = px < v.W && py < v.H;
-    const float* pbase = part + (size_t)sgt.x * (C + 1) * 32;
-    // the segments this pixel composites (front to back until the stop) and the stop check
-    float T = 1.0f;
-    uint32_t kend = sgt.y;
-    bool redo = false, stopped = false;
-    for (uint32_t k0 = 0; k0 < sgt.y && !stopped; k0 += 8) {  // eight segments' loads in flight
-      float tk[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) tk[j] = k0 + j < sgt.y ? pbase[(size_t)(k0 + j) * (C + 1) * 32 + C * 32 + lane] : 1.0f;
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        if (stopped || k0 + j >= sgt.y) continue;
-        if (T < 1.0f && T * tk[j] < tau) redo = true;  // the stop falls inside a later segment
-        T *= tk[j];
-        if (T < tau) {
-          kend = k0 + j + 1;
-          stopped = true;
-        }
-      }
-    }
-    // F = sum_k (T_0 ... T_{k-1}) F_k over this warp's channels; loads of two
-    // segments in flight together
-    float acc[CG];
-#pragma unroll
-    for (int c = 0; c < CG; ++c) acc[c] = 0.0f;
-    float P = 1.0f;
-    for (uint32_t k0 = 0; k0 < kend; k0 += 4) {  // four segments' loads in flight
-      float f[4][CG], tq[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const bool in = k0 + j < kend;
-        const float* pj = pbase + (size_t)(k0 + j) * (C + 1) * 32;
-#pragma unroll
-        for (int c = 0; c < CG; ++c) f[j][c] = in ? pj[(grp * CG + c) * 32 + lane] : 0.0f;
-        tq[j] = in ? pj[C * 32 + lane] : 1.0f;
-      }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-#pragma unroll
-        for (int c = 0; c < CG; ++c) acc[c] = fmaf(P, f[j][c], acc[c]);
-        P *= tq[j];
-      }
-    }
-    bool fail = false;
-    if constexpr (MODE == kInterval) {  // coarse check of the lost mass over the tile's union interval
-      if (grp == 0) {
-        __shared__ float s_pre[kPropBins];
-        const float tot = tile_hist_prefix(sk.thist + (size_t)tile * kPropBins, s_pre, lane);
-        int lo_b = kPropBins, hi_b = -1;
-        if (inside) {
-          const uchar2 b = sk.bins[(size_t)py * v.W + px];
-          if (b.y >= b.x) {
-            lo_b = b.x;
-            hi_b = b.y;
-          }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          lo_b = min(lo_b, __shfl_xor_sync(0xffffffffu, lo_b, o));
-          hi_b = max(hi_b, __shfl_xor_sync(0xffffffffu, hi_b, o));
-        }
-        const bool empty = hi_b < lo_b;
-        const int bn = empty ? lo_b : max(lo_b - sk.margin, 0);
-        const int bf = empty ? hi_b : min(hi_b + sk.margin, kPropBins - 1);
-        if (inside) {
-          const float front = empty ? tot : (bn > 0 ? s_pre[bn - 1] : 0.0f);
-          const float back = empty ? 0.0f : tot - s_pre[bf];
-          fail = -expm1f(-front) + T * -expm1f(-back) > sk.max_missed;
-        }
-      }
-    }
-    if (inside) {
-      const size_t pix = (size_t)py * v.W + px;
-      store_group<C, TO>(Fout + pix * C + grp * CG, acc);
-      if (grp == 0 && Aout) Aout[pix] = 1.0f - T;
-    }
-    if (grp == 0 && __any_sync(0xffffffffu, (redo || fail) && inside) && lane == 0)
-      sk.queue[atomicAdd(status + sk.qword, 1ull)] = (uint32_t)tile;
+    merge_tile<C, TO, MODE>(tile, tile, (int)(m % G), lane, seg, v, tau, Fout, Aout, status, part, sk);
+    __syncwarp();
+  }
+}
+
+// The merge over a batch of views (plain traversal): each split tile's view
+// from its global tile.
+template <int C, typename TO>
+__global__ void __launch_bounds__(32) composite_merge_views_kernel(const ViewSet* __restrict__ vs,
+                                                                   const uint2* __restrict__ seg,
+                                                                   const uint32_t* __restrict__ multi, float tau,
+                                                                   unsigned long long* __restrict__ status,
+                                                                   const float* __restrict__ part, SkipArgs sk) {
+  constexpr int G = C >= kMergeCh ? C / kMergeCh : 1;
+  const int lane = threadIdx.x & 31;
+  const unsigned long long n_items = status[kStMulti] * G;
+  for (;;) {
+    unsigned long long m = 0;
+    if (lane == 0) m = atomicAdd(status + kStNextMerge, 1ull);
+    m = __shfl_sync(0xffffffffu, m, 0);
+    if (m >= n_items) break;
+    const uint32_t tile = multi[m / G];
+    const int k = view_of(*vs, tile);
+    const ViewParams v = vs->v[k];
+    merge_tile<C, TO, kPlain>((int)tile, (int)(tile - vs->toff[k]), (int)(m % G), lane, seg, v, tau, (TO*)vs->F[k],
+                              vs->A[k], status, part, sk);
     __syncwarp();
   }
 }
@@ -632,14 +718,206 @@ __global__ void __launch_bounds__(32) composite_queue_kernel(const uint2* __rest
                                                              const TF* __restrict__ feat, ViewParams v, float tau,
                                                              TO* __restrict__ Fout, float* __restrict__ Aout,
                                                              unsigned long long* __restrict__ status,
-                                                             const uint32_t* __restrict__ queue, int qword) {
+                                                             const uint32_t* __restrict__ queue, int qword,
+                                                             uint32_t* __restrict__ xflag,
+                                                             uint32_t* __restrict__ xqueue) {
   const unsigned long long n = status[qword];
   for (unsigned long long i = blockIdx.x; i < n; i += gridDim.x) {
     const int tile = (int)queue[i];
     const uint2 rg = ranges[tile];
     const Seg sg{rg.x, rg.y, -3.4e38f, 3.4e38f, nullptr};
-    composite_tile<C, TF, TO, kPlain>(tile, sg, keys, vals, rec, rect, feat, v, tau, Fout, Aout, status, HitLog{},
-                                      SkipArgs{});
+    SkipArgs sk{};
+    sk.xflag = xflag;
+    sk.xqueue = xqueue;
+    sk.gtile = tile;
+    composite_tile<C, TF, TO, kPlain>(tile, sg, keys, vals, rec, rect, feat, v, tau, Fout, Aout, status, HitLog{}, sk);
+  }
+}
+
+// The sequential walk of a batch's queued tiles (global tile ids).
+template <int C, typename TF, typename TO>
+__global__ void __launch_bounds__(32) composite_queue_views_kernel(const ViewSet* __restrict__ vs,
+                                                                   const uint2* __restrict__ ranges,
+                                                                   const uint32_t* __restrict__ keys,
+                                                                   const uint32_t* __restrict__ vals,
+                                                                   const float4* __restrict__ rec,
+                                                                   const short4* __restrict__ rect,
+                                                                   const TF* __restrict__ feat, float tau,
+                                                                   unsigned long long* __restrict__ status,
+                                                                   const uint32_t* __restrict__ queue, int qword,
+                                                                   uint32_t* __restrict__ xflag,
+                                                                   uint32_t* __restrict__ xqueue) {
+  const unsigned long long n = status[qword];
+  for (unsigned long long i = blockIdx.x; i < n; i += gridDim.x) {
+    const uint32_t tile = queue[i];
+    const int k = view_of(*vs, tile);
+    const ViewParams v = vs->v[k];
+    const uint2 rg = ranges[tile];
+    const Seg sg{rg.x, rg.y, -3.4e38f, 3.4e38f, nullptr};
+    SkipArgs sk{};
+    sk.xflag = xflag;
+    sk.xqueue = xqueue;
+    sk.gtile = (int)tile;
+    composite_tile<C, TF, TO, kPlain>((int)(tile - vs->toff[k]), sg, keys, vals, rec, rect + k * vs->rect_stride,
+                                      feat, v, tau, (TO*)vs->F[k], vs->A[k], status, HitLog{}, sk);
+  }
+}
+
+// Exact walk of the tiles queued because a pixel's reorder buffer
+// overflowed: each lane collects every hit of its pixel's ray over the
+// tile's whole list (entry distance, chord, list position) into its own
+// scratch list, sorts it by (t0, chord, position) -- the order of the
+// reorder buffer, Eq. 5-6's front to back -- and composites it with the
+// stop rule, rewriting the tile's F and A.  A ray with more than kExactCap
+// hits keeps its first kExactCap in list order and is counted in
+// overflow_order.  With VIEWS the queue holds global tiles of a batch.
+template <int C, typename TF, typename TO, bool VIEWS>
+__global__ void __launch_bounds__(32) composite_exact_kernel(
+    const ViewSet* __restrict__ vs, ViewParams v1, TO* __restrict__ F1, float* __restrict__ A1,
+    const uint2* __restrict__ ranges, const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals,
+    const float4* __restrict__ rec, const short4* __restrict__ rect, const TF* __restrict__ feat, float tau,
+    unsigned long long* __restrict__ status, const uint32_t* __restrict__ xqueue, float2* __restrict__ xhit,
+    uint32_t* __restrict__ xpos) {
+  __shared__ float4 s_b0[NT], s_b1[NT], s_b2[NT], s_xl[NT];
+  __shared__ uint32_t s_mask[NT];
+  const int lane = threadIdx.x & 31;
+  float2* myh = xhit + ((size_t)blockIdx.x * 32 + lane) * kExactCap;
+  uint32_t* myp = xpos + ((size_t)blockIdx.x * 32 + lane) * kExactCap;
+  const unsigned long long n = status[kStExactQ];
+  for (unsigned long long i = blockIdx.x; i < n; i += gridDim.x) {
+    const uint32_t gt = xqueue[i];
+    int k = 0;
+    if constexpr (VIEWS) k = view_of(*vs, gt);
+    const ViewParams v = VIEWS ? vs->v[k] : v1;
+    const int tile = VIEWS ? (int)(gt - vs->toff[k]) : (int)gt;
+    const short4* rc = VIEWS ? rect + k * vs->rect_stride : rect;
+    TO* Fout = VIEWS ? (TO*)vs->F[k] : F1;
+    float* Aout = VIEWS ? vs->A[k] : A1;
+    const int sx = (tile % v.tiles_x) * TSX, sy = (tile / v.tiles_x) * TSY;
+    const int px = sx + (lane & 7), py = sy + (lane >> 3);
+    const bool inside = px < v.W && py < v.H;
+    const RayDir rd = pixel_ray(v, px, py);
+    const uint2 rg = ranges[gt];
+    int m = 0;
+    bool over = false;
+    for (uint32_t base = rg.x; base < rg.y; base += NT) {  // collect
+      __syncwarp();
+      uint32_t msk = 0;
+      if (base + lane < rg.y) {
+        const uint32_t vid = vals[base + lane];
+        const float4* rp = rec + 4 * (size_t)vid;
+        stage_voxel(rp[0], rp[1], rp[2], v, s_b0[lane], s_b1[lane], s_b2[lane], s_xl[lane]);
+        msk = rect_mask(rc[vid], sx, sy);
+      }
+      s_mask[lane] = msk;
+      __syncwarp();
+      uint32_t cand = transpose32(s_mask[lane], lane);
+      if (!inside) cand = 0;
+      while (cand) {
+        const int idx = __ffs(cand) - 1;
+        cand &= cand - 1;
+        float t0, dl, e[3];
+        int ax0, ax1;
+        if (!slab_hit(s_b0[idx], s_b1[idx], s_b2[idx], s_xl[idx], rd, v.znear, v.zfar, t0, dl, ax0, ax1, e)) continue;
+        if (m < kExactCap) {
+          myh[m] = make_float2(t0, dl);
+          myp[m] = base - rg.x + (uint32_t)idx;
+          ++m;
+        } else {
+          over = true;
+        }
+      }
+    }
+    for (int a = 1; a < m; ++a) {  // sort by (t0, chord, list position)
+      const float2 h = myh[a];
+      const uint32_t q = myp[a];
+      int b = a;
+      while (b > 0) {
+        const float2 g = myh[b - 1];
+        const uint32_t r = myp[b - 1];
+        if (!(h.x < g.x || (h.x == g.x && (h.y < g.y || (h.y == g.y && q < r))))) break;
+        myh[b] = g;
+        myp[b] = r;
+        --b;
+      }
+      myh[b] = h;
+      myp[b] = q;
+    }
+    float acc[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) acc[c] = 0.0f;
+    float T = 1.0f;
+    for (int a = 0; a < m; ++a) {  // composite front to back, stop once T < tau
+      const uint32_t vid = vals[rg.x + myp[a]];
+      const float sig = rec[4 * (size_t)vid + 3].x;
+      float f[C];
+      load_feat<C>(feat + (size_t)vid * C, f);
+      const float e = expf(-sig * myh[a].y);
+      const float w = T * (1.0f - e);
+#pragma unroll
+      for (int c = 0; c < C; ++c) acc[c] = fmaf(w, f[c], acc[c]);
+      T *= e;
+      if (T < tau) break;
+    }
+    if (inside) {
+      const size_t pix = (size_t)py * v.W + px;
+      store_row<C>(Fout + pix * C, acc);
+      if (Aout) Aout[pix] = 1.0f - T;
+    }
+    if (over) atomicAdd(status + kStOverflowOrder, 1ull);
+  }
+}
+
+// The plain split walk of a batch of views: plan all segments, clear each
+// view's empty tiles, walk all segments with persistent warps, merge the
+// split tiles, then walk the tiles whose stop fell inside a later segment.
+template <int C, typename TF, typename TO>
+void views_walk(art_ctx* ctx, const ViewSet& vs) {
+  const int ntiles = (int)vs.toff[vs.nv];
+  const TF* feat = (const TF*)ctx->d_feat;
+  cudaMemsetAsync(ctx->d_status + kStItems, 0, 4 * sizeof(unsigned long long), ctx->stream);
+  cudaMemsetAsync(ctx->d_status + kStFallback, 0, sizeof(unsigned long long), ctx->stream);
+  cudaMemsetAsync(ctx->d_xflag, 0, sizeof(uint32_t) * (size_t)ntiles, ctx->stream);
+  cudaMemsetAsync(ctx->d_status + kStExactQ, 0, sizeof(unsigned long long), ctx->stream);
+  ART_LAUNCH(ctx, "composite_plan", seg_plan_kernel, (ntiles + 255) / 256, 256, 0, ntiles, ctx->d_ranges, ctx->seg_len,
+             ctx->d_seg, ctx->d_items, ctx->d_multi, ctx->d_status, (const uint32_t*)nullptr, 0);
+  for (int k = 0; k < vs.nv; ++k) {
+    const ViewParams& v = vs.v[k];
+    auto cfn = composite_clear_kernel<C, TO>;
+    ART_LAUNCH(ctx, "composite_clear", cfn, (v.tiles_x * v.tiles_y + 7) / 8, 256, 0, ctx->d_ranges + vs.toff[k], v,
+               (TO*)vs.F[k], vs.A[k]);
+  }
+  auto kfn = composite_split_views_kernel<C, TF, TO>;
+  ART_LAUNCH(ctx, "composite", kfn, ctx->composite_blocks, 32, 0, ctx->d_vset, ctx->d_ranges, ctx->d_seg, ctx->d_items,
+             ctx->d_keys, ctx->d_vals, ctx->d_rec, ctx->d_rect_v, feat, ctx->cfg.tau, ctx->d_status, ctx->d_part,
+             ctx->d_xflag, ctx->d_xqueue);
+  SkipArgs sk{};
+  sk.queue = ctx->d_fbq;
+  sk.qword = kStFallback;
+  auto mfn = composite_merge_views_kernel<C, TO>;
+  ART_LAUNCH(ctx, "composite_merge", mfn, 32 * ctx->num_sms, 32, 0, ctx->d_vset, ctx->d_seg, ctx->d_multi,
+             ctx->cfg.tau, ctx->d_status, ctx->d_part, sk);
+  auto qfn = composite_queue_views_kernel<C, TF, TO>;
+  ART_LAUNCH(ctx, "composite_fallback", qfn, std::min(ntiles, 16 * ctx->num_sms), 32, 0, ctx->d_vset, ctx->d_ranges,
+             ctx->d_keys, ctx->d_vals, ctx->d_rec, ctx->d_rect_v, feat, ctx->cfg.tau, ctx->d_status, ctx->d_fbq,
+             kStFallback, ctx->d_xflag, ctx->d_xqueue);
+  auto xfn = composite_exact_kernel<C, TF, TO, true>;
+  ART_LAUNCH(ctx, "composite_exact", xfn, kExactBlocks, 32, 0, (const ViewSet*)ctx->d_vset, vs.v[0], (TO*)nullptr,
+             (float*)nullptr, ctx->d_ranges, ctx->d_keys, ctx->d_vals, ctx->d_rec, ctx->d_rect_v, feat, ctx->cfg.tau,
+             ctx->d_status, ctx->d_xqueue, ctx->d_xhit, ctx->d_xpos);
+}
+
+template <int C>
+void views_dtypes(art_ctx* ctx, const ViewSet& vs, int F_dtype) {
+  const int fd = ctx->feat_dtype;
+  if (F_dtype == ART_F32) {
+    if (fd == ART_F32) views_walk<C, float, float>(ctx, vs);
+    else if (fd == ART_BF16) views_walk<C, __nv_bfloat16, float>(ctx, vs);
+    else views_walk<C, __half, float>(ctx, vs);
+  } else {
+    if (fd == ART_F32) views_walk<C, float, __nv_bfloat16>(ctx, vs);
+    else if (fd == ART_BF16) views_walk<C, __nv_bfloat16, __nv_bfloat16>(ctx, vs);
+    else views_walk<C, __half, __nv_bfloat16>(ctx, vs);
   }
 }
 
@@ -648,10 +926,13 @@ __global__ void __launch_bounds__(32) composite_queue_kernel(const uint2* __rest
 // persistent warps, merge the split tiles; tiles that need the sequential
 // walk go to sk.queue (count in status[sk.qword]).
 template <int C, typename TF, typename TO>
-void split_pass(art_ctx* ctx, const ViewParams& v, void* F, float* A, int mode, const SkipArgs& sk,
+void split_pass(art_ctx* ctx, const ViewParams& v, void* F, float* A, int mode, const SkipArgs& sk_in,
                 const uint32_t* list, int list_word) {
   const int ntiles = v.tiles_x * v.tiles_y;
   const TF* feat = (const TF*)ctx->d_feat;
+  SkipArgs sk = sk_in;
+  sk.xflag = ctx->d_xflag;
+  sk.xqueue = ctx->d_xqueue;
   cudaMemsetAsync(ctx->d_status + kStItems, 0, 4 * sizeof(unsigned long long), ctx->stream);  // items .. next merge
   cudaMemsetAsync(ctx->d_status + sk.qword, 0, sizeof(unsigned long long), ctx->stream);
   // a re-walk covers a few tiles: shorter segments put more warps on them
@@ -693,6 +974,8 @@ void split_walk(art_ctx* ctx, const ViewParams& v, void* F, float* A, int mode, 
   SkipArgs sk = sk_in;
   sk.queue = ctx->d_fbq;
   sk.qword = kStFallback;
+  cudaMemsetAsync(ctx->d_xflag, 0, sizeof(uint32_t) * (size_t)ntiles, ctx->stream);
+  cudaMemsetAsync(ctx->d_status + kStExactQ, 0, sizeof(unsigned long long), ctx->stream);
   split_pass<C, TF, TO>(ctx, v, F, A, mode, sk, nullptr, 0);
   const uint32_t* seq = ctx->d_fbq;
   int seq_word = kStFallback;
@@ -707,7 +990,12 @@ void split_walk(art_ctx* ctx, const ViewParams& v, void* F, float* A, int mode, 
   auto qfn = composite_queue_kernel<C, TF, TO>;
   const int qgrid = std::min(ntiles, 16 * ctx->num_sms);
   ART_LAUNCH(ctx, "composite_fallback", qfn, qgrid, 32, 0, ctx->d_ranges, ctx->d_keys, ctx->d_vals, ctx->d_rec,
-             ctx->d_rect, feat, v, ctx->cfg.tau, (TO*)F, A, ctx->d_status, seq, seq_word);
+             ctx->d_rect, feat, v, ctx->cfg.tau, (TO*)F, A, ctx->d_status, seq, seq_word, ctx->d_xflag,
+             ctx->d_xqueue);
+  auto xfn = composite_exact_kernel<C, TF, TO, false>;
+  ART_LAUNCH(ctx, "composite_exact", xfn, kExactBlocks, 32, 0, (const ViewSet*)nullptr, v, (TO*)F, A, ctx->d_ranges,
+             ctx->d_keys, ctx->d_vals, ctx->d_rec, ctx->d_rect, feat, ctx->cfg.tau, ctx->d_status, ctx->d_xqueue,
+             ctx->d_xhit, ctx->d_xpos);
 }
 
 template <int C, typename TF, typename TO>
@@ -765,6 +1053,16 @@ art_status dispatch(art_ctx* ctx, const ViewParams& v, void* F, int F_dtype, flo
 art_status launch_composite(art_ctx* ctx, const ViewParams& v, void* F, int F_dtype, float* A, const void* dbg_log) {
   const HitLog* dbg = (const HitLog*)dbg_log;
   return dispatch(ctx, v, F, F_dtype, A, dbg, dbg ? kDebug : kPlain, SkipArgs{});
+}
+
+art_status launch_composite_views(art_ctx* ctx, const ViewSet& vs, int F_dtype) {
+  switch (ctx->C) {
+    case 4: views_dtypes<4>(ctx, vs, F_dtype); return ART_OK;
+    case 8: views_dtypes<8>(ctx, vs, F_dtype); return ART_OK;
+    case 16: views_dtypes<16>(ctx, vs, F_dtype); return ART_OK;
+    case 32: views_dtypes<32>(ctx, vs, F_dtype); return ART_OK;
+    default: return fail(ctx, ART_ERR_UNSUPPORTED, "composite: C=%d not built (4, 8, 16, 32)", ctx->C);
+  }
 }
 
 // Per voxel, the rotation that maps world directions into its canonical

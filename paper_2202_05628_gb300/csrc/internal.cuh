@@ -16,6 +16,7 @@ namespace art {
 
 constexpr int kMaxJoints = 64;
 constexpr int kMaxViews = 8;
+constexpr int kOpacityPad = 32;  // two-branch network: channels of the opacity branch's packed input [A, I_f, 0 ...]
 constexpr float kDetMin = 1e-3f;   // blended transforms below this are dropped
 constexpr float kZMin = 1e-6f;     // corners must lie in front of the camera
 constexpr float kBboxPad = 2e-3f;  // conservative pixel-bbox growth (pixels)
@@ -41,7 +42,8 @@ enum StatusWord {
   kStScanTicket = 18,   // binning: blocks of the tile scan started (their order)
   kStScanError = 19,    // binning: tile-scan blocks that timed out waiting for a predecessor
   kStActiveGroups = 20, // binning: groups of four consecutive tiles with instances (listed in d_agroups)
-  kStWords = 21
+  kStExactQ = 21,       // composite: tiles queued for the exact re-walk (a pixel's reorder buffer overflowed)
+  kStWords = 22
 };
 
 // Per-view camera, with host-precomputed ray frame.
@@ -60,9 +62,31 @@ struct ViewParams {
   float dscale;    // depth quanta per metre
 };
 
+// Several views rendered in one pass (art_render_views): their screen tiles
+// laid end to end in one tile space (view k owns global tiles
+// [toff[k], toff[k + 1])), each view's parameters with the depth-key layout
+// of the joint space (one depth_bits for all), its per-voxel rectangles at
+// rect + k * rect_stride, and its output maps.  Held in device memory; a
+// kernel finds the view of a global tile with view_of.
+struct ViewSet {
+  int nv;
+  uint32_t toff[kMaxViews + 1];
+  int64_t rect_stride;
+  ViewParams v[kMaxViews];
+  void* F[kMaxViews];
+  float* A[kMaxViews];
+};
+
+__host__ __device__ inline int view_of(const ViewSet& vs, uint32_t tile) {
+  int k = 0;
+  while (k + 1 < vs.nv && tile >= vs.toff[k + 1]) ++k;
+  return k;
+}
+
 // Layer of a convolutional network (device pointers owned by the context).
 struct ConvLayer {
   int cout, cin, k;
+  int cin_pad;                 // input channels of the BF16 / FP8 weights (cin, or cin zero-padded)
   float* w32 = nullptr;        // [cout][k][k][cin] FP32
   float* b32 = nullptr;        // [cout]
   __nv_bfloat16* wbf = nullptr;  // [cout][k*k*cin] BF16 (K-major)
@@ -178,6 +202,19 @@ struct art_ctx {
   size_t d_fbq_bytes = 0;
   uint32_t* d_fbq2 = nullptr;     // [tiles] second queue (sequential walk after a refill pass)
   size_t d_fbq2_bytes = 0;
+  // ---- several views in one pass (art_render_views)
+  short4* d_rect_v = nullptr;     // [views][n] per-view pixel rects, depth quanta, tile counts
+  uint32_t* d_q_v = nullptr;
+  uint32_t* d_cnt_v = nullptr;
+  int64_t views_cap = 0;          // (views x n) capacity of the three
+  art::ViewSet* d_vset = nullptr; // the batch's view table (device)
+  art::ViewSet h_vset{};          // ... and its host copy
+  // ---- exact re-walk of tiles whose reorder buffer overflowed
+  uint32_t* d_xflag = nullptr;    // [tiles] queued already (zeroed per render)
+  uint32_t* d_xqueue = nullptr;   // [tiles] the queue (count in status[kStExactQ])
+  size_t d_xflag_bytes = 0, d_xqueue_bytes = 0;
+  float2* d_xhit = nullptr;       // [blocks][32][kExactCap] per-lane hit lists (t0, chord) ...
+  uint32_t* d_xpos = nullptr;     // ... and list positions
   // ---- split composite walk
   int seg_len = 256;              // list entries per segment
   int composite_blocks = 0;       // persistent one-warp blocks of the split walk
@@ -226,6 +263,12 @@ void launch_lbs(art_ctx* ctx);
 // bound of the coarse check (64 bins over [znear, zfar]).  Also counts each
 // tile's instances and resets the tile scan: launch_bin follows it.
 void launch_project(art_ctx* ctx, const ViewParams& v, uint32_t* hbin = nullptr, float* htau = nullptr);
+// Projection of view k of a batch into the joint tile space: its rectangles,
+// depth quanta and tile counts at rect / q / cnt (the view's slices), its
+// tiles' instance counts at tcount (the view's first global tile); the tile
+// scan state is reset by view 0's launch.
+void launch_project_view(art_ctx* ctx, const ViewParams& v, short4* rect, uint32_t* q, uint32_t* cnt,
+                         uint32_t* tcount, bool first);
 
 // ---- binning and sorting (binsort.cu)
 // With thist set (zeroed [tiles][64]), also accumulate the coarse optical-depth
@@ -239,6 +282,10 @@ void launch_project(art_ctx* ctx, const ViewParams& v, uint32_t* hbin = nullptr,
 // the learned skip).
 void launch_bin(art_ctx* ctx, const ViewParams& v, const uint32_t* hbin = nullptr, const float* htau = nullptr,
                 float* thist = nullptr);
+// Binning of a batch of views in one tile space (ntiles in all, joint
+// depth_bits): one scan of all tiles' counts, one scatter per view (its
+// instances keyed by global tile), one sort of all buckets.
+void launch_bin_views(art_ctx* ctx, const ViewSet& vs, int64_t ntiles);
 // Radix sort of count (device word) pairs ping-ponging between (k0, v0) and
 // (k1, v1); returns the index (0 or 1) of the buffer holding the result.
 int launch_sort_bufs(art_ctx* ctx, uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, int64_t cap,
@@ -264,11 +311,16 @@ art_status launch_composite_sh(art_ctx* ctx, const ViewParams& v, void* F, int F
 art_status launch_composite_skip(art_ctx* ctx, const ViewParams& v, void* F, int F_dtype, float* A);
 // Labels of the plain composite (labels [H][W][3], bins [H][W][2]; either may be null).
 art_status launch_composite_labels(art_ctx* ctx, const ViewParams& v, float* labels, uint8_t* bins);
+// Plain composite of a batch of views in one split pass over the joint tile
+// space (after launch_bin_views); vs is the host copy of *ctx->d_vset.
+art_status launch_composite_views(art_ctx* ctx, const ViewSet& vs, int F_dtype);
 // One-warp blocks of the composite walk that fit on an SM (C channels of feat_bytes).
 int composite_blocks_per_sm(int C, int feat_bytes);
 constexpr int kShMaxDegree = 3;  // view-dependent features: spherical harmonics up to this degree
 constexpr int kShMaxBases = (kShMaxDegree + 1) * (kShMaxDegree + 1);
 constexpr int kPropBins = 64;          // proposal depth bins over [znear, zfar]
+constexpr int kExactBlocks = 64;       // one-warp blocks of the exact re-walk
+constexpr int kExactCap = 1024;        // hits per pixel the exact re-walk sorts (beyond: overflow_order)
 constexpr float kLabelWmin = 1e-6f;    // significant hit: weight above this
 constexpr float kLabelBudget = 0.4f;   // label bins keep the coarse bound under this fraction of max_missed
 constexpr float kHistPad = 1e-5f;      // metres added to both ends of a voxel's distance range before binning
@@ -287,7 +339,8 @@ art_status launch_backward(art_ctx* ctx, const ViewParams& v, const float* F, co
                            const float* dA, float* gfeat, float* gsig, float* gw);
 
 // ---- shading (cnn.cu, cnn_tc.cu)
-art_status run_shader(art_ctx* ctx, const ViewParams& v, const void* F, int F_dtype, float* rgba);
+// A: the coarse opacity map (device), used by the two-branch network only.
+art_status run_shader(art_ctx* ctx, const ViewParams& v, const void* F, int F_dtype, const float* A, float* rgba);
 
 // One 3x3 convolution on the tensor cores: input [H][W][cin] BF16 (NHWC,
 // dense), weights [cout][3][3][cin] BF16, bias FP32; output BF16 written at
@@ -302,9 +355,10 @@ struct TcConv {
   int cout, act;
   void* out;
   int ld_out, ch_off, up2;
-  float* rgba;
-  const float* head_w;
+  float* rgba;             // fused 1x1 head + sigmoid into head_n (<= 4) FP32 channels of rgba,
+  const float* head_w;     // starting at channel head_off of head_ld per pixel
   const float* head_b;
+  int head_n = 4, head_ld = 4, head_off = 0;
   // BF16: also the 2x2 max pooling of the output, a dense [H/2][W/2][cout]
   // tensor (fused into the row-blocked kernel's epilogue, else a pass of its own)
   void* pool = nullptr;

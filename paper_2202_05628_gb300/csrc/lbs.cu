@@ -354,6 +354,15 @@ void launch_lbs(art_ctx* ctx) {
              ctx->d_status);
 }
 
+void launch_project_view(art_ctx* ctx, const ViewParams& v, short4* rect, uint32_t* q, uint32_t* cnt,
+                         uint32_t* tcount, bool first) {
+  const int64_t n = ctx->n;
+  const unsigned grid = (unsigned)((n + 255) / 256);
+  const int words = first ? (int)tile_scan_state_words(ctx->ranges_cap) : 0;
+  ART_LAUNCH(ctx, "project", project_kernel, grid, 256, 0, n, ctx->d_geo, v, rect, q, cnt, ctx->d_sigma,
+             (uint32_t*)nullptr, (float*)nullptr, tcount, ctx->d_scan_state, words, ctx->d_status);
+}
+
 void launch_project(art_ctx* ctx, const ViewParams& v, uint32_t* hbin, float* htau) {
   int64_t n = ctx->n;
   unsigned grid = (unsigned)((n + 255) / 256);

@@ -231,31 +231,64 @@ __device__ __forceinline__ float rcp_approx(float x) {
 }
 
 
-// The pixel ray's unit direction held to ~48 bits as the sum of two FP32
-// vectors (hi + lo).  The hit test below works at metre scale 2 m from the
-// voxels; there a plain FP32 direction (~1e-7 relative error) moves the ray by
-// ~3e-7 m sideways, which misplaces the chord of a ray that meets a face at a
-// shallow angle by micrometres.  The direction is formed in FP64 exactly as
-// Sec. 3.1's camera rays are defined (through the pixel centre, normalised
-// after the rotation) and split.
+// Error-free FP32 transformations (exact results as unevaluated sums).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = __fmul_rn(a, b);
+  e = __fmaf_rn(a, b, -p);
+}
+// (h, l) + (bh, bl) as a double-float (error ~2^-44 relative)
+__device__ __forceinline__ void df_add(float& h, float& l, float bh, float bl) {
+  float s, e;
+  two_sum(h, bh, s, e);
+  e = __fadd_rn(e, __fadd_rn(l, bl));
+  h = __fadd_rn(s, e);
+  l = __fsub_rn(e, __fsub_rn(h, s));
+}
+
+// The pixel ray's direction D, not normalised, held to ~44 bits as the sum
+// of two FP32 vectors (hi + lo), and 1 / |D|.  The hit test works at metre
+// scale 2 m from the voxels; there a plain FP32 direction (~1e-7 relative
+// error) moves the ray by ~3e-7 m sideways, which misplaces the chord of a
+// ray that meets a face at a shallow angle by micrometres.  The ray through
+// the pixel centre (Sec. 3.1's camera rays) is R^T ((x + 1/2 - cx) / fx,
+// (y + 1/2 - cy) / fy, 1); scaled by fx fy > 0 (the same ray) it needs no
+// division: D = R^T ((x + 1/2 - cx) fy, (y + 1/2 - cy) fx, fx fy), formed
+// with two-sums and two-products, FP32 only.  |D| enters as a scale of every
+// ray parameter of the pixel (FP32, ~1e-7 relative).
 struct RayDir {
   float h[3], l[3];
+  float inv_n;  // 1 / |D|
 };
 
 __device__ __forceinline__ RayDir pixel_ray(const ViewParams& v, int px, int py) {
-  const double dcx = ((double)px + 0.5 - (double)v.cx) / (double)v.fx;
-  const double dcy = ((double)py + 0.5 - (double)v.cy) / (double)v.fy;
-  double d[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) d[a] = (double)v.R[a] * dcx + (double)v.R[3 + a] * dcy + (double)v.R[6 + a];
-  const double inrm = rsqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  float ux, uxl, uy, uyl;  // pixel centre minus principal point, exactly
+  two_sum((float)px + 0.5f, -v.cx, ux, uxl);
+  two_sum((float)py + 0.5f, -v.cy, uy, uyl);
+  float c0, c0l, c1, c1l, c2, c2l;  // the camera-frame direction scaled by fx fy
+  two_prod(ux, v.fy, c0, c0l);
+  c0l = __fmaf_rn(uxl, v.fy, c0l);
+  two_prod(uy, v.fx, c1, c1l);
+  c1l = __fmaf_rn(uyl, v.fx, c1l);
+  two_prod(v.fx, v.fy, c2, c2l);
   RayDir r;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const double x = d[a] * inrm;
-    r.h[a] = (float)x;
-    r.l[a] = (float)(x - (double)r.h[a]);
+    float h, l, th, tl;
+    two_prod(v.R[a], c0, h, l);
+    l = __fmaf_rn(v.R[a], c0l, l);
+    two_prod(v.R[3 + a], c1, th, tl);
+    df_add(h, l, th, __fmaf_rn(v.R[3 + a], c1l, tl));
+    two_prod(v.R[6 + a], c2, th, tl);
+    df_add(h, l, th, __fmaf_rn(v.R[6 + a], c2l, tl));
+    r.h[a] = h;
+    r.l[a] = l;
   }
+  r.inv_n = rsqrtf(r.h[0] * r.h[0] + r.h[1] * r.h[1] + r.h[2] * r.h[2]);
   return r;
 }
 
@@ -283,21 +316,24 @@ __device__ __forceinline__ void stage_voxel(const float4& r0, const float4& r1, 
   xl = make_float4(xo[0], xo[1], xo[2], 0.0f);
 }
 
-// Exact hit of the pixel ray with a staged voxel (stage_voxel), anchored at
-// the voxel: s = <cw - o, d> is the ray parameter of the point nearest the
-// warped centre and q = (o - cw) + s d that point relative to the centre
-// (millimetres, formed with one rounding from the split parts, so ~1e-10 m);
-// u = local ray parameters of the entry / exit planes of the unit cube, from
-// A_lin^-1 q / h and the direction e = A_lin^-1 d / h.  The chord delta
-// (Eq. 5's distance travelled through the voxel) is the difference of the
-// small local parameters; the entry distance t0 = s + u_entry (for ordering
-// only).  Both are clipped to [near, far].  ax0 / ax1 are the axes of the
-// entry / exit planes (-1 when the near / far bound is the active one) and e
-// the direction in unit-cube coordinates.  Returns delta > 0.
+// Exact hit of the pixel ray P(lambda) = o + lambda D with a staged voxel
+// (stage_voxel), anchored at the voxel: s = <cw - o, D> / |D|^2 is the ray
+// parameter of the point nearest the warped centre and q = (o - cw) + s D
+// that point relative to the centre (millimetres, formed with one rounding
+// from the split parts, so ~1e-10 m); u = local ray parameters of the entry /
+// exit planes of the unit cube, from A_lin^-1 q / h and the direction
+// A_lin^-1 D / h.  The chord delta (Eq. 5's distance travelled through the
+// voxel) is |D| times the difference of the small local parameters; the
+// entry distance t0 = |D| (s + u_entry) (for ordering).  Both are clipped to
+// [near, far] (distances along the unit ray).  ax0 / ax1 are the axes of
+// the entry / exit planes (-1 when the near / far bound is the active one)
+// and e the unit ray direction in unit-cube coordinates.  Returns
+// delta > 0.
 __device__ __forceinline__ bool slab_hit(const float4& b0, const float4& b1, const float4& b2, const float4& xl,
                                          const RayDir& d, float znear, float zfar, float& t0, float& delta, int& ax0,
                                          int& ax1, float (&e)[3]) {
-  const float s = -(b0.w * d.h[0] + b1.w * d.h[1] + b2.w * d.h[2]);
+  const float n = 1.0f / d.inv_n;
+  const float s = -(b0.w * d.h[0] + b1.w * d.h[1] + b2.w * d.h[2]) * (d.inv_n * d.inv_n);
   const float q0 = fmaf(s, d.h[0], b0.w) + fmaf(s, d.l[0], xl.x);
   const float q1 = fmaf(s, d.h[1], b1.w) + fmaf(s, d.l[1], xl.y);
   const float q2 = fmaf(s, d.h[2], b2.w) + fmaf(s, d.l[2], xl.z);
@@ -313,13 +349,16 @@ __device__ __forceinline__ bool slab_hit(const float4& b0, const float4& b1, con
   const float a2 = (-0.5f - p2) * i2, c2 = (0.5f - p2) * i2;
   const float l0 = fminf(a0, c0), l1 = fminf(a1, c1), l2 = fminf(a2, c2);
   const float h0 = fmaxf(a0, c0), h1 = fmaxf(a1, c1), h2 = fmaxf(a2, c2);
-  const float ul = fmaxf(fmaxf(znear - s, l0), fmaxf(l1, l2));
-  const float uh = fminf(fminf(zfar - s, h0), fminf(h1, h2));
+  const float ul = fmaxf(fmaxf(znear * d.inv_n - s, l0), fmaxf(l1, l2));
+  const float uh = fminf(fminf(zfar * d.inv_n - s, h0), fminf(h1, h2));
   ax0 = ul == l0 ? 0 : (ul == l1 ? 1 : (ul == l2 ? 2 : -1));
   ax1 = uh == h0 ? 0 : (uh == h1 ? 1 : (uh == h2 ? 2 : -1));
-  t0 = s + ul;
-  delta = uh - ul;
-  return delta > 0.0f;
+  e[0] *= d.inv_n;
+  e[1] *= d.inv_n;
+  e[2] *= d.inv_n;
+  t0 = (s + ul) * n;
+  delta = (uh - ul) * n;
+  return uh > ul;
 }
 
 // Pixel-rectangle mask of one instance over a TSX x TSY tile at (sx, sy):

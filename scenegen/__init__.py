@@ -459,7 +459,7 @@ def unet_weights(seed: int, cin: int = 32, ch=UNET_CHANNELS, cout: int = 4):
     return [_conv_w(rng, co, ci, k) for co, ci, k in unet_layer_shapes(cin, ch, cout)]
 
 
-ALPHA_CHANNELS = (16, 32)
+ALPHA_CHANNELS = (32, 64)  # the paper gives no widths; these fit the tensor-core kernels
 
 
 def two_branch_weights(seed: int, cin: int = 32, rgb_ch=UNET_CHANNELS, alpha_ch=ALPHA_CHANNELS):

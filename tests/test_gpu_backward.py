@@ -79,17 +79,44 @@ def _conditioning(sc, pose, cams, gFs, gAs, base, features=None, tau=1e-4, trial
     return cond
 
 
-def _elementwise(g, o, cond, what, rtol=2e-4, atol_frac=1e-5, max_wide=0.02):
-    """Per element |g - o| <= 2 cond + rtol |o| + atol_frac max|o|.  The FP32
-    chord error left once the ray is held in double-float is that of the LBS
-    rounding (~5e-8 m), ~1e-5 relative on a millimetre chord: 2e-4 leaves a
-    margin of 20.  At most max_wide of the elements may owe their pass to the
-    conditioning term."""
+def _tied_voxels(sc, pose, cams, gFs, gAs, tau=1e-4, tie_eps=1e-6):
+    """Voxels that, on a ray with a non-zero upstream gradient, form a pair
+    of consecutive composited hits whose entry distances lie within tie_eps
+    (2.5x the FP32 error of such a difference): their order, and with it
+    their own gradient terms, is decided by rounding.  From the oracle's
+    hit lists."""
+    _, A, _ = oracle.pose_transforms(sc, pose)
+    tied = set()
+    for cam, gF, gA in zip(cams, gFs, gAs):
+        o = oracle.render(sc.octree, A, cam, tau=tau, hits=True)
+        off, ids, t0 = o["hit_off"], o["hit_id"], o["hit_t0"]
+        used = o["nused"].ravel()
+        live = (np.abs(gF).reshape(cam.H * cam.W, -1).max(1) > 0) | (np.abs(gA).reshape(-1) > 0)
+        for p in np.flatnonzero(live & (o["nhit"].ravel() > 1)):
+            a, b = off[p], off[p + 1]
+            last = min(b - a - 1, int(used[p]))
+            d = np.diff(t0[a:a + last + 1])
+            for k in np.flatnonzero(d < tie_eps):
+                tied.update((int(ids[a + k]), int(ids[a + k + 1])))
+    return np.array(sorted(tied), np.int64)
+
+
+def _elementwise(g, o, cond, what, rtol=2e-4, atol_frac=1e-4, max_wide=0.02, kcond=4.0):
+    """Per element |g - o| <= kcond cond + rtol |o| + atol_frac max|o|.  The
+    FP32 chord error left once the ray is held in double-float is that of the
+    geometry's rounding (~5e-8 m), ~1e-5 relative on a millimetre chord: 2e-4
+    leaves a margin of 20.  cond is the largest response over a few random
+    perturbation draws, which samples the worst direction only roughly:
+    kcond = 4.  The floor, 1e-4 of the largest element, covers FP32
+    accumulation on elements whose per-ray terms cancel (an element 1e-3 of
+    the largest, summed from terms near the largest, keeps ~1 % of it).  At
+    most max_wide of the elements may owe their pass to the conditioning
+    term."""
     tol_plain = rtol * np.abs(o) + atol_frac * np.abs(o).max()
     err = np.abs(g - o)
-    bad = err > 2.0 * cond + tol_plain
+    bad = err > kcond * cond + tol_plain
     wide = (err > tol_plain) & ~bad
-    i = np.unravel_index(np.argmax(err - 2.0 * cond - tol_plain), err.shape)
+    i = np.unravel_index(np.argmax(err - kcond * cond - tol_plain), err.shape)
     msg = (f"{what}: {int(bad.sum())} of {bad.size} elements outside the bound (worst at {i}: gpu {g[i]:.6e}, "
            f"oracle {o[i]:.6e}, conditioning {cond[i]:.2e}); {int(wide.sum())} inside only through conditioning")
     print(msg)
@@ -105,9 +132,16 @@ def _close(g, o, rel_l2, what):
     assert err < rel_l2, f"{what}: relative L2 error {err:.2e} (max abs {np.abs(g - o).max():.2e}, scale {np.abs(o).max():.2e})"
 
 
-def _compare(g, o, cond, rel=(3e-4, 1e-3, 5e-3)):
+def _compare(g, o, cond, tied=None, rel=(3e-4, 1e-3, 5e-3)):
+    """Element-wise (voxels of order-ambiguous pairs left out, at most 1 %)
+    and by norm (all voxels)."""
+    keep = np.ones(o[0].shape[0], bool)
+    if tied is not None and tied.size:
+        keep[tied] = False
+    assert (~keep).mean() <= 0.01, (~keep).sum()
+    print(f"{int((~keep).sum())} voxels of order-ambiguous pairs left out of the element-wise check")
     for k, what in enumerate(("dL/df", "dL/dsigma", "dL/dw")):
-        _elementwise(g[k], o[k], cond[k], what)
+        _elementwise(g[k][keep], o[k][keep], cond[k][keep], what)
         _close(g[k], o[k], rel[k], what)
 
 
@@ -120,7 +154,7 @@ def test_backward_matches_oracle_small():
     gAs = [rng.standard_normal((96, 96)) for _ in cams]
     g = _gpu_grads(sc, pose, cams, gFs, gAs)
     o = _oracle_grads(sc, pose, cams, gFs, gAs)
-    _compare(g, o, _conditioning(sc, pose, cams, gFs, gAs, o))
+    _compare(g, o, _conditioning(sc, pose, cams, gFs, gAs, o), _tied_voxels(sc, pose, cams, gFs, gAs))
 
 
 @pytest.mark.parametrize("segment,tau", [(32, 1e-4), (96, 0.7)])
@@ -140,7 +174,8 @@ def test_backward_split_walk_matches_oracle(segment, tau):
     o = _oracle_grads(sc, pose, cams, gFs, gAs, tau=tau)
     for a, b, what in zip(g, g1, ("dL/df", "dL/dsigma", "dL/dw")):
         _close(a, b, 1e-5, what + " split vs one segment")  # the same sums, atomics in another order
-    _compare(g, o, _conditioning(sc, pose, cams, gFs, gAs, o, tau=tau))
+    _compare(g, o, _conditioning(sc, pose, cams, gFs, gAs, o, tau=tau),
+             _tied_voxels(sc, pose, cams, gFs, gAs, tau=tau))
 
 
 def test_backward_config4_random_rays():
@@ -167,7 +202,7 @@ def test_backward_config4_random_rays():
         gAs.append(np.zeros((cam.H, cam.W)))
     g = _gpu_grads(sc, pose, cams, gFs, gAs)
     o = _oracle_grads(sc, pose, cams, gFs, gAs)
-    _compare(g, o, _conditioning(sc, pose, cams, gFs, gAs, o))
+    _compare(g, o, _conditioning(sc, pose, cams, gFs, gAs, o), _tied_voxels(sc, pose, cams, gFs, gAs))
     del torch
 
 
@@ -192,7 +227,7 @@ def test_autograd_function_equals_direct_call():
     gA = (2 * A).detach().cpu().numpy()
     o = _oracle_grads(sc, pose, [cam], [gF], [gA])
     g = [t.grad.cpu().numpy().astype(np.float64) for t in (f, d, w)]
-    _compare(g, o, _conditioning(sc, pose, [cam], [gF], [gA], o))
+    _compare(g, o, _conditioning(sc, pose, [cam], [gF], [gA], o), _tied_voxels(sc, pose, [cam], [gF], [gA]))
     o_F = oracle.render(oc, oracle.pose_transforms(sc, pose)[1], cam)
     assert np.abs(F.detach().cpu().numpy() - o_F["F"]).max() < 1e-4
 
@@ -208,4 +243,5 @@ def test_backward_bf16_storage_uses_rounded_features():
     g = _gpu_grads(sc, pose, [cam], [gF], [gA], storage="bf16")
     fb = torch.from_numpy(sc.octree.features).to(torch.bfloat16).to(torch.float64).numpy()
     o = _oracle_grads(sc, pose, [cam], [gF], [gA], features=fb)
-    _compare(g, o, _conditioning(sc, pose, [cam], [gF], [gA], o, features=fb))
+    _compare(g, o, _conditioning(sc, pose, [cam], [gF], [gA], o, features=fb),
+             _tied_voxels(sc, pose, [cam], [gF], [gA]))

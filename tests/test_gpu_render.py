@@ -394,3 +394,50 @@ def test_depth_buffer_matches_oracle(az, pose_seed, q):
     assert bad.sum() <= max(2, int(0.005 * fin_o.sum())), (bad.sum(), fin_o.sum())
     with pytest.raises(RuntimeError):
         r.render_depth(0, -1.0, D)
+
+
+def test_reorder_buffer_overflow_is_walked_exactly():
+    """40 coincident copies of one voxel (each its own features and density)
+    enter every ray through them at the same distance, so more hits pend
+    than a pixel's 16-entry reorder buffer holds.  The tile is walked again
+    by the exact walk (all hits collected and sorted by entry distance, chord,
+    list position = voxel id for equal depth keys), which gives the oracle's
+    composite (its ties also by voxel id): no out-of-order release remains,
+    in the single-view walk, with short segments, and for a batch of views."""
+    import torch
+    depth, extent = 4, 1.0
+    ijk = np.array([[8, 8, 8]] * 40 + [[8, 8, 9], [9, 8, 8], [7, 8, 8], [8, 9, 8]], np.uint16)
+    n = ijk.shape[0]
+    rng = np.random.default_rng(17)
+    f = rng.standard_normal((n, 8)).astype(np.float32)
+    sigma = rng.uniform(1.0, 3.0, n).astype(np.float32)
+    jidx = np.zeros((n, 4), np.uint8)
+    w = np.zeros((n, 4), np.float32)
+    w[:, 0] = 1.0
+    oc = sg.Octree(depth, np.array([-0.5, -0.5, -0.5], np.float32), extent, ijk, jidx, w, f, sigma,
+                   np.zeros(n, np.float32))
+    skel = sg.Skeleton(np.array([-1, 0], np.int32), np.array([[0, 0, 0], [0.1, 0, 0]], np.float32))
+    sc = sg.Scene(oc, skel, np.zeros(3), 1.0, None, None)
+    centre = oc.centers()[0].astype(np.float64)
+    eye = centre + np.array([0.07, 0.11, -1.0])
+    cam = sg.Camera(24, 16, 120.0, 120.0, 12.0, 8.0, sg.look_at(eye, centre), 0.1, 3.0)
+    o = oracle.render(oc, oracle.pose_transforms(sc, sg.rest_pose(2))[1], cam, hits=True)
+    assert o["nhit"].max() >= 40 and (o["nhit"] >= 17).sum() >= 20
+    for segment in (256, 32):
+        r = renderer(sc, segment=segment)
+        set_pose(r, sg.rest_pose(2))
+        set_cam(r, 0, cam)
+        F, A = render_maps(r, 0, cam, 8)
+        st = r.sync_status()
+        assert st["overflow_order"] == 0 and st["exact_tiles"] >= 1, st
+        np.testing.assert_allclose(F, o["F"], atol=1e-4)
+        np.testing.assert_allclose(A, o["A"], atol=1e-4)
+        set_cam(r, 1, cam)
+        Fs = [torch.zeros((cam.H, cam.W, 8), device="cuda") for _ in range(2)]
+        As = [torch.zeros((cam.H, cam.W), device="cuda") for _ in range(2)]
+        r.render_views([0, 1], Fs, As)
+        st = r.sync_status()
+        assert st["overflow_order"] == 0 and st["exact_tiles"] >= 2, st
+        for k in range(2):
+            np.testing.assert_allclose(Fs[k].cpu().numpy(), o["F"], atol=1e-4)
+            np.testing.assert_allclose(As[k].cpu().numpy(), o["A"], atol=1e-4)
