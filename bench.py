@@ -500,6 +500,62 @@ def walk_quality(sc, cams, poses, layers, prop, psnr_frames=(20, 40), n_cov=48, 
             "what": "per walk-cycle frame (pose f, azimuth of step f) against the FP64 oracle"}
 
 
+def grid_timing(sc, cams, poses, flush, steps, warmup=3):
+    """The paper's per-frame index (art_config.index = ART_INDEX_GRID: warped
+    centres snapped to the leaf lattice, the smallest id surviving a cell,
+    the occupied cells rendered as leaf boxes) against the exact warped
+    boxes, BF16 features: time per frame of pose + F/A maps (CUDA events,
+    L2 flushed between frames), the share of placed voxels lost to
+    collisions, and the PSNR of the index's feature map against the exact
+    boxes' (scaled to the boxes' feature range) on the walk-cycle frames."""
+    import torch
+    oc = sc.octree
+    out = {}
+    Fs = {}
+    for name, index in (("boxes", 0), ("grid", 1)):
+        r = setup_renderer(sc, cams, None, "bf16")
+        r.set_config(tau=1e-4, skip=0, segment=SEGMENT, index=index)
+        F = torch.empty((RES, RES, oc.C), dtype=torch.bfloat16, device="cuda")
+        A = torch.empty((RES, RES), dtype=torch.float32, device="cuda")
+        stream = torch.cuda.current_stream()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for k in range(warmup + steps):
+            pi, vi = step_indices(k)
+            p = poses[pi]
+            flush.zero_()
+            if k >= warmup:
+                ev[k - warmup][0].record(stream)
+            r.set_pose(p.axis_angle, p.R, p.T)
+            r.render_feature_maps(vi, F, A, "bf16")
+            if k >= warmup:
+                ev[k - warmup][1].record(stream)
+        torch.cuda.synchronize()
+        ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+        st = r.sync_status()
+        cells, placed = st["grid_cells"], oc.n - st["degenerate"]
+        psnr = []
+        for k in range(0, steps, max(1, steps // 4)):
+            pi, vi = step_indices(warmup + k)
+            p = poses[pi]
+            r.set_pose(p.axis_angle, p.R, p.T)
+            r.render_feature_maps(vi, F, A, "bf16")
+            torch.cuda.synchronize()
+            Fs.setdefault(name, []).append(F.float().cpu().numpy())
+        r.close()
+        out[name] = {"ms_per_frame": ms, "frames_per_s": 1e3 / ms}
+        if index == 1:
+            out[name]["occupied_cells_last_frame"] = int(cells)
+            out[name]["collided_share_last_frame"] = 1.0 - cells / max(placed, 1)
+    for a, b in zip(Fs["boxes"], Fs["grid"]):
+        rng_ = float(np.abs(a).max())
+        mse = float(np.mean((a - b) ** 2)) / max(rng_ * rng_, 1e-30)
+        psnr.append(10.0 * np.log10(1.0 / max(mse, 1e-30)))
+    out["feature_psnr_db_vs_boxes"] = psnr
+    out["what"] = ("pose + F/A maps of one 1024^2 view per frame (BF16 features), plain traversal; "
+                   "PSNR of F against the exact boxes' F, peak = the boxes' max |F|")
+    return out
+
+
 def gpu_arm(args):
     import torch
     import torch.distributed as dist
@@ -642,6 +698,7 @@ def gpu_arm(args):
                 result[form + "_form"] = side(form, args.side_steps)
         result["backward"] = backward_timing(sc, cams, poses, layers, args.side_steps, flush)
         result["two_branch"] = two_branch_timing(sc, cams, poses, flush)
+        result["grid_index"] = grid_timing(sc, cams, poses, flush, args.side_steps)
         result["stereo_1080p"] = stereo_timing(sc, poses, layers, prop, flush, max(4, args.side_steps // 2),
                                                oracle_psnr=(rank == 0 and world == 1 and not args.no_cpu_baseline))
     # end to end through the public call with host buffers

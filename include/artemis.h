@@ -352,7 +352,15 @@ typedef struct {
   int margin;              /* learned skip: bins added on both sides of the predicted interval (default 0) */
   int segment;             /* composite: a tile's list is walked in segments of about this many entries by
                               separate warps and merged front to back (0 = default 256; >= 32) */
+  int index;               /* ART_INDEX_BOXES (default): every warped voxel is its exact parallelepiped;
+                              ART_INDEX_GRID: the paper's per-frame index (Sec. 3.1 "Dynamic Volume
+                              Rendering"): each warped centre is snapped to the cell of the leaf lattice
+                              (canonical origin, leaf size h) that holds it, the smallest voxel id of a
+                              cell survives, and each occupied cell renders as its axis-aligned leaf box
+                              with its survivor's feature and density (forward only; no SH features) */
 } art_config;
+
+enum { ART_INDEX_BOXES = 0, ART_INDEX_GRID = 1 };
 
 #define ART_SKIP_PLAIN 0
 #define ART_SKIP_LEARNED 1
@@ -370,6 +378,7 @@ typedef struct {
   int64_t fallback_tiles;  /* learned skip: tiles of the last render traversed again in full */
   int64_t exact_tiles;     /* tiles of the last render walked again exactly because a pixel
                               had more pending hits than its 16-entry reorder buffer holds */
+  int64_t grid_cells;      /* ART_INDEX_GRID: occupied lattice cells of the last pose (the survivors) */
 } art_stats;
 
 /* Synchronise the stream, fill *out (may be NULL) and return

@@ -22,6 +22,7 @@ ART_NET_TINY, ART_NET_UNET, ART_NET_TWO_BRANCH = 0, 1, 2
 (BUF_JOINT_G, BUF_VOXEL_REC, BUF_VOXEL_GEO, BUF_RECT, BUF_DEPTHKEY, BUF_KEYS, BUF_VALS, BUF_RANGES, BUF_FP8_SCALES,
  BUF_ACTIVATIONS, BUF_BINS, BUF_FALLBACK, BUF_TAU_HIST) = range(13)
 SKIP_PLAIN, SKIP_LEARNED = 0, 1
+INDEX_BOXES, INDEX_GRID = 0, 1
 PROPOSAL_PARAMS = 27712  # 64*107+64 + 3*(64*64+64) + 128*64+128
 _STATUS = {0: "ART_OK", 1: "ART_ERR_INVALID_ARG", 2: "ART_ERR_CUDA", 3: "ART_ERR_OOM", 4: "ART_ERR_OVERFLOW",
            5: "ART_ERR_STATE", 6: "ART_ERR_UNSUPPORTED"}
@@ -42,13 +43,13 @@ class NetDesc(ctypes.Structure):
 class Config(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_float), ("instance_cap", ctypes.c_int64), ("tile_log2", ctypes.c_int),
                 ("profile", ctypes.c_int), ("skip", ctypes.c_int), ("max_missed", ctypes.c_float),
-                ("margin", ctypes.c_int), ("segment", ctypes.c_int)]
+                ("margin", ctypes.c_int), ("segment", ctypes.c_int), ("index", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [("instances", ctypes.c_int64), ("degenerate", ctypes.c_int64), ("overflow_inst", ctypes.c_int64),
                 ("overflow_order", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
-                ("fallback_tiles", ctypes.c_int64), ("exact_tiles", ctypes.c_int64)]
+                ("fallback_tiles", ctypes.c_int64), ("exact_tiles", ctypes.c_int64), ("grid_cells", ctypes.c_int64)]
 
 
 def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -150,9 +151,10 @@ class Renderer:
 
     # ----------------------------------------------------------------- setup
     def set_config(self, tau: float = 1e-4, instance_cap: int = 0, tile_log2: int = 3, profile: bool = False,
-                   skip: int = SKIP_PLAIN, max_missed: float = 1e-3, margin: int = 0, segment: int = 256):
+                   skip: int = SKIP_PLAIN, max_missed: float = 1e-3, margin: int = 0, segment: int = 256,
+                   index: int = 0):
         c = Config(tau, instance_cap, tile_log2, int(profile), int(skip), float(max_missed), int(margin),
-                   int(segment))
+                   int(segment), int(index))
         self._check(_lib.art_set_config(self._h, ctypes.byref(c)))
 
     def load_octree(self, depth: int, origin, extent: float, ijk, joint_idx, weights, features, density,
@@ -256,7 +258,7 @@ class Renderer:
             self._check(st)
         return dict(instances=s.instances, degenerate=s.degenerate, overflow_inst=s.overflow_inst,
                     overflow_order=s.overflow_order, kernel_launches=s.kernel_launches,
-                    fallback_tiles=s.fallback_tiles, exact_tiles=s.exact_tiles, status=st)
+                    fallback_tiles=s.fallback_tiles, exact_tiles=s.exact_tiles, grid_cells=s.grid_cells, status=st)
 
     def kernel_times(self, reset: bool = False) -> dict:
         cap = 64

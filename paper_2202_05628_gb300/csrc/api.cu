@@ -185,7 +185,8 @@ void free_all(art_ctx* ctx) {
                   ctx->d_prop_f32, ctx->d_pose_bias, ctx->d_bins, ctx->d_thist, ctx->d_hbin, ctx->d_htau, ctx->d_fbq,
                   ctx->d_seg, ctx->d_items, ctx->d_multi, ctx->d_part, ctx->d_fbq2, ctx->d_tcount, ctx->d_toff,
                   ctx->d_sortlist, ctx->d_scan_state, ctx->d_agroups, ctx->d_sh, ctx->d_sh_rot, ctx->d_rect_v,
-                  ctx->d_q_v, ctx->d_cnt_v, ctx->d_vset, ctx->d_xflag, ctx->d_xqueue, ctx->d_xhit, ctx->d_xpos};
+                  ctx->d_q_v, ctx->d_cnt_v, ctx->d_vset, ctx->d_xflag, ctx->d_xqueue, ctx->d_xhit, ctx->d_xpos,
+                  ctx->d_gkeys, ctx->d_gvals};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& L : ctx->layers) {
@@ -213,6 +214,7 @@ art_config default_config() {
   c.max_missed = 1e-3f;
   c.margin = 0;
   c.segment = 256;
+  c.index = ART_INDEX_BOXES;
   return c;
 }
 
@@ -352,6 +354,8 @@ art_status art_set_config(art_ctx* ctx, const art_config* cfg) {
   if (c.margin < 0 || c.margin > 63) return fail(ctx, ART_ERR_INVALID_ARG, "margin must be in [0, 63]");
   if (c.segment == 0) c.segment = 256;
   if (c.segment < 32 || c.segment > (1 << 24)) return fail(ctx, ART_ERR_INVALID_ARG, "segment must be in [32, 2^24]");
+  if (c.index != ART_INDEX_BOXES && c.index != ART_INDEX_GRID) return fail(ctx, ART_ERR_INVALID_ARG, "index %d", c.index);
+  if (c.index != ctx->cfg.index) ctx->posed = false;  // the records of the last pose follow the other index
   ctx->cfg = c;
   ctx->seg_len = c.segment;
   return ART_OK;
@@ -484,6 +488,16 @@ art_status art_set_pose(art_ctx* ctx, const float* axis_angle, const float R[3],
   cudaMemsetAsync(ctx->d_status + kStRmax, 0, sizeof(unsigned long long), ctx->stream);
   launch_fk(ctx);
   launch_lbs(ctx);
+  if (ctx->cfg.index == ART_INDEX_GRID) {
+    if (ctx->grid_slots < 2 * ctx->n) {
+      int64_t slots = 1024;
+      while (slots < 2 * ctx->n) slots <<= 1;
+      if ((st = alloc(ctx, &ctx->d_gkeys, (size_t)slots, "lattice index keys")) != ART_OK) return st;
+      if ((st = alloc(ctx, &ctx->d_gvals, (size_t)slots, "lattice index voxels")) != ART_OK) return st;
+      ctx->grid_slots = slots;
+    }
+    launch_grid_snap(ctx);
+  }
   if (ctx->prop_loaded) launch_pose_bias(ctx);
   if ((st = launch_check(ctx, "set_pose")) != ART_OK) return st;
   ctx->posed = true;
@@ -596,6 +610,8 @@ static art_status render_to_device(art_ctx* ctx, int view, void* F, int F_dtype,
   }
   launch_project(ctx, v);
   launch_bin(ctx, v);
+  if (ctx->sh_degree >= 0 && ctx->cfg.index == ART_INDEX_GRID)
+    return fail(ctx, ART_ERR_UNSUPPORTED, "view-dependent (SH) features need the exact boxes (index 0)");
   if (ctx->sh_degree >= 0) {  // view-dependent features (Eq. 2)
     if ((st = launch_composite_sh(ctx, v, F, F_dtype, A)) != ART_OK) return st;
     return launch_check(ctx, "render_feature_maps (SH)");
@@ -932,6 +948,7 @@ art_status art_sync_status(art_ctx* ctx, art_stats* out) {
     out->kernel_launches = ctx->launches;
     out->fallback_tiles = (int64_t)h[kStFallback];
     out->exact_tiles = (int64_t)h[kStExactQ];
+    out->grid_cells = ctx->cfg.index == ART_INDEX_GRID ? (int64_t)h[kStGridCells] : 0;
   }
   if (h[kStTcError]) {
     art_status r = fail(ctx, ART_ERR_CUDA, "tensor-core convolution: %llu CTAs timed out waiting on their pipeline",
@@ -1036,6 +1053,7 @@ art_status art_render_backward(art_ctx* ctx, int view, const float* F, const flo
   if (view < 0 || view >= kMaxViews || !ctx->view_set[view]) return fail(ctx, ART_ERR_STATE, "view %d not set", view);
   if (!ctx->posed) return fail(ctx, ART_ERR_STATE, "render_backward before set_pose");
   if (ctx->sh_degree >= 0) return fail(ctx, ART_ERR_UNSUPPORTED, "render_backward: view-dependent (SH) features");
+  if (ctx->cfg.index == ART_INDEX_GRID) return fail(ctx, ART_ERR_UNSUPPORTED, "render_backward: the lattice index");
   if (!F || !A || !dF || !d_features || !d_density || !d_weights)
     return fail(ctx, ART_ERR_INVALID_ARG, "null pointer");
   const void* dev[] = {F, A, dF, d_features, d_density, d_weights};

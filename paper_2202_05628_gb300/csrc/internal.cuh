@@ -43,7 +43,8 @@ enum StatusWord {
   kStScanError = 19,    // binning: tile-scan blocks that timed out waiting for a predecessor
   kStActiveGroups = 20, // binning: groups of four consecutive tiles with instances (listed in d_agroups)
   kStExactQ = 21,       // composite: tiles queued for the exact re-walk (a pixel's reorder buffer overflowed)
-  kStWords = 22
+  kStGridCells = 22,    // lattice index: occupied cells of the last pose
+  kStWords = 23
 };
 
 // Per-view camera, with host-precomputed ray frame.
@@ -209,6 +210,10 @@ struct art_ctx {
   int64_t views_cap = 0;          // (views x n) capacity of the three
   art::ViewSet* d_vset = nullptr; // the batch's view table (device)
   art::ViewSet h_vset{};          // ... and its host copy
+  // ---- the paper's per-frame lattice index (art_config.index = ART_INDEX_GRID)
+  unsigned long long* d_gkeys = nullptr;  // [slots] packed cell of each hash slot (all ones: empty)
+  uint32_t* d_gvals = nullptr;            // [slots] smallest voxel id of the slot's cell
+  int64_t grid_slots = 0;                 // power of two >= 2 n
   // ---- exact re-walk of tiles whose reorder buffer overflowed
   uint32_t* d_xflag = nullptr;    // [tiles] queued already (zeroed per render)
   uint32_t* d_xqueue = nullptr;   // [tiles] the queue (count in status[kStExactQ])
@@ -259,6 +264,11 @@ void prof_end(art_ctx* ctx);
 // ---- kernels: LBS (lbs.cu)
 void launch_fk(art_ctx* ctx);
 void launch_lbs(art_ctx* ctx);
+// The paper's per-frame index after LBS: snap each placed voxel's warped
+// centre to the leaf lattice (hash table of cells, the smallest id wins a
+// cell) and rewrite the records so that survivors are their cells'
+// axis-aligned leaf boxes and the others are dropped.
+void launch_grid_snap(art_ctx* ctx);
 // With hbin / htau set, also the per-voxel depth-bin range and optical-depth
 // bound of the coarse check (64 bins over [znear, zfar]).  Also counts each
 // tile's instances and resets the tile scan: launch_bin follows it.

@@ -344,6 +344,126 @@ __global__ void __launch_bounds__(256) project_kernel(int64_t n, const float4* _
 
 }  // namespace
 
+// ---------------------------------------------------- the lattice index
+//
+// The paper rebuilds an index over the warped voxels every frame (Sec. 3.1
+// "Dynamic Volume Rendering") and lets voxels that land on one grid location
+// collide.  Here the grid is the lattice of the canonical octree's leaves
+// (origin, leaf size h): voxel i goes to the cell floor((cw_i - origin) / h)
+// of its warped centre, the cells of a pose are keys of an open-addressing
+// hash table (linear probing, load <= 1/2) holding the smallest voxel id
+// that landed there, and that voxel survives.  Cells more than 2^20 from the
+// origin along an axis are not placed.
+
+constexpr unsigned long long kGridEmpty = ~0ull;
+constexpr int kGridBits = 21;  // per axis, two's complement
+
+__device__ __forceinline__ bool grid_cell(const float4& r0, const float4& r1, const float4& r2, float ox, float oy,
+                                          float oz, float inv_h, unsigned long long& key) {
+  const float c[3] = {floorf((r0.w - ox) * inv_h), floorf((r1.w - oy) * inv_h), floorf((r2.w - oz) * inv_h)};
+  key = 0ull;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (!(fabsf(c[a]) < (float)(1 << (kGridBits - 1)))) return false;
+    key |= ((unsigned long long)((int)c[a]) & ((1ull << kGridBits) - 1ull)) << (kGridBits * a);
+  }
+  return true;
+}
+
+__device__ __forceinline__ uint64_t grid_hash(unsigned long long key) {
+  key ^= key >> 33;
+  key *= 0xff51afd7ed558ccdull;
+  key ^= key >> 33;
+  key *= 0xc4ceb9fe1a85ec53ull;
+  key ^= key >> 33;
+  return key;
+}
+
+// Probe for the cell's slot; insert the key when it is absent.  Returns the
+// slot, or -1 when the table is full (never with load <= 1/2).
+__device__ __forceinline__ int64_t grid_slot(unsigned long long* keys, int64_t mask, unsigned long long key,
+                                             bool insert) {
+  int64_t s = (int64_t)(grid_hash(key) & (uint64_t)mask);
+  for (int64_t probe = 0; probe <= mask; ++probe) {
+    unsigned long long k = keys[s];
+    if (k == key) return s;
+    if (k == kGridEmpty) {
+      if (!insert) return -1;
+      k = atomicCAS(keys + s, kGridEmpty, key);
+      if (k == kGridEmpty || k == key) return s;
+    }
+    s = (s + 1) & mask;
+  }
+  return -1;
+}
+
+__global__ void __launch_bounds__(256) grid_insert_kernel(int64_t n, const float4* __restrict__ rec, float ox, float oy,
+                                                         float oz, float inv_h, unsigned long long* __restrict__ keys,
+                                                         uint32_t* __restrict__ vals, int64_t mask) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float4* r = rec + 4 * i;
+  if (r[3].y == 0.0f) return;  // dropped (degenerate blend)
+  unsigned long long key;
+  if (!grid_cell(r[0], r[1], r[2], ox, oy, oz, inv_h, key)) return;
+  const int64_t s = grid_slot(keys, mask, key, true);
+  if (s >= 0) atomicMin(vals + s, (uint32_t)i);
+}
+
+// Survivors become their cell's axis-aligned leaf box (unit-cube map I / h,
+// centre origin + (cell + 1/2) h, bounding radius sqrt(3) h / 2, half axes
+// h / 2 along x, y, z); every other voxel is dropped like a degenerate one.
+__global__ void __launch_bounds__(256) grid_rewrite_kernel(int64_t n, float4* __restrict__ rec, float4* __restrict__ geo,
+                                                          float ox, float oy, float oz, float h,
+                                                          const unsigned long long* __restrict__ keys,
+                                                          const uint32_t* __restrict__ vals, int64_t mask,
+                                                          unsigned long long* __restrict__ status) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool survive = false;
+  if (i < n) {
+    float4* r = rec + 4 * i;
+    float4* g = geo + 4 * i;
+    const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3];
+    unsigned long long key;
+    int64_t s = -1;
+    if (r3.y != 0.0f && grid_cell(r0, r1, r2, ox, oy, oz, 1.0f / h, key))
+      s = grid_slot(const_cast<unsigned long long*>(keys), mask, key, false);
+    survive = s >= 0 && vals[s] == (uint32_t)i;
+    if (survive) {
+      const float ih = 1.0f / h, hh = 0.5f * h;
+      const float cx = ox + (floorf((r0.w - ox) * ih) + 0.5f) * h;
+      const float cy = oy + (floorf((r1.w - oy) * ih) + 0.5f) * h;
+      const float cz = oz + (floorf((r2.w - oz) * ih) + 0.5f) * h;
+      r[0] = make_float4(ih, 0.0f, 0.0f, cx);
+      r[1] = make_float4(0.0f, ih, 0.0f, cy);
+      r[2] = make_float4(0.0f, 0.0f, ih, cz);
+      g[0] = make_float4(cx, cy, cz, 0.8660254f * h * (1.0f + 1e-6f) + 1e-9f);
+      g[1] = make_float4(hh, 0.0f, 0.0f, 0.0f);
+      g[2] = make_float4(0.0f, hh, 0.0f, 0.0f);
+      g[3] = make_float4(0.0f, 0.0f, hh, 0.0f);
+    } else if (r3.y != 0.0f) {
+      r[0] = r[1] = r[2] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      r[3] = make_float4(r3.x, 0.0f, 0.0f, 0.0f);
+      g[0] = make_float4(g[0].x, g[0].y, g[0].z, -1.0f);
+    }
+  }
+  const unsigned cnt = __popc(__ballot_sync(0xffffffffu, survive));
+  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(status + kStGridCells, (unsigned long long)cnt);
+}
+
+void launch_grid_snap(art_ctx* ctx) {
+  const int64_t n = ctx->n;
+  const unsigned grid = (unsigned)((n + 255) / 256);
+  const int64_t mask = ctx->grid_slots - 1;
+  cudaMemsetAsync(ctx->d_gkeys, 0xFF, sizeof(unsigned long long) * (size_t)ctx->grid_slots, ctx->stream);
+  cudaMemsetAsync(ctx->d_gvals, 0xFF, sizeof(uint32_t) * (size_t)ctx->grid_slots, ctx->stream);
+  cudaMemsetAsync(ctx->d_status + kStGridCells, 0, sizeof(unsigned long long), ctx->stream);
+  ART_LAUNCH(ctx, "grid_insert", grid_insert_kernel, grid, 256, 0, n, ctx->d_rec, ctx->origin[0], ctx->origin[1],
+             ctx->origin[2], 1.0f / ctx->h, ctx->d_gkeys, ctx->d_gvals, mask);
+  ART_LAUNCH(ctx, "grid_rewrite", grid_rewrite_kernel, grid, 256, 0, n, ctx->d_rec, ctx->d_geo, ctx->origin[0],
+             ctx->origin[1], ctx->origin[2], ctx->h, ctx->d_gkeys, ctx->d_gvals, mask, ctx->d_status);
+}
+
 void launch_fk(art_ctx* ctx) { ART_LAUNCH(ctx, "fk", fk_kernel, 1, kMaxJoints, 0, ctx->J, ctx->d_skel, ctx->d_pose, ctx->d_G); }
 
 void launch_lbs(art_ctx* ctx) {
