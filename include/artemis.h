@@ -379,6 +379,8 @@ typedef struct {
   int64_t exact_tiles;     /* tiles of the last render walked again exactly because a pixel
                               had more pending hits than its 16-entry reorder buffer holds */
   int64_t grid_cells;      /* ART_INDEX_GRID: occupied lattice cells of the last pose (the survivors) */
+  int64_t forced_tiles;    /* learned skip: tiles of the last render whose coarse bound alone fixes the
+                              walk (the whole range, or nothing), rendered without a prediction */
 } art_stats;
 
 /* Synchronise the stream, fill *out (may be NULL) and return

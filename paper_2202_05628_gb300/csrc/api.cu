@@ -186,7 +186,7 @@ void free_all(art_ctx* ctx) {
                   ctx->d_seg, ctx->d_items, ctx->d_multi, ctx->d_part, ctx->d_fbq2, ctx->d_tcount, ctx->d_toff,
                   ctx->d_sortlist, ctx->d_scan_state, ctx->d_agroups, ctx->d_sh, ctx->d_sh_rot, ctx->d_rect_v,
                   ctx->d_q_v, ctx->d_cnt_v, ctx->d_vset, ctx->d_xflag, ctx->d_xqueue, ctx->d_xhit, ctx->d_xpos,
-                  ctx->d_gkeys, ctx->d_gvals};
+                  ctx->d_gkeys, ctx->d_gvals, ctx->d_pgroups, ctx->d_tclass};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& L : ctx->layers) {
@@ -237,6 +237,8 @@ art_status ensure_bin_buffers(art_ctx* ctx, int64_t ntiles) {
     if ((st = alloc(ctx, &ctx->d_sortlist, (size_t)ntiles, "tile sort list")) != ART_OK) return st;
     if ((st = alloc(ctx, &ctx->d_scan_state, tile_scan_state_words(ntiles), "tile scan state")) != ART_OK) return st;
     if ((st = alloc(ctx, &ctx->d_agroups, (size_t)(ntiles + 3) / 4, "active tile groups")) != ART_OK) return st;
+    if ((st = alloc(ctx, &ctx->d_pgroups, (size_t)(ntiles + 3) / 4, "predicted tile groups")) != ART_OK) return st;
+    if ((st = alloc(ctx, &ctx->d_tclass, (size_t)ntiles, "tile classes")) != ART_OK) return st;
     ctx->ranges_cap = ntiles;
   }
   return ART_OK;
@@ -604,7 +606,8 @@ static art_status render_to_device(art_ctx* ctx, int view, void* F, int F_dtype,
     if ((st = ensure_skip_buffers(ctx, v)) != ART_OK) return st;
     launch_project(ctx, v, ctx->d_hbin, ctx->d_htau);
     launch_bin(ctx, v, ctx->d_hbin, ctx->d_htau, ctx->d_thist);
-    if ((st = launch_proposal(ctx, v, ctx->d_bins, nullptr, true)) != ART_OK) return st;
+    launch_tile_class(ctx, v, ctx->d_bins);
+    if ((st = launch_proposal(ctx, v, ctx->d_bins, nullptr, true, true)) != ART_OK) return st;
     if ((st = launch_composite_skip(ctx, v, F, F_dtype, A)) != ART_OK) return st;
     return launch_check(ctx, "render_feature_maps");
   }
@@ -949,6 +952,7 @@ art_status art_sync_status(art_ctx* ctx, art_stats* out) {
     out->fallback_tiles = (int64_t)h[kStFallback];
     out->exact_tiles = (int64_t)h[kStExactQ];
     out->grid_cells = ctx->cfg.index == ART_INDEX_GRID ? (int64_t)h[kStGridCells] : 0;
+    out->forced_tiles = (int64_t)h[kStForcedTiles];
   }
   if (h[kStTcError]) {
     art_status r = fail(ctx, ART_ERR_CUDA, "tensor-core convolution: %llu CTAs timed out waiting on their pipeline",

@@ -363,9 +363,9 @@ constexpr int kRows = 4;
 // the unit: 3 inside, 2 or 1 at the unit's edge rows) columns, accumulates into
 // every row it touches.  Every MMA accumulates; the epilogue zeroes each
 // slot after reading it.
-template <int N, int KCB>
+template <int N, int KCB, bool F8 = false>
 struct RowCfg {
-  static constexpr int KC = KCB / 2;  // channels per chunk
+  static constexpr int KC = F8 ? KCB : KCB / 2;  // channels per chunk (KCB bytes)
   static constexpr int kSlots = kRows;
   static constexpr int kBufCols = kSlots * N;  // columns of one accumulator buffer
   static constexpr int kHalo = 130;                                   // input pixels of a row box (128 + 2)
@@ -382,10 +382,10 @@ struct RowParams {
   int nbuf;       // accumulator buffers (2, or 1 when two CTAs share an SM's TMEM)
 };
 
-template <int N, int KCB>
+template <int N, int KCB, bool F8>
 __global__ void __launch_bounds__(kThreads, 1)
     conv_rows_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, RowParams rp) {
-  using Cfg = RowCfg<N, KCB>;
+  using Cfg = RowCfg<N, KCB, F8>;
   const TcParams& p = rp.p;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -402,6 +402,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   float* s_bias = reinterpret_cast<float*>(tmem_slot + 4);
   float* s_head = s_bias + N;
+  float* s_wsc = s_head + 4 * 32 + 4;  // FP8 per-output-channel weight scales
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int cpt = rp.cpt;
@@ -430,6 +431,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (p.rgba)
     for (int i = threadIdx.x; i < 4 * N + 4; i += kThreads)  // rows beyond head_n are zero
       s_head[i] = i < 4 * N ? (i < p.head_n * N ? p.head_w[i] : 0.0f) : (i - 4 * N < p.head_n ? p.head_b[i - 4 * N] : 0.0f);
+  if (F8)
+    for (int i = threadIdx.x; i < N; i += kThreads) s_wsc[i] = i < p.cout ? p.w_scale[i] : 0.0f;
   const int nbuf = rp.nbuf;
   const uint32_t tmem_cols = (uint32_t)(nbuf * Cfg::kBufCols);
   if (warp == 1) tmem_alloc(tmem_slot, tmem_cols);
@@ -489,13 +492,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           // (slots R - 1 - j + lo ..., consecutive like the stacked taps' weight blocks)
           const int lo = max(0, j - kRows + 1), hi = min(2, j);
           const uint32_t dj = d0 + (uint32_t)((kRows - 1 - j + lo) * N);
-          const uint32_t idesc = idesc_bf16(128, (hi - lo + 1) * N);
+          const uint32_t idesc = F8 ? idesc_e4m3(128, (hi - lo + 1) * N) : idesc_bf16(128, (hi - lo + 1) * N);
 #pragma unroll
           for (int dxi = 0; dxi < 3; ++dxi) {
             const uint32_t bw = wbase + (uint32_t)((wblk(0, dxi, c) + lo) * N * KCB);
 #pragma unroll
             for (int kk = 0; kk < KCB / 32; ++kk)
-              umma<false>(dj, umma_desc<KCB>(a0 + dxi * KCB + kk * 32), umma_desc<KCB>(bw + kk * 32), idesc, 1u);
+              umma<F8>(dj, umma_desc<KCB>(a0 + dxi * KCB + kk * 32), umma_desc<KCB>(bw + kk * 32), idesc, 1u);
           }
           umma_commit(&empty[s]);
           if (++s == S) {
@@ -517,6 +520,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int qd = warp & 3;
     const int m = qd * 32 + lane;
     const uint32_t tq = tmem_base + ((uint32_t)(qd * 32) << 16);  // this warp's lane quarter
+    const float in_s = F8 ? *p.in_scale : 1.0f;
+    const float out_inv = (F8 && p.out) ? 1.0f / *p.out_scale : 1.0f;
     uint32_t keep[N / 2];  // fused pooling: the first row of the pair, packed BF16
     int buf = 0;
     uint32_t aph = 0;
@@ -534,10 +539,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int slot = kRows - 1 - r;
         const uint32_t ta = tq + (uint32_t)(buf * Cfg::kBufCols + slot * N);
         if (y0 + r < p.H) {
-          if (p.pool)
+          if (!F8 && p.pool)
             epi_row_pool<N>(p, ta, y0 + r, x, s_bias, keep, (r & 1) != 0);
           else
-            epi_row<N, false>(p, ta, y0 + r, x, s_bias, s_head, nullptr, 1.0f, 1.0f, amax);
+            epi_row<N, F8>(p, ta, y0 + r, x, s_bias, s_head, s_wsc, in_s, out_inv, amax);
         }
 #pragma unroll
         for (int c0 = 0; c0 < N; c0 += 32) tmem_zero32(ta + (uint32_t)c0);
@@ -550,6 +555,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         aph ^= 1u;
       }
     }
+  }
+  if (F8 && warp >= 2 && p.out_amax) {  // running max |output| for the next call's scale
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    if (lane == 0) atomicMax(p.out_amax, __float_as_uint(amax));
   }
   tc_fence_before();
   __syncthreads();
@@ -692,27 +702,30 @@ namespace {
 
 constexpr int kRowsMaxWeights = 80 * 1024;  // resident weights of the row-blocked kernel
 
-template <int N, int KCB>
+template <int N, int KCB, bool F8>
 art_status launch_rows(art_ctx* ctx, const TcConv& c) {
-  using Cfg = RowCfg<N, KCB>;
+  using Cfg = RowCfg<N, KCB, F8>;
+  constexpr int kEs = F8 ? 1 : 2;
+  const CUtensorMapDataType dt = F8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   CUtensorMap tmA, tmB;
-  const CUtensorMapSwizzle swz = KCB == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+  const CUtensorMapSwizzle swz = KCB == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                            : (KCB == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B);
   {
     cuuint64_t dims[3] = {(cuuint64_t)c.cin, (cuuint64_t)c.W, (cuuint64_t)c.H};
-    cuuint64_t strides[2] = {(cuuint64_t)c.cin * 2, (cuuint64_t)c.W * c.cin * 2};
+    cuuint64_t strides[2] = {(cuuint64_t)c.cin * kEs, (cuuint64_t)c.W * c.cin * kEs};
     cuuint32_t box[3] = {(cuuint32_t)Cfg::KC, (cuuint32_t)Cfg::kHalo, 1};
     cuuint32_t es[3] = {1, 1, 1};
-    CUresult r = g_encode(&tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)c.in, dims, strides, box, es,
+    CUresult r = g_encode(&tmA, dt, 3, (void*)c.in, dims, strides, box, es,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(ctx, ART_ERR_CUDA, "cuTensorMapEncodeTiled (activations) failed: %d", (int)r);
   }
   {
     cuuint64_t dims[2] = {(cuuint64_t)9 * c.cin, (cuuint64_t)c.cout};
-    cuuint64_t strides[1] = {(cuuint64_t)9 * c.cin * 2};
+    cuuint64_t strides[1] = {(cuuint64_t)9 * c.cin * kEs};
     cuuint32_t box[2] = {(cuuint32_t)Cfg::KC, (cuuint32_t)N};
     cuuint32_t es[2] = {1, 1};
-    CUresult r = g_encode(&tmB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)c.w, dims, strides, box, es,
+    CUresult r = g_encode(&tmB, dt, 2, (void*)c.w, dims, strides, box, es,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(ctx, ART_ERR_CUDA, "cuTensorMapEncodeTiled (weights) failed: %d", (int)r);
@@ -738,12 +751,16 @@ art_status launch_rows(art_ctx* ctx, const TcConv& c) {
   p.head_n = c.head_n;
   p.head_ld = c.head_ld;
   p.head_off = c.head_off;
-  p.pool = (__nv_bfloat16*)c.pool;
+  p.pool = F8 ? nullptr : (__nv_bfloat16*)c.pool;  // the FP8 network pools in a pass of its own
+  p.in_scale = c.in_scale;
+  p.w_scale = c.w_scale;
+  p.out_scale = c.out_scale;
+  p.out_amax = c.out_amax;
   p.err = ctx->d_status + kStTcError;
   rp.cpt = c.cin / Cfg::KC;
   rp.n_units = ((c.H + kRows - 1) / kRows) * p.tiles_per_row;
   rp.w_bytes = 9 * rp.cpt * N * KCB;
-  const int tail = 8 * (2 * 24 + 5) + 16 + 4 * N + 4 * (4 * 32 + 4);
+  const int tail = 8 * (2 * 24 + 5) + 16 + 4 * N + 4 * (4 * 32 + 4) + 4 * N;
   // two CTAs per SM (two issuing threads, one accumulator buffer each) when
   // the resident weights and three stages fit in half the shared memory
   const int half = 232448 / 2 - 1024 - rp.w_bytes - tail;
@@ -753,11 +770,11 @@ art_status launch_rows(art_ctx* ctx, const TcConv& c) {
   rp.n_stages = std::min(24, avail / Cfg::kStageBytes);
   if (rp.n_stages < 2) return fail(ctx, ART_ERR_UNSUPPORTED, "row-blocked conv: weights too large");
   const int smem = 1024 + rp.w_bytes + rp.n_stages * Cfg::kStageBytes + tail;
-  auto kfn = conv_rows_kernel<N, KCB>;
+  auto kfn = conv_rows_kernel<N, KCB, F8>;
   cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "conv_rows shared memory attribute");
   const int grid = std::min(rp.n_units, ctas * ctx->num_sms);
-  ART_LAUNCH(ctx, "conv_tc", kfn, grid, kThreads, smem, tmA, tmB, rp);
+  ART_LAUNCH(ctx, F8 ? "conv_tc_fp8" : "conv_tc", kfn, grid, kThreads, smem, tmA, tmB, rp);
   return ART_OK;
 }
 
@@ -774,6 +791,17 @@ art_status launch_tc_conv(art_ctx* ctx, const TcConv& c) {
   if (!tc_conv_ok(c)) return fail(ctx, ART_ERR_UNSUPPORTED, "tensor-core conv: unsupported shape");
   if (c.f8) {  // row bytes = channels per K chunk: 128, 64 or 32
     const int kcb = c.cin % 128 == 0 ? 128 : (c.cin % 64 == 0 ? 64 : 32);
+    if ((c.cout == 32 || c.cout == 64) && 9 * c.cin * c.cout <= kRowsMaxWeights && ctx->conv_rows) {
+      // the narrow layers on the row-blocked kernel: K = 32 per FP8 MMA halves its instruction count
+#define ART_F8R(NN)                                                                \
+  return kcb == 128 ? launch_rows<NN, 128, true>(ctx, c)                           \
+                    : (kcb == 64 ? launch_rows<NN, 64, true>(ctx, c) : launch_rows<NN, 32, true>(ctx, c))
+      if (c.cout == 32) {
+        ART_F8R(32);
+      }
+      ART_F8R(64);
+#undef ART_F8R
+    }
 #define ART_F8(NN)                                                             \
   return kcb == 128 ? launch_typed<NN, 128, true>(ctx, c)                      \
                     : (kcb == 64 ? launch_typed<NN, 64, true>(ctx, c) : launch_typed<NN, 32, true>(ctx, c))
@@ -788,8 +816,8 @@ art_status launch_tc_conv(art_ctx* ctx, const TcConv& c) {
   const bool k64 = c.cin % 64 == 0;  // BF16: 64 channels = 128-B rows, else 32 = 64-B rows
   if ((c.cout == 32 || c.cout == 64) && 9 * c.cin * c.cout * 2 <= kRowsMaxWeights && ctx->conv_rows &&
       (!c.pool || (!c.up2 && !c.rgba))) {
-    if (c.cout == 32) return k64 ? launch_rows<32, 128>(ctx, c) : launch_rows<32, 64>(ctx, c);
-    return k64 ? launch_rows<64, 128>(ctx, c) : launch_rows<64, 64>(ctx, c);
+    if (c.cout == 32) return k64 ? launch_rows<32, 128, false>(ctx, c) : launch_rows<32, 64, false>(ctx, c);
+    return k64 ? launch_rows<64, 128, false>(ctx, c) : launch_rows<64, 64, false>(ctx, c);
   }
   art_status st;
   switch (c.cout) {

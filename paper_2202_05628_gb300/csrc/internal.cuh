@@ -44,7 +44,9 @@ enum StatusWord {
   kStActiveGroups = 20, // binning: groups of four consecutive tiles with instances (listed in d_agroups)
   kStExactQ = 21,       // composite: tiles queued for the exact re-walk (a pixel's reorder buffer overflowed)
   kStGridCells = 22,    // lattice index: occupied cells of the last pose
-  kStWords = 23
+  kStPredGroups = 23,   // learned skip: tile groups holding a tile whose interval the proposal predicts
+  kStForcedTiles = 24,  // learned skip: tiles walked in full (or not at all) without a prediction
+  kStWords = 25
 };
 
 // Per-view camera, with host-precomputed ray frame.
@@ -160,6 +162,8 @@ struct art_ctx {
   uint32_t* d_sortlist = nullptr;  // tiles whose bucket needs sorting
   unsigned long long* d_scan_state = nullptr;  // tile scan: per block aggregate and inclusive prefix words
   uint32_t* d_agroups = nullptr;  // groups of four consecutive tiles with instances (unordered)
+  uint32_t* d_pgroups = nullptr;  // learned skip: the groups with a tile to predict (unordered)
+  uint8_t* d_tclass = nullptr;    // learned skip: per tile 0 = predict, 1 = whole range, 2 = nothing
   unsigned long long* d_status = nullptr;
   unsigned long long* h_status = nullptr;  // pinned
   float* d_sh = nullptr;        // [n][(L+1)^2][C] spherical-harmonics coefficients (view-dependent features)
@@ -340,7 +344,14 @@ art_status load_proposal(art_ctx* ctx, const float* params);
 void launch_pose_bias(art_ctx* ctx);
 // bins [H][W][2] (may be null), logits [H][W][128] (may be null); with
 // active_only, only 4-tile groups with a non-empty tile are predicted.
-art_status launch_proposal(art_ctx* ctx, const ViewParams& v, uint8_t* bins, float* logits, bool active_only);
+// classified: only the groups the tile classes list (launch_tile_class), and
+// only their class-0 tiles' bins written.
+art_status launch_proposal(art_ctx* ctx, const ViewParams& v, uint8_t* bins, float* logits, bool active_only,
+                           bool classified = false);
+// Learned skip, after launch_bin with the tile histogram: per tile with
+// instances whether the proposal can change its walk (class 0), else its
+// bins set to the whole range (1) or to nothing (2); lists the groups to predict.
+void launch_tile_class(art_ctx* ctx, const ViewParams& v, uint8_t* bins);
 void* make_hit_log(int32_t* count, uint32_t* ids, float* t0, float* t1, int cap);
 void free_hit_log(void* p);
 

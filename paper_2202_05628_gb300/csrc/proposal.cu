@@ -53,6 +53,7 @@ struct PropParams {
   int active_only;         // only the groups listed in agroups (count: *n_active)
   const uint32_t* agroups;
   const unsigned long long* n_active;
+  const uint8_t* tclass;   // per tile: predict only class 0 (null: every tile)
   uint8_t* bins;           // [H][W][2] or null
   float* logits;           // [H][W][128] or null
   unsigned long long* err;
@@ -218,7 +219,8 @@ __global__ void __launch_bounds__(128) proposal_kernel(PropParams p) {
             }
           }
         }
-        if (p.bins && inside) reinterpret_cast<uchar2*>(p.bins)[pix] = make_uchar2((uint8_t)bn, (uint8_t)bf);
+        if (p.bins && inside && (!p.tclass || p.tclass[tile] == 0))
+          reinterpret_cast<uchar2*>(p.bins)[pix] = make_uchar2((uint8_t)bn, (uint8_t)bf);
         tc_fence_before();
         __syncthreads();  // TMEM and the input rows are reused by the next group
       }
@@ -282,7 +284,83 @@ void launch_pose_bias(art_ctx* ctx) {
   ART_LAUNCH(ctx, "proposal_pose_bias", pose_bias_kernel, 1, 256, 0, ctx->d_prop_f32, ctx->d_pose, ctx->d_pose_bias);
 }
 
-art_status launch_proposal(art_ctx* ctx, const ViewParams& v, uint8_t* bins, float* logits, bool active_only) {
+// Tiles whose walk the proposal cannot change (learned skip).  From a tile's
+// coarse optical-depth bound per depth bin (h, total tot, first and last
+// occupied bins lo, hi) and the check lost = (1 - e^-front) + T_end
+// (1 - e^-back) <= max_missed (front / back: the bins before / after the
+// interval):
+//   - if 1 - e^-tot <= max_missed, the empty interval passes: the tile
+//     composites nothing (class 2);
+//   - if 1 - e^-h[lo] > max_missed, no interval may start after bin lo; if
+//     e^-tot (1 - e^-h[hi]) > max_missed, none may end before bin hi, since
+//     every ray's T_end >= e^-tot (the bound sums every hit's sigma 2 r); with
+//     both, every passing interval covers [lo, hi], which holds all of the
+//     tile's hits: the tile is walked in full without a prediction (class 1).
+// Other tiles are predicted (class 0); the groups holding one are listed for
+// the proposal.  Classes 1 and 2 write their pixels' bins (0, 63) and
+// (63, 0): the composite and its check read them as they read predictions.
+__global__ void __launch_bounds__(128) tile_class_kernel(ViewParams v, const uint2* __restrict__ ranges,
+                                                        const float* __restrict__ thist,
+                                                        const uint32_t* __restrict__ agroups,
+                                                        unsigned long long* __restrict__ status, float max_missed,
+                                                        uint8_t* __restrict__ tclass, uint32_t* __restrict__ pgroups,
+                                                        uint8_t* __restrict__ bins) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned long long n_groups = status[kStActiveGroups];
+  const int ntiles = v.tiles_x * v.tiles_y;
+  for (unsigned long long gi = blockIdx.x; gi < n_groups; gi += gridDim.x) {
+    const int g = (int)agroups[gi];
+    const int tile = 4 * g + warp;
+    int cls = 3;  // no instances: not walked, not predicted
+    if (tile < ntiles) {
+      const uint2 rg = ranges[tile];
+      if (rg.y > rg.x) {
+        const float h0 = thist[(size_t)tile * kPropBins + lane], h1 = thist[(size_t)tile * kPropBins + 32 + lane];
+        float tot = h0 + h1;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+        const uint32_t m0 = __ballot_sync(0xffffffffu, h0 > 0.0f), m1 = __ballot_sync(0xffffffffu, h1 > 0.0f);
+        const int lo = m0 ? __ffs(m0) - 1 : (m1 ? 32 + __ffs(m1) - 1 : 0);
+        const int hi = m1 ? 63 - __clz(m1) : (m0 ? 31 - __clz(m0) : 0);
+        const float hlo = __shfl_sync(0xffffffffu, lo < 32 ? h0 : h1, lo & 31);
+        const float hhi = __shfl_sync(0xffffffffu, hi < 32 ? h0 : h1, hi & 31);
+        if (-expm1f(-tot) <= max_missed) {
+          cls = 2;
+        } else if (-expm1f(-hlo) > max_missed && expf(-tot) * -expm1f(-hhi) > max_missed) {
+          cls = 1;
+        } else {
+          cls = 0;
+        }
+        if (cls != 0) {
+          const int px = (tile % v.tiles_x) * TSX + (lane & 7), py = (tile / v.tiles_x) * TSY + (lane >> 3);
+          if (px < v.W && py < v.H)
+            reinterpret_cast<uchar2*>(bins)[(size_t)py * v.W + px] = cls == 1 ? make_uchar2(0, kPropBins - 1)
+                                                                               : make_uchar2(kPropBins - 1, 0);
+        }
+      }
+    }
+    if (tile < ntiles && lane == 0) tclass[tile] = (uint8_t)cls;
+    __shared__ int s_pred[4];
+    if (lane == 0) s_pred[warp] = cls == 0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (s_pred[0] | s_pred[1] | s_pred[2] | s_pred[3]) pgroups[atomicAdd(status + kStPredGroups, 1ull)] = (uint32_t)g;
+    }
+    __syncthreads();
+    if (lane == 0 && (cls == 1 || cls == 2)) atomicAdd(status + kStForcedTiles, 1ull);
+  }
+}
+
+void launch_tile_class(art_ctx* ctx, const ViewParams& v, uint8_t* bins) {
+  cudaMemsetAsync(ctx->d_status + kStPredGroups, 0, 2 * sizeof(unsigned long long), ctx->stream);
+  const int ngroups = (v.tiles_x * v.tiles_y + 3) / 4;
+  ART_LAUNCH(ctx, "tile_class", tile_class_kernel, std::max(1, std::min(ngroups, 8 * ctx->num_sms)), 128, 0, v,
+             ctx->d_ranges, ctx->d_thist, ctx->d_agroups, ctx->d_status, ctx->cfg.max_missed, ctx->d_tclass,
+             ctx->d_pgroups, bins);
+}
+
+art_status launch_proposal(art_ctx* ctx, const ViewParams& v, uint8_t* bins, float* logits, bool active_only,
+                           bool classified) {
   if (!ctx->attr_proposal) {  // (a function attribute holds per device: set once per context)
     cudaError_t e = cudaFuncSetAttribute(proposal_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "proposal smem attribute");
@@ -297,8 +375,9 @@ art_status launch_proposal(art_ctx* ctx, const ViewParams& v, uint8_t* bins, flo
   const int ntiles = v.tiles_x * v.tiles_y;
   p.ngroups = (ntiles + 3) / 4;
   p.active_only = active_only ? 1 : 0;
-  p.agroups = ctx->d_agroups;
-  p.n_active = ctx->d_status + kStActiveGroups;
+  p.agroups = classified ? ctx->d_pgroups : ctx->d_agroups;
+  p.n_active = ctx->d_status + (classified ? kStPredGroups : kStActiveGroups);
+  p.tclass = classified ? ctx->d_tclass : nullptr;
   p.bins = bins;
   p.logits = logits;
   p.err = ctx->d_status + kStTcError;

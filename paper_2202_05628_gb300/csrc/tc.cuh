@@ -147,6 +147,10 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
+// kind::f8f6f4 with E4M3 A and B (format 0), FP32 D.
+__host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
 
 // TMEM allocation of `cols` columns by one whole warp; the base address is
 // written to shared memory.
