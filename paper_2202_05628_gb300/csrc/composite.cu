@@ -503,7 +503,7 @@ __global__ void __launch_bounds__(256) composite_clear_kernel(const uint2* __res
 }
 
 template <int C, typename TF, typename TO, int MODE>
-__global__ void __launch_bounds__(32, 12) composite_split_kernel(
+__global__ void __launch_bounds__(32, kCompositeWarps) composite_split_kernel(
     const uint2* __restrict__ ranges, const uint2* __restrict__ seg, const uint32_t* __restrict__ items,
     const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals, const float4* __restrict__ rec,
     const short4* __restrict__ rect, const TF* __restrict__ feat, ViewParams v, float tau, TO* __restrict__ Fout,
@@ -531,7 +531,7 @@ __global__ void __launch_bounds__(32, 12) composite_split_kernel(
 // tile names its view (vs->toff), whose parameters, rectangles and output
 // maps it composites with.
 template <int C, typename TF, typename TO>
-__global__ void __launch_bounds__(32, 12) composite_split_views_kernel(
+__global__ void __launch_bounds__(32, kCompositeWarps) composite_split_views_kernel(
     const ViewSet* __restrict__ vs, const uint2* __restrict__ ranges, const uint2* __restrict__ seg,
     const uint32_t* __restrict__ items, const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals,
     const float4* __restrict__ rec, const short4* __restrict__ rect, const TF* __restrict__ feat, float tau,
@@ -1114,10 +1114,10 @@ art_status launch_composite_skip(art_ctx* ctx, const ViewParams& v, void* F, int
 
 int composite_blocks_per_sm(int C, int feat_bytes) {
   // one-warp blocks, limited by shared memory (staged-feature ring, chunk
-  // geometry, double-buffered records) and by registers (12 blocks)
-  const int ring = std::max(1, std::min(16, 10240 / (NT * C * feat_bytes)));
+  // geometry, double-buffered records) and by registers (kCompositeWarps)
+  const int ring = std::max(1, std::min(16, kRingBytes / (NT * C * feat_bytes)));
   const int smem = ring * NT * (C * feat_bytes + 8) + NT * (4 * 16 + 8) + 2 * NT * (64 + 8) + 4 * kPropBins + 64;
-  return std::max(1, std::min(12, (227 * 1024) / smem));
+  return std::max(1, std::min(kCompositeWarps, (227 * 1024) / smem));
 }
 
 art_status launch_composite_labels(art_ctx* ctx, const ViewParams& v, float* labels, uint8_t* bins) {

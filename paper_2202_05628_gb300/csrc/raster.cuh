@@ -136,12 +136,17 @@ __device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
 constexpr int TSX = 8, TSY = 4;  // tile: 8 x 4 pixels = one warp
 constexpr int NT = 32;           // instances per staged chunk
 
+// Resident one-warp blocks of the composite walk per SM (its register cap is
+// 64K / (32 x this)) and the shared memory of each block's feature ring.
+constexpr int kCompositeWarps = 12;
+constexpr int kRingBytes = 10240;
+
 template <int C, typename TF>
 struct Ring {
-  // chunks of staged feature rows kept in shared memory (<= 10 KB, 1 .. 16):
-  // small enough for many resident one-warp blocks; a hit released after its
-  // chunk left the ring reads its voxel again from global memory
-  static constexpr int kRaw = 10240 / (NT * C * (int)sizeof(TF));
+  // chunks of staged feature rows kept in shared memory (<= kRingBytes, 1 ..
+  // 16): small enough for many resident one-warp blocks; a hit released
+  // after its chunk left the ring reads its voxel again from global memory
+  static constexpr int kRaw = kRingBytes / (NT * C * (int)sizeof(TF));
   static constexpr int kChunks = kRaw < 1 ? 1 : (kRaw < 16 ? kRaw : 16);
 };
 

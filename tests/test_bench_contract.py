@@ -26,9 +26,11 @@ def test_roofline_of_the_convolutions():
     assert math.isclose(r["achieved"], per_launch / 0.05e-3 / 1e12, rel_tol=1e-12)
     assert math.isclose(r["frac"], r["achieved"] / 1713.7, rel_tol=1e-12)
     assert r["peak_is"] == "measured sustained BF16" and r["traffic"] > 0
-    # the back-to-back launch time replaces the event time when given
-    r2 = bench.roofline(kt, {"instances": 900000}, peaks, "bf16_skip", 1000000, 32, frames, conv_launch_ms=0.04)
+    # the back-to-back launch time replaces the event time when given, against the burst peak
+    peaks_b = dict(peaks, bf16_tflops=1934.1)
+    r2 = bench.roofline(kt, {"instances": 900000}, peaks_b, "bf16_skip", 1000000, 32, frames, conv_launch_ms=0.04)
     assert math.isclose(r2["avg_ms"], 0.04) and math.isclose(r2["achieved"], per_launch / 0.04e-3 / 1e12)
+    assert r2["peak"] == 1934.1 and r2["peak_is"] == "measured burst BF16"
     # no measured peaks: the fallback figures, labelled so
     r3 = bench.roofline(kt, {"instances": 900000}, {}, "bf16_skip", 1000000, 32, frames)
     assert r3["peak"] == 1700.0 and r3["peak_is"].startswith("fallback")
