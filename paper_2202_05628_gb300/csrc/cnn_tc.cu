@@ -251,6 +251,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
   float amax = 0.0f;  // FP8 epilogue: max |output| seen by this thread
+  grid_dep_launch();  // the next layer may start its prologue where this one's CTAs leave SMs
+  grid_dep_wait();    // the previous layer's outputs (this one's input) are complete
 
   if (warp == 0) {
     // ---------------------------------------------------------------- TMA
@@ -444,13 +446,17 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   // A stage is one input row and channel chunk in its three horizontal
   // shifts (three boxes, one barrier round trip).
+  grid_dep_launch();  // the next layer may start its prologue where this one's CTAs leave SMs
   if (warp == 0) {
     // ------------------------------------------------------------ TMA
     if (lane == 0) {
-      mbar_expect_tx(wbar, (uint32_t)rp.w_bytes);
+      mbar_expect_tx(wbar, (uint32_t)rp.w_bytes);  // the weights are static: loaded before the wait
       for (int tap = 0; tap < 9; ++tap)
         for (int c = 0; c < cpt; ++c)
           tma_load_2d(wsm + (size_t)wblk(tap / 3, tap % 3, c) * N * KCB, &tmB, wbar, tap * p.cin + c * Cfg::KC, 0);
+    }
+    grid_dep_wait();  // the previous layer's outputs (this one's input) are complete
+    if (lane == 0) {
       int s = 0;
       uint32_t ph = 0;
       for (int u = blockIdx.x; u < rp.n_units && !*abort_flag; u += gridDim.x) {
@@ -470,6 +476,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA
+    grid_dep_wait();
     if (lane == 0) {
       int s = 0, buf = 0;
       uint32_t ph = 0, aph = 0;
@@ -517,6 +524,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncwarp();
   } else {
     // ------------------------------------------------------------ epilogue
+    grid_dep_wait();  // the output tensors may still be read by the previous layer
     const int qd = warp & 3;
     const int m = qd * 32 + lane;
     const uint32_t tq = tmem_base + ((uint32_t)(qd * 32) << 16);  // this warp's lane quarter
@@ -667,7 +675,7 @@ art_status launch_typed(art_ctx* ctx, const TcConv& c) {
   cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "conv_tc shared memory attribute");
   const int grid = std::min(p.n_tiles, Cfg::kCtas * ctx->num_sms);
-  ART_LAUNCH(ctx, F8 ? "conv_tc_fp8" : "conv_tc", kfn, grid, kThreads, Cfg::kSmem, tmA, tmB, p);
+  ART_LAUNCH_PDL(ctx, F8 ? "conv_tc_fp8" : "conv_tc", kfn, grid, kThreads, Cfg::kSmem, tmA, tmB, p);
   return ART_OK;
 }
 
@@ -774,7 +782,7 @@ art_status launch_rows(art_ctx* ctx, const TcConv& c) {
   cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "conv_rows shared memory attribute");
   const int grid = std::min(rp.n_units, ctas * ctx->num_sms);
-  ART_LAUNCH(ctx, F8 ? "conv_tc_fp8" : "conv_tc", kfn, grid, kThreads, smem, tmA, tmB, rp);
+  ART_LAUNCH_PDL(ctx, F8 ? "conv_tc_fp8" : "conv_tc", kfn, grid, kThreads, smem, tmA, tmB, rp);
   return ART_OK;
 }
 

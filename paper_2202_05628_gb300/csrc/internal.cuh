@@ -406,6 +406,27 @@ constexpr int kF8Tensors = 11;  // FP8 U-Net activation tensors with their own s
 }  // namespace art
 
 // Launch helper: counts and (optionally) times every kernel launch.
+// A launch that may overlap the tail of the previous kernel of the stream
+// (programmatic dependent launch): the kernel itself waits (griddepcontrol)
+// before it reads or writes memory the previous kernel touches.
+#define ART_LAUNCH_PDL(ctx, name, kernel, grid, block, smem, ...)              \
+  do {                                                                         \
+    art::prof_begin((ctx), (name));                                            \
+    cudaLaunchAttribute pdl_attr_[1];                                          \
+    pdl_attr_[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;     \
+    pdl_attr_[0].val.programmaticStreamSerializationAllowed = 1;               \
+    cudaLaunchConfig_t pdl_cfg_ = {};                                          \
+    pdl_cfg_.gridDim = dim3(grid);                                             \
+    pdl_cfg_.blockDim = dim3(block);                                           \
+    pdl_cfg_.dynamicSmemBytes = (smem);                                        \
+    pdl_cfg_.stream = (ctx)->stream;                                           \
+    pdl_cfg_.attrs = pdl_attr_;                                                \
+    pdl_cfg_.numAttrs = 1;                                                     \
+    cudaLaunchKernelEx(&pdl_cfg_, kernel, __VA_ARGS__);                        \
+    art::prof_end((ctx));                                                      \
+    (ctx)->launches++;                                                         \
+  } while (0)
+
 #define ART_LAUNCH(ctx, name, kernel, grid, block, smem, ...)                  \
   do {                                                                         \
     art::prof_begin((ctx), (name));                                            \

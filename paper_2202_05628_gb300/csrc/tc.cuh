@@ -152,6 +152,13 @@ __host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N) {
   return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialization may start while the previous kernel of the stream still
+// runs; grid_dep_wait blocks until that kernel has completed and its memory
+// is visible, grid_dep_launch lets the next kernel start launching.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
 // TMEM allocation of `cols` columns by one whole warp; the base address is
 // written to shared memory.
 __device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t cols) {
