@@ -275,6 +275,7 @@ __global__ void __launch_bounds__(kTileScanThreads) tile_scan_kernel(int ntiles,
                                                                      ScanWords* __restrict__ sw,
                                                                      uint32_t* __restrict__ agroups,
                                                                      unsigned long long* __restrict__ status) {
+  ART_PDL_ENTRY();
   __shared__ unsigned long long s_b, s_pi, s_pl;
   if (threadIdx.x == 0) s_b = atomicAdd(status + kStScanTicket, 1ull);
   __syncthreads();
@@ -425,6 +426,7 @@ __global__ void __launch_bounds__(256) bucket_emit_kernel(int64_t n, const uint3
                                                           unsigned long long* __restrict__ status,
                                                           const uint32_t* __restrict__ hbin,
                                                           const float* __restrict__ htau, float* __restrict__ thist) {
+  ART_PDL_ENTRY();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
   uint32_t c = 0, qq = 0;
@@ -638,6 +640,7 @@ __global__ void __launch_bounds__(kTileSortThreads) tile_sort_kernel(const uint2
                                                                      uint32_t* __restrict__ vals,
                                                                      unsigned long long* __restrict__ scratch,
                                                                      unsigned long long* __restrict__ status) {
+  ART_PDL_ENTRY();
   extern __shared__ unsigned long long sk[];
   __shared__ unsigned long long s_item;
   const uint32_t qmask = (1u << depth_bits) - 1u;
@@ -698,12 +701,12 @@ void launch_bin(art_ctx* ctx, const ViewParams& v, const uint32_t* hbin, const f
     ctx->attr_tile_sort = true;
   }
   const int nsb = (ntiles + kTileScanBlock - 1) / kTileScanBlock;
-  ART_LAUNCH(ctx, "bin_scan", tile_scan_kernel, nsb, kTileScanThreads, 0, ntiles, ctx->d_tcount, ctx->inst_cap,
+  ART_LAUNCH_PDL(ctx, "bin_scan", tile_scan_kernel, nsb, kTileScanThreads, 0, ntiles, ctx->d_tcount, ctx->inst_cap,
              ctx->d_toff, ctx->d_ranges, ctx->d_sortlist, reinterpret_cast<ScanWords*>(ctx->d_scan_state),
              ctx->d_agroups, ctx->d_status);
-  ART_LAUNCH(ctx, "bin_emit", bucket_emit_kernel, vb, 256, 0, n, ctx->d_cnt, ctx->d_rect, ctx->d_q, v, ctx->inst_cap,
+  ART_LAUNCH_PDL(ctx, "bin_emit", bucket_emit_kernel, vb, 256, 0, n, ctx->d_cnt, ctx->d_rect, ctx->d_q, v, ctx->inst_cap,
              0u, ctx->d_toff, ctx->d_keys, ctx->d_vals, ctx->d_status, hbin, htau, thist);
-  ART_LAUNCH(ctx, "tile_sort", tile_sort_kernel, 2 * ctx->num_sms, kTileSortThreads, kTileSortSmem * 8, ctx->d_ranges,
+  ART_LAUNCH_PDL(ctx, "tile_sort", tile_sort_kernel, 2 * ctx->num_sms, kTileSortThreads, kTileSortSmem * 8, ctx->d_ranges,
              ctx->d_sortlist, ntiles, v.depth_bits, ctx->d_keys, ctx->d_vals, ctx->d_sort_tmp, ctx->d_status);
 }
 
@@ -716,16 +719,16 @@ void launch_bin_views(art_ctx* ctx, const ViewSet& vs, int64_t ntiles) {
   }
   const int nt = (int)ntiles;
   const int nsb = (nt + kTileScanBlock - 1) / kTileScanBlock;
-  ART_LAUNCH(ctx, "bin_scan", tile_scan_kernel, nsb, kTileScanThreads, 0, nt, ctx->d_tcount, ctx->inst_cap,
+  ART_LAUNCH_PDL(ctx, "bin_scan", tile_scan_kernel, nsb, kTileScanThreads, 0, nt, ctx->d_tcount, ctx->inst_cap,
              ctx->d_toff, ctx->d_ranges, ctx->d_sortlist, reinterpret_cast<ScanWords*>(ctx->d_scan_state),
              ctx->d_agroups, ctx->d_status);
   for (int k = 0; k < vs.nv; ++k) {
     const int64_t o = (int64_t)k * vs.rect_stride;
-    ART_LAUNCH(ctx, "bin_emit", bucket_emit_kernel, vb, 256, 0, n, ctx->d_cnt_v + o, ctx->d_rect_v + o,
+    ART_LAUNCH_PDL(ctx, "bin_emit", bucket_emit_kernel, vb, 256, 0, n, ctx->d_cnt_v + o, ctx->d_rect_v + o,
                ctx->d_q_v + o, vs.v[k], ctx->inst_cap, vs.toff[k], ctx->d_toff, ctx->d_keys, ctx->d_vals,
                ctx->d_status, (const uint32_t*)nullptr, (const float*)nullptr, (float*)nullptr);
   }
-  ART_LAUNCH(ctx, "tile_sort", tile_sort_kernel, 2 * ctx->num_sms, kTileSortThreads, kTileSortSmem * 8, ctx->d_ranges,
+  ART_LAUNCH_PDL(ctx, "tile_sort", tile_sort_kernel, 2 * ctx->num_sms, kTileSortThreads, kTileSortSmem * 8, ctx->d_ranges,
              ctx->d_sortlist, nt, vs.v[0].depth_bits, ctx->d_keys, ctx->d_vals, ctx->d_sort_tmp, ctx->d_status);
 }
 

@@ -476,6 +476,7 @@ __global__ void __launch_bounds__(32) composite_kernel(const uint2* __restrict__
 template <int C, typename TO>
 __global__ void __launch_bounds__(256) composite_clear_kernel(const uint2* __restrict__ ranges, ViewParams v,
                                                               TO* __restrict__ Fout, float* __restrict__ Aout) {
+  ART_PDL_ENTRY();
   const int tile = blockIdx.x * 8 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (tile >= v.tiles_x * v.tiles_y) return;
@@ -508,6 +509,7 @@ __global__ void __launch_bounds__(32, kCompositeWarps) composite_split_kernel(
     const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals, const float4* __restrict__ rec,
     const short4* __restrict__ rect, const TF* __restrict__ feat, ViewParams v, float tau, TO* __restrict__ Fout,
     float* __restrict__ Aout, unsigned long long* __restrict__ status, float* __restrict__ part, SkipArgs sk) {
+  ART_PDL_ENTRY();
   const int lane = threadIdx.x & 31;
   const unsigned long long n_items = status[kStItems];
   const uint32_t wq = seg_window(v, status);
@@ -537,6 +539,7 @@ __global__ void __launch_bounds__(32, kCompositeWarps) composite_split_views_ker
     const float4* __restrict__ rec, const short4* __restrict__ rect, const TF* __restrict__ feat, float tau,
     unsigned long long* __restrict__ status, float* __restrict__ part, uint32_t* __restrict__ xflag,
     uint32_t* __restrict__ xqueue) {
+  ART_PDL_ENTRY();
   const int lane = threadIdx.x & 31;
   const unsigned long long n_items = status[kStItems];
   for (;;) {
@@ -669,6 +672,7 @@ __global__ void __launch_bounds__(32) composite_merge_kernel(const uint2* __rest
                                                              float* __restrict__ Aout,
                                                              unsigned long long* __restrict__ status,
                                                              const float* __restrict__ part, SkipArgs sk) {
+  ART_PDL_ENTRY();
   constexpr int G = C >= kMergeCh ? C / kMergeCh : 1;  // channel groups
   const int lane = threadIdx.x & 31;
   const unsigned long long n_items = status[kStMulti] * G;
@@ -691,6 +695,7 @@ __global__ void __launch_bounds__(32) composite_merge_views_kernel(const ViewSet
                                                                    const uint32_t* __restrict__ multi, float tau,
                                                                    unsigned long long* __restrict__ status,
                                                                    const float* __restrict__ part, SkipArgs sk) {
+  ART_PDL_ENTRY();
   constexpr int G = C >= kMergeCh ? C / kMergeCh : 1;
   const int lane = threadIdx.x & 31;
   const unsigned long long n_items = status[kStMulti] * G;
@@ -721,6 +726,7 @@ __global__ void __launch_bounds__(32) composite_queue_kernel(const uint2* __rest
                                                              const uint32_t* __restrict__ queue, int qword,
                                                              uint32_t* __restrict__ xflag,
                                                              uint32_t* __restrict__ xqueue) {
+  ART_PDL_ENTRY();
   const unsigned long long n = status[qword];
   for (unsigned long long i = blockIdx.x; i < n; i += gridDim.x) {
     const int tile = (int)queue[i];
@@ -747,6 +753,7 @@ __global__ void __launch_bounds__(32) composite_queue_views_kernel(const ViewSet
                                                                    const uint32_t* __restrict__ queue, int qword,
                                                                    uint32_t* __restrict__ xflag,
                                                                    uint32_t* __restrict__ xqueue) {
+  ART_PDL_ENTRY();
   const unsigned long long n = status[qword];
   for (unsigned long long i = blockIdx.x; i < n; i += gridDim.x) {
     const uint32_t tile = queue[i];
@@ -778,6 +785,7 @@ __global__ void __launch_bounds__(32) composite_exact_kernel(
     const float4* __restrict__ rec, const short4* __restrict__ rect, const TF* __restrict__ feat, float tau,
     unsigned long long* __restrict__ status, const uint32_t* __restrict__ xqueue, float2* __restrict__ xhit,
     uint32_t* __restrict__ xpos) {
+  ART_PDL_ENTRY();
   __shared__ float4 s_b0[NT], s_b1[NT], s_b2[NT], s_xl[NT];
   __shared__ uint32_t s_mask[NT];
   const int lane = threadIdx.x & 31;
@@ -879,30 +887,30 @@ void views_walk(art_ctx* ctx, const ViewSet& vs) {
   cudaMemsetAsync(ctx->d_status + kStFallback, 0, sizeof(unsigned long long), ctx->stream);
   cudaMemsetAsync(ctx->d_xflag, 0, sizeof(uint32_t) * (size_t)ntiles, ctx->stream);
   cudaMemsetAsync(ctx->d_status + kStExactQ, 0, sizeof(unsigned long long), ctx->stream);
-  ART_LAUNCH(ctx, "composite_plan", seg_plan_kernel, (ntiles + 255) / 256, 256, 0, ntiles, ctx->d_ranges, ctx->seg_len,
+  ART_LAUNCH_PDL(ctx, "composite_plan", seg_plan_kernel, (ntiles + 255) / 256, 256, 0, ntiles, ctx->d_ranges, ctx->seg_len,
              ctx->d_seg, ctx->d_items, ctx->d_multi, ctx->d_status, (const uint32_t*)nullptr, 0);
   for (int k = 0; k < vs.nv; ++k) {
     const ViewParams& v = vs.v[k];
     auto cfn = composite_clear_kernel<C, TO>;
-    ART_LAUNCH(ctx, "composite_clear", cfn, (v.tiles_x * v.tiles_y + 7) / 8, 256, 0, ctx->d_ranges + vs.toff[k], v,
+    ART_LAUNCH_PDL(ctx, "composite_clear", cfn, (v.tiles_x * v.tiles_y + 7) / 8, 256, 0, ctx->d_ranges + vs.toff[k], v,
                (TO*)vs.F[k], vs.A[k]);
   }
   auto kfn = composite_split_views_kernel<C, TF, TO>;
-  ART_LAUNCH(ctx, "composite", kfn, ctx->composite_blocks, 32, 0, ctx->d_vset, ctx->d_ranges, ctx->d_seg, ctx->d_items,
+  ART_LAUNCH_PDL(ctx, "composite", kfn, ctx->composite_blocks, 32, 0, ctx->d_vset, ctx->d_ranges, ctx->d_seg, ctx->d_items,
              ctx->d_keys, ctx->d_vals, ctx->d_rec, ctx->d_rect_v, feat, ctx->cfg.tau, ctx->d_status, ctx->d_part,
              ctx->d_xflag, ctx->d_xqueue);
   SkipArgs sk{};
   sk.queue = ctx->d_fbq;
   sk.qword = kStFallback;
   auto mfn = composite_merge_views_kernel<C, TO>;
-  ART_LAUNCH(ctx, "composite_merge", mfn, 32 * ctx->num_sms, 32, 0, ctx->d_vset, ctx->d_seg, ctx->d_multi,
+  ART_LAUNCH_PDL(ctx, "composite_merge", mfn, 32 * ctx->num_sms, 32, 0, ctx->d_vset, ctx->d_seg, ctx->d_multi,
              ctx->cfg.tau, ctx->d_status, ctx->d_part, sk);
   auto qfn = composite_queue_views_kernel<C, TF, TO>;
-  ART_LAUNCH(ctx, "composite_fallback", qfn, std::min(ntiles, 16 * ctx->num_sms), 32, 0, ctx->d_vset, ctx->d_ranges,
+  ART_LAUNCH_PDL(ctx, "composite_fallback", qfn, std::min(ntiles, 16 * ctx->num_sms), 32, 0, ctx->d_vset, ctx->d_ranges,
              ctx->d_keys, ctx->d_vals, ctx->d_rec, ctx->d_rect_v, feat, ctx->cfg.tau, ctx->d_status, ctx->d_fbq,
              kStFallback, ctx->d_xflag, ctx->d_xqueue);
   auto xfn = composite_exact_kernel<C, TF, TO, true>;
-  ART_LAUNCH(ctx, "composite_exact", xfn, kExactBlocks, 32, 0, (const ViewSet*)ctx->d_vset, vs.v[0], (TO*)nullptr,
+  ART_LAUNCH_PDL(ctx, "composite_exact", xfn, kExactBlocks, 32, 0, (const ViewSet*)ctx->d_vset, vs.v[0], (TO*)nullptr,
              (float*)nullptr, ctx->d_ranges, ctx->d_keys, ctx->d_vals, ctx->d_rec, ctx->d_rect_v, feat, ctx->cfg.tau,
              ctx->d_status, ctx->d_xqueue, ctx->d_xhit, ctx->d_xpos);
 }
@@ -937,28 +945,28 @@ void split_pass(art_ctx* ctx, const ViewParams& v, void* F, float* A, int mode, 
   cudaMemsetAsync(ctx->d_status + sk.qword, 0, sizeof(unsigned long long), ctx->stream);
   // a re-walk covers a few tiles: shorter segments put more warps on them
   const int seg_len = list ? std::max(32, ctx->seg_len / 4) : ctx->seg_len;
-  ART_LAUNCH(ctx, list ? "composite_replan" : "composite_plan", seg_plan_kernel, (ntiles + 255) / 256, 256, 0, ntiles,
+  ART_LAUNCH_PDL(ctx, list ? "composite_replan" : "composite_plan", seg_plan_kernel, (ntiles + 255) / 256, 256, 0, ntiles,
              ctx->d_ranges, seg_len, ctx->d_seg, ctx->d_items, ctx->d_multi, ctx->d_status, list, list_word);
   if (!list) {
     auto cfn = composite_clear_kernel<C, TO>;
-    ART_LAUNCH(ctx, "composite_clear", cfn, (ntiles + 7) / 8, 256, 0, ctx->d_ranges, v, (TO*)F, A);
+    ART_LAUNCH_PDL(ctx, "composite_clear", cfn, (ntiles + 7) / 8, 256, 0, ctx->d_ranges, v, (TO*)F, A);
   }
   const int grid = ctx->composite_blocks;
   if (mode == kInterval) {
     auto kfn = composite_split_kernel<C, TF, TO, kInterval>;
-    ART_LAUNCH(ctx, "composite_skip", kfn, grid, 32, 0, ctx->d_ranges, ctx->d_seg, ctx->d_items, ctx->d_keys,
+    ART_LAUNCH_PDL(ctx, "composite_skip", kfn, grid, 32, 0, ctx->d_ranges, ctx->d_seg, ctx->d_items, ctx->d_keys,
                ctx->d_vals, ctx->d_rec, ctx->d_rect, feat, v, ctx->cfg.tau, (TO*)F, A, ctx->d_status, ctx->d_part,
                sk);
     auto mfn = composite_merge_kernel<C, TO, kInterval>;
-    ART_LAUNCH(ctx, "composite_merge", mfn, 32 * ctx->num_sms, 32, 0, ctx->d_seg, ctx->d_multi, v, ctx->cfg.tau, (TO*)F,
+    ART_LAUNCH_PDL(ctx, "composite_merge", mfn, 32 * ctx->num_sms, 32, 0, ctx->d_seg, ctx->d_multi, v, ctx->cfg.tau, (TO*)F,
                A, ctx->d_status, ctx->d_part, sk);
   } else {
     auto kfn = composite_split_kernel<C, TF, TO, kPlain>;
-    ART_LAUNCH(ctx, list ? "composite_refill" : "composite", kfn, grid, 32, 0, ctx->d_ranges, ctx->d_seg, ctx->d_items,
+    ART_LAUNCH_PDL(ctx, list ? "composite_refill" : "composite", kfn, grid, 32, 0, ctx->d_ranges, ctx->d_seg, ctx->d_items,
                ctx->d_keys, ctx->d_vals, ctx->d_rec, ctx->d_rect, feat, v, ctx->cfg.tau, (TO*)F, A,
                ctx->d_status, ctx->d_part, sk);
     auto mfn = composite_merge_kernel<C, TO, kPlain>;
-    ART_LAUNCH(ctx, "composite_merge", mfn, 32 * ctx->num_sms, 32, 0, ctx->d_seg, ctx->d_multi, v, ctx->cfg.tau, (TO*)F,
+    ART_LAUNCH_PDL(ctx, "composite_merge", mfn, 32 * ctx->num_sms, 32, 0, ctx->d_seg, ctx->d_multi, v, ctx->cfg.tau, (TO*)F,
                A, ctx->d_status, ctx->d_part, sk);
   }
 }
@@ -989,11 +997,11 @@ void split_walk(art_ctx* ctx, const ViewParams& v, void* F, float* A, int mode, 
   }
   auto qfn = composite_queue_kernel<C, TF, TO>;
   const int qgrid = std::min(ntiles, 16 * ctx->num_sms);
-  ART_LAUNCH(ctx, "composite_fallback", qfn, qgrid, 32, 0, ctx->d_ranges, ctx->d_keys, ctx->d_vals, ctx->d_rec,
+  ART_LAUNCH_PDL(ctx, "composite_fallback", qfn, qgrid, 32, 0, ctx->d_ranges, ctx->d_keys, ctx->d_vals, ctx->d_rec,
              ctx->d_rect, feat, v, ctx->cfg.tau, (TO*)F, A, ctx->d_status, seq, seq_word, ctx->d_xflag,
              ctx->d_xqueue);
   auto xfn = composite_exact_kernel<C, TF, TO, false>;
-  ART_LAUNCH(ctx, "composite_exact", xfn, kExactBlocks, 32, 0, (const ViewSet*)nullptr, v, (TO*)F, A, ctx->d_ranges,
+  ART_LAUNCH_PDL(ctx, "composite_exact", xfn, kExactBlocks, 32, 0, (const ViewSet*)nullptr, v, (TO*)F, A, ctx->d_ranges,
              ctx->d_keys, ctx->d_vals, ctx->d_rec, ctx->d_rect, feat, ctx->cfg.tau, ctx->d_status, ctx->d_xqueue,
              ctx->d_xhit, ctx->d_xpos);
 }

@@ -406,6 +406,16 @@ constexpr int kF8Tensors = 11;  // FP8 U-Net activation tensors with their own s
 }  // namespace art
 
 // Launch helper: counts and (optionally) times every kernel launch.
+// First statement of a kernel launched with ART_LAUNCH_PDL: wait until the
+// previous kernel of the stream has completed (its memory visible), then let
+// the next kernel start launching.  Only the launch and the ramp of the grid
+// overlap the previous one.
+#define ART_PDL_ENTRY()                                        \
+  do {                                                         \
+    asm volatile("griddepcontrol.wait;" ::: "memory");         \
+    asm volatile("griddepcontrol.launch_dependents;" :::);     \
+  } while (0)
+
 // A launch that may overlap the tail of the previous kernel of the stream
 // (programmatic dependent launch): the kernel itself waits (griddepcontrol)
 // before it reads or writes memory the previous kernel touches.

@@ -36,6 +36,7 @@ __device__ void rodrigues(const float* r, float* R) {
 // skel: J parent indices stored as floats, then rest[J][3]; pose: r[J][3], R[3], T[3].
 __global__ void __launch_bounds__(kMaxJoints) fk_kernel(int J, const float* __restrict__ skel,
                                                         const float* __restrict__ pose, float* __restrict__ G) {
+  ART_PDL_ENTRY();
   __shared__ float sL[kMaxJoints][12];
   __shared__ float sM[kMaxJoints][12];
   __shared__ int sp[kMaxJoints];
@@ -115,6 +116,7 @@ __global__ void __launch_bounds__(256) lbs_kernel(int64_t n, int J, const float*
                                                   const float4* __restrict__ wts, const float* __restrict__ sigma,
                                                   float ox, float oy, float oz, float h, float4* __restrict__ rec,
                                                   float4* __restrict__ geo, unsigned long long* __restrict__ status) {
+  ART_PDL_ENTRY();
   __shared__ float4 sG[kMaxJoints * 3];  // G_j as three float4 rows
   __shared__ float4 s_out[2][8][32 * 4];  // per warp: the 32 voxels' records and bounds
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -320,6 +322,7 @@ __global__ void __launch_bounds__(256) project_kernel(int64_t n, const float4* _
                                                       uint32_t* __restrict__ tcount,
                                                       unsigned long long* __restrict__ scan_state, int scan_words,
                                                       unsigned long long* __restrict__ status) {
+  ART_PDL_ENTRY();
   if (blockIdx.x == 0) {
     for (int k = threadIdx.x; k < scan_words; k += blockDim.x) scan_state[k] = 0ull;
     if (threadIdx.x == 0) {
@@ -400,6 +403,7 @@ __device__ __forceinline__ int64_t grid_slot(unsigned long long* keys, int64_t m
 __global__ void __launch_bounds__(256) grid_insert_kernel(int64_t n, const float4* __restrict__ rec, float ox, float oy,
                                                          float oz, float inv_h, unsigned long long* __restrict__ keys,
                                                          uint32_t* __restrict__ vals, int64_t mask) {
+  ART_PDL_ENTRY();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const float4* r = rec + 4 * i;
@@ -418,6 +422,7 @@ __global__ void __launch_bounds__(256) grid_rewrite_kernel(int64_t n, float4* __
                                                           const unsigned long long* __restrict__ keys,
                                                           const uint32_t* __restrict__ vals, int64_t mask,
                                                           unsigned long long* __restrict__ status) {
+  ART_PDL_ENTRY();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   bool survive = false;
   if (i < n) {
@@ -458,18 +463,18 @@ void launch_grid_snap(art_ctx* ctx) {
   cudaMemsetAsync(ctx->d_gkeys, 0xFF, sizeof(unsigned long long) * (size_t)ctx->grid_slots, ctx->stream);
   cudaMemsetAsync(ctx->d_gvals, 0xFF, sizeof(uint32_t) * (size_t)ctx->grid_slots, ctx->stream);
   cudaMemsetAsync(ctx->d_status + kStGridCells, 0, sizeof(unsigned long long), ctx->stream);
-  ART_LAUNCH(ctx, "grid_insert", grid_insert_kernel, grid, 256, 0, n, ctx->d_rec, ctx->origin[0], ctx->origin[1],
+  ART_LAUNCH_PDL(ctx, "grid_insert", grid_insert_kernel, grid, 256, 0, n, ctx->d_rec, ctx->origin[0], ctx->origin[1],
              ctx->origin[2], 1.0f / ctx->h, ctx->d_gkeys, ctx->d_gvals, mask);
-  ART_LAUNCH(ctx, "grid_rewrite", grid_rewrite_kernel, grid, 256, 0, n, ctx->d_rec, ctx->d_geo, ctx->origin[0],
+  ART_LAUNCH_PDL(ctx, "grid_rewrite", grid_rewrite_kernel, grid, 256, 0, n, ctx->d_rec, ctx->d_geo, ctx->origin[0],
              ctx->origin[1], ctx->origin[2], ctx->h, ctx->d_gkeys, ctx->d_gvals, mask, ctx->d_status);
 }
 
-void launch_fk(art_ctx* ctx) { ART_LAUNCH(ctx, "fk", fk_kernel, 1, kMaxJoints, 0, ctx->J, ctx->d_skel, ctx->d_pose, ctx->d_G); }
+void launch_fk(art_ctx* ctx) { ART_LAUNCH_PDL(ctx, "fk", fk_kernel, 1, kMaxJoints, 0, ctx->J, ctx->d_skel, ctx->d_pose, ctx->d_G); }
 
 void launch_lbs(art_ctx* ctx) {
   int64_t n = ctx->n;
   unsigned grid = (unsigned)((n + 255) / 256);
-  ART_LAUNCH(ctx, "lbs", lbs_kernel, grid, 256, 0, n, ctx->J, ctx->d_G, ctx->d_ijk, ctx->d_jidx, ctx->d_w,
+  ART_LAUNCH_PDL(ctx, "lbs", lbs_kernel, grid, 256, 0, n, ctx->J, ctx->d_G, ctx->d_ijk, ctx->d_jidx, ctx->d_w,
              ctx->d_sigma, ctx->origin[0], ctx->origin[1], ctx->origin[2], ctx->h, ctx->d_rec, ctx->d_geo,
              ctx->d_status);
 }
@@ -479,7 +484,7 @@ void launch_project_view(art_ctx* ctx, const ViewParams& v, short4* rect, uint32
   const int64_t n = ctx->n;
   const unsigned grid = (unsigned)((n + 255) / 256);
   const int words = first ? (int)tile_scan_state_words(ctx->ranges_cap) : 0;
-  ART_LAUNCH(ctx, "project", project_kernel, grid, 256, 0, n, ctx->d_geo, v, rect, q, cnt, ctx->d_sigma,
+  ART_LAUNCH_PDL(ctx, "project", project_kernel, grid, 256, 0, n, ctx->d_geo, v, rect, q, cnt, ctx->d_sigma,
              (uint32_t*)nullptr, (float*)nullptr, tcount, ctx->d_scan_state, words, ctx->d_status);
 }
 
@@ -488,7 +493,7 @@ void launch_project(art_ctx* ctx, const ViewParams& v, uint32_t* hbin, float* ht
   unsigned grid = (unsigned)((n + 255) / 256);
   const int ntiles = v.tiles_x * v.tiles_y;
   cudaMemsetAsync(ctx->d_tcount, 0, sizeof(uint32_t) * (size_t)ntiles, ctx->stream);
-  ART_LAUNCH(ctx, "project", project_kernel, grid, 256, 0, n, ctx->d_geo, v, ctx->d_rect, ctx->d_q, ctx->d_cnt,
+  ART_LAUNCH_PDL(ctx, "project", project_kernel, grid, 256, 0, n, ctx->d_geo, v, ctx->d_rect, ctx->d_q, ctx->d_cnt,
              ctx->d_sigma, hbin, htau, ctx->d_tcount, ctx->d_scan_state, (int)tile_scan_state_words(ntiles),
              ctx->d_status);
 }

@@ -69,6 +69,7 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 // threads share an output (k = q, q + 4, ...), summed in a fixed order.
 __global__ void __launch_bounds__(256) pose_bias_kernel(const float* __restrict__ f32, const float* __restrict__ pose,
                                                         float* __restrict__ out) {
+  ART_PDL_ENTRY();
   __shared__ float sx[kPoseIn];
   const int j = threadIdx.x >> 2, q = threadIdx.x & 3;
   float w[kPoseIn / 4];  // this thread's weights, loaded together
@@ -85,6 +86,7 @@ __global__ void __launch_bounds__(256) pose_bias_kernel(const float* __restrict_
 }
 
 __global__ void __launch_bounds__(128) proposal_kernel(PropParams p) {
+  ART_PDL_ENTRY();
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   uint8_t* sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
@@ -281,7 +283,7 @@ art_status load_proposal(art_ctx* ctx, const float* params) {
 }
 
 void launch_pose_bias(art_ctx* ctx) {
-  ART_LAUNCH(ctx, "proposal_pose_bias", pose_bias_kernel, 1, 256, 0, ctx->d_prop_f32, ctx->d_pose, ctx->d_pose_bias);
+  ART_LAUNCH_PDL(ctx, "proposal_pose_bias", pose_bias_kernel, 1, 256, 0, ctx->d_prop_f32, ctx->d_pose, ctx->d_pose_bias);
 }
 
 // Tiles whose walk the proposal cannot change (learned skip).  From a tile's
@@ -305,6 +307,7 @@ __global__ void __launch_bounds__(128) tile_class_kernel(ViewParams v, const uin
                                                         unsigned long long* __restrict__ status, float max_missed,
                                                         uint8_t* __restrict__ tclass, uint32_t* __restrict__ pgroups,
                                                         uint8_t* __restrict__ bins) {
+  ART_PDL_ENTRY();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned long long n_groups = status[kStActiveGroups];
   const int ntiles = v.tiles_x * v.tiles_y;
@@ -354,7 +357,7 @@ __global__ void __launch_bounds__(128) tile_class_kernel(ViewParams v, const uin
 void launch_tile_class(art_ctx* ctx, const ViewParams& v, uint8_t* bins) {
   cudaMemsetAsync(ctx->d_status + kStPredGroups, 0, 2 * sizeof(unsigned long long), ctx->stream);
   const int ngroups = (v.tiles_x * v.tiles_y + 3) / 4;
-  ART_LAUNCH(ctx, "tile_class", tile_class_kernel, std::max(1, std::min(ngroups, 8 * ctx->num_sms)), 128, 0, v,
+  ART_LAUNCH_PDL(ctx, "tile_class", tile_class_kernel, std::max(1, std::min(ngroups, 8 * ctx->num_sms)), 128, 0, v,
              ctx->d_ranges, ctx->d_thist, ctx->d_agroups, ctx->d_status, ctx->cfg.max_missed, ctx->d_tclass,
              ctx->d_pgroups, bins);
 }
@@ -382,7 +385,7 @@ art_status launch_proposal(art_ctx* ctx, const ViewParams& v, uint8_t* bins, flo
   p.logits = logits;
   p.err = ctx->d_status + kStTcError;
   const int grid = std::min(p.ngroups, 3 * ctx->num_sms);
-  ART_LAUNCH(ctx, "proposal_mlp", proposal_kernel, grid, 128, kSmem, p);
+  ART_LAUNCH_PDL(ctx, "proposal_mlp", proposal_kernel, grid, 128, kSmem, p);
   return ART_OK;
 }
 

@@ -412,6 +412,7 @@ static __global__ void seg_plan_kernel(int ntiles, const uint2* __restrict__ ran
                                 uint32_t* __restrict__ items, uint32_t* __restrict__ multi,
                                 unsigned long long* __restrict__ status, const uint32_t* __restrict__ tiles_in,
                                 int in_word) {
+  ART_PDL_ENTRY();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   int t = i;
   if (tiles_in) {
