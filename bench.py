@@ -258,9 +258,12 @@ def roofline(kt, stats, peaks, form, n_vox, C, frames, conv_launch_ms=None):
             peak, bound, note = 2.0 * bf16, "tensor", f"{src} {kind} BF16 x 2 (nominal FP8 / BF16 ratio)"
         else:
             peak, bound, note = bf16, "tensor", f"{src} {kind} BF16"
-        # DRAM bytes per launch of the BF16 convolutions, from one ncu capture of a frame's 14 launches
-        # DRAM reads + writes of the 14 launches of one frame from an ncu capture (cold cache): 931.6 MB
-        traffic = 931.6e6 / 14 if net == "bf16" else None
+        # DRAM reads + writes per launch of the BF16 convolutions from the committed ncu capture
+        # (paper_2202_05628_gb300/profile_capture.py), while it matches the current sources
+        traffic = None
+        if net == "bf16":
+            from paper_2202_05628_gb300.profile_capture import committed_traffic
+            traffic = committed_traffic()
         out.update(bound=bound, achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak, traffic=traffic, peak_is=note)
     else:
         fb = 2 if storage == "bf16" else 4
@@ -274,6 +277,31 @@ def roofline(kt, stats, peaks, form, n_vox, C, frames, conv_launch_ms=None):
         out.update(bound="hbm", achieved=ach, peak=peak, unit="GB/s", frac=ach / peak, traffic=None,
                    peak_is=("measured" if "hbm_gbs" in peaks else "fallback") + " copy bandwidth")
     return out
+
+
+COMPOSITE_KERNELS = ("composite", "composite_skip", "composite_merge", "composite_refill", "composite_clear",
+                     "composite_plan", "composite_replan", "composite_fallback", "composite_exact")
+
+
+def composite_roofline(kt, stats, peaks, form, C, frames):
+    """The composite stage as one unit: the summed per-frame time of its
+    kernels (interval / plain walk, merge, refill, clear, plans, fallback and
+    exact walks) against its algorithmic bytes per frame: per instance the
+    key and value (8 B), the 64-B voxel record, the 8-B pixel rectangle and
+    the feature row (C x 2 B BF16 / 4 B FP32), each read once; per pixel the
+    F row and A written once."""
+    storage = FORMS[form][0]
+    fb = 2 if storage == "bf16" else 4
+    ms = sum(kt[k][1] for k in COMPOSITE_KERNELS if k in kt) / max(frames, 1)
+    if ms <= 0:
+        return None
+    byts = stats["instances"] * (8 + 64 + 8 + C * fb) + RES * RES * (C * fb + 4)
+    ach = byts / (ms * 1e-3) / 1e9
+    peak = peaks.get("hbm_gbs", 6800.0)
+    return {"kernels": [k for k in COMPOSITE_KERNELS if k in kt], "ms_per_frame": ms, "bytes_per_frame": byts,
+            "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "peak_is": ("measured" if "hbm_gbs" in peaks else "fallback") + " copy bandwidth",
+            "note": "per-kernel CUDA-event times of the second timed pass (events add gaps between launches)"}
 
 
 def unet_flops(H, W, cin=32, ch=(32, 64, 128, 256)):
@@ -616,6 +644,7 @@ def gpu_arm(args):
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
         "roofline": roofline(kt, stats, peaks, args.form, oc.n, oc.C, args.steps, conv_launch_ms),
+        "composite_roofline": composite_roofline(kt, stats, peaks, args.form, oc.C, args.steps) if kt else None,
         "kernels_ms_per_frame": {k: round(v[1] / args.steps, 4) for k, v in sorted(kt.items(), key=lambda kv: -kv[1][1])},
         "kernel_events": "second timed pass over the same frames (per-kernel events slow the frame)",
         "instances": stats["instances"], "overflow": stats["status"],
@@ -676,7 +705,7 @@ def gpu_arm(args):
     torch.cuda.synchronize()
     result["sh_features"] = {"ms_per_call": float(np.mean([a.elapsed_time(b) for a, b in sev])), "degree": sh_deg,
                              "what": "art_render_feature_maps of one 1024^2 view with SH features: projection, "
-                                     "binning, one warp per tile evaluating each hit's harmonics"}
+                                     "binning, the split walk evaluating each hit's harmonics"}
     r.load_sh_features(-1)
     del coef
     r.close()

@@ -713,8 +713,8 @@ __global__ void __launch_bounds__(32) composite_merge_views_kernel(const ViewSet
   }
 }
 
-// The plain walk over the tiles queued by the learned-skip pass.
-template <int C, typename TF, typename TO>
+// The sequential walk over queued tiles (plain, or with SH features).
+template <int C, typename TF, typename TO, int MODE>
 __global__ void __launch_bounds__(32) composite_queue_kernel(const uint2* __restrict__ ranges,
                                                              const uint32_t* __restrict__ keys,
                                                              const uint32_t* __restrict__ vals,
@@ -724,19 +724,16 @@ __global__ void __launch_bounds__(32) composite_queue_kernel(const uint2* __rest
                                                              TO* __restrict__ Fout, float* __restrict__ Aout,
                                                              unsigned long long* __restrict__ status,
                                                              const uint32_t* __restrict__ queue, int qword,
-                                                             uint32_t* __restrict__ xflag,
-                                                             uint32_t* __restrict__ xqueue) {
+                                                             SkipArgs sk_in) {
   ART_PDL_ENTRY();
   const unsigned long long n = status[qword];
   for (unsigned long long i = blockIdx.x; i < n; i += gridDim.x) {
     const int tile = (int)queue[i];
     const uint2 rg = ranges[tile];
     const Seg sg{rg.x, rg.y, -3.4e38f, 3.4e38f, nullptr};
-    SkipArgs sk{};
-    sk.xflag = xflag;
-    sk.xqueue = xqueue;
+    SkipArgs sk = sk_in;
     sk.gtile = tile;
-    composite_tile<C, TF, TO, kPlain>(tile, sg, keys, vals, rec, rect, feat, v, tau, Fout, Aout, status, HitLog{}, sk);
+    composite_tile<C, TF, TO, MODE>(tile, sg, keys, vals, rec, rect, feat, v, tau, Fout, Aout, status, HitLog{}, sk);
   }
 }
 
@@ -939,8 +936,10 @@ void split_pass(art_ctx* ctx, const ViewParams& v, void* F, float* A, int mode, 
   const int ntiles = v.tiles_x * v.tiles_y;
   const TF* feat = (const TF*)ctx->d_feat;
   SkipArgs sk = sk_in;
-  sk.xflag = ctx->d_xflag;
-  sk.xqueue = ctx->d_xqueue;
+  if (mode != kSH) {  // the exact re-walk composites stored feature rows: not for SH features
+    sk.xflag = ctx->d_xflag;
+    sk.xqueue = ctx->d_xqueue;
+  }
   cudaMemsetAsync(ctx->d_status + kStItems, 0, 4 * sizeof(unsigned long long), ctx->stream);  // items .. next merge
   cudaMemsetAsync(ctx->d_status + sk.qword, 0, sizeof(unsigned long long), ctx->stream);
   // a re-walk covers a few tiles: shorter segments put more warps on them
@@ -960,6 +959,14 @@ void split_pass(art_ctx* ctx, const ViewParams& v, void* F, float* A, int mode, 
     auto mfn = composite_merge_kernel<C, TO, kInterval>;
     ART_LAUNCH_PDL(ctx, "composite_merge", mfn, 32 * ctx->num_sms, 32, 0, ctx->d_seg, ctx->d_multi, v, ctx->cfg.tau, (TO*)F,
                A, ctx->d_status, ctx->d_part, sk);
+  } else if (mode == kSH) {
+    auto kfn = composite_split_kernel<C, TF, TO, kSH>;
+    ART_LAUNCH_PDL(ctx, "composite_sh", kfn, grid, 32, 0, ctx->d_ranges, ctx->d_seg, ctx->d_items, ctx->d_keys,
+                   ctx->d_vals, ctx->d_rec, ctx->d_rect, feat, v, ctx->cfg.tau, (TO*)F, A, ctx->d_status, ctx->d_part,
+                   sk);
+    auto mfn = composite_merge_kernel<C, TO, kPlain>;
+    ART_LAUNCH_PDL(ctx, "composite_merge", mfn, 32 * ctx->num_sms, 32, 0, ctx->d_seg, ctx->d_multi, v, ctx->cfg.tau,
+                   (TO*)F, A, ctx->d_status, ctx->d_part, sk);
   } else {
     auto kfn = composite_split_kernel<C, TF, TO, kPlain>;
     ART_LAUNCH_PDL(ctx, list ? "composite_refill" : "composite", kfn, grid, 32, 0, ctx->d_ranges, ctx->d_seg, ctx->d_items,
@@ -995,11 +1002,20 @@ void split_walk(art_ctx* ctx, const ViewParams& v, void* F, float* A, int mode, 
     seq = ctx->d_fbq2;
     seq_word = kStFallback2;
   }
-  auto qfn = composite_queue_kernel<C, TF, TO>;
   const int qgrid = std::min(ntiles, 16 * ctx->num_sms);
+  SkipArgs sq{};
+  if (mode == kSH) {  // the stop cases of SH features: their sequential walk evaluates the harmonics
+    sq = sk_in;
+    auto qfn = composite_queue_kernel<C, TF, TO, kSH>;
+    ART_LAUNCH_PDL(ctx, "composite_fallback", qfn, qgrid, 32, 0, ctx->d_ranges, ctx->d_keys, ctx->d_vals, ctx->d_rec,
+                   ctx->d_rect, feat, v, ctx->cfg.tau, (TO*)F, A, ctx->d_status, seq, seq_word, sq);
+    return;
+  }
+  sq.xflag = ctx->d_xflag;
+  sq.xqueue = ctx->d_xqueue;
+  auto qfn = composite_queue_kernel<C, TF, TO, kPlain>;
   ART_LAUNCH_PDL(ctx, "composite_fallback", qfn, qgrid, 32, 0, ctx->d_ranges, ctx->d_keys, ctx->d_vals, ctx->d_rec,
-             ctx->d_rect, feat, v, ctx->cfg.tau, (TO*)F, A, ctx->d_status, seq, seq_word, ctx->d_xflag,
-             ctx->d_xqueue);
+             ctx->d_rect, feat, v, ctx->cfg.tau, (TO*)F, A, ctx->d_status, seq, seq_word, sq);
   auto xfn = composite_exact_kernel<C, TF, TO, false>;
   ART_LAUNCH_PDL(ctx, "composite_exact", xfn, kExactBlocks, 32, 0, (const ViewSet*)nullptr, v, (TO*)F, A, ctx->d_ranges,
              ctx->d_keys, ctx->d_vals, ctx->d_rec, ctx->d_rect, feat, ctx->cfg.tau, ctx->d_status, ctx->d_xqueue,
@@ -1017,10 +1033,6 @@ void launch_c(art_ctx* ctx, const ViewParams& v, void* F, float* A, const HitLog
   } else if (mode == kLabel) {
     auto kfn = composite_kernel<C, TF, TO, kLabel>;
     ART_LAUNCH(ctx, "composite_labels", kfn, ntiles, 32, 0, ctx->d_ranges, ctx->d_keys, ctx->d_vals, ctx->d_rec,
-               ctx->d_rect, feat, v, ctx->cfg.tau, (TO*)F, A, ctx->d_status, HitLog{}, sk);
-  } else if (mode == kSH) {  // sequential walk, one warp per tile
-    auto kfn = composite_kernel<C, TF, TO, kSH>;
-    ART_LAUNCH(ctx, "composite_sh", kfn, ntiles, 32, 0, ctx->d_ranges, ctx->d_keys, ctx->d_vals, ctx->d_rec,
                ctx->d_rect, feat, v, ctx->cfg.tau, (TO*)F, A, ctx->d_status, HitLog{}, sk);
   } else {
     split_walk<C, TF, TO>(ctx, v, F, A, mode, sk);
