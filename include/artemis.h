@@ -120,12 +120,18 @@ art_status art_load_skeleton(art_ctx* ctx, int J, const int32_t* parent, const f
 art_status art_set_pose(art_ctx* ctx, const float* axis_angle, const float R[3], const float T[3]);
 
 /*
- * Set camera `view` (0 .. 7): pinhole with intrinsics fx, fy, cx, cy in
- * pixels, world_to_cam[12] the 3x4 row-major [R | t] (x_cam = R x + t; +x
+ * Set camera `view` (0 .. 7): the camera whose pixel rays are cast through
+ * the warped volume (Sec. 3.1 "Dynamic Volume Rendering": a ray per pixel,
+ * composited front to back, Eq. 5-6).  Pinhole with intrinsics fx, fy, cx, cy
+ * in pixels, world_to_cam[12] the 3x4 row-major [R | t] (x_cam = R x + t; +x
  * right, +y down, +z forward), image W x H (1 .. 8192 each).  Pixel (x, y) is
  * sampled at its centre; its ray is o = -R^T t, d = R^T dc / |R^T dc| with
  * dc = ((x+1/2-cx)/fx, (y+1/2-cy)/fy, 1).  znear < zfar are distances along
- * the unit ray.
+ * the unit ray.  world_to_cam may be host or device memory (copied); the
+ * call is synchronous with respect to the host.  Errors: ART_ERR_INVALID_ARG
+ * for a view out of range, sizes out of range, non-positive focal lengths or
+ * znear >= zfar; ART_ERR_UNSUPPORTED when the image has too many screen
+ * tiles for the 32-bit depth keys.
  */
 art_status art_set_camera(art_ctx* ctx, int view, int W, int H, float fx, float fy, float cx, float cy,
                           const float world_to_cam[12], float znear, float zfar);

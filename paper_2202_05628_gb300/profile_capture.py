@@ -18,6 +18,7 @@ import csv
 import hashlib
 import io
 import os
+import re
 import subprocess
 import sys
 
@@ -76,11 +77,12 @@ def capture() -> None:
     text = res.stdout[res.stdout.index('"ID"'):]
     per = {}
     for row in csv.DictReader(io.StringIO(text)):
-        k = (int(row["ID"]), row["Kernel Name"].split("(")[0].split("<")[0])
+        m = re.search(r"(\w+_kernel)", row["Kernel Name"])  # the kernel, without namespace and arguments
+        k = (int(row["ID"]), m.group(1) if m else row["Kernel Name"][:40])
         v = float(row["Metric Value"].replace(",", ""))
-        unit = row["Metric Unit"]
-        scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "nsecond": 1e-3, "usecond": 1.0,
-                 "msecond": 1e3}.get(unit, 1.0)
+        unit = row["Metric Unit"].strip()
+        scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "nsecond": 1e-3, "ns": 1e-3,
+                 "usecond": 1.0, "us": 1.0, "msecond": 1e3, "ms": 1e3}.get(unit, 1.0)
         per.setdefault(k, {})[row["Metric Name"]] = v * scale
     rows = sorted(per.items())
     total = sum(m.get("dram__bytes_read.sum", 0) + m.get("dram__bytes_write.sum", 0) for _, m in rows)
