@@ -124,16 +124,95 @@ __device__ __forceinline__ void epi_row(const TcParams& p, uint32_t taddr, int y
   }
 }
 
+// Row-blocked epilogue, stores staged through shared memory.  A lane holds
+// its pixel's N output channels (U 16-byte chunks after packing to BF16 or
+// E4M3); written as they are, a warp store would put 32 16-byte pieces one
+// pixel stride apart (32 cache lines per instruction, four times over with
+// the 2x2 upsampling).  Instead the warp's 32 pixels are transposed through
+// a 32 x U chunk buffer (chunk k of pixel q at q U + (k ^ (q % U)), so that
+// neither the writes nor the reads conflict on banks) and stored U lanes per
+// pixel: each store instruction covers 32 / U whole pixel blocks.
+template <int N, bool F8>
+struct RowOut {
+  static constexpr int kEs = F8 ? 1 : 2;
+  static constexpr int U = N * kEs / 16;  // 16-byte chunks of one pixel's outputs
+};
+
+// Bias, ReLU, rounding (BF16, or E4M3 with the dequantisation and output
+// scales) of all N channels of this lane's pixel into pk.
+template <int N, bool F8>
+__device__ __forceinline__ void epi_pack(const TcParams& p, uint32_t taddr, const float* s_bias, const float* s_wsc,
+                                         float in_s, float out_inv, float& amax, bool valid,
+                                         uint4 (&pk)[RowOut<N, F8>::U]) {
+#pragma unroll
+  for (int c0 = 0; c0 < N; c0 += 32) {
+    uint32_t r[32];
+    tmem_ld32(taddr + (uint32_t)c0, r);
+    float v[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const float acc = F8 ? __uint_as_float(r[j]) * (in_s * s_wsc[c0 + j]) : __uint_as_float(r[j]);
+      const float t = acc + s_bias[c0 + j];
+      v[j] = p.act == 1 ? fmaxf(t, 0.0f) : t;
+    }
+    if constexpr (F8) {
+      uint16_t* w = reinterpret_cast<uint16_t*>(pk) + c0 / 2;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        if (valid) amax = fmaxf(amax, fmaxf(fabsf(v[2 * j]), fabsf(v[2 * j + 1])));  // pixels of the image only
+        w[j] = (uint16_t)__nv_cvt_float2_to_fp8x2(make_float2(v[2 * j] * out_inv, v[2 * j + 1] * out_inv),
+                                                  __NV_SATFINITE, __NV_E4M3);
+      }
+    } else {
+      uint32_t* w = reinterpret_cast<uint32_t*>(pk) + c0 / 2;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        __nv_bfloat162 b2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+        w[j] = *reinterpret_cast<uint32_t*>(&b2);
+      }
+    }
+  }
+}
+
+// The warp's 32 pixels of output row y, x0 .. x0 + 31 (this lane: x0 + lane),
+// through the staging buffer stage[32 U] into channels [ch_off, ch_off + N)
+// of the ld_out-channel output (with up2: its 2x2 block of the 2H x 2W
+// output).
+template <int N, bool F8>
+__device__ __forceinline__ void store_staged(const TcParams& p, int y, int x0, int lane,
+                                             const uint4 (&pk)[RowOut<N, F8>::U], uint4* stage) {
+  constexpr int U = RowOut<N, F8>::U;
+  constexpr int kEs = RowOut<N, F8>::kEs;
+#pragma unroll
+  for (int k = 0; k < U; ++k) stage[lane * U + (k ^ (lane % U))] = pk[k];
+  __syncwarp();
+  uint8_t* outb = reinterpret_cast<uint8_t*>(p.out);
+  const int nd = p.up2 ? 4 : 1;
+  const int Wd = p.up2 ? 2 * p.W : p.W;
+  for (int d = 0; d < nd; ++d) {
+#pragma unroll
+    for (int i = 0; i < U; ++i) {
+      const int f = i * 32 + lane, q = f / U, c = f % U;
+      const int x = x0 + q;
+      if (x < p.W) {
+        const int X = p.up2 ? 2 * x + (d & 1) : x, Y = p.up2 ? 2 * y + (d >> 1) : y;
+        uint4* dst = reinterpret_cast<uint4*>(outb + (((size_t)Y * Wd + X) * p.ld_out + p.ch_off) * kEs) + c;
+        *dst = stage[q * U + (c ^ (q % U))];
+      }
+    }
+  }
+  __syncwarp();
+}
+
 // Epilogue of one output row of the row-blocked kernel with the 2x2 max
-// pooling fused: the row is stored as by epi_row (BF16, no upsampling), and
-// its packed values are kept (first row of a pair) or pooled with the kept
+// pooling fused: the row's packed values are returned for the staged store
+// (BF16, no upsampling), and kept (first row of a pair) or pooled with the kept
 // row and the neighbouring pixel's lane (second row), the pooled pixel stored
 // by the even lane.  Max and BF16 rounding commute, so this equals pooling
 // the stored tensor.
 template <int N>
 __device__ __forceinline__ void epi_row_pool(const TcParams& p, uint32_t taddr, int y, int x, const float* s_bias,
-                                             uint32_t (&keep)[N / 2], bool second) {
-  const bool valid = x < p.W;
+                                             uint32_t (&keep)[N / 2], bool second, uint4 (&pk_all)[N / 8]) {
 #pragma unroll
   for (int c0 = 0; c0 < N; c0 += 32) {
     uint32_t r[32];
@@ -151,12 +230,8 @@ __device__ __forceinline__ void epi_row_pool(const TcParams& p, uint32_t taddr, 
       __nv_bfloat162 b2 = __floats2bfloat162_rn(t0, t1);
       w[j] = *reinterpret_cast<uint32_t*>(&b2);
     }
-    if (valid) {
-      uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(p.out) +
-                                            ((size_t)y * p.W + x) * p.ld_out + p.ch_off + c0);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) dst[k] = pk[k];
-    }
+    for (int k = 0; k < 4; ++k) pk_all[c0 / 8 + k] = pk[k];  // the row itself: stored staged by the caller
     if (!second) {
 #pragma unroll
       for (int j = 0; j < 16; ++j) keep[c0 / 2 + j] = w[j];
@@ -405,6 +480,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   float* s_bias = reinterpret_cast<float*>(tmem_slot + 4);
   float* s_head = s_bias + N;
   float* s_wsc = s_head + 4 * 32 + 4;  // FP8 per-output-channel weight scales
+  // epilogue store staging: 32 pixels x U chunks per epilogue warp (16-B aligned)
+  uint4* s_stage = reinterpret_cast<uint4*>((reinterpret_cast<uintptr_t>(s_wsc + N) + 15) & ~(uintptr_t)15);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int cpt = rp.cpt;
@@ -547,10 +624,20 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int slot = kRows - 1 - r;
         const uint32_t ta = tq + (uint32_t)(buf * Cfg::kBufCols + slot * N);
         if (y0 + r < p.H) {
-          if (!F8 && p.pool)
-            epi_row_pool<N>(p, ta, y0 + r, x, s_bias, keep, (r & 1) != 0);
-          else
-            epi_row<N, F8>(p, ta, y0 + r, x, s_bias, s_head, s_wsc, in_s, out_inv, amax);
+          uint4* stg = s_stage + (warp - 2) * 32 * RowOut<N, F8>::U;
+          const int xw = (u % p.tiles_per_row) * 128 + qd * 32;  // this warp's first pixel
+          if (p.rgba) {
+            epi_row<N, F8>(p, ta, y0 + r, x, s_bias, s_head, s_wsc, in_s, out_inv, amax);  // coalesced already
+          } else if constexpr (!F8) {
+            uint4 pk[RowOut<N, false>::U];
+            if (p.pool)
+              epi_row_pool<N>(p, ta, y0 + r, x, s_bias, keep, (r & 1) != 0, pk);
+            else
+              epi_pack<N, false>(p, ta, s_bias, s_wsc, in_s, out_inv, amax, x < p.W, pk);
+            store_staged<N, false>(p, y0 + r, xw, lane, pk, stg);
+          } else {  // E4M3 rows are 32 or 64 bytes: stored directly (staging measured slower)
+            epi_row<N, true>(p, ta, y0 + r, x, s_bias, s_head, s_wsc, in_s, out_inv, amax);
+          }
         }
 #pragma unroll
         for (int c0 = 0; c0 < N; c0 += 32) tmem_zero32(ta + (uint32_t)c0);
@@ -768,7 +855,7 @@ art_status launch_rows(art_ctx* ctx, const TcConv& c) {
   rp.cpt = c.cin / Cfg::KC;
   rp.n_units = ((c.H + kRows - 1) / kRows) * p.tiles_per_row;
   rp.w_bytes = 9 * rp.cpt * N * KCB;
-  const int tail = 8 * (2 * 24 + 5) + 16 + 4 * N + 4 * (4 * 32 + 4) + 4 * N;
+  const int tail = 8 * (2 * 24 + 5) + 16 + 4 * N + 4 * (4 * 32 + 4) + 4 * N + 16 + (F8 ? 0 : 4 * 32 * 16 * RowOut<N, F8>::U);
   // two CTAs per SM (two issuing threads, one accumulator buffer each) when
   // the resident weights and three stages fit in half the shared memory
   const int half = 232448 / 2 - 1024 - rp.w_bytes - tail;
