@@ -46,6 +46,33 @@ struct TcParams {
   unsigned long long* err;
 };
 
+// One 32-channel BF16 group (64 B per pixel) of the warp's 32 pixels of
+// output row y (this lane: x0 + lane), staged through stage[32 x 4] (chunk k
+// of pixel q at 4 q + (k ^ (q % 4))) and stored four lanes per pixel into
+// channels [ch_off + c0, + 32) (with up2: the pixel's 2x2 block).
+__device__ __forceinline__ void store_staged_group(const TcParams& p, int y, int x0, int lane, int c0,
+                                                   const uint4 (&pk)[4], uint4* stage) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) stage[lane * 4 + (k ^ (lane & 3))] = pk[k];
+  __syncwarp();
+  __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(p.out);
+  const int nd = p.up2 ? 4 : 1;
+  const int Wd = p.up2 ? 2 * p.W : p.W;
+  for (int d = 0; d < nd; ++d) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int f = i * 32 + lane, q = f >> 2, c = f & 3;
+      const int x = x0 + q;
+      if (x < p.W) {
+        const int X = p.up2 ? 2 * x + (d & 1) : x, Y = p.up2 ? 2 * y + (d >> 1) : y;
+        uint4* dst = reinterpret_cast<uint4*>(out + ((size_t)Y * Wd + X) * p.ld_out + p.ch_off + c0) + c;
+        *dst = stage[q * 4 + (c ^ (q & 3))];
+      }
+    }
+  }
+  __syncwarp();
+}
+
 // Epilogue of one 128-pixel output row segment: this thread's pixel x of
 // row y; the accumulator's N columns start at TMEM address taddr (lane
 // quarter included).  Bias, ReLU, then BF16 / E4M3 store (optionally 2x2
@@ -53,7 +80,7 @@ struct TcParams {
 template <int N, bool F8>
 __device__ __forceinline__ void epi_row(const TcParams& p, uint32_t taddr, int y, int x, const float* s_bias,
                                         const float* s_head, const float* s_wsc, float in_s, float out_inv,
-                                        float& amax) {
+                                        float& amax, uint4* stage = nullptr, int x0 = 0, int lane = 0) {
   const bool valid = x < p.W;
 #pragma unroll 1
   for (int c0 = 0; c0 < N; c0 += 32) {
@@ -65,6 +92,17 @@ __device__ __forceinline__ void epi_row(const TcParams& p, uint32_t taddr, int y
       const float acc = F8 ? __uint_as_float(r[j]) * (in_s * s_wsc[c0 + j]) : __uint_as_float(r[j]);
       const float t = acc + s_bias[c0 + j];
       v[j] = p.act == 1 ? fmaxf(t, 0.0f) : t;
+    }
+    if (!F8 && stage && !p.rgba) {  // BF16 group staged: the warp stores 8 pixels x 64 B per instruction
+      uint4 pk[4];
+      uint32_t* w = reinterpret_cast<uint32_t*>(pk);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        __nv_bfloat162 b2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+        w[j] = *reinterpret_cast<uint32_t*>(&b2);
+      }
+      store_staged_group(p, y, x0, lane, c0, pk, stage);
+      continue;
     }
     if (!valid) continue;
     if (p.rgba) {  // fused 1x1 head (N == 32) + sigmoid -> head_n FP32 channels of the output
@@ -272,11 +310,13 @@ struct TcCfg {
                                      | (kFmt << 7) | (kFmt << 10)       // A, B formats
                                      | ((uint32_t)(N >> 3) << 17)       // N / 8
                                      | ((uint32_t)(128 >> 4) << 24);    // M / 16
-  static constexpr int kSmem = kStages * kStage + 1024 + 8 * (2 * kStages + 4) + 16 + 4 * N + 4 * (4 * 32 + 4) + 4 * N;
+  static constexpr int kStageBuf = F8 ? 0 : 4 * 32 * 4 * 16;  // BF16 epilogue staging: 4 warps x 32 pixels x 64 B
+  static constexpr int kSmem =
+      kStages * kStage + 1024 + 8 * (2 * kStages + 4) + 16 + 4 * N + 4 * (4 * 32 + 4) + 4 * N + 16 + kStageBuf;
 };
 
 template <int N, int KCB, bool F8>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, TcCfg<N, KCB, F8>::kCtas)
     conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcParams p) {
   using Cfg = TcCfg<N, KCB, F8>;
   constexpr int KC = F8 ? KCB : KCB / 2;  // channels per K chunk
@@ -293,6 +333,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   float* s_bias = reinterpret_cast<float*>(tmem_slot + 4);
   float* s_head = s_bias + N;
   float* s_wsc = s_head + 4 * 32 + 4;  // FP8 per-output-channel weight scales
+  uint4* s_stage = reinterpret_cast<uint4*>((reinterpret_cast<uintptr_t>(s_wsc + N) + 15) & ~(uintptr_t)15);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int cpt = p.cin / KC;  // K chunks per tap
@@ -399,7 +440,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc_fence_after();
       const int y = tile / p.tiles_per_row, x = (tile % p.tiles_per_row) * 128 + m;
       epi_row<N, F8>(p, tmem_base + ((uint32_t)(qd * 32) << 16) + (uint32_t)(buf * N), y, x, s_bias, s_head, s_wsc,
-                     in_s, out_inv, amax);
+                     in_s, out_inv, amax, F8 ? nullptr : s_stage + (warp - 2) * 32 * 4, x - lane, lane);
       tc_fence_before();
       mbar_arrive(&acce[buf]);
       if (++buf == 2) {
@@ -460,7 +501,7 @@ struct RowParams {
 };
 
 template <int N, int KCB, bool F8>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, 2)
     conv_rows_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, RowParams rp) {
   using Cfg = RowCfg<N, KCB, F8>;
   const TcParams& p = rp.p;
@@ -859,13 +900,15 @@ art_status launch_rows(art_ctx* ctx, const TcConv& c) {
   // two CTAs per SM (two issuing threads, one accumulator buffer each) when
   // the resident weights and three stages fit in half the shared memory
   const int half = 232448 / 2 - 1024 - rp.w_bytes - tail;
-  const int ctas = half >= 3 * Cfg::kStageBytes ? 2 : 1;
+  auto kfn = conv_rows_kernel<N, KCB, F8>;
+  cudaFuncAttributes fa;
+  const bool regs2 = cudaFuncGetAttributes(&fa, kfn) == cudaSuccess && 2 * kThreads * fa.numRegs <= 65536;
+  const int ctas = (half >= 3 * Cfg::kStageBytes && regs2) ? 2 : 1;  // and both CTAs' registers fit
   const int avail = 232448 / ctas - 1024 - rp.w_bytes - tail;
   rp.nbuf = (ctas == 2 && Cfg::kBufCols > 128) ? 1 : 2;  // 512 TMEM columns per SM
   rp.n_stages = std::min(24, avail / Cfg::kStageBytes);
   if (rp.n_stages < 2) return fail(ctx, ART_ERR_UNSUPPORTED, "row-blocked conv: weights too large");
   const int smem = 1024 + rp.w_bytes + rp.n_stages * Cfg::kStageBytes + tail;
-  auto kfn = conv_rows_kernel<N, KCB, F8>;
   cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "conv_rows shared memory attribute");
   const int grid = std::min(rp.n_units, ctas * ctx->num_sms);
