@@ -354,7 +354,7 @@ def backward_timing(sc, cams, poses, layers, steps, flush, warmup=3):
             "what": "dL/df, dL/dsigma, dL/dw through the F and A maps, dense upstream gradient"}
 
 
-STEREO = (1920, 1080, 0.032)  # config 5: two 1920x1080 eyes, 6.4 cm baseline
+STEREO = (1920, 1080, 0.032)  # stereo VR pair: two 1920x1080 eyes, 6.4 cm baseline (camera offsets of +-3.2 cm)
 
 
 def stereo_cams(sc, az_index):

@@ -178,7 +178,7 @@ def test_backward_split_walk_matches_oracle(segment, tau):
              _tied_voxels(sc, pose, cams, gFs, gAs, tau=tau))
 
 
-def test_backward_config4_random_rays():
+def test_backward_200k_voxels_65536_random_rays():
     """200k voxels (C=16), 8 views at 512x512, MSE of F to a random target on
     65,536 random rays."""
     import torch
