@@ -202,6 +202,9 @@ void free_all(art_ctx* ctx) {
     cudaEventDestroy(t.e1);
   }
   for (auto e : ctx->free_events) cudaEventDestroy(e);
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+  if (ctx->side) cudaStreamDestroy(ctx->side);
 }
 
 art_config default_config() {
@@ -594,6 +597,40 @@ art_status art_set_camera(art_ctx* ctx, int view, int W, int H, float fx, float 
   return ART_OK;
 }
 
+// The side stream and its two events, made on first use.
+static art_status ensure_side(art_ctx* ctx) {
+  if (ctx->side) return ART_OK;
+  cudaError_t e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "side stream");
+  return ART_OK;
+}
+
+// After the scan and scatter of a view: the work that needs only the tile
+// ranges and the coarse bound (tile classes and proposal for the learned
+// skip, the clear of the empty tiles) runs on the side stream while the
+// bucket sort runs on the main one; the main stream then waits for both.
+static art_status sort_beside(art_ctx* ctx, const ViewParams& v, void* F, int F_dtype, float* A, bool skip) {
+  art_status st = ensure_side(ctx);
+  if (st != ART_OK) return st;
+  cudaStream_t main_stream = ctx->stream;
+  cudaEventRecord(ctx->ev_fork, main_stream);
+  cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
+  ctx->stream = ctx->side;
+  if (skip) {
+    launch_tile_class(ctx, v, ctx->d_bins);
+    st = launch_proposal(ctx, v, ctx->d_bins, nullptr, true, true);
+  }
+  if (st == ART_OK) st = launch_composite_clear(ctx, v, F, F_dtype, A);
+  cudaEventRecord(ctx->ev_join, ctx->side);
+  ctx->stream = main_stream;
+  launch_tile_sort(ctx, v);
+  cudaStreamWaitEvent(main_stream, ctx->ev_join, 0);
+  ctx->f_cleared = st == ART_OK;
+  return st;
+}
+
 static art_status render_to_device(art_ctx* ctx, int view, void* F, int F_dtype, float* A) {
   const ViewParams& v = ctx->views[view];
   art_status st = ensure_bin_buffers(ctx, (int64_t)v.tiles_x * v.tiles_y);
@@ -605,22 +642,27 @@ static art_status render_to_device(art_ctx* ctx, int view, void* F, int F_dtype,
     if (!ctx->prop_loaded) return fail(ctx, ART_ERR_STATE, "learned skip without a proposal (art_load_proposal)");
     if ((st = ensure_skip_buffers(ctx, v)) != ART_OK) return st;
     launch_project(ctx, v, ctx->d_hbin, ctx->d_htau);
-    launch_bin(ctx, v, ctx->d_hbin, ctx->d_htau, ctx->d_thist);
-    launch_tile_class(ctx, v, ctx->d_bins);
-    if ((st = launch_proposal(ctx, v, ctx->d_bins, nullptr, true, true)) != ART_OK) return st;
-    if ((st = launch_composite_skip(ctx, v, F, F_dtype, A)) != ART_OK) return st;
+    launch_bin(ctx, v, ctx->d_hbin, ctx->d_htau, ctx->d_thist, false);
+    st = sort_beside(ctx, v, F, F_dtype, A, true);
+    if (st == ART_OK) st = launch_composite_skip(ctx, v, F, F_dtype, A);
+    ctx->f_cleared = false;
+    if (st != ART_OK) return st;
     return launch_check(ctx, "render_feature_maps");
   }
-  launch_project(ctx, v);
-  launch_bin(ctx, v);
   if (ctx->sh_degree >= 0 && ctx->cfg.index == ART_INDEX_GRID)
     return fail(ctx, ART_ERR_UNSUPPORTED, "view-dependent (SH) features need the exact boxes (index 0)");
-  if (ctx->sh_degree >= 0) {  // view-dependent features (Eq. 2)
-    if ((st = launch_composite_sh(ctx, v, F, F_dtype, A)) != ART_OK) return st;
-    return launch_check(ctx, "render_feature_maps (SH)");
+  launch_project(ctx, v);
+  launch_bin(ctx, v, nullptr, nullptr, nullptr, false);
+  st = sort_beside(ctx, v, F, F_dtype, A, false);
+  if (st == ART_OK) {
+    if (ctx->sh_degree >= 0)  // view-dependent features (Eq. 2)
+      st = launch_composite_sh(ctx, v, F, F_dtype, A);
+    else
+      st = launch_composite(ctx, v, F, F_dtype, A);
   }
-  if ((st = launch_composite(ctx, v, F, F_dtype, A)) != ART_OK) return st;
-  return launch_check(ctx, "render_feature_maps");
+  ctx->f_cleared = false;
+  if (st != ART_OK) return st;
+  return launch_check(ctx, ctx->sh_degree >= 0 ? "render_feature_maps (SH)" : "render_feature_maps");
 }
 
 art_status art_render_views(art_ctx* ctx, int nv, const int* views, void* const* F_out, int F_dtype,

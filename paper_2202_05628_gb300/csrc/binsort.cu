@@ -692,7 +692,7 @@ size_t sort_hist_words(int64_t inst_cap) {
   return (size_t)(nb * kRadix);
 }
 
-void launch_bin(art_ctx* ctx, const ViewParams& v, const uint32_t* hbin, const float* htau, float* thist) {
+void launch_bin(art_ctx* ctx, const ViewParams& v, const uint32_t* hbin, const float* htau, float* thist, bool sort) {
   const int64_t n = ctx->n;
   const int ntiles = v.tiles_x * v.tiles_y;
   const unsigned vb = (unsigned)((n + 255) / 256);
@@ -706,6 +706,11 @@ void launch_bin(art_ctx* ctx, const ViewParams& v, const uint32_t* hbin, const f
              ctx->d_agroups, ctx->d_status);
   ART_LAUNCH_PDL(ctx, "bin_emit", bucket_emit_kernel, vb, 256, 0, n, ctx->d_cnt, ctx->d_rect, ctx->d_q, v, ctx->inst_cap,
              0u, ctx->d_toff, ctx->d_keys, ctx->d_vals, ctx->d_status, hbin, htau, thist);
+  if (sort) launch_tile_sort(ctx, v);
+}
+
+void launch_tile_sort(art_ctx* ctx, const ViewParams& v) {
+  const int ntiles = v.tiles_x * v.tiles_y;
   ART_LAUNCH_PDL(ctx, "tile_sort", tile_sort_kernel, 2 * ctx->num_sms, kTileSortThreads, kTileSortSmem * 8, ctx->d_ranges,
              ctx->d_sortlist, ntiles, v.depth_bits, ctx->d_keys, ctx->d_vals, ctx->d_sort_tmp, ctx->d_status);
 }

@@ -14,7 +14,10 @@
 // in a small register reorder buffer sorted by (t0, t1, list position), and
 // composites a hit front to back once no later list entry can start before it
 // (t0 < the distance bound of the next chunk, or of the candidate when the
-// buffer is full).  The walk ends once every pixel of the tile has stopped
+// buffer is full).  The reorder buffer is a per-lane ring in shared memory
+// (slot-major, so the lanes of a warp touch 32 different banks): hits arrive
+// nearly in order, so an insertion moves at most a few entries and a release
+// only advances the ring's head.  The walk ends once every pixel of the tile has stopped
 // (T < tau).
 #include <algorithm>
 
@@ -166,14 +169,17 @@ __device__ __forceinline__ void composite_tile(const int tile, const Seg& sg,
   constexpr bool SH = MODE == kSH;                 // features evaluated per hit from SH coefficients
   constexpr bool FEAT = MODE != kLabel && !SH;  // staged feature rows (labels need densities only)
   constexpr int RING = Ring<C, TF>::kChunks;
-  __shared__ float4 s_b0[NT], s_b1[NT], s_b2[NT], s_xl[NT];
   __shared__ float s_thr[NT];
   __shared__ uint32_t s_mask[NT];
   __shared__ float s_sig[RING][NT];
   __shared__ uint32_t s_vid[RING][NT];
   __shared__ __align__(16) TF s_feat[RING][NT][C];
-  __shared__ __align__(16) float4 s_rec[2][NT][4];  // raw voxel records of this chunk and the next
+  // raw voxel records of this chunk and the next; once a chunk is staged its
+  // slots hold the instance's slab frame (b0, b1, b2, xl of stage_voxel)
+  __shared__ __align__(16) float4 s_rec[2][NT][4];
   __shared__ short4 s_rc[2][NT];
+  __shared__ float s_pt0[kPend][NT], s_pdl[kPend][NT];  // pending hits: ring of kPend per lane
+  __shared__ uint32_t s_ppos[kPend][NT];
 
   const int lane = threadIdx.x & 31;
   const int tx = tile % v.tiles_x, ty = tile / v.tiles_x;
@@ -188,10 +194,8 @@ __device__ __forceinline__ void composite_tile(const int tile, const Seg& sg,
   for (int c = 0; c < C; ++c) acc[c] = 0.0f;
   float T = 1.0f;
   bool done = !inside;
-  Pend buf[kPend];
-#pragma unroll
-  for (int k = 0; k < kPend; ++k) buf[k] = Pend{0.f, 0.f, 0u};
-  int nb = 0;
+  int nb = 0, hd = 0;      // pending hits and the ring slot of the earliest
+  float front = 3.4e38f;   // t0 of the earliest pending hit (while nb > 0)
   uint32_t n_over = 0;
   const uint32_t qmask = (1u << v.depth_bits) - 1u;
   const float qinv = 1.0f / v.dscale;
@@ -232,10 +236,9 @@ __device__ __forceinline__ void composite_tile(const int tile, const Seg& sg,
   float lab_lo = 3.4e38f, lab_hi = -3.4e38f, lab_T = 1.0f;
 
   auto release_front = [&]() {
-    Pend h = buf[0];
-#pragma unroll
-    for (int k = 0; k < kPend - 1; ++k) buf[k] = buf[k + 1];
-    --nb;
+    const Pend h{s_pt0[hd][lane], s_pdl[hd][lane], s_ppos[hd][lane]};
+    hd = (hd + 1) & (kPend - 1);
+    if (--nb > 0) front = s_pt0[hd][lane];
     const int ch = (int)(h.pos / NT), sl = (int)(h.pos % NT);
     float f[C];
     float sig;
@@ -322,7 +325,7 @@ __device__ __forceinline__ void composite_tile(const int tile, const Seg& sg,
         const float4 r0 = s_rec[b][lane][0], r1 = s_rec[b][lane][1], r2 = s_rec[b][lane][2],
                      r3 = s_rec[b][lane][3];
         const short4 rc = s_rc[b][lane];
-        stage_voxel(r0, r1, r2, v, s_b0[lane], s_b1[lane], s_b2[lane], s_xl[lane]);
+        stage_voxel(r0, r1, r2, v, s_rec[b][lane][0], s_rec[b][lane][1], s_rec[b][lane][2], s_rec[b][lane][3]);
         s_sig[slot][lane] = r3.x;
         s_vid[slot][lane] = vid;
         thr = v.znear + (float)(key & qmask) * qinv;
@@ -340,7 +343,7 @@ __device__ __forceinline__ void composite_tile(const int tile, const Seg& sg,
     }
     // every instance of this chunk and later enters at t >= the first threshold
     const float thr0 = s_thr[0];
-    while (!done && nb > 0 && buf[0].t0 < thr0) release_front();
+    while (!done && nb > 0 && front < thr0) release_front();
     uint32_t cand = transpose32(s_mask[lane], lane);
     if (done) cand = 0;
     while (cand) {
@@ -348,7 +351,9 @@ __device__ __forceinline__ void composite_tile(const int tile, const Seg& sg,
       cand &= cand - 1;
       float t0, dl, e[3];
       int ax0, ax1;
-      if (!slab_hit(s_b0[idx], s_b1[idx], s_b2[idx], s_xl[idx], rd, v.znear, v.zfar, t0, dl, ax0, ax1, e)) continue;
+      if (!slab_hit(s_rec[b][idx][0], s_rec[b][idx][1], s_rec[b][idx][2], s_rec[b][idx][3], rd, v.znear, v.zfar, t0,
+                    dl, ax0, ax1, e))
+        continue;
       if (t0 < sg.t0_lo || t0 >= sg.t0_hi) continue;  // another segment's hit
       if constexpr (MODE == kInterval) {
         if (t0 + dl < t_lo || t0 > t_hi) continue;  // outside this pixel's interval
@@ -358,7 +363,7 @@ __device__ __forceinline__ void composite_tile(const int tile, const Seg& sg,
         // buffer full: release what this candidate's own bound allows (still
         // exact), and only if nothing can go, the earliest hit (counted)
         const float thr = s_thr[idx];
-        while (!done && nb > 0 && buf[0].t0 < thr) release_front();
+        while (!done && nb > 0 && front < thr) release_front();
         if (!done && nb == kPend) {
           ++n_over;
           release_front();
@@ -368,17 +373,25 @@ __device__ __forceinline__ void composite_tile(const int tile, const Seg& sg,
           break;
         }
       }
-#pragma unroll
-      for (int q = 0; q < kPend; ++q)
-        if (q == nb) buf[q] = p;
-#pragma unroll
-      for (int q = kPend - 1; q >= 1; --q) {
-        if (q <= nb && pless(buf[q], buf[q - 1])) {
-          const Pend tmp = buf[q];
-          buf[q] = buf[q - 1];
-          buf[q - 1] = tmp;
-        }
+      // insertion from the back: move the later pending hits up one slot
+      int q = nb;
+      while (q > 0) {
+        const int j = (hd + q - 1) & (kPend - 1);
+        const float bt = s_pt0[j][lane];
+        if (p.t0 > bt) break;
+        const Pend o{bt, s_pdl[j][lane], s_ppos[j][lane]};
+        if (!pless(p, o)) break;
+        const int k = (j + 1) & (kPend - 1);
+        s_pt0[k][lane] = o.t0;
+        s_pdl[k][lane] = o.dl;
+        s_ppos[k][lane] = o.pos;
+        --q;
       }
+      const int k = (hd + q) & (kPend - 1);
+      s_pt0[k][lane] = p.t0;
+      s_pdl[k][lane] = p.dl;
+      s_ppos[k][lane] = p.pos;
+      if (q == 0) front = p.t0;
       ++nb;
     }
     if (__all_sync(0xffffffffu, done)) break;
@@ -946,7 +959,7 @@ void split_pass(art_ctx* ctx, const ViewParams& v, void* F, float* A, int mode, 
   const int seg_len = list ? std::max(32, ctx->seg_len / 4) : ctx->seg_len;
   ART_LAUNCH_PDL(ctx, list ? "composite_replan" : "composite_plan", seg_plan_kernel, (ntiles + 255) / 256, 256, 0, ntiles,
              ctx->d_ranges, seg_len, ctx->d_seg, ctx->d_items, ctx->d_multi, ctx->d_status, list, list_word);
-  if (!list) {
+  if (!list && !ctx->f_cleared) {
     auto cfn = composite_clear_kernel<C, TO>;
     ART_LAUNCH_PDL(ctx, "composite_clear", cfn, (ntiles + 7) / 8, 256, 0, ctx->d_ranges, v, (TO*)F, A);
   }
@@ -1132,12 +1145,60 @@ art_status launch_composite_skip(art_ctx* ctx, const ViewParams& v, void* F, int
   return dispatch(ctx, v, F, F_dtype, A, nullptr, kInterval, sk);
 }
 
+namespace {
+// Resident one-warp blocks per SM of the interval walk (the largest shared
+// memory of the split walk's modes): its feature ring, pending-hit rings and
+// staged records bound it, and so do its registers (kCompositeWarps).
+template <int C, typename TF>
+int split_blocks_per_sm() {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, composite_split_kernel<C, TF, __nv_bfloat16, kInterval>, 32,
+                                                    0) != cudaSuccess) {
+    cudaGetLastError();
+    n = 0;
+  }
+  return std::max(1, std::min(kCompositeWarps, n));
+}
+
+template <int C>
+int split_blocks_c(int feat_bytes) {
+  return feat_bytes == 4 ? split_blocks_per_sm<C, float>() : split_blocks_per_sm<C, __nv_bfloat16>();
+}
+}  // namespace
+
 int composite_blocks_per_sm(int C, int feat_bytes) {
-  // one-warp blocks, limited by shared memory (staged-feature ring, chunk
-  // geometry, double-buffered records) and by registers (kCompositeWarps)
-  const int ring = std::max(1, std::min(16, kRingBytes / (NT * C * feat_bytes)));
-  const int smem = ring * NT * (C * feat_bytes + 8) + NT * (4 * 16 + 8) + 2 * NT * (64 + 8) + 4 * kPropBins + 64;
-  return std::max(1, std::min(kCompositeWarps, (227 * 1024) / smem));
+  switch (C) {
+    case 4: return split_blocks_c<4>(feat_bytes);
+    case 8: return split_blocks_c<8>(feat_bytes);
+    case 16: return split_blocks_c<16>(feat_bytes);
+    default: return split_blocks_c<32>(feat_bytes);
+  }
+}
+
+namespace {
+template <int C>
+void clear_c(art_ctx* ctx, const ViewParams& v, void* F, int F_dtype, float* A) {
+  const int ntiles = v.tiles_x * v.tiles_y;
+  if (F_dtype == ART_F32) {
+    ART_LAUNCH_PDL(ctx, "composite_clear", (composite_clear_kernel<C, float>), (ntiles + 7) / 8, 256, 0, ctx->d_ranges,
+                   v, (float*)F, A);
+  } else {
+    ART_LAUNCH_PDL(ctx, "composite_clear", (composite_clear_kernel<C, __nv_bfloat16>), (ntiles + 7) / 8, 256, 0,
+                   ctx->d_ranges, v, (__nv_bfloat16*)F, A);
+  }
+}
+}  // namespace
+
+art_status launch_composite_clear(art_ctx* ctx, const ViewParams& v, void* F, int F_dtype, float* A) {
+  if (v.tile_w != TSX || v.tile_h != TSY) return fail(ctx, ART_ERR_UNSUPPORTED, "composite: tiles must be 8x4");
+  switch (ctx->C) {
+    case 4: clear_c<4>(ctx, v, F, F_dtype, A); break;
+    case 8: clear_c<8>(ctx, v, F, F_dtype, A); break;
+    case 16: clear_c<16>(ctx, v, F, F_dtype, A); break;
+    case 32: clear_c<32>(ctx, v, F, F_dtype, A); break;
+    default: return fail(ctx, ART_ERR_UNSUPPORTED, "composite: C=%d not built (4, 8, 16, 32)", ctx->C);
+  }
+  return ART_OK;
 }
 
 art_status launch_composite_labels(art_ctx* ctx, const ViewParams& v, float* labels, uint8_t* bins) {

@@ -112,6 +112,11 @@ struct KernelStat {
 
 struct art_ctx {
   cudaStream_t stream = nullptr;
+  // a second stream for work beside the bucket sort (tile classes, proposal,
+  // clear of the empty tiles), forked from and joined into `stream` by events
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  bool f_cleared = false;  // the empty tiles of this frame's F and A are cleared already
   std::string err;
   art_config cfg{};
   int device = 0;
@@ -294,8 +299,11 @@ void launch_project_view(art_ctx* ctx, const ViewParams& v, short4* rect, uint32
 // scatter also adds each voxel's optical-depth bound htau to the depth bins
 // hbin of each of its tiles (thist: zeroed [tiles][64]; the coarse check of
 // the learned skip).
+// With sort false the bucket sort is left to launch_tile_sort (so that work
+// which needs only the ranges can run beside it).
 void launch_bin(art_ctx* ctx, const ViewParams& v, const uint32_t* hbin = nullptr, const float* htau = nullptr,
-                float* thist = nullptr);
+                float* thist = nullptr, bool sort = true);
+void launch_tile_sort(art_ctx* ctx, const ViewParams& v);
 // Binning of a batch of views in one tile space (ntiles in all, joint
 // depth_bits): one scan of all tiles' counts, one scatter per view (its
 // instances keyed by global tile), one sort of all buckets.
@@ -323,6 +331,10 @@ art_status launch_composite_sh(art_ctx* ctx, const ViewParams& v, void* F, int F
 // Learned skip: composite over the proposal intervals (ctx->d_bins), coarse
 // check against ctx->d_thist, then the full traversal of the queued tiles.
 art_status launch_composite_skip(art_ctx* ctx, const ViewParams& v, void* F, int F_dtype, float* A);
+// Zero F and A of the tiles without instances (needs only the tile ranges);
+// a composite that follows on the same frame with ctx->f_cleared set skips
+// its own clear.
+art_status launch_composite_clear(art_ctx* ctx, const ViewParams& v, void* F, int F_dtype, float* A);
 // Labels of the plain composite (labels [H][W][3], bins [H][W][2]; either may be null).
 art_status launch_composite_labels(art_ctx* ctx, const ViewParams& v, float* labels, uint8_t* bins);
 // Plain composite of a batch of views in one split pass over the joint tile

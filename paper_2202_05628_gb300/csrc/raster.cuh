@@ -10,6 +10,7 @@
 namespace art {
 
 constexpr int kPend = 16;  // reorder-buffer depth per pixel
+static_assert((kPend & (kPend - 1)) == 0, "the composite keeps its pending hits in a power-of-two ring");
 
 // Optional per-pixel record of the composited hits (inspection only).
 struct HitLog {
