@@ -236,6 +236,8 @@ art_status ensure_bin_buffers(art_ctx* ctx, int64_t ntiles) {
   if (more_tiles) {
     if ((st = alloc(ctx, &ctx->d_ranges, (size_t)ntiles, "tile ranges")) != ART_OK) return st;
     if ((st = alloc(ctx, &ctx->d_tcount, (size_t)ntiles, "tile counts")) != ART_OK) return st;
+    // zero once: from then on every tile scan zeroes the counts it read
+    cudaMemsetAsync(ctx->d_tcount, 0, sizeof(uint32_t) * (size_t)ntiles, ctx->stream);
     if ((st = alloc(ctx, &ctx->d_toff, (size_t)ntiles, "tile offsets")) != ART_OK) return st;
     if ((st = alloc(ctx, &ctx->d_sortlist, (size_t)ntiles, "tile sort list")) != ART_OK) return st;
     if ((st = alloc(ctx, &ctx->d_scan_state, tile_scan_state_words(ntiles), "tile scan state")) != ART_OK) return st;
@@ -258,12 +260,14 @@ art_status ensure_skip_buffers(art_ctx* ctx, const ViewParams& v) {
     ctx->hist_n_cap = ctx->n;
   }
   const size_t ntiles = (size_t)v.tiles_x * v.tiles_y;
+  const float* thist_was = ctx->d_thist;
   if ((st = ensure(ctx, (void**)&ctx->d_thist, &ctx->d_thist_bytes, ntiles * kPropBins * 4, "tile histogram")) != ART_OK)
     return st;
+  // zeroed once; the tile scan zeroes the rows of the tiles it gives instances
+  if (ctx->d_thist != thist_was) cudaMemsetAsync(ctx->d_thist, 0, ctx->d_thist_bytes, ctx->stream);
   if ((st = ensure(ctx, (void**)&ctx->d_fbq, &ctx->d_fbq_bytes, ntiles * 4, "fallback queue")) != ART_OK) return st;
   if ((st = ensure(ctx, (void**)&ctx->d_bins, &ctx->d_bins_bytes, (size_t)v.W * v.H * 2, "proposal bins")) != ART_OK)
     return st;
-  cudaMemsetAsync(ctx->d_thist, 0, ntiles * kPropBins * 4, ctx->stream);
   return ART_OK;
 }
 
@@ -282,8 +286,13 @@ art_status ensure_split_buffers(art_ctx* ctx, size_t ntiles) {
   if ((st = ensure(ctx, (void**)&ctx->d_fbq, &ctx->d_fbq_bytes, ntiles * 4, "fallback queue")) != ART_OK) return st;
   if ((st = ensure(ctx, (void**)&ctx->d_fbq2, &ctx->d_fbq2_bytes, ntiles * 4, "second fallback queue")) != ART_OK)
     return st;
+  const uint32_t* xflag_was = ctx->d_xflag;
   if ((st = ensure(ctx, (void**)&ctx->d_xflag, &ctx->d_xflag_bytes, ntiles * 4, "exact re-walk flags")) != ART_OK)
     return st;
+  if (ctx->d_xflag != xflag_was) {  // stamps start over on a new array
+    cudaMemsetAsync(ctx->d_xflag, 0, ctx->d_xflag_bytes, ctx->stream);
+    ctx->xstamp = 0;
+  }
   if ((st = ensure(ctx, (void**)&ctx->d_xqueue, &ctx->d_xqueue_bytes, ntiles * 4, "exact re-walk queue")) != ART_OK)
     return st;
   if (!ctx->d_xhit) {
@@ -292,7 +301,10 @@ art_status ensure_split_buffers(art_ctx* ctx, size_t ntiles) {
     if ((st = alloc(ctx, &ctx->d_xpos, m, "exact re-walk list positions")) != ART_OK) return st;
   }
   const int fb = ctx->feat_dtype == ART_F32 ? 4 : 2;
-  ctx->composite_blocks = ctx->num_sms * composite_blocks_per_sm(ctx->C, fb);
+  if (ctx->composite_key != ctx->C * 8 + fb) {  // resident walk blocks for this channel count and storage
+    ctx->composite_blocks = ctx->num_sms * composite_blocks_per_sm(ctx->C, fb);
+    ctx->composite_key = ctx->C * 8 + fb;
+  }
   return ART_OK;
 }
 
@@ -489,9 +501,7 @@ art_status art_set_pose(art_ctx* ctx, const float* axis_angle, const float R[3],
       return fail(ctx, ART_ERR_INVALID_ARG, "%llu voxels reference joints >= J=%d", ctx->h_status[7], J);
     ctx->jidx_ok = true;
   }
-  cudaMemsetAsync(ctx->d_status + kStDegenerate, 0, sizeof(unsigned long long), ctx->stream);
-  cudaMemsetAsync(ctx->d_status + kStRmax, 0, sizeof(unsigned long long), ctx->stream);
-  launch_fk(ctx);
+  launch_fk(ctx);  // (zeroes the pose's counters, kStDegenerate and kStRmax)
   launch_lbs(ctx);
   if (ctx->cfg.index == ART_INDEX_GRID) {
     if (ctx->grid_slots < 2 * ctx->n) {
@@ -720,8 +730,7 @@ art_status art_render_views(art_ctx* ctx, int nv, const int* views, void* const*
   if (!ctx->d_vset && (st = alloc(ctx, &ctx->d_vset, 1, "view table")) != ART_OK) return st;
   vs.rect_stride = ctx->n;
   if ((st = copy_in(ctx, ctx->d_vset, &vs, sizeof(ViewSet), "copy view table")) != ART_OK) return st;
-  cudaMemsetAsync(ctx->d_tcount, 0, sizeof(uint32_t) * (size_t)total, ctx->stream);
-  for (int k = 0; k < nv; ++k) {
+  for (int k = 0; k < nv; ++k) {  // (the counts are zero: the last tile scan cleared them)
     const int64_t o = (int64_t)k * ctx->n;
     launch_project_view(ctx, vs.v[k], ctx->d_rect_v + o, ctx->d_q_v + o, ctx->d_cnt_v + o, ctx->d_tcount + vs.toff[k],
                         k == 0);

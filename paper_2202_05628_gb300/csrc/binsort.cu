@@ -256,7 +256,10 @@ __device__ __forceinline__ uint32_t rect_tile(const ViewParams& v, int tx0, int 
 // total into kStInstances, and the tiles whose bucket needs sorting: those of
 // 2..kWarpSortCap instances from the front of sort_list, longer ones from its
 // end (kStSortTiles and kStSortBig of them, written by the last block, which
-// also resets both work counters).
+// also resets both work counters).  The counts it reads are zeroed for the
+// next projection, and with thist the 64 depth bins of every tile with
+// instances are zeroed for the scatter that adds into them (rows of tiles
+// without instances are not read).
 struct ScanWords {  // per block: aggregate and inclusive prefix, each (instances, lists)
   unsigned long long agg_i, agg_l, inc_i, inc_l;
 };
@@ -268,13 +271,14 @@ __device__ __forceinline__ void st_volatile(unsigned long long* p, unsigned long
   *reinterpret_cast<volatile unsigned long long*>(p) = x;
 }
 
-__global__ void __launch_bounds__(kTileScanThreads) tile_scan_kernel(int ntiles, const uint32_t* __restrict__ tcount,
+__global__ void __launch_bounds__(kTileScanThreads) tile_scan_kernel(int ntiles, uint32_t* __restrict__ tcount,
                                                                      int64_t cap, uint32_t* __restrict__ toff,
                                                                      uint2* __restrict__ ranges,
                                                                      uint32_t* __restrict__ sort_list,
                                                                      ScanWords* __restrict__ sw,
                                                                      uint32_t* __restrict__ agroups,
-                                                                     unsigned long long* __restrict__ status) {
+                                                                     unsigned long long* __restrict__ status,
+                                                                     float* __restrict__ thist) {
   ART_PDL_ENTRY();
   __shared__ unsigned long long s_b, s_pi, s_pl;
   if (threadIdx.x == 0) s_b = atomicAdd(status + kStScanTicket, 1ull);
@@ -292,6 +296,19 @@ __global__ void __launch_bounds__(kTileScanThreads) tile_scan_kernel(int ntiles,
   } else {
 #pragma unroll
     for (int k = 0; k < kTileScanItems; ++k) c[k] = base + k < ntiles ? tcount[base + k] : 0u;
+  }
+  // the counts are read: zero them for the next projection, and the depth
+  // histograms of the tiles that will receive instances for this scatter
+#pragma unroll
+  for (int k = 0; k < kTileScanItems; ++k) {
+    if (base + k < ntiles && c[k]) {
+      tcount[base + k] = 0u;
+      if (thist) {
+        float4* row = reinterpret_cast<float4*>(thist + (size_t)(base + k) * kPropBins);
+#pragma unroll
+        for (int j = 0; j < kPropBins / 4; ++j) row[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
   }
   uint32_t s = 0, lists = 0;  // lists: small | big << 16 (per block < 2^16 each)
 #pragma unroll
@@ -703,7 +720,7 @@ void launch_bin(art_ctx* ctx, const ViewParams& v, const uint32_t* hbin, const f
   const int nsb = (ntiles + kTileScanBlock - 1) / kTileScanBlock;
   ART_LAUNCH_PDL(ctx, "bin_scan", tile_scan_kernel, nsb, kTileScanThreads, 0, ntiles, ctx->d_tcount, ctx->inst_cap,
              ctx->d_toff, ctx->d_ranges, ctx->d_sortlist, reinterpret_cast<ScanWords*>(ctx->d_scan_state),
-             ctx->d_agroups, ctx->d_status);
+             ctx->d_agroups, ctx->d_status, thist);
   ART_LAUNCH_PDL(ctx, "bin_emit", bucket_emit_kernel, vb, 256, 0, n, ctx->d_cnt, ctx->d_rect, ctx->d_q, v, ctx->inst_cap,
              0u, ctx->d_toff, ctx->d_keys, ctx->d_vals, ctx->d_status, hbin, htau, thist);
   if (sort) launch_tile_sort(ctx, v);
@@ -726,7 +743,7 @@ void launch_bin_views(art_ctx* ctx, const ViewSet& vs, int64_t ntiles) {
   const int nsb = (nt + kTileScanBlock - 1) / kTileScanBlock;
   ART_LAUNCH_PDL(ctx, "bin_scan", tile_scan_kernel, nsb, kTileScanThreads, 0, nt, ctx->d_tcount, ctx->inst_cap,
              ctx->d_toff, ctx->d_ranges, ctx->d_sortlist, reinterpret_cast<ScanWords*>(ctx->d_scan_state),
-             ctx->d_agroups, ctx->d_status);
+             ctx->d_agroups, ctx->d_status, (float*)nullptr);
   for (int k = 0; k < vs.nv; ++k) {
     const int64_t o = (int64_t)k * vs.rect_stride;
     ART_LAUNCH_PDL(ctx, "bin_emit", bucket_emit_kernel, vb, 256, 0, n, ctx->d_cnt_v + o, ctx->d_rect_v + o,

@@ -27,6 +27,11 @@ namespace art {
 namespace {
 
 constexpr int kThreads = 192;  // warp 0 TMA, warp 1 MMA + TMEM, warps 2..5 epilogue
+
+__device__ __forceinline__ float* align16(float* p) {
+  return reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(p) + 15) & ~(uintptr_t)15);
+}
+
 struct TcParams {
   int H, W, cin, cout;
   int tiles_per_row, n_tiles;
@@ -107,12 +112,19 @@ __device__ __forceinline__ void epi_row(const TcParams& p, uint32_t taddr, int y
     if (!valid) continue;
     if (p.rgba) {  // fused 1x1 head (N == 32) + sigmoid -> head_n FP32 channels of the output
       float o[4];
+      const float4* hw = reinterpret_cast<const float4*>(s_head + c0);  // 16-B aligned rows of N weights
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         float acc = s_head[4 * N + k];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) acc = fmaf(s_head[k * N + c0 + j], v[j], acc);
-        o[k] = 1.0f / (1.0f + expf(-acc));
+        for (int q = 0; q < 8; ++q) {
+          const float4 w = hw[k * (N / 4) + q];
+          acc = fmaf(w.x, v[4 * q], acc);
+          acc = fmaf(w.y, v[4 * q + 1], acc);
+          acc = fmaf(w.z, v[4 * q + 2], acc);
+          acc = fmaf(w.w, v[4 * q + 3], acc);
+        }
+        o[k] = __frcp_rn(1.0f + __expf(-acc));  // (fast exponential: relative error ~1e-6 on a [0, 1] output)
       }
       float* dst = p.rgba + (size_t)(y * p.W + x) * p.head_ld + p.head_off;
       if (p.head_n == 4 && p.head_ld == 4) {
@@ -312,7 +324,7 @@ struct TcCfg {
                                      | ((uint32_t)(128 >> 4) << 24);    // M / 16
   static constexpr int kStageBuf = F8 ? 0 : 4 * 32 * 4 * 16;  // BF16 epilogue staging: 4 warps x 32 pixels x 64 B
   static constexpr int kSmem =
-      kStages * kStage + 1024 + 8 * (2 * kStages + 4) + 16 + 4 * N + 4 * (4 * 32 + 4) + 4 * N + 16 + kStageBuf;
+      kStages * kStage + 1024 + 8 * (2 * kStages + 4) + 16 + 4 * N + 16 + 4 * (4 * 32 + 4) + 4 * N + 16 + kStageBuf;
 };
 
 template <int N, int KCB, bool F8>
@@ -331,7 +343,7 @@ __global__ void __launch_bounds__(kThreads, TcCfg<N, KCB, F8>::kCtas)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   float* s_bias = reinterpret_cast<float*>(tmem_slot + 4);
-  float* s_head = s_bias + N;
+  float* s_head = align16(s_bias + N);  // (read as float4 rows)
   float* s_wsc = s_head + 4 * 32 + 4;  // FP8 per-output-channel weight scales
   uint4* s_stage = reinterpret_cast<uint4*>((reinterpret_cast<uintptr_t>(s_wsc + N) + 15) & ~(uintptr_t)15);
 
@@ -519,7 +531,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(wbar + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   float* s_bias = reinterpret_cast<float*>(tmem_slot + 4);
-  float* s_head = s_bias + N;
+  float* s_head = align16(s_bias + N);  // (read as float4 rows)
   float* s_wsc = s_head + 4 * 32 + 4;  // FP8 per-output-channel weight scales
   // epilogue store staging: 32 pixels x U chunks per epilogue warp (16-B aligned)
   uint4* s_stage = reinterpret_cast<uint4*>((reinterpret_cast<uintptr_t>(s_wsc + N) + 15) & ~(uintptr_t)15);
@@ -896,7 +908,8 @@ art_status launch_rows(art_ctx* ctx, const TcConv& c) {
   rp.cpt = c.cin / Cfg::KC;
   rp.n_units = ((c.H + kRows - 1) / kRows) * p.tiles_per_row;
   rp.w_bytes = 9 * rp.cpt * N * KCB;
-  const int tail = 8 * (2 * 24 + 5) + 16 + 4 * N + 4 * (4 * 32 + 4) + 4 * N + 16 + (F8 ? 0 : 4 * 32 * 16 * RowOut<N, F8>::U);
+  const int tail =
+      8 * (2 * 24 + 5) + 16 + 4 * N + 16 + 4 * (4 * 32 + 4) + 4 * N + 16 + (F8 ? 0 : 4 * 32 * 16 * RowOut<N, F8>::U);
   // two CTAs per SM (two issuing threads, one accumulator buffer each) when
   // the resident weights and three stages fit in half the shared memory
   const int half = 232448 / 2 - 1024 - rp.w_bytes - tail;

@@ -41,9 +41,11 @@ struct SkipArgs {
   const float* sh_coef; // kSH: [n][(L+1)^2][C] spherical-harmonics coefficients
   const float* sh_rot;  // kSH: [n][9] per voxel the map of world directions into its canonical frame
   int sh_degree;        // kSH: L (0 .. kShMaxDegree)
-  uint32_t* xflag;      // kPlain, kInterval: per global tile, queued for the exact re-walk already
-  uint32_t* xqueue;     // ... the queue (count in status[kStExactQ])
+  uint32_t* xflag;      // kPlain, kInterval: per global tile, the stamp of the render that queued it
+  uint32_t* xqueue;     // ... for the exact re-walk (count in status[kStExactQ])
+  uint32_t xstamp;      // this render's stamp (never 0)
   int gtile;            // the walked tile's index in the (joint) tile space
+  const uint8_t* tclass;  // kInterval: tile classes; forced tiles (class != 0) need no coarse check
 };
 
 // Real orthonormal spherical harmonics of degree <= L (<= kShMaxDegree) at
@@ -149,7 +151,7 @@ __device__ __forceinline__ void report_overflow(uint32_t n_over, const SkipArgs&
   const bool any = __any_sync(0xffffffffu, n_over != 0);
   if (!any) return;
   if (sk.xqueue) {
-    if (lane == 0 && atomicExch(sk.xflag + sk.gtile, 1u) == 0u)
+    if (lane == 0 && atomicExch(sk.xflag + sk.gtile, sk.xstamp) != sk.xstamp)
       sk.xqueue[atomicAdd(status + kStExactQ, 1ull)] = (uint32_t)sk.gtile;
   } else if (n_over) {
     atomicAdd(status + kStOverflowOrder, (unsigned long long)n_over);
@@ -407,44 +409,48 @@ __device__ __forceinline__ void composite_tile(const int tile, const Seg& sg,
     report_overflow(n_over, sk, status, lane);
     return;
   }
+  // a forced tile (walked over its whole list, or holding less than the
+  // threshold in all) passes the coarse check by construction
   if constexpr (MODE == kLabel || MODE == kInterval) {
-    __shared__ float s_pre[kPropBins];
-    const float tot = tile_hist_prefix(sk.thist + (size_t)tile * kPropBins, s_pre, lane);
-    if constexpr (MODE == kInterval) {  // coarse check of the lost mass
-      bool fail = false;
-      if (inside) {
-        const float front = empty ? tot : (bn > 0 ? s_pre[bn - 1] : 0.0f);
-        const float back = empty ? 0.0f : tot - s_pre[bf];
-        fail = -expm1f(-front) + T * -expm1f(-back) > sk.max_missed;
-      }
-      if (__any_sync(0xffffffffu, fail) && lane == 0) {
-        const unsigned long long q = atomicAdd(status + sk.qword, 1ull);
-        sk.queue[q] = (uint32_t)tile;
-      }
-    } else {  // label bins: keep the significant hits and pass the check
-      const float budget = kLabelBudget * sk.max_missed;
-      const float tau_b = -log1pf(-budget);
-      const bool c0 = (lane == 0 ? 0.0f : s_pre[lane - 1]) <= tau_b;
-      const bool c1 = s_pre[31 + lane] <= tau_b;
-      const int front = __popc(__ballot_sync(0xffffffffu, c0)) + __popc(__ballot_sync(0xffffffffu, c1)) - 1;
-      if (inside) {
-        const bool sig = lab_lo < 3.0e38f;
-        const float bs = (float)kPropBins / (v.zfar - v.znear);
-        const int blo = sig ? min(max((int)floorf((lab_lo - v.znear) * bs), 0), kPropBins - 1) : kPropBins - 1;
-        const int bhi = sig ? min(max((int)floorf((lab_hi - v.znear) * bs), 0), kPropBins - 1) : 0;
-        const float Ts = sig ? lab_T : 1.0f;
-        int lbf = kPropBins - 1;
-        for (int b = bhi; b < kPropBins; ++b)
-          if (Ts * -expm1f(-(tot - s_pre[b])) <= budget) {
-            lbf = b;
-            break;
-          }
-        if (sk.labels) {
-          sk.labels[3 * pix] = sig ? lab_lo : __int_as_float(0x7f800000);
-          sk.labels[3 * pix + 1] = sig ? lab_hi : __int_as_float(0xff800000);
-          sk.labels[3 * pix + 2] = Ts;
+    if (MODE == kLabel || !(sk.tclass && sk.tclass[tile] != 0)) {
+      __shared__ float s_pre[kPropBins];
+      const float tot = tile_hist_prefix(sk.thist + (size_t)tile * kPropBins, s_pre, lane);
+      if constexpr (MODE == kInterval) {  // coarse check of the lost mass
+        bool fail = false;
+        if (inside) {
+          const float front = empty ? tot : (bn > 0 ? s_pre[bn - 1] : 0.0f);
+          const float back = empty ? 0.0f : tot - s_pre[bf];
+          fail = -expm1f(-front) + T * -expm1f(-back) > sk.max_missed;
         }
-        if (sk.lbins) sk.lbins[pix] = make_uchar2((uint8_t)min(blo, front), (uint8_t)lbf);
+        if (__any_sync(0xffffffffu, fail) && lane == 0) {
+          const unsigned long long q = atomicAdd(status + sk.qword, 1ull);
+          sk.queue[q] = (uint32_t)tile;
+        }
+      } else {  // label bins: keep the significant hits and pass the check
+        const float budget = kLabelBudget * sk.max_missed;
+        const float tau_b = -log1pf(-budget);
+        const bool c0 = (lane == 0 ? 0.0f : s_pre[lane - 1]) <= tau_b;
+        const bool c1 = s_pre[31 + lane] <= tau_b;
+        const int front = __popc(__ballot_sync(0xffffffffu, c0)) + __popc(__ballot_sync(0xffffffffu, c1)) - 1;
+        if (inside) {
+          const bool sig = lab_lo < 3.0e38f;
+          const float bs = (float)kPropBins / (v.zfar - v.znear);
+          const int blo = sig ? min(max((int)floorf((lab_lo - v.znear) * bs), 0), kPropBins - 1) : kPropBins - 1;
+          const int bhi = sig ? min(max((int)floorf((lab_hi - v.znear) * bs), 0), kPropBins - 1) : 0;
+          const float Ts = sig ? lab_T : 1.0f;
+          int lbf = kPropBins - 1;
+          for (int b = bhi; b < kPropBins; ++b)
+            if (Ts * -expm1f(-(tot - s_pre[b])) <= budget) {
+              lbf = b;
+              break;
+            }
+          if (sk.labels) {
+            sk.labels[3 * pix] = sig ? lab_lo : __int_as_float(0x7f800000);
+            sk.labels[3 * pix + 1] = sig ? lab_hi : __int_as_float(0xff800000);
+            sk.labels[3 * pix + 2] = Ts;
+          }
+          if (sk.lbins) sk.lbins[pix] = make_uchar2((uint8_t)min(blo, front), (uint8_t)lbf);
+        }
       }
     }
   }
@@ -551,7 +557,7 @@ __global__ void __launch_bounds__(32, kCompositeWarps) composite_split_views_ker
     const uint32_t* __restrict__ items, const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals,
     const float4* __restrict__ rec, const short4* __restrict__ rect, const TF* __restrict__ feat, float tau,
     unsigned long long* __restrict__ status, float* __restrict__ part, uint32_t* __restrict__ xflag,
-    uint32_t* __restrict__ xqueue) {
+    uint32_t* __restrict__ xqueue, uint32_t xstamp) {
   ART_PDL_ENTRY();
   const int lane = threadIdx.x & 31;
   const unsigned long long n_items = status[kStItems];
@@ -569,6 +575,7 @@ __global__ void __launch_bounds__(32, kCompositeWarps) composite_split_views_ker
     SkipArgs sk{};
     sk.xflag = xflag;
     sk.xqueue = xqueue;
+    sk.xstamp = xstamp;
     sk.gtile = (int)tile;
     composite_tile<C, TF, TO, kPlain>((int)(tile - vs->toff[k]), sg, keys, vals, rec, rect + k * vs->rect_stride, feat,
                                       v, tau, (TO*)vs->F[k], vs->A[k], status, HitLog{}, sk);
@@ -643,7 +650,7 @@ __device__ __forceinline__ void merge_tile(int tile, int tl, int grp, int lane, 
   }
   bool fail = false;
   if constexpr (MODE == kInterval) {  // coarse check of the lost mass over the tile's union interval
-    if (grp == 0) {
+    if (grp == 0 && !(sk.tclass && sk.tclass[tile] != 0)) {  // (forced tiles pass by construction)
       __shared__ float s_pre[kPropBins];
       const float tot = tile_hist_prefix(sk.thist + (size_t)tile * kPropBins, s_pre, lane);
       int lo_b = kPropBins, hi_b = -1;
@@ -762,7 +769,7 @@ __global__ void __launch_bounds__(32) composite_queue_views_kernel(const ViewSet
                                                                    unsigned long long* __restrict__ status,
                                                                    const uint32_t* __restrict__ queue, int qword,
                                                                    uint32_t* __restrict__ xflag,
-                                                                   uint32_t* __restrict__ xqueue) {
+                                                                   uint32_t* __restrict__ xqueue, uint32_t xstamp) {
   ART_PDL_ENTRY();
   const unsigned long long n = status[qword];
   for (unsigned long long i = blockIdx.x; i < n; i += gridDim.x) {
@@ -774,6 +781,7 @@ __global__ void __launch_bounds__(32) composite_queue_views_kernel(const ViewSet
     SkipArgs sk{};
     sk.xflag = xflag;
     sk.xqueue = xqueue;
+    sk.xstamp = xstamp;
     sk.gtile = (int)tile;
     composite_tile<C, TF, TO, kPlain>((int)(tile - vs->toff[k]), sg, keys, vals, rec, rect + k * vs->rect_stride,
                                       feat, v, tau, (TO*)vs->F[k], vs->A[k], status, HitLog{}, sk);
@@ -886,6 +894,32 @@ __global__ void __launch_bounds__(32) composite_exact_kernel(
   }
 }
 
+// Zeroes the status words whose bits are set in mask, in the stream's chain
+// of kernels (a memset node between two kernels would end their overlap).
+__global__ void __launch_bounds__(32) zero_words_kernel(unsigned long long* __restrict__ status, uint32_t mask) {
+  ART_PDL_ENTRY();
+  if ((mask >> threadIdx.x) & 1u) status[threadIdx.x] = 0ull;
+}
+static_assert(kStWords <= 32, "zero_words_kernel covers the status words with one warp");
+
+constexpr uint32_t bit(int w) { return 1u << w; }
+// the counters of one split pass: segments, split tiles, both work counters
+constexpr uint32_t kPassWords = bit(kStItems) | bit(kStMulti) | bit(kStNext) | bit(kStNextMerge);
+
+void zero_words(art_ctx* ctx, uint32_t mask) {
+  ART_LAUNCH_PDL(ctx, "composite_zero", zero_words_kernel, 1, 32, 0, ctx->d_status, mask);
+}
+
+// This render's stamp for the exact re-walk flags (a tile is queued once per
+// stamp); the flags are zeroed when the stamps wrap.
+uint32_t next_xstamp(art_ctx* ctx, size_t ntiles) {
+  if (++ctx->xstamp == 0u) {
+    cudaMemsetAsync(ctx->d_xflag, 0, sizeof(uint32_t) * ntiles, ctx->stream);
+    ctx->xstamp = 1u;
+  }
+  return ctx->xstamp;
+}
+
 // The plain split walk of a batch of views: plan all segments, clear each
 // view's empty tiles, walk all segments with persistent warps, merge the
 // split tiles, then walk the tiles whose stop fell inside a later segment.
@@ -893,10 +927,8 @@ template <int C, typename TF, typename TO>
 void views_walk(art_ctx* ctx, const ViewSet& vs) {
   const int ntiles = (int)vs.toff[vs.nv];
   const TF* feat = (const TF*)ctx->d_feat;
-  cudaMemsetAsync(ctx->d_status + kStItems, 0, 4 * sizeof(unsigned long long), ctx->stream);
-  cudaMemsetAsync(ctx->d_status + kStFallback, 0, sizeof(unsigned long long), ctx->stream);
-  cudaMemsetAsync(ctx->d_xflag, 0, sizeof(uint32_t) * (size_t)ntiles, ctx->stream);
-  cudaMemsetAsync(ctx->d_status + kStExactQ, 0, sizeof(unsigned long long), ctx->stream);
+  const uint32_t xstamp = next_xstamp(ctx, (size_t)ntiles);
+  zero_words(ctx, kPassWords | bit(kStFallback) | bit(kStExactQ));
   ART_LAUNCH_PDL(ctx, "composite_plan", seg_plan_kernel, (ntiles + 255) / 256, 256, 0, ntiles, ctx->d_ranges, ctx->seg_len,
              ctx->d_seg, ctx->d_items, ctx->d_multi, ctx->d_status, (const uint32_t*)nullptr, 0);
   for (int k = 0; k < vs.nv; ++k) {
@@ -908,7 +940,7 @@ void views_walk(art_ctx* ctx, const ViewSet& vs) {
   auto kfn = composite_split_views_kernel<C, TF, TO>;
   ART_LAUNCH_PDL(ctx, "composite", kfn, ctx->composite_blocks, 32, 0, ctx->d_vset, ctx->d_ranges, ctx->d_seg, ctx->d_items,
              ctx->d_keys, ctx->d_vals, ctx->d_rec, ctx->d_rect_v, feat, ctx->cfg.tau, ctx->d_status, ctx->d_part,
-             ctx->d_xflag, ctx->d_xqueue);
+             ctx->d_xflag, ctx->d_xqueue, xstamp);
   SkipArgs sk{};
   sk.queue = ctx->d_fbq;
   sk.qword = kStFallback;
@@ -918,7 +950,7 @@ void views_walk(art_ctx* ctx, const ViewSet& vs) {
   auto qfn = composite_queue_views_kernel<C, TF, TO>;
   ART_LAUNCH_PDL(ctx, "composite_fallback", qfn, std::min(ntiles, 16 * ctx->num_sms), 32, 0, ctx->d_vset, ctx->d_ranges,
              ctx->d_keys, ctx->d_vals, ctx->d_rec, ctx->d_rect_v, feat, ctx->cfg.tau, ctx->d_status, ctx->d_fbq,
-             kStFallback, ctx->d_xflag, ctx->d_xqueue);
+             kStFallback, ctx->d_xflag, ctx->d_xqueue, xstamp);
   auto xfn = composite_exact_kernel<C, TF, TO, true>;
   ART_LAUNCH_PDL(ctx, "composite_exact", xfn, kExactBlocks, 32, 0, (const ViewSet*)ctx->d_vset, vs.v[0], (TO*)nullptr,
              (float*)nullptr, ctx->d_ranges, ctx->d_keys, ctx->d_vals, ctx->d_rec, ctx->d_rect_v, feat, ctx->cfg.tau,
@@ -953,8 +985,7 @@ void split_pass(art_ctx* ctx, const ViewParams& v, void* F, float* A, int mode, 
     sk.xflag = ctx->d_xflag;
     sk.xqueue = ctx->d_xqueue;
   }
-  cudaMemsetAsync(ctx->d_status + kStItems, 0, 4 * sizeof(unsigned long long), ctx->stream);  // items .. next merge
-  cudaMemsetAsync(ctx->d_status + sk.qword, 0, sizeof(unsigned long long), ctx->stream);
+  if (list) zero_words(ctx, kPassWords | bit(sk.qword));  // (the first pass's words: zeroed by split_walk)
   // a re-walk covers a few tiles: shorter segments put more warps on them
   const int seg_len = list ? std::max(32, ctx->seg_len / 4) : ctx->seg_len;
   ART_LAUNCH_PDL(ctx, list ? "composite_replan" : "composite_plan", seg_plan_kernel, (ntiles + 255) / 256, 256, 0, ntiles,
@@ -963,14 +994,17 @@ void split_pass(art_ctx* ctx, const ViewParams& v, void* F, float* A, int mode, 
     auto cfn = composite_clear_kernel<C, TO>;
     ART_LAUNCH_PDL(ctx, "composite_clear", cfn, (ntiles + 7) / 8, 256, 0, ctx->d_ranges, v, (TO*)F, A);
   }
-  const int grid = ctx->composite_blocks;
+  // the re-walk of the tiles that failed the coarse check: a few tiles, so
+  // fewer persistent warps (and merge warps) than the first pass
+  const int grid = list ? std::min(ctx->composite_blocks, 2 * ctx->num_sms) : ctx->composite_blocks;
+  const int mgrid = list ? 4 * ctx->num_sms : 32 * ctx->num_sms;
   if (mode == kInterval) {
     auto kfn = composite_split_kernel<C, TF, TO, kInterval>;
     ART_LAUNCH_PDL(ctx, "composite_skip", kfn, grid, 32, 0, ctx->d_ranges, ctx->d_seg, ctx->d_items, ctx->d_keys,
                ctx->d_vals, ctx->d_rec, ctx->d_rect, feat, v, ctx->cfg.tau, (TO*)F, A, ctx->d_status, ctx->d_part,
                sk);
     auto mfn = composite_merge_kernel<C, TO, kInterval>;
-    ART_LAUNCH_PDL(ctx, "composite_merge", mfn, 32 * ctx->num_sms, 32, 0, ctx->d_seg, ctx->d_multi, v, ctx->cfg.tau, (TO*)F,
+    ART_LAUNCH_PDL(ctx, "composite_merge", mfn, mgrid, 32, 0, ctx->d_seg, ctx->d_multi, v, ctx->cfg.tau, (TO*)F,
                A, ctx->d_status, ctx->d_part, sk);
   } else if (mode == kSH) {
     auto kfn = composite_split_kernel<C, TF, TO, kSH>;
@@ -978,7 +1012,7 @@ void split_pass(art_ctx* ctx, const ViewParams& v, void* F, float* A, int mode, 
                    ctx->d_vals, ctx->d_rec, ctx->d_rect, feat, v, ctx->cfg.tau, (TO*)F, A, ctx->d_status, ctx->d_part,
                    sk);
     auto mfn = composite_merge_kernel<C, TO, kPlain>;
-    ART_LAUNCH_PDL(ctx, "composite_merge", mfn, 32 * ctx->num_sms, 32, 0, ctx->d_seg, ctx->d_multi, v, ctx->cfg.tau,
+    ART_LAUNCH_PDL(ctx, "composite_merge", mfn, mgrid, 32, 0, ctx->d_seg, ctx->d_multi, v, ctx->cfg.tau,
                    (TO*)F, A, ctx->d_status, ctx->d_part, sk);
   } else {
     auto kfn = composite_split_kernel<C, TF, TO, kPlain>;
@@ -986,7 +1020,7 @@ void split_pass(art_ctx* ctx, const ViewParams& v, void* F, float* A, int mode, 
                ctx->d_keys, ctx->d_vals, ctx->d_rec, ctx->d_rect, feat, v, ctx->cfg.tau, (TO*)F, A,
                ctx->d_status, ctx->d_part, sk);
     auto mfn = composite_merge_kernel<C, TO, kPlain>;
-    ART_LAUNCH_PDL(ctx, "composite_merge", mfn, 32 * ctx->num_sms, 32, 0, ctx->d_seg, ctx->d_multi, v, ctx->cfg.tau, (TO*)F,
+    ART_LAUNCH_PDL(ctx, "composite_merge", mfn, mgrid, 32, 0, ctx->d_seg, ctx->d_multi, v, ctx->cfg.tau, (TO*)F,
                A, ctx->d_status, ctx->d_part, sk);
   }
 }
@@ -1002,8 +1036,8 @@ void split_walk(art_ctx* ctx, const ViewParams& v, void* F, float* A, int mode, 
   SkipArgs sk = sk_in;
   sk.queue = ctx->d_fbq;
   sk.qword = kStFallback;
-  cudaMemsetAsync(ctx->d_xflag, 0, sizeof(uint32_t) * (size_t)ntiles, ctx->stream);
-  cudaMemsetAsync(ctx->d_status + kStExactQ, 0, sizeof(unsigned long long), ctx->stream);
+  sk.xstamp = next_xstamp(ctx, (size_t)ntiles);
+  zero_words(ctx, kPassWords | bit(kStFallback) | bit(kStFallback2) | bit(kStExactQ));
   split_pass<C, TF, TO>(ctx, v, F, A, mode, sk, nullptr, 0);
   const uint32_t* seq = ctx->d_fbq;
   int seq_word = kStFallback;
@@ -1011,6 +1045,7 @@ void split_walk(art_ctx* ctx, const ViewParams& v, void* F, float* A, int mode, 
     SkipArgs sp{};
     sp.queue = ctx->d_fbq2;
     sp.qword = kStFallback2;
+    sp.xstamp = sk.xstamp;
     split_pass<C, TF, TO>(ctx, v, F, A, kPlain, sp, ctx->d_fbq, kStFallback);
     seq = ctx->d_fbq2;
     seq_word = kStFallback2;
@@ -1026,6 +1061,7 @@ void split_walk(art_ctx* ctx, const ViewParams& v, void* F, float* A, int mode, 
   }
   sq.xflag = ctx->d_xflag;
   sq.xqueue = ctx->d_xqueue;
+  sq.xstamp = sk.xstamp;
   auto qfn = composite_queue_kernel<C, TF, TO, kPlain>;
   ART_LAUNCH_PDL(ctx, "composite_fallback", qfn, qgrid, 32, 0, ctx->d_ranges, ctx->d_keys, ctx->d_vals, ctx->d_rec,
              ctx->d_rect, feat, v, ctx->cfg.tau, (TO*)F, A, ctx->d_status, seq, seq_word, sq);
@@ -1142,6 +1178,7 @@ art_status launch_composite_skip(art_ctx* ctx, const ViewParams& v, void* F, int
   sk.thist = ctx->d_thist;
   sk.max_missed = ctx->cfg.max_missed;
   sk.margin = ctx->cfg.margin;
+  sk.tclass = ctx->d_tclass;  // (launch_tile_class ran for this view)
   return dispatch(ctx, v, F, F_dtype, A, nullptr, kInterval, sk);
 }
 

@@ -224,7 +224,8 @@ struct art_ctx {
   uint32_t* d_gvals = nullptr;            // [slots] smallest voxel id of the slot's cell
   int64_t grid_slots = 0;                 // power of two >= 2 n
   // ---- exact re-walk of tiles whose reorder buffer overflowed
-  uint32_t* d_xflag = nullptr;    // [tiles] queued already (zeroed per render)
+  uint32_t* d_xflag = nullptr;    // [tiles] stamp of the render that queued the tile (zeroed when allocated)
+  uint32_t xstamp = 0;            // the last render's stamp
   uint32_t* d_xqueue = nullptr;   // [tiles] the queue (count in status[kStExactQ])
   size_t d_xflag_bytes = 0, d_xqueue_bytes = 0;
   float2* d_xhit = nullptr;       // [blocks][32][kExactCap] per-lane hit lists (t0, chord) ...
@@ -232,6 +233,7 @@ struct art_ctx {
   // ---- split composite walk
   int seg_len = 256;              // list entries per segment
   int composite_blocks = 0;       // persistent one-warp blocks of the split walk
+  int composite_key = 0;          // (C, feature bytes) composite_blocks was computed for
   uint2* d_seg = nullptr;         // [tiles] (first segment, segment count)
   size_t d_seg_bytes = 0;
   uint32_t* d_items = nullptr;    // [segments] tile of each segment

@@ -35,8 +35,13 @@ __device__ void rodrigues(const float* r, float* R) {
 // every joint writes G_j = M_j [I | -rest_j].
 // skel: J parent indices stored as floats, then rest[J][3]; pose: r[J][3], R[3], T[3].
 __global__ void __launch_bounds__(kMaxJoints) fk_kernel(int J, const float* __restrict__ skel,
-                                                        const float* __restrict__ pose, float* __restrict__ G) {
+                                                        const float* __restrict__ pose, float* __restrict__ G,
+                                                        unsigned long long* __restrict__ status) {
   ART_PDL_ENTRY();
+  if (threadIdx.x == 0) {  // the pose's counters, accumulated by the skinning that follows
+    status[kStDegenerate] = 0ull;
+    status[kStRmax] = 0ull;
+  }
   __shared__ float sL[kMaxJoints][12];
   __shared__ float sM[kMaxJoints][12];
   __shared__ int sp[kMaxJoints];
@@ -469,7 +474,9 @@ void launch_grid_snap(art_ctx* ctx) {
              ctx->origin[1], ctx->origin[2], ctx->h, ctx->d_gkeys, ctx->d_gvals, mask, ctx->d_status);
 }
 
-void launch_fk(art_ctx* ctx) { ART_LAUNCH_PDL(ctx, "fk", fk_kernel, 1, kMaxJoints, 0, ctx->J, ctx->d_skel, ctx->d_pose, ctx->d_G); }
+void launch_fk(art_ctx* ctx) {
+  ART_LAUNCH_PDL(ctx, "fk", fk_kernel, 1, kMaxJoints, 0, ctx->J, ctx->d_skel, ctx->d_pose, ctx->d_G, ctx->d_status);
+}
 
 void launch_lbs(art_ctx* ctx) {
   int64_t n = ctx->n;
@@ -491,8 +498,7 @@ void launch_project_view(art_ctx* ctx, const ViewParams& v, short4* rect, uint32
 void launch_project(art_ctx* ctx, const ViewParams& v, uint32_t* hbin, float* htau) {
   int64_t n = ctx->n;
   unsigned grid = (unsigned)((n + 255) / 256);
-  const int ntiles = v.tiles_x * v.tiles_y;
-  cudaMemsetAsync(ctx->d_tcount, 0, sizeof(uint32_t) * (size_t)ntiles, ctx->stream);
+  const int ntiles = v.tiles_x * v.tiles_y;  // (the counts are zero: the last tile scan cleared them)
   ART_LAUNCH_PDL(ctx, "project", project_kernel, grid, 256, 0, n, ctx->d_geo, v, ctx->d_rect, ctx->d_q, ctx->d_cnt,
              ctx->d_sigma, hbin, htau, ctx->d_tcount, ctx->d_scan_state, (int)tile_scan_state_words(ntiles),
              ctx->d_status);
