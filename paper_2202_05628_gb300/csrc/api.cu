@@ -204,6 +204,7 @@ void free_all(art_ctx* ctx) {
   for (auto e : ctx->free_events) cudaEventDestroy(e);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+  if (ctx->ev_pose) cudaEventDestroy(ctx->ev_pose);
   if (ctx->side) cudaStreamDestroy(ctx->side);
 }
 
@@ -346,6 +347,7 @@ art_status art_create(art_ctx** out, void* cuda_stream) {
 void art_destroy(art_ctx* ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->stream);
+  if (ctx->side) cudaStreamSynchronize(ctx->side);
   free_all(ctx);
   delete ctx;
 }
@@ -483,6 +485,40 @@ art_status art_load_skeleton(art_ctx* ctx, int J, const int32_t* parent, const f
   return ART_OK;
 }
 
+// The side stream and its events, made on first use.
+static art_status ensure_side(art_ctx* ctx) {
+  if (ctx->side) return ART_OK;
+  cudaError_t e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_pose, cudaEventDisableTiming);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "side stream");
+  return ART_OK;
+}
+
+// The proposal's per-pose bias runs on the side stream beside FK and LBS;
+// work on the main stream that reads the bias or the proposal's weights
+// waits for it first (pose_bias_join).
+static art_status pose_bias_beside(art_ctx* ctx) {
+  art_status st = ensure_side(ctx);
+  if (st != ART_OK) return st;
+  cudaStream_t main_stream = ctx->stream;
+  cudaEventRecord(ctx->ev_fork, main_stream);
+  cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
+  ctx->stream = ctx->side;
+  launch_pose_bias(ctx);
+  cudaEventRecord(ctx->ev_pose, ctx->side);
+  ctx->stream = main_stream;
+  ctx->pose_bias_side = true;
+  return ART_OK;
+}
+
+static void pose_bias_join(art_ctx* ctx) {
+  if (!ctx->pose_bias_side) return;
+  cudaStreamWaitEvent(ctx->stream, ctx->ev_pose, 0);
+  ctx->pose_bias_side = false;
+}
+
 art_status art_set_pose(art_ctx* ctx, const float* axis_angle, const float R[3], const float T[3]) {
   if (!ctx) return ART_ERR_INVALID_ARG;
   if (ctx->n == 0 || ctx->J == 0) return fail(ctx, ART_ERR_STATE, "set_pose before load_octree/load_skeleton");
@@ -513,7 +549,7 @@ art_status art_set_pose(art_ctx* ctx, const float* axis_angle, const float R[3],
     }
     launch_grid_snap(ctx);
   }
-  if (ctx->prop_loaded) launch_pose_bias(ctx);
+  if (ctx->prop_loaded && (st = pose_bias_beside(ctx)) != ART_OK) return st;
   if ((st = launch_check(ctx, "set_pose")) != ART_OK) return st;
   ctx->posed = true;
   return ART_OK;
@@ -526,6 +562,7 @@ art_status art_load_proposal(art_ctx* ctx, const float* params, int64_t n_params
     return fail(ctx, ART_ERR_INVALID_ARG, "proposal params: %lld given, %d expected", (long long)n_params,
                 ART_PROPOSAL_PARAMS);
   if (ctx->J != 24) return fail(ctx, ART_ERR_STATE, "the proposal takes a 24-joint pose (load_skeleton first)");
+  pose_bias_join(ctx);  // (a bias still being computed reads the weights about to be replaced)
   art_status st = load_proposal(ctx, params);
   if (st != ART_OK) return st;
   if (ctx->posed) launch_pose_bias(ctx);
@@ -539,6 +576,7 @@ art_status art_run_proposal(art_ctx* ctx, int view, uint8_t* bins_out, float* lo
   if (!ctx->prop_loaded) return fail(ctx, ART_ERR_STATE, "run_proposal before load_proposal");
   if ((bins_out && !is_device_ptr(bins_out)) || (logits_out && !is_device_ptr(logits_out)))
     return fail(ctx, ART_ERR_INVALID_ARG, "run_proposal writes device arrays");
+  pose_bias_join(ctx);
   art_status st = launch_proposal(ctx, ctx->views[view], bins_out, logits_out, false);
   if (st != ART_OK) return st;
   return launch_check(ctx, "run_proposal");
@@ -607,16 +645,6 @@ art_status art_set_camera(art_ctx* ctx, int view, int W, int H, float fx, float 
   return ART_OK;
 }
 
-// The side stream and its two events, made on first use.
-static art_status ensure_side(art_ctx* ctx) {
-  if (ctx->side) return ART_OK;
-  cudaError_t e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "side stream");
-  return ART_OK;
-}
-
 // After the scan and scatter of a view: the work that needs only the tile
 // ranges and the coarse bound (tile classes and proposal for the learned
 // skip, the clear of the empty tiles) runs on the side stream while the
@@ -637,6 +665,7 @@ static art_status sort_beside(art_ctx* ctx, const ViewParams& v, void* F, int F_
   ctx->stream = main_stream;
   launch_tile_sort(ctx, v);
   cudaStreamWaitEvent(main_stream, ctx->ev_join, 0);
+  ctx->pose_bias_side = false;  // (the join follows the side stream's pose bias too)
   ctx->f_cleared = st == ART_OK;
   return st;
 }

@@ -471,6 +471,7 @@ __global__ void __launch_bounds__(256) bucket_emit_kernel(int64_t n, const uint3
     uint32_t pos = 0;
     if (tile != 0xFFFFFFFFu && lane == leader) pos = atomicAdd(toff + tile, (uint32_t)__popc(grp));
     pos = __shfl_sync(0xFFFFFFFFu, pos, leader) + (uint32_t)__popc(grp & ((1u << lane) - 1u));
+    const unsigned valid = __ballot_sync(0xFFFFFFFFu, tile != 0xFFFFFFFFu);
     if (tile == 0xFFFFFFFFu) continue;
     if (pos < (uint64_t)cap) {
       keys[pos] = (tile << v.depth_bits) | qq;
@@ -478,7 +479,19 @@ __global__ void __launch_bounds__(256) bucket_emit_kernel(int64_t n, const uint3
     } else {
       ++over;
     }
-    for (int b = hb0; b <= hb1; ++b) atomicAdd(thist + (size_t)tile * kPropBins + b, ht);
+    if (thist) {
+      // a voxel almost always spans one depth bin: lanes adding to the same
+      // (tile, bin) sum their bounds first and one of them adds the sum
+      const uint32_t hk = hb0 == hb1 ? tile * kPropBins + (uint32_t)hb0 : 0xFFFFFFFFu - (uint32_t)lane;
+      const unsigned g2 = __match_any_sync(valid, hk);
+      if (hb0 == hb1) {
+        float sum = 0.0f;
+        for (unsigned m = g2; m; m &= m - 1) sum += __shfl_sync(g2, ht, __ffs(m) - 1);
+        if (lane == __ffs(g2) - 1) atomicAdd(thist + hk, sum);
+      } else {
+        for (int b = hb0; b <= hb1; ++b) atomicAdd(thist + (size_t)tile * kPropBins + b, ht);
+      }
+    }
   }
   if (over) atomicAdd(status + kStOverflowInst, (unsigned long long)over);
 }

@@ -197,7 +197,8 @@ __device__ __forceinline__ void composite_tile(const int tile, const Seg& sg,
   float T = 1.0f;
   bool done = !inside;
   int nb = 0, hd = 0;      // pending hits and the ring slot of the earliest
-  float front = 3.4e38f;   // t0 of the earliest pending hit (while nb > 0)
+  Pend head{0.f, 0.f, 0u};  // the earliest pending hit (while nb > 0), kept in registers
+  float t_back = 0.0f;      // t0 of the latest pending hit (while nb > 0)
   uint32_t n_over = 0;
   const uint32_t qmask = (1u << v.depth_bits) - 1u;
   const float qinv = 1.0f / v.dscale;
@@ -238,9 +239,9 @@ __device__ __forceinline__ void composite_tile(const int tile, const Seg& sg,
   float lab_lo = 3.4e38f, lab_hi = -3.4e38f, lab_T = 1.0f;
 
   auto release_front = [&]() {
-    const Pend h{s_pt0[hd][lane], s_pdl[hd][lane], s_ppos[hd][lane]};
+    const Pend h = head;
     hd = (hd + 1) & (kPend - 1);
-    if (--nb > 0) front = s_pt0[hd][lane];
+    if (--nb > 0) head = Pend{s_pt0[hd][lane], s_pdl[hd][lane], s_ppos[hd][lane]};  // (used at the next release)
     const int ch = (int)(h.pos / NT), sl = (int)(h.pos % NT);
     float f[C];
     float sig;
@@ -345,17 +346,26 @@ __device__ __forceinline__ void composite_tile(const int tile, const Seg& sg,
     }
     // every instance of this chunk and later enters at t >= the first threshold
     const float thr0 = s_thr[0];
-    while (!done && nb > 0 && front < thr0) release_front();
+    while (!done && nb > 0 && head.t0 < thr0) release_front();
     uint32_t cand = transpose32(s_mask[lane], lane);
     if (done) cand = 0;
+    // the slab frame of the next candidate is read while the current one is tested
+    int nidx = cand ? __ffs(cand) - 1 : 0;
+    float4 f0 = s_rec[b][nidx][0], f1 = s_rec[b][nidx][1], f2 = s_rec[b][nidx][2], f3 = s_rec[b][nidx][3];
     while (cand) {
-      const int idx = __ffs(cand) - 1;
+      const int idx = nidx;
       cand &= cand - 1;
+      const float4 g0 = f0, g1 = f1, g2 = f2, g3 = f3;
+      if (cand) {
+        nidx = __ffs(cand) - 1;
+        f0 = s_rec[b][nidx][0];
+        f1 = s_rec[b][nidx][1];
+        f2 = s_rec[b][nidx][2];
+        f3 = s_rec[b][nidx][3];
+      }
       float t0, dl, e[3];
       int ax0, ax1;
-      if (!slab_hit(s_rec[b][idx][0], s_rec[b][idx][1], s_rec[b][idx][2], s_rec[b][idx][3], rd, v.znear, v.zfar, t0,
-                    dl, ax0, ax1, e))
-        continue;
+      if (!slab_hit(g0, g1, g2, g3, rd, v.znear, v.zfar, t0, dl, ax0, ax1, e)) continue;
       if (t0 < sg.t0_lo || t0 >= sg.t0_hi) continue;  // another segment's hit
       if constexpr (MODE == kInterval) {
         if (t0 + dl < t_lo || t0 > t_hi) continue;  // outside this pixel's interval
@@ -365,7 +375,7 @@ __device__ __forceinline__ void composite_tile(const int tile, const Seg& sg,
         // buffer full: release what this candidate's own bound allows (still
         // exact), and only if nothing can go, the earliest hit (counted)
         const float thr = s_thr[idx];
-        while (!done && nb > 0 && front < thr) release_front();
+        while (!done && nb > 0 && head.t0 < thr) release_front();
         if (!done && nb == kPend) {
           ++n_over;
           release_front();
@@ -375,25 +385,28 @@ __device__ __forceinline__ void composite_tile(const int tile, const Seg& sg,
           break;
         }
       }
-      // insertion from the back: move the later pending hits up one slot
       int q = nb;
-      while (q > 0) {
-        const int j = (hd + q - 1) & (kPend - 1);
-        const float bt = s_pt0[j][lane];
-        if (p.t0 > bt) break;
-        const Pend o{bt, s_pdl[j][lane], s_ppos[j][lane]};
-        if (!pless(p, o)) break;
-        const int k = (j + 1) & (kPend - 1);
-        s_pt0[k][lane] = o.t0;
-        s_pdl[k][lane] = o.dl;
-        s_ppos[k][lane] = o.pos;
-        --q;
+      if (nb > 0 && p.t0 <= t_back) {  // out of order: move the later pending hits up one slot
+        while (q > 0) {
+          const int j = (hd + q - 1) & (kPend - 1);
+          const float bt = s_pt0[j][lane];
+          if (p.t0 > bt) break;
+          const Pend o{bt, s_pdl[j][lane], s_ppos[j][lane]};
+          if (!pless(p, o)) break;
+          const int k = (j + 1) & (kPend - 1);
+          s_pt0[k][lane] = o.t0;
+          s_pdl[k][lane] = o.dl;
+          s_ppos[k][lane] = o.pos;
+          --q;
+        }
+      } else {
+        t_back = p.t0;  // appended: the latest pending hit
       }
       const int k = (hd + q) & (kPend - 1);
       s_pt0[k][lane] = p.t0;
       s_pdl[k][lane] = p.dl;
       s_ppos[k][lane] = p.pos;
-      if (q == 0) front = p.t0;
+      if (q == 0) head = p;
       ++nb;
     }
     if (__all_sync(0xffffffffu, done)) break;

@@ -115,7 +115,8 @@ struct art_ctx {
   // a second stream for work beside the bucket sort (tile classes, proposal,
   // clear of the empty tiles), forked from and joined into `stream` by events
   cudaStream_t side = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_pose = nullptr;
+  bool pose_bias_side = false;  // the proposal's pose bias is being computed on the side stream
   bool f_cleared = false;  // the empty tiles of this frame's F and A are cleared already
   std::string err;
   art_config cfg{};
