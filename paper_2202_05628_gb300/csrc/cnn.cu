@@ -436,7 +436,7 @@ art_status run_unet_f8(art_ctx* ctx, const ViewParams& v, const __nv_bfloat16* F
   unsigned int* am = ctx->d_f8_amax;
   const auto& L = ctx->layers;
   auto conv = [&](int in, int sin, int cin, int h, int w, int li, int out, int sout, int ld, int off, int up2,
-                  float* head_out) {
+                  float* head_out, int pooled = -1) {
     TcConv c;
     c.in = P(in);
     c.cin = cin;
@@ -458,6 +458,7 @@ art_status run_unet_f8(art_ctx* ctx, const ViewParams& v, const __nv_bfloat16* F
     c.w_scale = L[li].wscale;
     c.out_scale = out >= 0 ? sc + sout : nullptr;
     c.out_amax = out >= 0 ? am + sout : nullptr;
+    c.pool = pooled >= 0 ? P(pooled) : nullptr;  // (shares the output's scale)
     return launch_tc_conv(ctx, c);
   };
   auto network = [&]() -> art_status {
@@ -466,14 +467,11 @@ art_status run_unet_f8(art_ctx* ctx, const ViewParams& v, const __nv_bfloat16* F
   if ((st = (x)) != ART_OK) return st
     launch_quantize_input(ctx, F, (int64_t)H * W * nd.cin, sc + 0, P(fin), am + 0);
     ART_TRY(conv(fin, 0, nd.cin, H, W, 0, e0a, 1, c0, 0, 0, nullptr));
-    ART_TRY(conv(e0a, 1, c0, H, W, 1, cat0, 2, c1 + c0, c1, 0, nullptr));
-    launch_pool_fp8(ctx, P(cat0), c1 + c0, c1, P(p0), H, W, c0);
+    ART_TRY(conv(e0a, 1, c0, H, W, 1, cat0, 2, c1 + c0, c1, 0, nullptr, p0));
     ART_TRY(conv(p0, 2, c0, H / 2, W / 2, 2, e1a, 3, c1, 0, 0, nullptr));
-    ART_TRY(conv(e1a, 3, c1, H / 2, W / 2, 3, cat1, 4, c2 + c1, c2, 0, nullptr));
-    launch_pool_fp8(ctx, P(cat1), c2 + c1, c2, P(p1), H / 2, W / 2, c1);
+    ART_TRY(conv(e1a, 3, c1, H / 2, W / 2, 3, cat1, 4, c2 + c1, c2, 0, nullptr, p1));
     ART_TRY(conv(p1, 4, c1, H / 4, W / 4, 4, e2a, 5, c2, 0, 0, nullptr));
-    ART_TRY(conv(e2a, 5, c2, H / 4, W / 4, 5, cat2, 6, c3 + c2, c3, 0, nullptr));
-    launch_pool_fp8(ctx, P(cat2), c3 + c2, c3, P(p2), H / 4, W / 4, c2);
+    ART_TRY(conv(e2a, 5, c2, H / 4, W / 4, 5, cat2, 6, c3 + c2, c3, 0, nullptr, p2));
     ART_TRY(conv(p2, 6, c2, H / 8, W / 8, 6, e3a, 7, c3, 0, 0, nullptr));
     ART_TRY(conv(e3a, 7, c3, H / 8, W / 8, 7, cat2, 6, c3 + c2, 0, 1, nullptr));
     ART_TRY(conv(cat2, 6, c3 + c2, H / 4, W / 4, 8, d2a, 8, c2, 0, 0, nullptr));

@@ -47,7 +47,7 @@ struct TcParams {
   const float* head_w;   // [head_n][cout]
   const float* head_b;   // [head_n]
   int head_n, head_ld, head_off;  // head outputs, FP32 values per output pixel, channel of the first
-  __nv_bfloat16* pool;   // row-blocked kernel: fused 2x2 max pooling, dense [H/2][W/2][cout]
+  void* pool;            // row-blocked kernel: fused 2x2 max pooling, dense [H/2][W/2][cout] (BF16 or E4M3)
   unsigned long long* err;
 };
 
@@ -299,9 +299,64 @@ __device__ __forceinline__ void epi_row_pool(const TcParams& p, uint32_t taddr, 
       }
       const int Wp = p.W / 2, Hp = p.H / 2;
       if (!(x & 1) && (x >> 1) < Wp && (y >> 1) < Hp) {
-        uint4* dst = reinterpret_cast<uint4*>(p.pool + ((size_t)(y >> 1) * Wp + (x >> 1)) * N + c0);
+        uint4* dst =
+            reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(p.pool) + ((size_t)(y >> 1) * Wp + (x >> 1)) * N + c0);
 #pragma unroll
         for (int k = 0; k < 4; ++k) dst[k] = pk[k];
+      }
+    }
+  }
+}
+
+// E4M3 epilogue of one output row with the fused 2x2 max pooling: the row
+// is stored as epi_row stores it; the first row of a pair keeps its codes,
+// the second takes the byte-wise maximum with them and with the neighbouring
+// lane's (the codes of one scale order like their values, as the pooling
+// pass of its own compares them) and writes the pooled pixel.
+template <int N>
+__device__ __forceinline__ void epi_row_pool_f8(const TcParams& p, uint32_t taddr, int y, int x, const float* s_bias,
+                                                const float* s_wsc, float in_s, float out_inv, float& amax,
+                                                uint32_t* keep, bool second) {
+  const bool valid = x < p.W;
+#pragma unroll
+  for (int c0 = 0; c0 < N; c0 += 32) {
+    uint32_t r[32];
+    tmem_ld32(taddr + (uint32_t)c0, r);
+    uint4 pk[2];
+    uint16_t* w = reinterpret_cast<uint16_t*>(pk);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      float t0 = __uint_as_float(r[2 * j]) * (in_s * s_wsc[c0 + 2 * j]) + s_bias[c0 + 2 * j];
+      float t1 = __uint_as_float(r[2 * j + 1]) * (in_s * s_wsc[c0 + 2 * j + 1]) + s_bias[c0 + 2 * j + 1];
+      if (p.act == 1) {
+        t0 = fmaxf(t0, 0.0f);
+        t1 = fmaxf(t1, 0.0f);
+      }
+      if (valid) amax = fmaxf(amax, fmaxf(fabsf(t0), fabsf(t1)));
+      w[j] = (uint16_t)__nv_cvt_float2_to_fp8x2(make_float2(t0 * out_inv, t1 * out_inv), __NV_SATFINITE, __NV_E4M3);
+    }
+    if (valid) {
+      uint4* dst = reinterpret_cast<uint4*>(static_cast<uint8_t*>(p.out) + ((size_t)y * p.W + x) * p.ld_out +
+                                            p.ch_off + c0);
+      dst[0] = pk[0];
+      dst[1] = pk[1];
+    }
+    uint32_t* u = reinterpret_cast<uint32_t*>(pk);
+    if (!second) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) keep[c0 / 4 + k] = u[k];
+    } else {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const uint32_t m = __vmaxu4(keep[c0 / 4 + k], u[k]);
+        u[k] = __vmaxu4(m, __shfl_xor_sync(0xffffffffu, m, 1));
+      }
+      const int Wp = p.W / 2, Hp = p.H / 2;
+      if (!(x & 1) && (x >> 1) < Wp && (y >> 1) < Hp) {
+        uint4* dst = reinterpret_cast<uint4*>(static_cast<uint8_t*>(p.pool) + ((size_t)(y >> 1) * Wp + (x >> 1)) * N +
+                                              c0);
+        dst[0] = pk[0];
+        dst[1] = pk[1];
       }
     }
   }
@@ -499,8 +554,13 @@ struct RowCfg {
   static constexpr int kSlots = kRows;
   static constexpr int kBufCols = kSlots * N;  // columns of one accumulator buffer
   static constexpr int kHalo = 130;                                   // input pixels of a row box (128 + 2)
-  static constexpr int kBoxBytes = kHalo * KCB;
+  // input rows per stage (one box); two measured slower on the 32-channel
+  // layers (a deeper box per barrier round trip, half as many stages in flight)
+  static constexpr int kStageRows = 1;
+  static constexpr int kRowBytes = kHalo * KCB;                       // one input row of the box
+  static constexpr int kBoxBytes = kStageRows * kRowBytes;
   static constexpr int kStageBytes = (kBoxBytes + 1023) / 1024 * 1024;  // stages stay on swizzle-atom boundaries
+  static_assert((kRows + 2) % kStageRows == 0, "a unit's input rows fill whole stages");
 };
 
 struct RowParams {
@@ -538,8 +598,8 @@ __global__ void __launch_bounds__(kThreads, 2)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int cpt = rp.cpt;
-  const int n_stage_unit = (kRows + 2) * cpt;  // stages per unit
-  const int kStage = Cfg::kStageBytes;         // one box of 130 pixels: the three shifts are row offsets
+  const int n_stage_unit = (kRows + 2) / Cfg::kStageRows * cpt;  // stages per unit
+  const int kStage = Cfg::kStageBytes;  // one box of kStageRows rows of 130 pixels: the three shifts are row offsets
   // the swizzle follows the absolute shared-memory address, so a descriptor
   // may start at any row of the box: shift dx is the box from row dx on
   // resident weight block of (dy + 1, dx + 1, chunk): the three vertical
@@ -574,8 +634,8 @@ __global__ void __launch_bounds__(kThreads, 2)
   const uint32_t tmem_base = *tmem_slot;
   float amax = 0.0f;
 
-  // A stage is one input row and channel chunk in its three horizontal
-  // shifts (three boxes, one barrier round trip).
+  // A stage is kStageRows input rows of one channel chunk (one box, one
+  // barrier round trip); each row serves the three horizontal shifts.
   grid_dep_launch();  // the next layer may start its prologue where this one's CTAs leave SMs
   if (warp == 0) {
     // ------------------------------------------------------------ TMA
@@ -593,10 +653,10 @@ __global__ void __launch_bounds__(kThreads, 2)
         const int y0 = (u / p.tiles_per_row) * kRows, x0 = (u % p.tiles_per_row) * 128;
         for (int st = 0; st < n_stage_unit; ++st) {
           if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) break;
-          const int j = st / cpt, c = st - j * cpt;
+          const int jj = st / cpt, c = st - jj * cpt;
           uint8_t* dst = stages + (size_t)s * kStage;
           mbar_expect_tx(&full[s], (uint32_t)Cfg::kBoxBytes);
-          tma_load_3d(dst, &tmA, &full[s], c * Cfg::KC, x0 - 1, y0 - 1 + j);
+          tma_load_3d(dst, &tmA, &full[s], c * Cfg::KC, x0 - 1, y0 - 1 + jj * Cfg::kStageRows);
           if (++s == S) {
             s = 0;
             ph ^= 1u;
@@ -623,19 +683,23 @@ __global__ void __launch_bounds__(kThreads, 2)
             break;
           }
           tc_fence_after();
-          const int j = st / cpt, c = st - j * cpt;
-          const uint32_t a0 = smem_u32(stages + (size_t)s * kStage);
-          // input row j feeds output rows j - dyi of the unit for the taps dyi in [lo, hi]
-          // (slots R - 1 - j + lo ..., consecutive like the stacked taps' weight blocks)
-          const int lo = max(0, j - kRows + 1), hi = min(2, j);
-          const uint32_t dj = d0 + (uint32_t)((kRows - 1 - j + lo) * N);
-          const uint32_t idesc = F8 ? idesc_e4m3(128, (hi - lo + 1) * N) : idesc_bf16(128, (hi - lo + 1) * N);
+          const int jj = st / cpt, c = st - jj * cpt;
 #pragma unroll
-          for (int dxi = 0; dxi < 3; ++dxi) {
-            const uint32_t bw = wbase + (uint32_t)((wblk(0, dxi, c) + lo) * N * KCB);
+          for (int r = 0; r < Cfg::kStageRows; ++r) {
+            const int j = jj * Cfg::kStageRows + r;
+            const uint32_t a0 = smem_u32(stages + (size_t)s * kStage) + (uint32_t)(r * Cfg::kRowBytes);
+            // input row j feeds output rows j - dyi of the unit for the taps dyi in [lo, hi]
+            // (slots R - 1 - j + lo ..., consecutive like the stacked taps' weight blocks)
+            const int lo = max(0, j - kRows + 1), hi = min(2, j);
+            const uint32_t dj = d0 + (uint32_t)((kRows - 1 - j + lo) * N);
+            const uint32_t idesc = F8 ? idesc_e4m3(128, (hi - lo + 1) * N) : idesc_bf16(128, (hi - lo + 1) * N);
 #pragma unroll
-            for (int kk = 0; kk < KCB / 32; ++kk)
-              umma<F8>(dj, umma_desc<KCB>(a0 + dxi * KCB + kk * 32), umma_desc<KCB>(bw + kk * 32), idesc, 1u);
+            for (int dxi = 0; dxi < 3; ++dxi) {
+              const uint32_t bw = wbase + (uint32_t)((wblk(0, dxi, c) + lo) * N * KCB);
+#pragma unroll
+              for (int kk = 0; kk < KCB / 32; ++kk)
+                umma<F8>(dj, umma_desc<KCB>(a0 + dxi * KCB + kk * 32), umma_desc<KCB>(bw + kk * 32), idesc, 1u);
+            }
           }
           umma_commit(&empty[s]);
           if (++s == S) {
@@ -660,7 +724,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     const uint32_t tq = tmem_base + ((uint32_t)(qd * 32) << 16);  // this warp's lane quarter
     const float in_s = F8 ? *p.in_scale : 1.0f;
     const float out_inv = (F8 && p.out) ? 1.0f / *p.out_scale : 1.0f;
-    uint32_t keep[N / 2];  // fused pooling: the first row of the pair, packed BF16
+    uint32_t keep[N / 2];  // fused pooling: the first row of the pair, packed BF16 (or E4M3 codes)
     int buf = 0;
     uint32_t aph = 0;
     {  // zero every slot of both buffers, then release them to the MMA
@@ -688,7 +752,9 @@ __global__ void __launch_bounds__(kThreads, 2)
             else
               epi_pack<N, false>(p, ta, s_bias, s_wsc, in_s, out_inv, amax, x < p.W, pk);
             store_staged<N, false>(p, y0 + r, xw, lane, pk, stg);
-          } else {  // E4M3 rows are 32 or 64 bytes: stored directly (staging measured slower)
+          } else if (p.pool) {  // E4M3 rows are 32 or 64 bytes: stored directly (staging measured slower)
+            epi_row_pool_f8<N>(p, ta, y0 + r, x, s_bias, s_wsc, in_s, out_inv, amax, keep, (r & 1) != 0);
+          } else {
             epi_row<N, true>(p, ta, y0 + r, x, s_bias, s_head, s_wsc, in_s, out_inv, amax);
           }
         }
@@ -861,7 +927,7 @@ art_status launch_rows(art_ctx* ctx, const TcConv& c) {
   {
     cuuint64_t dims[3] = {(cuuint64_t)c.cin, (cuuint64_t)c.W, (cuuint64_t)c.H};
     cuuint64_t strides[2] = {(cuuint64_t)c.cin * kEs, (cuuint64_t)c.W * c.cin * kEs};
-    cuuint32_t box[3] = {(cuuint32_t)Cfg::KC, (cuuint32_t)Cfg::kHalo, 1};
+    cuuint32_t box[3] = {(cuuint32_t)Cfg::KC, (cuuint32_t)Cfg::kHalo, (cuuint32_t)Cfg::kStageRows};
     cuuint32_t es[3] = {1, 1, 1};
     CUresult r = g_encode(&tmA, dt, 3, (void*)c.in, dims, strides, box, es,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -899,7 +965,7 @@ art_status launch_rows(art_ctx* ctx, const TcConv& c) {
   p.head_n = c.head_n;
   p.head_ld = c.head_ld;
   p.head_off = c.head_off;
-  p.pool = F8 ? nullptr : (__nv_bfloat16*)c.pool;  // the FP8 network pools in a pass of its own
+  p.pool = c.pool;
   p.in_scale = c.in_scale;
   p.w_scale = c.w_scale;
   p.out_scale = c.out_scale;
@@ -911,12 +977,13 @@ art_status launch_rows(art_ctx* ctx, const TcConv& c) {
   const int tail =
       8 * (2 * 24 + 5) + 16 + 4 * N + 16 + 4 * (4 * 32 + 4) + 4 * N + 16 + (F8 ? 0 : 4 * 32 * 16 * RowOut<N, F8>::U);
   // two CTAs per SM (two issuing threads, one accumulator buffer each) when
-  // the resident weights and three stages fit in half the shared memory
+  // the resident weights and three input rows fit in half the shared memory
   const int half = 232448 / 2 - 1024 - rp.w_bytes - tail;
   auto kfn = conv_rows_kernel<N, KCB, F8>;
   cudaFuncAttributes fa;
   const bool regs2 = cudaFuncGetAttributes(&fa, kfn) == cudaSuccess && 2 * kThreads * fa.numRegs <= 65536;
-  const int ctas = (half >= 3 * Cfg::kStageBytes && regs2) ? 2 : 1;  // and both CTAs' registers fit
+  // (at least three input rows in flight per CTA) and both CTAs' registers fit
+  const int ctas = (half >= (3 + Cfg::kStageRows - 1) / Cfg::kStageRows * Cfg::kStageBytes && regs2) ? 2 : 1;
   const int avail = 232448 / ctas - 1024 - rp.w_bytes - tail;
   rp.nbuf = (ctas == 2 && Cfg::kBufCols > 128) ? 1 : 2;  // 512 TMEM columns per SM
   rp.n_stages = std::min(24, avail / Cfg::kStageBytes);
@@ -942,7 +1009,8 @@ art_status launch_tc_conv(art_ctx* ctx, const TcConv& c) {
   if (!tc_conv_ok(c)) return fail(ctx, ART_ERR_UNSUPPORTED, "tensor-core conv: unsupported shape");
   if (c.f8) {  // row bytes = channels per K chunk: 128, 64 or 32
     const int kcb = c.cin % 128 == 0 ? 128 : (c.cin % 64 == 0 ? 64 : 32);
-    if ((c.cout == 32 || c.cout == 64) && 9 * c.cin * c.cout <= kRowsMaxWeights && ctx->conv_rows) {
+    if ((c.cout == 32 || c.cout == 64) && 9 * c.cin * c.cout <= kRowsMaxWeights && ctx->conv_rows &&
+        (!c.pool || (!c.up2 && !c.rgba))) {
       // the narrow layers on the row-blocked kernel: K = 32 per FP8 MMA halves its instruction count
 #define ART_F8R(NN)                                                                \
   return kcb == 128 ? launch_rows<NN, 128, true>(ctx, c)                           \
@@ -954,15 +1022,19 @@ art_status launch_tc_conv(art_ctx* ctx, const TcConv& c) {
 #undef ART_F8R
     }
 #define ART_F8(NN)                                                             \
-  return kcb == 128 ? launch_typed<NN, 128, true>(ctx, c)                      \
-                    : (kcb == 64 ? launch_typed<NN, 64, true>(ctx, c) : launch_typed<NN, 32, true>(ctx, c))
+  st = kcb == 128 ? launch_typed<NN, 128, true>(ctx, c)                        \
+                  : (kcb == 64 ? launch_typed<NN, 64, true>(ctx, c) : launch_typed<NN, 32, true>(ctx, c))
+    art_status st;
     switch (c.cout) {
-      case 32: ART_F8(32);
-      case 64: ART_F8(64);
-      case 128: ART_F8(128);
-      default: ART_F8(256);
+      case 32: ART_F8(32); break;
+      case 64: ART_F8(64); break;
+      case 128: ART_F8(128); break;
+      default: ART_F8(256); break;
     }
 #undef ART_F8
+    if (st == ART_OK && c.pool)  // (the tap-by-tap kernel pools in a pass of its own)
+      launch_pool_fp8(ctx, (const uint8_t*)c.out, c.ld_out, c.ch_off, (uint8_t*)c.pool, c.H, c.W, c.cout);
+    return st;
   }
   const bool k64 = c.cin % 64 == 0;  // BF16: 64 channels = 128-B rows, else 32 = 64-B rows
   if ((c.cout == 32 || c.cout == 64) && 9 * c.cin * c.cout * 2 <= kRowsMaxWeights && ctx->conv_rows &&

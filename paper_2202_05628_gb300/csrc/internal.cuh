@@ -395,8 +395,8 @@ struct TcConv {
   const float* head_w;     // starting at channel head_off of head_ld per pixel
   const float* head_b;
   int head_n = 4, head_ld = 4, head_off = 0;
-  // BF16: also the 2x2 max pooling of the output, a dense [H/2][W/2][cout]
-  // tensor (fused into the row-blocked kernel's epilogue, else a pass of its own)
+  // also the 2x2 max pooling of the output, a dense [H/2][W/2][cout] tensor
+  // (BF16 or E4M3; fused into the row-blocked kernel's epilogue, else a pass of its own)
   void* pool = nullptr;
   // FP8 (E4M3) network: operands and output in E4M3; the accumulator is
   // dequantised by in_scale x w_scale[co], the output quantised by out_scale
