@@ -915,6 +915,8 @@ __global__ void maxpool2_fp8_kernel(const uint8_t* __restrict__ in, int ld, int 
 namespace {
 
 constexpr int kRowsMaxWeights = 80 * 1024;  // resident weights of the row-blocked kernel
+// E4M3: up to the 192 -> 64 layer (110.6 KB, one CTA per SM)
+constexpr int kRowsMaxWeightsF8 = 112 * 1024;
 
 template <int N, int KCB, bool F8>
 art_status launch_rows(art_ctx* ctx, const TcConv& c) {
@@ -1009,7 +1011,7 @@ art_status launch_tc_conv(art_ctx* ctx, const TcConv& c) {
   if (!tc_conv_ok(c)) return fail(ctx, ART_ERR_UNSUPPORTED, "tensor-core conv: unsupported shape");
   if (c.f8) {  // row bytes = channels per K chunk: 128, 64 or 32
     const int kcb = c.cin % 128 == 0 ? 128 : (c.cin % 64 == 0 ? 64 : 32);
-    if ((c.cout == 32 || c.cout == 64) && 9 * c.cin * c.cout <= kRowsMaxWeights && ctx->conv_rows &&
+    if ((c.cout == 32 || c.cout == 64) && 9 * c.cin * c.cout <= kRowsMaxWeightsF8 && ctx->conv_rows &&
         (!c.pool || (!c.up2 && !c.rgba))) {
       // the narrow layers on the row-blocked kernel: K = 32 per FP8 MMA halves its instruction count
 #define ART_F8R(NN)                                                                \
@@ -1092,11 +1094,36 @@ __global__ void quantize_weights_kernel(const float* __restrict__ w, int K, uint
 }
 
 // BF16 feature map -> E4M3 with the current input scale; records max |F|.
+// Sixteen values per thread and step (two 16-B loads, one 16-B store) when
+// both arrays are 16-byte aligned (vec); the rest pair by pair.
 __global__ void quantize_input_kernel(const __nv_bfloat16* __restrict__ in, int64_t m, const float* __restrict__ scale,
-                                      uint8_t* __restrict__ out, unsigned int* __restrict__ amax) {
+                                      uint8_t* __restrict__ out, unsigned int* __restrict__ amax, int vec) {
+  ART_PDL_ENTRY();
   const float inv = 1.0f / *scale;
   float a = 0.0f;
-  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 2; i < m; i += (int64_t)gridDim.x * blockDim.x * 2) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
+  const int64_t m16 = vec ? m / 16 : 0;
+  for (int64_t g = tid; g < m16; g += nth) {
+    const uint4* src = reinterpret_cast<const uint4*>(in + g * 16);
+    const uint4 x0 = src[0], x1 = src[1];
+    const uint32_t w[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+    uint32_t o[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      uint32_t u = 0;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const uint32_t b = w[2 * k + h];
+        const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&b));
+        a = fmaxf(a, fmaxf(fabsf(v.x), fabsf(v.y)));
+        u |= (uint32_t)(uint16_t)__nv_cvt_float2_to_fp8x2(make_float2(v.x * inv, v.y * inv), __NV_SATFINITE, __NV_E4M3)
+             << (16 * h);
+      }
+      o[k] = u;
+    }
+    *reinterpret_cast<uint4*>(out + g * 16) = make_uint4(o[0], o[1], o[2], o[3]);
+  }
+  for (int64_t i = m16 * 16 + tid * 2; i < m; i += nth * 2) {
     const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(in + i));
     a = fmaxf(a, fmaxf(fabsf(v.x), fabsf(v.y)));
     *reinterpret_cast<uint16_t*>(out + i) =
@@ -1110,6 +1137,7 @@ __global__ void quantize_input_kernel(const __nv_bfloat16* __restrict__ in, int6
 // Delayed scaling: next call's scale = max |value| of this call / 448; or a
 // fixed value (calibration).
 __global__ void update_scales_kernel(float* __restrict__ scale, unsigned int* __restrict__ amax, int n, float fixed) {
+  ART_PDL_ENTRY();
   const int i = threadIdx.x;
   if (i >= n) return;
   scale[i] = fixed > 0.0f ? fixed : fmaxf(__uint_as_float(amax[i]), 1e-12f) / kE4M3Max;
@@ -1124,12 +1152,14 @@ void launch_quantize_weights(art_ctx* ctx, const float* w, int cout, int K, uint
 
 void launch_quantize_input(art_ctx* ctx, const __nv_bfloat16* in, int64_t m, const float* scale, uint8_t* out,
                            unsigned int* amax) {
-  const int grid = (int)std::min<int64_t>((m / 2 + 255) / 256, (int64_t)ctx->num_sms * 8);
-  ART_LAUNCH(ctx, "quantize_f_fp8", quantize_input_kernel, grid, 256, 0, in, m, scale, out, amax);
+  const int vec = ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15) == 0;
+  const int64_t per = vec ? 16 : 2;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((m / per + 255) / 256, (int64_t)ctx->num_sms * 8));
+  ART_LAUNCH_PDL(ctx, "quantize_f_fp8", quantize_input_kernel, grid, 256, 0, in, m, scale, out, amax, vec);
 }
 
 void launch_update_scales(art_ctx* ctx, float* scale, unsigned int* amax, int n, float fixed) {
-  ART_LAUNCH(ctx, "fp8_scales", update_scales_kernel, 1, 32, 0, scale, amax, n, fixed);
+  ART_LAUNCH_PDL(ctx, "fp8_scales", update_scales_kernel, 1, 32, 0, scale, amax, n, fixed);
 }
 
 void launch_pool_fp8(art_ctx* ctx, const uint8_t* in, int ld, int ch_off, uint8_t* out, int H, int W, int C) {
