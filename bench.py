@@ -242,7 +242,10 @@ def roofline(kt, stats, peaks, form, n_vox, C, frames, conv_launch_ms=None):
         out.update(avg_ms=avg_ms, avg_ms_from="shading network called back to back, time / its 14 "
                    "convolution launches (its one pooling launch included)")
     if name.startswith("conv"):
-        per_launch = unet_flops(RES, RES) * frames / max(nl, 1)
+        # the FLOPs the network executes (BF16: the sub-pixel decoder convolution at level 0)
+        flops = unet_flops(RES, RES, subpixel=(net == "bf16"))
+        per_launch = flops * frames / max(nl, 1)
+        out.update(flops_per_frame=flops, flops_plain_definition=unet_flops(RES, RES))
         ach = per_launch / (avg_ms * 1e-3) / 1e12
         # measured peaks of MEASURED_PEAKS.json, else the profiling recipe's fallback figures: the
         # burst figure, since the launch time comes from the network called back to back in isolation
@@ -279,13 +282,13 @@ def roofline(kt, stats, peaks, form, n_vox, C, frames, conv_launch_ms=None):
     return out
 
 
-COMPOSITE_KERNELS = ("composite", "composite_skip", "composite_merge", "composite_refill", "composite_clear",
-                     "composite_plan", "composite_replan", "composite_fallback", "composite_exact")
+COMPOSITE_KERNELS = ("composite", "composite_skip", "composite_merge", "composite_clear", "composite_plan",
+                     "composite_fallback", "composite_exact")
 
 
 def composite_roofline(kt, stats, peaks, form, C, frames):
     """The composite stage as one unit: the summed per-frame time of its
-    kernels (interval / plain walk, merge, refill, clear, plans, fallback and
+    kernels (interval / plain walk, merge, clear, plan, sequential and
     exact walks) against its algorithmic bytes per frame: per instance the
     key and value (8 B), the 64-B voxel record, the 8-B pixel rectangle and
     the feature row (C x 2 B BF16 / 4 B FP32), each read once; per pixel the
@@ -304,13 +307,20 @@ def composite_roofline(kt, stats, peaks, form, C, frames):
             "note": "per-kernel CUDA-event times of the second timed pass (events add gaps between launches)"}
 
 
-def unet_flops(H, W, cin=32, ch=(32, 64, 128, 256)):
+def unet_flops(H, W, cin=32, ch=(32, 64, 128, 256), subpixel=False):
+    """FLOPs of the 4-level U-Net on an H x W map.  subpixel: as the BF16
+    tensor-core network executes it, level 0's decoder convolution over
+    [up2(d1) | e0] in its sub-pixel form (the upsampled part through 4 taps
+    per output pixel instead of 9)."""
     import scenegen as sg
     tot = 0
     shapes = sg.unet_layer_shapes(cin, ch)
     lvl = [0, 0, 1, 1, 2, 2, 3, 3, 2, 2, 1, 1, 0, 0, 0]
-    for (co, ci, k), l in zip(shapes, lvl):
-        tot += 2 * (H >> l) * (W >> l) * co * ci * k * k
+    for idx, ((co, ci, k), l) in enumerate(zip(shapes, lvl)):
+        if subpixel and idx == 12:
+            tot += 2 * H * W * co * (9 * ch[0] + 4 * ch[1])
+        else:
+            tot += 2 * (H >> l) * (W >> l) * co * ci * k * k
     return tot
 
 
@@ -656,7 +666,7 @@ def gpu_arm(args):
             pi, vi = step_indices(k)
             p = poses[pi]
             r.render_frame(vi, p.axis_angle, p.R, p.T, rgba)
-            n_fb += r.sync_status(raise_on_overflow=False)["fallback_tiles"]
+            n_fb += r.sync_status(raise_on_overflow=False)["check_fail_tiles"]
             rg = r.debug_buffer(7, np.uint32).reshape(-1, 2)[:tw * ((RES + 3) // 4)]
             n_act += int(np.sum(rg[:, 1] > rg[:, 0]))
         result["skip"] = {"fallback_tiles_per_frame": n_fb / N_POSES, "active_tiles_per_frame": n_act / N_POSES,

@@ -309,10 +309,12 @@ art_status art_render_frame(art_ctx* ctx, int view, const float* axis_angle, con
  * Coarse check: each voxel adds sigma_i 2 r_i (a bound of its optical depth on
  * any ray) to every depth bin its distance range |c_i - o| -+ r_i overlaps, in
  * every screen tile it covers.  A ray's lost mass is bounded by (1 - exp(-sum
- * of its tile's bins before bn)) + T_end (1 - exp(-sum after bf)) (empty: the
- * first term over all bins), T_end its transmittance after the interval; if
- * the bound of any ray of an 8 x 4 tile exceeds config.max_missed, the whole
- * tile is composited again without the interval (the fallback).
+ * of its tile's bins before the tile's interval)) + (1 - exp(-sum after it))
+ * (empty: the first term over all bins; the transmittance after the interval
+ * is bounded by 1).  The check runs with the proposal, before compositing: a
+ * tile whose bound exceeds config.max_missed is composited over its whole
+ * list instead of the interval, in the same pass (the fallback), and counted
+ * in art_stats.check_fail_tiles.
  */
 
 #define ART_PROPOSAL_PARAMS 27712 /* 64*107+64 + 3*(64*64+64) + 128*64+128 */
@@ -354,7 +356,7 @@ typedef struct {
   int skip;                /* ART_SKIP_PLAIN (default) or ART_SKIP_LEARNED: composite each ray only
                               over the depth interval its proposal predicts (art_load_proposal) */
   float max_missed;        /* learned skip: coarse-check threshold of lost transmittance mass
-                              (0 = default 1e-3); a tile with a ray above it is traversed again in full */
+                              (0 = default 1e-3); a tile above it is traversed in full */
   int margin;              /* learned skip: bins added on both sides of the predicted interval (default 0) */
   int segment;             /* composite: a tile's list is walked in segments of about this many entries by
                               separate warps and merged front to back (0 = default 256; >= 32) */
@@ -381,12 +383,15 @@ typedef struct {
   int64_t overflow_order;  /* pixels whose hits could not all be put in order: more than
                               1024 hits on one ray (result may be out of order) */
   int64_t kernel_launches; /* kernels launched by this context so far */
-  int64_t fallback_tiles;  /* learned skip: tiles of the last render traversed again in full */
+  int64_t fallback_tiles;  /* tiles of the last render walked again by the sequential walk: a pixel's
+                              stop (T < tau) fell inside a later segment of the split walk */
   int64_t exact_tiles;     /* tiles of the last render walked again exactly because a pixel
                               had more pending hits than its 16-entry reorder buffer holds */
   int64_t grid_cells;      /* ART_INDEX_GRID: occupied lattice cells of the last pose (the survivors) */
   int64_t forced_tiles;    /* learned skip: tiles of the last render whose coarse bound alone fixes the
                               walk (the whole range, or nothing), rendered without a prediction */
+  int64_t check_fail_tiles; /* learned skip: predicted tiles of the last render that failed the coarse
+                               check, composited over their whole list instead of the interval */
 } art_stats;
 
 /* Synchronise the stream, fill *out (may be NULL) and return
@@ -469,7 +474,8 @@ enum {
                              tensors without the input.  cat = [upsampled decoder | encoder] */
   ART_BUF_BINS = 10,      /* [H][W][2] uint8: proposal bins of the last learned-skip render (tiles
                              without instances are not predicted) */
-  ART_BUF_FALLBACK = 11,  /* [fallback_tiles] uint32: tiles of the last learned-skip render traversed again */
+  ART_BUF_FALLBACK = 11,  /* [check_fail_tiles] uint32: tiles of the last learned-skip render that failed
+                             the coarse check */
   ART_BUF_TAU_HIST = 12   /* [tiles][64] float: coarse optical-depth bound per (tile, depth bin) of the
                              last learned-skip or label render */
 };

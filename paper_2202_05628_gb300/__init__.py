@@ -50,7 +50,7 @@ class Stats(ctypes.Structure):
     _fields_ = [("instances", ctypes.c_int64), ("degenerate", ctypes.c_int64), ("overflow_inst", ctypes.c_int64),
                 ("overflow_order", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
                 ("fallback_tiles", ctypes.c_int64), ("exact_tiles", ctypes.c_int64), ("grid_cells", ctypes.c_int64),
-                ("forced_tiles", ctypes.c_int64)]
+                ("forced_tiles", ctypes.c_int64), ("check_fail_tiles", ctypes.c_int64)]
 
 
 def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -260,7 +260,7 @@ class Renderer:
         return dict(instances=s.instances, degenerate=s.degenerate, overflow_inst=s.overflow_inst,
                     overflow_order=s.overflow_order, kernel_launches=s.kernel_launches,
                     fallback_tiles=s.fallback_tiles, exact_tiles=s.exact_tiles, grid_cells=s.grid_cells,
-                    forced_tiles=s.forced_tiles, status=st)
+                    forced_tiles=s.forced_tiles, check_fail_tiles=s.check_fail_tiles, status=st)
 
     def kernel_times(self, reset: bool = False) -> dict:
         cap = 64

@@ -193,6 +193,7 @@ void free_all(art_ctx* ctx) {
     if (L.w32) cudaFree(L.w32);
     if (L.b32) cudaFree(L.b32);
     if (L.wbf) cudaFree(L.wbf);
+    if (L.wsub) cudaFree(L.wsub);
     if (L.w8) cudaFree(L.w8);
     if (L.wscale) cudaFree(L.wscale);
   }
@@ -285,7 +286,7 @@ art_status ensure_split_buffers(art_ctx* ctx, size_t ntiles) {
                    "segment partial sums")) != ART_OK)
     return st;
   if ((st = ensure(ctx, (void**)&ctx->d_fbq, &ctx->d_fbq_bytes, ntiles * 4, "fallback queue")) != ART_OK) return st;
-  if ((st = ensure(ctx, (void**)&ctx->d_fbq2, &ctx->d_fbq2_bytes, ntiles * 4, "second fallback queue")) != ART_OK)
+  if ((st = ensure(ctx, (void**)&ctx->d_fbq2, &ctx->d_fbq2_bytes, ntiles * 4, "coarse-check failures")) != ART_OK)
     return st;
   const uint32_t* xflag_was = ctx->d_xflag;
   if ((st = ensure(ctx, (void**)&ctx->d_xflag, &ctx->d_xflag_bytes, ntiles * 4, "exact re-walk flags")) != ART_OK)
@@ -897,6 +898,7 @@ art_status art_load_shader(art_ctx* ctx, const art_net_desc* desc, const float* 
     if (L.w32) cudaFree(L.w32);
     if (L.b32) cudaFree(L.b32);
     if (L.wbf) cudaFree(L.wbf);
+    if (L.wsub) cudaFree(L.wsub);
     if (L.w8) cudaFree(L.w8);
     if (L.wscale) cudaFree(L.wscale);
   }
@@ -930,6 +932,25 @@ art_status art_load_shader(art_ctx* ctx, const art_net_desc* desc, const float* 
       launch_quantize_weights(ctx, L.w32, L.cout, L.k * L.k * L.cin, L.w8, L.wscale);
     }
     ctx->layers.push_back(L);
+  }
+  if (st != ART_OK) return st;
+  // level 0's decoder convolution (after the concatenation with the
+  // upsampled level-1 output) in its sub-pixel form: its weight blocks
+  auto sub_blocks = [&](int li, int cs, int cu) -> art_status {
+    if (li >= (int)ctx->layers.size()) return ART_OK;
+    ConvLayer& L = ctx->layers[li];
+    if (L.k != 3 || L.cin != cs + cu || L.cin_pad != L.cin || !sub_conv_ok(L.cout, cs, cu, 2, 2)) return ART_OK;
+    art_status s2 = alloc(ctx, &L.wsub, sub_weight_elems(cs, cu), "sub-pixel weights");
+    if (s2 != ART_OK) return s2;
+    launch_sub_weights(ctx, L.w32, cs, cu, L.wsub);
+    L.sub_cs = cs;
+    L.sub_cu = cu;
+    return ART_OK;
+  };
+  if (compute_dtype == ART_BF16 && d.arch == ART_NET_UNET) st = sub_blocks(12, d.ch[0], d.ch[1]);
+  if (compute_dtype == ART_BF16 && d.arch == ART_NET_TWO_BRANCH) {
+    st = sub_blocks(12, d.ch[0], d.ch[1]);
+    if (st == ART_OK) st = sub_blocks(19, d.ach[0], d.ach[1]);
   }
   if (st != ART_OK) return st;
   ctx->net = d;
@@ -1033,6 +1054,7 @@ art_status art_sync_status(art_ctx* ctx, art_stats* out) {
     out->exact_tiles = (int64_t)h[kStExactQ];
     out->grid_cells = ctx->cfg.index == ART_INDEX_GRID ? (int64_t)h[kStGridCells] : 0;
     out->forced_tiles = (int64_t)h[kStForcedTiles];
+    out->check_fail_tiles = (int64_t)h[kStCheckFail];
   }
   if (h[kStTcError]) {
     art_status r = fail(ctx, ART_ERR_CUDA, "tensor-core convolution: %llu CTAs timed out waiting on their pipeline",
@@ -1182,9 +1204,9 @@ art_status art_debug_buffer(art_ctx* ctx, int which, void* dst, int64_t bytes, i
     case ART_BUF_BINS: src = ctx->d_bins; sz = ctx->d_bins ? (int64_t)ctx->d_bins_bytes : 0; break;
     case ART_BUF_FALLBACK: {
       unsigned long long nf = 0;
-      cudaMemcpy(&nf, ctx->d_status + kStFallback, sizeof(nf), cudaMemcpyDeviceToHost);
-      src = ctx->d_fbq;
-      sz = ctx->d_fbq ? (int64_t)std::min<unsigned long long>(nf, ctx->d_fbq_bytes / 4) * 4 : 0;
+      cudaMemcpy(&nf, ctx->d_status + kStCheckFail, sizeof(nf), cudaMemcpyDeviceToHost);
+      src = ctx->d_fbq2;
+      sz = ctx->d_fbq2 ? (int64_t)std::min<unsigned long long>(nf, ctx->d_fbq2_bytes / 4) * 4 : 0;
       break;
     }
     case ART_BUF_TAU_HIST: src = ctx->d_thist; sz = ctx->d_thist ? (int64_t)ctx->d_thist_bytes : 0; break;

@@ -312,9 +312,13 @@ size_t unet_tc_bytes(int H, int W, int levels, const int* ch) {
 // cat_l = [up(decoder below) | encoder skip] by the producing convolutions'
 // epilogues, so every decoder convolution reads one dense tensor; the last
 // convolution carries the 1x1 head + sigmoid in its epilogue, into head_n
-// FP32 channels at head_off of head_ld per pixel.  Arena order (from
-// arena_off): e0a, cat0, p0, e1a, cat1, p1, ..., bottleneck a, then the
-// decoders' first outputs from the deepest level up.
+// FP32 channels at head_off of head_ld per pixel.  Level 0's decoder
+// convolution runs in its sub-pixel form when its layer has the blocks
+// (launch_sub_conv): cat0's space then holds the skip tensor, x-phase
+// split, and the decoder output of level 1 at its own resolution (no 2x2
+// replicated copy).  Arena order (from arena_off): e0a, cat0, p0, e1a,
+// cat1, p1, ..., bottleneck a, then the decoders' first outputs from the
+// deepest level up.
 art_status unet_tc(art_ctx* ctx, int H, int W, const __nv_bfloat16* in, int cin, int lb, int levels, const int* ch,
                    float* out, int head_n, int head_ld, int head_off, size_t arena_off) {
   const size_t need = arena_off + unet_tc_bytes(H, W, levels, ch);
@@ -335,6 +339,14 @@ art_status unet_tc(art_ctx* ctx, int H, int W, const __nv_bfloat16* in, int cin,
   for (int l = levels - 2; l >= 0; --l) da[l] = take(l, ch[l], 0);
   const auto& Ls = ctx->layers;
   const int head = lb + 4 * levels - 2;
+  // level 0's decoder convolution in the sub-pixel form: its skip input
+  // (x-phase split) and its low-resolution input, both in cat0's space
+  const ConvLayer& L0 = Ls[lb + 4 * levels - 4];
+  const bool sub0 = L0.wsub && L0.sub_cs == ch[0] && L0.sub_cu == ch[1] && ctx->conv_rows &&
+                    sub_conv_ok(L0.cout, ch[0], ch[1], H, W);
+  __nv_bfloat16* sk0 = cat[0];
+  __nv_bfloat16* u0 = (__nv_bfloat16*)((char*)cat[0] + align256((size_t)H * W * ch[0] * 2));
+  int psplit = 0;
   auto conv = [&](const __nv_bfloat16* x, int xc, int l, int li, __nv_bfloat16* o, int ld, int o_off, int up2,
                   bool to_head, __nv_bfloat16* pooled) {
     TcConv c;
@@ -357,7 +369,13 @@ art_status unet_tc(art_ctx* ctx, int H, int W, const __nv_bfloat16* in, int cin,
     c.head_ld = head_ld;
     c.head_off = head_off;
     c.pool = pooled;
+    c.psplit = psplit;
     return launch_tc_conv(ctx, c);
+  };
+  // the block output of level l + 1 that level l's decoder reads upsampled
+  auto up_into = [&](const __nv_bfloat16* x, int l, int li) {
+    if (l == 0 && sub0) return conv(x, ch[1], 1, li, u0, ch[1], 0, 0, false, nullptr);
+    return conv(x, ch[l + 1], l + 1, li, cat[l], ch[l + 1] + ch[l], 0, 1, false, nullptr);
   };
   art_status st = ART_OK;
 #define ART_TRY(x)                  \
@@ -366,18 +384,39 @@ art_status unet_tc(art_ctx* ctx, int H, int W, const __nv_bfloat16* in, int cin,
   int xc = cin;
   for (int l = 0; l + 1 < levels; ++l) {  // encoder: the block output goes into cat_l as the skip, + 2x2 pooling
     ART_TRY(conv(x, xc, l, 2 * l, ea[l], ch[l], 0, 0, false, nullptr));
-    ART_TRY(conv(ea[l], ch[l], l, 2 * l + 1, cat[l], ch[l + 1] + ch[l], ch[l + 1], 0, false, pl[l]));
+    if (l == 0 && sub0) {  // dense and x-phase split for the sub-pixel decoder convolution
+      psplit = 1;
+      st = conv(ea[0], ch[0], 0, 1, sk0, ch[0], 0, 0, false, pl[0]);
+      psplit = 0;
+      if (st != ART_OK) return st;
+    } else {
+      ART_TRY(conv(ea[l], ch[l], l, 2 * l + 1, cat[l], ch[l + 1] + ch[l], ch[l + 1], 0, false, pl[l]));
+    }
     x = pl[l];
     xc = ch[l];
   }
   const int lL = levels - 1;  // bottleneck: its block output goes up x2 into cat of the level above
   ART_TRY(conv(x, xc, lL, 2 * lL, ea[lL], ch[lL], 0, 0, false, nullptr));
-  ART_TRY(conv(ea[lL], ch[lL], lL, 2 * lL + 1, cat[lL - 1], ch[lL] + ch[lL - 1], 0, 1, false, nullptr));
+  ART_TRY(up_into(ea[lL], lL - 1, 2 * lL + 1));
   int li = 2 * levels;
   for (int l = levels - 2; l >= 0; --l, li += 2) {
-    ART_TRY(conv(cat[l], ch[l + 1] + ch[l], l, li, da[l], ch[l], 0, 0, false, nullptr));
+    if (l == 0 && sub0) {
+      SubConv sc;
+      sc.skip = sk0;
+      sc.cs = ch[0];
+      sc.up = u0;
+      sc.cu = ch[1];
+      sc.H = H;
+      sc.W = W;
+      sc.w = L0.wsub;
+      sc.bias = L0.b32;
+      sc.out = da[0];
+      ART_TRY(launch_sub_conv(ctx, sc));
+    } else {
+      ART_TRY(conv(cat[l], ch[l + 1] + ch[l], l, li, da[l], ch[l], 0, 0, false, nullptr));
+    }
     if (l > 0) {
-      ART_TRY(conv(da[l], ch[l], l, li + 1, cat[l - 1], ch[l] + ch[l - 1], 0, 1, false, nullptr));  // up x2
+      ART_TRY(up_into(da[l], l - 1, li + 1));  // up x2
     } else {
       ART_TRY(conv(da[0], ch[0], 0, li + 1, nullptr, 0, 0, 0, true, nullptr));  // + fused 1x1 head, sigmoid
     }

@@ -48,6 +48,7 @@ struct TcParams {
   const float* head_b;   // [head_n]
   int head_n, head_ld, head_off;  // head outputs, FP32 values per output pixel, channel of the first
   void* pool;            // row-blocked kernel: fused 2x2 max pooling, dense [H/2][W/2][cout] (BF16 or E4M3)
+  int psplit;            // staged BF16 stores: x-phase split rows (even pixels, then odd)
   unsigned long long* err;
 };
 
@@ -245,7 +246,8 @@ __device__ __forceinline__ void store_staged(const TcParams& p, int y, int x0, i
       const int f = i * 32 + lane, q = f / U, c = f % U;
       const int x = x0 + q;
       if (x < p.W) {
-        const int X = p.up2 ? 2 * x + (d & 1) : x, Y = p.up2 ? 2 * y + (d >> 1) : y;
+        const int X = p.up2 ? 2 * x + (d & 1) : (p.psplit ? (x & 1) * (p.W >> 1) + (x >> 1) : x);
+        const int Y = p.up2 ? 2 * y + (d >> 1) : y;
         uint4* dst = reinterpret_cast<uint4*>(outb + (((size_t)Y * Wd + X) * p.ld_out + p.ch_off) * kEs) + c;
         *dst = stage[q * U + (c ^ (q % U))];
       }
@@ -876,6 +878,7 @@ art_status launch_typed(art_ctx* ctx, const TcConv& c) {
   p.head_ld = c.head_ld;
   p.head_off = c.head_off;
   p.pool = nullptr;  // pooled by a pass of its own
+  p.psplit = 0;
   p.err = ctx->d_status + kStTcError;
   auto kfn = conv_tc_kernel<N, KCB, F8>;
   cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem);
@@ -968,6 +971,7 @@ art_status launch_rows(art_ctx* ctx, const TcConv& c) {
   p.head_ld = c.head_ld;
   p.head_off = c.head_off;
   p.pool = c.pool;
+  p.psplit = c.psplit;
   p.in_scale = c.in_scale;
   p.w_scale = c.w_scale;
   p.out_scale = c.out_scale;
@@ -1000,15 +1004,21 @@ art_status launch_rows(art_ctx* ctx, const TcConv& c) {
 
 }  // namespace
 
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() { return encode_fn() ? g_encode : nullptr; }
+
 bool tc_conv_ok(const TcConv& c) {
   const bool n_ok = c.cout == 32 || c.cout == 64 || c.cout == 128 || c.cout == 256;
   const int al = c.f8 ? 16 : 8;  // 16-byte aligned output rows and channel offsets
+  // x-phase split output: BF16 through the row-blocked kernel's staged stores, even widths
+  const bool ps_ok = !c.psplit || (!c.f8 && !c.up2 && !c.rgba && c.W % 2 == 0 && (c.cout == 32 || c.cout == 64));
   return n_ok && (c.cin % 32 == 0) && c.cin >= 32 && (c.ld_out % al == 0) && (c.ch_off % al == 0) &&
-         (!c.rgba || c.cout == 32) && encode_fn();
+         (!c.rgba || c.cout == 32) && ps_ok && encode_fn();
 }
 
 art_status launch_tc_conv(art_ctx* ctx, const TcConv& c) {
   if (!tc_conv_ok(c)) return fail(ctx, ART_ERR_UNSUPPORTED, "tensor-core conv: unsupported shape");
+  if (c.psplit && !(9 * c.cin * c.cout * 2 <= kRowsMaxWeights && ctx->conv_rows))
+    return fail(ctx, ART_ERR_UNSUPPORTED, "x-phase split output: row-blocked kernel only");
   if (c.f8) {  // row bytes = channels per K chunk: 128, 64 or 32
     const int kcb = c.cin % 128 == 0 ? 128 : (c.cin % 64 == 0 ? 64 : 32);
     if ((c.cout == 32 || c.cout == 64) && 9 * c.cin * c.cout <= kRowsMaxWeightsF8 && ctx->conv_rows &&

@@ -422,24 +422,14 @@ __device__ __forceinline__ void composite_tile(const int tile, const Seg& sg,
     report_overflow(n_over, sk, status, lane);
     return;
   }
-  // a forced tile (walked over its whole list, or holding less than the
-  // threshold in all) passes the coarse check by construction
-  if constexpr (MODE == kLabel || MODE == kInterval) {
-    if (MODE == kLabel || !(sk.tclass && sk.tclass[tile] != 0)) {
+  // (the learned skip's coarse check ran with the proposal: a tile walked
+  // here over its predicted interval passed it, the others over their
+  // whole list)
+  if constexpr (MODE == kLabel) {
+    {
       __shared__ float s_pre[kPropBins];
       const float tot = tile_hist_prefix(sk.thist + (size_t)tile * kPropBins, s_pre, lane);
-      if constexpr (MODE == kInterval) {  // coarse check of the lost mass
-        bool fail = false;
-        if (inside) {
-          const float front = empty ? tot : (bn > 0 ? s_pre[bn - 1] : 0.0f);
-          const float back = empty ? 0.0f : tot - s_pre[bf];
-          fail = -expm1f(-front) + T * -expm1f(-back) > sk.max_missed;
-        }
-        if (__any_sync(0xffffffffu, fail) && lane == 0) {
-          const unsigned long long q = atomicAdd(status + sk.qword, 1ull);
-          sk.queue[q] = (uint32_t)tile;
-        }
-      } else {  // label bins: keep the significant hits and pass the check
+      {  // label bins: keep the significant hits and pass the check
         const float budget = kLabelBudget * sk.max_missed;
         const float tau_b = -log1pf(-budget);
         const bool c0 = (lane == 0 ? 0.0f : s_pre[lane - 1]) <= tau_b;
@@ -595,8 +585,8 @@ __global__ void __launch_bounds__(32, kCompositeWarps) composite_split_views_ker
   }
 }
 
-// Merge of the segments of the tiles with two or more: outputs, the coarse
-// check of the learned skip, and the fallback queue.
+// Merge of the segments of the tiles with two or more: outputs, and the
+// queue of the tiles whose stop falls inside a later segment.
 // Channels merged by one warp: a split tile is merged by C / kMergeCh warps,
 // each owning a channel group (the transmittance and the flags are computed
 // by all of them; group 0 writes A and queues the tile).
@@ -661,40 +651,12 @@ __device__ __forceinline__ void merge_tile(int tile, int tl, int grp, int lane, 
       P *= tq[j];
     }
   }
-  bool fail = false;
-  if constexpr (MODE == kInterval) {  // coarse check of the lost mass over the tile's union interval
-    if (grp == 0 && !(sk.tclass && sk.tclass[tile] != 0)) {  // (forced tiles pass by construction)
-      __shared__ float s_pre[kPropBins];
-      const float tot = tile_hist_prefix(sk.thist + (size_t)tile * kPropBins, s_pre, lane);
-      int lo_b = kPropBins, hi_b = -1;
-      if (inside) {
-        const uchar2 b = sk.bins[(size_t)py * v.W + px];
-        if (b.y >= b.x) {
-          lo_b = b.x;
-          hi_b = b.y;
-        }
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        lo_b = min(lo_b, __shfl_xor_sync(0xffffffffu, lo_b, o));
-        hi_b = max(hi_b, __shfl_xor_sync(0xffffffffu, hi_b, o));
-      }
-      const bool empty = hi_b < lo_b;
-      const int bn = empty ? lo_b : max(lo_b - sk.margin, 0);
-      const int bf = empty ? hi_b : min(hi_b + sk.margin, kPropBins - 1);
-      if (inside) {
-        const float front = empty ? tot : (bn > 0 ? s_pre[bn - 1] : 0.0f);
-        const float back = empty ? 0.0f : tot - s_pre[bf];
-        fail = -expm1f(-front) + T * -expm1f(-back) > sk.max_missed;
-      }
-    }
-  }
   if (inside) {
     const size_t pix = (size_t)py * v.W + px;
     store_group<C, TO>(Fout + pix * C + grp * CG, acc);
     if (grp == 0 && Aout) Aout[pix] = 1.0f - T;
   }
-  if (grp == 0 && __any_sync(0xffffffffu, (redo || fail) && inside) && lane == 0)
+  if (grp == 0 && __any_sync(0xffffffffu, redo && inside) && lane == 0)
     sk.queue[atomicAdd(status + sk.qword, 1ull)] = (uint32_t)tile;
 }
 
@@ -984,13 +946,11 @@ void views_dtypes(art_ctx* ctx, const ViewSet& vs, int F_dtype) {
   }
 }
 
-// One split pass, plain or learned-skip, over all tiles or the tiles listed
-// in `list` (count in status[list_word]): plan the segments, walk them with
-// persistent warps, merge the split tiles; tiles that need the sequential
-// walk go to sk.queue (count in status[sk.qword]).
+// One split pass, plain, learned-skip or SH: plan the segments, walk them
+// with persistent warps, merge the split tiles; tiles that need the
+// sequential walk go to sk.queue (count in status[sk.qword]).
 template <int C, typename TF, typename TO>
-void split_pass(art_ctx* ctx, const ViewParams& v, void* F, float* A, int mode, const SkipArgs& sk_in,
-                const uint32_t* list, int list_word) {
+void split_pass(art_ctx* ctx, const ViewParams& v, void* F, float* A, int mode, const SkipArgs& sk_in) {
   const int ntiles = v.tiles_x * v.tiles_y;
   const TF* feat = (const TF*)ctx->d_feat;
   SkipArgs sk = sk_in;
@@ -998,19 +958,14 @@ void split_pass(art_ctx* ctx, const ViewParams& v, void* F, float* A, int mode, 
     sk.xflag = ctx->d_xflag;
     sk.xqueue = ctx->d_xqueue;
   }
-  if (list) zero_words(ctx, kPassWords | bit(sk.qword));  // (the first pass's words: zeroed by split_walk)
-  // a re-walk covers a few tiles: shorter segments put more warps on them
-  const int seg_len = list ? std::max(32, ctx->seg_len / 4) : ctx->seg_len;
-  ART_LAUNCH_PDL(ctx, list ? "composite_replan" : "composite_plan", seg_plan_kernel, (ntiles + 255) / 256, 256, 0, ntiles,
-             ctx->d_ranges, seg_len, ctx->d_seg, ctx->d_items, ctx->d_multi, ctx->d_status, list, list_word);
-  if (!list && !ctx->f_cleared) {
+  ART_LAUNCH_PDL(ctx, "composite_plan", seg_plan_kernel, (ntiles + 255) / 256, 256, 0, ntiles, ctx->d_ranges,
+                 ctx->seg_len, ctx->d_seg, ctx->d_items, ctx->d_multi, ctx->d_status, (const uint32_t*)nullptr, 0);
+  if (!ctx->f_cleared) {
     auto cfn = composite_clear_kernel<C, TO>;
     ART_LAUNCH_PDL(ctx, "composite_clear", cfn, (ntiles + 7) / 8, 256, 0, ctx->d_ranges, v, (TO*)F, A);
   }
-  // the re-walk of the tiles that failed the coarse check: a few tiles, so
-  // fewer persistent warps (and merge warps) than the first pass
-  const int grid = list ? std::min(ctx->composite_blocks, 2 * ctx->num_sms) : ctx->composite_blocks;
-  const int mgrid = list ? 4 * ctx->num_sms : 32 * ctx->num_sms;
+  const int grid = ctx->composite_blocks;
+  const int mgrid = 32 * ctx->num_sms;
   if (mode == kInterval) {
     auto kfn = composite_split_kernel<C, TF, TO, kInterval>;
     ART_LAUNCH_PDL(ctx, "composite_skip", kfn, grid, 32, 0, ctx->d_ranges, ctx->d_seg, ctx->d_items, ctx->d_keys,
@@ -1029,7 +984,7 @@ void split_pass(art_ctx* ctx, const ViewParams& v, void* F, float* A, int mode, 
                    (TO*)F, A, ctx->d_status, ctx->d_part, sk);
   } else {
     auto kfn = composite_split_kernel<C, TF, TO, kPlain>;
-    ART_LAUNCH_PDL(ctx, list ? "composite_refill" : "composite", kfn, grid, 32, 0, ctx->d_ranges, ctx->d_seg, ctx->d_items,
+    ART_LAUNCH_PDL(ctx, "composite", kfn, grid, 32, 0, ctx->d_ranges, ctx->d_seg, ctx->d_items,
                ctx->d_keys, ctx->d_vals, ctx->d_rec, ctx->d_rect, feat, v, ctx->cfg.tau, (TO*)F, A,
                ctx->d_status, ctx->d_part, sk);
     auto mfn = composite_merge_kernel<C, TO, kPlain>;
@@ -1038,10 +993,10 @@ void split_pass(art_ctx* ctx, const ViewParams& v, void* F, float* A, int mode, 
   }
 }
 
-// Plain composite: one split pass, then the sequential walk of the tiles
-// whose stop fell inside a later segment.  Learned skip: the interval pass,
-// then a plain split pass over the tiles that failed the coarse check, then
-// the sequential walk of that pass's stop cases.
+// One split pass (plain, learned-skip intervals or SH features), then the
+// sequential walk of the tiles whose stop fell inside a later segment.
+// With the learned skip, the tiles that failed the coarse check (run with
+// the proposal) are walked in full by the same pass.
 template <int C, typename TF, typename TO>
 void split_walk(art_ctx* ctx, const ViewParams& v, void* F, float* A, int mode, const SkipArgs& sk_in) {
   const int ntiles = v.tiles_x * v.tiles_y;
@@ -1050,19 +1005,10 @@ void split_walk(art_ctx* ctx, const ViewParams& v, void* F, float* A, int mode, 
   sk.queue = ctx->d_fbq;
   sk.qword = kStFallback;
   sk.xstamp = next_xstamp(ctx, (size_t)ntiles);
-  zero_words(ctx, kPassWords | bit(kStFallback) | bit(kStFallback2) | bit(kStExactQ));
-  split_pass<C, TF, TO>(ctx, v, F, A, mode, sk, nullptr, 0);
+  zero_words(ctx, kPassWords | bit(kStFallback) | bit(kStExactQ));
+  split_pass<C, TF, TO>(ctx, v, F, A, mode, sk);
   const uint32_t* seq = ctx->d_fbq;
-  int seq_word = kStFallback;
-  if (mode == kInterval) {  // the tiles that failed the check, walked in full (split again)
-    SkipArgs sp{};
-    sp.queue = ctx->d_fbq2;
-    sp.qword = kStFallback2;
-    sp.xstamp = sk.xstamp;
-    split_pass<C, TF, TO>(ctx, v, F, A, kPlain, sp, ctx->d_fbq, kStFallback);
-    seq = ctx->d_fbq2;
-    seq_word = kStFallback2;
-  }
+  const int seq_word = kStFallback;
   const int qgrid = std::min(ntiles, 16 * ctx->num_sms);
   SkipArgs sq{};
   if (mode == kSH) {  // the stop cases of SH features: their sequential walk evaluates the harmonics

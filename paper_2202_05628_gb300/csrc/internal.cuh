@@ -4,6 +4,8 @@
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -34,7 +36,7 @@ enum StatusWord {
   kStNext = 10,         // next segment to walk (work counter)
   kStNextMerge = 11,    // next split tile to merge (work counter)
   kStRmax = 12,         // largest voxel bounding radius of the last pose (float bits)
-  kStFallback2 = 13,    // learned skip: tiles of the full pass whose stop needs the sequential walk
+  kStFallback2 = 13,    // (unused)
   kStSortTiles = 14,    // binning: tiles whose bucket needs sorting
   kStSortNext = 15,     // binning: next bucket to sort (work counter)
   kStSortBig = 16,      // binning: buckets sorted by a whole block
@@ -46,7 +48,8 @@ enum StatusWord {
   kStGridCells = 22,    // lattice index: occupied cells of the last pose
   kStPredGroups = 23,   // learned skip: tile groups holding a tile whose interval the proposal predicts
   kStForcedTiles = 24,  // learned skip: tiles walked in full (or not at all) without a prediction
-  kStWords = 25
+  kStCheckFail = 25,    // learned skip: predicted tiles that failed the coarse check, walked in full (listed in d_fbq2)
+  kStWords = 26
 };
 
 // Per-view camera, with host-precomputed ray frame.
@@ -93,6 +96,11 @@ struct ConvLayer {
   float* w32 = nullptr;        // [cout][k][k][cin] FP32
   float* b32 = nullptr;        // [cout]
   __nv_bfloat16* wbf = nullptr;  // [cout][k*k*cin] BF16 (K-major)
+  // the first decoder convolution of a level-0 U-Net block in its sub-pixel
+  // form (launch_sub_conv): BF16 weight blocks of the skip part, then of the
+  // low-resolution part; sub_cs / sub_cu = their input channels
+  __nv_bfloat16* wsub = nullptr;
+  int sub_cs = 0, sub_cu = 0;
   uint8_t* w8 = nullptr;       // [cout][k*k*cin] E4M3
   float* wscale = nullptr;     // [cout] FP8 per-output-channel scale
 };
@@ -209,9 +217,9 @@ struct art_ctx {
   uint32_t* d_hbin = nullptr;     // [n] per-voxel depth-bin range b0 | b1 << 8 (0xFFFF: none)
   float* d_htau = nullptr;        // [n] per-voxel optical-depth bound sigma 2 r
   int64_t hist_n_cap = 0;
-  uint32_t* d_fbq = nullptr;      // [tiles] fallback queue
+  uint32_t* d_fbq = nullptr;      // [tiles] tiles for the sequential walk (stop inside a later segment)
   size_t d_fbq_bytes = 0;
-  uint32_t* d_fbq2 = nullptr;     // [tiles] second queue (sequential walk after a refill pass)
+  uint32_t* d_fbq2 = nullptr;     // [tiles] learned skip: tiles that failed the coarse check
   size_t d_fbq2_bytes = 0;
   // ---- several views in one pass (art_render_views)
   short4* d_rect_v = nullptr;     // [views][n] per-view pixel rects, depth quanta, tile counts
@@ -398,6 +406,10 @@ struct TcConv {
   // also the 2x2 max pooling of the output, a dense [H/2][W/2][cout] tensor
   // (BF16 or E4M3; fused into the row-blocked kernel's epilogue, else a pass of its own)
   void* pool = nullptr;
+  // BF16 output stored x-phase split: row y holds the even pixels, then the
+  // odd ones ([H][2][W/2][ld_out]), the layout launch_sub_conv reads its
+  // skip input in (row-blocked kernel, BF16 only)
+  int psplit = 0;
   // FP8 (E4M3) network: operands and output in E4M3; the accumulator is
   // dequantised by in_scale x w_scale[co], the output quantised by out_scale
   // and its max |value| recorded in out_amax (float bits).
@@ -409,6 +421,30 @@ struct TcConv {
 };
 bool tc_conv_ok(const TcConv& c);
 art_status launch_tc_conv(art_ctx* ctx, const TcConv& c);
+// cuTensorMapEncodeTiled from the driver (null when unavailable)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
+
+// Sub-pixel form of conv3x3 + ReLU over the concatenation [up2(u) | s] (the
+// first convolution of a U-Net decoder block at level 0): 32 output
+// channels at H x W; s = the skip tensor, x-phase split ([H][2][W/2][cs]),
+// u = the low-resolution tensor ([H/2][W/2][cu]) that nearest x2
+// upsampling would repeat; w = the layer's wsub blocks.
+struct SubConv {
+  const void* skip;
+  int cs;
+  const void* up;
+  int cu;
+  int H, W;
+  const void* w;
+  const float* bias;
+  void* out;  // [H][W][32] BF16
+};
+bool sub_conv_ok(int cout, int cs, int cu, int H, int W);
+size_t sub_weight_elems(int cs, int cu);
+// Builds wsub from the layer's FP32 weights [32][3][3][cu + cs] (channels
+// of the low-resolution part first, as in the concatenation).
+void launch_sub_weights(art_ctx* ctx, const float* w32, int cs, int cu, __nv_bfloat16* wsub);
+art_status launch_sub_conv(art_ctx* ctx, const SubConv& c);
 void launch_pool_bf16(art_ctx* ctx, const __nv_bfloat16* in, int ld, int ch_off, __nv_bfloat16* out, int H, int W,
                       int C);
 void launch_pool_fp8(art_ctx* ctx, const uint8_t* in, int ld, int ch_off, uint8_t* out, int H, int W, int C);

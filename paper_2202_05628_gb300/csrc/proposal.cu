@@ -53,8 +53,16 @@ struct PropParams {
   int active_only;         // only the groups listed in agroups (count: *n_active)
   const uint32_t* agroups;
   const unsigned long long* n_active;
-  const uint8_t* tclass;   // per tile: predict only class 0 (null: every tile)
+  uint8_t* tclass;         // per tile: predict only class 0 (null: every tile); failed checks become class 1
   uint8_t* bins;           // [H][W][2] or null
+  // with tclass: the coarse check of each predicted tile (tile depth-bin
+  // bounds thist, threshold max_missed, union widened by margin); failing
+  // tiles are listed in fail_list (count *fail_count)
+  const float* thist;
+  float max_missed;
+  int margin;
+  uint32_t* fail_list;
+  unsigned long long* fail_count;
   float* logits;           // [H][W][128] or null
   unsigned long long* err;
 };
@@ -221,8 +229,57 @@ __global__ void __launch_bounds__(128) proposal_kernel(PropParams p) {
             }
           }
         }
-        if (p.bins && inside && (!p.tclass || p.tclass[tile] == 0))
-          reinterpret_cast<uchar2*>(p.bins)[pix] = make_uchar2((uint8_t)bn, (uint8_t)bf);
+        const bool pred = tile < ntiles && (!p.tclass || p.tclass[tile] == 0);  // (uniform over the warp)
+        if (p.bins && inside && pred) reinterpret_cast<uchar2*>(p.bins)[pix] = make_uchar2((uint8_t)bn, (uint8_t)bf);
+        if (p.bins && p.tclass && pred) {
+          // Coarse check of the tile's interval (the union of its pixels'
+          // predictions, widened by the margin, as the composite walks it):
+          // lost mass <= (1 - e^-front) + (1 - e^-back), front / back = the
+          // tile's optical-depth bound in the bins before / after the
+          // interval (T_end <= 1 bounds the back part).  A tile that fails is
+          // walked in full in the same pass: its pixels get bins (0, 63) and
+          // the tile class 1, like the tiles no prediction can change.
+          int lo_b = kPropBins, hi_b = -1;
+          if (inside && bf >= bn) {
+            lo_b = bn;
+            hi_b = bf;
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            lo_b = min(lo_b, __shfl_xor_sync(0xffffffffu, lo_b, o));
+            hi_b = max(hi_b, __shfl_xor_sync(0xffffffffu, hi_b, o));
+          }
+          const bool empty = hi_b < lo_b;
+          const int b_n = empty ? lo_b : max(lo_b - p.margin, 0);
+          const int b_f = empty ? hi_b : min(hi_b + p.margin, kPropBins - 1);
+          const float* th = p.thist + (size_t)tile * kPropBins;
+          float p0 = th[lane], p1 = th[32 + lane];  // inclusive prefix sums over the 64 bins
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const float a = __shfl_up_sync(0xffffffffu, p0, o), b = __shfl_up_sync(0xffffffffu, p1, o);
+            if (lane >= o) {
+              p0 += a;
+              p1 += b;
+            }
+          }
+          p1 += __shfl_sync(0xffffffffu, p0, 31);
+          const float tot = __shfl_sync(0xffffffffu, p1, 31);
+          auto pre = [&](int k) {  // prefix through bin k (k warp-uniform)
+            const float x = __shfl_sync(0xffffffffu, k < 32 ? p0 : p1, k & 31);
+            return k < 0 ? 0.0f : x;
+          };
+          const float f_pre = pre(b_n - 1), b_pre = pre(b_f);
+          const float front = empty ? tot : f_pre;
+          const float back = empty ? 0.0f : tot - b_pre;
+          const bool fail = -expm1f(-front) + -expm1f(-back) > p.max_missed;
+          if (fail && __any_sync(0xffffffffu, inside)) {
+            if (inside) reinterpret_cast<uchar2*>(p.bins)[pix] = make_uchar2(0, kPropBins - 1);
+            if (lane == 0) {
+              p.tclass[tile] = 1;
+              p.fail_list[atomicAdd(p.fail_count, 1ull)] = (uint32_t)tile;
+            }
+          }
+        }
         tc_fence_before();
         __syncthreads();  // TMEM and the input rows are reused by the next group
       }
@@ -355,7 +412,9 @@ __global__ void __launch_bounds__(128) tile_class_kernel(ViewParams v, const uin
 }
 
 void launch_tile_class(art_ctx* ctx, const ViewParams& v, uint8_t* bins) {
-  cudaMemsetAsync(ctx->d_status + kStPredGroups, 0, 2 * sizeof(unsigned long long), ctx->stream);
+  // (kStPredGroups, kStForcedTiles, kStCheckFail)
+  static_assert(kStForcedTiles == kStPredGroups + 1 && kStCheckFail == kStPredGroups + 2, "status words");
+  cudaMemsetAsync(ctx->d_status + kStPredGroups, 0, 3 * sizeof(unsigned long long), ctx->stream);
   const int ngroups = (v.tiles_x * v.tiles_y + 3) / 4;
   ART_LAUNCH_PDL(ctx, "tile_class", tile_class_kernel, std::max(1, std::min(ngroups, 8 * ctx->num_sms)), 128, 0, v,
              ctx->d_ranges, ctx->d_thist, ctx->d_agroups, ctx->d_status, ctx->cfg.max_missed, ctx->d_tclass,
@@ -382,6 +441,11 @@ art_status launch_proposal(art_ctx* ctx, const ViewParams& v, uint8_t* bins, flo
   p.n_active = ctx->d_status + (classified ? kStPredGroups : kStActiveGroups);
   p.tclass = classified ? ctx->d_tclass : nullptr;
   p.bins = bins;
+  p.thist = ctx->d_thist;
+  p.max_missed = ctx->cfg.max_missed;
+  p.margin = ctx->cfg.margin;
+  p.fail_list = ctx->d_fbq2;
+  p.fail_count = ctx->d_status + kStCheckFail;
   p.logits = logits;
   p.err = ctx->d_status + kStTcError;
   const int grid = std::min(p.ngroups, 3 * ctx->num_sms);

@@ -25,7 +25,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SUMMARY = os.path.join(ROOT, "profiles", "conv_unet_1024_traffic.md")
-SOURCES = [os.path.join(HERE, "csrc", f) for f in ("cnn_tc.cu", "tc.cuh", "cnn.cu")]
+SOURCES = [os.path.join(HERE, "csrc", f) for f in ("cnn_tc.cu", "cnn_sub.cu", "tc.cuh", "cnn.cu")]
 RES = 1024
 CALLS = 3
 LAUNCHES = 14

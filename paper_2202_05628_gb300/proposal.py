@@ -218,7 +218,7 @@ def evaluate(renderer, params, poses, cams, margin: int = 1, max_missed: float =
         n_over += st["overflow_order"]
         rg = renderer.debug_buffer(7, np.uint32).reshape(-1, 2)[:((cam.W + 7) // 8) * ((cam.H + 3) // 4)]
         n_act += int(np.sum(rg[:, 1] > rg[:, 0]))
-        n_fb += st["fallback_tiles"]
+        n_fb += st["check_fail_tiles"]
         dF = max(dF, torch.abs(F1 - F0).max().item())
         dA = max(dA, torch.abs(A1 - A0).max().item())
     renderer.set_config(skip=0)

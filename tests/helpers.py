@@ -117,3 +117,31 @@ def order_ambiguous(o, octree, H, W, tie_eps=1e-6, effect=1e-5, features=None):
                     break
             optical += sig[ids[k]] * (t1[k] - t0[k])
     return out.reshape(H, W)
+
+
+def subpixel_cat_conv(d, e, layer, bf16=True):
+    """ReLU(conv3x3([up2(d) | e]) + b) as the sub-pixel decoder convolution
+    computes it: the skip part e with the BF16-rounded 3x3 weights; the
+    upsampled part per output phase (py, px) as a 3x3-footprint convolution
+    of the low-resolution d whose taps are the FP32 sums (in the kernel's
+    order dy, dx = -1 .. 1) of the weights that land on the same
+    low-resolution pixel, rounded once to BF16 (bf16=False: no rounding,
+    the exact identity with the concatenated convolution)."""
+    import torch
+    import torch.nn.functional as Fn
+    bf = (lambda t: t.to(torch.bfloat16).to(torch.float64)) if bf16 else (lambda t: t)
+    w, b = np.asarray(layer[0], np.float32), np.asarray(layer[1], np.float64)
+    cu = d.shape[1]
+    ws = bf(torch.from_numpy(w[..., cu:].astype(np.float64))).permute(0, 3, 1, 2)
+    out = Fn.conv2d(e, ws, padding=1)
+    half = lambda v: (v + 2) // 2 - 1  # floor(v / 2) for v in -1 .. 2
+    for py in (0, 1):
+        for px in (0, 1):
+            kd = np.float32 if bf16 else np.float64
+            K = np.zeros((w.shape[0], 3, 3, cu), kd)
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    K[:, half(py + dy) + 1, half(px + dx) + 1] += w[:, dy + 1, dx + 1, :cu].astype(kd)
+            Kb = bf(torch.from_numpy(K.astype(np.float64))).permute(0, 3, 1, 2)
+            out[:, :, py::2, px::2] += Fn.conv2d(d, Kb, padding=1)
+    return torch.relu(out + torch.from_numpy(b)[None, :, None, None])

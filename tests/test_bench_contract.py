@@ -14,6 +14,10 @@ def test_unet_flops_by_hand():
     want = sum(2 * (H >> l) * (W >> l) * co * ci * 9 for l, co, ci in convs) + 2 * H * W * 4 * 32
     assert bench.unet_flops(H, W) == want
     assert abs(want / 1e9 - 357.4) < 0.5
+    # executed by the BF16 network: level 0's decoder convolution over [up2(d1) (64) | e0 (32)]
+    # takes 9 taps of the 32 skip channels and 4 of the 64 low-resolution ones per output pixel
+    d0a_plain, d0a_sub = 2 * H * W * 32 * 96 * 9, 2 * H * W * 32 * (32 * 9 + 64 * 4)
+    assert bench.unet_flops(H, W, subpixel=True) == want - d0a_plain + d0a_sub
 
 
 def test_roofline_of_the_convolutions():
@@ -21,7 +25,8 @@ def test_roofline_of_the_convolutions():
     kt = {"conv_tc": (14 * frames, 14 * frames * 0.05), "composite_skip": (2 * frames, 0.3 * frames)}
     peaks = {"hbm_gbs": 6783.5, "bf16_tflops_sustained": 1713.7}
     r = bench.roofline(kt, {"instances": 900000}, peaks, "bf16_skip", 1000000, 32, frames)
-    per_launch = bench.unet_flops(1024, 1024) / 14
+    per_launch = bench.unet_flops(1024, 1024, subpixel=True) / 14  # (the BF16 network executes the sub-pixel form)
+    assert r["flops_plain_definition"] == bench.unet_flops(1024, 1024)
     assert r["kernel"] == "conv_tc" and r["bound"] == "tensor" and r["unit"] == "TFLOP/s"
     assert math.isclose(r["achieved"], per_launch / 0.05e-3 / 1e12, rel_tol=1e-12)
     assert math.isclose(r["frac"], r["achieved"] / 1713.7, rel_tol=1e-12)

@@ -108,7 +108,7 @@ def test_fullsize_stereo_1080p_bf16_learned_skip_sampled():
         assert st["overflow_inst"] == 0 and st["overflow_order"] == 0
         ranges = r.debug_buffer(7, np.uint32).reshape(-1, 2)
         act += int(np.sum(ranges[:, 1] > ranges[:, 0]))
-        fb += st["fallback_tiles"]
+        fb += st["check_fail_tiles"]
         F, A = F.cpu().numpy(), A.cpu().numpy()
         px, py = _samples(A, 256, 32, seed=20 + v)
         o = oracle.pixels(oc, A_or, cam, px, py, features=feat16)

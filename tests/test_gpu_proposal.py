@@ -151,10 +151,12 @@ def test_labels_match_oracle():
 @pytest.mark.parametrize("seed,margin", [(2, 0), (5, 1)])
 def test_skip_render_matches_oracle(seed, margin):
     """Learned-skip render with an untrained proposal (arbitrary intervals):
-    queued tiles equal the plain render up to FP32 regrouping; tiles that pass the
-    coarse check equal the oracle's interval-restricted composite with the
-    same bins and lose at most the threshold of mass; the queue agrees with
-    the oracle's coarse check."""
+    tiles that fail the coarse check (composited over their whole list in
+    the same pass) equal the plain render up to FP32 regrouping; tiles that
+    pass it equal the oracle's interval-restricted composite with the same
+    bins and lose at most the threshold of mass; the failing tiles are the
+    oracle's coarse check with the transmittance after the interval bounded
+    by 1 (the check runs before compositing)."""
     import torch
     sc, cam, pose, r, A = _setup(pose_seed=seed)
     H, W, C = cam.H, cam.W, sc.octree.C
@@ -171,8 +173,8 @@ def test_skip_render_matches_oracle(seed, margin):
     kt = r.kernel_times()
     assert kt["composite_skip"][0] == 1 and kt["composite_fallback"][0] == 1 and kt["proposal_mlp"][0] == 1
     bins = r.debug_buffer(10, np.uint8)[:H * W * 2].reshape(-1, 2).astype(np.int32)
-    fb = r.debug_buffer(11, np.uint32)[:st["fallback_tiles"]] if st["fallback_tiles"] else np.zeros(0, np.uint32)
-    assert len(np.unique(fb)) == len(fb) == st["fallback_tiles"]
+    fb = r.debug_buffer(11, np.uint32)[:st["check_fail_tiles"]] if st["check_fail_tiles"] else np.zeros(0, np.uint32)
+    assert len(np.unique(fb)) == len(fb) == st["check_fail_tiles"]
     hist_o = oracle.tau_hist(sc.octree, A, cam)
     active = hist_o.sum(1) > 0
     tile = _tile_of_pixels(cam).reshape(-1)
@@ -180,7 +182,7 @@ def test_skip_render_matches_oracle(seed, margin):
     Fg, Ag = F.cpu().numpy().reshape(-1, C), Am.cpu().numpy().reshape(-1)
     F0g, A0g = F0.cpu().numpy().reshape(-1, C), A0.cpu().numpy().reshape(-1)
     in_fb = np.isin(tile, fb)
-    # the fallback is the plain walk (sequential; the plain render regroups the same sum by segments)
+    # the fallback is the plain walk (the same segments, the same sums)
     np.testing.assert_allclose(Fg[in_fb], F0g[in_fb], atol=1e-6)
     np.testing.assert_allclose(Ag[in_fb], A0g[in_fb], atol=1e-6)
     # bins as the kernel used them (tile union, margin), for the oracle's restricted composite
@@ -199,8 +201,16 @@ def test_skip_render_matches_oracle(seed, margin):
     np.testing.assert_allclose(Ag[keep], ro["A"].reshape(-1)[keep], atol=1e-4)
     # what passed the check lost no more than the threshold
     assert ro["missed"].reshape(-1)[~in_fb & act_px].max(initial=0.0) <= 1e-3 * (1 + 1e-3)
-    # the queue is the oracle's coarse check, up to bounds within 1 % of the threshold
-    bound = oracle.coarse_bound(hist_o, bu, 1.0 - ro["A"], cam).reshape(-1)
+    # the failing tiles are the oracle's coarse check of the predicted intervals (the failing
+    # tiles' bins were replaced by the full range: their predictions again, from run_proposal),
+    # up to bounds within 1 % of the threshold
+    raw = torch.zeros((H, W, 2), dtype=torch.uint8, device="cuda")
+    r.run_proposal(0, raw, None)
+    pred = bins.copy()
+    pred[in_fb] = raw.cpu().numpy().reshape(-1, 2).astype(np.int32)[in_fb]
+    bp = oracle.tile_union_bins(pred, cam, margin)
+    bp[~act_px] = [0, 63]
+    bound = oracle.coarse_bound(hist_o, bp, np.ones((H, W)), cam).reshape(-1)
     tmax = np.zeros(active.size)
     np.maximum.at(tmax, tile, bound)
     fail_o = tmax > 1e-3
@@ -254,7 +264,7 @@ def test_trained_proposal_skips_with_few_fallbacks():
         st = r.sync_status()
         ranges = r.debug_buffer(7, np.uint32).reshape(-1, 2)
         n_act += int(np.sum(ranges[:, 1] > ranges[:, 0]))
-        n_fb += st["fallback_tiles"]
+        n_fb += st["check_fail_tiles"]
         assert torch.abs(F1 - F0).max().item() <= 2e-3 * fmax + 1e-4
         assert torch.abs(A1 - A0).max().item() <= 2e-3 + 1e-4
     print(f"trained proposal: near/far accuracy {acc_n:.3f}/{acc_f:.3f}, cover {cover:.3f}, "

@@ -5,7 +5,7 @@ import pytest
 
 import oracle
 import scenegen as sg
-from helpers import psnr, render_maps, renderer, set_cam, set_pose, tiny_setup
+from helpers import psnr, render_maps, renderer, set_cam, set_pose, subpixel_cat_conv, tiny_setup
 
 pytestmark = pytest.mark.gpu
 TOL_F32 = 1e-4
@@ -69,7 +69,9 @@ def test_unet_f32_matches_oracle(H, W):
 def _unet_bf16_emulated(F, layers):
     """FP64 U-Net that rounds to BF16 exactly where the tensor-core path
     stores BF16: the input, the 3x3 weights and every stored activation; the
-    1x1 head reads the last convolution's FP32 output (fused epilogue)."""
+    1x1 head reads the last convolution's FP32 output (fused epilogue).  The
+    first convolution of the level-0 decoder block runs in its sub-pixel
+    form (helpers.subpixel_cat_conv)."""
     import torch
     import torch.nn.functional as Fn
     bf = lambda t: t.to(torch.bfloat16).to(torch.float64)
@@ -84,7 +86,7 @@ def _unet_bf16_emulated(F, layers):
     e3 = bf(conv(bf(conv(Fn.max_pool2d(e2, 2), 6)), 7))
     d2 = bf(conv(bf(conv(torch.cat([up(e3), e2], 1), 8)), 9))
     d1 = bf(conv(bf(conv(torch.cat([up(d2), e1], 1), 10)), 11))
-    d0 = conv(bf(conv(torch.cat([up(d1), e0], 1), 12)), 13)  # FP32 in the fused epilogue
+    d0 = conv(bf(subpixel_cat_conv(d1, e0, layers[12])), 13)  # FP32 in the fused epilogue
     wh = torch.from_numpy(layers[14][0].astype(np.float64)).to(torch.bfloat16).to(torch.float64)
     head = Fn.conv2d(d0, wh.permute(0, 3, 1, 2), torch.from_numpy(layers[14][1].astype(np.float64)))
     return torch.sigmoid(head)[0].permute(1, 2, 0).numpy()
