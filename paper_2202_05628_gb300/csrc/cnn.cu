@@ -2,6 +2,8 @@
 // layer orchestration and the CUDA-core implicit-GEMM convolution used for the
 // FP32 form.  The BF16 form runs its 3x3 layers on the tensor cores
 // (cnn_tc.cu).
+#include <type_traits>
+
 #include "internal.cuh"
 
 namespace art {
@@ -117,6 +119,134 @@ __global__ void __launch_bounds__(256) conv_simt_kernel(ConvArgs a) {
   }
 }
 
+// FP32 implicit GEMM on CUDA cores for the FP32 network: a CTA computes BM
+// consecutive pixels of one row x BN output channels (128 x 64, or 256 x 32
+// for the 32-channel layers), a thread 8 pixels (4 t .. 4 t + 3 and the same
+// BM / 2 further, so that a warp's 16-byte reads of a K row are contiguous)
+// x 4 channels: 32 FMAs per three 16-byte shared-memory reads; K runs over
+// taps x 16-channel chunks,
+// double-buffered in shared memory (one barrier per chunk) with the next
+// chunk's global loads (16 B: four channels of one pixel) in flight while the
+// current one is multiplied.  Needs channel counts and output offsets that
+// are multiples of 4 (16-byte rows); the layer's zero padding is the
+// out-of-image pixels loading as zeros.
+template <int BM, int BN>
+__global__ void __launch_bounds__(256) conv_f32_kernel(ConvArgs a) {
+  constexpr int BK = 16, TM = 8, TN = 4, NT = 256;
+  constexpr int NTM = BM / TM;  // threads along the pixels
+  static_assert(NTM * (BN / TN) == NT, "256 threads tile BM x BN");
+  constexpr int A_F4 = BM * BK / 4 / NT;        // 16-byte A loads per thread and chunk
+  constexpr int B_F4 = BN * BK / 4;             // 16-byte B loads per chunk (threads below it)
+  static_assert(B_F4 <= NT, "one B load per thread");
+  __shared__ __align__(16) float As[2][BK][BM + 4];
+  __shared__ __align__(16) float Bs[2][BK][BN + 4];
+  const int tid = threadIdx.x;
+  const int tm = tid % NTM, tn = tid / NTM;
+  const int tpr = (a.W + BM - 1) / BM;
+  const int y = blockIdx.x / tpr;
+  const int x0 = (blockIdx.x % tpr) * BM;
+  const int co0 = blockIdx.y * BN;
+  const int cin = a.c0 + a.c1;
+  const int pad = a.k / 2;
+  const float* s0 = (const float*)a.src0;
+  const float* s1 = (const float*)a.src1;
+  const int W0 = a.up0 ? a.W / 2 : a.W;
+  const int nch = (cin + BK - 1) / BK;
+  const int nk = a.k * a.k * nch;
+
+  float4 ra[A_F4], rb;
+  auto load = [&](int kk) {
+    const int tap = kk / nch, cb = (kk - tap * nch) * BK;
+    const int r = tap / a.k, sx = tap - r * a.k;
+    const int yy = y + r - pad;
+#pragma unroll
+    for (int e = 0; e < A_F4; ++e) {
+      const int f = tid + NT * e, i = f >> 2, ch = cb + 4 * (f & 3);
+      const int xx = x0 + i + sx - pad;
+      float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      if (yy >= 0 && yy < a.H && xx >= 0 && xx < a.W && ch < cin) {
+        if (ch < a.c0) {
+          const int ys = a.up0 ? yy >> 1 : yy, xs = a.up0 ? xx >> 1 : xx;
+          v = __ldg(reinterpret_cast<const float4*>(s0 + ((size_t)ys * W0 + xs) * a.c0 + ch));
+        } else {
+          v = __ldg(reinterpret_cast<const float4*>(s1 + ((size_t)yy * a.W + xx) * a.c1 + (ch - a.c0)));
+        }
+      }
+      ra[e] = v;
+    }
+    rb = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (tid < B_F4) {
+      const int co = co0 + (tid >> 2), ch = cb + 4 * (tid & 3);
+      if (co < a.cout && ch < cin)
+        rb = __ldg(reinterpret_cast<const float4*>(a.w + (((size_t)co * a.k + r) * a.k + sx) * cin + ch));
+    }
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int e = 0; e < A_F4; ++e) {
+      const int f = tid + NT * e, i = f >> 2, c = 4 * (f & 3);
+      As[buf][c][i] = ra[e].x;
+      As[buf][c + 1][i] = ra[e].y;
+      As[buf][c + 2][i] = ra[e].z;
+      As[buf][c + 3][i] = ra[e].w;
+    }
+    if (tid < B_F4) {
+      const int j = tid >> 2, c = 4 * (tid & 3);
+      Bs[buf][c][j] = rb.x;
+      Bs[buf][c + 1][j] = rb.y;
+      Bs[buf][c + 2][j] = rb.z;
+      Bs[buf][c + 3][j] = rb.w;
+    }
+  };
+
+  float acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0.0f;
+  load(0);
+  store(0);
+  __syncthreads();
+  for (int kk = 0; kk < nk; ++kk) {
+    const int buf = kk & 1;
+    if (kk + 1 < nk) load(kk + 1);  // in flight while this chunk is multiplied
+#pragma unroll
+    for (int c = 0; c < BK; ++c) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][c][4 * tm]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][c][BM / 2 + 4 * tm]);
+      const float4 b = *reinterpret_cast<const float4*>(&Bs[buf][c][tn * TN]);
+      const float av[TM] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float bv[TN] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+    }
+    if (kk + 1 < nk) store(buf ^ 1);  // (the other buffer was last read before the previous barrier)
+    __syncthreads();
+  }
+  const int cb0 = co0 + tn * TN;
+  float bias[TN];
+#pragma unroll
+  for (int j = 0; j < TN; ++j) bias[j] = cb0 + j < a.cout ? a.b[cb0 + j] : 0.0f;
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    const int x = x0 + (i < 4 ? 4 * tm + i : BM / 2 + 4 * tm + i - 4);
+    if (x >= a.W) continue;
+    float v[TN];
+#pragma unroll
+    for (int j = 0; j < TN; ++j) v[j] = activate(acc[i][j] + bias[j], a.act);
+    float* o = (float*)a.out + ((size_t)y * a.W + x) * a.out_ld + a.out_off + cb0;
+    if (cb0 + TN <= a.cout) {
+      *reinterpret_cast<float4*>(o) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < TN; ++j)
+        if (cb0 + j < a.cout) o[j] = v[j];
+    }
+  }
+}
+
 template <typename T>
 __global__ void maxpool2_kernel(const T* __restrict__ in, T* __restrict__ out, int H, int W, int C) {
   int64_t total = (int64_t)(H / 2) * (W / 2) * C;
@@ -134,6 +264,23 @@ __global__ void maxpool2_kernel(const T* __restrict__ in, T* __restrict__ out, i
 template <typename TI>
 void conv(art_ctx* ctx, const ConvArgs& a, const ConvLayer& L) {
   (void)L;
+  // FP32 activations in and out, 16-byte channel rows: the register-blocked kernel
+  auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+  const bool f32_ok = std::is_same<TI, float>::value && a.c0 % 4 == 0 && a.c1 % 4 == 0 && a.out_ld % 4 == 0 &&
+                      a.out_off % 4 == 0 && al16(a.out) && al16(a.src0) && al16(a.src1) && al16(a.w) &&
+                      (a.up0 == 0 || (a.W % 2 == 0 && a.H % 2 == 0));
+  if (f32_ok) {
+    if (a.cout <= 32) {
+      dim3 grid(((a.W + 255) / 256) * a.H, (a.cout + 31) / 32);
+      auto kfn = conv_f32_kernel<256, 32>;
+      ART_LAUNCH(ctx, "conv_simt", kfn, grid, 256, 0, a);
+    } else {
+      dim3 grid(((a.W + 127) / 128) * a.H, (a.cout + 63) / 64);
+      auto kfn = conv_f32_kernel<128, 64>;
+      ART_LAUNCH(ctx, "conv_simt", kfn, grid, 256, 0, a);
+    }
+    return;
+  }
   int tpr = (a.W + 63) / 64;
   dim3 grid(tpr * a.H, (a.cout + 63) / 64);
   auto kfn = conv_simt_kernel<TI>;
