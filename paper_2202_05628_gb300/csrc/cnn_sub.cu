@@ -49,7 +49,7 @@ constexpr int kKCB = 64;        // bytes per row of a K chunk: 32 BF16 channels 
 constexpr int kKC = 32;
 constexpr int kHalo = 130;      // input pixels of a row box (128 + 2)
 constexpr int kBoxBytes = kHalo * kKCB;
-constexpr int kStageBytes = (kBoxBytes + 1023) / 1024 * 1024;
+constexpr int kStageBytes = (kBoxBytes + 511) / 512 * 512;  // stages on 64-B swizzle atoms (8 rows x 64 B)
 constexpr int kBlock = kC * kKCB;  // one weight block: 32 output x 32 input channels
 constexpr int kSkipEntries = 18;   // per row phase: (r, c, px) of the skip part
 constexpr int kUpEntries = 8;      // per row phase: (oy, ox, px) of the low-resolution part
@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(kThreads, kCtas)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(wbar + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   float* s_bias = reinterpret_cast<float*>(tmem_slot + 4);
-  // epilogue store staging: 32 low-resolution pixels x 8 16-B chunks (two output pixels) per warp
+  // epilogue store staging: 32 output pixels x 4 16-B chunks per warp
   uint4* s_stage = reinterpret_cast<uint4*>((reinterpret_cast<uintptr_t>(s_bias + kC) + 15) & ~(uintptr_t)15);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(kThreads, kCtas)
     grid_dep_wait();  // the output tensor may still be read by the previous layer
     const int qd = warp & 3;
     const uint32_t tq = tmem_base + ((uint32_t)(qd * 32) << 16);  // this warp's lane quarter
-    uint4* stg = s_stage + (warp - 2) * 32 * 8;
+    uint4* stg = s_stage + (warp - 2) * 32 * 4;
     {  // zero both accumulators, then release them to the MMA
       for (int c0 = 0; c0 < 2 * kAccCols; c0 += 32) tmem_zero32(tq + (uint32_t)c0);
       tmem_wait_st();
@@ -265,31 +265,30 @@ __global__ void __launch_bounds__(kThreads, kCtas)
       const int i = u / p.tiles_per_row;
       const int jw = (u % p.tiles_per_row) * 128 + qd * 32;  // this warp's first low-resolution pixel
       const uint32_t tb = tq + (uint32_t)(buf * kAccCols);
-      {
+      // output row 2i + py: per column phase px the warp's 32 pixels 2j + px, staged
+      // (chunk k of pixel q at 4 q + (k ^ q % 4)) and stored 8 pixels x 64 B per instruction
+      __nv_bfloat16* orow = p.out + (size_t)(2 * i + py) * p.W * kC;
 #pragma unroll
-        for (int px = 0; px < 2; ++px) {
-          uint32_t r[32];
-          tmem_ld32(tb + (uint32_t)(px * kC), r);
-          uint4 pk[4];
-          uint32_t* w = reinterpret_cast<uint32_t*>(pk);
+      for (int px = 0; px < 2; ++px) {
+        uint32_t r[32];
+        tmem_ld32(tb + (uint32_t)(px * kC), r);
+        uint4 pk[4];
+        uint32_t* w = reinterpret_cast<uint32_t*>(pk);
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const float t0 = fmaxf(__uint_as_float(r[2 * j]) + s_bias[2 * j], 0.0f);
-            const float t1 = fmaxf(__uint_as_float(r[2 * j + 1]) + s_bias[2 * j + 1], 0.0f);
-            __nv_bfloat162 b2 = __floats2bfloat162_rn(t0, t1);
-            w[j] = *reinterpret_cast<uint32_t*>(&b2);
-          }
-          // chunk k of this lane's pixel pair (X = 2j, 2j + 1: 8 chunks of 16 B) at lane * 8 + (k ^ lane % 8)
-#pragma unroll
-          for (int k = 0; k < 4; ++k) stg[lane * 8 + ((px * 4 + k) ^ (lane & 7))] = pk[k];
+        for (int j = 0; j < 16; ++j) {
+          const float t0 = fmaxf(__uint_as_float(r[2 * j]) + s_bias[2 * j], 0.0f);
+          const float t1 = fmaxf(__uint_as_float(r[2 * j + 1]) + s_bias[2 * j + 1], 0.0f);
+          __nv_bfloat162 b2 = __floats2bfloat162_rn(t0, t1);
+          w[j] = *reinterpret_cast<uint32_t*>(&b2);
         }
-        __syncwarp();
-        // the warp's 64 output pixels of row 2i + py are 4 KB in a row: 512 B per store
-        uint4* dst = reinterpret_cast<uint4*>(p.out + ((size_t)(2 * i + py) * p.W + 2 * (size_t)jw) * kC);
 #pragma unroll
-        for (int t = 0; t < 8; ++t) {
-          const int f = t * 32 + lane, q = f >> 3, c8 = f & 7;
-          if (jw + q < p.w) dst[f] = stg[q * 8 + (c8 ^ (q & 7))];
+        for (int k = 0; k < 4; ++k) stg[lane * 4 + (k ^ (lane & 3))] = pk[k];
+        __syncwarp();
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int f = t * 32 + lane, q = f >> 2, c4 = f & 3;
+          if (jw + q < p.w)
+            reinterpret_cast<uint4*>(orow + (size_t)(2 * (jw + q) + px) * kC)[c4] = stg[q * 4 + (c4 ^ (q & 3))];
         }
         __syncwarp();
       }
@@ -423,7 +422,7 @@ art_status launch_sub_conv(art_ctx* ctx, const SubConv& c) {
   p.bias = c.bias;
   p.out = (__nv_bfloat16*)c.out;
   p.err = ctx->d_status + kStTcError;
-  const int tail = 8 * (2 * kMaxStages + 5) + 16 + 4 * kC + 16 + 4 * 32 * 8 * 16;
+  const int tail = 8 * (2 * kMaxStages + 5) + 16 + 4 * kC + 16 + 4 * 32 * 4 * 16;
   // two CTAs per SM: each within half of the SM's shared memory (less what
   // the runtime reserves per CTA)
   const int avail = 232448 / kCtas - 1024 - 1024 - p.w_bytes - tail;
