@@ -309,16 +309,16 @@ def composite_roofline(kt, stats, peaks, form, C, frames):
 
 def unet_flops(H, W, cin=32, ch=(32, 64, 128, 256), subpixel=False):
     """FLOPs of the 4-level U-Net on an H x W map.  subpixel: as the BF16
-    tensor-core network executes it, level 0's decoder convolution over
-    [up2(d1) | e0] in its sub-pixel form (the upsampled part through 4 taps
-    per output pixel instead of 9)."""
+    tensor-core network executes it, each decoder block's first convolution
+    over [up2(d) | e] in its sub-pixel form (the upsampled part through 4
+    taps per output pixel instead of 9)."""
     import scenegen as sg
     tot = 0
     shapes = sg.unet_layer_shapes(cin, ch)
     lvl = [0, 0, 1, 1, 2, 2, 3, 3, 2, 2, 1, 1, 0, 0, 0]
     for idx, ((co, ci, k), l) in enumerate(zip(shapes, lvl)):
-        if subpixel and idx == 12:
-            tot += 2 * H * W * co * (9 * ch[0] + 4 * ch[1])
+        if subpixel and idx in (8, 10, 12):
+            tot += 2 * (H >> l) * (W >> l) * co * (9 * ch[l] + 4 * ch[l + 1])
         else:
             tot += 2 * (H >> l) * (W >> l) * co * ci * k * k
     return tot

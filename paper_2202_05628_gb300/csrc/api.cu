@@ -194,6 +194,7 @@ void free_all(art_ctx* ctx) {
     if (L.b32) cudaFree(L.b32);
     if (L.wbf) cudaFree(L.wbf);
     if (L.wsub) cudaFree(L.wsub);
+    if (L.wtap) cudaFree(L.wtap);
     if (L.w8) cudaFree(L.w8);
     if (L.wscale) cudaFree(L.wscale);
   }
@@ -899,6 +900,7 @@ art_status art_load_shader(art_ctx* ctx, const art_net_desc* desc, const float* 
     if (L.b32) cudaFree(L.b32);
     if (L.wbf) cudaFree(L.wbf);
     if (L.wsub) cudaFree(L.wsub);
+    if (L.wtap) cudaFree(L.wtap);
     if (L.w8) cudaFree(L.w8);
     if (L.wscale) cudaFree(L.wscale);
   }
@@ -947,10 +949,23 @@ art_status art_load_shader(art_ctx* ctx, const art_net_desc* desc, const float* 
     L.sub_cu = cu;
     return ART_OK;
   };
-  if (compute_dtype == ART_BF16 && d.arch == ART_NET_UNET) st = sub_blocks(12, d.ch[0], d.ch[1]);
-  if (compute_dtype == ART_BF16 && d.arch == ART_NET_TWO_BRANCH) {
-    st = sub_blocks(12, d.ch[0], d.ch[1]);
-    if (st == ART_OK) st = sub_blocks(19, d.ach[0], d.ach[1]);
+  // ... and those of levels 1 and 2 (the tap-by-tap kernel's per-phase weights)
+  auto tap_blocks = [&](int li, int cs, int cu) -> art_status {
+    if (li >= (int)ctx->layers.size()) return ART_OK;
+    ConvLayer& L = ctx->layers[li];
+    if (L.k != 3 || L.cin != cs + cu || L.cin_pad != L.cin || cs % 32 || cu % 32) return ART_OK;
+    art_status s2 = alloc(ctx, &L.wtap, (size_t)4 * L.cout * (9 * cs + 4 * cu), "sub-pixel weights");
+    if (s2 != ART_OK) return s2;
+    launch_sub_tap_weights(ctx, L.w32, L.cout, cs, cu, L.wtap);
+    L.sub_cs = cs;
+    L.sub_cu = cu;
+    return ART_OK;
+  };
+  if (compute_dtype == ART_BF16 && (d.arch == ART_NET_UNET || d.arch == ART_NET_TWO_BRANCH)) {
+    st = sub_blocks(12, d.ch[0], d.ch[1]);                  // decoder of level 0
+    if (st == ART_OK) st = tap_blocks(10, d.ch[1], d.ch[2]);  // level 1
+    if (st == ART_OK) st = tap_blocks(8, d.ch[2], d.ch[3]);   // level 2
+    if (st == ART_OK && d.arch == ART_NET_TWO_BRANCH) st = sub_blocks(19, d.ach[0], d.ach[1]);
   }
   if (st != ART_OK) return st;
   ctx->net = d;

@@ -459,11 +459,11 @@ size_t unet_tc_bytes(int H, int W, int levels, const int* ch) {
 // cat_l = [up(decoder below) | encoder skip] by the producing convolutions'
 // epilogues, so every decoder convolution reads one dense tensor; the last
 // convolution carries the 1x1 head + sigmoid in its epilogue, into head_n
-// FP32 channels at head_off of head_ld per pixel.  Level 0's decoder
-// convolution runs in its sub-pixel form when its layer has the blocks
-// (launch_sub_conv): cat0's space then holds the skip tensor, x-phase
-// split, and the decoder output of level 1 at its own resolution (no 2x2
-// replicated copy).  Arena order (from arena_off): e0a, cat0, p0, e1a,
+// FP32 channels at head_off of head_ld per pixel.  A decoder convolution
+// runs in its sub-pixel form when its layer has the blocks (level 0:
+// launch_sub_conv; levels 1 and 2: the tap-by-tap kernel): cat_l's space then
+// holds the skip tensor, x-phase split, and the block output of level l + 1
+// at its own resolution (no 2x2-replicated copy).  Arena order (from arena_off): e0a, cat0, p0, e1a,
 // cat1, p1, ..., bottleneck a, then the decoders' first outputs from the
 // deepest level up.
 art_status unet_tc(art_ctx* ctx, int H, int W, const __nv_bfloat16* in, int cin, int lb, int levels, const int* ch,
@@ -486,13 +486,32 @@ art_status unet_tc(art_ctx* ctx, int H, int W, const __nv_bfloat16* in, int cin,
   for (int l = levels - 2; l >= 0; --l) da[l] = take(l, ch[l], 0);
   const auto& Ls = ctx->layers;
   const int head = lb + 4 * levels - 2;
-  // level 0's decoder convolution in the sub-pixel form: its skip input
-  // (x-phase split) and its low-resolution input, both in cat0's space
-  const ConvLayer& L0 = Ls[lb + 4 * levels - 4];
-  const bool sub0 = L0.wsub && L0.sub_cs == ch[0] && L0.sub_cu == ch[1] && ctx->conv_rows &&
-                    sub_conv_ok(L0.cout, ch[0], ch[1], H, W);
-  __nv_bfloat16* sk0 = cat[0];
-  __nv_bfloat16* u0 = (__nv_bfloat16*)((char*)cat[0] + align256((size_t)H * W * ch[0] * 2));
+  // decoder convolutions in the sub-pixel form (level 0: conv_sub_kernel;
+  // levels >= 1: the tap-by-tap kernel): their skip input (x-phase split) and
+  // their low-resolution input, both in cat_l's space
+  bool sub[4] = {};
+  __nv_bfloat16 *sk[4] = {}, *ul[4] = {};
+  for (int l = 0; l + 1 < levels; ++l) {
+    const ConvLayer& L = Ls[lb + 2 * levels + 2 * (levels - 2 - l)];
+    const int h = H >> l, w = W >> l;
+    if (l == 0) {
+      sub[0] = L.wsub && L.sub_cs == ch[0] && L.sub_cu == ch[1] && ctx->conv_rows &&
+               sub_conv_ok(L.cout, ch[0], ch[1], h, w);
+    } else {
+      TcConv t{};
+      t.sub = 1;
+      t.cs = ch[l];
+      t.cu = ch[l + 1];
+      t.cin = ch[l] + ch[l + 1];
+      t.cout = L.cout;
+      t.H = h;
+      t.W = w;
+      t.ld_out = L.cout;
+      sub[l] = L.wtap && L.sub_cs == ch[l] && L.sub_cu == ch[l + 1] && tc_conv_ok(t);
+    }
+    sk[l] = cat[l];
+    ul[l] = (__nv_bfloat16*)((char*)cat[l] + align256((size_t)h * w * ch[l] * 2));
+  }
   int psplit = 0;
   auto conv = [&](const __nv_bfloat16* x, int xc, int l, int li, __nv_bfloat16* o, int ld, int o_off, int up2,
                   bool to_head, __nv_bfloat16* pooled) {
@@ -521,7 +540,7 @@ art_status unet_tc(art_ctx* ctx, int H, int W, const __nv_bfloat16* in, int cin,
   };
   // the block output of level l + 1 that level l's decoder reads upsampled
   auto up_into = [&](const __nv_bfloat16* x, int l, int li) {
-    if (l == 0 && sub0) return conv(x, ch[1], 1, li, u0, ch[1], 0, 0, false, nullptr);
+    if (sub[l]) return conv(x, ch[l + 1], l + 1, li, ul[l], ch[l + 1], 0, 0, false, nullptr);
     return conv(x, ch[l + 1], l + 1, li, cat[l], ch[l + 1] + ch[l], 0, 1, false, nullptr);
   };
   art_status st = ART_OK;
@@ -531,9 +550,9 @@ art_status unet_tc(art_ctx* ctx, int H, int W, const __nv_bfloat16* in, int cin,
   int xc = cin;
   for (int l = 0; l + 1 < levels; ++l) {  // encoder: the block output goes into cat_l as the skip, + 2x2 pooling
     ART_TRY(conv(x, xc, l, 2 * l, ea[l], ch[l], 0, 0, false, nullptr));
-    if (l == 0 && sub0) {  // dense and x-phase split for the sub-pixel decoder convolution
+    if (sub[l]) {  // dense and x-phase split for the sub-pixel decoder convolution
       psplit = 1;
-      st = conv(ea[0], ch[0], 0, 1, sk0, ch[0], 0, 0, false, pl[0]);
+      st = conv(ea[l], ch[l], l, 2 * l + 1, sk[l], ch[l], 0, 0, false, pl[l]);
       psplit = 0;
       if (st != ART_OK) return st;
     } else {
@@ -547,18 +566,36 @@ art_status unet_tc(art_ctx* ctx, int H, int W, const __nv_bfloat16* in, int cin,
   ART_TRY(up_into(ea[lL], lL - 1, 2 * lL + 1));
   int li = 2 * levels;
   for (int l = levels - 2; l >= 0; --l, li += 2) {
-    if (l == 0 && sub0) {
+    const ConvLayer& L = Ls[lb + li];
+    if (l == 0 && sub[0]) {
       SubConv sc;
-      sc.skip = sk0;
+      sc.skip = sk[0];
       sc.cs = ch[0];
-      sc.up = u0;
+      sc.up = ul[0];
       sc.cu = ch[1];
       sc.H = H;
       sc.W = W;
-      sc.w = L0.wsub;
-      sc.bias = L0.b32;
+      sc.w = L.wsub;
+      sc.bias = L.b32;
       sc.out = da[0];
       ART_TRY(launch_sub_conv(ctx, sc));
+    } else if (sub[l]) {
+      TcConv c{};
+      c.sub = 1;
+      c.in = sk[l];
+      c.cs = ch[l];
+      c.up = ul[l];
+      c.cu = ch[l + 1];
+      c.cin = ch[l] + ch[l + 1];
+      c.H = H >> l;
+      c.W = W >> l;
+      c.w = L.wtap;
+      c.bias = L.b32;
+      c.cout = L.cout;
+      c.act = 1;
+      c.out = da[l];
+      c.ld_out = L.cout;
+      ART_TRY(launch_tc_conv(ctx, c));
     } else {
       ART_TRY(conv(cat[l], ch[l + 1] + ch[l], l, li, da[l], ch[l], 0, 0, false, nullptr));
     }

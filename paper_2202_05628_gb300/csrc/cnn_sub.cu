@@ -355,6 +355,36 @@ __global__ void sub_weights_kernel(const float* __restrict__ w32, int cs, int cu
   }
 }
 
+// Per output phase (py, px) of the tap-by-tap sub-pixel form: row co of
+// phase ph holds the skip part's 9 taps (tap = (dy + 1) 3 + dx + 1:
+// W[dy][dx][cu + ci]) and then the low-resolution part's 4 taps (tu: oy =
+// py - 1 + tu / 2, ox = px - 1 + tu % 2: the FP32 sum of W[dy][dx][ci] over
+// the taps with floor((py + dy) / 2) = oy and floor((px + dx) / 2) = ox),
+// rounded to BF16.
+__global__ void sub_tap_weights_kernel(const float* __restrict__ w32, int cout, int cs, int cu,
+                                       __nv_bfloat16* __restrict__ out) {
+  const int K = 9 * cs + 4 * cu, cin = cu + cs;
+  const int64_t n = 4LL * cout * K;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(idx % K);
+    const int row = (int)(idx / K);
+    const int co = row % cout, ph = row / cout, py = ph >> 1, px = ph & 1;
+    const float* wc = w32 + (size_t)co * 9 * cin;
+    if (k < 9 * cs) {
+      const int tap = k / cs, ci = k % cs;
+      out[idx] = __float2bfloat16_rn(wc[tap * cin + cu + ci]);
+    } else {
+      const int tu = (k - 9 * cs) / cu, ci = (k - 9 * cs) % cu;
+      const int oy = py - 1 + (tu >> 1), ox = px - 1 + (tu & 1);
+      float acc = 0.0f;
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx)
+          if (half_floor(py + dy) == oy && half_floor(px + dx) == ox) acc += wc[((dy + 1) * 3 + (dx + 1)) * cin + ci];
+      out[idx] = __float2bfloat16_rn(acc);
+    }
+  }
+}
+
 }  // namespace
 
 size_t sub_weight_elems(int cs, int cu) { return 2 * ((size_t)kSkipEntries * kC * cs + (size_t)kUpEntries * kC * cu); }
@@ -370,6 +400,12 @@ void launch_sub_weights(art_ctx* ctx, const float* w32, int cs, int cu, __nv_bfl
   const int grid = (int)std::min<int64_t>((n + 255) / 256, 1024);
   ART_LAUNCH(ctx, "sub_weights", sub_weights_kernel, grid, 256, 0, w32, cs, cu, wsub,
              wsub + 2 * (size_t)kSkipEntries * kC * cs);
+}
+
+void launch_sub_tap_weights(art_ctx* ctx, const float* w32, int cout, int cs, int cu, __nv_bfloat16* wtap) {
+  const int64_t n = 4LL * cout * (9 * cs + 4 * cu);
+  const int grid = (int)std::min<int64_t>((n + 255) / 256, 4096);
+  ART_LAUNCH(ctx, "sub_weights", sub_tap_weights_kernel, grid, 256, 0, w32, cout, cs, cu, wtap);
 }
 
 art_status launch_sub_conv(art_ctx* ctx, const SubConv& c) {

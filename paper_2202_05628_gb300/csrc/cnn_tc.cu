@@ -49,28 +49,43 @@ struct TcParams {
   int head_n, head_ld, head_off;  // head outputs, FP32 values per output pixel, channel of the first
   void* pool;            // row-blocked kernel: fused 2x2 max pooling, dense [H/2][W/2][cout] (BF16 or E4M3)
   int psplit;            // staged BF16 stores: x-phase split rows (even pixels, then odd)
+  // sub-pixel decoder convolution (tap-by-tap kernel, BF16): H x W is the
+  // low-resolution grid; a tile is (output phase, low-resolution row,
+  // 128-pixel segment); its K chunks are 9 taps of the x-phase split skip
+  // tensor (tmA, cs_ch chunks each) then 4 taps of the low-resolution tensor
+  // (tmU, cu_ch chunks each); output pixel (2y + py, 2x + px)
+  int sub, cs_ch, cu_ch;
   unsigned long long* err;
 };
 
 // One 32-channel BF16 group (64 B per pixel) of the warp's 32 pixels of
 // output row y (this lane: x0 + lane), staged through stage[32 x 4] (chunk k
 // of pixel q at 4 q + (k ^ (q % 4))) and stored four lanes per pixel into
-// channels [ch_off + c0, + 32) (with up2: the pixel's 2x2 block).
+// channels [ch_off + c0, + 32) (with up2: the pixel's 2x2 block; with an
+// output phase ph >= 0 (sub-pixel tiles): pixel (2y + ph / 2, 2x + ph % 2)
+// of the 2H x 2W output; with psplit: x-phase split rows).
 __device__ __forceinline__ void store_staged_group(const TcParams& p, int y, int x0, int lane, int c0,
-                                                   const uint4 (&pk)[4], uint4* stage) {
+                                                   const uint4 (&pk)[4], uint4* stage, int ph = -1) {
 #pragma unroll
   for (int k = 0; k < 4; ++k) stage[lane * 4 + (k ^ (lane & 3))] = pk[k];
   __syncwarp();
   __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(p.out);
   const int nd = p.up2 ? 4 : 1;
-  const int Wd = p.up2 ? 2 * p.W : p.W;
+  const int Wd = (p.up2 || ph >= 0) ? 2 * p.W : p.W;
   for (int d = 0; d < nd; ++d) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int f = i * 32 + lane, q = f >> 2, c = f & 3;
       const int x = x0 + q;
       if (x < p.W) {
-        const int X = p.up2 ? 2 * x + (d & 1) : x, Y = p.up2 ? 2 * y + (d >> 1) : y;
+        int X, Y;
+        if (ph >= 0) {
+          X = 2 * x + (ph & 1);
+          Y = 2 * y + (ph >> 1);
+        } else {
+          X = p.up2 ? 2 * x + (d & 1) : (p.psplit ? (x & 1) * (p.W >> 1) + (x >> 1) : x);
+          Y = p.up2 ? 2 * y + (d >> 1) : y;
+        }
         uint4* dst = reinterpret_cast<uint4*>(out + ((size_t)Y * Wd + X) * p.ld_out + p.ch_off + c0) + c;
         *dst = stage[q * 4 + (c ^ (q & 3))];
       }
@@ -86,7 +101,7 @@ __device__ __forceinline__ void store_staged_group(const TcParams& p, int y, int
 template <int N, bool F8>
 __device__ __forceinline__ void epi_row(const TcParams& p, uint32_t taddr, int y, int x, const float* s_bias,
                                         const float* s_head, const float* s_wsc, float in_s, float out_inv,
-                                        float& amax, uint4* stage = nullptr, int x0 = 0, int lane = 0) {
+                                        float& amax, uint4* stage = nullptr, int x0 = 0, int lane = 0, int ph = -1) {
   const bool valid = x < p.W;
 #pragma unroll 1
   for (int c0 = 0; c0 < N; c0 += 32) {
@@ -107,7 +122,7 @@ __device__ __forceinline__ void epi_row(const TcParams& p, uint32_t taddr, int y
         __nv_bfloat162 b2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
         w[j] = *reinterpret_cast<uint32_t*>(&b2);
       }
-      store_staged_group(p, y, x0, lane, c0, pk, stage);
+      store_staged_group(p, y, x0, lane, c0, pk, stage, ph);
       continue;
     }
     if (!valid) continue;
@@ -386,7 +401,8 @@ struct TcCfg {
 
 template <int N, int KCB, bool F8>
 __global__ void __launch_bounds__(kThreads, TcCfg<N, KCB, F8>::kCtas)
-    conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcParams p) {
+    conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const __grid_constant__ CUtensorMap tmU, TcParams p) {
   using Cfg = TcCfg<N, KCB, F8>;
   constexpr int KC = F8 ? KCB : KCB / 2;  // channels per K chunk
   extern __shared__ uint8_t smem_raw[];
@@ -406,7 +422,8 @@ __global__ void __launch_bounds__(kThreads, TcCfg<N, KCB, F8>::kCtas)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int cpt = p.cin / KC;  // K chunks per tap
-  const int n_chunks = 9 * cpt;
+  const int n_skip = 9 * p.cs_ch;  // sub-pixel tiles: the skip part's chunks, then 4 taps x cu_ch
+  const int n_chunks = p.sub ? n_skip + 4 * p.cu_ch : 9 * cpt;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < Cfg::kStages; ++s) {
@@ -445,15 +462,31 @@ __global__ void __launch_bounds__(kThreads, TcCfg<N, KCB, F8>::kCtas)
       int s = 0;
       uint32_t ph = 0;
       for (int tile = blockIdx.x; tile < p.n_tiles && !*abort_flag; tile += gridDim.x) {
-        const int y = tile / p.tiles_per_row, x0 = (tile % p.tiles_per_row) * 128;
+        const int st = p.sub ? tile >> 2 : tile, oph = tile & 3;  // (sub-pixel: output phase (py, px))
+        const int y = st / p.tiles_per_row, x0 = (st % p.tiles_per_row) * 128;
         for (int c = 0; c < n_chunks; ++c) {
           if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) break;
-          const int tap = c / cpt, cc = c - tap * cpt;
-          const int r = tap / 3, q = tap - 3 * (tap / 3);
           uint8_t* a = stages + s * Cfg::kStage;
           mbar_expect_tx(&full[s], Cfg::kStage);
-          tma_load_3d(a, &tmA, &full[s], cc * KC, x0 + q - 1, y + r - 1);
-          tma_load_2d(a + Cfg::kA, &tmB, &full[s], tap * p.cin + cc * KC, 0);
+          if (!p.sub) {
+            const int tap = c / cpt, cc = c - tap * cpt;
+            const int r = tap / 3, q = tap - 3 * (tap / 3);
+            tma_load_3d(a, &tmA, &full[s], cc * KC, x0 + q - 1, y + r - 1);
+            tma_load_2d(a + Cfg::kA, &tmB, &full[s], tap * p.cin + cc * KC, 0);
+          } else if (c < n_skip) {
+            // skip tap (dy, dx): input column 2x + px + dx = 2 (x + jo) + q of the x-phase split rows
+            const int tap = c / p.cs_ch, cc = c - tap * p.cs_ch;
+            const int dy = tap / 3 - 1, cpos = (oph & 1) + tap % 3 - 1;
+            const int q = cpos & 1, jo = (cpos - q) / 2;
+            tma_load_4d(a, &tmA, &full[s], cc * KC, x0 + jo, q, 2 * y + (oph >> 1) + dy);
+            tma_load_2d(a + Cfg::kA, &tmB, &full[s], tap * p.cs_ch * KC + cc * KC, oph * N);
+          } else {
+            // low-resolution tap (oy, ox), oy in {py - 1, py}, ox in {px - 1, px}
+            const int t = c - n_skip, tu = t / p.cu_ch, cc = t - tu * p.cu_ch;
+            const int oy = (oph >> 1) - 1 + (tu >> 1), ox = (oph & 1) - 1 + (tu & 1);
+            tma_load_3d(a, &tmU, &full[s], cc * KC, x0 + ox, y + oy);
+            tma_load_2d(a + Cfg::kA, &tmB, &full[s], (9 * p.cs_ch + tu * p.cu_ch) * KC + cc * KC, oph * N);
+          }
           if (++s == Cfg::kStages) {
             s = 0;
             ph ^= 1u;
@@ -507,9 +540,11 @@ __global__ void __launch_bounds__(kThreads, TcCfg<N, KCB, F8>::kCtas)
     for (int tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x) {
       if (!mbar_wait(&accf[buf], aph, abort_flag, 256)) break;
       tc_fence_after();
-      const int y = tile / p.tiles_per_row, x = (tile % p.tiles_per_row) * 128 + m;
+      const int st = p.sub ? tile >> 2 : tile;
+      const int y = st / p.tiles_per_row, x = (st % p.tiles_per_row) * 128 + m;
       epi_row<N, F8>(p, tmem_base + ((uint32_t)(qd * 32) << 16) + (uint32_t)(buf * N), y, x, s_bias, s_head, s_wsc,
-                     in_s, out_inv, amax, F8 ? nullptr : s_stage + (warp - 2) * 32 * 4, x - lane, lane);
+                     in_s, out_inv, amax, F8 ? nullptr : s_stage + (warp - 2) * 32 * 4, x - lane, lane,
+                     p.sub ? (tile & 3) : -1);
       tc_fence_before();
       mbar_arrive(&acce[buf]);
       if (++buf == 2) {
@@ -785,9 +820,10 @@ __global__ void __launch_bounds__(kThreads, 2)
 }
 
 // 2x2 max pooling of a channel slice [ch_off, ch_off + C) of an NHWC tensor
-// with ld channels per pixel, into a dense [H/2][W/2][C] tensor.
+// with ld channels per pixel (rows x-phase split when psplit: even pixels,
+// then odd), into a dense [H/2][W/2][C] tensor.
 __global__ void maxpool2_bf16_kernel(const __nv_bfloat16* __restrict__ in, int ld, int ch_off,
-                                     __nv_bfloat16* __restrict__ out, int H, int W, int C) {
+                                     __nv_bfloat16* __restrict__ out, int H, int W, int C, int psplit) {
   const int C8 = C / 8;
   const int64_t total = (int64_t)(H / 2) * (W / 2) * C8;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -795,11 +831,13 @@ __global__ void maxpool2_bf16_kernel(const __nv_bfloat16* __restrict__ in, int l
     const int c = (int)(idx % C8) * 8;
     const int64_t pp = idx / C8;
     const int x = (int)(pp % (W / 2)), y = (int)(pp / (W / 2));
-    const __nv_bfloat16* q = in + (((size_t)(2 * y) * W) + 2 * x) * ld + ch_off + c;
+    // pixel 2x of row 2y and its right neighbour (in the odd half when x-phase split)
+    const __nv_bfloat16* q = in + (((size_t)(2 * y) * W) + (psplit ? x : 2 * x)) * ld + ch_off + c;
+    const size_t nb = psplit ? (size_t)(W / 2) * ld : (size_t)ld;
     uint4 a = *reinterpret_cast<const uint4*>(q);
-    uint4 b = *reinterpret_cast<const uint4*>(q + ld);
+    uint4 b = *reinterpret_cast<const uint4*>(q + nb);
     uint4 cc = *reinterpret_cast<const uint4*>(q + (size_t)W * ld);
-    uint4 d = *reinterpret_cast<const uint4*>(q + (size_t)W * ld + ld);
+    uint4 d = *reinterpret_cast<const uint4*>(q + (size_t)W * ld + nb);
     const __nv_bfloat162* pa = reinterpret_cast<const __nv_bfloat162*>(&a);
     const __nv_bfloat162* pb = reinterpret_cast<const __nv_bfloat162*>(&b);
     const __nv_bfloat162* pc = reinterpret_cast<const __nv_bfloat162*>(&cc);
@@ -835,8 +873,9 @@ art_status launch_typed(art_ctx* ctx, const TcConv& c) {
   const CUtensorMapDataType dt = F8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   const CUtensorMapSwizzle swz = KCB == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
                                             : (KCB == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B);
-  CUtensorMap tmA, tmB;
-  {
+  CUtensorMap tmA, tmB, tmU;
+  const int gh = c.sub ? c.H / 2 : c.H, gw = c.sub ? c.W / 2 : c.W;  // the kernel's pixel grid
+  if (!c.sub) {
     cuuint64_t dims[3] = {(cuuint64_t)c.cin, (cuuint64_t)c.W, (cuuint64_t)c.H};
     cuuint64_t strides[2] = {(cuuint64_t)c.cin * kEs, (cuuint64_t)c.W * c.cin * kEs};
     cuuint32_t box[3] = {(cuuint32_t)KC, 128, 1};
@@ -844,10 +883,31 @@ art_status launch_typed(art_ctx* ctx, const TcConv& c) {
     CUresult r = g_encode(&tmA, dt, 3, (void*)c.in, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(ctx, ART_ERR_CUDA, "cuTensorMapEncodeTiled (activations) failed: %d", (int)r);
+    tmU = tmA;
+  } else {
+    {  // skip tensor, x-phase split: (channel, x / 2, x % 2, y) at the output resolution
+      cuuint64_t dims[4] = {(cuuint64_t)c.cs, (cuuint64_t)gw, 2, (cuuint64_t)c.H};
+      cuuint64_t strides[3] = {(cuuint64_t)c.cs * kEs, (cuuint64_t)gw * c.cs * kEs, (cuuint64_t)c.W * c.cs * kEs};
+      cuuint32_t box[4] = {(cuuint32_t)KC, 128, 1, 1};
+      cuuint32_t es[4] = {1, 1, 1, 1};
+      CUresult r = g_encode(&tmA, dt, 4, (void*)c.in, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) return fail(ctx, ART_ERR_CUDA, "cuTensorMapEncodeTiled (skip) failed: %d", (int)r);
+    }
+    {  // low-resolution tensor: (channel, x, y)
+      cuuint64_t dims[3] = {(cuuint64_t)c.cu, (cuuint64_t)gw, (cuuint64_t)gh};
+      cuuint64_t strides[2] = {(cuuint64_t)c.cu * kEs, (cuuint64_t)gw * c.cu * kEs};
+      cuuint32_t box[3] = {(cuuint32_t)KC, 128, 1};
+      cuuint32_t es[3] = {1, 1, 1};
+      CUresult r = g_encode(&tmU, dt, 3, (void*)c.up, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) return fail(ctx, ART_ERR_CUDA, "cuTensorMapEncodeTiled (low resolution) failed: %d", (int)r);
+    }
   }
-  {
-    cuuint64_t dims[2] = {(cuuint64_t)9 * c.cin, (cuuint64_t)c.cout};
-    cuuint64_t strides[1] = {(cuuint64_t)9 * c.cin * kEs};
+  {  // weights: [cout][9 cin] (K-major), or per output phase [4][cout][9 cs + 4 cu]
+    const int K = c.sub ? 9 * c.cs + 4 * c.cu : 9 * c.cin;
+    cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)(c.sub ? 4 : 1) * c.cout};
+    cuuint64_t strides[1] = {(cuuint64_t)K * kEs};
     cuuint32_t box[2] = {(cuuint32_t)KC, (cuuint32_t)N};
     cuuint32_t es[2] = {1, 1};
     CUresult r = g_encode(&tmB, dt, 2, (void*)c.w, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
@@ -855,12 +915,15 @@ art_status launch_typed(art_ctx* ctx, const TcConv& c) {
     if (r != CUDA_SUCCESS) return fail(ctx, ART_ERR_CUDA, "cuTensorMapEncodeTiled (weights) failed: %d", (int)r);
   }
   TcParams p;
-  p.H = c.H;
-  p.W = c.W;
-  p.cin = c.cin;
+  p.H = gh;
+  p.W = gw;
+  p.cin = c.sub ? c.cs + c.cu : c.cin;
   p.cout = c.cout;
-  p.tiles_per_row = (c.W + 127) / 128;
-  p.n_tiles = p.tiles_per_row * c.H;
+  p.tiles_per_row = (gw + 127) / 128;
+  p.n_tiles = p.tiles_per_row * gh * (c.sub ? 4 : 1);
+  p.sub = c.sub;
+  p.cs_ch = c.sub ? c.cs / KC : 0;
+  p.cu_ch = c.sub ? c.cu / KC : 0;
   p.act = c.act;
   p.bias = c.bias;
   p.out = c.out;
@@ -878,13 +941,13 @@ art_status launch_typed(art_ctx* ctx, const TcConv& c) {
   p.head_ld = c.head_ld;
   p.head_off = c.head_off;
   p.pool = nullptr;  // pooled by a pass of its own
-  p.psplit = 0;
+  p.psplit = c.psplit;
   p.err = ctx->d_status + kStTcError;
   auto kfn = conv_tc_kernel<N, KCB, F8>;
   cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "conv_tc shared memory attribute");
   const int grid = std::min(p.n_tiles, Cfg::kCtas * ctx->num_sms);
-  ART_LAUNCH_PDL(ctx, F8 ? "conv_tc_fp8" : "conv_tc", kfn, grid, kThreads, Cfg::kSmem, tmA, tmB, p);
+  ART_LAUNCH_PDL(ctx, F8 ? "conv_tc_fp8" : "conv_tc", kfn, grid, kThreads, Cfg::kSmem, tmA, tmB, tmU, p);
   return ART_OK;
 }
 
@@ -1009,16 +1072,27 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() { return encode_fn() ? g_
 bool tc_conv_ok(const TcConv& c) {
   const bool n_ok = c.cout == 32 || c.cout == 64 || c.cout == 128 || c.cout == 256;
   const int al = c.f8 ? 16 : 8;  // 16-byte aligned output rows and channel offsets
-  // x-phase split output: BF16 through the row-blocked kernel's staged stores, even widths
-  const bool ps_ok = !c.psplit || (!c.f8 && !c.up2 && !c.rgba && c.W % 2 == 0 && (c.cout == 32 || c.cout == 64));
+  // x-phase split output: BF16 through the staged stores, even widths
+  const bool ps_ok = !c.psplit || (!c.f8 && !c.up2 && !c.rgba && c.W % 2 == 0);
+  // sub-pixel decoder convolution: BF16, dense output, 32-channel chunks of both parts
+  const bool sub_ok = !c.sub || (!c.f8 && !c.up2 && !c.rgba && !c.pool && !c.psplit && c.ch_off == 0 &&
+                                 c.ld_out == c.cout && c.H % 2 == 0 && c.W % 2 == 0 && c.cs % 32 == 0 &&
+                                 c.cu % 32 == 0 && c.cs > 0 && c.cu > 0 && c.cin == c.cs + c.cu);
   return n_ok && (c.cin % 32 == 0) && c.cin >= 32 && (c.ld_out % al == 0) && (c.ch_off % al == 0) &&
-         (!c.rgba || c.cout == 32) && ps_ok && encode_fn();
+         (!c.rgba || c.cout == 32) && ps_ok && sub_ok && encode_fn();
 }
 
 art_status launch_tc_conv(art_ctx* ctx, const TcConv& c) {
   if (!tc_conv_ok(c)) return fail(ctx, ART_ERR_UNSUPPORTED, "tensor-core conv: unsupported shape");
-  if (c.psplit && !(9 * c.cin * c.cout * 2 <= kRowsMaxWeights && ctx->conv_rows))
-    return fail(ctx, ART_ERR_UNSUPPORTED, "x-phase split output: row-blocked kernel only");
+  if (c.sub) {  // the tap-by-tap kernel over sub-pixel tiles
+    const bool k64 = c.cs % 64 == 0 && c.cu % 64 == 0;
+    switch (c.cout) {
+      case 32: return k64 ? launch_typed<32, 128, false>(ctx, c) : launch_typed<32, 64, false>(ctx, c);
+      case 64: return k64 ? launch_typed<64, 128, false>(ctx, c) : launch_typed<64, 64, false>(ctx, c);
+      case 128: return k64 ? launch_typed<128, 128, false>(ctx, c) : launch_typed<128, 64, false>(ctx, c);
+      default: return k64 ? launch_typed<256, 128, false>(ctx, c) : launch_typed<256, 64, false>(ctx, c);
+    }
+  }
   if (c.f8) {  // row bytes = channels per K chunk: 128, 64 or 32
     const int kcb = c.cin % 128 == 0 ? 128 : (c.cin % 64 == 0 ? 64 : 32);
     if ((c.cout == 32 || c.cout == 64) && 9 * c.cin * c.cout <= kRowsMaxWeightsF8 && ctx->conv_rows &&
@@ -1062,15 +1136,16 @@ art_status launch_tc_conv(art_ctx* ctx, const TcConv& c) {
     default: st = k64 ? launch_typed<256, 128, false>(ctx, c) : launch_typed<256, 64, false>(ctx, c); break;
   }
   if (st == ART_OK && c.pool)
-    launch_pool_bf16(ctx, (const __nv_bfloat16*)c.out, c.ld_out, c.ch_off, (__nv_bfloat16*)c.pool, c.H, c.W, c.cout);
+    launch_pool_bf16(ctx, (const __nv_bfloat16*)c.out, c.ld_out, c.ch_off, (__nv_bfloat16*)c.pool, c.H, c.W, c.cout,
+                     c.psplit);
   return st;
 }
 
 void launch_pool_bf16(art_ctx* ctx, const __nv_bfloat16* in, int ld, int ch_off, __nv_bfloat16* out, int H, int W,
-                      int C) {
+                      int C, int psplit) {
   const int64_t total = (int64_t)(H / 2) * (W / 2) * (C / 8);
   const int grid = (int)std::min<int64_t>((total + 255) / 256, (int64_t)ctx->num_sms * 8);
-  ART_LAUNCH(ctx, "maxpool2_bf16", maxpool2_bf16_kernel, grid, 256, 0, in, ld, ch_off, out, H, W, C);
+  ART_LAUNCH(ctx, "maxpool2_bf16", maxpool2_bf16_kernel, grid, 256, 0, in, ld, ch_off, out, H, W, C, psplit);
 }
 
 namespace {

@@ -101,6 +101,9 @@ struct ConvLayer {
   // low-resolution part; sub_cs / sub_cu = their input channels
   __nv_bfloat16* wsub = nullptr;
   int sub_cs = 0, sub_cu = 0;
+  // ... of levels 1 and up (the tap-by-tap kernel, TcConv::sub): per output
+  // phase [4][cout][9 cs + 4 cu]
+  __nv_bfloat16* wtap = nullptr;
   uint8_t* w8 = nullptr;       // [cout][k*k*cin] E4M3
   float* wscale = nullptr;     // [cout] FP8 per-output-channel scale
 };
@@ -407,9 +410,16 @@ struct TcConv {
   // (BF16 or E4M3; fused into the row-blocked kernel's epilogue, else a pass of its own)
   void* pool = nullptr;
   // BF16 output stored x-phase split: row y holds the even pixels, then the
-  // odd ones ([H][2][W/2][ld_out]), the layout launch_sub_conv reads its
-  // skip input in (row-blocked kernel, BF16 only)
+  // odd ones ([H][2][W/2][ld_out]), the layout the sub-pixel decoder
+  // convolutions read their skip input in (BF16 only)
   int psplit = 0;
+  // sub-pixel decoder convolution over [up2(up) | in] (BF16, tap-by-tap
+  // kernel): H x W is the output; `in` = the skip tensor, x-phase split
+  // ([H][2][W/2][cs]), `up` = the low-resolution tensor ([H/2][W/2][cu]),
+  // w = the layer's wtap blocks, cin = cs + cu; dense [H][W][cout] output
+  int sub = 0;
+  const void* up = nullptr;
+  int cs = 0, cu = 0;
   // FP8 (E4M3) network: operands and output in E4M3; the accumulator is
   // dequantised by in_scale x w_scale[co], the output quantised by out_scale
   // and its max |value| recorded in out_amax (float bits).
@@ -444,9 +454,14 @@ size_t sub_weight_elems(int cs, int cu);
 // Builds wsub from the layer's FP32 weights [32][3][3][cu + cs] (channels
 // of the low-resolution part first, as in the concatenation).
 void launch_sub_weights(art_ctx* ctx, const float* w32, int cs, int cu, __nv_bfloat16* wsub);
+// The per-phase weights of the tap-by-tap sub-pixel form from the FP32
+// weights [cout][3][3][cu + cs]: [4][cout][9 cs + 4 cu], per output phase
+// (py, px) the skip part's 9 taps (W[dy][dx][cu + ci]) then the 4 summed
+// taps of the low-resolution part ((oy, ox) in {py - 1, py} x {px - 1, px}).
+void launch_sub_tap_weights(art_ctx* ctx, const float* w32, int cout, int cs, int cu, __nv_bfloat16* wtap);
 art_status launch_sub_conv(art_ctx* ctx, const SubConv& c);
 void launch_pool_bf16(art_ctx* ctx, const __nv_bfloat16* in, int ld, int ch_off, __nv_bfloat16* out, int H, int W,
-                      int C);
+                      int C, int psplit = 0);
 void launch_pool_fp8(art_ctx* ctx, const uint8_t* in, int ld, int ch_off, uint8_t* out, int H, int W, int C);
 void launch_quantize_weights(art_ctx* ctx, const float* w, int cout, int K, uint8_t* w8, float* scale);
 void launch_quantize_input(art_ctx* ctx, const __nv_bfloat16* in, int64_t m, const float* scale, uint8_t* out,

@@ -14,10 +14,12 @@ def test_unet_flops_by_hand():
     want = sum(2 * (H >> l) * (W >> l) * co * ci * 9 for l, co, ci in convs) + 2 * H * W * 4 * 32
     assert bench.unet_flops(H, W) == want
     assert abs(want / 1e9 - 357.4) < 0.5
-    # executed by the BF16 network: level 0's decoder convolution over [up2(d1) (64) | e0 (32)]
-    # takes 9 taps of the 32 skip channels and 4 of the 64 low-resolution ones per output pixel
-    d0a_plain, d0a_sub = 2 * H * W * 32 * 96 * 9, 2 * H * W * 32 * (32 * 9 + 64 * 4)
-    assert bench.unet_flops(H, W, subpixel=True) == want - d0a_plain + d0a_sub
+    # executed by the BF16 network: each decoder block's first convolution over [up2(d) | e]
+    # takes 9 taps of the skip channels and 4 of the low-resolution ones per output pixel
+    sub = [(l, co, cs, cu) for l, co, cs, cu in ((2, 128, 128, 256), (1, 64, 64, 128), (0, 32, 32, 64))]
+    plain = sum(2 * (H >> l) * (W >> l) * co * (cs + cu) * 9 for l, co, cs, cu in sub)
+    subp = sum(2 * (H >> l) * (W >> l) * co * (cs * 9 + cu * 4) for l, co, cs, cu in sub)
+    assert bench.unet_flops(H, W, subpixel=True) == want - plain + subp
 
 
 def test_roofline_of_the_convolutions():

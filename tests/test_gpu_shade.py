@@ -49,7 +49,8 @@ def test_tiny_net_f32_matches_oracle():
     assert np.abs(out - rgba_or).max() < TOL_F32
 
 
-@pytest.mark.parametrize("H,W", [(64, 64), (96, 160)])
+# (136, 264): ragged tails of the FP32 kernel's 256- and 128-pixel row tiles at every level
+@pytest.mark.parametrize("H,W", [(64, 64), (96, 160), (136, 264)])
 def test_unet_f32_matches_oracle(H, W):
     import paper_2202_05628_gb300 as art
     rng = np.random.default_rng(H + W)
@@ -70,8 +71,8 @@ def _unet_bf16_emulated(F, layers):
     """FP64 U-Net that rounds to BF16 exactly where the tensor-core path
     stores BF16: the input, the 3x3 weights and every stored activation; the
     1x1 head reads the last convolution's FP32 output (fused epilogue).  The
-    first convolution of the level-0 decoder block runs in its sub-pixel
-    form (helpers.subpixel_cat_conv)."""
+    first convolution of every decoder block runs in its sub-pixel form
+    (helpers.subpixel_cat_conv)."""
     import torch
     import torch.nn.functional as Fn
     bf = lambda t: t.to(torch.bfloat16).to(torch.float64)
@@ -84,8 +85,8 @@ def _unet_bf16_emulated(F, layers):
     e1 = bf(conv(bf(conv(Fn.max_pool2d(e0, 2), 2)), 3))
     e2 = bf(conv(bf(conv(Fn.max_pool2d(e1, 2), 4)), 5))
     e3 = bf(conv(bf(conv(Fn.max_pool2d(e2, 2), 6)), 7))
-    d2 = bf(conv(bf(conv(torch.cat([up(e3), e2], 1), 8)), 9))
-    d1 = bf(conv(bf(conv(torch.cat([up(d2), e1], 1), 10)), 11))
+    d2 = bf(conv(bf(subpixel_cat_conv(e3, e2, layers[8])), 9))
+    d1 = bf(conv(bf(subpixel_cat_conv(d2, e1, layers[10])), 11))
     d0 = conv(bf(subpixel_cat_conv(d1, e0, layers[12])), 13)  # FP32 in the fused epilogue
     wh = torch.from_numpy(layers[14][0].astype(np.float64)).to(torch.bfloat16).to(torch.float64)
     head = Fn.conv2d(d0, wh.permute(0, 3, 1, 2), torch.from_numpy(layers[14][1].astype(np.float64)))
@@ -276,7 +277,7 @@ def _shade_two(r, F, A, cam, F_dtype):
     return out.cpu().numpy()
 
 
-@pytest.mark.parametrize("H,W", [(64, 64), (96, 160)])
+@pytest.mark.parametrize("H,W", [(64, 64), (96, 160), (136, 264)])
 def test_two_branch_f32_matches_oracle(H, W):
     """The paper's two-branch G (appearance U-Net F -> I_f, opacity U-Net
     [A, I_f] -> alpha) in FP32 against the oracle's composition."""
