@@ -268,6 +268,8 @@ def roofline(kt, stats, peaks, form, n_vox, C, frames, conv_launch_ms=None):
             from paper_2202_05628_gb300.profile_capture import committed_traffic
             traffic = committed_traffic()
         out.update(bound=bound, achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak, traffic=traffic, peak_is=note)
+        if flops != out["flops_plain_definition"]:  # the same launches credited with the plain definition's FLOPs
+            out["frac_plain_definition"] = ach * out["flops_plain_definition"] / flops / peak
     else:
         fb = 2 if storage == "bf16" else 4
         inst = stats["instances"]

@@ -29,6 +29,7 @@ def test_roofline_of_the_convolutions():
     r = bench.roofline(kt, {"instances": 900000}, peaks, "bf16_skip", 1000000, 32, frames)
     per_launch = bench.unet_flops(1024, 1024, subpixel=True) / 14  # (the BF16 network executes the sub-pixel form)
     assert r["flops_plain_definition"] == bench.unet_flops(1024, 1024)
+    assert math.isclose(r["frac_plain_definition"] / r["frac"], bench.unet_flops(1024, 1024) / (per_launch * 14))
     assert r["kernel"] == "conv_tc" and r["bound"] == "tensor" and r["unit"] == "TFLOP/s"
     assert math.isclose(r["achieved"], per_launch / 0.05e-3 / 1e12, rel_tol=1e-12)
     assert math.isclose(r["frac"], r["achieved"] / 1713.7, rel_tol=1e-12)
