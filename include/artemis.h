@@ -366,6 +366,11 @@ typedef struct {
                               (canonical origin, leaf size h) that holds it, the smallest voxel id of a
                               cell survives, and each occupied cell renders as its axis-aligned leaf box
                               with its survivor's feature and density (forward only; no SH features) */
+  int no_subpixel;         /* BF16 U-Net: 0 (default) runs each decoder block's first convolution over
+                              [up2(d) | e] in its sub-pixel form (per output phase, 9 taps of e and 4 taps
+                              of the low-resolution d with summed weights, which are rounded to BF16 once);
+                              1 runs it over the 2x2-replicated concatenation (the same function, another
+                              rounding of the weights, more work) */
 } art_config;
 
 enum { ART_INDEX_BOXES = 0, ART_INDEX_GRID = 1 };

@@ -43,7 +43,8 @@ class NetDesc(ctypes.Structure):
 class Config(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_float), ("instance_cap", ctypes.c_int64), ("tile_log2", ctypes.c_int),
                 ("profile", ctypes.c_int), ("skip", ctypes.c_int), ("max_missed", ctypes.c_float),
-                ("margin", ctypes.c_int), ("segment", ctypes.c_int), ("index", ctypes.c_int)]
+                ("margin", ctypes.c_int), ("segment", ctypes.c_int), ("index", ctypes.c_int),
+                ("no_subpixel", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -153,9 +154,9 @@ class Renderer:
     # ----------------------------------------------------------------- setup
     def set_config(self, tau: float = 1e-4, instance_cap: int = 0, tile_log2: int = 3, profile: bool = False,
                    skip: int = SKIP_PLAIN, max_missed: float = 1e-3, margin: int = 0, segment: int = 256,
-                   index: int = 0):
+                   index: int = 0, no_subpixel: bool = False):
         c = Config(tau, instance_cap, tile_log2, int(profile), int(skip), float(max_missed), int(margin),
-                   int(segment), int(index))
+                   int(segment), int(index), int(no_subpixel))
         self._check(_lib.art_set_config(self._h, ctypes.byref(c)))
 
     def load_octree(self, depth: int, origin, extent: float, ijk, joint_idx, weights, features, density,

@@ -221,6 +221,7 @@ art_config default_config() {
   c.margin = 0;
   c.segment = 256;
   c.index = ART_INDEX_BOXES;
+  c.no_subpixel = 0;
   return c;
 }
 
@@ -376,6 +377,7 @@ art_status art_set_config(art_ctx* ctx, const art_config* cfg) {
   if (c.segment == 0) c.segment = 256;
   if (c.segment < 32 || c.segment > (1 << 24)) return fail(ctx, ART_ERR_INVALID_ARG, "segment must be in [32, 2^24]");
   if (c.index != ART_INDEX_BOXES && c.index != ART_INDEX_GRID) return fail(ctx, ART_ERR_INVALID_ARG, "index %d", c.index);
+  if (c.no_subpixel != 0 && c.no_subpixel != 1) return fail(ctx, ART_ERR_INVALID_ARG, "no_subpixel must be 0 or 1");
   if (c.index != ctx->cfg.index) ctx->posed = false;  // the records of the last pose follow the other index
   ctx->cfg = c;
   ctx->seg_len = c.segment;

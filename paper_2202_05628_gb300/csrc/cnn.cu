@@ -491,7 +491,7 @@ art_status unet_tc(art_ctx* ctx, int H, int W, const __nv_bfloat16* in, int cin,
   // their low-resolution input, both in cat_l's space
   bool sub[4] = {};
   __nv_bfloat16 *sk[4] = {}, *ul[4] = {};
-  for (int l = 0; l + 1 < levels; ++l) {
+  for (int l = 0; l + 1 < levels && !ctx->cfg.no_subpixel; ++l) {
     const ConvLayer& L = Ls[lb + 2 * levels + 2 * (levels - 2 - l)];
     const int h = H >> l, w = W >> l;
     if (l == 0) {
@@ -509,8 +509,10 @@ art_status unet_tc(art_ctx* ctx, int H, int W, const __nv_bfloat16* in, int cin,
       t.ld_out = L.cout;
       sub[l] = L.wtap && L.sub_cs == ch[l] && L.sub_cu == ch[l + 1] && tc_conv_ok(t);
     }
+  }
+  for (int l = 0; l + 1 < levels; ++l) {
     sk[l] = cat[l];
-    ul[l] = (__nv_bfloat16*)((char*)cat[l] + align256((size_t)h * w * ch[l] * 2));
+    ul[l] = (__nv_bfloat16*)((char*)cat[l] + align256((size_t)(H >> l) * (W >> l) * ch[l] * 2));
   }
   int psplit = 0;
   auto conv = [&](const __nv_bfloat16* x, int xc, int l, int li, __nv_bfloat16* o, int ld, int o_off, int up2,

@@ -129,19 +129,27 @@ __device__ __forceinline__ void epi_row(const TcParams& p, uint32_t taddr, int y
     if (p.rgba) {  // fused 1x1 head (N == 32) + sigmoid -> head_n FP32 channels of the output
       float o[4];
       const float4* hw = reinterpret_cast<const float4*>(s_head + c0);  // 16-B aligned rows of N weights
+      // two partial sums per output: eight independent FMA chains of 16
+      float a0[4], a1[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        float acc = s_head[4 * N + k];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const float4 w = hw[k * (N / 4) + q];
-          acc = fmaf(w.x, v[4 * q], acc);
-          acc = fmaf(w.y, v[4 * q + 1], acc);
-          acc = fmaf(w.z, v[4 * q + 2], acc);
-          acc = fmaf(w.w, v[4 * q + 3], acc);
-        }
-        o[k] = __frcp_rn(1.0f + __expf(-acc));  // (fast exponential: relative error ~1e-6 on a [0, 1] output)
+        a0[k] = s_head[4 * N + k];
+        a1[k] = 0.0f;
       }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const float4 w = hw[k * (N / 4) + q];
+          a0[k] = fmaf(w.x, v[4 * q], a0[k]);
+          a1[k] = fmaf(w.y, v[4 * q + 1], a1[k]);
+          a0[k] = fmaf(w.z, v[4 * q + 2], a0[k]);
+          a1[k] = fmaf(w.w, v[4 * q + 3], a1[k]);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        o[k] = __frcp_rn(1.0f + __expf(-(a0[k] + a1[k])));  // (fast exponential: relative error ~1e-6 on a [0, 1] output)
       float* dst = p.rgba + (size_t)(y * p.W + x) * p.head_ld + p.head_off;
       if (p.head_n == 4 && p.head_ld == 4) {
         *reinterpret_cast<float4*>(dst) = make_float4(o[0], o[1], o[2], o[3]);

@@ -67,12 +67,13 @@ def test_unet_f32_matches_oracle(H, W):
     assert np.abs(rgba - ref).max() < TOL_F32
 
 
-def _unet_bf16_emulated(F, layers):
+def _unet_bf16_emulated(F, layers, subpixel=True):
     """FP64 U-Net that rounds to BF16 exactly where the tensor-core path
     stores BF16: the input, the 3x3 weights and every stored activation; the
     1x1 head reads the last convolution's FP32 output (fused epilogue).  The
     first convolution of every decoder block runs in its sub-pixel form
-    (helpers.subpixel_cat_conv)."""
+    (helpers.subpixel_cat_conv), or over the concatenation (subpixel=False,
+    the library's art_config.no_subpixel)."""
     import torch
     import torch.nn.functional as Fn
     bf = lambda t: t.to(torch.bfloat16).to(torch.float64)
@@ -85,16 +86,20 @@ def _unet_bf16_emulated(F, layers):
     e1 = bf(conv(bf(conv(Fn.max_pool2d(e0, 2), 2)), 3))
     e2 = bf(conv(bf(conv(Fn.max_pool2d(e1, 2), 4)), 5))
     e3 = bf(conv(bf(conv(Fn.max_pool2d(e2, 2), 6)), 7))
-    d2 = bf(conv(bf(subpixel_cat_conv(e3, e2, layers[8])), 9))
-    d1 = bf(conv(bf(subpixel_cat_conv(d2, e1, layers[10])), 11))
-    d0 = conv(bf(subpixel_cat_conv(d1, e0, layers[12])), 13)  # FP32 in the fused epilogue
+    if subpixel:
+        cat = lambda d, e, i: subpixel_cat_conv(d, e, layers[i])
+    else:
+        cat = lambda d, e, i: conv(torch.cat([up(d), e], 1), i)
+    d2 = bf(conv(bf(cat(e3, e2, 8)), 9))
+    d1 = bf(conv(bf(cat(d2, e1, 10)), 11))
+    d0 = conv(bf(cat(d1, e0, 12)), 13)  # FP32 in the fused epilogue
     wh = torch.from_numpy(layers[14][0].astype(np.float64)).to(torch.bfloat16).to(torch.float64)
     head = Fn.conv2d(d0, wh.permute(0, 3, 1, 2), torch.from_numpy(layers[14][1].astype(np.float64)))
     return torch.sigmoid(head)[0].permute(1, 2, 0).numpy()
 
 
-@pytest.mark.parametrize("H,W", [(64, 64), (136, 264)])
-def test_unet_bf16_tensor_cores_match_emulation(H, W):
+@pytest.mark.parametrize("H,W,subpixel", [(64, 64, True), (136, 264, True), (136, 264, False)])
+def test_unet_bf16_tensor_cores_match_emulation(H, W, subpixel):
     """Every 3x3 layer on tcgen05 (BF16 x BF16 -> FP32): equal to the emulated
     BF16 network up to FP32 summation order and the BF16 roundings it flips."""
     import paper_2202_05628_gb300 as art
@@ -102,9 +107,10 @@ def test_unet_bf16_tensor_cores_match_emulation(H, W):
     F = (rng.standard_normal((H, W, 32)) * 0.3).astype(np.float32)
     F[rng.uniform(size=(H, W)) < 0.3] = 0.0
     layers = sg.unet_weights(5, cin=32)
-    ref = _unet_bf16_emulated(F, layers)
+    ref = _unet_bf16_emulated(F, layers, subpixel)
     sc = sg.preset("mini")
     r = renderer(sc, profile=True)
+    r.set_config(profile=True, no_subpixel=not subpixel)
     cam = sg.orbit_camera(sc.centroid, W, H)
     set_cam(r, 0, cam)
     r.load_shader(art.ART_NET_UNET, 32, sg.UNET_CHANNELS, 4, art.flat_params(layers), "bf16")
