@@ -117,8 +117,20 @@ __device__ __forceinline__ void sh_feature(const SkipArgs& sk, uint32_t vid, flo
 #pragma unroll
   for (int h = 0; h < kShMaxBases; ++h) {
     if (h < H) {
+      if constexpr (C % 4 == 0) {  // 16-byte loads (the rows of [n][H][C] stay 16-byte aligned)
+        const float4* k4 = reinterpret_cast<const float4*>(k + h * C);
 #pragma unroll
-      for (int c = 0; c < C; ++c) f[c] = fmaf(__ldg(k + h * C + c), Y[h], f[c]);
+        for (int q = 0; q < C / 4; ++q) {
+          const float4 w = __ldg(k4 + q);
+          f[4 * q] = fmaf(w.x, Y[h], f[4 * q]);
+          f[4 * q + 1] = fmaf(w.y, Y[h], f[4 * q + 1]);
+          f[4 * q + 2] = fmaf(w.z, Y[h], f[4 * q + 2]);
+          f[4 * q + 3] = fmaf(w.w, Y[h], f[4 * q + 3]);
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < C; ++c) f[c] = fmaf(__ldg(k + h * C + c), Y[h], f[c]);
+      }
     }
   }
 }
