@@ -126,6 +126,34 @@ def test_unet_bf16_tensor_cores_match_emulation(H, W, subpixel):
     assert psnr(rgba, ref) > 60.0
 
 
+def test_unet_bf16_subpixel_matches_concatenated_at_1024():
+    """At the workload's 1024^2 (sub-pixel tiles: 4 segments per row at
+    level 0, 2 at level 1) the sub-pixel decoder convolutions and the
+    concatenated ones agree to BF16 rounding on a seeded input with a covered
+    disc; an indexing slip in a tile beyond the first would give ~20-30 dB."""
+    import torch
+    import paper_2202_05628_gb300 as art
+    n = 1024
+    rng = np.random.default_rng(n)
+    F = (rng.standard_normal((n, n, 32)) * 0.5).astype(np.float32)
+    yy, xx = np.mgrid[0:n, 0:n]
+    F[(yy - n // 2) ** 2 + (xx - n // 2 + 7) ** 2 > (n // 5) ** 2] = 0.0
+    layers = sg.unet_weights(0, cin=32)
+    sc = sg.preset("mini")
+    cam = sg.orbit_camera(sc.centroid, n, n)
+    outs = []
+    for no_sub in (False, True):
+        r = renderer(sc)
+        r.set_config(no_subpixel=no_sub)
+        set_cam(r, 0, cam)
+        r.load_shader(art.ART_NET_UNET, 32, sg.UNET_CHANNELS, 4, art.flat_params(layers), "bf16")
+        outs.append(_shade(r, 0, F, cam, F_dtype="bf16"))
+        r.close()
+    d = np.abs(outs[0] - outs[1])
+    print(f"sub-pixel vs concatenated at 1024^2: PSNR {psnr(outs[0], outs[1]):.1f} dB, max {d.max():.2e}")
+    assert psnr(outs[0], outs[1]) > 50.0 and d.max() < 5e-2
+
+
 def _e4m3_codes(x32):
     """Round-to-nearest-even to E4M3 with saturation at +-448: the byte codes."""
     import torch
