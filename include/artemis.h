@@ -287,6 +287,28 @@ art_status art_render_views(art_ctx* ctx, int nv, const int* views, void* const*
 art_status art_render_frame(art_ctx* ctx, int view, const float* axis_angle, const float R[3], const float T[3],
                             float* rgba_out);
 
+/*
+ * The frame of art_render_frame with a HOST rgba_out ([H][W][cout] float),
+ * without waiting for it (a frame loop that overlaps frame k's copy to the
+ * host and the host's queueing of frame k + 1 with the GPU's work; Sec. 5's
+ * per-frame order pose -> LBS -> tracing -> shading is unchanged).  The call
+ * queues the pose upload, the render and the network into one of two
+ * library-owned device slots, then the slot's copy to rgba_out on a second
+ * stream, and returns.  At most two frames are in flight: a third call first
+ * waits for the oldest frame's copy.  rgba_out, and the pose arrays when they
+ * are pinned host memory (read when their copy runs), must stay valid and
+ * unchanged until art_wait_frames returns; rgba_out should be pinned (a
+ * pageable buffer makes the copy synchronous).  Errors of the queued work
+ * are reported by art_wait_frames (or a later call); ART_ERR_INVALID_ARG for
+ * a device rgba_out.
+ */
+art_status art_render_frame_async(art_ctx* ctx, int view, const float* axis_angle, const float R[3], const float T[3],
+                                  float* rgba_out);
+
+/* Waits until every frame queued by art_render_frame_async has reached its
+ * host buffer and the library's stream is idle; returns the first error. */
+art_status art_wait_frames(art_ctx* ctx);
+
 /* ------------------------------------------- learned ray-interval proposal */
 
 /*

@@ -73,6 +73,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "art_load_shader": [vp, ctypes.POINTER(NetDesc), vp, i64, i32],
         "art_shade": [vp, i32, vp, i32, vp],
         "art_render_frame": [vp, i32, vp, vp, vp, vp],
+        "art_render_frame_async": [vp, i32, vp, vp, vp, vp],
+        "art_wait_frames": [vp],
         "art_set_config": [vp, ctypes.POINTER(Config)],
         "art_sync_status": [vp, ctypes.POINTER(Stats)],
         "art_get_kernel_times": [vp, i32, vp, vp, vp, ctypes.POINTER(i32), i32],
@@ -224,6 +226,18 @@ class Renderer:
         R = R if hasattr(R, "data_ptr") else _np(R, np.float32)
         T = T if hasattr(T, "data_ptr") else _np(T, np.float32)
         self._check(_lib.art_render_frame(self._h, view, _ptr(aa), _ptr(R), _ptr(T), _ptr(rgba_out)))
+
+    def render_frame_async(self, view: int, axis_angle, R, T, rgba_out):
+        """art_render_frame_async: queue a frame whose RGBA is copied into the
+        host buffer rgba_out (pinned for an asynchronous copy); rgba_out and
+        pinned pose tensors must stay unchanged until wait_frames()."""
+        aa = axis_angle if hasattr(axis_angle, "data_ptr") else _np(axis_angle, np.float32)
+        R = R if hasattr(R, "data_ptr") else _np(R, np.float32)
+        T = T if hasattr(T, "data_ptr") else _np(T, np.float32)
+        self._check(_lib.art_render_frame_async(self._h, view, _ptr(aa), _ptr(R), _ptr(T), _ptr(rgba_out)))
+
+    def wait_frames(self):
+        self._check(_lib.art_wait_frames(self._h))
 
     def update_voxels(self, features=None, density=None, weights=None):
         self._check(_lib.art_update_voxels(self._h, _ptr(features), _ptr(density), _ptr(weights)))

@@ -208,6 +208,12 @@ void free_all(art_ctx* ctx) {
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   if (ctx->ev_pose) cudaEventDestroy(ctx->ev_pose);
   if (ctx->side) cudaStreamDestroy(ctx->side);
+  for (int k = 0; k < 2; ++k) {
+    if (ctx->d_rgba_slot[k]) cudaFree(ctx->d_rgba_slot[k]);
+    if (ctx->ev_ready[k]) cudaEventDestroy(ctx->ev_ready[k]);
+    if (ctx->ev_done[k]) cudaEventDestroy(ctx->ev_done[k]);
+  }
+  if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
 }
 
 art_config default_config() {
@@ -351,6 +357,7 @@ void art_destroy(art_ctx* ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->stream);
   if (ctx->side) cudaStreamSynchronize(ctx->side);
+  if (ctx->copy_stream) cudaStreamSynchronize(ctx->copy_stream);
   free_all(ctx);
   delete ctx;
 }
@@ -1052,6 +1059,66 @@ art_status art_render_frame(art_ctx* ctx, int view, const float* axis_angle, con
   if ((st = ensure(ctx, (void**)&ctx->d_A, &ctx->d_A_bytes, (size_t)v.W * v.H * 4, "A buffer")) != ART_OK) return st;
   if ((st = render_to_device(ctx, view, ctx->d_F, fdt, ctx->d_A)) != ART_OK) return st;
   return shade_impl(ctx, view, ctx->d_F, fdt, ctx->d_A, rgba_out);
+}
+
+namespace {
+// Waits for the oldest frame in flight of art_render_frame_async (its RGBA
+// has reached the host) and drops it from the ring.
+art_status wait_oldest_frame(art_ctx* ctx) {
+  const int s = ctx->fr_head;
+  const cudaError_t e = cudaEventSynchronize(ctx->ev_done[s]);
+  ctx->fr_head = (ctx->fr_head + 1) % 2;
+  --ctx->fr_n;
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "render_frame_async (copy out)");
+  return ART_OK;
+}
+}  // namespace
+
+art_status art_render_frame_async(art_ctx* ctx, int view, const float* axis_angle, const float R[3], const float T[3],
+                                  float* rgba_out) {
+  if (!ctx) return ART_ERR_INVALID_ARG;
+  if (!rgba_out) return fail(ctx, ART_ERR_INVALID_ARG, "rgba_out is null");
+  if (is_device_ptr(rgba_out))
+    return fail(ctx, ART_ERR_INVALID_ARG, "render_frame_async copies to a host buffer (art_render_frame takes device buffers)");
+  if (ctx->layers.empty()) return fail(ctx, ART_ERR_STATE, "render_frame_async before load_shader");
+  if (view < 0 || view >= kMaxViews || !ctx->view_set[view]) return fail(ctx, ART_ERR_STATE, "view %d not set", view);
+  art_status st;
+  if (!ctx->copy_stream) {
+    cudaError_t e = cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+      e = cudaEventCreateWithFlags(&ctx->ev_ready[k], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_done[k], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "copy stream");
+  }
+  // two frames in flight at most: a third waits for the oldest's copy
+  if (ctx->fr_n == 2 && (st = wait_oldest_frame(ctx)) != ART_OK) return st;
+  const int slot = (ctx->fr_head + ctx->fr_n) % 2;  // (its last copy has landed)
+  const ViewParams& v = ctx->views[view];
+  const size_t obytes = (size_t)v.W * v.H * ctx->net.cout * 4;
+  if ((st = ensure(ctx, (void**)&ctx->d_rgba_slot[slot], &ctx->d_rgba_slot_bytes[slot], obytes, "rgba slot")) != ART_OK)
+    return st;
+  // the frame into the device slot (no synchronisation), then its copy on the copy stream
+  if ((st = art_render_frame(ctx, view, axis_angle, R, T, ctx->d_rgba_slot[slot])) != ART_OK) return st;
+  cudaError_t e = cudaEventRecord(ctx->ev_ready[slot], ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_ready[slot], 0);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(rgba_out, ctx->d_rgba_slot[slot], obytes, cudaMemcpyDeviceToHost, ctx->copy_stream);
+  if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_done[slot], ctx->copy_stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "render_frame_async (copy out)");
+  ++ctx->fr_n;
+  return ART_OK;
+}
+
+art_status art_wait_frames(art_ctx* ctx) {
+  if (!ctx) return ART_ERR_INVALID_ARG;
+  art_status st = ART_OK;
+  while (ctx->fr_n > 0) {
+    const art_status s2 = wait_oldest_frame(ctx);
+    if (st == ART_OK) st = s2;
+  }
+  if (st != ART_OK) return st;
+  return sync_check(ctx, "wait_frames");
 }
 
 art_status art_sync_status(art_ctx* ctx, art_stats* out) {

@@ -127,6 +127,14 @@ struct art_ctx {
   // clear of the empty tiles), forked from and joined into `stream` by events
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_pose = nullptr;
+  // frames in flight of art_render_frame_async: their RGBA in two device
+  // slots, copied to the host on copy_stream (ev_ready: the slot is written;
+  // ev_done: its copy has landed); frame k of the ring is slot (head + k) % 2
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_ready[2] = {}, ev_done[2] = {};
+  float* d_rgba_slot[2] = {};
+  size_t d_rgba_slot_bytes[2] = {};
+  int fr_head = 0, fr_n = 0;
   bool pose_bias_side = false;  // the proposal's pose bias is being computed on the side stream
   bool f_cleared = false;  // the empty tiles of this frame's F and A are cleared already
   std::string err;
