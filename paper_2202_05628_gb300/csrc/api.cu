@@ -260,8 +260,8 @@ art_status ensure_bin_buffers(art_ctx* ctx, int64_t ntiles) {
 }
 
 // Buffers of the coarse check (per-voxel bins and bounds, per-tile histogram,
-// fallback queue) and of the proposal bins, for `view`; the histogram is
-// zeroed on the stream.
+// the queue of tiles for the sequential walk) and of the proposal bins, for
+// `view`; the histogram is zeroed on the stream.
 art_status ensure_skip_buffers(art_ctx* ctx, const ViewParams& v) {
   art_status st;
   if (ctx->hist_n_cap < ctx->n) {
@@ -285,7 +285,8 @@ art_status ensure_skip_buffers(art_ctx* ctx, const ViewParams& v) {
 // lists and partial sums (segments <= instances / seg_len + tiles).
 art_status ensure_split_buffers(art_ctx* ctx, size_t ntiles) {
   art_status st;
-  const size_t items = (size_t)(ctx->inst_cap / std::max(32, ctx->seg_len / 4)) + ntiles + 1;  // re-walks: seg_len / 4
+  // a tile of len entries is cut into ceil(len / seg_len) <= len / seg_len + 1 segments
+  const size_t items = (size_t)(ctx->inst_cap / std::max(32, ctx->seg_len)) + ntiles + 1;
   if ((st = ensure(ctx, (void**)&ctx->d_seg, &ctx->d_seg_bytes, ntiles * sizeof(uint2), "segment plan")) != ART_OK)
     return st;
   if ((st = ensure(ctx, (void**)&ctx->d_multi, &ctx->d_multi_bytes, ntiles * 4, "split tiles")) != ART_OK) return st;
