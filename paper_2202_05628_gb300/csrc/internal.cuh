@@ -36,7 +36,7 @@ enum StatusWord {
   kStNext = 10,         // next segment to walk (work counter)
   kStNextMerge = 11,    // next split tile to merge (work counter)
   kStRmax = 12,         // largest voxel bounding radius of the last pose (float bits)
-  kStFallback2 = 13,    // (unused)
+  kStReserved13 = 13,   // (reserved)
   kStSortTiles = 14,    // binning: tiles whose bucket needs sorting
   kStSortNext = 15,     // binning: next bucket to sort (work counter)
   kStSortBig = 16,      // binning: buckets sorted by a whole block

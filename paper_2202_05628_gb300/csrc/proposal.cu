@@ -345,19 +345,21 @@ void launch_pose_bias(art_ctx* ctx) {
 
 // Tiles whose walk the proposal cannot change (learned skip).  From a tile's
 // coarse optical-depth bound per depth bin (h, total tot, first and last
-// occupied bins lo, hi) and the check lost = (1 - e^-front) + T_end
-// (1 - e^-back) <= max_missed (front / back: the bins before / after the
-// interval):
+// occupied bins lo, hi) and the check lost = (1 - e^-front) + (1 - e^-back)
+// <= max_missed (front / back: the bins before / after the interval; the
+// transmittance after the interval, T_end <= 1, left out):
 //   - if 1 - e^-tot <= max_missed, the empty interval passes: the tile
 //     composites nothing (class 2);
 //   - if 1 - e^-h[lo] > max_missed, no interval may start after bin lo; if
-//     e^-tot (1 - e^-h[hi]) > max_missed, none may end before bin hi, since
-//     every ray's T_end >= e^-tot (the bound sums every hit's sigma 2 r); with
-//     both, every passing interval covers [lo, hi], which holds all of the
-//     tile's hits: the tile is walked in full without a prediction (class 1).
+//     e^-tot (1 - e^-h[hi]) > max_missed, none may end before bin hi (this
+//     holds even with the check weighted by T_end >= e^-tot, as the bound
+//     sums every hit's sigma 2 r); with both, every passing interval covers
+//     [lo, hi], which holds all of the tile's hits: the tile is walked in full
+//     without a prediction (class 1).
 // Other tiles are predicted (class 0); the groups holding one are listed for
-// the proposal.  Classes 1 and 2 write their pixels' bins (0, 63) and
-// (63, 0): the composite and its check read them as they read predictions.
+// the proposal, whose epilogue applies the check to their intervals.
+// Classes 1 and 2 write their pixels' bins (0, 63) and (63, 0): the
+// composite reads them as it reads predictions.
 __global__ void __launch_bounds__(128) tile_class_kernel(ViewParams v, const uint2* __restrict__ ranges,
                                                         const float* __restrict__ thist,
                                                         const uint32_t* __restrict__ agroups,
